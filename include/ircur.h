@@ -1,0 +1,157 @@
+/*
+ * ircur.h -- C ABI of libircur, a GB300 (sm_103a) implementation of IRCUR
+ * (Iterated Robust CUR) for robust PCA, D = L + S, after Cai, Hamm, Huang,
+ * Li, Wang, "Rapid Robust Principal Component Analysis: CUR Accelerated
+ * Inexact Low Rank Estimation" (arXiv 2010.07422).
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Matrices are FP32, row-major, with an explicit leading dimension (the
+ *   distance in elements between the starts of consecutive rows, >= the
+ *   number of columns).  "device" pointers are CUDA device (or managed)
+ *   memory of the device that was current when the context was created;
+ *   "host" pointers are ordinary host memory (pinned memory is faster).
+ * - The caller owns every buffer it passes in; the library never frees or
+ *   keeps them past the call.  The library owns only its context and the
+ *   workspace the context allocates at creation.
+ * - All device work is issued on the stream given to ircur_create; calls
+ *   return once the work is queued, except where a call says it synchronises.
+ * - Functions return an ircur_status and never abort, throw or print.
+ *   IRCUR_EINVAL leaves the context unchanged; IRCUR_ECUDA means a CUDA call
+ *   failed (ircur_last_error_string gives the CUDA message).
+ * - Index sets are int32, sorted strictly ascending, 0-based.
+ */
+#ifndef IRCUR_H
+#define IRCUR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IRCUR_OK = 0,
+  IRCUR_EINVAL = 1,        /* bad argument, size, pointer alignment, index set, NaN/Inf in D */
+  IRCUR_ENOMEM = 2,        /* workspace allocation failed */
+  IRCUR_ECUDA = 3,         /* a CUDA runtime call failed */
+  IRCUR_ESVD_NOCONV = 4,   /* reserved: the core SVD never returns it as an error (see flags) */
+  IRCUR_ETIMEOUT = 5,      /* a bounded device wait ran out; the context stays usable */
+  IRCUR_ESTATE = 6,        /* call out of order (e.g. factors before any solve) */
+  IRCUR_ENOTSUP = 7        /* parameter combination not built (e.g. r > 16) */
+} ircur_status;
+
+/* ircur_result.flags bits */
+#define IRCUR_FLAG_WRANK 1u        /* some core had numerical rank < r (pinv used that rank) */
+#define IRCUR_FLAG_SVD_NOCONV 2u   /* the core's subspace iteration hit its step cap */
+
+/* Largest rank r this build supports. */
+#define IRCUR_MAX_RANK 16
+
+typedef struct {
+  int64_t n1, n2;    /* D is n1 x n2 (Alg. 1 input D) */
+  int32_t r;         /* target rank r, 1 <= r <= IRCUR_MAX_RANK (Alg. 1) */
+  int32_t nI, nJ;    /* |I|, |J|: r <= nI <= n1, r <= nJ <= n2 (Thm 1 needs |I|,|J| >= r);
+                        0 = ceil(4 r ln n) capped at n (Sec. 3.5, c_I = 4) */
+  double zeta0;      /* initial threshold zeta_0 (Alg. 1); <= 0 means max|D_ij| */
+  double gamma;      /* threshold decay gamma in (0,1) (Alg. 1, Sec. 3.5) */
+  double tol;        /* target precision epsilon > 0: stop once e_k <= tol (Sec. 3.3) */
+  int32_t max_iter;  /* iteration cap, >= 1 (the paper loops until e_k <= tol) */
+  int32_t resample;  /* 0 = IRCUR-F (fixed I,J), 1 = IRCUR-R (fresh I,J each iteration), Sec. 3.4 */
+  uint64_t seed;     /* index-stream seed (used when the caller passes no index sets) */
+  int32_t precision; /* 0 = FP32 (the only value built) */
+  int32_t reserved;  /* must be 0 */
+} ircur_params;
+
+typedef struct {
+  int32_t iters;      /* iterations run, K */
+  int32_t converged;  /* 1 if e_K <= tol */
+  uint32_t flags;     /* IRCUR_FLAG_* */
+  int32_t svd_steps;  /* subspace-iteration steps summed over all iterations */
+  double final_err;   /* e_K, the stopping criterion of Sec. 3.3 */
+  double zeta0;       /* zeta_0 actually used (max|D| when requested) */
+  double zeta_next;   /* gamma^K zeta_0, the threshold ircur_reconstruct uses for S */
+} ircur_result;
+
+typedef struct ircur_ctx ircur_ctx;
+
+/* Create a context for problems of the given shape and parameters and
+ * allocate its device workspace (about 4*(n1 + n2)*(2r + |J| + |I|) bytes
+ * plus max_iter*(|I|+|J|)*4 bytes of index sets).  stream: a cudaStream_t
+ * (NULL = legacy default stream).  Returns EINVAL for out-of-range
+ * parameters, ENOTSUP for r > IRCUR_MAX_RANK or precision != 0, ENOMEM if
+ * the workspace cannot be allocated.  *out is NULL on failure. */
+ircur_status ircur_create(const ircur_params* params, void* stream, ircur_ctx** out);
+
+/* Release the context and its workspace (synchronises the stream first).
+ * NULL is ignored. */
+void ircur_destroy(ircur_ctx* ctx);
+
+/* Run Algorithm 1 on device matrix D (n1 x n2, leading dimension ldD >= n2,
+ * 4-byte aligned; 16-byte alignment of D and ldD % 4 == 0 enable the bulk-copy
+ * paths).  idx_I / idx_J: optional device int32 index sets, each holding
+ * (resample ? max_iter : 1) consecutive sorted sets of nI (resp. nJ)
+ * indices; pass NULL for both to draw them with the library's counter-based
+ * sampler (seed in params).  Both or neither must be given.  Until the loop
+ * ends nothing is read back: the iterations run as one CUDA graph whose
+ * while-node is driven by the device-side stopping test.  On return (the
+ * call synchronises the stream) *out holds the iteration count, e_K, flags.
+ * Errors: EINVAL (bad pointer/ld, unsorted or out-of-range indices, NaN or
+ * Inf in D when zeta0 <= 0), ECUDA, ETIMEOUT. */
+ircur_status ircur_solve(ircur_ctx* ctx, const float* D, int64_t ldD, const int32_t* idx_I,
+                         const int32_t* idx_J, ircur_result* out);
+
+/* Copy the low-rank factors of the last solve into caller buffers (device):
+ * A (n1 x r, row-major, ld = r) and B (r x n2, row-major, ld = n2) with
+ * L = A B = C U^+ R, A = C V_r Sigma_r^{-1}, B = W_r^T R (Thm 1 with
+ * U = H_r(core) = W_r Sigma_r V_r^T).  Either pointer may be NULL.
+ * ESTATE before the first solve. */
+ircur_status ircur_get_factors(ircur_ctx* ctx, float* A, float* B);
+
+/* Copy the index sets the last iteration used (device int32 buffers of nI
+ * and nJ entries) and, if sigma is not NULL, the r singular values of the
+ * last core (device FP32).  ESTATE before the first solve. */
+ircur_status ircur_get_indices(ircur_ctx* ctx, int32_t* I, int32_t* J, float* sigma);
+
+/* Copy the stopping-criterion history e_1..e_K of the last solve into the
+ * host array errs (room for max_iter doubles); synchronises.  Returns the
+ * count in *count.  ESTATE before the first solve. */
+ircur_status ircur_get_errors(ircur_ctx* ctx, double* errs, int32_t* count);
+
+/* Write the dense low-rank part L = C U^+ R of the last solve into L (device,
+ * n1 x n2, ldL >= n2) and, if S is not NULL, the sparse part
+ * S = T_zeta(D - L) with zeta = zeta_next (the threshold the next Phase I
+ * would apply; T is the hard threshold of Sec. 3.2, strict >) into S
+ * (device, ldS >= n2), reading D (device, ldD).  ESTATE before a solve. */
+ircur_status ircur_reconstruct(ircur_ctx* ctx, const float* D, int64_t ldD, float* L, int64_t ldL,
+                               float* S, int64_t ldS);
+
+/* Whole pipeline from host memory: copy D_host (n1 x n2, ld = n2) to the
+ * device, solve, reconstruct, and copy L (and S if S_host is not NULL) back
+ * to host arrays of n1 x n2 (ld = n2).  Device buffers for D, L and S are
+ * allocated on the first call and kept by the context.  Synchronises. */
+ircur_status ircur_solve_host(ircur_ctx* ctx, const float* D_host, float* L_host, float* S_host,
+                              ircur_result* out);
+
+/* The index sampler on its own: write the sorted m-subset of [0, n) that
+ * draw `draw` on axis `axis` (0 = rows, 1 = columns) of the stream `seed`
+ * selects into out (device int32[m]); 1 <= m <= n < 2^31.  Element i gets
+ * key splitmix64(splitmix64(splitmix64(seed) ^ (2 draw + axis)) ^ i) and
+ * the m smallest keys (ties: smaller index first) are kept -- a uniform
+ * m-subset, i.e. uniform sampling of Alg. 1.  stream: cudaStream_t. */
+ircur_status ircur_sample_indices(uint64_t seed, int32_t draw, int32_t axis, int64_t n, int32_t m,
+                                  int32_t* out, void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* ircur_status_string(ircur_status s);
+
+/* Message of the last CUDA error seen by this thread's calls (static
+ * thread-local storage; empty if none). */
+const char* ircur_last_error_string(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IRCUR_H */

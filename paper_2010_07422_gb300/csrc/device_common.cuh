@@ -1,0 +1,105 @@
+// Device helpers shared by the kernels of libircur.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ircur {
+
+// splitmix64 output for state x (Steele, Lea, Flood, OOPSLA 2014): the
+// finaliser applied to x + golden ratio, all arithmetic mod 2^64.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// The low-rank estimate at one entry, L_k(i,j) = A_k(i,:) B_k(:,j), as an FMA
+// chain in the fixed order t = 0..R-1.  Every kernel that evaluates L_k at an
+// entry of the (I,J) block uses this function, so the core, the row panel and
+// the column panel see bit-identical values there.
+template <int R>
+__device__ __forceinline__ float lowrank_entry(const float* a, const float* b) {
+  float acc = 0.f;
+#pragma unroll
+  for (int t = 0; t < R; ++t) acc = fmaf(a[t], b[t], acc);
+  return acc;
+}
+
+// One entry of D - S_{k+1} on a panel (Alg. 1, Phase I then Phase II):
+// S = T_zeta(D - L_k) keeps the residual where |D - L_k| > zeta (Sec. 3.2,
+// strict >), so D - S equals L_k there and D elsewhere.
+__device__ __forceinline__ float panel_value(float d, float l, float zeta) {
+  const float res = d - l;
+  return fabsf(res) > zeta ? l : d;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---- mbarrier / bulk-copy primitives (inline PTX, sm_90+ forms valid on sm_103a)
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on phase `parity` of an mbarrier: true when the phase
+// completed, false after kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, long long limit) {
+  for (long long it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// 1-D bulk copy global -> shared through the TMA engine, completing on an
+// mbarrier.  dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Streaming 16-byte store (evict-first): outputs written once, never re-read here.
+__device__ __forceinline__ void st_stream(float4* p, float4 v) { __stcs(p, v); }
+
+}  // namespace ircur

@@ -1,0 +1,86 @@
+// Internal declarations shared by the translation units of libircur.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ircur.h"
+
+namespace ircur {
+
+// Number of SMs on GB300; grids of the streaming kernels are multiples of it.
+constexpr int kNumSMsHint = 152;
+
+// Upper bound of spin iterations for every device-side wait (mbarrier polls).
+// A poll takes tens of nanoseconds, so this is far above any legitimate wait
+// but ends a lost wait within a few seconds.
+constexpr long long kSpinLimit = 1ll << 26;
+
+// Device-resident solver state, written only by the kernels of one solve.
+struct State {
+  int k;            // iterations completed
+  int done;         // 1 once e_k <= tol or k == max_iter
+  int status;       // ircur_status raised on the device (0 = fine)
+  unsigned flags;   // IRCUR_FLAG_*
+  double zeta;      // threshold of the current iteration, zeta_0 gamma^k
+  double zeta0;     // zeta_0 in use
+  double e;         // last stopping value e_k
+  unsigned counter; // block-completion counter of the pass kernel
+  unsigned maxabs_bits;  // max|D| as float bits (non-negative floats order like uints)
+  int nonfinite;    // a NaN or Inf was seen in D
+  int svd_steps;    // subspace-iteration steps, summed
+  int svd_last_steps;
+};
+
+// Everything one iteration's kernels need; passed by value as a kernel
+// parameter (constant bank), fixed for a captured graph.
+struct IterDesc {
+  int64_t n1, n2;
+  int r, nI, nJ, max_iter, resample;
+  double gamma, tol;
+  // row-panel source: row a of D(I,:) starts at row_src + (row_map ? row_map[a] : a) * row_ld
+  const float* D;
+  int64_t ldD;
+  const float* Prow;  // F: compact D(I,:) (nI x ldPr); R: nullptr
+  int64_t ldPr;
+  const float* Pcol;  // F: compact D(:,J) (n1 x ldPc); R: nullptr
+  int64_t ldPc;
+  const int* I_all;   // (resample ? max_iter : 1) x nI
+  const int* J_all;   // (resample ? max_iter : 1) x nJ
+  float* A[2];        // n1 x R row-major (R = padded rank of the kernels)
+  float* B[2];        // R x n2 row-major
+  float* core;        // nI x nJ, row-major
+  float* W;           // nI x R   left singular vectors of the core
+  float* V;           // nJ x R   right singular vectors
+  float* Vs;          // nJ x R   V_r Sigma_r^{-1} (zero for dropped directions)
+  float* sigma;       // R
+  double* partials;   // 4 per pass block
+  double* errs;       // max_iter
+  State* st;
+  int rowTile;        // columns per row-pass block (== blockDim.x)
+  int nRowBlocks, nColBlocks;
+  int rowBulk;        // 1: row tiles via cp.async.bulk (16-byte aligned rows)
+  int svdMaxSteps;
+  long long spinLimit;      // first bounded wait on a bulk copy (kSpinLimit unless a fault is injected)
+  unsigned long long cond;  // graph conditional handle (0 = no graph)
+  uint64_t seed;
+};
+
+// Launch wrappers (return cudaGetLastError()).
+cudaError_t launch_sample(uint64_t seed, int draw0, int draws, int64_t n1, int64_t n2, int nI, int nJ,
+                          int* I_all, int* J_all, int only_axis, cudaStream_t s);
+cudaError_t launch_check_indices(const int* idx, int sets, int m, int64_t n, int* status,
+                                 cudaStream_t s);
+cudaError_t launch_maxabs(const float* D, int64_t n1, int64_t n2, int64_t ldD, State* st,
+                          cudaStream_t s);
+cudaError_t launch_setup(const IterDesc& d, double zeta0, cudaStream_t s);
+cudaError_t launch_gather(const IterDesc& d, cudaStream_t s);
+cudaError_t launch_iteration(const IterDesc& d, int Rpad, cudaStream_t s);
+cudaError_t launch_reconstruct(const float* A, const float* B, int Rpad, int64_t n1, int64_t n2,
+                               const float* D, int64_t ldD, float* L, int64_t ldL, float* S,
+                               int64_t ldS, const State* st, cudaStream_t s);
+size_t svd_smem_bytes(int nI, int nJ, int Rpad, bool* core_in_smem);
+size_t pass_smem_bytes(int nI, int nJ, int Rpad, int rowTile);
+int pad_rank(int r);
+
+}  // namespace ircur

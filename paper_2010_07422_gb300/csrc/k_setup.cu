@@ -1,0 +1,289 @@
+// Solve set-up kernels: index sampling (Alg. 1, uniform I and J), index-set
+// validation, max|D| for zeta_0 (Sec. 3.5), the fixed-index panel gathers of
+// IRCUR-F (Sec. 3.4) and the state reset.
+#include <float.h>
+
+#include "device_common.cuh"
+#include "ircur_internal.cuh"
+
+namespace ircur {
+
+// ---------------------------------------------------------------------------
+// Block-wide exclusive scan of one 32-bit count per thread (blockDim = 1024).
+__device__ unsigned block_exclusive_scan(unsigned v, unsigned* warp_tot, unsigned* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    unsigned w = (lane < (int)(blockDim.x >> 5)) ? warp_tot[lane] : 0u;
+    unsigned s = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    warp_tot[lane] = s - w;  // exclusive prefix of warp totals
+    if (lane == 31) *total = s;
+  }
+  __syncthreads();
+  unsigned r = warp_tot[wid] + x - v;
+  __syncthreads();
+  return r;
+}
+
+// Uniform m-subset of [0, n) for one (draw, axis): the m smallest keys
+// key(i) = splitmix64(base ^ i), base = splitmix64(splitmix64(seed) ^ (2 draw + axis)),
+// ties broken by the smaller index, written in ascending index order.
+// One block of 1024 threads per (draw, axis); MSB-first radix select on the
+// 64-bit keys (8 passes of 8 bits), then an order-preserving compaction.
+__global__ void __launch_bounds__(1024) sample_kernel(uint64_t seed, int draw0, int64_t n1, int64_t n2,
+                                                      int nI, int nJ, int* I_all, int* J_all, int only_axis) {
+  const int draw = draw0 + (int)blockIdx.x;
+  const int axis = only_axis >= 0 ? only_axis : (int)blockIdx.y;
+  const int64_t n = axis ? n2 : n1;
+  const int m = axis ? nJ : nI;
+  int* out = axis ? (J_all + (int64_t)blockIdx.x * nJ) : (I_all + (int64_t)blockIdx.x * nI);
+  const uint64_t base = splitmix64(splitmix64(seed) ^ (uint64_t)(2 * draw + axis));
+
+  __shared__ unsigned hist[256];
+  __shared__ unsigned long long s_prefix;
+  __shared__ long long s_want;
+  __shared__ unsigned warp_tot[32];
+  __shared__ unsigned s_total;
+
+  uint64_t prefix = 0, mask = 0;
+  long long want = m;  // rank (1-based) of the target among keys matching `prefix`
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint64_t key = splitmix64(base ^ (uint64_t)i);
+      if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long cum = 0;
+      int dg = 0;
+      for (; dg < 255; ++dg) {
+        if (cum + (long long)hist[dg] >= want) break;
+        cum += hist[dg];
+      }
+      s_want = want - cum;
+      s_prefix = prefix | ((uint64_t)dg << shift);
+    }
+    __syncthreads();
+    want = s_want;
+    prefix = s_prefix;
+    mask |= (0xFFull << shift);
+    __syncthreads();
+  }
+  // prefix is now the m-th smallest key T; `want` keys equal to T are taken.
+  const uint64_t T = prefix;
+  const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
+  const int64_t lo = (int64_t)threadIdx.x * chunk;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  unsigned less = 0, eq = 0;
+  for (int64_t i = lo; i < hi; ++i) {
+    const uint64_t key = splitmix64(base ^ (uint64_t)i);
+    less += key < T;
+    eq += key == T;
+  }
+  const unsigned eq_before = block_exclusive_scan(eq, warp_tot, &s_total);
+  long long take_eq = want - (long long)eq_before;
+  take_eq = take_eq < 0 ? 0 : (take_eq > (long long)eq ? (long long)eq : take_eq);
+  const unsigned sel = less + (unsigned)take_eq;
+  unsigned pos = block_exclusive_scan(sel, warp_tot, &s_total);
+  unsigned eq_rank = eq_before;
+  for (int64_t i = lo; i < hi; ++i) {
+    const uint64_t key = splitmix64(base ^ (uint64_t)i);
+    bool take = key < T;
+    if (key == T) {
+      take = (long long)eq_rank < want;
+      ++eq_rank;
+    }
+    if (take && pos < (unsigned)m) out[pos++] = (int)i;
+  }
+}
+
+cudaError_t launch_sample(uint64_t seed, int draw0, int draws, int64_t n1, int64_t n2, int nI, int nJ,
+                          int* I_all, int* J_all, int only_axis, cudaStream_t s) {
+  dim3 grid(draws, only_axis >= 0 ? 1 : 2);
+  sample_kernel<<<grid, 1024, 0, s>>>(seed, draw0, n1, n2, nI, nJ, I_all, J_all, only_axis);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Caller-supplied index sets: strictly ascending, inside [0, n).
+__global__ void check_indices_kernel(const int* idx, int sets, int m, int64_t n, int* status) {
+  const int64_t total = (int64_t)sets * m;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(q % m);
+    const int v = idx[q];
+    bool bad = v < 0 || (int64_t)v >= n;
+    if (p > 0 && idx[q - 1] >= v) bad = true;
+    if (bad) atomicExch(status, (int)IRCUR_EINVAL);
+  }
+}
+
+cudaError_t launch_check_indices(const int* idx, int sets, int m, int64_t n, int* status,
+                                 cudaStream_t s) {
+  const int64_t total = (int64_t)sets * m;
+  int blocks = (int)((total + 255) / 256);
+  blocks = blocks < 1 ? 1 : (blocks > 4 * kNumSMsHint ? 4 * kNumSMsHint : blocks);
+  check_indices_kernel<<<blocks, 256, 0, s>>>(idx, sets, m, n, status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// max|D_ij| over the whole matrix (zeta_0 = max|D| reading) and a NaN/Inf scan.
+// Streaming read of D: 16-byte loads when rows are 16-byte aligned.
+__global__ void __launch_bounds__(256) maxabs_kernel(const float* __restrict__ D, int64_t n1,
+                                                     int64_t n2, int64_t ldD, int vec,
+                                                     State* st) {
+  float m = 0.f;
+  bool bad = false;
+  if (vec) {
+    const int64_t n4 = n2 >> 2;
+    for (int64_t i = blockIdx.x; i < n1; i += gridDim.x) {
+      const float4* row = reinterpret_cast<const float4*>(D + i * ldD);
+      int64_t j = threadIdx.x;
+      for (; j + 3 * 256 < n4; j += 4 * 256) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = __ldcs(row + j + u * 256);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float a = fmaxf(fmaxf(fabsf(v[u].x), fabsf(v[u].y)), fmaxf(fabsf(v[u].z), fabsf(v[u].w)));
+          bad |= !(fabsf(v[u].x) <= FLT_MAX) || !(fabsf(v[u].y) <= FLT_MAX) ||
+                 !(fabsf(v[u].z) <= FLT_MAX) || !(fabsf(v[u].w) <= FLT_MAX);
+          m = fmaxf(m, a);
+        }
+      }
+      for (; j < n4; j += 256) {
+        const float4 v = __ldcs(row + j);
+        bad |= !(fabsf(v.x) <= FLT_MAX) || !(fabsf(v.y) <= FLT_MAX) || !(fabsf(v.z) <= FLT_MAX) ||
+               !(fabsf(v.w) <= FLT_MAX);
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+      }
+      for (int64_t jj = (n4 << 2) + threadIdx.x; jj < n2; jj += 256) {
+        const float x = D[i * ldD + jj];
+        bad |= !(fabsf(x) <= FLT_MAX);
+        m = fmaxf(m, fabsf(x));
+      }
+    }
+  } else {
+    for (int64_t i = blockIdx.x; i < n1; i += gridDim.x)
+      for (int64_t j = threadIdx.x; j < n2; j += 256) {
+        const float x = D[i * ldD + j];
+        bad |= !(fabsf(x) <= FLT_MAX);
+        m = fmaxf(m, fabsf(x));
+      }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  bad = __any_sync(0xffffffffu, bad);
+  __shared__ float wm[8];
+  __shared__ int wb[8];
+  if ((threadIdx.x & 31) == 0) {
+    wm[threadIdx.x >> 5] = m;
+    wb[threadIdx.x >> 5] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float b = 0.f;
+    int anybad = 0;
+    for (int w = 0; w < 8; ++w) {
+      b = fmaxf(b, wm[w]);
+      anybad |= wb[w];
+    }
+    atomicMax(&st->maxabs_bits, __float_as_uint(b));
+    if (anybad) atomicExch(&st->nonfinite, 1);
+  }
+}
+
+__global__ void finalize_zeta_kernel(State* st) {
+  if (st->nonfinite) {
+    st->status = IRCUR_EINVAL;
+    st->done = 1;
+    return;
+  }
+  const double z = (double)__uint_as_float(st->maxabs_bits);
+  st->zeta0 = z;
+  st->zeta = z;
+}
+
+cudaError_t launch_maxabs(const float* D, int64_t n1, int64_t n2, int64_t ldD, State* st,
+                          cudaStream_t s) {
+  const int vec = ((reinterpret_cast<uintptr_t>(D) & 15) == 0) && (ldD % 4 == 0);
+  int blocks = (int)(n1 < 8 * kNumSMsHint ? n1 : 8 * kNumSMsHint);
+  if (blocks < 1) blocks = 1;
+  maxabs_kernel<<<blocks, 256, 0, s>>>(D, n1, n2, ldD, vec, st);
+  finalize_zeta_kernel<<<1, 1, 0, s>>>(st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// State reset at the start of a solve.
+__global__ void setup_kernel(State* st, double zeta0, int max_iter) {
+  st->k = 0;
+  st->done = max_iter <= 0;
+  st->status = 0;
+  st->flags = 0u;
+  st->zeta = zeta0;
+  st->zeta0 = zeta0;
+  st->e = 1.0;
+  st->counter = 0u;
+  st->maxabs_bits = 0u;
+  st->nonfinite = 0;
+  st->svd_steps = 0;
+  st->svd_last_steps = 0;
+}
+
+cudaError_t launch_setup(const IterDesc& d, double zeta0, cudaStream_t s) {
+  setup_kernel<<<1, 1, 0, s>>>(d.st, zeta0, d.max_iter);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// IRCUR-F: gather the fixed panels once, D(I,:) -> Prow (nI x ldPr) and
+// D(:,J) -> Pcol (n1 x ldPc, row i holds D(i, J)).
+__global__ void __launch_bounds__(256) gather_rows_kernel(IterDesc d) {
+  const int a = blockIdx.y;
+  const int* I = d.I_all;
+  const float* src = d.D + (int64_t)I[a] * d.ldD;
+  float* dst = const_cast<float*>(d.Prow) + (int64_t)a * d.ldPr;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n2;
+       j += (int64_t)gridDim.x * blockDim.x)
+    dst[j] = __ldg(src + j);
+}
+
+__global__ void __launch_bounds__(256) gather_cols_kernel(IterDesc d) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int* J = d.J_all;
+  for (int64_t i = warp; i < d.n1; i += nwarps) {
+    const float* src = d.D + i * d.ldD;
+    float* dst = const_cast<float*>(d.Pcol) + i * d.ldPc;
+    for (int b = lane; b < d.nJ; b += 32) dst[b] = __ldg(src + J[b]);
+  }
+}
+
+cudaError_t launch_gather(const IterDesc& d, cudaStream_t s) {
+  int gx = (int)((d.n2 + 255) / 256);
+  if (gx > 64) gx = 64;
+  gather_rows_kernel<<<dim3(gx, d.nI), 256, 0, s>>>(d);
+  int blocks = (int)((d.n1 + 7) / 8);
+  if (blocks > 8 * kNumSMsHint) blocks = 8 * kNumSMsHint;
+  gather_cols_kernel<<<blocks, 256, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+}  // namespace ircur

@@ -1,0 +1,244 @@
+"""Python binding of libircur (ctypes): the C-ABI entry points under the same
+names, plus a small convenience layer over torch tensors.
+
+Argument marshalling only: every step of IRCUR runs in the CUDA library.  If
+the library is missing the first call raises; there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libircur.so")
+
+IRCUR_OK, IRCUR_EINVAL, IRCUR_ENOMEM, IRCUR_ECUDA = 0, 1, 2, 3
+IRCUR_ESVD_NOCONV, IRCUR_ETIMEOUT, IRCUR_ESTATE, IRCUR_ENOTSUP = 4, 5, 6, 7
+IRCUR_FLAG_WRANK, IRCUR_FLAG_SVD_NOCONV = 1, 2
+IRCUR_MAX_RANK = 16
+
+EXPORTED = (
+    "ircur_create", "ircur_destroy", "ircur_solve", "ircur_get_factors", "ircur_get_indices",
+    "ircur_get_errors", "ircur_reconstruct", "ircur_solve_host", "ircur_sample_indices",
+    "ircur_status_string", "ircur_last_error_string",
+)
+
+
+class ircur_params(C.Structure):
+    _fields_ = [("n1", C.c_int64), ("n2", C.c_int64), ("r", C.c_int32), ("nI", C.c_int32),
+                ("nJ", C.c_int32), ("zeta0", C.c_double), ("gamma", C.c_double), ("tol", C.c_double),
+                ("max_iter", C.c_int32), ("resample", C.c_int32), ("seed", C.c_uint64),
+                ("precision", C.c_int32), ("reserved", C.c_int32)]
+
+
+class ircur_result(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("flags", C.c_uint32),
+                ("svd_steps", C.c_int32), ("final_err", C.c_double), ("zeta0", C.c_double),
+                ("zeta_next", C.c_double)]
+
+
+class IrcurError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        lib = _lib()
+        msg = lib.ircur_status_string(status).decode()
+        cuda = lib.ircur_last_error_string().decode()
+        super().__init__(f"{where}: {msg}" + (f" [{cuda}]" if cuda and status == IRCUR_ECUDA else ""))
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(the IRCUR path has no CPU fallback)")
+        lib = C.CDLL(LIB_PATH)
+        P, I64, I32, U64 = C.c_void_p, C.c_int64, C.c_int32, C.c_uint64
+        lib.ircur_create.argtypes = [C.POINTER(ircur_params), P, C.POINTER(P)]
+        lib.ircur_destroy.argtypes = [P]
+        lib.ircur_destroy.restype = None
+        lib.ircur_solve.argtypes = [P, P, I64, P, P, C.POINTER(ircur_result)]
+        lib.ircur_get_factors.argtypes = [P, P, P]
+        lib.ircur_get_indices.argtypes = [P, P, P, P]
+        lib.ircur_get_errors.argtypes = [P, C.POINTER(C.c_double), C.POINTER(I32)]
+        lib.ircur_reconstruct.argtypes = [P, P, I64, P, I64, P, I64]
+        lib.ircur_solve_host.argtypes = [P, P, P, P, C.POINTER(ircur_result)]
+        lib.ircur_sample_indices.argtypes = [U64, I32, I32, I64, I32, P, P]
+        lib.ircur_status_string.argtypes = [C.c_int]
+        lib.ircur_status_string.restype = C.c_char_p
+        lib.ircur_last_error_string.argtypes = []
+        lib.ircur_last_error_string.restype = C.c_char_p
+        for name in EXPORTED:
+            if name not in ("ircur_destroy", "ircur_status_string", "ircur_last_error_string"):
+                getattr(lib, name).restype = C.c_int
+        _LIB = lib
+    return _LIB
+
+
+def _check(status, where):
+    if status != IRCUR_OK:
+        raise IrcurError(status, where)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream_handle(device=None):
+    import torch
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def sample_size(c, r, n):
+    """|I| = ceil(c r ln n), capped at n (Sec. 3.5)."""
+    return int(min(n, math.ceil(c * r * math.log(n))))
+
+
+# ---------------------------------------------------------------- raw entry points
+def ircur_create(params: ircur_params, stream=None):
+    ctx = C.c_void_p()
+    _check(_lib().ircur_create(C.byref(params), stream, C.byref(ctx)), "ircur_create")
+    return ctx
+
+
+def ircur_destroy(ctx):
+    _lib().ircur_destroy(ctx)
+
+
+def ircur_solve(ctx, D, ldD, idx_I=None, idx_J=None):
+    res = ircur_result()
+    _check(_lib().ircur_solve(ctx, _ptr(D), ldD, _ptr(idx_I), _ptr(idx_J), C.byref(res)), "ircur_solve")
+    return res
+
+
+def ircur_get_factors(ctx, A=None, B=None):
+    _check(_lib().ircur_get_factors(ctx, _ptr(A), _ptr(B)), "ircur_get_factors")
+
+
+def ircur_get_indices(ctx, I=None, J=None, sigma=None):
+    _check(_lib().ircur_get_indices(ctx, _ptr(I), _ptr(J), _ptr(sigma)), "ircur_get_indices")
+
+
+def ircur_get_errors(ctx, max_iter):
+    buf = (C.c_double * max_iter)()
+    cnt = C.c_int32()
+    _check(_lib().ircur_get_errors(ctx, buf, C.byref(cnt)), "ircur_get_errors")
+    return list(buf[: cnt.value])
+
+
+def ircur_reconstruct(ctx, D, ldD, L, ldL, S=None, ldS=0):
+    _check(_lib().ircur_reconstruct(ctx, _ptr(D), ldD, _ptr(L), ldL, _ptr(S), ldS), "ircur_reconstruct")
+
+
+def ircur_solve_host(ctx, D_host, L_host, S_host=None):
+    """D_host, L_host, S_host: C-contiguous float32 numpy arrays or pinned CPU tensors."""
+    def hp(a):
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):
+            return C.c_void_p(a.data_ptr())
+        return a.ctypes.data_as(C.c_void_p)
+    res = ircur_result()
+    _check(_lib().ircur_solve_host(ctx, hp(D_host), hp(L_host), hp(S_host), C.byref(res)),
+           "ircur_solve_host")
+    return res
+
+
+def ircur_sample_indices(seed, draw, axis, n, m, out, stream=None):
+    _check(_lib().ircur_sample_indices(seed, draw, axis, n, m, _ptr(out), stream), "ircur_sample_indices")
+
+
+# ---------------------------------------------------------------- convenience layer
+@dataclass
+class Result:
+    iters: int
+    converged: bool
+    flags: int
+    svd_steps: int
+    final_err: float
+    zeta0: float
+    zeta_next: float
+
+
+class IRCUR:
+    """One IRCUR problem shape bound to a CUDA device and stream.
+
+    solver = IRCUR(n1, n2, r, resample=True)
+    res = solver.solve(D)                 # D: float32 CUDA tensor, n1 x n2
+    L, S = solver.reconstruct(D)          # dense outputs
+    """
+
+    def __init__(self, n1, n2, r, *, nI=0, nJ=0, zeta0=0.0, gamma=0.7, tol=1e-5, max_iter=100,
+                 resample=True, seed=0, stream=None):
+        import torch
+        self.p = ircur_params(n1=n1, n2=n2, r=r, nI=nI, nJ=nJ, zeta0=zeta0, gamma=gamma, tol=tol,
+                              max_iter=max_iter, resample=int(bool(resample)), seed=seed,
+                              precision=0, reserved=0)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._ctx = ircur_create(self.p, C.c_void_p(self.stream.cuda_stream))
+        self.nI = nI if nI else sample_size(4, r, n1)
+        self.nJ = nJ if nJ else sample_size(4, r, n2)
+        self.last = None
+
+    def close(self):
+        if self._ctx:
+            ircur_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, D, idx_I=None, idx_J=None):
+        assert D.is_cuda and D.dtype.itemsize == 4 and D.stride(1) == 1
+        r = ircur_solve(self._ctx, D, D.stride(0), idx_I, idx_J)
+        self.last = Result(r.iters, bool(r.converged), r.flags, r.svd_steps, r.final_err, r.zeta0,
+                           r.zeta_next)
+        return self.last
+
+    def factors(self):
+        import torch
+        A = torch.empty((self.p.n1, self.p.r), dtype=torch.float32, device="cuda")
+        B = torch.empty((self.p.r, self.p.n2), dtype=torch.float32, device="cuda")
+        ircur_get_factors(self._ctx, A, B)
+        return A, B
+
+    def indices(self):
+        import torch
+        I = torch.empty(self.nI, dtype=torch.int32, device="cuda")
+        J = torch.empty(self.nJ, dtype=torch.int32, device="cuda")
+        sig = torch.empty(self.p.r, dtype=torch.float32, device="cuda")
+        ircur_get_indices(self._ctx, I, J, sig)
+        return I, J, sig
+
+    def errors(self):
+        return ircur_get_errors(self._ctx, self.p.max_iter)
+
+    def reconstruct(self, D=None, with_sparse=True, L=None, S=None):
+        import torch
+        n1, n2 = self.p.n1, self.p.n2
+        if L is None:
+            L = torch.empty((n1, n2), dtype=torch.float32, device="cuda")
+        if with_sparse and S is None:
+            S = torch.empty((n1, n2), dtype=torch.float32, device="cuda")
+        if not with_sparse:
+            S = None
+        ircur_reconstruct(self._ctx, D, D.stride(0) if D is not None else 0, L, L.stride(0),
+                          S, S.stride(0) if S is not None else 0)
+        return L, S
+
+
+def sample_indices(seed, draw, axis, n, m):
+    """Device sampler (one draw): sorted uniform m-subset of [0, n)."""
+    import torch
+    out = torch.empty(m, dtype=torch.int32, device="cuda")
+    ircur_sample_indices(seed, draw, axis, n, m, out, _stream_handle())
+    return out

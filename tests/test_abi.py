@@ -1,0 +1,84 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+entry point include/ircur.h declares; the Python binding wraps each one."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+           if f.endswith(".h")]
+
+
+def declared_functions():
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(ircur_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2010_07422_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("ircur_create", "ircur_solve", "ircur_reconstruct", "ircur_destroy"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2010_07422_gb300 import ircur
+    assert set(declared_functions()) <= set(ircur.EXPORTED)
+
+
+def test_status_strings_and_param_validation_without_gpu(lib):
+    """Argument checks run on the host before any CUDA call."""
+    from paper_2010_07422_gb300 import ircur as ir
+    lib = ir._lib()
+    assert lib.ircur_status_string(ir.IRCUR_EINVAL).decode().startswith("IRCUR_EINVAL")
+    ctx = ctypes.c_void_p()
+
+    def create(**kw):
+        base = dict(n1=100, n2=80, r=3, nI=0, nJ=0, zeta0=0.0, gamma=0.7, tol=1e-5, max_iter=10,
+                    resample=1, seed=0, precision=0, reserved=0)
+        base.update(kw)
+        return lib.ircur_create(ctypes.byref(ir.ircur_params(**base)), None, ctypes.byref(ctx))
+
+    assert create(r=0) == ir.IRCUR_EINVAL
+    assert create(r=17) == ir.IRCUR_ENOTSUP
+    assert create(gamma=1.0) == ir.IRCUR_EINVAL
+    assert create(gamma=0.0) == ir.IRCUR_EINVAL
+    assert create(tol=0.0) == ir.IRCUR_EINVAL
+    assert create(max_iter=0) == ir.IRCUR_EINVAL
+    assert create(nI=2) == ir.IRCUR_EINVAL        # |I| < r violates Thm 1's |I| >= r
+    assert create(nJ=81) == ir.IRCUR_EINVAL       # |J| > n2
+    assert create(resample=2) == ir.IRCUR_EINVAL
+    assert create(precision=1) == ir.IRCUR_ENOTSUP
+    assert create(n1=0) == ir.IRCUR_EINVAL
+    assert ctx.value is None
+    # sampler argument checks
+    assert lib.ircur_sample_indices(0, 0, 0, 10, 11, None, None) == ir.IRCUR_EINVAL
+    assert lib.ircur_sample_indices(0, 0, 2, 10, 5, ctypes.c_void_p(16), None) == ir.IRCUR_EINVAL
+
+
+def test_fault_injection_alloc_returns_enomem(lib, monkeypatch):
+    from paper_2010_07422_gb300 import ircur as ir
+    monkeypatch.setenv("IRCUR_FAULT", "alloc")
+    ctx = ctypes.c_void_p()
+    p = ir.ircur_params(n1=100, n2=80, r=3, nI=0, nJ=0, zeta0=0.0, gamma=0.7, tol=1e-5, max_iter=10,
+                        resample=1, seed=0, precision=0, reserved=0)
+    assert ir._lib().ircur_create(ctypes.byref(p), None, ctypes.byref(ctx)) == ir.IRCUR_ENOMEM
+    assert ctx.value is None
