@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""IRCUR benchmark: time-to-tolerance and iterations/s at n1 = n2 = 10^4, r = 5.
+
+One step = one whole pass of the hot path on one synthetic D: index sampling,
+zeta_0 = max|D|, the iterations of Alg. 1 until e_k <= 1e-5 (IRCUR-R: fresh
+I, J every iteration), then the dense L = C U^+ R and S = T_zeta(D - L).
+D (400 MB FP32) is larger than L2, so every step starts cold.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun every rank solves its own independent instance (different
+seed): the method has no exchange between independent problems, so N GPUs run
+N replicas (weak scaling) with no data-path collective; rank 0 prints one JSON
+line with the whole-job iterations/s (sum over ranks / max time over ranks).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "IRCUR time-to-1e-5 rel err & iters/s at n=10^4,r=5; HBM GB/s % of peak"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variant", default="R", choices=["R", "F"])
+    ap.add_argument("--n", type=int, default=10000)
+    ap.add_argument("--r", type=int, default=5)
+    ap.add_argument("--alpha", type=float, default=0.1)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    nI = math.ceil(4 * a.r * math.log(a.n))
+    return (f"IRCUR-{a.variant} planted rank-{a.r} + {a.alpha:g}-sparse D, n1=n2={a.n}, |I|=|J|={nI}, "
+            f"zeta0=max|D|, gamma=0.7, tol=1e-5, max_iter=100, then dense L and S")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            mp = json.load(f)
+        return float(mp["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def dram_traffic(kernel, workload_tag):
+    """DRAM bytes per launch recorded from an ncu capture in profiles/, or None
+    when no capture exists or the kernel's source changed since it was taken."""
+    prof = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    if not os.path.exists(prof):
+        return None
+    for line in open(prof):
+        m = re.match(r"\|\s*(\S+)\s*\|\s*(\S+)\s*\|\s*([0-9.e+]+)\s*\|\s*(\S+)\s*\|\s*(\S+)\s*\|", line)
+        if not m or m.group(1) != kernel or m.group(2) != workload_tag:
+            continue
+        src = os.path.join(ROOT, "paper_2010_07422_gb300", "csrc", m.group(4))
+        if not os.path.exists(src):
+            return None
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
+        return float(m.group(3)) if sha == m.group(5) else None
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_input(a, rank):
+    from paper_2010_07422_gb300 import synth
+    return synth.planted(a.n, a.n, a.r, a.alpha, seed=a.seed + 1000 * rank)
+
+
+def cpu_oracle_sample(p, a, seconds, max_steps=None):
+    """The FP64 oracle as it stands, timed on the host cores: whole IRCUR solves
+    (same workload, same variant) until about `seconds` of CPU work."""
+    import oracle
+    D64 = p.D  # the oracle promotes to FP64 per panel gather
+    t0 = time.perf_counter()
+    iters = solves = 0
+    last = None
+    while True:
+        res = oracle.ircur(D64, a.r, 0, 0.7, 1e-5, 100, resample=(a.variant == "R"), seed=a.seed + 1 + solves)
+        iters += res.iters
+        solves += 1
+        last = res
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_steps and solves >= max_steps):
+            break
+    return iters, solves, el, last
+
+
+def run_reference(a, rank, world):
+    """--impl reference: the FP64 CPU oracle on the same workload, rank 0 only.
+    Each step is a bounded sample: an oracle solve truncated to a fixed number
+    of iterations chosen so that warmup + steps end within about two minutes."""
+    if rank != 0:
+        return
+    import oracle
+    p = make_input(a, 0)
+    # calibrate one iteration
+    t0 = time.perf_counter()
+    oracle.ircur(p.D, a.r, 0, 0.7, 1e-5, 1, resample=(a.variant == "R"), seed=a.seed + 1)
+    t_it = time.perf_counter() - t0
+    per_step = int(max(1, min(100, 110.0 / max(1e-3, t_it) / max(1, a.steps + a.warmup))))
+    for w in range(a.warmup):
+        oracle.ircur(p.D, a.r, 0, 0.7, 1e-5, per_step, resample=(a.variant == "R"), seed=a.seed + 1 + w)
+    t0 = time.perf_counter()
+    iters = 0
+    for s in range(a.steps):
+        res = oracle.ircur(p.D, a.r, 0, 0.7, 1e-5, per_step, resample=(a.variant == "R"), seed=a.seed + 1 + s)
+        iters += res.iters
+    el = time.perf_counter() - t0
+    value = iters / el
+    cores = os.cpu_count()
+    sample = (f"{a.steps} steps x oracle solve truncated to {per_step} iterations "
+              f"(numpy FP64, n={a.n}, r={a.r}, IRCUR-{a.variant})")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * el / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "n1": a.n, "n2": a.n, "r": a.r, "alpha": a.alpha,
+                       "variant": a.variant, "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2010_07422_gb300 import ircur as ir
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    p = make_input(a, rank)
+    n = a.n
+    D = torch.from_numpy(p.D).cuda()
+    L = torch.empty_like(D)
+    S = torch.empty_like(D)
+    resample = a.variant == "R"
+    solver = ir.IRCUR(n, n, a.r, gamma=0.7, tol=1e-5, max_iter=100, resample=resample, seed=a.seed + 1 + rank)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        res = solver.solve(D)
+        solver.reconstruct(D, L=L, S=S)
+        return res
+
+    for _ in range(max(3, a.warmup)):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+
+    clk = ClockSampler(local)
+    clk.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    rec = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    sol = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    iters = []
+    flags = 0
+    svd_steps = 0
+    ev0.record(stream)
+    for k in range(a.steps):
+        sol[k][0].record(stream)
+        res = solver.solve(D)
+        sol[k][1].record(stream)
+        rec[k][0].record(stream)
+        solver.reconstruct(D, L=L, S=S)
+        rec[k][1].record(stream)
+        iters.append(res.iters)
+        flags |= res.flags
+        svd_steps += res.svd_steps
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    barrier()
+    total_ms = ev0.elapsed_time(ev1)
+    recon_ms = [s.elapsed_time(e) for s, e in rec]
+    solve_ms = [s.elapsed_time(e) for s, e in sol]
+    my_iters = float(sum(iters))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        it = torch.tensor([my_iters], dtype=torch.float64, device="cuda")
+        dist.all_reduce(it, op=dist.ReduceOp.SUM)
+        total_ms_max, all_iters = float(t.item()), float(it.item())
+    else:
+        total_ms_max, all_iters = total_ms, my_iters
+
+    # accuracy of the last step against the planted truth, on sampled entries
+    rng = np.random.default_rng(0)
+    ri = rng.integers(0, n, 200000)
+    ci = rng.integers(0, n, 200000)
+    Lg = L[torch.from_numpy(ri).cuda(), torch.from_numpy(ci).cuda()].double().cpu().numpy()
+    Lt = p.L_entries(ri, ci)
+    rel_err_truth = float(np.linalg.norm(Lg - Lt) / np.linalg.norm(Lt))
+
+    # roofline of the reconstruction kernel (read D, write L and S: 12 bytes per entry)
+    hbm_peak, peak_src = peaks()
+    rec_bytes = 12.0 * n * n + 4.0 * a.r * 2 * n
+    rec_avg_s = float(np.mean(recon_ms)) / 1e3
+    achieved = rec_bytes / rec_avg_s / 1e9
+    traffic = dram_traffic("recon_vec_kernel", f"n{n}_r{a.r}")
+
+    e2e = None
+    if a.e2e_steps > 0:
+        Dh = torch.from_numpy(p.D).pin_memory()
+        Lh = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        Sh = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        e2e_solver = ir.IRCUR(n, n, a.r, gamma=0.7, tol=1e-5, max_iter=100, resample=resample,
+                              seed=a.seed + 1 + rank)
+        ir.ircur_solve_host(e2e_solver._ctx, Dh, Lh, Sh)  # warm-up (allocates the device buffers)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        e_iters = 0
+        for _ in range(a.e2e_steps):
+            r2 = ir.ircur_solve_host(e2e_solver._ctx, Dh, Lh, Sh)
+            e_iters += r2.iters
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            it = torch.tensor([float(e_iters)], dtype=torch.float64, device="cuda")
+            dist.all_reduce(it, op=dist.ReduceOp.SUM)
+            el, e_iters = float(t.item()), float(it.item())
+        e2e = {"value": e_iters / el, "unit": "iters/s", "h2d_bytes_per_step": 4 * n * n,
+               "d2h_bytes_per_step": 8 * n * n, "ms_per_step": 1e3 * el / a.e2e_steps,
+               "api": "ircur_solve_host (pinned host D in, dense L and S out)"}
+        e2e_solver.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        c_iters, c_solves, c_el, _ = cpu_oracle_sample(p, a, a.cpu_seconds)
+        cpu = {"value": c_iters / c_el, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{c_solves} whole oracle solve(s) of the same workload (numpy FP64, "
+                         f"{c_iters} iterations, {c_el:.1f} s), numpy/BLAS default threads",
+               "time_to_tol_ms": 1e3 * c_el / c_solves}
+
+    if rank == 0:
+        launches_per_step = [4 + (2 if not resample else 0) + 3 * it + 1 for it in iters]
+        line = {
+            "metric": METRIC, "value": all_iters / (total_ms_max / 1e3), "unit": "iters/s",
+            "n_gpus": world, "steps": a.steps, "warmup": max(3, a.warmup),
+            "ms_per_step": total_ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(a), "n1": n, "n2": n, "r": a.r, "alpha": a.alpha,
+                       "variant": a.variant, "nI": solver.nI, "nJ": solver.nJ,
+                       "l2": "inputs larger than L2 (D is 400 MB; 1.2 GB streamed per step)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "time_to_tol_ms": float(np.mean(solve_ms)),
+            "reconstruct_ms": float(np.mean(recon_ms)),
+            "iters_per_solve": float(np.mean(iters)),
+            "svd_steps_per_iter": svd_steps / max(1.0, my_iters),
+            "flags": flags,
+            "rel_err_vs_truth": rel_err_truth,
+            "roofline": {"kernel": "recon_vec_kernel (dense L and S)", "bound": "hbm",
+                         "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": traffic,
+                         "peak_source": f"{peak_src} STREAM-style copy (MEASURED_PEAKS.json hbm_gbs)"
+                                        if peak_src == "measured" else "fallback 6.8 TB/s",
+                         "algorithmic_bytes_per_launch": rec_bytes},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(sum(launches_per_step)),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -63,8 +63,9 @@ struct ircur_ctx {
   int* I_all;
   int* J_all;
   float* Prow;
-  float* Pcol;
-  int64_t ldPr, ldPc;
+  float* PcolT;
+  float* DT;
+  int64_t ldPr, ldPc, ldDT;
   float* A[2];
   float* B[2];
   float* core;
@@ -108,6 +109,7 @@ static ircur_status validate_params(const ircur_params* p, ircur_params* out) {
   if (q.nJ == 0) q.nJ = default_sample_size(q.r, q.n2);
   if (q.nI < q.r || q.nJ < q.r || q.nI > q.n1 || q.nJ > q.n2) return IRCUR_EINVAL;
   if (q.nI > 512 || q.nJ > 512) return IRCUR_ENOTSUP;
+  if (pass_smem_bytes(q.nI, q.nJ, pad_rank(q.r)) > 227 * 1024) return IRCUR_ENOTSUP;
   if (!(q.gamma > 0.0 && q.gamma < 1.0)) return IRCUR_EINVAL;
   if (!(q.tol > 0.0)) return IRCUR_EINVAL;
   if (q.max_iter < 1) return IRCUR_EINVAL;
@@ -136,15 +138,14 @@ extern "C" ircur_status ircur_create(const ircur_params* params, void* stream, i
   const int R = c->Rpad;
   const int64_t n1 = p.n1, n2 = p.n2;
   c->ldPr = (n2 + 3) & ~3ll;
-  c->ldPc = ((int64_t)p.nJ + 3) & ~3ll;
+  c->ldPc = (n1 + 3) & ~3ll;
+  c->ldDT = (n1 + 3) & ~3ll;
 
   // tile configuration of the pass kernel
   IterDesc& d = c->desc;
   memset(&d, 0, sizeof(d));
-  d.rowTile = p.nI <= 192 ? 128 : 64;
-  d.nRowBlocks = (int)((n2 + d.rowTile - 1) / d.rowTile);
-  int64_t ncb = (n1 + 31) / 32;
-  d.nColBlocks = (int)(ncb < 1 ? 1 : ncb);
+  d.nRowTiles = (int)((n2 + kPanelCols - 1) / kPanelCols);
+  d.nColTiles = (int)((n1 + kPanelCols - 1) / kPanelCols);
 
   // workspace carve-up (256-byte aligned pieces)
   size_t off = 0;
@@ -156,13 +157,14 @@ extern "C" ircur_status ircur_create(const ircur_params* params, void* stream, i
   const size_t oI = take((size_t)c->draws * p.nI * 4);
   const size_t oJ = take((size_t)c->draws * p.nJ * 4);
   const size_t oPr = p.resample ? 0 : take((size_t)p.nI * c->ldPr * 4);
-  const size_t oPc = p.resample ? 0 : take((size_t)n1 * c->ldPc * 4);
+  const size_t oPc = p.resample ? 0 : take((size_t)p.nJ * c->ldPc * 4);
+  const size_t oDT = p.resample ? take((size_t)n2 * c->ldDT * 4) : 0;
   const size_t oA0 = take((size_t)n1 * R * 4), oA1 = take((size_t)n1 * R * 4);
   const size_t oB0 = take((size_t)R * n2 * 4), oB1 = take((size_t)R * n2 * 4);
   const size_t oCore = take((size_t)p.nI * p.nJ * 4);
   const size_t oW = take((size_t)p.nI * R * 4), oV = take((size_t)p.nJ * R * 4), oVs = take((size_t)p.nJ * R * 4);
   const size_t oSig = take((size_t)R * 4);
-  const size_t oPart = take((size_t)(d.nRowBlocks + d.nColBlocks) * 4 * 8);
+  const size_t oPart = take((size_t)(d.nRowTiles + d.nColTiles) * 2 * 8);
   const size_t oErr = take((size_t)p.max_iter * 8);
   const size_t oSt = take(sizeof(State));
   c->ws_bytes = off;
@@ -184,7 +186,8 @@ extern "C" ircur_status ircur_create(const ircur_params* params, void* stream, i
   c->I_all = reinterpret_cast<int*>(base + oI);
   c->J_all = reinterpret_cast<int*>(base + oJ);
   c->Prow = p.resample ? nullptr : reinterpret_cast<float*>(base + oPr);
-  c->Pcol = p.resample ? nullptr : reinterpret_cast<float*>(base + oPc);
+  c->PcolT = p.resample ? nullptr : reinterpret_cast<float*>(base + oPc);
+  c->DT = p.resample ? reinterpret_cast<float*>(base + oDT) : nullptr;
   c->A[0] = reinterpret_cast<float*>(base + oA0);
   c->A[1] = reinterpret_cast<float*>(base + oA1);
   c->B[0] = reinterpret_cast<float*>(base + oB0);
@@ -218,8 +221,13 @@ extern "C" ircur_status ircur_create(const ircur_params* params, void* stream, i
   d.tol = p.tol;
   d.Prow = c->Prow;
   d.ldPr = c->ldPr;
-  d.Pcol = c->Pcol;
+  d.PcolT = c->PcolT;
   d.ldPc = c->ldPc;
+  d.DT = c->DT;
+  d.ldDT = c->ldDT;
+  d.colSrc = p.resample ? c->DT : c->PcolT;
+  d.colLd = p.resample ? c->ldDT : c->ldPc;
+  d.colBulk = 1;
   d.I_all = c->I_all;
   d.J_all = c->J_all;
   d.A[0] = c->A[0];
@@ -318,8 +326,9 @@ extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, c
   IterDesc d = c->desc;
   d.D = D;
   d.ldD = ldD;
-  const bool rows_aligned = p.resample ? (aligned16(D) && ldD % 4 == 0) : true;
-  d.rowBulk = rows_aligned ? 1 : 0;
+  d.rowSrc = p.resample ? D : c->Prow;
+  d.rowLd = p.resample ? ldD : c->ldPr;
+  d.rowBulk = p.resample ? ((aligned16(D) && ldD % 4 == 0) ? 1 : 0) : 1;
   c->desc = d;
 
   const double zeta0 = p.zeta0 > 0 ? p.zeta0 : 0.0;
@@ -332,7 +341,13 @@ extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, c
   } else {
     IRCUR_CK(launch_sample(p.seed, 0, c->draws, p.n1, p.n2, p.nI, p.nJ, c->I_all, c->J_all, -1, s));
   }
-  if (!(p.zeta0 > 0)) IRCUR_CK(launch_maxabs(D, p.n1, p.n2, ldD, c->st, s));
+  if (p.resample) {
+    // D^T for the column panels, with max|D| and the NaN/Inf scan in the same pass
+    IRCUR_CK(launch_transpose_maxabs(D, p.n1, p.n2, ldD, c->DT, c->ldDT, c->st, s));
+  } else if (!(p.zeta0 > 0)) {
+    IRCUR_CK(launch_maxabs(D, p.n1, p.n2, ldD, c->st, s));
+  }
+  if (!(p.zeta0 > 0)) IRCUR_CK(launch_finalize_zeta(c->st, s));
   if (!p.resample) IRCUR_CK(launch_gather(d, s));
   IRCUR_CK(cudaMemsetAsync(c->A[0], 0, (size_t)p.n1 * c->Rpad * 4, s));
   IRCUR_CK(cudaMemsetAsync(c->B[0], 0, (size_t)c->Rpad * p.n2 * 4, s));
@@ -344,7 +359,16 @@ extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, c
     }
     IRCUR_CK(cudaGraphLaunch(c->exec, s));
   } else {
-    for (int it = 0; it < p.max_iter; ++it) IRCUR_CK(launch_iteration(d, c->Rpad, s));
+    // Host-driven loop (profiling and debugging: every kernel is a separate
+    // launch).  The device flag is polled every few iterations.
+    for (int it = 0; it < p.max_iter; ++it) {
+      IRCUR_CK(launch_iteration(d, c->Rpad, s));
+      if ((it & 3) == 3) {
+        ircur_status rs = read_state(c);
+        if (rs != IRCUR_OK) return rs;
+        if (c->host_state.done) break;
+      }
+    }
   }
   ircur_status rs = read_state(c);
   if (rs != IRCUR_OK) return rs;

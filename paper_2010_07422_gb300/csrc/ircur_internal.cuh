@@ -16,6 +16,13 @@ constexpr int kNumSMsHint = 152;
 // but ends a lost wait within a few seconds.
 constexpr long long kSpinLimit = 1ll << 26;
 
+// Panel-pass tiling: a block covers kPanelCols consecutive panel columns with
+// kPanelSplit threads per column, each thread handling a contiguous share of
+// the panel's rows.
+constexpr int kPanelCols = 64;
+constexpr int kPanelSplit = 4;
+constexpr int kPanelThreads = kPanelCols * kPanelSplit;
+
 // Device-resident solver state, written only by the kernels of one solve.
 struct State {
   int k;            // iterations completed
@@ -34,32 +41,43 @@ struct State {
 
 // Everything one iteration's kernels need; passed by value as a kernel
 // parameter (constant bank), fixed for a captured graph.
+//
+// Panels.  The row panel D(I,:) is read row by row from `rowSrc`: panel row a
+// is rowSrc + (rowMap ? rowMap[a] : a) * rowLd, where rowMap is the current I
+// (IRCUR-R, rows of D itself) or null (IRCUR-F, the compact copy made once).
+// The column panel D(:,J) is read the same way from its transpose: panel row
+// b (column J_b of D) is colSrc + (colMap ? J[b] : b) * colLd, where colSrc is
+// D^T (IRCUR-R, transposed once per solve) or the compact copy D(:,J)^T.
 struct IterDesc {
   int64_t n1, n2;
   int r, nI, nJ, max_iter, resample;
   double gamma, tol;
-  // row-panel source: row a of D(I,:) starts at row_src + (row_map ? row_map[a] : a) * row_ld
   const float* D;
   int64_t ldD;
-  const float* Prow;  // F: compact D(I,:) (nI x ldPr); R: nullptr
+  const float* rowSrc;  // D (R) or Prow (F)
+  int64_t rowLd;
+  const float* colSrc;  // D^T (R) or PcolT (F)
+  int64_t colLd;
+  float* Prow;          // F: nI x ldPr
   int64_t ldPr;
-  const float* Pcol;  // F: compact D(:,J) (n1 x ldPc); R: nullptr
+  float* PcolT;         // F: nJ x ldPc
   int64_t ldPc;
-  const int* I_all;   // (resample ? max_iter : 1) x nI
-  const int* J_all;   // (resample ? max_iter : 1) x nJ
-  float* A[2];        // n1 x R row-major (R = padded rank of the kernels)
-  float* B[2];        // R x n2 row-major
-  float* core;        // nI x nJ, row-major
-  float* W;           // nI x R   left singular vectors of the core
-  float* V;           // nJ x R   right singular vectors
-  float* Vs;          // nJ x R   V_r Sigma_r^{-1} (zero for dropped directions)
-  float* sigma;       // R
-  double* partials;   // 4 per pass block
-  double* errs;       // max_iter
+  float* DT;            // R: n2 x n1 (leading dimension ldDT)
+  int64_t ldDT;
+  const int* I_all;     // (resample ? max_iter : 1) x nI
+  const int* J_all;     // (resample ? max_iter : 1) x nJ
+  float* A[2];          // n1 x R row-major (R = padded rank of the kernels)
+  float* B[2];          // R x n2 row-major
+  float* core;          // nI x nJ, row-major
+  float* W;             // nI x R   left singular vectors of the core
+  float* V;             // nJ x R   right singular vectors
+  float* Vs;            // nJ x R   V_r Sigma_r^{-1} (zero for dropped directions)
+  float* sigma;         // R
+  double* partials;     // 2 per pass block
+  double* errs;         // max_iter
   State* st;
-  int rowTile;        // columns per row-pass block (== blockDim.x)
-  int nRowBlocks, nColBlocks;
-  int rowBulk;        // 1: row tiles via cp.async.bulk (16-byte aligned rows)
+  int nRowTiles, nColTiles;
+  int rowBulk, colBulk; // 1: panel tiles via cp.async.bulk (16-byte aligned rows)
   int svdMaxSteps;
   long long spinLimit;      // first bounded wait on a bulk copy (kSpinLimit unless a fault is injected)
   unsigned long long cond;  // graph conditional handle (0 = no graph)
@@ -73,6 +91,9 @@ cudaError_t launch_check_indices(const int* idx, int sets, int m, int64_t n, int
                                  cudaStream_t s);
 cudaError_t launch_maxabs(const float* D, int64_t n1, int64_t n2, int64_t ldD, State* st,
                           cudaStream_t s);
+cudaError_t launch_transpose_maxabs(const float* D, int64_t n1, int64_t n2, int64_t ldD, float* DT,
+                                    int64_t ldDT, State* st, cudaStream_t s);
+cudaError_t launch_finalize_zeta(State* st, cudaStream_t s);
 cudaError_t launch_setup(const IterDesc& d, double zeta0, cudaStream_t s);
 cudaError_t launch_gather(const IterDesc& d, cudaStream_t s);
 cudaError_t launch_iteration(const IterDesc& d, int Rpad, cudaStream_t s);
@@ -80,7 +101,7 @@ cudaError_t launch_reconstruct(const float* A, const float* B, int Rpad, int64_t
                                const float* D, int64_t ldD, float* L, int64_t ldL, float* S,
                                int64_t ldS, const State* st, cudaStream_t s);
 size_t svd_smem_bytes(int nI, int nJ, int Rpad, bool* core_in_smem);
-size_t pass_smem_bytes(int nI, int nJ, int Rpad, int rowTile);
+size_t pass_smem_bytes(int nI, int nJ, int Rpad);
 int pad_rank(int r);
 
 }  // namespace ircur

@@ -225,7 +225,78 @@ cudaError_t launch_maxabs(const float* D, int64_t n1, int64_t n2, int64_t ldD, S
   int blocks = (int)(n1 < 8 * kNumSMsHint ? n1 : 8 * kNumSMsHint);
   if (blocks < 1) blocks = 1;
   maxabs_kernel<<<blocks, 256, 0, s>>>(D, n1, n2, ldD, vec, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_zeta(State* st, cudaStream_t s) {
   finalize_zeta_kernel<<<1, 1, 0, s>>>(st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// IRCUR-R: D^T (n2 x n1) once per solve, so that the column panels D(:,J_k)
+// of every iteration are row gathers of D^T; the same pass takes max|D| and
+// the NaN/Inf scan.  32 x 32 tiles through padded shared memory; every global
+// access is a coalesced 128-byte row segment.
+__global__ void __launch_bounds__(256) transpose_maxabs_kernel(const float* __restrict__ D, int64_t n1,
+                                                               int64_t n2, int64_t ldD, float* __restrict__ DT,
+                                                               int64_t ldDT, State* st) {
+  __shared__ float tile[32][33];
+  const int64_t tiles_i = (n1 + 31) / 32, tiles_j = (n2 + 31) / 32;
+  const int64_t ntiles = tiles_i * tiles_j;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  float m = 0.f;
+  bool bad = false;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t ti = t / tiles_j, tj = t - ti * tiles_j;
+    const int64_t i0 = ti * 32, j0 = tj * 32;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t i = i0 + ty + 8 * q, j = j0 + tx;
+      float x = 0.f;
+      if (i < n1 && j < n2) {
+        x = __ldcs(D + i * ldD + j);
+        bad |= !(fabsf(x) <= FLT_MAX);
+        m = fmaxf(m, fabsf(x));
+      }
+      tile[ty + 8 * q][tx] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t j = j0 + ty + 8 * q, i = i0 + tx;
+      if (i < n1 && j < n2) DT[j * ldDT + i] = tile[tx][ty + 8 * q];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  bad = __any_sync(0xffffffffu, bad);
+  __shared__ float wm[8];
+  __shared__ int wb[8];
+  if (tx == 0) {
+    wm[ty] = m;
+    wb[ty] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float b = 0.f;
+    int anybad = 0;
+    for (int w = 0; w < 8; ++w) {
+      b = fmaxf(b, wm[w]);
+      anybad |= wb[w];
+    }
+    atomicMax(&st->maxabs_bits, __float_as_uint(b));
+    if (anybad) atomicExch(&st->nonfinite, 1);
+  }
+}
+
+cudaError_t launch_transpose_maxabs(const float* D, int64_t n1, int64_t n2, int64_t ldD, float* DT,
+                                    int64_t ldDT, State* st, cudaStream_t s) {
+  const int64_t ntiles = ((n1 + 31) / 32) * ((n2 + 31) / 32);
+  int blocks = (int)(ntiles < 16 * kNumSMsHint ? ntiles : 16 * kNumSMsHint);
+  if (blocks < 1) blocks = 1;
+  transpose_maxabs_kernel<<<blocks, 256, 0, s>>>(D, n1, n2, ldD, DT, ldDT, st);
   return cudaGetLastError();
 }
 
@@ -253,36 +324,32 @@ cudaError_t launch_setup(const IterDesc& d, double zeta0, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------
 // IRCUR-F: gather the fixed panels once, D(I,:) -> Prow (nI x ldPr) and
-// D(:,J) -> Pcol (n1 x ldPc, row i holds D(i, J)).
+// D(:,J)^T -> PcolT (nJ x ldPc, row b holds column J_b of D).
 __global__ void __launch_bounds__(256) gather_rows_kernel(IterDesc d) {
   const int a = blockIdx.y;
-  const int* I = d.I_all;
-  const float* src = d.D + (int64_t)I[a] * d.ldD;
-  float* dst = const_cast<float*>(d.Prow) + (int64_t)a * d.ldPr;
+  const float* src = d.D + (int64_t)d.I_all[a] * d.ldD;
+  float* dst = d.Prow + (int64_t)a * d.ldPr;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n2;
        j += (int64_t)gridDim.x * blockDim.x)
     dst[j] = __ldg(src + j);
 }
 
 __global__ void __launch_bounds__(256) gather_cols_kernel(IterDesc d) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int* J = d.J_all;
-  for (int64_t i = warp; i < d.n1; i += nwarps) {
-    const float* src = d.D + i * d.ldD;
-    float* dst = const_cast<float*>(d.Pcol) + i * d.ldPc;
-    for (int b = lane; b < d.nJ; b += 32) dst[b] = __ldg(src + J[b]);
-  }
+  const int b = blockIdx.y;
+  const int64_t j = d.J_all[b];
+  float* dst = d.PcolT + (int64_t)b * d.ldPc;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.n1;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = __ldg(d.D + i * d.ldD + j);
 }
 
 cudaError_t launch_gather(const IterDesc& d, cudaStream_t s) {
   int gx = (int)((d.n2 + 255) / 256);
   if (gx > 64) gx = 64;
   gather_rows_kernel<<<dim3(gx, d.nI), 256, 0, s>>>(d);
-  int blocks = (int)((d.n1 + 7) / 8);
-  if (blocks > 8 * kNumSMsHint) blocks = 8 * kNumSMsHint;
-  gather_cols_kernel<<<blocks, 256, 0, s>>>(d);
+  int gy = (int)((d.n1 + 255) / 256);
+  if (gy > 64) gy = 64;
+  gather_cols_kernel<<<dim3(gy, d.nJ), 256, 0, s>>>(d);
   return cudaGetLastError();
 }
 

@@ -3,21 +3,24 @@
 // U^+ = V_r Sigma_r^{-1} W_r^T).
 //
 // One CTA of 512 threads.  The dominant rank-r singular subspaces are found
-// by two-sided subspace (orthogonal) iteration with Cholesky-QR, warm-started
+// by two-sided subspace (orthogonal) iteration with Cholesky QR, warm-started
 // from the previous iterate's right factor B_k(:,J)^T, whose row space is the
 // right singular subspace of L_k(I,J); the core of iteration k+1 differs from
-// L_k(I,J) only by the change of the thresholded entries.  Each step is
-//     P = core X,  Y Rc = P (CholQR),  Q = core^T Y,
-// and stops once the residual E = Q - X Rc^T (the part of core^T Y outside
-// span X) is below 1e-6 ||Rc||_F, or stagnates below 1e-4 ||Rc||_F.  The r x r
-// Rayleigh-Ritz matrix T = Y^T core X is then diagonalised by a one-sided
-// Jacobi SVD in one warp, giving W_r = Y U_T, V_r = X V_T, sigma_r.
-// Singular values <= max(|I|,|J|) * FLT_EPSILON * sigma_1 are dropped
-// (numerical rank; IRCUR_FLAG_WRANK).
+// L_k(I,J) only where the threshold decisions differ.  One step is
+//     P = core X,  Y Rp = P (CholQR),  Q = core^T Y,
+// and the iteration stops once E = Q - X Rp^T, the part of core^T Y outside
+// span X, is below 1e-6 ||Rp||_F (or has stopped shrinking below 1e-5).
+// Then Y and X get a second CholQR pass, the r x r Rayleigh-Ritz matrix
+// T = Y^T core X follows from the triangular factors without another
+// product, and a one-sided Jacobi SVD of T in one warp gives
+// W_r = Y U_T, V_r = X V_T and sigma_r.  Singular values
+// <= max(|I|,|J|) * FLT_EPSILON * sigma_1 are dropped (numerical rank,
+// IRCUR_FLAG_WRANK).
 //
-// Precision: the core and the m-long products are FP32; Gram matrices are
-// accumulated per lane in FP32 and across lanes in FP64, and the Cholesky
-// factorisation and triangular inverse run in FP64.
+// Precision: FP32 throughout.  GB300's FP64 pipe runs at a small fraction of
+// its FP32 rate, and the serial FP64 Cholesky/sqrt/divide chains of a first
+// version cost more than the whole rest of the iteration; CholQR2 (the
+// second pass) restores orthogonality to FP32 rounding.
 #include <float.h>
 
 #include "device_common.cuh"
@@ -30,11 +33,13 @@ constexpr int kSvdThreads = 512;
 __host__ __device__ constexpr int round_up4(int x) { return (x + 3) & ~3; }
 
 struct SvdLayout {
-  int ldu;       // leading dimension of the core copy in shared memory (odd)
-  int rx;        // row stride of the m x R blocks (R rounded up to 4)
-  int mmax;      // max(nI, nJ)
-  size_t off_us, off_x, off_y, off_p, off_q, off_part, off_small, total;
+  int ldu;   // leading dimension of the core copy in shared memory (odd)
+  int rx;    // row stride of the m x R blocks (R rounded up to 4)
+  int mmax;  // max(nI, nJ)
+  size_t off_us, off_x, off_y, off_q, off_part, off_small, total;
 };
+
+constexpr int kSmallMats = 9;  // G, Rp, U, U2y, U2x, T, Ut, Vt, scratch (R x R each)
 
 __host__ __device__ inline SvdLayout svd_layout(int nI, int nJ, int R, bool core_in_smem) {
   SvdLayout L;
@@ -49,15 +54,12 @@ __host__ __device__ inline SvdLayout svd_layout(int nI, int nJ, int R, bool core
   off += (size_t)L.mmax * L.rx * 4;
   L.off_y = off;
   off += (size_t)L.mmax * L.rx * 4;
-  L.off_p = off;
-  off += (size_t)L.mmax * L.rx * 4;
   L.off_q = off;
   off += (size_t)L.mmax * L.rx * 4;
   L.off_part = off;
   off += (size_t)kSvdThreads * L.rx * 4;
   L.off_small = off;
-  // G, Rc (double R*R each), Rinv, T, Ut, Vt (float R*R each), sig, scalars
-  off += 2 * (size_t)R * R * 8 + 4 * (size_t)R * R * 4 + 64 * 4 + 256;
+  off += (size_t)kSmallMats * R * R * 4 + 3 * 32 * 4 + 64;
   L.total = (off + 15) & ~(size_t)15;
   return L;
 }
@@ -73,20 +75,24 @@ size_t svd_smem_bytes(int nI, int nJ, int Rpad, bool* core_in_smem) {
 }
 
 struct SvdSmall {
-  double* G;     // R x R Gram
-  double* Rc;    // R x R upper Cholesky factor
-  float* Rinv;   // R x R inverse of Rc (zero rows/cols for dropped pivots)
-  float* T;      // R x R Rayleigh-Ritz matrix
-  float* Ut;     // R x R
-  float* Vt;     // R x R
-  float* sig;    // R
-  float* red;    // 32 reduction slots
-  int* ibuf;     // 8 ints
+  float* G;     // R x R Gram matrix
+  float* Rp;    // R x R factor of the last P = core X
+  float* U;     // R x R upper Cholesky factor of the last cholqr
+  float* U2y;   // second-pass factor of Y
+  float* U2x;   // second-pass factor of X
+  float* T;     // R x R Rayleigh-Ritz matrix
+  float* Ut;    // R x R
+  float* Vt;    // R x R
+  float* tmp;   // R x R
+  float* dinv;  // R reciprocal pivots
+  float* sig;   // R
+  float* red;   // 32 reduction slots
+  int* ibuf;    // 16 ints
 };
 
 // out(o, t) = sum_q U(o, q) in(q, t), U = core (nI x nJ) or its transpose.
-// Threads are laid out as (chunk, row): the inner index range is split in
-// nch chunks whose partial sums are added in a fixed order (deterministic).
+// Threads are laid out as (chunk, row): the inner index range is split in nch
+// chunks whose partial sums are added in a fixed order (deterministic).
 template <int R>
 __device__ void core_product(const float* __restrict__ U, int ldu, bool transposed, int nout, int nin,
                              const float* __restrict__ in, float* __restrict__ out, float* part, int rx) {
@@ -98,31 +104,58 @@ __device__ void core_product(const float* __restrict__ U, int ldu, bool transpos
 #pragma unroll
     for (int t = 0; t < R; ++t) acc[t] = 0.f;
     const int q0 = (int)((long long)c * nin / nch), q1 = (int)((long long)(c + 1) * nin / nch);
-    for (int q = q0; q < q1; ++q) {
-      const float u = transposed ? U[(size_t)q * ldu + o] : U[(size_t)o * ldu + q];
-      const float* m = in + (size_t)q * rx;
+    if (transposed) {
+      for (int q = q0; q < q1; ++q) {
+        const float u = U[(size_t)q * ldu + o];
+        const float* m = in + (size_t)q * rx;
 #pragma unroll
-      for (int t = 0; t < R; ++t) acc[t] = fmaf(u, m[t], acc[t]);
+        for (int t = 0; t < R; ++t) acc[t] = fmaf(u, m[t], acc[t]);
+      }
+    } else {
+      for (int q = q0; q < q1; ++q) {
+        const float u = U[(size_t)o * ldu + q];
+        const float* m = in + (size_t)q * rx;
+#pragma unroll
+        for (int t = 0; t < R; ++t) acc[t] = fmaf(u, m[t], acc[t]);
+      }
     }
+    if (nch == 1) {
 #pragma unroll
-    for (int t = 0; t < R; ++t) part[((size_t)c * rows32 + o) * rx + t] = acc[t];
+      for (int t = 0; t < R; ++t) out[(size_t)o * rx + t] = acc[t];
+    } else {
+#pragma unroll
+      for (int t = 0; t < R; ++t) part[((size_t)c * rows32 + o) * rx + t] = acc[t];
+    }
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < nout * R; idx += blockDim.x) {
-    const int oo = idx / R, t = idx % R;
-    float s = 0.f;
-    for (int cc = 0; cc < nch; ++cc) s += part[((size_t)cc * rows32 + oo) * rx + t];
-    out[(size_t)oo * rx + t] = s;
+  if (nch > 1) {
+    for (int idx = threadIdx.x; idx < nout * R; idx += blockDim.x) {
+      const int oo = idx / R, t = idx % R;
+      float s = 0.f;
+      for (int cc = 0; cc < nch; ++cc) s += part[((size_t)cc * rows32 + oo) * rx + t];
+      out[(size_t)oo * rx + t] = s;
+    }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
-// In-place Cholesky QR of the nrows x r block M (stride rx): M <- M Rc^{-1},
-// Rc (FP64, upper) with M_in = M_out Rc.  Pivots below 1e-10 of the largest
-// diagonal entry are treated as dependent columns: they become zero columns
-// and count as breakdowns (returned).
 template <int R>
-__device__ int cholqr(float* M, int nrows, int r, int rx, const SvdSmall& sm) {
+__device__ __forceinline__ float sel(const float (&g)[R], int t) {
+  float v = 0.f;
+#pragma unroll
+  for (int u = 0; u < R; ++u)
+    if (u == t) v = g[u];
+  return v;
+}
+
+// Cholesky QR of the nrows x r block Min (stride rx) into Mout (may alias):
+// Min = Mout U with U upper triangular (written to Uout).  The Gram matrix is
+// formed by warps (one entry per warp), factorised by warp 0 (lane l holds row
+// l of the Schur complement), and applied by forward substitution row by row.
+// Pivots <= 1e-12 of the largest diagonal entry mark dependent columns: they
+// become zero columns and are counted (returned).
+template <int R>
+__device__ int cholqr(const float* Min, float* Mout, int nrows, int r, int rx, float* Uout, const SvdSmall& sm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int npairs = r * (r + 1) / 2;
   for (int p = warp; p < npairs; p += nwarps) {
@@ -133,85 +166,69 @@ __device__ int cholqr(float* M, int nrows, int r, int rx, const SvdSmall& sm) {
     }
     const int t = s + rem;
     float acc = 0.f;
-    for (int i = lane; i < nrows; i += 32) acc = fmaf(M[(size_t)i * rx + s], M[(size_t)i * rx + t], acc);
-    const double tot = warp_sum((double)acc);
+    for (int i = lane; i < nrows; i += 32) acc = fmaf(Min[(size_t)i * rx + s], Min[(size_t)i * rx + t], acc);
+    acc = warp_sum(acc);
     if (lane == 0) {
-      sm.G[s * R + t] = tot;
-      sm.G[t * R + s] = tot;
+      sm.G[s * R + t] = acc;
+      sm.G[t * R + s] = acc;
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double maxd = 0.0;
-    for (int t = 0; t < r; ++t) maxd = fmax(maxd, sm.G[t * R + t]);
-    int brk = 0;
-    for (int s = 0; s < R; ++s)
-      for (int t = 0; t < R; ++t) sm.Rc[s * R + t] = 0.0;
-    for (int t = 0; t < r; ++t) {
-      double dg = sm.G[t * R + t];
-      for (int s = 0; s < t; ++s) dg -= sm.Rc[s * R + t] * sm.Rc[s * R + t];
-      if (!(dg > 1e-10 * maxd) || !(maxd > 0.0)) {
-        ++brk;
-        continue;  // dependent column: zero row of Rc
-      }
-      const double d = sqrt(dg);
-      sm.Rc[t * R + t] = d;
-      for (int u = t + 1; u < r; ++u) {
-        double v = sm.G[t * R + u];
-        for (int s = 0; s < t; ++s) v -= sm.Rc[s * R + t] * sm.Rc[s * R + u];
-        sm.Rc[t * R + u] = v / d;
-      }
-    }
-    // inverse of the upper-triangular Rc (skipping dropped pivots)
-    double inv[R * R];
-    for (int s = 0; s < R * R; ++s) inv[s] = 0.0;
-    for (int t = 0; t < r; ++t) {
-      if (sm.Rc[t * R + t] == 0.0) continue;
-      inv[t * R + t] = 1.0 / sm.Rc[t * R + t];
-      for (int s = t - 1; s >= 0; --s) {
-        if (sm.Rc[s * R + s] == 0.0) continue;
-        double v = 0.0;
-        for (int u = s + 1; u <= t; ++u) v += sm.Rc[s * R + u] * inv[u * R + t];
-        inv[s * R + t] = -v / sm.Rc[s * R + s];
-      }
-    }
-    for (int s = 0; s < R * R; ++s) sm.Rinv[s] = (float)inv[s];
-    sm.ibuf[0] = brk;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
-    float m[R], o[R];
+  if (warp == 0) {
+    float g[R];
 #pragma unroll
-    for (int s = 0; s < R; ++s) m[s] = M[(size_t)i * rx + s];
+    for (int u = 0; u < R; ++u) g[u] = (lane < r && u < r) ? sm.G[lane * R + u] : 0.f;
+    float maxd = sel<R>(g, lane);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxd = fmaxf(maxd, __shfl_xor_sync(0xffffffffu, maxd, o));
+    int brk = 0;
+    for (int t = 0; t < r; ++t) {
+      const float gt = sel<R>(g, t);  // this lane's entry (lane, t) = (t, lane) of the complement
+      const float dgt = __shfl_sync(0xffffffffu, gt, t);
+      const bool keep = dgt > 1e-12f * maxd && dgt <= FLT_MAX;
+      const float rinv = keep ? rsqrtf(dgt) : 0.f;
+      const float ul = gt * rinv;  // U(t, lane)
+      float urow[R];
+#pragma unroll
+      for (int u = 0; u < R; ++u) urow[u] = __shfl_sync(0xffffffffu, ul, u);  // U(t, u)
+      if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < R; ++u) Uout[t * R + u] = (u >= t) ? urow[u] : 0.f;
+        sm.dinv[t] = rinv;
+      }
+      if (lane > t) {
+#pragma unroll
+        for (int u = 0; u < R; ++u) g[u] = fmaf(-ul, urow[u], g[u]);
+      }
+      brk += keep ? 0 : 1;
+    }
+    if (lane == 0) {
+      for (int t = r; t < R; ++t) {
+        sm.dinv[t] = 0.f;
+        for (int u = 0; u < R; ++u) Uout[t * R + u] = 0.f;
+      }
+      sm.ibuf[0] = brk;
+    }
+  }
+  __syncthreads();
+  // Mout = Min U^{-1}: forward substitution y U = m for every row
+  for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+    float m[R], y[R];
+#pragma unroll
+    for (int s = 0; s < R; ++s) m[s] = Min[(size_t)i * rx + s];
 #pragma unroll
     for (int t = 0; t < R; ++t) {
-      float v = 0.f;
+      float v = m[t];
 #pragma unroll
-      for (int s = 0; s <= t; ++s) v = fmaf(m[s], sm.Rinv[s * R + t], v);
-      o[t] = v;
+      for (int s = 0; s < t; ++s) v = fmaf(-y[s], Uout[s * R + t], v);
+      y[t] = v * sm.dinv[t];
     }
 #pragma unroll
-    for (int t = 0; t < R; ++t) M[(size_t)i * rx + t] = o[t];
+    for (int t = 0; t < R; ++t) Mout[(size_t)i * rx + t] = y[t];
   }
   const int brk = sm.ibuf[0];
   __syncthreads();
   return brk;
-}
-
-__device__ float block_sum(float v, float* red) {
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  float s = 0.f;
-  if (threadIdx.x == 0) {
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    red[31] = s;
-  }
-  __syncthreads();
-  s = red[31];
-  __syncthreads();
-  return s;
 }
 
 __device__ __forceinline__ float hash_uniform(uint64_t seed, uint64_t ctr) {
@@ -228,7 +245,7 @@ __device__ __forceinline__ int rr_partner(int p, int k, int n) {
 }
 
 template <int R>
-__global__ void __launch_bounds__(kSvdThreads) svd_kernel(IterDesc d, int core_in_smem) {
+__global__ void __launch_bounds__(kSvdThreads, 1) svd_kernel(IterDesc d, int core_in_smem) {
   State* st = d.st;
   if (st->done || st->status) return;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -242,28 +259,35 @@ __global__ void __launch_bounds__(kSvdThreads) svd_kernel(IterDesc d, int core_i
   const int ldu = core_in_smem ? L.ldu : nJ;
   float* X = reinterpret_cast<float*>(smem + L.off_x);
   float* Y = reinterpret_cast<float*>(smem + L.off_y);
-  float* P = reinterpret_cast<float*>(smem + L.off_p);
   float* Q = reinterpret_cast<float*>(smem + L.off_q);
   float* part = reinterpret_cast<float*>(smem + L.off_part);
   SvdSmall sm;
   {
-    unsigned char* p = smem + L.off_small;
-    sm.G = reinterpret_cast<double*>(p);
-    p += (size_t)R * R * 8;
-    sm.Rc = reinterpret_cast<double*>(p);
-    p += (size_t)R * R * 8;
-    sm.Rinv = reinterpret_cast<float*>(p);
-    p += (size_t)R * R * 4;
-    sm.T = reinterpret_cast<float*>(p);
-    p += (size_t)R * R * 4;
-    sm.Ut = reinterpret_cast<float*>(p);
-    p += (size_t)R * R * 4;
-    sm.Vt = reinterpret_cast<float*>(p);
-    p += (size_t)R * R * 4;
-    sm.sig = reinterpret_cast<float*>(p);
-    p += 32 * 4;
-    sm.red = reinterpret_cast<float*>(p);
-    p += 32 * 4;
+    float* p = reinterpret_cast<float*>(smem + L.off_small);
+    sm.G = p;
+    p += R * R;
+    sm.Rp = p;
+    p += R * R;
+    sm.U = p;
+    p += R * R;
+    sm.U2y = p;
+    p += R * R;
+    sm.U2x = p;
+    p += R * R;
+    sm.T = p;
+    p += R * R;
+    sm.Ut = p;
+    p += R * R;
+    sm.Vt = p;
+    p += R * R;
+    sm.tmp = p;
+    p += R * R;
+    sm.dinv = p;
+    p += 32;
+    sm.sig = p;
+    p += 32;
+    sm.red = p;
+    p += 32;
     sm.ibuf = reinterpret_cast<int*>(p);
   }
 
@@ -281,66 +305,82 @@ __global__ void __launch_bounds__(kSvdThreads) svd_kernel(IterDesc d, int core_i
     X[q] = (t < r) ? Bk[(int64_t)t * d.n2 + J[b]] : 0.f;
   }
   __syncthreads();
-  int brk = cholqr<R>(X, nJ, r, rx, sm);
+  int brk = cholqr<R>(X, X, nJ, r, rx, sm.U, sm);
   if (brk > 0) {  // first iteration (B_0 = 0) or a deficient factor: random start
     for (int q = threadIdx.x; q < nJ * rx; q += blockDim.x) {
       const int t = q % rx;
       X[q] = (t < r) ? hash_uniform(d.seed ^ 0x5bd1e995ull, ((uint64_t)k << 32) ^ (uint64_t)q) : 0.f;
     }
     __syncthreads();
-    cholqr<R>(X, nJ, r, rx, sm);
+    cholqr<R>(X, X, nJ, r, rx, sm.U, sm);
   }
 
   // ---- subspace iteration
   int steps = 0;
   bool converged = false;
   float prev_res = 0.f;
-  while (steps < d.svdMaxSteps) {
+  while (true) {
     ++steps;
     core_product<R>(Us, ldu, false, nI, nJ, X, Y, part, rx);  // Y = core X
-    cholqr<R>(Y, nI, r, rx, sm);                               // Y Rc = core X
+    cholqr<R>(Y, Y, nI, r, rx, sm.Rp, sm);                     // Y Rp = core X
     core_product<R>(Us, ldu, true, nJ, nI, Y, Q, part, rx);    // Q = core^T Y
-    // E = Q - X Rc^T ; ||E||_F^2 and ||Rc||_F^2
+    // ||Q - X Rp^T||_F^2 and ||Rp||_F^2 in one block reduction
     float e2 = 0.f;
     for (int q = threadIdx.x; q < nJ * r; q += blockDim.x) {
       const int b = q / r, t = q - b * r;
       float v = Q[(size_t)b * rx + t];
-      for (int s = t; s < r; ++s) v -= X[(size_t)b * rx + s] * (float)sm.Rc[t * R + s];
+      for (int s = t; s < r; ++s) v = fmaf(-X[(size_t)b * rx + s], sm.Rp[t * R + s], v);
       e2 = fmaf(v, v, e2);
     }
     float rc2 = 0.f;
-    if (threadIdx.x < R * R) {
-      const float v = (float)sm.Rc[threadIdx.x];
-      rc2 = v * v;
+    if (threadIdx.x < R * R) rc2 = sm.Rp[threadIdx.x] * sm.Rp[threadIdx.x];
+    e2 = warp_sum(e2);
+    rc2 = warp_sum(rc2);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+      sm.red[warp] = e2;
+      sm.red[16 + warp] = rc2;
     }
-    const float E2 = block_sum(e2, sm.red);
-    const float RC2 = block_sum(rc2, sm.red);
+    __syncthreads();
+    float E2 = 0.f, RC2 = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      E2 += sm.red[w];
+      RC2 += sm.red[16 + w];
+    }
     const float res = sqrtf(E2), nrm = sqrtf(RC2);
-    if (res <= 1e-6f * nrm || (steps > 1 && res > 0.5f * prev_res && res <= 1e-4f * nrm) || !(nrm > 0.f)) {
+    if (res <= 1e-6f * nrm || (steps > 1 && res > 0.5f * prev_res && res <= 1e-5f * nrm) || !(nrm > 0.f)) {
       converged = true;
       break;
     }
+    if (steps >= d.svdMaxSteps) break;  // keep X, Y, Rp of the same step
     prev_res = res;
-    for (int q = threadIdx.x; q < nJ * rx; q += blockDim.x) X[q] = Q[q];
-    __syncthreads();
-    cholqr<R>(X, nJ, r, rx, sm);
+    cholqr<R>(Q, X, nJ, r, rx, sm.U, sm);  // X = orth(core^T Y)
   }
 
-  // ---- final bases: X re-orthonormalised, Y = orth(core X) twice, T = Y^T core X
-  cholqr<R>(X, nJ, r, rx, sm);
-  core_product<R>(Us, ldu, false, nI, nJ, X, P, part, rx);  // P = core X
-  for (int q = threadIdx.x; q < nI * rx; q += blockDim.x) Y[q] = P[q];
-  __syncthreads();
-  cholqr<R>(Y, nI, r, rx, sm);
-  cholqr<R>(Y, nI, r, rx, sm);
-  {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int p = warp; p < r * r; p += nwarps) {
-      const int s = p / r, t = p % r;
-      float acc = 0.f;
-      for (int i = lane; i < nI; i += 32) acc = fmaf(Y[(size_t)i * rx + s], P[(size_t)i * rx + t], acc);
-      acc = warp_sum(acc);
-      if (lane == 0) sm.T[s * R + t] = acc;
+  // ---- second CholQR passes; T = U2y Rp U2x^{-1} = Y^T core X for the new bases
+  cholqr<R>(Y, Y, nI, r, rx, sm.U2y, sm);
+  cholqr<R>(X, X, nJ, r, rx, sm.U2x, sm);
+  if (threadIdx.x < 32) {
+    const int s = threadIdx.x;
+    if (s < r) {
+      float row[R];  // (U2y Rp)(s, :)
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        float v = 0.f;
+        for (int u = 0; u < r; ++u) v = fmaf(sm.U2y[s * R + u], sm.Rp[u * R + t], v);
+        row[t] = v;
+      }
+      // T(s,:) U2x = row  (forward substitution; dropped pivots give zeros)
+      float tr[R];
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        float v = row[t];
+#pragma unroll
+        for (int u = 0; u < t; ++u) v = fmaf(-tr[u], sm.U2x[u * R + t], v);
+        tr[t] = (t < r) ? v * sm.dinv[t] : 0.f;
+      }
+#pragma unroll
+      for (int t = 0; t < R; ++t) sm.T[s * R + t] = tr[t];
     }
   }
   __syncthreads();
@@ -380,7 +420,7 @@ __global__ void __launch_bounds__(kSvdThreads) svd_kernel(IterDesc d, int core_i
             rotated = 1;
             const float zeta = (aqq - app) / (2.f * apq);
             const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-            const float c = 1.f / sqrtf(1.f + tt * tt), s = c * tt;
+            const float c = rsqrtf(1.f + tt * tt), s = c * tt;
 #pragma unroll
             for (int i = 0; i < R; ++i) {
               const float a = lo ? tc[i] : tq[i], b = lo ? tq[i] : tc[i];
@@ -411,16 +451,15 @@ __global__ void __launch_bounds__(kSvdThreads) svd_kernel(IterDesc d, int core_i
       }
       sm.sig[pos] = sg;
     }
-  }
-  __syncthreads();
-  // numerical rank
-  if (threadIdx.x == 0) {
-    const float s0 = sm.sig[0];
-    const float tol = (float)(nI > nJ ? nI : nJ) * FLT_EPSILON * s0;
-    int rank = 0;
-    for (int t = 0; t < r; ++t) rank += sm.sig[t] > tol && sm.sig[t] > 0.f;
-    sm.ibuf[1] = rank;
-    for (int t = r; t < R; ++t) sm.sig[t] = 0.f;
+    __syncwarp();
+    if (p == 0) {
+      const float s0 = sm.sig[0];
+      const float tol = (float)(nI > nJ ? nI : nJ) * FLT_EPSILON * s0;
+      int rank = 0;
+      for (int t = 0; t < r; ++t) rank += sm.sig[t] > tol && sm.sig[t] > 0.f;
+      sm.ibuf[1] = rank;
+      for (int t = r; t < R; ++t) sm.sig[t] = 0.f;
+    }
   }
   __syncthreads();
   const int rank = sm.ibuf[1];

@@ -64,7 +64,8 @@ def _distinct_positions(rng, total, k):
     got = np.zeros(0, np.int64)
     while got.size < k:
         extra = rng.integers(0, total, size=int(1.25 * (k - got.size)) + 16, dtype=np.int64)
-        got = np.unique(np.concatenate([got, extra]))
+        got = np.sort(np.concatenate([got, extra]))
+        got = got[np.concatenate([[True], got[1:] != got[:-1]])]  # sorted distinct values
     pick = rng.choice(got.size, size=k, replace=False)
     return np.sort(got[pick])
 
