@@ -73,6 +73,7 @@ struct ircur_ctx {
   float* V;
   float* Vs;
   float* sigma;
+  float* Tm;
   double* partials;
   double* errs;
   State* st;
@@ -110,6 +111,10 @@ static ircur_status validate_params(const ircur_params* p, ircur_params* out) {
   if (q.nI < q.r || q.nJ < q.r || q.nI > q.n1 || q.nJ > q.n2) return IRCUR_EINVAL;
   if (q.nI > 512 || q.nJ > 512) return IRCUR_ENOTSUP;
   if (pass_smem_bytes(q.nI, q.nJ, pad_rank(q.r)) > 227 * 1024) return IRCUR_ENOTSUP;
+  {
+    bool in_smem = false;
+    if (svd_smem_bytes(q.nI, q.nJ, pad_rank(q.r), &in_smem) > 227 * 1024) return IRCUR_ENOTSUP;
+  }
   if (!(q.gamma > 0.0 && q.gamma < 1.0)) return IRCUR_EINVAL;
   if (!(q.tol > 0.0)) return IRCUR_EINVAL;
   if (q.max_iter < 1) return IRCUR_EINVAL;
@@ -161,9 +166,13 @@ extern "C" ircur_status ircur_create(const ircur_params* params, void* stream, i
   const size_t oDT = p.resample ? take((size_t)n2 * c->ldDT * 4) : 0;
   const size_t oA0 = take((size_t)n1 * R * 4), oA1 = take((size_t)n1 * R * 4);
   const size_t oB0 = take((size_t)R * n2 * 4), oB1 = take((size_t)R * n2 * 4);
-  const size_t oCore = take((size_t)p.nI * p.nJ * 4);
+  int ldCore = (p.nJ + 3) & ~3;
+  if (((ldCore / 4) & 1) == 0) ldCore += 4;
+  d.ldCore = ldCore;
+  const size_t oCore = take((size_t)p.nI * ldCore * 4);
   const size_t oW = take((size_t)p.nI * R * 4), oV = take((size_t)p.nJ * R * 4), oVs = take((size_t)p.nJ * R * 4);
   const size_t oSig = take((size_t)R * 4);
+  const size_t oTm = take((size_t)R * R * 4);
   const size_t oPart = take((size_t)(d.nRowTiles + d.nColTiles) * 2 * 8);
   const size_t oErr = take((size_t)p.max_iter * 8);
   const size_t oSt = take(sizeof(State));
@@ -197,6 +206,7 @@ extern "C" ircur_status ircur_create(const ircur_params* params, void* stream, i
   c->V = reinterpret_cast<float*>(base + oV);
   c->Vs = reinterpret_cast<float*>(base + oVs);
   c->sigma = reinterpret_cast<float*>(base + oSig);
+  c->Tm = reinterpret_cast<float*>(base + oTm);
   c->partials = reinterpret_cast<double*>(base + oPart);
   c->errs = reinterpret_cast<double*>(base + oErr);
   c->st = reinterpret_cast<State*>(base + oSt);
@@ -239,6 +249,7 @@ extern "C" ircur_status ircur_create(const ircur_params* params, void* stream, i
   d.V = c->V;
   d.Vs = c->Vs;
   d.sigma = c->sigma;
+  d.Tm = c->Tm;
   d.partials = c->partials;
   d.errs = c->errs;
   d.st = c->st;
@@ -413,8 +424,7 @@ extern "C" ircur_status ircur_get_indices(ircur_ctx* c, int32_t* I, int32_t* J, 
   if (J)
     IRCUR_CK(cudaMemcpyAsync(J, c->J_all + (size_t)draw * c->p.nJ, (size_t)c->p.nJ * 4, cudaMemcpyDeviceToDevice,
                              c->stream));
-  if (sigma)
-    IRCUR_CK(cudaMemcpyAsync(sigma, c->sigma, (size_t)c->p.r * 4, cudaMemcpyDeviceToDevice, c->stream));
+  if (sigma) IRCUR_CK(launch_sigma(c->Tm, c->p.r, c->Rpad, sigma, c->stream));
   return IRCUR_OK;
 }
 

@@ -68,11 +68,13 @@ struct IterDesc {
   const int* J_all;     // (resample ? max_iter : 1) x nJ
   float* A[2];          // n1 x R row-major (R = padded rank of the kernels)
   float* B[2];          // R x n2 row-major
-  float* core;          // nI x nJ, row-major
-  float* W;             // nI x R   left singular vectors of the core
-  float* V;             // nJ x R   right singular vectors
-  float* Vs;            // nJ x R   V_r Sigma_r^{-1} (zero for dropped directions)
-  float* sigma;         // R
+  float* core;          // nI x ldCore, row-major (columns nJ..ldCore-1 stay zero)
+  int ldCore;           // nJ rounded up to 4, with ldCore/4 odd (conflict-free 16-byte rows)
+  float* W;             // nI x R   Y: orthonormal basis of the core's dominant left subspace
+  float* V;             // nJ x R   X T^T (column-pass reconstruction)
+  float* Vs;            // nJ x R   X T^{-1} (column-pass projection; zero for dropped directions)
+  float* sigma;         // R        |diag T| (diagnostic)
+  float* Tm;            // R x R    Rayleigh-Ritz matrix T = Y^T core X of the last iteration
   double* partials;     // 2 per pass block
   double* errs;         // max_iter
   State* st;
@@ -101,6 +103,7 @@ cudaError_t launch_reconstruct(const float* A, const float* B, int Rpad, int64_t
                                const float* D, int64_t ldD, float* L, int64_t ldL, float* S,
                                int64_t ldS, const State* st, cudaStream_t s);
 size_t svd_smem_bytes(int nI, int nJ, int Rpad, bool* core_in_smem);
+cudaError_t launch_sigma(const float* Tm, int r, int Rpad, float* sigma, cudaStream_t s);
 size_t pass_smem_bytes(int nI, int nJ, int Rpad);
 int pad_rank(int r);
 

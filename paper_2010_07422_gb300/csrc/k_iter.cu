@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) core_kernel(IterDesc d) {
 #pragma unroll
       for (int t = 0; t < R; ++t) bcol[t] = B[(int64_t)t * d.n2 + j];
       const float l = lowrank_entry<R>(arow, bcol);
-      d.core[(int64_t)a * d.nJ + b] = panel_value(rowp[j], l, zeta);
+      d.core[(int64_t)a * d.ldCore + b] = panel_value(rowp[j], l, zeta);
     }
   }
 }
@@ -59,15 +59,15 @@ __global__ void __launch_bounds__(256) core_kernel(IterDesc d) {
 //
 // Row pass (COL = false): the panel is D(I,:) (m = |I| rows); for column j
 //   R_{k+1}(:,j) = D(I,j) - T_zeta(D(I,j) - A_k(I,:) B_k(:,j)),
-//   B_{k+1}(:,j) = W_r^T R_{k+1}(:,j),
-//   num += ||R_{k+1}(:,j) - W_r B_{k+1}(:,j)||^2,  den += ||D(I,j)||^2.
+//   B_{k+1}(:,j) = Y^T R_{k+1}(:,j),
+//   num += ||R_{k+1}(:,j) - Y B_{k+1}(:,j)||^2,  den += ||D(I,j)||^2.
 // Column pass (COL = true): the panel is D(:,J)^T (m = |J| rows); for row i
 //   C_{k+1}(i,:) = D(i,J) - T_zeta(D(i,J) - A_k(i,:) B_k(:,J)),
-//   A_{k+1}(i,:) = C_{k+1}(i,:) V_r Sigma_r^{-1},
-//   num += ||C_{k+1}(i,:) - A_{k+1}(i,:) Sigma_r V_r^T||^2,  den += ||D(i,J)||^2.
+//   A_{k+1}(i,:) = C_{k+1}(i,:) X T^{-1},
+//   num += ||C_{k+1}(i,:) - A_{k+1}(i,:) T X^T||^2,  den += ||D(i,J)||^2.
 // Both are the same computation on a row-major m x n panel with
 //   side = A_k(I,:) | B_k(:,J)^T (m x R), vec = B_k(:,j) | A_k(i,:)^T,
-//   proj = W_r | V_r Sigma_r^{-1},  recon = W_r | V_r Sigma_r.
+//   proj = Y | X T^{-1},  recon = Y | X T^T  (U^+ = X T^{-1} Y^T, see k_svd.cu).
 // The m x kPanelCols tile is staged in shared memory by one bulk copy (TMA
 // engine) per panel row, overwritten with D - S, and read back by the second
 // sweep for the explicit residual.  kPanelSplit threads share a column, each
@@ -115,7 +115,7 @@ __device__ void panel_pass(const IterDesc& d, int tile, int k, float zeta, unsig
       const int b = q / R, t = q - b * R;
       side[q] = B[(int64_t)t * d.n2 + J[b]];
       proj[q] = d.Vs[q];
-      recon[q] = d.V[q] * d.sigma[t];
+      recon[q] = d.V[q];
     }
   }
   __syncthreads();

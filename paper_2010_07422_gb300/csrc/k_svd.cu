@@ -10,17 +10,25 @@
 //     P = core X,  Y Rp = P (CholQR),  Q = core^T Y,
 // and the iteration stops once E = Q - X Rp^T, the part of core^T Y outside
 // span X, is below 1e-6 ||Rp||_F (or has stopped shrinking below 1e-5).
-// Then Y and X get a second CholQR pass, the r x r Rayleigh-Ritz matrix
-// T = Y^T core X follows from the triangular factors without another
-// product, and a one-sided Jacobi SVD of T in one warp gives
-// W_r = Y U_T, V_r = X V_T and sigma_r.  Singular values
-// <= max(|I|,|J|) * FLT_EPSILON * sigma_1 are dropped (numerical rank,
-// IRCUR_FLAG_WRANK).
+// Then Y and X get a second CholQR pass and the r x r Rayleigh-Ritz matrix
+// T = Y^T core X follows from the triangular factors without another product
+// (T is upper triangular).  With span Y = span W_r and span X = span V_r,
+// H_r(core) = Y T X^T and its pseudo-inverse is X T^{-1} Y^T = V_r
+// Sigma_r^{-1} W_r^T, so the panel passes need only Y, X T^{-1} and X T^T: no
+// r x r SVD on the iteration's path (sigma_kernel computes the singular
+// values of T on request).  Pivots of T <= max(|I|,|J|) * FLT_EPSILON times
+// the largest are dropped (numerical rank, IRCUR_FLAG_WRANK).
+//
+// Layout: the core sits in shared memory (one bulk copy) with a leading
+// dimension ldu = 4 (mod 8) floats, so 16-byte row vectors read by lanes on
+// consecutive rows hit distinct banks.  The m x r blocks X, Y, Q and the
+// partial sums are column-major (entry (i, t) at t * ldm + i): lanes always
+// run over i, so every access is conflict-free or a broadcast.
 //
 // Precision: FP32 throughout.  GB300's FP64 pipe runs at a small fraction of
-// its FP32 rate, and the serial FP64 Cholesky/sqrt/divide chains of a first
-// version cost more than the whole rest of the iteration; CholQR2 (the
-// second pass) restores orthogonality to FP32 rounding.
+// its FP32 rate, and serial FP64 Cholesky/sqrt/divide chains cost more than
+// the whole rest of the iteration; CholQR2 (the second pass) restores
+// orthogonality to FP32 rounding.
 #include <float.h>
 
 #include "device_common.cuh"
@@ -29,49 +37,65 @@
 namespace ircur {
 
 constexpr int kSvdThreads = 512;
+constexpr int kProdChunks = 8;  // max inner-dimension chunks of a core product
+constexpr int kSmallMats = 9;   // G, Rp, U, U2y, U2x, T, Ut, Vt, scratch (R x R each)
+constexpr size_t kSvdSmemBudget = 220 * 1024;
 
 __host__ __device__ constexpr int round_up4(int x) { return (x + 3) & ~3; }
 
 struct SvdLayout {
-  int ldu;   // leading dimension of the core copy in shared memory (odd)
-  int rx;    // row stride of the m x R blocks (R rounded up to 4)
-  int mmax;  // max(nI, nJ)
-  size_t off_us, off_x, off_y, off_q, off_part, off_small, total;
+  int ldu;  // leading dimension of the core (== ldCore: multiple of 4, ldu/4 odd)
+  int ldm;  // column stride of the m x R blocks: max(nI, nJ) rounded up to 4
+  int pch;  // inner-dimension chunks the partial-sum buffer holds (1..kProdChunks)
+  size_t off_us, off_x, off_y, off_q, off_part, off_small, off_bar, total;
 };
 
-constexpr int kSmallMats = 9;  // G, Rp, U, U2y, U2x, T, Ut, Vt, scratch (R x R each)
-
-__host__ __device__ inline SvdLayout svd_layout(int nI, int nJ, int R, bool core_in_smem) {
+__host__ __device__ inline SvdLayout svd_layout(int nI, int nJ, int ldCore, int R, bool core_in_smem) {
   SvdLayout L;
-  L.ldu = nJ | 1;
-  L.rx = round_up4(R);
-  L.mmax = nI > nJ ? nI : nJ;
+  L.ldu = ldCore;
+  L.ldm = round_up4(nI > nJ ? nI : nJ);
+  const size_t blk = (size_t)L.ldm * R * 4;
+  const size_t small = (size_t)kSmallMats * R * R * 4 + 3 * 32 * 4 + 64;
+  const size_t fixed = (core_in_smem ? (size_t)nI * L.ldu * 4 : 0) + 3 * blk + small + 16;
+  int pch = fixed < kSvdSmemBudget ? (int)((kSvdSmemBudget - fixed) / blk) : 0;
+  L.pch = pch < 1 ? 1 : (pch > kProdChunks ? kProdChunks : pch);
   size_t off = 0;
   L.off_us = off;
   if (core_in_smem) off += (size_t)nI * L.ldu * 4;
-  off = (off + 15) & ~(size_t)15;
   L.off_x = off;
-  off += (size_t)L.mmax * L.rx * 4;
+  off += blk;
   L.off_y = off;
-  off += (size_t)L.mmax * L.rx * 4;
+  off += blk;
   L.off_q = off;
-  off += (size_t)L.mmax * L.rx * 4;
+  off += blk;
   L.off_part = off;
-  off += (size_t)kSvdThreads * L.rx * 4;
+  off += (size_t)L.pch * blk;
   L.off_small = off;
-  off += (size_t)kSmallMats * R * R * 4 + 3 * 32 * 4 + 64;
+  off += small;
+  off = (off + 7) & ~(size_t)7;
+  L.off_bar = off;
+  off += 8;
   L.total = (off + 15) & ~(size_t)15;
   return L;
 }
 
+static int ld_core(int nJ) {
+  int ld = (nJ + 3) & ~3;
+  if (((ld / 4) & 1) == 0) ld += 4;
+  return ld;
+}
+
+// The core stays in shared memory when that leaves room for at least two
+// partial-sum chunks; otherwise the products read it from global memory (L2).
 size_t svd_smem_bytes(int nI, int nJ, int Rpad, bool* core_in_smem) {
-  SvdLayout L = svd_layout(nI, nJ, Rpad, true);
-  if (L.total <= 220 * 1024) {
+  const int ldc = ld_core(nJ);
+  SvdLayout L = svd_layout(nI, nJ, ldc, Rpad, true);
+  if (L.pch >= 2 && L.total <= kSvdSmemBudget) {
     *core_in_smem = true;
     return L.total;
   }
   *core_in_smem = false;
-  return svd_layout(nI, nJ, Rpad, false).total;
+  return svd_layout(nI, nJ, ldc, Rpad, false).total;
 }
 
 struct SvdSmall {
@@ -90,53 +114,113 @@ struct SvdSmall {
   int* ibuf;    // 16 ints
 };
 
-// out(o, t) = sum_q U(o, q) in(q, t), U = core (nI x nJ) or its transpose.
-// Threads are laid out as (chunk, row): the inner index range is split in nch
-// chunks whose partial sums are added in a fixed order (deterministic).
+// Adds the partial sums of a product (chunk-major, column-major blocks) in a
+// fixed order.
 template <int R>
-__device__ void core_product(const float* __restrict__ U, int ldu, bool transposed, int nout, int nin,
-                             const float* __restrict__ in, float* __restrict__ out, float* part, int rx) {
-  const int rows32 = (nout + 31) & ~31;
-  const int nch = blockDim.x / rows32 > 0 ? (int)(blockDim.x / rows32) : 1;
-  const int c = threadIdx.x / rows32, o = threadIdx.x % rows32;
-  if (c < nch && o < nout) {
-    float acc[R];
-#pragma unroll
-    for (int t = 0; t < R; ++t) acc[t] = 0.f;
-    const int q0 = (int)((long long)c * nin / nch), q1 = (int)((long long)(c + 1) * nin / nch);
-    if (transposed) {
-      for (int q = q0; q < q1; ++q) {
-        const float u = U[(size_t)q * ldu + o];
-        const float* m = in + (size_t)q * rx;
-#pragma unroll
-        for (int t = 0; t < R; ++t) acc[t] = fmaf(u, m[t], acc[t]);
-      }
-    } else {
-      for (int q = q0; q < q1; ++q) {
-        const float u = U[(size_t)o * ldu + q];
-        const float* m = in + (size_t)q * rx;
-#pragma unroll
-        for (int t = 0; t < R; ++t) acc[t] = fmaf(u, m[t], acc[t]);
-      }
-    }
-    if (nch == 1) {
-#pragma unroll
-      for (int t = 0; t < R; ++t) out[(size_t)o * rx + t] = acc[t];
-    } else {
-#pragma unroll
-      for (int t = 0; t < R; ++t) part[((size_t)c * rows32 + o) * rx + t] = acc[t];
+__device__ __forceinline__ void reduce_parts(const float* part, int nch, int nout, int ldm, float* out) {
+  __syncthreads();
+  for (int t = 0; t < R; ++t) {
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+      float s = 0.f;
+      for (int c = 0; c < nch; ++c) s += part[(size_t)c * R * ldm + (size_t)t * ldm + o];
+      out[(size_t)t * ldm + o] = s;
     }
   }
   __syncthreads();
-  if (nch > 1) {
-    for (int idx = threadIdx.x; idx < nout * R; idx += blockDim.x) {
-      const int oo = idx / R, t = idx % R;
-      float s = 0.f;
-      for (int cc = 0; cc < nch; ++cc) s += part[((size_t)cc * rows32 + oo) * rx + t];
-      out[(size_t)oo * rx + t] = s;
+}
+
+// out = core X (nout = |I| rows, inner nin = |J|).  A thread owns RB rows
+// spaced G apart (lanes on consecutive rows) and an inner chunk; core rows are
+// read as 16-byte vectors and each 4-row slab of every column of X is a
+// 16-byte broadcast shared by the RB rows.  Rows of X beyond nin are zero.
+template <int R, int RB = (R > 10 ? 2 : 4)>
+__device__ void core_times(const float* __restrict__ U, int ldu, int nout, int nin, const float* __restrict__ in,
+                           float* __restrict__ out, float* part, int ldm, int pch) {
+  const int G = (nout + RB - 1) / RB;
+  const int lanes = (G + 31) & ~31;
+  int nch = (int)blockDim.x / lanes;
+  nch = nch < 1 ? 1 : (nch > pch ? pch : nch);
+  const int c = threadIdx.x / lanes, og = threadIdx.x % lanes;
+  const int nin4 = round_up4(nin);
+  const int qc = round_up4((nin4 + nch - 1) / nch);
+  if (c < nch && og < G) {
+    float acc[RB][R];
+#pragma unroll
+    for (int kk = 0; kk < RB; ++kk)
+#pragma unroll
+      for (int t = 0; t < R; ++t) acc[kk][t] = 0.f;
+    const int q0 = c * qc, q1 = q0 + qc < nin4 ? q0 + qc : nin4;
+    for (int q = q0; q < q1; q += 4) {
+      float4 u[RB];
+#pragma unroll
+      for (int kk = 0; kk < RB; ++kk) {
+        const int o = og + kk * G;
+        u[kk] = o < nout ? *reinterpret_cast<const float4*>(U + (size_t)o * ldu + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        const float4 x = *reinterpret_cast<const float4*>(in + (size_t)t * ldm + q);
+#pragma unroll
+        for (int kk = 0; kk < RB; ++kk) {
+          float a = acc[kk][t];
+          a = fmaf(u[kk].x, x.x, a);
+          a = fmaf(u[kk].y, x.y, a);
+          a = fmaf(u[kk].z, x.z, a);
+          a = fmaf(u[kk].w, x.w, a);
+          acc[kk][t] = a;
+        }
+      }
     }
-    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < RB; ++kk) {
+      const int o = og + kk * G;
+      if (o < nout) {
+#pragma unroll
+        for (int t = 0; t < R; ++t) part[(size_t)c * R * ldm + (size_t)t * ldm + o] = acc[kk][t];
+      }
+    }
   }
+  reduce_parts<R>(part, nch, nout, ldm, out);
+}
+
+// out = core^T Y (nout = |J| rows, inner nin = |I|).  A thread owns one
+// output row j (lanes on consecutive j) and an inner chunk stepped by 4: four
+// core entries down column j and one 16-byte broadcast per column of Y.
+// Rows of Y beyond nin are zero.
+template <int R>
+__device__ void core_t_times(const float* __restrict__ U, int ldu, int nout, int nin, const float* __restrict__ in,
+                             float* __restrict__ out, float* part, int ldm, int pch) {
+  const int lanes = (nout + 31) & ~31;
+  int nch = (int)blockDim.x / lanes;
+  nch = nch < 1 ? 1 : (nch > pch ? pch : nch);
+  const int c = threadIdx.x / lanes, j = threadIdx.x % lanes;
+  const int nin4 = round_up4(nin);
+  const int ic = round_up4((nin4 + nch - 1) / nch);
+  if (c < nch && j < nout) {
+    float acc[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) acc[t] = 0.f;
+    const int i0 = c * ic, i1 = i0 + ic < nin4 ? i0 + ic : nin4;
+    for (int i = i0; i < i1; i += 4) {
+      const float u0 = U[(size_t)i * ldu + j];
+      const float u1 = i + 1 < nin ? U[(size_t)(i + 1) * ldu + j] : 0.f;
+      const float u2 = i + 2 < nin ? U[(size_t)(i + 2) * ldu + j] : 0.f;
+      const float u3 = i + 3 < nin ? U[(size_t)(i + 3) * ldu + j] : 0.f;
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        const float4 y = *reinterpret_cast<const float4*>(in + (size_t)t * ldm + i);
+        float a = acc[t];
+        a = fmaf(u0, y.x, a);
+        a = fmaf(u1, y.y, a);
+        a = fmaf(u2, y.z, a);
+        a = fmaf(u3, y.w, a);
+        acc[t] = a;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < R; ++t) part[(size_t)c * R * ldm + (size_t)t * ldm + j] = acc[t];
+  }
+  reduce_parts<R>(part, nch, nout, ldm, out);
 }
 
 template <int R>
@@ -148,14 +232,14 @@ __device__ __forceinline__ float sel(const float (&g)[R], int t) {
   return v;
 }
 
-// Cholesky QR of the nrows x r block Min (stride rx) into Mout (may alias):
-// Min = Mout U with U upper triangular (written to Uout).  The Gram matrix is
-// formed by warps (one entry per warp), factorised by warp 0 (lane l holds row
-// l of the Schur complement), and applied by forward substitution row by row.
-// Pivots <= 1e-12 of the largest diagonal entry mark dependent columns: they
-// become zero columns and are counted (returned).
+// Cholesky QR of the nrows x r block Min (column-major, stride ldm) into Mout
+// (may alias): Min = Mout U with U upper triangular (written to Uout).  The
+// Gram matrix is formed by warps (one entry per warp), factorised by warp 0
+// (lane l holds row l of the Schur complement), and applied by forward
+// substitution row by row.  Pivots <= 1e-12 of the largest diagonal entry
+// mark dependent columns: they become zero columns and are counted.
 template <int R>
-__device__ int cholqr(const float* Min, float* Mout, int nrows, int r, int rx, float* Uout, const SvdSmall& sm) {
+__device__ int cholqr(const float* Min, float* Mout, int nrows, int r, int ldm, float* Uout, const SvdSmall& sm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int npairs = r * (r + 1) / 2;
   for (int p = warp; p < npairs; p += nwarps) {
@@ -165,8 +249,10 @@ __device__ int cholqr(const float* Min, float* Mout, int nrows, int r, int rx, f
       ++s;
     }
     const int t = s + rem;
+    const float* ms = Min + (size_t)s * ldm;
+    const float* mt = Min + (size_t)t * ldm;
     float acc = 0.f;
-    for (int i = lane; i < nrows; i += 32) acc = fmaf(Min[(size_t)i * rx + s], Min[(size_t)i * rx + t], acc);
+    for (int i = lane; i < nrows; i += 32) acc = fmaf(ms[i], mt[i], acc);
     acc = warp_sum(acc);
     if (lane == 0) {
       sm.G[s * R + t] = acc;
@@ -183,7 +269,7 @@ __device__ int cholqr(const float* Min, float* Mout, int nrows, int r, int rx, f
     for (int o = 16; o > 0; o >>= 1) maxd = fmaxf(maxd, __shfl_xor_sync(0xffffffffu, maxd, o));
     int brk = 0;
     for (int t = 0; t < r; ++t) {
-      const float gt = sel<R>(g, t);  // this lane's entry (lane, t) = (t, lane) of the complement
+      const float gt = sel<R>(g, t);  // entry (lane, t) = (t, lane) of the Schur complement
       const float dgt = __shfl_sync(0xffffffffu, gt, t);
       const bool keep = dgt > 1e-12f * maxd && dgt <= FLT_MAX;
       const float rinv = keep ? rsqrtf(dgt) : 0.f;
@@ -215,7 +301,7 @@ __device__ int cholqr(const float* Min, float* Mout, int nrows, int r, int rx, f
   for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
     float m[R], y[R];
 #pragma unroll
-    for (int s = 0; s < R; ++s) m[s] = Min[(size_t)i * rx + s];
+    for (int s = 0; s < R; ++s) m[s] = Min[(size_t)s * ldm + i];
 #pragma unroll
     for (int t = 0; t < R; ++t) {
       float v = m[t];
@@ -224,7 +310,7 @@ __device__ int cholqr(const float* Min, float* Mout, int nrows, int r, int rx, f
       y[t] = v * sm.dinv[t];
     }
 #pragma unroll
-    for (int t = 0; t < R; ++t) Mout[(size_t)i * rx + t] = y[t];
+    for (int t = 0; t < R; ++t) Mout[(size_t)t * ldm + i] = y[t];
   }
   const int brk = sm.ibuf[0];
   __syncthreads();
@@ -253,14 +339,14 @@ __global__ void __launch_bounds__(kSvdThreads, 1) svd_kernel(IterDesc d, int cor
   const int cur = k & 1;
   const int nI = d.nI, nJ = d.nJ, r = d.r;
   const int* J = d.J_all + (d.resample ? (int64_t)k * nJ : 0);
-  const SvdLayout L = svd_layout(nI, nJ, R, core_in_smem != 0);
-  const int rx = L.rx;
+  const SvdLayout L = svd_layout(nI, nJ, d.ldCore, R, core_in_smem != 0);
+  const int ldm = L.ldm, ldu = L.ldu;
   float* Us = core_in_smem ? reinterpret_cast<float*>(smem + L.off_us) : d.core;
-  const int ldu = core_in_smem ? L.ldu : nJ;
   float* X = reinterpret_cast<float*>(smem + L.off_x);
   float* Y = reinterpret_cast<float*>(smem + L.off_y);
   float* Q = reinterpret_cast<float*>(smem + L.off_q);
   float* part = reinterpret_cast<float*>(smem + L.off_part);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.off_bar);
   SvdSmall sm;
   {
     float* p = reinterpret_cast<float*>(smem + L.off_small);
@@ -290,29 +376,44 @@ __global__ void __launch_bounds__(kSvdThreads, 1) svd_kernel(IterDesc d, int cor
     p += 32;
     sm.ibuf = reinterpret_cast<int*>(p);
   }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 
-  // ---- core into shared memory (odd leading dimension: conflict-free columns)
-  if (core_in_smem) {
-    for (int q = threadIdx.x; q < nI * nJ; q += blockDim.x) {
-      const int i = q / nJ, j = q - i * nJ;
-      Us[(size_t)i * ldu + j] = d.core[q];
-    }
+  // ---- core into shared memory: one bulk copy (TMA engine) of nI x ldu floats
+  const unsigned core_bytes = (unsigned)((size_t)nI * ldu * 4);
+  if (core_in_smem && threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(bar, core_bytes);
+    bulk_g2s(Us, d.core, core_bytes, bar);
   }
-  // ---- warm start X = B_k(:,J)^T (zero columns t >= r)
+  // ---- X, Y, Q zeroed (padding rows must read as zero); warm start X = B_k(:,J)^T
+  for (int q = threadIdx.x; q < 3 * R * ldm; q += blockDim.x) X[q] = 0.f;  // X, Y, Q are contiguous
+  __syncthreads();
   const float* Bk = d.B[cur];
-  for (int q = threadIdx.x; q < nJ * rx; q += blockDim.x) {
-    const int b = q / rx, t = q - b * rx;
-    X[q] = (t < r) ? Bk[(int64_t)t * d.n2 + J[b]] : 0.f;
+  for (int b = threadIdx.x; b < nJ; b += blockDim.x) {
+    const int64_t jb = J[b];
+#pragma unroll
+    for (int t = 0; t < R; ++t) X[(size_t)t * ldm + b] = (t < r) ? Bk[(int64_t)t * d.n2 + jb] : 0.f;
   }
   __syncthreads();
-  int brk = cholqr<R>(X, X, nJ, r, rx, sm.U, sm);
+  int brk = cholqr<R>(X, X, nJ, r, ldm, sm.U, sm);
   if (brk > 0) {  // first iteration (B_0 = 0) or a deficient factor: random start
-    for (int q = threadIdx.x; q < nJ * rx; q += blockDim.x) {
-      const int t = q % rx;
-      X[q] = (t < r) ? hash_uniform(d.seed ^ 0x5bd1e995ull, ((uint64_t)k << 32) ^ (uint64_t)q) : 0.f;
+    for (int b = threadIdx.x; b < nJ; b += blockDim.x) {
+#pragma unroll
+      for (int t = 0; t < R; ++t)
+        X[(size_t)t * ldm + b] =
+            (t < r) ? hash_uniform(d.seed ^ 0x5bd1e995ull, ((uint64_t)k << 32) ^ (uint64_t)(b * R + t)) : 0.f;
     }
     __syncthreads();
-    cholqr<R>(X, X, nJ, r, rx, sm.U, sm);
+    cholqr<R>(X, X, nJ, r, ldm, sm.U, sm);
+  }
+  if (core_in_smem) {
+    bool ok = mbar_wait_bounded(bar, 0, d.spinLimit);
+    if (!ok) {
+      if (threadIdx.x == 0) atomicExch(&st->status, (int)IRCUR_ETIMEOUT);
+      mbar_wait_bounded(bar, 0, kSpinLimit);  // let the copy land before the block exits
+    }
+    if (!__syncthreads_and(ok)) return;
   }
 
   // ---- subspace iteration
@@ -321,29 +422,34 @@ __global__ void __launch_bounds__(kSvdThreads, 1) svd_kernel(IterDesc d, int cor
   float prev_res = 0.f;
   while (true) {
     ++steps;
-    core_product<R>(Us, ldu, false, nI, nJ, X, Y, part, rx);  // Y = core X
-    cholqr<R>(Y, Y, nI, r, rx, sm.Rp, sm);                     // Y Rp = core X
-    core_product<R>(Us, ldu, true, nJ, nI, Y, Q, part, rx);    // Q = core^T Y
+    core_times<R>(Us, ldu, nI, nJ, X, Y, part, ldm, L.pch);    // Y = core X
+    cholqr<R>(Y, Y, nI, r, ldm, sm.Rp, sm);                    // Y Rp = core X
+    core_t_times<R>(Us, ldu, nJ, nI, Y, Q, part, ldm, L.pch);  // Q = core^T Y
     // ||Q - X Rp^T||_F^2 and ||Rp||_F^2 in one block reduction
     float e2 = 0.f;
-    for (int q = threadIdx.x; q < nJ * r; q += blockDim.x) {
-      const int b = q / r, t = q - b * r;
-      float v = Q[(size_t)b * rx + t];
-      for (int s = t; s < r; ++s) v = fmaf(-X[(size_t)b * rx + s], sm.Rp[t * R + s], v);
-      e2 = fmaf(v, v, e2);
+    for (int b = threadIdx.x; b < nJ; b += blockDim.x) {
+      float xr[R];
+#pragma unroll
+      for (int t = 0; t < R; ++t) xr[t] = X[(size_t)t * ldm + b];
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        float v = Q[(size_t)t * ldm + b];
+#pragma unroll
+        for (int s2 = t; s2 < R; ++s2) v = fmaf(-xr[s2], sm.Rp[t * R + s2], v);
+        e2 = fmaf(v, v, e2);
+      }
     }
     float rc2 = 0.f;
     if (threadIdx.x < R * R) rc2 = sm.Rp[threadIdx.x] * sm.Rp[threadIdx.x];
     e2 = warp_sum(e2);
     rc2 = warp_sum(rc2);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
       sm.red[warp] = e2;
       sm.red[16 + warp] = rc2;
     }
     __syncthreads();
     float E2 = 0.f, RC2 = 0.f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    for (int w = 0; w < nwarps; ++w) {
       E2 += sm.red[w];
       RC2 += sm.red[16 + w];
     }
@@ -354,12 +460,12 @@ __global__ void __launch_bounds__(kSvdThreads, 1) svd_kernel(IterDesc d, int cor
     }
     if (steps >= d.svdMaxSteps) break;  // keep X, Y, Rp of the same step
     prev_res = res;
-    cholqr<R>(Q, X, nJ, r, rx, sm.U, sm);  // X = orth(core^T Y)
+    cholqr<R>(Q, X, nJ, r, ldm, sm.U, sm);  // X = orth(core^T Y)
   }
 
   // ---- second CholQR passes; T = U2y Rp U2x^{-1} = Y^T core X for the new bases
-  cholqr<R>(Y, Y, nI, r, rx, sm.U2y, sm);
-  cholqr<R>(X, X, nJ, r, rx, sm.U2x, sm);
+  cholqr<R>(Y, Y, nI, r, ldm, sm.U2y, sm);
+  cholqr<R>(X, X, nJ, r, ldm, sm.U2x, sm);
   if (threadIdx.x < 32) {
     const int s = threadIdx.x;
     if (s < r) {
@@ -385,101 +491,70 @@ __global__ void __launch_bounds__(kSvdThreads, 1) svd_kernel(IterDesc d, int cor
   }
   __syncthreads();
 
-  // ---- one-sided Jacobi SVD of T (r x r) in warp 0: lane p owns column p
-  if (threadIdx.x < 32) {
-    const int p = threadIdx.x;
-    float tc[R], vc[R];
+  // ---- numerical rank from the diagonal of the upper-triangular T (its
+  // singular values up to the off-diagonal part, which the iteration has
+  // driven below 1e-6 of ||T||), and the inverse of T on the kept pivots.
+  if (warp == 0) {
+    const float dabs = lane < r ? fabsf(sm.T[lane * R + lane]) : 0.f;
+    float dmax = dabs;
 #pragma unroll
-    for (int i = 0; i < R; ++i) {
-      tc[i] = (p < r && i < r) ? sm.T[i * R + p] : 0.f;
-      vc[i] = (i == p) ? 1.f : 0.f;
-    }
-    const int nplay = (r + 1) & ~1;
-    for (int sweep = 0; sweep < 40; ++sweep) {
-      int rotated = 0;
-      for (int rnd = 0; rnd < nplay - 1; ++rnd) {
-        const int q = (p < nplay) ? rr_partner(p, rnd, nplay) : p;
-        float tq[R], vq[R];
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-          tq[i] = __shfl_sync(0xffffffffu, tc[i], q);
-          vq[i] = __shfl_sync(0xffffffffu, vc[i], q);
+    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    const float tol = (float)(nI > nJ ? nI : nJ) * FLT_EPSILON * dmax;
+    const bool keep = lane < r && dabs > tol && dabs > 0.f;
+    const unsigned kmask = __ballot_sync(0xffffffffu, keep);
+    if (lane < r) {  // column `lane` of T^{-1} by back substitution
+      const int c = lane;
+      for (int s2 = R - 1; s2 >= 0; --s2) {
+        float v = 0.f;
+        if (s2 <= c && ((kmask >> s2) & 1u)) {
+          v = (s2 == c) ? 1.f : 0.f;
+          for (int u = s2 + 1; u <= c; ++u) v = fmaf(-sm.T[s2 * R + u], sm.tmp[u * R + c], v);
+          v = v / sm.T[s2 * R + s2];
         }
-        if (p < r && q < r && q != p) {
-          const bool lo = p < q;
-          float app = 0.f, aqq = 0.f, apq = 0.f;
-#pragma unroll
-          for (int i = 0; i < R; ++i) {
-            const float a = lo ? tc[i] : tq[i];
-            const float b = lo ? tq[i] : tc[i];
-            app = fmaf(a, a, app);
-            aqq = fmaf(b, b, aqq);
-            apq = fmaf(a, b, apq);
-          }
-          if (fabsf(apq) > 1e-7f * sqrtf(app * aqq) && apq != 0.f) {
-            rotated = 1;
-            const float zeta = (aqq - app) / (2.f * apq);
-            const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-            const float c = rsqrtf(1.f + tt * tt), s = c * tt;
-#pragma unroll
-            for (int i = 0; i < R; ++i) {
-              const float a = lo ? tc[i] : tq[i], b = lo ? tq[i] : tc[i];
-              const float va = lo ? vc[i] : vq[i], vb = lo ? vq[i] : vc[i];
-              tc[i] = lo ? (c * a - s * b) : (s * a + c * b);
-              vc[i] = lo ? (c * va - s * vb) : (s * va + c * vb);
-            }
-          }
-        }
+        sm.tmp[s2 * R + c] = v;
       }
-      if (!__any_sync(0xffffffffu, rotated)) break;
+      sm.sig[lane] = keep ? dabs : 0.f;
     }
-    float s2 = 0.f;
-#pragma unroll
-    for (int i = 0; i < R; ++i) s2 = fmaf(tc[i], tc[i], s2);
-    const float sg = (p < r) ? sqrtf(s2) : -1.f;
-    int pos = 0;
-    for (int q = 0; q < r; ++q) {
-      const float sq = __shfl_sync(0xffffffffu, sg, q);
-      pos += (sq > sg) || (sq == sg && q < p);
-    }
-    if (p < r) {
-      const float inv = sg > 0.f ? 1.f / sg : 0.f;
-#pragma unroll
-      for (int i = 0; i < R; ++i) {
-        sm.Ut[i * R + pos] = tc[i] * inv;
-        sm.Vt[i * R + pos] = vc[i];
+    if (lane == 0) {
+      sm.ibuf[1] = __popc(kmask);
+      sm.ibuf[2] = (int)kmask;
+      for (int t = r; t < R; ++t) {
+        sm.sig[t] = 0.f;
+        for (int u = 0; u < R; ++u) sm.tmp[u * R + t] = 0.f;
       }
-      sm.sig[pos] = sg;
-    }
-    __syncwarp();
-    if (p == 0) {
-      const float s0 = sm.sig[0];
-      const float tol = (float)(nI > nJ ? nI : nJ) * FLT_EPSILON * s0;
-      int rank = 0;
-      for (int t = 0; t < r; ++t) rank += sm.sig[t] > tol && sm.sig[t] > 0.f;
-      sm.ibuf[1] = rank;
-      for (int t = r; t < R; ++t) sm.sig[t] = 0.f;
     }
   }
   __syncthreads();
   const int rank = sm.ibuf[1];
-  // W = Y Ut (nI x R), V = X Vt, Vs = V / sigma; zero columns beyond the rank
-  for (int q = threadIdx.x; q < nI * R; q += blockDim.x) {
-    const int i = q / R, t = q - i * R;
-    float v = 0.f;
-    if (t < rank)
-      for (int s = 0; s < r; ++s) v = fmaf(Y[(size_t)i * rx + s], sm.Ut[s * R + t], v);
-    d.W[q] = v;
+  const unsigned kmask = (unsigned)sm.ibuf[2];
+  // Outputs for the panel passes (U^+ = X T^{-1} Y^T, the pseudo-inverse of
+  // H_r(core) = Y T X^T):
+  //   W  = Y          (row pass: B_{k+1} = Y^T R, residual R - Y Y^T R),
+  //   Vs = X T^{-1}   (column pass: A_{k+1} = C X T^{-1}),
+  //   V  = X T^T      (column pass residual C - A_{k+1} T X^T = C - C X X^T).
+  for (int i = threadIdx.x; i < nI; i += blockDim.x) {
+#pragma unroll
+    for (int t = 0; t < R; ++t) d.W[(size_t)i * R + t] = ((kmask >> t) & 1u) ? Y[(size_t)t * ldm + i] : 0.f;
   }
-  for (int q = threadIdx.x; q < nJ * R; q += blockDim.x) {
-    const int b = q / R, t = q - b * R;
-    float v = 0.f;
-    if (t < rank)
-      for (int s = 0; s < r; ++s) v = fmaf(X[(size_t)b * rx + s], sm.Vt[s * R + t], v);
-    d.V[q] = v;
-    d.Vs[q] = (t < rank) ? v / sm.sig[t] : 0.f;
+  for (int b = threadIdx.x; b < nJ; b += blockDim.x) {
+    float x[R];
+#pragma unroll
+    for (int s2 = 0; s2 < R; ++s2) x[s2] = X[(size_t)s2 * ldm + b];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      float vp = 0.f, vr = 0.f;
+#pragma unroll
+      for (int s2 = 0; s2 < R; ++s2) {
+        vp = fmaf(x[s2], sm.tmp[s2 * R + t], vp);
+        vr = fmaf(x[s2], sm.T[t * R + s2], vr);
+      }
+      const bool kt = (kmask >> t) & 1u;
+      d.Vs[(size_t)b * R + t] = kt ? vp : 0.f;
+      d.V[(size_t)b * R + t] = kt ? vr : 0.f;
+    }
   }
-  if (threadIdx.x < R) d.sigma[threadIdx.x] = (threadIdx.x < rank) ? sm.sig[threadIdx.x] : 0.f;
+  if (threadIdx.x < R) d.sigma[threadIdx.x] = sm.sig[threadIdx.x];
+  if (threadIdx.x < R * R) d.Tm[threadIdx.x] = sm.T[threadIdx.x];
   if (threadIdx.x == 0) {
     unsigned f = 0u;
     if (rank < r) f |= IRCUR_FLAG_WRANK;
@@ -487,6 +562,85 @@ __global__ void __launch_bounds__(kSvdThreads, 1) svd_kernel(IterDesc d, int cor
     if (f) atomicOr(&st->flags, f);
     st->svd_steps += steps;
     st->svd_last_steps = steps;
+  }
+}
+
+// Singular values of the last Rayleigh-Ritz matrix T (the r largest singular
+// values of the last core, descending): one-sided Jacobi in one warp, lane p
+// owning column p, round-robin pair ordering.  Used on request only.
+template <int R>
+__global__ void sigma_kernel(const float* __restrict__ Tm, int r, float* __restrict__ sigma) {
+  const int p = threadIdx.x;
+  float tc[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) tc[i] = (p < r && i < r) ? Tm[i * R + p] : 0.f;
+  const int nplay = (r + 1) & ~1;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    int rotated = 0;
+    for (int rnd = 0; rnd < nplay - 1; ++rnd) {
+      const int q = (p < nplay) ? rr_partner(p, rnd, nplay) : p;
+      float tq[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) tq[i] = __shfl_sync(0xffffffffu, tc[i], q);
+      if (p < r && q < r && q != p) {
+        const bool lo = p < q;
+        float app = 0.f, aqq = 0.f, apq = 0.f;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          const float a = lo ? tc[i] : tq[i];
+          const float b = lo ? tq[i] : tc[i];
+          app = fmaf(a, a, app);
+          aqq = fmaf(b, b, aqq);
+          apq = fmaf(a, b, apq);
+        }
+        if (fabsf(apq) > 1e-6f * sqrtf(app * aqq)) {
+          rotated = 1;
+          const float zeta = (aqq - app) / (2.f * apq);
+          const float tt = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          const float c = rsqrtf(1.f + tt * tt), s = c * tt;
+#pragma unroll
+          for (int i = 0; i < R; ++i) {
+            const float a = lo ? tc[i] : tq[i], b = lo ? tq[i] : tc[i];
+            tc[i] = lo ? (c * a - s * b) : (s * a + c * b);
+          }
+        }
+      }
+    }
+    if (!__any_sync(0xffffffffu, rotated)) break;
+  }
+  float s2 = 0.f;
+#pragma unroll
+  for (int i = 0; i < R; ++i) s2 = fmaf(tc[i], tc[i], s2);
+  const float sg = (p < r) ? sqrtf(s2) : -1.f;
+  int pos = 0;
+  for (int q = 0; q < r; ++q) {
+    const float sq = __shfl_sync(0xffffffffu, sg, q);
+    pos += (sq > sg) || (sq == sg && q < p);
+  }
+  if (p < r) sigma[pos] = sg;
+}
+
+template <int R>
+static cudaError_t launch_sigma_r(const float* Tm, int r, float* sigma, cudaStream_t s) {
+  sigma_kernel<R><<<1, 32, 0, s>>>(Tm, r, sigma);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sigma(const float* Tm, int r, int Rpad, float* sigma, cudaStream_t s) {
+  switch (Rpad) {
+    case 1: return launch_sigma_r<1>(Tm, r, sigma, s);
+    case 2: return launch_sigma_r<2>(Tm, r, sigma, s);
+    case 3: return launch_sigma_r<3>(Tm, r, sigma, s);
+    case 4: return launch_sigma_r<4>(Tm, r, sigma, s);
+    case 5: return launch_sigma_r<5>(Tm, r, sigma, s);
+    case 6: return launch_sigma_r<6>(Tm, r, sigma, s);
+    case 7: return launch_sigma_r<7>(Tm, r, sigma, s);
+    case 8: return launch_sigma_r<8>(Tm, r, sigma, s);
+    case 9: return launch_sigma_r<9>(Tm, r, sigma, s);
+    case 10: return launch_sigma_r<10>(Tm, r, sigma, s);
+    case 12: return launch_sigma_r<12>(Tm, r, sigma, s);
+    case 16: return launch_sigma_r<16>(Tm, r, sigma, s);
+    default: return cudaErrorInvalidValue;
   }
 }
 
