@@ -68,6 +68,8 @@ struct ircur_ctx {
   int64_t ldPr, ldPc, ldDT;
   float* A[2];
   float* B[2];
+  float* AI;
+  float* BJt;
   float* core;
   float* W;
   float* V;
@@ -82,6 +84,7 @@ struct ircur_ctx {
   cudaGraphExec_t exec;
   const float* graph_D;
   int64_t graph_ldD;
+  int graph_sample_ahead;
   // last solve
   int solved;
   State host_state;
@@ -170,10 +173,11 @@ extern "C" ircur_status ircur_create(const ircur_params* params, void* stream, i
   if (((ldCore / 4) & 1) == 0) ldCore += 4;
   d.ldCore = ldCore;
   const size_t oCore = take((size_t)p.nI * ldCore * 4);
+  const size_t oAI = take((size_t)p.nI * R * 4), oBJ = take((size_t)p.nJ * R * 4);
   const size_t oW = take((size_t)p.nI * R * 4), oV = take((size_t)p.nJ * R * 4), oVs = take((size_t)p.nJ * R * 4);
   const size_t oSig = take((size_t)R * 4);
   const size_t oTm = take((size_t)R * R * 4);
-  const size_t oPart = take((size_t)(d.nRowTiles + d.nColTiles) * 2 * 8);
+  const size_t oPart = take((size_t)(d.nRowTiles + d.nColTiles + 2) * 2 * 8);  // + the two sampler blocks
   const size_t oErr = take((size_t)p.max_iter * 8);
   const size_t oSt = take(sizeof(State));
   c->ws_bytes = off;
@@ -202,6 +206,8 @@ extern "C" ircur_status ircur_create(const ircur_params* params, void* stream, i
   c->B[0] = reinterpret_cast<float*>(base + oB0);
   c->B[1] = reinterpret_cast<float*>(base + oB1);
   c->core = reinterpret_cast<float*>(base + oCore);
+  c->AI = reinterpret_cast<float*>(base + oAI);
+  c->BJt = reinterpret_cast<float*>(base + oBJ);
   c->W = reinterpret_cast<float*>(base + oW);
   c->V = reinterpret_cast<float*>(base + oV);
   c->Vs = reinterpret_cast<float*>(base + oVs);
@@ -245,6 +251,8 @@ extern "C" ircur_status ircur_create(const ircur_params* params, void* stream, i
   d.B[0] = c->B[0];
   d.B[1] = c->B[1];
   d.core = c->core;
+  d.AI = c->AI;
+  d.BJt = c->BJt;
   d.W = c->W;
   d.V = c->V;
   d.Vs = c->Vs;
@@ -318,6 +326,7 @@ static ircur_status build_graph(ircur_ctx* c, const IterDesc& d0) {
   IRCUR_CK(cudaGraphInstantiate(&c->exec, c->graph, 0));
   c->graph_D = d0.D;
   c->graph_ldD = d0.ldD;
+  c->graph_sample_ahead = d0.sampleAhead;
   return IRCUR_OK;
 }
 
@@ -340,6 +349,7 @@ extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, c
   d.rowSrc = p.resample ? D : c->Prow;
   d.rowLd = p.resample ? ldD : c->ldPr;
   d.rowBulk = p.resample ? ((aligned16(D) && ldD % 4 == 0) ? 1 : 0) : 1;
+  d.sampleAhead = (p.resample && !idx_I) ? 1 : 0;
   c->desc = d;
 
   const double zeta0 = p.zeta0 > 0 ? p.zeta0 : 0.0;
@@ -350,7 +360,8 @@ extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, c
     IRCUR_CK(launch_check_indices(c->I_all, c->draws, p.nI, p.n1, &c->st->status, s));
     IRCUR_CK(launch_check_indices(c->J_all, c->draws, p.nJ, p.n2, &c->st->status, s));
   } else {
-    IRCUR_CK(launch_sample(p.seed, 0, c->draws, p.n1, p.n2, p.nI, p.nJ, c->I_all, c->J_all, -1, s));
+    // draw 0 now; IRCUR-R draws k+1 inside iteration k's pass kernel
+    IRCUR_CK(launch_sample(p.seed, 0, 1, p.n1, p.n2, p.nI, p.nJ, c->I_all, c->J_all, -1, s));
   }
   if (p.resample) {
     // D^T for the column panels, with max|D| and the NaN/Inf scan in the same pass
@@ -364,7 +375,7 @@ extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, c
   IRCUR_CK(cudaMemsetAsync(c->B[0], 0, (size_t)c->Rpad * p.n2 * 4, s));
 
   if (use_graph()) {
-    if (!c->exec || c->graph_D != D || c->graph_ldD != ldD) {
+    if (!c->exec || c->graph_D != D || c->graph_ldD != ldD || c->graph_sample_ahead != d.sampleAhead) {
       ircur_status bs = build_graph(c, d);
       if (bs != IRCUR_OK) return bs;
     }

@@ -99,6 +99,14 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
+// 16-byte asynchronous global -> shared copy (L2 only, no L1 allocation) and
+// the wait for all of a thread's outstanding copies.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Streaming 16-byte store (evict-first): outputs written once, never re-read here.
 __device__ __forceinline__ void st_stream(float4* p, float4 v) { __stcs(p, v); }
 

@@ -16,12 +16,13 @@ constexpr int kNumSMsHint = 152;
 // but ends a lost wait within a few seconds.
 constexpr long long kSpinLimit = 1ll << 26;
 
-// Panel-pass tiling: a block covers kPanelCols consecutive panel columns with
-// kPanelSplit threads per column, each thread handling a contiguous share of
-// the panel's rows.
-constexpr int kPanelCols = 64;
-constexpr int kPanelSplit = 4;
-constexpr int kPanelThreads = kPanelCols * kPanelSplit;
+// Panel-pass tiling: a block covers kPanelCols consecutive panel columns; a
+// thread owns two adjacent columns and one of kPanelSplit contiguous shares
+// of the panel's rows.
+constexpr int kPanelCols = 32;
+constexpr int kPanelSplit = 16;
+constexpr int kPanelThreads = (kPanelCols / 2) * kPanelSplit;
+constexpr int kMaxPanelRows = 512;  // largest |I|, |J| the kernels are built for
 
 // Device-resident solver state, written only by the kernels of one solve.
 struct State {
@@ -68,6 +69,8 @@ struct IterDesc {
   const int* J_all;     // (resample ? max_iter : 1) x nJ
   float* A[2];          // n1 x R row-major (R = padded rank of the kernels)
   float* B[2];          // R x n2 row-major
+  float* AI;            // nI x R    A_k(I,:) gathered by the core kernel
+  float* BJt;           // nJ x R    B_k(:,J)^T gathered by the core kernel
   float* core;          // nI x ldCore, row-major (columns nJ..ldCore-1 stay zero)
   int ldCore;           // nJ rounded up to 4, with ldCore/4 odd (conflict-free 16-byte rows)
   float* W;             // nI x R   Y: orthonormal basis of the core's dominant left subspace
@@ -79,8 +82,9 @@ struct IterDesc {
   double* errs;         // max_iter
   State* st;
   int nRowTiles, nColTiles;
-  int rowBulk, colBulk; // 1: panel tiles via cp.async.bulk (16-byte aligned rows)
+  int rowBulk, colBulk; // 1: panel rows are 16-byte aligned (tiles via 16-byte async copies)
   int svdMaxSteps;
+  int sampleAhead;      // 1: the pass kernel draws the next iteration's I, J (IRCUR-R, own sampler)
   long long spinLimit;      // first bounded wait on a bulk copy (kSpinLimit unless a fault is injected)
   unsigned long long cond;  // graph conditional handle (0 = no graph)
   uint64_t seed;

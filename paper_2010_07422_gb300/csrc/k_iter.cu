@@ -16,6 +16,7 @@
 // each residual formed explicitly (no difference of squared norms).
 #include "device_common.cuh"
 #include "ircur_internal.cuh"
+#include "sampler.cuh"
 
 namespace ircur {
 
@@ -42,12 +43,17 @@ __global__ void __launch_bounds__(256) core_kernel(IterDesc d) {
     float arow[R];
 #pragma unroll
     for (int t = 0; t < R; ++t) arow[t] = A[(int64_t)ia * R + t];
+    if (threadIdx.x < R) d.AI[(size_t)a * R + threadIdx.x] = A[(int64_t)ia * R + threadIdx.x];
     const float* rowp = d.rowSrc + (int64_t)(d.resample ? ia : a) * d.rowLd;
     for (int b = threadIdx.x; b < d.nJ; b += blockDim.x) {
       const int j = J[b];
       float bcol[R];
 #pragma unroll
       for (int t = 0; t < R; ++t) bcol[t] = B[(int64_t)t * d.n2 + j];
+      if (a == 0) {
+#pragma unroll
+        for (int t = 0; t < R; ++t) d.BJt[(size_t)b * R + t] = bcol[t];
+      }
       const float l = lowrank_entry<R>(arow, bcol);
       d.core[(int64_t)a * d.ldCore + b] = panel_value(rowp[j], l, zeta);
     }
@@ -68,11 +74,12 @@ __global__ void __launch_bounds__(256) core_kernel(IterDesc d) {
 // Both are the same computation on a row-major m x n panel with
 //   side = A_k(I,:) | B_k(:,J)^T (m x R), vec = B_k(:,j) | A_k(i,:)^T,
 //   proj = Y | X T^{-1},  recon = Y | X T^T  (U^+ = X T^{-1} Y^T, see k_svd.cu).
-// The m x kPanelCols tile is staged in shared memory by one bulk copy (TMA
-// engine) per panel row, overwritten with D - S, and read back by the second
-// sweep for the explicit residual.  kPanelSplit threads share a column, each
-// sweeping a contiguous share of the rows; their partial projections are
-// added in a fixed order.
+// The m x kPanelCols tile is staged in shared memory by 16-byte asynchronous
+// copies (the rows are gathered: one small segment per panel row, which the
+// per-instruction cost of bulk TMA copies makes slower), overwritten with
+// D - S, and read back by the second sweep for the explicit residual.  A
+// thread owns two adjacent columns and a contiguous share of the rows
+// (kPanelSplit shares); the partial projections are added in a fixed order.
 template <int R, bool COL>
 __device__ void panel_pass(const IterDesc& d, int tile, int k, float zeta, unsigned char* smem, double* acc2) {
   const int m = COL ? d.nJ : d.nI;
@@ -85,54 +92,26 @@ __device__ void panel_pass(const IterDesc& d, int tile, int k, float zeta, unsig
   const float* src = COL ? d.colSrc : d.rowSrc;
   const int64_t ld = COL ? d.colLd : d.rowLd;
 
+  constexpr int RX = (R + 3) & ~3;                         // 16-byte rows of the small matrices
   float* tileS = reinterpret_cast<float*>(smem);           // m x kPanelCols
-  float* side = tileS + (size_t)m * kPanelCols;             // m x R
-  float* proj = side + (size_t)m * R;                       // m x R
-  float* recon = COL ? proj + (size_t)m * R : proj;         // m x R (row pass: recon == proj)
-  float* part = proj + (size_t)(COL ? 2 : 1) * m * R;       // kPanelSplit x kPanelCols x R
-  // 8-byte aligned slot after the partial sums
-  uintptr_t bp = reinterpret_cast<uintptr_t>(part + (size_t)kPanelSplit * kPanelCols * R);
-  uint64_t* bar = reinterpret_cast<uint64_t*>((bp + 7) & ~(uintptr_t)7);
+  float* side = tileS + (size_t)m * kPanelCols;             // m x RX
+  float* proj = side + (size_t)m * RX;                      // m x RX
+  float* recon = COL ? proj + (size_t)m * RX : proj;        // m x RX (row pass: recon == proj)
+  float* part = proj + (size_t)(COL ? 2 : 1) * m * RX;      // kPanelSplit x kPanelCols x RX
+  float* outS = part + (size_t)kPanelSplit * kPanelCols * RX;  // kPanelCols x RX
 
   const int64_t j0 = (int64_t)tile * kPanelCols;
   const int ncols = (int)((ncolsTotal - j0) < kPanelCols ? (ncolsTotal - j0) : kPanelCols);
-  const bool bulk = (COL ? d.colBulk : d.rowBulk) && ncols == kPanelCols;
+  const bool vec16 = (COL ? d.colBulk : d.rowBulk) && ncols == kPanelCols;
 
-  if (bulk && threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
-  if (!COL) {
-    const float* A = d.A[cur];
-    for (int q = threadIdx.x; q < m * R; q += blockDim.x) {
-      const int a = q / R, t = q - a * R;
-      side[q] = A[(int64_t)I[a] * R + t];
-      proj[q] = d.W[q];
-    }
-  } else {
-    const float* B = d.B[cur];
-    for (int q = threadIdx.x; q < m * R; q += blockDim.x) {
-      const int b = q / R, t = q - b * R;
-      side[q] = B[(int64_t)t * d.n2 + J[b]];
-      proj[q] = d.Vs[q];
-      recon[q] = d.V[q];
-    }
-  }
-  __syncthreads();
-  bool ok = true;
-  if (bulk) {
-    if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, (unsigned)(m * kPanelCols * 4));
-    __syncwarp();
-    if (threadIdx.x < 32) {
-      for (int a = threadIdx.x; a < m; a += 32) {
-        const int64_t row = mapped ? map[a] : a;
-        bulk_g2s(tileS + (size_t)a * kPanelCols, src + row * ld + j0, (unsigned)(kPanelCols * 4), bar);
-      }
-    }
-    ok = mbar_wait_bounded(bar, 0, d.spinLimit);
-    if (!ok) {
-      atomicExch(&d.st->status, (int)IRCUR_ETIMEOUT);
-      mbar_wait_bounded(bar, 0, kSpinLimit);  // let copies in flight land before the block exits
+  // 1. the panel tile: 16-byte asynchronous copies issued first, so that they
+  //    fly during the staging of the small matrices
+  if (vec16) {
+    constexpr int kV = kPanelCols / 4;
+    for (int q = threadIdx.x; q < m * kV; q += blockDim.x) {
+      const int a = q / kV, c4 = q - a * kV;
+      const int64_t row = mapped ? __ldg(map + a) : a;
+      cp_async16(tileS + (size_t)a * kPanelCols + 4 * c4, src + row * ld + j0 + 4 * c4);
     }
   } else {
     for (int q = threadIdx.x; q < m * kPanelCols; q += blockDim.x) {
@@ -141,72 +120,138 @@ __device__ void panel_pass(const IterDesc& d, int tile, int k, float zeta, unsig
       tileS[q] = c < ncols ? src[row * ld + j0 + c] : 0.f;
     }
   }
-  ok = __syncthreads_and(ok);
-  if (!ok) return;
-
-  const int c = threadIdx.x % kPanelCols, h = threadIdx.x / kPanelCols;
-  const int a0 = (int)((long long)h * m / kPanelSplit), a1 = (int)((long long)(h + 1) * m / kPanelSplit);
-  const bool live = c < ncols;
-  const int64_t j = j0 + c;
-  float vec[R], acc[R];
-#pragma unroll
-  for (int t = 0; t < R; ++t) {
-    vec[t] = 0.f;
-    acc[t] = 0.f;
-  }
-  if (live) {
-    if (COL) {
-      const float* A = d.A[cur];
-#pragma unroll
-      for (int t = 0; t < R; ++t) vec[t] = A[j * R + t];
-    } else {
-      const float* B = d.B[cur];
-#pragma unroll
-      for (int t = 0; t < R; ++t) vec[t] = B[(int64_t)t * d.n2 + j];
+  // 2. the m x R side, projection and reconstruction matrices (rows padded to RX)
+  {
+    const float* sideG = COL ? d.BJt : d.AI;
+    for (int q = threadIdx.x; q < m * RX; q += blockDim.x) {
+      const int a = q / RX, t = q - a * RX;
+      const bool in = t < R;
+      side[q] = in ? sideG[a * R + t] : 0.f;
+      if (COL) {
+        proj[q] = in ? d.Vs[a * R + t] : 0.f;
+        recon[q] = in ? d.V[a * R + t] : 0.f;
+      } else {
+        proj[q] = in ? d.W[a * R + t] : 0.f;
+      }
     }
   }
-  float den = 0.f;
-  if (live) {
-    for (int a = a0; a < a1; ++a) {
-      float* cell = tileS + (size_t)a * kPanelCols + c;
-      const float dv = *cell;
-      const float v = panel_value(dv, lowrank_entry<R>(side + (size_t)a * R, vec), zeta);
-      *cell = v;
-      den = fmaf(dv, dv, den);
-#pragma unroll
-      for (int t = 0; t < R; ++t) acc[t] = fmaf(proj[(size_t)a * R + t], v, acc[t]);
-    }
-  }
-#pragma unroll
-  for (int t = 0; t < R; ++t) part[((size_t)h * kPanelCols + c) * R + t] = acc[t];
+  if (vec16) cp_async_wait_all();
   __syncthreads();
-  float out[R];
+
+  // thread = (column pair cp, row split h); columns c0 = 2 cp, c0 + 1
+  constexpr int kPairs = kPanelCols / 2;
+  const int cp = threadIdx.x % kPairs, h = threadIdx.x / kPairs;
+  const int c0 = 2 * cp;
+  const int a0 = (int)((long long)h * m / kPanelSplit), a1 = (int)((long long)(h + 1) * m / kPanelSplit);
+  const bool live0 = c0 < ncols, live1 = c0 + 1 < ncols;
+  const int64_t j = j0 + c0;
+  float vec0[R], vec1[R], acc0[R], acc1[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) {
-    float s = 0.f;
+    vec0[t] = vec1[t] = 0.f;
+    acc0[t] = acc1[t] = 0.f;
+  }
+  if (COL) {
+    const float* A = d.A[cur];
 #pragma unroll
-    for (int hh = 0; hh < kPanelSplit; ++hh) s += part[((size_t)hh * kPanelCols + c) * R + t];
-    out[t] = s;
+    for (int t = 0; t < R; ++t) {
+      if (live0) vec0[t] = A[j * R + t];
+      if (live1) vec1[t] = A[(j + 1) * R + t];
+    }
+  } else {
+    const float* B = d.B[cur];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      if (live0) vec0[t] = B[(int64_t)t * d.n2 + j];
+      if (live1) vec1[t] = B[(int64_t)t * d.n2 + j + 1];
+    }
+  }
+  const float m0 = live0 ? 1.f : 0.f, m1 = live1 ? 1.f : 0.f;
+  float den = 0.f;
+  for (int a = a0; a < a1; ++a) {
+    float2* cell = reinterpret_cast<float2*>(tileS + (size_t)a * kPanelCols + c0);
+    const float2 dv = *cell;
+    float sr[R], pr[R];
+#pragma unroll
+    for (int t4 = 0; t4 < RX / 4; ++t4) {
+      const float4 sv = *reinterpret_cast<const float4*>(side + (size_t)a * RX + 4 * t4);
+      const float4 pv = *reinterpret_cast<const float4*>(proj + (size_t)a * RX + 4 * t4);
+      const float s4[4] = {sv.x, sv.y, sv.z, sv.w}, p4[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (4 * t4 + e < R) {
+          sr[4 * t4 + e] = s4[e];
+          pr[4 * t4 + e] = p4[e];
+        }
+    }
+    const float v0 = panel_value(dv.x, lowrank_entry<R>(sr, vec0), zeta) * m0;
+    const float v1 = panel_value(dv.y, lowrank_entry<R>(sr, vec1), zeta) * m1;
+    *cell = make_float2(v0, v1);
+    den = fmaf(dv.x, dv.x, den);
+    den = fmaf(dv.y, dv.y, den);
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      acc0[t] = fmaf(pr[t], v0, acc0[t]);
+      acc1[t] = fmaf(pr[t], v1, acc1[t]);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    part[((size_t)h * kPanelCols + c0) * RX + t] = acc0[t];
+    part[((size_t)h * kPanelCols + c0 + 1) * RX + t] = acc1[t];
+  }
+  __syncthreads();
+  // projections of every column: the kPanelSplit partial sums in a fixed order
+  for (int q = threadIdx.x; q < kPanelCols * R; q += blockDim.x) {
+    const int cc = q / R, t = q - cc * R;
+    float sum = 0.f;
+#pragma unroll
+    for (int hh = 0; hh < kPanelSplit; ++hh) sum += part[((size_t)hh * kPanelCols + cc) * RX + t];
+    outS[cc * RX + t] = sum;
+  }
+  __syncthreads();
+  float out0[R], out1[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    out0[t] = outS[c0 * RX + t];
+    out1[t] = outS[(c0 + 1) * RX + t];
   }
   float num = 0.f;
-  if (live) {
-    for (int a = a0; a < a1; ++a) {
-      const float v = tileS[(size_t)a * kPanelCols + c];
-      float w = 0.f;
+  for (int a = a0; a < a1; ++a) {
+    const float2 v = *reinterpret_cast<const float2*>(tileS + (size_t)a * kPanelCols + c0);
+    float rr[R];
 #pragma unroll
-      for (int t = 0; t < R; ++t) w = fmaf(recon[(size_t)a * R + t], out[t], w);
-      const float rr = v - w;
-      num = fmaf(rr, rr, num);
+    for (int t4 = 0; t4 < RX / 4; ++t4) {
+      const float4 rv = *reinterpret_cast<const float4*>(recon + (size_t)a * RX + 4 * t4);
+      const float r4[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (4 * t4 + e < R) rr[4 * t4 + e] = r4[e];
     }
-    if (h == 0) {
-      if (COL) {
-        float* An = d.A[nxt];
+    float w0 = 0.f, w1 = 0.f;
 #pragma unroll
-        for (int t = 0; t < R; ++t) An[j * R + t] = out[t];
-      } else {
-        float* Bn = d.B[nxt];
+    for (int t = 0; t < R; ++t) {
+      w0 = fmaf(rr[t], out0[t], w0);
+      w1 = fmaf(rr[t], out1[t], w1);
+    }
+    const float e0 = (v.x - w0) * m0, e1 = (v.y - w1) * m1;
+    num = fmaf(e0, e0, num);
+    num = fmaf(e1, e1, num);
+  }
+  if (h == 0) {
+    if (COL) {
+      float* An = d.A[nxt];
 #pragma unroll
-        for (int t = 0; t < R; ++t) Bn[(int64_t)t * d.n2 + j] = out[t];
+      for (int t = 0; t < R; ++t) {
+        if (live0) An[j * R + t] = out0[t];
+        if (live1) An[(j + 1) * R + t] = out1[t];
+      }
+    } else {
+      float* Bn = d.B[nxt];
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        if (live0) Bn[(int64_t)t * d.n2 + j] = out0[t];
+        if (live1) Bn[(int64_t)t * d.n2 + j + 1] = out1[t];
       }
     }
   }
@@ -214,11 +259,13 @@ __device__ void panel_pass(const IterDesc& d, int tile, int k, float zeta, unsig
   acc2[1] += (double)den;
 }
 
-// Both passes in one grid (row tiles first); the last block to finish reduces
+// Both passes in one grid (row tiles first, then column tiles, then -- for
+// IRCUR-R drawing its own index sets -- two blocks sampling I_{k+1}, J_{k+1},
+// which no panel block depends on); the last block to finish reduces
 // the per-block partial sums in a fixed order, evaluates e_{k+1}, advances k
 // and zeta, and drives the graph's while-node (Alg. 1: "while e_k > epsilon").
 template <int R>
-__global__ void __launch_bounds__(kPanelThreads) pass_kernel(IterDesc d) {
+__global__ void __launch_bounds__(kPanelThreads, 3) pass_kernel(IterDesc d) {
   extern __shared__ __align__(16) unsigned char smem[];
   State* st = d.st;
   if (st->done || st->status) {
@@ -231,10 +278,19 @@ __global__ void __launch_bounds__(kPanelThreads) pass_kernel(IterDesc d) {
   const int k = st->k;
   const float zeta = (float)st->zeta;
   double acc[2] = {0.0, 0.0};
-  if ((int)blockIdx.x < d.nRowTiles)
+  const int nPanel = d.nRowTiles + d.nColTiles;
+  if ((int)blockIdx.x < d.nRowTiles) {
     panel_pass<R, false>(d, blockIdx.x, k, zeta, smem, acc);
-  else
+  } else if ((int)blockIdx.x < nPanel) {
     panel_pass<R, true>(d, blockIdx.x - d.nRowTiles, k, zeta, smem, acc);
+  } else if (k + 1 < d.max_iter) {
+    // IRCUR-R: the next iteration's index sets, drawn alongside the panels
+    const int axis = (int)blockIdx.x - nPanel;
+    int* out = axis ? const_cast<int*>(d.J_all) + (int64_t)(k + 1) * d.nJ
+                    : const_cast<int*>(d.I_all) + (int64_t)(k + 1) * d.nI;
+    sample_subset(d.seed, k + 1, axis, axis ? d.n2 : d.n1, axis ? d.nJ : d.nI, out,
+                  *reinterpret_cast<SamplerSmem*>(smem));
+  }
 
   __shared__ double red[4][kPanelThreads / 32];
   __shared__ int is_last;
@@ -286,8 +342,10 @@ __global__ void __launch_bounds__(kPanelThreads) pass_kernel(IterDesc d) {
 
 size_t pass_smem_bytes(int nI, int nJ, int Rpad) {
   const int m = nI > nJ ? nI : nJ;
-  return (size_t)m * kPanelCols * 4 + 3 * (size_t)m * Rpad * 4 + (size_t)kPanelSplit * kPanelCols * Rpad * 4 +
-         8 + 16;
+  const size_t rx = (size_t)((Rpad + 3) & ~3);
+  const size_t panel = (size_t)m * kPanelCols * 4 + 3 * (size_t)m * rx * 4 +
+                       (size_t)kPanelSplit * kPanelCols * rx * 4 + (size_t)kPanelCols * rx * 4 + 16;
+  return panel > sizeof(SamplerSmem) ? panel : sizeof(SamplerSmem);
 }
 
 cudaError_t launch_svd(const IterDesc& d, int Rpad, cudaStream_t s);
@@ -307,7 +365,7 @@ static cudaError_t launch_iter_r(const IterDesc& d, cudaStream_t s) {
   const size_t bytes = pass_smem_bytes(d.nI, d.nJ, R);
   cudaError_t e = cudaFuncSetAttribute(pass_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  pass_kernel<R><<<d.nRowTiles + d.nColTiles, kPanelThreads, bytes, s>>>(d);
+  pass_kernel<R><<<d.nRowTiles + d.nColTiles + (d.sampleAhead ? 2 : 0), kPanelThreads, bytes, s>>>(d);
   return cudaGetLastError();
 }
 

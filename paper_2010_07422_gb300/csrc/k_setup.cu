@@ -5,110 +5,19 @@
 
 #include "device_common.cuh"
 #include "ircur_internal.cuh"
+#include "sampler.cuh"
 
 namespace ircur {
 
 // ---------------------------------------------------------------------------
-// Block-wide exclusive scan of one 32-bit count per thread (blockDim = 1024).
-__device__ unsigned block_exclusive_scan(unsigned v, unsigned* warp_tot, unsigned* total) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) warp_tot[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    unsigned w = (lane < (int)(blockDim.x >> 5)) ? warp_tot[lane] : 0u;
-    unsigned s = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      unsigned y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
-    }
-    warp_tot[lane] = s - w;  // exclusive prefix of warp totals
-    if (lane == 31) *total = s;
-  }
-  __syncthreads();
-  unsigned r = warp_tot[wid] + x - v;
-  __syncthreads();
-  return r;
-}
-
-// Uniform m-subset of [0, n) for one (draw, axis): the m smallest keys
-// key(i) = splitmix64(base ^ i), base = splitmix64(splitmix64(seed) ^ (2 draw + axis)),
-// ties broken by the smaller index, written in ascending index order.
-// One block of 1024 threads per (draw, axis); MSB-first radix select on the
-// 64-bit keys (8 passes of 8 bits), then an order-preserving compaction.
+// Index sets for `draws` consecutive draws (blockIdx.x) and one or both axes
+// (blockIdx.y), one block per set; see sampler.cuh.
 __global__ void __launch_bounds__(1024) sample_kernel(uint64_t seed, int draw0, int64_t n1, int64_t n2,
                                                       int nI, int nJ, int* I_all, int* J_all, int only_axis) {
-  const int draw = draw0 + (int)blockIdx.x;
+  __shared__ SamplerSmem S;
   const int axis = only_axis >= 0 ? only_axis : (int)blockIdx.y;
-  const int64_t n = axis ? n2 : n1;
-  const int m = axis ? nJ : nI;
   int* out = axis ? (J_all + (int64_t)blockIdx.x * nJ) : (I_all + (int64_t)blockIdx.x * nI);
-  const uint64_t base = splitmix64(splitmix64(seed) ^ (uint64_t)(2 * draw + axis));
-
-  __shared__ unsigned hist[256];
-  __shared__ unsigned long long s_prefix;
-  __shared__ long long s_want;
-  __shared__ unsigned warp_tot[32];
-  __shared__ unsigned s_total;
-
-  uint64_t prefix = 0, mask = 0;
-  long long want = m;  // rank (1-based) of the target among keys matching `prefix`
-  for (int shift = 56; shift >= 0; shift -= 8) {
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0u;
-    __syncthreads();
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const uint64_t key = splitmix64(base ^ (uint64_t)i);
-      if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      long long cum = 0;
-      int dg = 0;
-      for (; dg < 255; ++dg) {
-        if (cum + (long long)hist[dg] >= want) break;
-        cum += hist[dg];
-      }
-      s_want = want - cum;
-      s_prefix = prefix | ((uint64_t)dg << shift);
-    }
-    __syncthreads();
-    want = s_want;
-    prefix = s_prefix;
-    mask |= (0xFFull << shift);
-    __syncthreads();
-  }
-  // prefix is now the m-th smallest key T; `want` keys equal to T are taken.
-  const uint64_t T = prefix;
-  const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
-  const int64_t lo = (int64_t)threadIdx.x * chunk;
-  const int64_t hi = lo + chunk < n ? lo + chunk : n;
-  unsigned less = 0, eq = 0;
-  for (int64_t i = lo; i < hi; ++i) {
-    const uint64_t key = splitmix64(base ^ (uint64_t)i);
-    less += key < T;
-    eq += key == T;
-  }
-  const unsigned eq_before = block_exclusive_scan(eq, warp_tot, &s_total);
-  long long take_eq = want - (long long)eq_before;
-  take_eq = take_eq < 0 ? 0 : (take_eq > (long long)eq ? (long long)eq : take_eq);
-  const unsigned sel = less + (unsigned)take_eq;
-  unsigned pos = block_exclusive_scan(sel, warp_tot, &s_total);
-  unsigned eq_rank = eq_before;
-  for (int64_t i = lo; i < hi; ++i) {
-    const uint64_t key = splitmix64(base ^ (uint64_t)i);
-    bool take = key < T;
-    if (key == T) {
-      take = (long long)eq_rank < want;
-      ++eq_rank;
-    }
-    if (take && pos < (unsigned)m) out[pos++] = (int)i;
-  }
+  sample_subset(seed, draw0 + (int)blockIdx.x, axis, axis ? n2 : n1, axis ? nJ : nI, out, S);
 }
 
 cudaError_t launch_sample(uint64_t seed, int draw0, int draws, int64_t n1, int64_t n2, int nI, int nJ,
@@ -236,36 +145,68 @@ cudaError_t launch_finalize_zeta(State* st, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // IRCUR-R: D^T (n2 x n1) once per solve, so that the column panels D(:,J_k)
 // of every iteration are row gathers of D^T; the same pass takes max|D| and
-// the NaN/Inf scan.  32 x 32 tiles through padded shared memory; every global
-// access is a coalesced 128-byte row segment.
+// the NaN/Inf scan.  64 x 64 tiles through padded shared memory, 256 threads:
+// 16-byte streaming loads along rows of D (when rows are 16-byte aligned),
+// 16-byte stores along rows of D^T, all coalesced.
+constexpr int kTT = 64;
 __global__ void __launch_bounds__(256) transpose_maxabs_kernel(const float* __restrict__ D, int64_t n1,
                                                                int64_t n2, int64_t ldD, float* __restrict__ DT,
-                                                               int64_t ldDT, State* st) {
-  __shared__ float tile[32][33];
-  const int64_t tiles_i = (n1 + 31) / 32, tiles_j = (n2 + 31) / 32;
+                                                               int64_t ldDT, int vec, State* st) {
+  __shared__ float tile[kTT][kTT + 1];
+  const int64_t tiles_i = (n1 + kTT - 1) / kTT, tiles_j = (n2 + kTT - 1) / kTT;
   const int64_t ntiles = tiles_i * tiles_j;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16
   float m = 0.f;
   bool bad = false;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t ti = t / tiles_j, tj = t - ti * tiles_j;
-    const int64_t i0 = ti * 32, j0 = tj * 32;
+    const int64_t i0 = ti * kTT, j0 = tj * kTT;
+    const bool full = vec && i0 + kTT <= n1 && j0 + kTT <= n2;
+    if (full) {
+      float4 v[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t i = i0 + ty + 8 * q, j = j0 + tx;
-      float x = 0.f;
-      if (i < n1 && j < n2) {
-        x = __ldcs(D + i * ldD + j);
-        bad |= !(fabsf(x) <= FLT_MAX);
-        m = fmaxf(m, fabsf(x));
+      for (int q = 0; q < 4; ++q) v[q] = __ldcs(reinterpret_cast<const float4*>(D + (i0 + ty + 16 * q) * ldD + j0) + tx);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float e[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          bad |= !(fabsf(e[u]) <= FLT_MAX);
+          m = fmaxf(m, fabsf(e[u]));
+          tile[ty + 16 * q][4 * tx + u] = e[u];
+        }
       }
-      tile[ty + 8 * q][tx] = x;
+    } else {
+      for (int q = threadIdx.x; q < kTT * kTT; q += blockDim.x) {
+        const int r = q / kTT, cc = q - r * kTT;
+        const int64_t i = i0 + r, j = j0 + cc;
+        float x = 0.f;
+        if (i < n1 && j < n2) {
+          x = D[i * ldD + j];
+          bad |= !(fabsf(x) <= FLT_MAX);
+          m = fmaxf(m, fabsf(x));
+        }
+        tile[r][cc] = x;
+      }
     }
     __syncthreads();
+    if (full) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int64_t j = j0 + ty + 8 * q, i = i0 + tx;
-      if (i < n1 && j < n2) DT[j * ldDT + i] = tile[tx][ty + 8 * q];
+      for (int q = 0; q < 4; ++q) {
+        const int jr = ty + 16 * q;  // row of D^T inside the tile
+        float4 o;
+        o.x = tile[4 * tx + 0][jr];
+        o.y = tile[4 * tx + 1][jr];
+        o.z = tile[4 * tx + 2][jr];
+        o.w = tile[4 * tx + 3][jr];
+        reinterpret_cast<float4*>(DT + (j0 + jr) * ldDT + i0)[tx] = o;
+      }
+    } else {
+      for (int q = threadIdx.x; q < kTT * kTT; q += blockDim.x) {
+        const int jr = q / kTT, ic = q - jr * kTT;
+        const int64_t j = j0 + jr, i = i0 + ic;
+        if (i < n1 && j < n2) DT[j * ldDT + i] = tile[ic][jr];
+      }
     }
     __syncthreads();
   }
@@ -274,9 +215,9 @@ __global__ void __launch_bounds__(256) transpose_maxabs_kernel(const float* __re
   bad = __any_sync(0xffffffffu, bad);
   __shared__ float wm[8];
   __shared__ int wb[8];
-  if (tx == 0) {
-    wm[ty] = m;
-    wb[ty] = bad;
+  if ((threadIdx.x & 31) == 0) {
+    wm[threadIdx.x >> 5] = m;
+    wb[threadIdx.x >> 5] = bad;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -293,10 +234,12 @@ __global__ void __launch_bounds__(256) transpose_maxabs_kernel(const float* __re
 
 cudaError_t launch_transpose_maxabs(const float* D, int64_t n1, int64_t n2, int64_t ldD, float* DT,
                                     int64_t ldDT, State* st, cudaStream_t s) {
-  const int64_t ntiles = ((n1 + 31) / 32) * ((n2 + 31) / 32);
-  int blocks = (int)(ntiles < 16 * kNumSMsHint ? ntiles : 16 * kNumSMsHint);
+  const int64_t ntiles = ((n1 + kTT - 1) / kTT) * ((n2 + kTT - 1) / kTT);
+  int blocks = (int)(ntiles < 8 * kNumSMsHint ? ntiles : 8 * kNumSMsHint);
   if (blocks < 1) blocks = 1;
-  transpose_maxabs_kernel<<<blocks, 256, 0, s>>>(D, n1, n2, ldD, DT, ldDT, st);
+  const int vec = ((reinterpret_cast<uintptr_t>(D) & 15) == 0) && (ldD % 4 == 0) &&
+                  ((reinterpret_cast<uintptr_t>(DT) & 15) == 0) && (ldDT % 4 == 0);
+  transpose_maxabs_kernel<<<blocks, 256, 0, s>>>(D, n1, n2, ldD, DT, ldDT, vec, st);
   return cudaGetLastError();
 }
 

@@ -36,7 +36,10 @@
 
 namespace ircur {
 
-constexpr int kSvdThreads = 512;
+template <int R>
+struct SvdThreads {
+  static constexpr int value = 512;
+};
 constexpr int kProdChunks = 8;  // max inner-dimension chunks of a core product
 constexpr int kSmallMats = 9;   // G, Rp, U, U2y, U2x, T, Ut, Vt, scratch (R x R each)
 constexpr size_t kSvdSmemBudget = 220 * 1024;
@@ -55,7 +58,7 @@ __host__ __device__ inline SvdLayout svd_layout(int nI, int nJ, int ldCore, int 
   L.ldu = ldCore;
   L.ldm = round_up4(nI > nJ ? nI : nJ);
   const size_t blk = (size_t)L.ldm * R * 4;
-  const size_t small = (size_t)kSmallMats * R * R * 4 + 3 * 32 * 4 + 64;
+  const size_t small = (size_t)kSmallMats * R * R * 4 + 4 * 32 * 4 + 64;
   const size_t fixed = (core_in_smem ? (size_t)nI * L.ldu * 4 : 0) + 3 * blk + small + 16;
   int pch = fixed < kSvdSmemBudget ? (int)((kSvdSmemBudget - fixed) / blk) : 0;
   L.pch = pch < 1 ? 1 : (pch > kProdChunks ? kProdChunks : pch);
@@ -110,7 +113,7 @@ struct SvdSmall {
   float* tmp;   // R x R
   float* dinv;  // R reciprocal pivots
   float* sig;   // R
-  float* red;   // 32 reduction slots
+  float* red;   // 64 reduction slots
   int* ibuf;    // 16 ints
 };
 
@@ -133,7 +136,7 @@ __device__ __forceinline__ void reduce_parts(const float* part, int nch, int nou
 // spaced G apart (lanes on consecutive rows) and an inner chunk; core rows are
 // read as 16-byte vectors and each 4-row slab of every column of X is a
 // 16-byte broadcast shared by the RB rows.  Rows of X beyond nin are zero.
-template <int R, int RB = (R > 10 ? 2 : 4)>
+template <int R, int RB = (R > 8 ? 2 : 4)>
 __device__ void core_times(const float* __restrict__ U, int ldu, int nout, int nin, const float* __restrict__ in,
                            float* __restrict__ out, float* part, int ldm, int pch) {
   const int G = (nout + RB - 1) / RB;
@@ -330,16 +333,17 @@ __device__ __forceinline__ int rr_partner(int p, int k, int n) {
   return q < 0 ? q + n - 1 : q;
 }
 
-template <int R>
-__global__ void __launch_bounds__(kSvdThreads, 1) svd_kernel(IterDesc d, int core_in_smem) {
+// CS: the core is held in shared memory (a compile-time property, so that
+// every core access compiles to a shared-memory load).
+template <int R, bool CS>
+__global__ void __launch_bounds__(SvdThreads<R>::value, 1) svd_kernel(IterDesc d) {
+  constexpr bool core_in_smem = CS;
   State* st = d.st;
   if (st->done || st->status) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int k = st->k;
-  const int cur = k & 1;
   const int nI = d.nI, nJ = d.nJ, r = d.r;
-  const int* J = d.J_all + (d.resample ? (int64_t)k * nJ : 0);
-  const SvdLayout L = svd_layout(nI, nJ, d.ldCore, R, core_in_smem != 0);
+  const SvdLayout L = svd_layout(nI, nJ, d.ldCore, R, core_in_smem);
   const int ldm = L.ldm, ldu = L.ldu;
   float* Us = core_in_smem ? reinterpret_cast<float*>(smem + L.off_us) : d.core;
   float* X = reinterpret_cast<float*>(smem + L.off_x);
@@ -373,7 +377,7 @@ __global__ void __launch_bounds__(kSvdThreads, 1) svd_kernel(IterDesc d, int cor
     sm.sig = p;
     p += 32;
     sm.red = p;
-    p += 32;
+    p += 64;
     sm.ibuf = reinterpret_cast<int*>(p);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -389,11 +393,9 @@ __global__ void __launch_bounds__(kSvdThreads, 1) svd_kernel(IterDesc d, int cor
   // ---- X, Y, Q zeroed (padding rows must read as zero); warm start X = B_k(:,J)^T
   for (int q = threadIdx.x; q < 3 * R * ldm; q += blockDim.x) X[q] = 0.f;  // X, Y, Q are contiguous
   __syncthreads();
-  const float* Bk = d.B[cur];
   for (int b = threadIdx.x; b < nJ; b += blockDim.x) {
-    const int64_t jb = J[b];
 #pragma unroll
-    for (int t = 0; t < R; ++t) X[(size_t)t * ldm + b] = (t < r) ? Bk[(int64_t)t * d.n2 + jb] : 0.f;
+    for (int t = 0; t < R; ++t) X[(size_t)t * ldm + b] = (t < r) ? d.BJt[(size_t)b * R + t] : 0.f;
   }
   __syncthreads();
   int brk = cholqr<R>(X, X, nJ, r, ldm, sm.U, sm);
@@ -445,13 +447,13 @@ __global__ void __launch_bounds__(kSvdThreads, 1) svd_kernel(IterDesc d, int cor
     rc2 = warp_sum(rc2);
     if (lane == 0) {
       sm.red[warp] = e2;
-      sm.red[16 + warp] = rc2;
+      sm.red[32 + warp] = rc2;
     }
     __syncthreads();
     float E2 = 0.f, RC2 = 0.f;
     for (int w = 0; w < nwarps; ++w) {
       E2 += sm.red[w];
-      RC2 += sm.red[16 + w];
+      RC2 += sm.red[32 + w];
     }
     const float res = sqrtf(E2), nrm = sqrtf(RC2);
     if (res <= 1e-6f * nrm || (steps > 1 && res > 0.5f * prev_res && res <= 1e-5f * nrm) || !(nrm > 0.f)) {
@@ -648,9 +650,15 @@ template <int R>
 static cudaError_t launch_svd_r(const IterDesc& d, cudaStream_t s) {
   bool in_smem = false;
   const size_t bytes = svd_smem_bytes(d.nI, d.nJ, R, &in_smem);
-  cudaError_t e = cudaFuncSetAttribute(svd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e != cudaSuccess) return e;
-  svd_kernel<R><<<1, kSvdThreads, bytes, s>>>(d, in_smem ? 1 : 0);
+  if (in_smem) {
+    cudaError_t e = cudaFuncSetAttribute(svd_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    svd_kernel<R, true><<<1, SvdThreads<R>::value, bytes, s>>>(d);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(svd_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    svd_kernel<R, false><<<1, SvdThreads<R>::value, bytes, s>>>(d);
+  }
   return cudaGetLastError();
 }
 
