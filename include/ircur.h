@@ -143,6 +143,30 @@ ircur_status ircur_solve_host(ircur_ctx* ctx, const float* D_host, float* L_host
 ircur_status ircur_sample_indices(uint64_t seed, int32_t draw, int32_t axis, int64_t n, int32_t m,
                                   int32_t* out, void* stream);
 
+/* Allocation-free one-shot solve: ircur_create + ircur_solve +
+ * ircur_get_factors for IRCUR-F (params->resample must be 0) without any
+ * device allocation.  The paper has no counterpart; this entry point exists
+ * for callers that may not allocate device memory -- a process whose memory
+ * pool already holds all the device memory it may use (a new cudaMalloc would
+ * fail or fragment it), or a latency-bound loop that cannot afford
+ * cudaMalloc's implicit synchronisation.  It runs the same kernels as
+ * ircur_solve, with the workspace carved from one fixed array of device
+ * memory inside the library (3.5 MB on every GPU that loads the library,
+ * held until the process exits), and calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ * Limits of that array: n1, n2 <= 2048, |I|, |J| <= 192, r <= 8,
+ * max_iter <= 256; larger problems (and resample != 0) return IRCUR_EINVAL.
+ * D: device, n1 x n2, ldD >= n2.  A (n1 x r, ld r) and B (r x n2, ld n2):
+ * device outputs with L = A B.  stream: cudaStream_t.  Synchronises the
+ * stream; *out as for ircur_solve.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  All calls share the one array (its
+ * contents persist between calls; each call clears what must start at
+ * zero), so calls that overlap on the GPU -- from several streams or host
+ * threads -- race and must not be issued. */
+ircur_status ircur_solve_noalloc(const ircur_params* params, const float* D, int64_t ldD, float* A, float* B,
+                                 ircur_result* out, void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* ircur_status_string(ircur_status s);
 

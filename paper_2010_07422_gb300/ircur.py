@@ -23,7 +23,7 @@ IRCUR_MAX_RANK = 16
 EXPORTED = (
     "ircur_create", "ircur_destroy", "ircur_solve", "ircur_get_factors", "ircur_get_indices",
     "ircur_get_errors", "ircur_reconstruct", "ircur_solve_host", "ircur_sample_indices",
-    "ircur_status_string", "ircur_last_error_string",
+    "ircur_status_string", "ircur_last_error_string", "ircur_solve_noalloc",
 )
 
 
@@ -70,6 +70,7 @@ def _lib():
         lib.ircur_reconstruct.argtypes = [P, P, I64, P, I64, P, I64]
         lib.ircur_solve_host.argtypes = [P, P, P, P, C.POINTER(ircur_result)]
         lib.ircur_sample_indices.argtypes = [U64, I32, I32, I64, I32, P, P]
+        lib.ircur_solve_noalloc.argtypes = [C.POINTER(ircur_params), P, I64, P, P, C.POINTER(ircur_result), P]
         lib.ircur_status_string.argtypes = [C.c_int]
         lib.ircur_status_string.restype = C.c_char_p
         lib.ircur_last_error_string.argtypes = []
@@ -152,6 +153,15 @@ def ircur_solve_host(ctx, D_host, L_host, S_host=None):
 
 def ircur_sample_indices(seed, draw, axis, n, m, out, stream=None):
     _check(_lib().ircur_sample_indices(seed, draw, axis, n, m, _ptr(out), stream), "ircur_sample_indices")
+
+
+def ircur_solve_noalloc(params: ircur_params, D, ldD, A, B, stream=None):
+    """Allocation-free IRCUR-F solve (see include/ircur.h): writes the factors
+    into the caller's device tensors A (n1 x r) and B (r x n2); L = A B."""
+    res = ircur_result()
+    _check(_lib().ircur_solve_noalloc(C.byref(params), _ptr(D), ldD, _ptr(A), _ptr(B), C.byref(res), stream),
+           "ircur_solve_noalloc")
+    return res
 
 
 # ---------------------------------------------------------------- convenience layer
