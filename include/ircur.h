@@ -114,6 +114,16 @@ ircur_status ircur_get_factors(ircur_ctx* ctx, float* A, float* B);
  * last core (device FP32).  ESTATE before the first solve. */
 ircur_status ircur_get_indices(ircur_ctx* ctx, int32_t* I, int32_t* J, float* sigma);
 
+/* Materialise the CUR decomposition of the last iterate (Alg. 1 output
+ * C_K, U_K, R_K; Thm 1: L = C U^+ R) into caller buffers (device, FP32,
+ * row-major, each may be NULL): C = [D - S_K]_{:,J} (n1 x nJ, ld nJ),
+ * U = H_r([D - S_K]_{I,J}) (nI x nJ, ld nJ) and R = [D - S_K]_{I,:}
+ * (nI x n2, ld n2), for the index sets ircur_get_indices returns.  C and R
+ * are recomputed from D (device, ldD; the matrix of the solve) with the
+ * previous iterate and threshold, entry for entry as the solve formed them.
+ * ESTATE before a solve. */
+ircur_status ircur_get_cur(ircur_ctx* ctx, const float* D, int64_t ldD, float* C, float* U, float* R);
+
 /* Copy the stopping-criterion history e_1..e_K of the last solve into the
  * host array errs (room for max_iter doubles); synchronises.  Returns the
  * count in *count.  ESTATE before the first solve. */
@@ -142,6 +152,20 @@ ircur_status ircur_solve_host(ircur_ctx* ctx, const float* D_host, float* L_host
  * m-subset, i.e. uniform sampling of Alg. 1.  stream: cudaStream_t. */
 ircur_status ircur_sample_indices(uint64_t seed, int32_t draw, int32_t axis, int64_t n, int32_t m,
                                   int32_t* out, void* stream);
+
+/* Kernel-span tracing (for profiling; off by default).  enable != 0
+ * allocates a small device buffer (48 * max_iter bytes) and makes every
+ * following ircur_solve record, per iteration, the span from the first block
+ * start to the last block end of its three kernels (core, core SVD, panel
+ * passes) with the device's nanosecond clock; enable == 0 frees it.  The
+ * spans are measured inside the CUDA graph, where host-side events cannot
+ * be placed. */
+ircur_status ircur_set_trace(ircur_ctx* ctx, int32_t enable);
+
+/* Spans of the last traced solve: span_us[3 k + {0, 1, 2}] = microseconds of
+ * the core, core-SVD and panel-pass kernels of iteration k (room for
+ * 3 * max_iter doubles, host); *iters = K.  ESTATE without tracing or solve. */
+ircur_status ircur_get_trace(ircur_ctx* ctx, double* span_us, int32_t* iters);
 
 /* Allocation-free one-shot solve: ircur_create + ircur_solve +
  * ircur_get_factors for IRCUR-F (params->resample must be 0) without any

@@ -85,6 +85,8 @@ struct ircur_ctx {
   const float* graph_D;
   int64_t graph_ldD;
   int graph_sample_ahead;
+  unsigned long long* graph_trace;
+  unsigned long long* trace;  // kernel-span trace buffer (2 * 3 * max_iter), or null
   // last solve
   int solved;
   State host_state;
@@ -177,7 +179,7 @@ extern "C" ircur_status ircur_create(const ircur_params* params, void* stream, i
   const size_t oW = take((size_t)p.nI * R * 4), oV = take((size_t)p.nJ * R * 4), oVs = take((size_t)p.nJ * R * 4);
   const size_t oSig = take((size_t)R * 4);
   const size_t oTm = take((size_t)R * R * 4);
-  const size_t oPart = take((size_t)(d.nRowTiles + d.nColTiles + 2) * 2 * 8);  // + the two sampler blocks
+  const size_t oPart = take((size_t)(d.nRowTiles + d.nColTiles) * 2 * 8);
   const size_t oErr = take((size_t)p.max_iter * 8);
   const size_t oSt = take(sizeof(State));
   c->ws_bytes = off;
@@ -273,6 +275,7 @@ extern "C" void ircur_destroy(ircur_ctx* c) {
   cudaStreamSynchronize(c->stream);
   reset_graph(c);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  if (c->trace) cudaFree(c->trace);
   if (c->hD) cudaFree(c->hD);
   if (c->hL) cudaFree(c->hL);
   if (c->hS) cudaFree(c->hS);
@@ -327,6 +330,7 @@ static ircur_status build_graph(ircur_ctx* c, const IterDesc& d0) {
   c->graph_D = d0.D;
   c->graph_ldD = d0.ldD;
   c->graph_sample_ahead = d0.sampleAhead;
+  c->graph_trace = d0.trace;
   return IRCUR_OK;
 }
 
@@ -350,7 +354,13 @@ extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, c
   d.rowLd = p.resample ? ldD : c->ldPr;
   d.rowBulk = p.resample ? ((aligned16(D) && ldD % 4 == 0) ? 1 : 0) : 1;
   d.sampleAhead = (p.resample && !idx_I) ? 1 : 0;
+  d.trace = c->trace;
   c->desc = d;
+  if (c->trace) {
+    const size_t half = (size_t)3 * p.max_iter * 8;
+    IRCUR_CK(cudaMemsetAsync(c->trace, 0xFF, half, s));
+    IRCUR_CK(cudaMemsetAsync(reinterpret_cast<char*>(c->trace) + half, 0, half, s));
+  }
 
   const double zeta0 = p.zeta0 > 0 ? p.zeta0 : 0.0;
   IRCUR_CK(launch_setup(d, zeta0, s));
@@ -360,7 +370,7 @@ extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, c
     IRCUR_CK(launch_check_indices(c->I_all, c->draws, p.nI, p.n1, &c->st->status, s));
     IRCUR_CK(launch_check_indices(c->J_all, c->draws, p.nJ, p.n2, &c->st->status, s));
   } else {
-    // draw 0 now; IRCUR-R draws k+1 inside iteration k's pass kernel
+    // draw 0 now; IRCUR-R draws k+1 alongside iteration k's core SVD
     IRCUR_CK(launch_sample(p.seed, 0, 1, p.n1, p.n2, p.nI, p.nJ, c->I_all, c->J_all, -1, s));
   }
   if (p.resample) {
@@ -375,7 +385,8 @@ extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, c
   IRCUR_CK(cudaMemsetAsync(c->B[0], 0, (size_t)c->Rpad * p.n2 * 4, s));
 
   if (use_graph()) {
-    if (!c->exec || c->graph_D != D || c->graph_ldD != ldD || c->graph_sample_ahead != d.sampleAhead) {
+    if (!c->exec || c->graph_D != D || c->graph_ldD != ldD || c->graph_sample_ahead != d.sampleAhead ||
+        c->graph_trace != d.trace) {
       ircur_status bs = build_graph(c, d);
       if (bs != IRCUR_OK) return bs;
     }
@@ -436,6 +447,15 @@ extern "C" ircur_status ircur_get_indices(ircur_ctx* c, int32_t* I, int32_t* J, 
     IRCUR_CK(cudaMemcpyAsync(J, c->J_all + (size_t)draw * c->p.nJ, (size_t)c->p.nJ * 4, cudaMemcpyDeviceToDevice,
                              c->stream));
   if (sigma) IRCUR_CK(launch_sigma(c->Tm, c->p.r, c->Rpad, sigma, c->stream));
+  return IRCUR_OK;
+}
+
+extern "C" ircur_status ircur_get_cur(ircur_ctx* c, const float* D, int64_t ldD, float* C, float* U, float* R) {
+  if (!c || !D) return IRCUR_EINVAL;
+  if (!c->solved || c->host_state.k < 1) return IRCUR_ESTATE;
+  if (ldD < c->p.n2 || (reinterpret_cast<uintptr_t>(D) & 3)) return IRCUR_EINVAL;
+  if (!C && !U && !R) return IRCUR_OK;
+  IRCUR_CK(launch_get_cur(c->desc, c->Rpad, c->host_state.k, D, ldD, C, U, R, c->stream));
   return IRCUR_OK;
 }
 
@@ -506,6 +526,45 @@ extern "C" ircur_status ircur_sample_indices(uint64_t seed, int32_t draw, int32_
     IRCUR_CK(launch_sample(seed, draw, 1, n, 1, m, 1, out, nullptr, 0, s));
   else
     IRCUR_CK(launch_sample(seed, draw, 1, 1, n, 1, m, nullptr, out, 1, s));
+  return IRCUR_OK;
+}
+
+extern "C" ircur_status ircur_set_trace(ircur_ctx* c, int32_t enable) {
+  if (!c) return IRCUR_EINVAL;
+  if (enable && !c->trace) {
+    cudaError_t e = cudaMalloc(&c->trace, (size_t)2 * 3 * c->p.max_iter * 8);
+    if (e != cudaSuccess) {
+      set_error("cudaMalloc(trace)", e);
+      cudaGetLastError();
+      c->trace = nullptr;
+      return IRCUR_ENOMEM;
+    }
+  } else if (!enable && c->trace) {
+    IRCUR_CK(cudaStreamSynchronize(c->stream));
+    cudaFree(c->trace);
+    c->trace = nullptr;
+  }
+  return IRCUR_OK;
+}
+
+extern "C" ircur_status ircur_get_trace(ircur_ctx* c, double* span_us, int32_t* iters) {
+  if (!c || !span_us || !iters) return IRCUR_EINVAL;
+  if (!c->trace || !c->solved) return IRCUR_ESTATE;
+  const int n = 3 * c->p.max_iter;
+  unsigned long long* h = new (std::nothrow) unsigned long long[2 * (size_t)n];
+  if (!h) return IRCUR_ENOMEM;
+  cudaError_t e = cudaMemcpyAsync(h, c->trace, (size_t)2 * n * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    delete[] h;
+    set_error("ircur_get_trace", e);
+    return IRCUR_ECUDA;
+  }
+  const int K = c->host_state.k;
+  for (int q = 0; q < 3 * K; ++q)
+    span_us[q] = (h[n + q] >= h[q] && h[q] != ~0ull) ? (double)(h[n + q] - h[q]) * 1e-3 : 0.0;
+  *iters = K;
+  delete[] h;
   return IRCUR_OK;
 }
 

@@ -44,7 +44,7 @@ constexpr size_t kNaBytes =
     na_piece((size_t)kNaMaxM * kNaMaxLdCore * 4) +                       // core
     3 * na_piece((size_t)kNaMaxM * kNaMaxR * 4) +                        // W, V, Vs
     na_piece((size_t)kNaMaxR * 4) + na_piece((size_t)kNaMaxR * kNaMaxR * 4) +  // sigma, T
-    na_piece((size_t)((kNaMaxN + kPanelCols - 1) / kPanelCols * 2 + 2) * 2 * 8) +  // partials
+    na_piece((size_t)((kNaMaxN + kPanelCols - 1) / kPanelCols * 2) * 2 * 8) +  // partials
     na_piece((size_t)kNaMaxIter * 8) +                                   // e_k history
     na_piece(sizeof(State));
 
@@ -127,7 +127,7 @@ extern "C" ircur_status ircur_solve_noalloc(const ircur_params* params, const fl
   float* Vs = reinterpret_cast<float*>(take((size_t)p.nJ * R * 4));
   float* sigma = reinterpret_cast<float*>(take((size_t)R * 4));
   float* Tm = reinterpret_cast<float*>(take((size_t)R * R * 4));
-  double* partials = reinterpret_cast<double*>(take((size_t)(d.nRowTiles + d.nColTiles + 2) * 2 * 8));
+  double* partials = reinterpret_cast<double*>(take((size_t)(d.nRowTiles + d.nColTiles) * 2 * 8));
   double* errs = reinterpret_cast<double*>(take((size_t)p.max_iter * 8));
   State* st = reinterpret_cast<State*>(take(sizeof(State)));
   if (off > kNaBytes) return IRCUR_EINVAL;  // cannot happen within the limits above

@@ -107,6 +107,22 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Nanosecond device clock (comparable across SMs).
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Kernel-span trace: trace[slot] = earliest block start, trace[nslots + slot]
+// = latest block end, in global_ns() units.  Null trace: no-op.
+__device__ __forceinline__ void trace_start(unsigned long long* trace, int slot) {
+  if (trace && threadIdx.x == 0) atomicMin(trace + slot, global_ns());
+}
+__device__ __forceinline__ void trace_stop(unsigned long long* trace, int nslots, int slot) {
+  if (trace && threadIdx.x == 0) atomicMax(trace + nslots + slot, global_ns());
+}
+
 // Streaming 16-byte store (evict-first): outputs written once, never re-read here.
 __device__ __forceinline__ void st_stream(float4* p, float4 v) { __stcs(p, v); }
 

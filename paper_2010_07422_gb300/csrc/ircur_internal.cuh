@@ -32,6 +32,7 @@ struct State {
   unsigned flags;   // IRCUR_FLAG_*
   double zeta;      // threshold of the current iteration, zeta_0 gamma^k
   double zeta0;     // zeta_0 in use
+  double zeta_last; // threshold of the last completed iteration
   double e;         // last stopping value e_k
   unsigned counter; // block-completion counter of the pass kernel
   unsigned maxabs_bits;  // max|D| as float bits (non-negative floats order like uints)
@@ -84,9 +85,10 @@ struct IterDesc {
   int nRowTiles, nColTiles;
   int rowBulk, colBulk; // 1: panel rows are 16-byte aligned (tiles via 16-byte async copies)
   int svdMaxSteps;
-  int sampleAhead;      // 1: the pass kernel draws the next iteration's I, J (IRCUR-R, own sampler)
+  int sampleAhead;      // 1: the core-SVD launch draws the next iteration's I, J (IRCUR-R, own sampler)
   long long spinLimit;      // first bounded wait on a bulk copy (kSpinLimit unless a fault is injected)
   unsigned long long cond;  // graph conditional handle (0 = no graph)
+  unsigned long long* trace;  // optional kernel spans: slot 3k + {0 core, 1 svd, 2 pass}, 3 max_iter slots
   uint64_t seed;
 };
 
@@ -106,6 +108,8 @@ cudaError_t launch_iteration(const IterDesc& d, int Rpad, cudaStream_t s);
 cudaError_t launch_reconstruct(const float* A, const float* B, int Rpad, int64_t n1, int64_t n2,
                                const float* D, int64_t ldD, float* L, int64_t ldL, float* S,
                                int64_t ldS, const State* st, cudaStream_t s);
+cudaError_t launch_get_cur(const IterDesc& d, int Rpad, int K, const float* D, int64_t ldD, float* C, float* U,
+                           float* Rm, cudaStream_t s);
 size_t svd_smem_bytes(int nI, int nJ, int Rpad, bool* core_in_smem);
 cudaError_t launch_sigma(const float* Tm, int r, int Rpad, float* sigma, cudaStream_t s);
 size_t pass_smem_bytes(int nI, int nJ, int Rpad);

@@ -16,7 +16,6 @@
 // each residual formed explicitly (no difference of squared norms).
 #include "device_common.cuh"
 #include "ircur_internal.cuh"
-#include "sampler.cuh"
 
 namespace ircur {
 
@@ -38,6 +37,7 @@ __global__ void __launch_bounds__(256) core_kernel(IterDesc d) {
   const int* J = d.J_all + (d.resample ? (int64_t)k * d.nJ : 0);
   const float* A = d.A[cur];
   const float* B = d.B[cur];
+  trace_start(d.trace, 3 * k + 0);
   for (int a = blockIdx.x; a < d.nI; a += gridDim.x) {
     const int ia = I[a];
     float arow[R];
@@ -57,6 +57,10 @@ __global__ void __launch_bounds__(256) core_kernel(IterDesc d) {
       const float l = lowrank_entry<R>(arow, bcol);
       d.core[(int64_t)a * d.ldCore + b] = panel_value(rowp[j], l, zeta);
     }
+  }
+  if (d.trace) {
+    __syncthreads();
+    trace_stop(d.trace, 3 * d.max_iter, 3 * k + 0);
   }
 }
 
@@ -259,9 +263,7 @@ __device__ void panel_pass(const IterDesc& d, int tile, int k, float zeta, unsig
   acc2[1] += (double)den;
 }
 
-// Both passes in one grid (row tiles first, then column tiles, then -- for
-// IRCUR-R drawing its own index sets -- two blocks sampling I_{k+1}, J_{k+1},
-// which no panel block depends on); the last block to finish reduces
+// Both passes in one grid (row tiles first); the last block to finish reduces
 // the per-block partial sums in a fixed order, evaluates e_{k+1}, advances k
 // and zeta, and drives the graph's while-node (Alg. 1: "while e_k > epsilon").
 template <int R>
@@ -277,19 +279,13 @@ __global__ void __launch_bounds__(kPanelThreads, 3) pass_kernel(IterDesc d) {
   }
   const int k = st->k;
   const float zeta = (float)st->zeta;
+  trace_start(d.trace, 3 * k + 2);
   double acc[2] = {0.0, 0.0};
   const int nPanel = d.nRowTiles + d.nColTiles;
   if ((int)blockIdx.x < d.nRowTiles) {
     panel_pass<R, false>(d, blockIdx.x, k, zeta, smem, acc);
   } else if ((int)blockIdx.x < nPanel) {
     panel_pass<R, true>(d, blockIdx.x - d.nRowTiles, k, zeta, smem, acc);
-  } else if (k + 1 < d.max_iter) {
-    // IRCUR-R: the next iteration's index sets, drawn alongside the panels
-    const int axis = (int)blockIdx.x - nPanel;
-    int* out = axis ? const_cast<int*>(d.J_all) + (int64_t)(k + 1) * d.nJ
-                    : const_cast<int*>(d.I_all) + (int64_t)(k + 1) * d.nI;
-    sample_subset(d.seed, k + 1, axis, axis ? d.n2 : d.n1, axis ? d.nJ : d.nI, out,
-                  *reinterpret_cast<SamplerSmem*>(smem));
   }
 
   __shared__ double red[4][kPanelThreads / 32];
@@ -308,6 +304,7 @@ __global__ void __launch_bounds__(kPanelThreads, 3) pass_kernel(IterDesc d) {
   }
   __threadfence();
   __syncthreads();
+  trace_stop(d.trace, 3 * d.max_iter, 3 * k + 2);
   if (threadIdx.x == 0) is_last = (atomicAdd(&st->counter, 1u) == gridDim.x - 1);
   __syncthreads();
   if (!is_last) return;
@@ -331,11 +328,13 @@ __global__ void __launch_bounds__(kPanelThreads, 3) pass_kernel(IterDesc d) {
     d.errs[k] = e;
     st->e = e;
     st->k = k + 1;
+    st->zeta_last = st->zeta;
     st->zeta = st->zeta * d.gamma;
     st->counter = 0u;
     const int done = (e <= d.tol) || (k + 1 >= d.max_iter) || (st->status != 0);
     st->done = done;
     __threadfence();
+    trace_stop(d.trace, 3 * d.max_iter, 3 * k + 2);
     if (d.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)d.cond, done ? 0u : 1u);
   }
 }
@@ -343,9 +342,8 @@ __global__ void __launch_bounds__(kPanelThreads, 3) pass_kernel(IterDesc d) {
 size_t pass_smem_bytes(int nI, int nJ, int Rpad) {
   const int m = nI > nJ ? nI : nJ;
   const size_t rx = (size_t)((Rpad + 3) & ~3);
-  const size_t panel = (size_t)m * kPanelCols * 4 + 3 * (size_t)m * rx * 4 +
-                       (size_t)kPanelSplit * kPanelCols * rx * 4 + (size_t)kPanelCols * rx * 4 + 16;
-  return panel > sizeof(SamplerSmem) ? panel : sizeof(SamplerSmem);
+  return (size_t)m * kPanelCols * 4 + 3 * (size_t)m * rx * 4 + (size_t)kPanelSplit * kPanelCols * rx * 4 +
+         (size_t)kPanelCols * rx * 4 + 16;
 }
 
 cudaError_t launch_svd(const IterDesc& d, int Rpad, cudaStream_t s);
@@ -365,7 +363,7 @@ static cudaError_t launch_iter_r(const IterDesc& d, cudaStream_t s) {
   const size_t bytes = pass_smem_bytes(d.nI, d.nJ, R);
   cudaError_t e = cudaFuncSetAttribute(pass_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  pass_kernel<R><<<d.nRowTiles + d.nColTiles + (d.sampleAhead ? 2 : 0), kPanelThreads, bytes, s>>>(d);
+  pass_kernel<R><<<d.nRowTiles + d.nColTiles, kPanelThreads, bytes, s>>>(d);
   return cudaGetLastError();
 }
 

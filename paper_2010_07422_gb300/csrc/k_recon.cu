@@ -148,4 +148,89 @@ cudaError_t launch_reconstruct(const float* A, const float* B, int Rpad, int64_t
   }
 }
 
+// ---------------------------------------------------------------------------
+// CUR factors of the last iterate K (Alg. 1 output "C_k, U_k, R_k"), on
+// request: C = [D - S_K]_{:,J}, R = [D - S_K]_{I,:} recomputed from D with
+// the factors and threshold of iteration K-1 (the same FMA chain as the panel
+// passes, so the entries are those the solve used), and U = H_r(core) =
+// Y T X^T = W V^T from the last core factorisation.
+template <int R>
+__global__ void __launch_bounds__(256) get_cur_kernel(IterDesc d, int K, const float* __restrict__ D, int64_t ldD,
+                                                      float* __restrict__ C, float* __restrict__ U,
+                                                      float* __restrict__ Rm) {
+  const int prev = (K - 1) & 1;
+  const int draw = d.resample ? K - 1 : 0;
+  const int* I = d.I_all + (int64_t)draw * d.nI;
+  const int* J = d.J_all + (int64_t)draw * d.nJ;
+  const float zeta = (float)d.st->zeta_last;
+  const float* A = d.A[prev];
+  const float* B = d.B[prev];
+  const int64_t nC = d.n1 * d.nJ, nR = (int64_t)d.nI * d.n2, nU = (int64_t)d.nI * d.nJ;
+  const int64_t total = (C ? nC : 0) + (Rm ? nR : 0) + (U ? nU : 0);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    int64_t e = q;
+    if (C && e < nC) {
+      const int64_t i = e / d.nJ;
+      const int b = (int)(e - i * d.nJ);
+      const int64_t j = J[b];
+      float arow[R], bcol[R];
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        arow[t] = A[i * R + t];
+        bcol[t] = B[(int64_t)t * d.n2 + j];
+      }
+      C[e] = panel_value(D[i * ldD + j], lowrank_entry<R>(arow, bcol), zeta);
+      continue;
+    }
+    if (C) e -= nC;
+    if (Rm && e < nR) {
+      const int a = (int)(e / d.n2);
+      const int64_t j = e - (int64_t)a * d.n2;
+      const int64_t i = I[a];
+      float arow[R], bcol[R];
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        arow[t] = A[i * R + t];
+        bcol[t] = B[(int64_t)t * d.n2 + j];
+      }
+      Rm[e] = panel_value(D[i * ldD + j], lowrank_entry<R>(arow, bcol), zeta);
+      continue;
+    }
+    if (Rm) e -= nR;
+    const int a = (int)(e / d.nJ);
+    const int b = (int)(e - (int64_t)a * d.nJ);
+    float u = 0.f;
+#pragma unroll
+    for (int t = 0; t < R; ++t) u = fmaf(d.W[(size_t)a * R + t], d.V[(size_t)b * R + t], u);
+    U[e] = u;
+  }
+}
+
+cudaError_t launch_get_cur(const IterDesc& d, int Rpad, int K, const float* D, int64_t ldD, float* C, float* U,
+                           float* Rm, cudaStream_t s) {
+  const int blocks = 4 * kNumSMsHint;
+  switch (Rpad) {
+#define IRCUR_CUR_CASE(RR) \
+  case RR:                 \
+    get_cur_kernel<RR><<<blocks, 256, 0, s>>>(d, K, D, ldD, C, U, Rm); \
+    break;
+    IRCUR_CUR_CASE(1)
+    IRCUR_CUR_CASE(2)
+    IRCUR_CUR_CASE(3)
+    IRCUR_CUR_CASE(4)
+    IRCUR_CUR_CASE(5)
+    IRCUR_CUR_CASE(6)
+    IRCUR_CUR_CASE(7)
+    IRCUR_CUR_CASE(8)
+    IRCUR_CUR_CASE(9)
+    IRCUR_CUR_CASE(10)
+    IRCUR_CUR_CASE(12)
+    IRCUR_CUR_CASE(16)
+#undef IRCUR_CUR_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace ircur

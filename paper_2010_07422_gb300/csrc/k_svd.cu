@@ -33,6 +33,7 @@
 
 #include "device_common.cuh"
 #include "ircur_internal.cuh"
+#include "sampler.cuh"
 
 namespace ircur {
 
@@ -93,12 +94,15 @@ static int ld_core(int nJ) {
 size_t svd_smem_bytes(int nI, int nJ, int Rpad, bool* core_in_smem) {
   const int ldc = ld_core(nJ);
   SvdLayout L = svd_layout(nI, nJ, ldc, Rpad, true);
+  size_t bytes;
   if (L.pch >= 2 && L.total <= kSvdSmemBudget) {
     *core_in_smem = true;
-    return L.total;
+    bytes = L.total;
+  } else {
+    *core_in_smem = false;
+    bytes = svd_layout(nI, nJ, ldc, Rpad, false).total;
   }
-  *core_in_smem = false;
-  return svd_layout(nI, nJ, ldc, Rpad, false).total;
+  return bytes > sizeof(SamplerSmem) ? bytes : sizeof(SamplerSmem);  // the sampler blocks share the launch
 }
 
 struct SvdSmall {
@@ -342,6 +346,20 @@ __global__ void __launch_bounds__(SvdThreads<R>::value, 1) svd_kernel(IterDesc d
   if (st->done || st->status) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int k = st->k;
+  if (blockIdx.x > 0) {
+    // IRCUR-R drawing its own index sets: blocks 1 and 2 draw I_{k+1}, J_{k+1}
+    // on otherwise idle SMs while block 0 factorises the core (nothing in this
+    // iteration reads them; the next iteration's core kernel does)
+    const int axis = (int)blockIdx.x - 1;
+    if (k + 1 < d.max_iter) {
+      int* out = axis ? const_cast<int*>(d.J_all) + (int64_t)(k + 1) * d.nJ
+                      : const_cast<int*>(d.I_all) + (int64_t)(k + 1) * d.nI;
+      sample_subset(d.seed, k + 1, axis, axis ? d.n2 : d.n1, axis ? d.nJ : d.nI, out,
+                    *reinterpret_cast<SamplerSmem*>(smem));
+    }
+    return;
+  }
+  trace_start(d.trace, 3 * k + 1);
   const int nI = d.nI, nJ = d.nJ, r = d.r;
   const SvdLayout L = svd_layout(nI, nJ, d.ldCore, R, core_in_smem);
   const int ldm = L.ldm, ldu = L.ldu;
@@ -565,6 +583,10 @@ __global__ void __launch_bounds__(SvdThreads<R>::value, 1) svd_kernel(IterDesc d
     st->svd_steps += steps;
     st->svd_last_steps = steps;
   }
+  if (d.trace) {
+    __syncthreads();
+    trace_stop(d.trace, 3 * d.max_iter, 3 * k + 1);
+  }
 }
 
 // Singular values of the last Rayleigh-Ritz matrix T (the r largest singular
@@ -653,11 +675,11 @@ static cudaError_t launch_svd_r(const IterDesc& d, cudaStream_t s) {
   if (in_smem) {
     cudaError_t e = cudaFuncSetAttribute(svd_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    svd_kernel<R, true><<<1, SvdThreads<R>::value, bytes, s>>>(d);
+    svd_kernel<R, true><<<1 + (d.sampleAhead ? 2 : 0), SvdThreads<R>::value, bytes, s>>>(d);
   } else {
     cudaError_t e = cudaFuncSetAttribute(svd_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    svd_kernel<R, false><<<1, SvdThreads<R>::value, bytes, s>>>(d);
+    svd_kernel<R, false><<<1 + (d.sampleAhead ? 2 : 0), SvdThreads<R>::value, bytes, s>>>(d);
   }
   return cudaGetLastError();
 }

@@ -23,7 +23,8 @@ IRCUR_MAX_RANK = 16
 EXPORTED = (
     "ircur_create", "ircur_destroy", "ircur_solve", "ircur_get_factors", "ircur_get_indices",
     "ircur_get_errors", "ircur_reconstruct", "ircur_solve_host", "ircur_sample_indices",
-    "ircur_status_string", "ircur_last_error_string", "ircur_solve_noalloc",
+    "ircur_status_string", "ircur_last_error_string", "ircur_solve_noalloc", "ircur_set_trace",
+    "ircur_get_trace", "ircur_get_cur",
 )
 
 
@@ -71,6 +72,9 @@ def _lib():
         lib.ircur_solve_host.argtypes = [P, P, P, P, C.POINTER(ircur_result)]
         lib.ircur_sample_indices.argtypes = [U64, I32, I32, I64, I32, P, P]
         lib.ircur_solve_noalloc.argtypes = [C.POINTER(ircur_params), P, I64, P, P, C.POINTER(ircur_result), P]
+        lib.ircur_set_trace.argtypes = [P, I32]
+        lib.ircur_get_cur.argtypes = [P, P, I64, P, P, P]
+        lib.ircur_get_trace.argtypes = [P, C.POINTER(C.c_double), C.POINTER(I32)]
         lib.ircur_status_string.argtypes = [C.c_int]
         lib.ircur_status_string.restype = C.c_char_p
         lib.ircur_last_error_string.argtypes = []
@@ -155,6 +159,22 @@ def ircur_sample_indices(seed, draw, axis, n, m, out, stream=None):
     _check(_lib().ircur_sample_indices(seed, draw, axis, n, m, _ptr(out), stream), "ircur_sample_indices")
 
 
+def ircur_get_cur(ctx, D, ldD, C=None, U=None, R=None):
+    _check(_lib().ircur_get_cur(ctx, _ptr(D), ldD, _ptr(C), _ptr(U), _ptr(R)), "ircur_get_cur")
+
+
+def ircur_set_trace(ctx, enable):
+    _check(_lib().ircur_set_trace(ctx, int(bool(enable))), "ircur_set_trace")
+
+
+def ircur_get_trace(ctx, max_iter):
+    """Per-iteration kernel spans (us) of the last traced solve: list of (core, svd, pass)."""
+    buf = (C.c_double * (3 * max_iter))()
+    cnt = C.c_int32()
+    _check(_lib().ircur_get_trace(ctx, buf, C.byref(cnt)), "ircur_get_trace")
+    return [(buf[3 * k], buf[3 * k + 1], buf[3 * k + 2]) for k in range(cnt.value)]
+
+
 def ircur_solve_noalloc(params: ircur_params, D, ldD, A, B, stream=None):
     """Allocation-free IRCUR-F solve (see include/ircur.h): writes the factors
     into the caller's device tensors A (n1 x r) and B (r x n2); L = A B."""
@@ -228,6 +248,15 @@ class IRCUR:
         sig = torch.empty(self.p.r, dtype=torch.float32, device="cuda")
         ircur_get_indices(self._ctx, I, J, sig)
         return I, J, sig
+
+    def cur(self, D):
+        """C (n1 x |J|), U (|I| x |J|), R (|I| x n2) of the last iterate (Alg. 1 output)."""
+        import torch
+        C = torch.empty((self.p.n1, self.nJ), dtype=torch.float32, device="cuda")
+        U = torch.empty((self.nI, self.nJ), dtype=torch.float32, device="cuda")
+        R = torch.empty((self.nI, self.p.n2), dtype=torch.float32, device="cuda")
+        ircur_get_cur(self._ctx, D, D.stride(0), C, U, R)
+        return C, U, R
 
     def errors(self):
         return ircur_get_errors(self._ctx, self.p.max_iter)

@@ -267,3 +267,29 @@ def test_metric_size_sampled_parity(resample):
     s2 = ir.IRCUR(n, n, r, tol=1e-5, max_iter=100, resample=resample, seed=1)
     res2 = s2.solve(D)
     assert res2.converged and abs(res2.iters - K) <= 1
+
+
+# ---------------------------------------------------------------- a10: CUR output
+@pytest.mark.parametrize("resample", [True, False])
+def test_cur_output_matches_oracle(resample):
+    """C_K, U_K, R_K (Alg. 1 output), the index sets and the singular values of
+    the last core against the oracle at equal iteration counts; C U^+ R = A B."""
+    n1, n2, r = 800, 700, 4
+    p = synth.planted(n1, n2, r, 0.1, seed=17)
+    ref = oracle_run(p.D, r, max_iter=100, tol=1e-5, resample=resample, seed=6)
+    K = ref.iters
+    D = torch.from_numpy(p.D).cuda()
+    s = ir.IRCUR(n1, n2, r, tol=1e-12, max_iter=K, resample=resample, seed=6)
+    s.solve(D)
+    C, U, R = s.cur(D)
+    I, J, sig = s.indices()
+    A, B = s.factors()
+    torch.cuda.synchronize()
+    assert np.array_equal(I.cpu().numpy(), ref.I) and np.array_equal(J.cpu().numpy(), ref.J)
+    Cg, Ug, Rg = (x.double().cpu().numpy() for x in (C, U, R))
+    assert rel(Cg, ref.C) <= TOL_LS and rel(Rg, ref.R) <= TOL_LS and rel(Ug, ref.U) <= TOL_LS
+    assert np.allclose(sig.cpu().numpy(), ref.s_r, rtol=1e-5)
+    Up = np.linalg.pinv(Ug, rcond=1e-6)
+    L_cur = Cg @ Up @ Rg
+    L_ab = A.double().cpu().numpy() @ B.double().cpu().numpy()
+    assert rel(L_cur, L_ab) <= 1e-4
