@@ -49,6 +49,9 @@ typedef enum {
 /* Largest rank r this build supports. */
 #define IRCUR_MAX_RANK 16
 
+/* Largest number of instances of one ircur_batch. */
+#define IRCUR_MAX_BATCH 4096
+
 typedef struct {
   int64_t n1, n2;    /* D is n1 x n2 (Alg. 1 input D) */
   int32_t r;         /* target rank r, 1 <= r <= IRCUR_MAX_RANK (Alg. 1) */
@@ -190,6 +193,43 @@ ircur_status ircur_get_trace(ircur_ctx* ctx, double* span_us, int32_t* iters);
  * threads -- race and must not be issued. */
 ircur_status ircur_solve_noalloc(const ircur_params* params, const float* D, int64_t ldD, float* A, float* B,
                                  ircur_result* out, void* stream);
+
+/* Batched solves of independent problems.  The paper solves one problem at
+ * a time (Alg. 1); a batch runs Alg. 1 on `count` unrelated problems at once
+ * -- each with its own shape, rank, sample sizes, thresholds, tolerance,
+ * iteration cap and variant (params[i]) -- so that many problems too small to
+ * fill the GPU on their own share every kernel launch.  Each instance
+ * computes what ircur_create + ircur_solve with params[i] (and no explicit
+ * index sets) computes: the same index sets, and the same iterates bit for bit
+ * when the batch's largest padded rank equals the instance's own (otherwise
+ * the wider padding changes only the rounding order of the core
+ * factorisation).  An instance that meets its stopping test stops while the
+ * others go on.  All instances use the stream given here.
+ * ircur_batch_create validates every params[i] as ircur_create does (the
+ * first failure is returned), allocates one workspace per instance, and
+ * returns ENOTSUP when the instances' shared padded rank (the largest of the
+ * batch) does not fit an instance's shared-memory layout.  count in
+ * [1, IRCUR_MAX_BATCH]. */
+typedef struct ircur_batch ircur_batch;
+ircur_status ircur_batch_create(const ircur_params* params, int32_t count, void* stream, ircur_batch** out);
+
+/* Release the batch and its instances (waits for the stream). */
+void ircur_batch_destroy(ircur_batch* b);
+
+/* Solve every instance.  D: host array of `count` device pointers, D[i] the
+ * n1_i x n2_i row-major data of instance i with leading dimension ldD[i]
+ * (host array, ldD[i] >= n2_i).  out: host array of `count` results, each as
+ * ircur_solve fills it.  Synchronises the stream.  Returns OK when every
+ * instance succeeded, else the first failing instance's status (every out[i]
+ * is still filled; instances that succeeded can be read).  The first solve
+ * with a given set of D pointers records a CUDA graph; later solves with the
+ * same pointers replay it. */
+ircur_status ircur_batch_solve(ircur_batch* b, const float* const* D, const int64_t* ldD, ircur_result* out);
+
+/* Context of instance i (owned by the batch: do not destroy it), for
+ * ircur_get_factors, ircur_get_indices, ircur_get_cur, ircur_get_errors and
+ * ircur_reconstruct after ircur_batch_solve.  Null for i out of range. */
+ircur_ctx* ircur_batch_instance(ircur_batch* b, int32_t i);
 
 /* Human-readable name of a status code (static string). */
 const char* ircur_status_string(ircur_status s);

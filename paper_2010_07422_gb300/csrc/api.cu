@@ -8,6 +8,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <memory>
 #include <new>
 
 #include "ircur.h"
@@ -131,7 +132,7 @@ static ircur_status validate_params(const ircur_params* p, ircur_params* out) {
   return IRCUR_OK;
 }
 
-extern "C" ircur_status ircur_create(const ircur_params* params, void* stream, ircur_ctx** out) {
+static ircur_status create_impl(const ircur_params* params, void* stream, int min_rpad, ircur_ctx** out) {
   if (!out) return IRCUR_EINVAL;
   *out = nullptr;
   ircur_params p;
@@ -142,7 +143,7 @@ extern "C" ircur_status ircur_create(const ircur_params* params, void* stream, i
   ircur_ctx* c = new (std::nothrow) ircur_ctx();
   if (!c) return IRCUR_ENOMEM;
   c->p = p;
-  c->Rpad = pad_rank(p.r);
+  c->Rpad = pad_rank(p.r > min_rpad ? p.r : min_rpad);
   c->stream = reinterpret_cast<cudaStream_t>(stream);
   c->draws = p.resample ? p.max_iter : 1;
   const int R = c->Rpad;
@@ -270,6 +271,10 @@ extern "C" ircur_status ircur_create(const ircur_params* params, void* stream, i
   return IRCUR_OK;
 }
 
+extern "C" ircur_status ircur_create(const ircur_params* params, void* stream, ircur_ctx** out) {
+  return create_impl(params, stream, 0, out);
+}
+
 extern "C" void ircur_destroy(ircur_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
@@ -340,13 +345,14 @@ static ircur_status read_state(ircur_ctx* c) {
   return IRCUR_OK;
 }
 
-extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, const int32_t* idx_I,
-                                    const int32_t* idx_J, ircur_result* out) {
-  if (!c || !D || !out) return IRCUR_EINVAL;
+// Everything of a solve before the iteration loop: descriptor for this D,
+// state reset, index sets, zeta_0 = max|D| (and D^T for IRCUR-R), the fixed
+// panels of IRCUR-F, A_0 = B_0 = 0.  Returns the descriptor in c->desc.
+static ircur_status solve_prologue(ircur_ctx* c, const float* D, int64_t ldD, const int32_t* idx_I,
+                                   const int32_t* idx_J, cudaStream_t s) {
   const ircur_params& p = c->p;
   if (ldD < p.n2 || (reinterpret_cast<uintptr_t>(D) & 3)) return IRCUR_EINVAL;
   if ((idx_I == nullptr) != (idx_J == nullptr)) return IRCUR_EINVAL;
-  cudaStream_t s = c->stream;
   IterDesc d = c->desc;
   d.D = D;
   d.ldD = ldD;
@@ -356,6 +362,7 @@ extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, c
   d.sampleAhead = (p.resample && !idx_I) ? 1 : 0;
   d.trace = c->trace;
   c->desc = d;
+  c->solved = 0;
   if (c->trace) {
     const size_t half = (size_t)3 * p.max_iter * 8;
     IRCUR_CK(cudaMemsetAsync(c->trace, 0xFF, half, s));
@@ -383,7 +390,36 @@ extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, c
   if (!p.resample) IRCUR_CK(launch_gather(d, s));
   IRCUR_CK(cudaMemsetAsync(c->A[0], 0, (size_t)p.n1 * c->Rpad * 4, s));
   IRCUR_CK(cudaMemsetAsync(c->B[0], 0, (size_t)c->Rpad * p.n2 * 4, s));
+  return IRCUR_OK;
+}
 
+// The result of a solve from the device state (already read into host_state).
+static ircur_status solve_epilogue(ircur_ctx* c, ircur_result* out) {
+  const State& h = c->host_state;
+  c->solved = 1;
+  memset(out, 0, sizeof(*out));
+  out->iters = h.k;
+  out->converged = (h.k > 0 && h.e <= c->p.tol) ? 1 : 0;
+  out->flags = h.flags;
+  out->svd_steps = h.svd_steps;
+  out->final_err = h.e;
+  out->zeta0 = h.zeta0;
+  out->zeta_next = h.zeta;
+  if (h.status != 0) {
+    c->solved = 0;
+    return (ircur_status)h.status;
+  }
+  return IRCUR_OK;
+}
+
+extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, const int32_t* idx_I,
+                                    const int32_t* idx_J, ircur_result* out) {
+  if (!c || !D || !out) return IRCUR_EINVAL;
+  const ircur_params& p = c->p;
+  ircur_status ps = solve_prologue(c, D, ldD, idx_I, idx_J, c->stream);
+  if (ps != IRCUR_OK) return ps;
+  const IterDesc& d = c->desc;
+  cudaStream_t s = c->stream;
   if (use_graph()) {
     if (!c->exec || c->graph_D != D || c->graph_ldD != ldD || c->graph_sample_ahead != d.sampleAhead ||
         c->graph_trace != d.trace) {
@@ -405,21 +441,7 @@ extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, c
   }
   ircur_status rs = read_state(c);
   if (rs != IRCUR_OK) return rs;
-  const State& h = c->host_state;
-  c->solved = 1;
-  memset(out, 0, sizeof(*out));
-  out->iters = h.k;
-  out->converged = (h.k > 0 && h.e <= p.tol) ? 1 : 0;
-  out->flags = h.flags;
-  out->svd_steps = h.svd_steps;
-  out->final_err = h.e;
-  out->zeta0 = h.zeta0;
-  out->zeta_next = h.zeta;
-  if (h.status != 0) {
-    c->solved = 0;
-    return (ircur_status)h.status;
-  }
-  return IRCUR_OK;
+  return solve_epilogue(c, out);
 }
 
 extern "C" ircur_status ircur_get_factors(ircur_ctx* c, float* A, float* B) {
@@ -583,3 +605,320 @@ extern "C" const char* ircur_status_string(ircur_status s) {
 }
 
 extern "C" const char* ircur_last_error_string(void) { return g_last_error; }
+
+// ---------------------------------------------------------------------------
+// Batches of independent problems (each with its own shape, rank, sample
+// sizes and variant) solved together.  Every iteration kernel is launched once
+// per iteration for the whole batch: the core and SVD launches index the
+// instance by a grid dimension, the pass launch lays all instances' tiles end
+// to end, and a one-block kernel ends the loop once every instance has met its
+// own stopping test (instances that stopped skip their blocks).  The instances
+// share one padded rank (the largest), so one set of kernel instantiations
+// serves the batch.
+
+struct ircur_batch {
+  int count;
+  int Rpad;
+  int max_iter;  // the largest max_iter of the batch
+  cudaStream_t stream;
+  cudaStream_t capture_stream;
+  cudaStream_t body_stream;
+  ircur_ctx** inst;
+  IterDesc* hdesc;
+  void* dws;        // device: descriptors, tile prefix sums, SVD lists, loop flag
+  State* hstates;   // pinned host copies of every instance's state after a solve
+  BatchLaunch bl;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  const float** graph_D;  // the D pointers and leading dimensions the graph was built for
+  int64_t* graph_ld;
+};
+
+static void batch_reset_graph(ircur_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+extern "C" void ircur_batch_destroy(ircur_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  batch_reset_graph(b);
+  if (b->inst) {
+    for (int i = 0; i < b->count; ++i) ircur_destroy(b->inst[i]);
+    delete[] b->inst;
+  }
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  if (b->body_stream) cudaStreamDestroy(b->body_stream);
+  if (b->dws) cudaFree(b->dws);
+  if (b->hstates) cudaFreeHost(b->hstates);
+  delete[] b->hdesc;
+  delete[] b->graph_D;
+  delete[] b->graph_ld;
+  delete b;
+}
+
+extern "C" ircur_status ircur_batch_create(const ircur_params* params, int32_t count, void* stream,
+                                           ircur_batch** out) {
+  if (!out) return IRCUR_EINVAL;
+  *out = nullptr;
+  if (!params || count < 1 || count > IRCUR_MAX_BATCH) return IRCUR_EINVAL;
+  int Rpad = 1;
+  for (int i = 0; i < count; ++i) {
+    ircur_params q;
+    ircur_status vs = validate_params(&params[i], &q);
+    if (vs != IRCUR_OK) return vs;
+    const int rp = pad_rank(q.r);
+    if (rp > Rpad) Rpad = rp;
+  }
+  ircur_batch* b = new (std::nothrow) ircur_batch();
+  if (!b) return IRCUR_ENOMEM;
+  b->count = count;
+  b->Rpad = Rpad;
+  b->stream = reinterpret_cast<cudaStream_t>(stream);
+  b->inst = new (std::nothrow) ircur_ctx*[count]();
+  b->hdesc = new (std::nothrow) IterDesc[count];
+  b->graph_D = new (std::nothrow) const float*[count]();
+  b->graph_ld = new (std::nothrow) int64_t[count]();
+  if (!b->inst || !b->hdesc || !b->graph_D || !b->graph_ld) {
+    ircur_batch_destroy(b);
+    return IRCUR_ENOMEM;
+  }
+  for (int i = 0; i < count; ++i) {
+    ircur_status cs = create_impl(&params[i], stream, Rpad, &b->inst[i]);
+    if (cs != IRCUR_OK) {
+      ircur_batch_destroy(b);
+      return cs;
+    }
+  }
+  // the shared padded rank must still fit each instance's shared-memory layouts
+  BatchLaunch& bl = b->bl;
+  memset(&bl, 0, sizeof(bl));
+  std::unique_ptr<int[]> tiles(new int[count + 1]);
+  std::unique_ptr<int[]> lists(new int[count]);
+  std::unique_ptr<unsigned char[]> grp(new unsigned char[count]);
+  int maxNI = 1, n0 = 0, roles = 1;
+  tiles[0] = 0;
+  for (int i = 0; i < count; ++i) {
+    const ircur_ctx* c = b->inst[i];
+    const ircur_params& p = c->p;
+    const size_t ps = pass_smem_bytes(p.nI, p.nJ, Rpad);
+    bool in_smem = false;
+    const size_t ss = svd_smem_bytes(p.nI, p.nJ, Rpad, &in_smem);
+    if (ps > 227 * 1024 || ss > 227 * 1024) {
+      ircur_batch_destroy(b);
+      return IRCUR_ENOTSUP;
+    }
+    if (ps > bl.pass_smem) bl.pass_smem = ps;
+    const int g = in_smem ? 0 : 1;
+    grp[i] = (unsigned char)g;
+    if (ss > bl.svd_smem[g]) bl.svd_smem[g] = ss;
+    if (g == 0) ++n0;
+    const int64_t t = (int64_t)tiles[i] + c->desc.nRowTiles + c->desc.nColTiles;
+    if (t > (1ll << 30)) {
+      ircur_batch_destroy(b);
+      return IRCUR_ENOTSUP;
+    }
+    tiles[i + 1] = (int)t;
+    if (p.nI > maxNI) maxNI = p.nI;
+    if (p.resample) roles = 3;
+    if (p.max_iter > b->max_iter) b->max_iter = p.max_iter;
+  }
+  {
+    int a = 0, z = n0;
+    for (int i = 0; i < count; ++i) lists[grp[i] ? z++ : a++] = i;
+  }
+  // device workspace: descriptors | tile prefix sums | SVD lists | loop flag
+  const size_t oDesc = 0;
+  const size_t oTiles = (oDesc + (size_t)count * sizeof(IterDesc) + 255) & ~(size_t)255;
+  const size_t oList = (oTiles + (size_t)(count + 1) * 4 + 255) & ~(size_t)255;
+  const size_t oFlag = (oList + (size_t)count * 4 + 255) & ~(size_t)255;
+  const size_t bytes = oFlag + 256;
+  cudaError_t e = cudaMalloc(&b->dws, bytes);
+  if (e != cudaSuccess) {
+    set_error("cudaMalloc(batch workspace)", e);
+    cudaGetLastError();
+    ircur_batch_destroy(b);
+    return IRCUR_ENOMEM;
+  }
+  e = cudaMallocHost(reinterpret_cast<void**>(&b->hstates), (size_t)count * sizeof(State));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->body_stream, cudaStreamNonBlocking);
+  char* base = static_cast<char*>(b->dws);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->dws, 0, bytes, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(base + oTiles, tiles.get(), (size_t)(count + 1) * 4, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(base + oList, lists.get(), (size_t)count * 4, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    set_error("ircur_batch_create", e);
+    ircur_batch_destroy(b);
+    return IRCUR_ECUDA;
+  }
+  bl.ds = reinterpret_cast<const IterDesc*>(base + oDesc);
+  bl.count = count;
+  bl.tile_base = reinterpret_cast<const int*>(base + oTiles);
+  bl.total_tiles = tiles[count];
+  {
+    const int want = (4 * kNumSMsHint + count - 1) / count;
+    bl.core_blocks = want < maxNI ? (want > 0 ? want : 1) : maxNI;
+  }
+  bl.svd_list[0] = reinterpret_cast<const int*>(base + oList);
+  bl.svd_list[1] = reinterpret_cast<const int*>(base + oList) + n0;
+  bl.svd_n[0] = n0;
+  bl.svd_n[1] = count - n0;
+  bl.svd_roles = roles;
+  bl.cond = 0;
+  bl.any_active = reinterpret_cast<int*>(base + oFlag);
+  *out = b;
+  return IRCUR_OK;
+}
+
+extern "C" ircur_ctx* ircur_batch_instance(ircur_batch* b, int32_t i) {
+  if (!b || i < 0 || i >= b->count) return nullptr;
+  return b->inst[i];
+}
+
+// Upload the descriptors the prologues left in each instance (no graph
+// condition of their own: the loop-control kernel owns the batch's).
+static ircur_status batch_upload_descs(ircur_batch* b) {
+  for (int i = 0; i < b->count; ++i) {
+    b->hdesc[i] = b->inst[i]->desc;
+    b->hdesc[i].cond = 0;
+  }
+  IRCUR_CK(cudaMemcpyAsync(const_cast<IterDesc*>(b->bl.ds), b->hdesc, (size_t)b->count * sizeof(IterDesc),
+                           cudaMemcpyHostToDevice, b->stream));
+  return IRCUR_OK;
+}
+
+static ircur_status batch_abort_capture(ircur_batch* b, cudaStream_t s, ircur_status st) {
+  cudaGraph_t g = nullptr;
+  cudaStreamEndCapture(s, &g);
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  batch_reset_graph(b);
+  return st;
+}
+
+// One graph for a whole batch solve: every instance's prologue, the
+// conditional while-node running the batched iteration, and the copies of the
+// instances' states to pinned host memory.
+static ircur_status batch_build_graph(ircur_batch* b, const float* const* D, const int64_t* ldD) {
+  batch_reset_graph(b);
+  cudaStream_t cs = b->capture_stream;
+  IRCUR_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+  for (int i = 0; i < b->count; ++i) {
+    ircur_status ps = solve_prologue(b->inst[i], D[i], ldD[i], nullptr, nullptr, cs);
+    if (ps != IRCUR_OK) return batch_abort_capture(b, cs, ps);
+  }
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &ndeps);
+  cudaGraphConditionalHandle h;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) {
+    set_error("batch graph: conditional handle", e);
+    return batch_abort_capture(b, cs, IRCUR_ECUDA);
+  }
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+  memset(raw, 0, sizeof(raw));
+  cudaGraphNodeParams* cp = reinterpret_cast<cudaGraphNodeParams*>(raw);
+  cp->type = cudaGraphNodeTypeConditional;
+  cp->conditional.handle = h;
+  cp->conditional.type = cudaGraphCondTypeWhile;
+  cp->conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, cp);
+  if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) {
+    set_error("batch graph: while node", e);
+    return batch_abort_capture(b, cs, IRCUR_ECUDA);
+  }
+  BatchLaunch bl = b->bl;
+  bl.cond = (unsigned long long)h;
+  e = cudaStreamBeginCaptureToGraph(b->body_stream, cp->conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    set_error("batch graph: body capture", e);
+    return batch_abort_capture(b, cs, IRCUR_ECUDA);
+  }
+  cudaError_t le = launch_batch_iteration(bl, b->Rpad, b->body_stream);
+  cudaGraph_t body = nullptr;
+  cudaError_t be = cudaStreamEndCapture(b->body_stream, &body);
+  if (le != cudaSuccess || be != cudaSuccess) {
+    set_error("batch graph: iteration", le != cudaSuccess ? le : be);
+    return batch_abort_capture(b, cs, IRCUR_ECUDA);
+  }
+  for (int i = 0; i < b->count; ++i) {
+    e = cudaMemcpyAsync(b->hstates + i, b->inst[i]->st, sizeof(State), cudaMemcpyDeviceToHost, cs);
+    if (e != cudaSuccess) {
+      set_error("batch graph: state copy", e);
+      return batch_abort_capture(b, cs, IRCUR_ECUDA);
+    }
+  }
+  e = cudaStreamEndCapture(cs, &b->graph);
+  if (e != cudaSuccess) {
+    set_error("batch graph: end capture", e);
+    batch_reset_graph(b);
+    return IRCUR_ECUDA;
+  }
+  IRCUR_CK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  ircur_status us = batch_upload_descs(b);
+  if (us != IRCUR_OK) {
+    batch_reset_graph(b);
+    return us;
+  }
+  for (int i = 0; i < b->count; ++i) {
+    b->graph_D[i] = D[i];
+    b->graph_ld[i] = ldD[i];
+  }
+  return IRCUR_OK;
+}
+
+extern "C" ircur_status ircur_batch_solve(ircur_batch* b, const float* const* D, const int64_t* ldD,
+                                          ircur_result* out) {
+  if (!b || !D || !ldD || !out) return IRCUR_EINVAL;
+  for (int i = 0; i < b->count; ++i) {
+    if (!D[i] || ldD[i] < b->inst[i]->p.n2 || (reinterpret_cast<uintptr_t>(D[i]) & 3)) return IRCUR_EINVAL;
+    b->inst[i]->solved = 0;
+  }
+  cudaStream_t s = b->stream;
+  if (use_graph()) {
+    bool same = b->exec != nullptr;
+    for (int i = 0; same && i < b->count; ++i) same = b->graph_D[i] == D[i] && b->graph_ld[i] == ldD[i];
+    if (!same) {
+      ircur_status bs = batch_build_graph(b, D, ldD);
+      if (bs != IRCUR_OK) return bs;
+    }
+    IRCUR_CK(cudaGraphLaunch(b->exec, s));
+  } else {
+    for (int i = 0; i < b->count; ++i) {
+      ircur_status ps = solve_prologue(b->inst[i], D[i], ldD[i], nullptr, nullptr, s);
+      if (ps != IRCUR_OK) return ps;
+    }
+    ircur_status us = batch_upload_descs(b);
+    if (us != IRCUR_OK) return us;
+    int active = 1;
+    for (int it = 0; it < b->max_iter && active; ++it) {
+      IRCUR_CK(launch_batch_iteration(b->bl, b->Rpad, s));
+      if ((it & 3) == 3) {
+        IRCUR_CK(cudaMemcpyAsync(&active, b->bl.any_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+        IRCUR_CK(cudaStreamSynchronize(s));
+      }
+    }
+    for (int i = 0; i < b->count; ++i)
+      IRCUR_CK(cudaMemcpyAsync(b->hstates + i, b->inst[i]->st, sizeof(State), cudaMemcpyDeviceToHost, s));
+  }
+  IRCUR_CK(cudaStreamSynchronize(s));
+  ircur_status first = IRCUR_OK;
+  for (int i = 0; i < b->count; ++i) {
+    b->inst[i]->host_state = b->hstates[i];
+    const ircur_status si = solve_epilogue(b->inst[i], &out[i]);
+    if (si != IRCUR_OK && first == IRCUR_OK) first = si;
+  }
+  return first;
+}

@@ -92,6 +92,23 @@ struct IterDesc {
   uint64_t seed;
 };
 
+// One iteration for a batch of independent instances (all with the same
+// padded rank): every kernel covers all instances of the batch.
+struct BatchLaunch {
+  const IterDesc* ds;      // device array, one descriptor per instance
+  int count;
+  const int* tile_base;    // device, count + 1 prefix sums of panel tiles
+  int total_tiles;
+  int core_blocks;         // blocks per instance of the core kernel
+  const int* svd_list[2];  // device instance lists: [0] core in shared memory, [1] core in global memory
+  int svd_n[2];
+  size_t svd_smem[2];
+  int svd_roles;           // 1, or 3 when some instance draws its next index sets
+  size_t pass_smem;
+  unsigned long long cond; // graph conditional handle (0 = no graph)
+  int* any_active;         // device flag written by the loop-control kernel
+};
+
 // Launch wrappers (return cudaGetLastError()).
 cudaError_t launch_sample(uint64_t seed, int draw0, int draws, int64_t n1, int64_t n2, int nI, int nJ,
                           int* I_all, int* J_all, int only_axis, cudaStream_t s);
@@ -111,6 +128,8 @@ cudaError_t launch_reconstruct(const float* A, const float* B, int Rpad, int64_t
 cudaError_t launch_get_cur(const IterDesc& d, int Rpad, int K, const float* D, int64_t ldD, float* C, float* U,
                            float* Rm, cudaStream_t s);
 size_t svd_smem_bytes(int nI, int nJ, int Rpad, bool* core_in_smem);
+cudaError_t launch_batch_iteration(const BatchLaunch& b, int Rpad, cudaStream_t s);
+cudaError_t launch_svd_batch(const BatchLaunch& b, int Rpad, cudaStream_t s);
 cudaError_t launch_sigma(const float* Tm, int r, int Rpad, float* sigma, cudaStream_t s);
 size_t pass_smem_bytes(int nI, int nJ, int Rpad);
 int pad_rank(int r);

@@ -27,7 +27,7 @@ int pad_rank(int r) {
 
 // ---------------------------------------------------------------------------
 template <int R>
-__global__ void __launch_bounds__(256) core_kernel(IterDesc d) {
+__device__ __forceinline__ void core_body(const IterDesc& d, int blk, int nblk) {
   const State* st = d.st;
   if (st->done || st->status) return;
   const int k = st->k;
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(256) core_kernel(IterDesc d) {
   const float* A = d.A[cur];
   const float* B = d.B[cur];
   trace_start(d.trace, 3 * k + 0);
-  for (int a = blockIdx.x; a < d.nI; a += gridDim.x) {
+  for (int a = blk; a < d.nI; a += nblk) {
     const int ia = I[a];
     float arow[R];
 #pragma unroll
@@ -62,6 +62,17 @@ __global__ void __launch_bounds__(256) core_kernel(IterDesc d) {
     __syncthreads();
     trace_stop(d.trace, 3 * d.max_iter, 3 * k + 0);
   }
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) core_kernel(IterDesc d) {
+  core_body<R>(d, blockIdx.x, gridDim.x);
+}
+
+// Batched form: blockIdx.y selects the instance.
+template <int R>
+__global__ void __launch_bounds__(256) core_batch_kernel(const IterDesc* __restrict__ ds) {
+  core_body<R>(ds[blockIdx.y], blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -267,11 +278,10 @@ __device__ void panel_pass(const IterDesc& d, int tile, int k, float zeta, unsig
 // the per-block partial sums in a fixed order, evaluates e_{k+1}, advances k
 // and zeta, and drives the graph's while-node (Alg. 1: "while e_k > epsilon").
 template <int R>
-__global__ void __launch_bounds__(kPanelThreads, 3) pass_kernel(IterDesc d) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void pass_body(const IterDesc& d, int blk, int nblk, unsigned char* smem) {
   State* st = d.st;
   if (st->done || st->status) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (blk == 0 && threadIdx.x == 0) {
       st->done = 1;
       if (d.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)d.cond, 0u);
     }
@@ -282,10 +292,10 @@ __global__ void __launch_bounds__(kPanelThreads, 3) pass_kernel(IterDesc d) {
   trace_start(d.trace, 3 * k + 2);
   double acc[2] = {0.0, 0.0};
   const int nPanel = d.nRowTiles + d.nColTiles;
-  if ((int)blockIdx.x < d.nRowTiles) {
-    panel_pass<R, false>(d, blockIdx.x, k, zeta, smem, acc);
-  } else if ((int)blockIdx.x < nPanel) {
-    panel_pass<R, true>(d, blockIdx.x - d.nRowTiles, k, zeta, smem, acc);
+  if (blk < d.nRowTiles) {
+    panel_pass<R, false>(d, blk, k, zeta, smem, acc);
+  } else if (blk < nPanel) {
+    panel_pass<R, true>(d, blk - d.nRowTiles, k, zeta, smem, acc);
   }
 
   __shared__ double red[4][kPanelThreads / 32];
@@ -300,12 +310,12 @@ __global__ void __launch_bounds__(kPanelThreads, 3) pass_kernel(IterDesc d) {
   if (threadIdx.x < 2) {
     double s = 0.0;
     for (int w = 0; w < kPanelThreads / 32; ++w) s += red[threadIdx.x][w];
-    d.partials[(size_t)blockIdx.x * 2 + threadIdx.x] = s;
+    d.partials[(size_t)blk * 2 + threadIdx.x] = s;
   }
   __threadfence();
   __syncthreads();
   trace_stop(d.trace, 3 * d.max_iter, 3 * k + 2);
-  if (threadIdx.x == 0) is_last = (atomicAdd(&st->counter, 1u) == gridDim.x - 1);
+  if (threadIdx.x == 0) is_last = (atomicAdd(&st->counter, 1u) == (unsigned)nblk - 1u);
   __syncthreads();
   if (!is_last) return;
   __threadfence();
@@ -313,7 +323,7 @@ __global__ void __launch_bounds__(kPanelThreads, 3) pass_kernel(IterDesc d) {
   if (warp < 4) {
     const int colside = warp >> 1, which = warp & 1;
     const unsigned b0 = colside ? (unsigned)d.nRowTiles : 0u;
-    const unsigned b1 = colside ? gridDim.x : (unsigned)d.nRowTiles;
+    const unsigned b1 = colside ? (unsigned)nblk : (unsigned)d.nRowTiles;
     double s = 0.0;
     const volatile double* pv = d.partials;
     for (unsigned b = b0 + lane; b < b1; b += 32) s += pv[(size_t)b * 2 + which];
@@ -336,6 +346,46 @@ __global__ void __launch_bounds__(kPanelThreads, 3) pass_kernel(IterDesc d) {
     __threadfence();
     trace_stop(d.trace, 3 * d.max_iter, 3 * k + 2);
     if (d.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)d.cond, done ? 0u : 1u);
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(kPanelThreads, 3) pass_kernel(IterDesc d) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  pass_body<R>(d, blockIdx.x, gridDim.x, smem);
+}
+
+// Batched form: the grid holds every instance's tiles back to back;
+// tile_base[i] is the first block of instance i (tile_base[count] = grid).
+template <int R>
+__global__ void __launch_bounds__(kPanelThreads, 3) pass_batch_kernel(const IterDesc* __restrict__ ds,
+                                                                      const int* __restrict__ tile_base, int count) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int lo = 0, hi = count - 1;  // instance i with tile_base[i] <= blockIdx.x < tile_base[i + 1]
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tile_base[mid] <= (int)blockIdx.x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  pass_body<R>(ds[lo], (int)blockIdx.x - tile_base[lo], tile_base[lo + 1] - tile_base[lo], smem);
+}
+
+// Batched loop control: the while-node continues while any instance runs.
+__global__ void batch_check_kernel(const IterDesc* __restrict__ ds, int count, unsigned long long cond,
+                                   int* any_active) {
+  __shared__ int act;
+  if (threadIdx.x == 0) act = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    const State* st = ds[i].st;
+    if (!st->done && !st->status) atomicOr(&act, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *any_active = act;
+    if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, act ? 1u : 0u);
   }
 }
 
@@ -365,6 +415,40 @@ static cudaError_t launch_iter_r(const IterDesc& d, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   pass_kernel<R><<<d.nRowTiles + d.nColTiles, kPanelThreads, bytes, s>>>(d);
   return cudaGetLastError();
+}
+
+template <int R>
+static cudaError_t launch_batch_iter_r(const BatchLaunch& b, cudaStream_t s) {
+  core_batch_kernel<R><<<dim3(b.core_blocks, b.count), 256, 0, s>>>(b.ds);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_svd_batch(b, R, s);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(pass_batch_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.pass_smem);
+  if (e != cudaSuccess) return e;
+  pass_batch_kernel<R><<<b.total_tiles, kPanelThreads, b.pass_smem, s>>>(b.ds, b.tile_base, b.count);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  batch_check_kernel<<<1, 256, 0, s>>>(b.ds, b.count, b.cond, b.any_active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_iteration(const BatchLaunch& b, int Rpad, cudaStream_t s) {
+  switch (Rpad) {
+    case 1: return launch_batch_iter_r<1>(b, s);
+    case 2: return launch_batch_iter_r<2>(b, s);
+    case 3: return launch_batch_iter_r<3>(b, s);
+    case 4: return launch_batch_iter_r<4>(b, s);
+    case 5: return launch_batch_iter_r<5>(b, s);
+    case 6: return launch_batch_iter_r<6>(b, s);
+    case 7: return launch_batch_iter_r<7>(b, s);
+    case 8: return launch_batch_iter_r<8>(b, s);
+    case 9: return launch_batch_iter_r<9>(b, s);
+    case 10: return launch_batch_iter_r<10>(b, s);
+    case 12: return launch_batch_iter_r<12>(b, s);
+    case 16: return launch_batch_iter_r<16>(b, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_iteration(const IterDesc& d, int Rpad, cudaStream_t s) {

@@ -340,18 +340,17 @@ __device__ __forceinline__ int rr_partner(int p, int k, int n) {
 // CS: the core is held in shared memory (a compile-time property, so that
 // every core access compiles to a shared-memory load).
 template <int R, bool CS>
-__global__ void __launch_bounds__(SvdThreads<R>::value, 1) svd_kernel(IterDesc d) {
+__device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned char* smem) {
   constexpr bool core_in_smem = CS;
   State* st = d.st;
   if (st->done || st->status) return;
-  extern __shared__ __align__(16) unsigned char smem[];
   const int k = st->k;
-  if (blockIdx.x > 0) {
+  if (role > 0) {
     // IRCUR-R drawing its own index sets: blocks 1 and 2 draw I_{k+1}, J_{k+1}
     // on otherwise idle SMs while block 0 factorises the core (nothing in this
     // iteration reads them; the next iteration's core kernel does)
-    const int axis = (int)blockIdx.x - 1;
-    if (k + 1 < d.max_iter) {
+    const int axis = role - 1;
+    if (d.sampleAhead && k + 1 < d.max_iter) {
       int* out = axis ? const_cast<int*>(d.J_all) + (int64_t)(k + 1) * d.nJ
                       : const_cast<int*>(d.I_all) + (int64_t)(k + 1) * d.nI;
       sample_subset(d.seed, k + 1, axis, axis ? d.n2 : d.n1, axis ? d.nJ : d.nI, out,
@@ -589,6 +588,21 @@ __global__ void __launch_bounds__(SvdThreads<R>::value, 1) svd_kernel(IterDesc d
   }
 }
 
+template <int R, bool CS>
+__global__ void __launch_bounds__(SvdThreads<R>::value, 1) svd_kernel(IterDesc d) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  svd_body<R, CS>(d, blockIdx.x, smem);
+}
+
+// Batched form: blockIdx.x indexes `list` (the instances of one core-layout
+// group), blockIdx.y is the role (0: core SVD, 1 and 2: next index sets).
+template <int R, bool CS>
+__global__ void __launch_bounds__(SvdThreads<R>::value, 1) svd_batch_kernel(const IterDesc* __restrict__ ds,
+                                                                           const int* __restrict__ list) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  svd_body<R, CS>(ds[list[blockIdx.x]], blockIdx.y, smem);
+}
+
 // Singular values of the last Rayleigh-Ritz matrix T (the r largest singular
 // values of the last core, descending): one-sided Jacobi in one warp, lane p
 // owning column p, round-robin pair ordering.  Used on request only.
@@ -682,6 +696,47 @@ static cudaError_t launch_svd_r(const IterDesc& d, cudaStream_t s) {
     svd_kernel<R, false><<<1 + (d.sampleAhead ? 2 : 0), SvdThreads<R>::value, bytes, s>>>(d);
   }
   return cudaGetLastError();
+}
+
+template <int R>
+static cudaError_t launch_svd_batch_r(const BatchLaunch& b, cudaStream_t s) {
+  if (b.svd_n[0] > 0) {
+    cudaError_t e = cudaFuncSetAttribute(svd_batch_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)b.svd_smem[0]);
+    if (e != cudaSuccess) return e;
+    svd_batch_kernel<R, true><<<dim3(b.svd_n[0], b.svd_roles), SvdThreads<R>::value, b.svd_smem[0], s>>>(
+        b.ds, b.svd_list[0]);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (b.svd_n[1] > 0) {
+    cudaError_t e = cudaFuncSetAttribute(svd_batch_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)b.svd_smem[1]);
+    if (e != cudaSuccess) return e;
+    svd_batch_kernel<R, false><<<dim3(b.svd_n[1], b.svd_roles), SvdThreads<R>::value, b.svd_smem[1], s>>>(
+        b.ds, b.svd_list[1]);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_svd_batch(const BatchLaunch& b, int Rpad, cudaStream_t s) {
+  switch (Rpad) {
+    case 1: return launch_svd_batch_r<1>(b, s);
+    case 2: return launch_svd_batch_r<2>(b, s);
+    case 3: return launch_svd_batch_r<3>(b, s);
+    case 4: return launch_svd_batch_r<4>(b, s);
+    case 5: return launch_svd_batch_r<5>(b, s);
+    case 6: return launch_svd_batch_r<6>(b, s);
+    case 7: return launch_svd_batch_r<7>(b, s);
+    case 8: return launch_svd_batch_r<8>(b, s);
+    case 9: return launch_svd_batch_r<9>(b, s);
+    case 10: return launch_svd_batch_r<10>(b, s);
+    case 12: return launch_svd_batch_r<12>(b, s);
+    case 16: return launch_svd_batch_r<16>(b, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_svd(const IterDesc& d, int Rpad, cudaStream_t s) {

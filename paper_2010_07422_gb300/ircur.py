@@ -24,7 +24,8 @@ EXPORTED = (
     "ircur_create", "ircur_destroy", "ircur_solve", "ircur_get_factors", "ircur_get_indices",
     "ircur_get_errors", "ircur_reconstruct", "ircur_solve_host", "ircur_sample_indices",
     "ircur_status_string", "ircur_last_error_string", "ircur_solve_noalloc", "ircur_set_trace",
-    "ircur_get_trace", "ircur_get_cur",
+    "ircur_get_trace", "ircur_get_cur", "ircur_batch_create", "ircur_batch_destroy", "ircur_batch_solve",
+    "ircur_batch_instance",
 )
 
 
@@ -75,12 +76,19 @@ def _lib():
         lib.ircur_set_trace.argtypes = [P, I32]
         lib.ircur_get_cur.argtypes = [P, P, I64, P, P, P]
         lib.ircur_get_trace.argtypes = [P, C.POINTER(C.c_double), C.POINTER(I32)]
+        lib.ircur_batch_create.argtypes = [C.POINTER(ircur_params), I32, P, C.POINTER(P)]
+        lib.ircur_batch_destroy.argtypes = [P]
+        lib.ircur_batch_destroy.restype = None
+        lib.ircur_batch_solve.argtypes = [P, C.POINTER(P), C.POINTER(I64), C.POINTER(ircur_result)]
+        lib.ircur_batch_instance.argtypes = [P, I32]
+        lib.ircur_batch_instance.restype = P
         lib.ircur_status_string.argtypes = [C.c_int]
         lib.ircur_status_string.restype = C.c_char_p
         lib.ircur_last_error_string.argtypes = []
         lib.ircur_last_error_string.restype = C.c_char_p
         for name in EXPORTED:
-            if name not in ("ircur_destroy", "ircur_status_string", "ircur_last_error_string"):
+            if name not in ("ircur_destroy", "ircur_status_string", "ircur_last_error_string",
+                            "ircur_batch_destroy", "ircur_batch_instance"):
                 getattr(lib, name).restype = C.c_int
         _LIB = lib
     return _LIB
@@ -184,6 +192,32 @@ def ircur_solve_noalloc(params: ircur_params, D, ldD, A, B, stream=None):
     return res
 
 
+def ircur_batch_create(params_list, stream=None):
+    n = len(params_list)
+    arr = (ircur_params * n)(*params_list)
+    b = C.c_void_p()
+    _check(_lib().ircur_batch_create(arr, n, stream, C.byref(b)), "ircur_batch_create")
+    return b
+
+
+def ircur_batch_destroy(b):
+    _lib().ircur_batch_destroy(b)
+
+
+def ircur_batch_solve(b, Ds, lds):
+    """Ds: device tensors (or raw pointers), lds: leading dimensions; returns the results."""
+    n = len(Ds)
+    ptrs = (C.c_void_p * n)(*[d.data_ptr() if hasattr(d, "data_ptr") else d for d in Ds])
+    ldv = (C.c_int64 * n)(*lds)
+    res = (ircur_result * n)()
+    status = _lib().ircur_batch_solve(b, ptrs, ldv, res)
+    return status, list(res)
+
+
+def ircur_batch_instance(b, i):
+    return C.c_void_p(_lib().ircur_batch_instance(b, i))
+
+
 # ---------------------------------------------------------------- convenience layer
 @dataclass
 class Result:
@@ -216,7 +250,20 @@ class IRCUR:
         self.nJ = nJ if nJ else sample_size(4, r, n2)
         self.last = None
 
+    @classmethod
+    def _view(cls, ctx, p, stream, owner):
+        """A non-owning handle on a context that `owner` (a batch) holds."""
+        self = cls.__new__(cls)
+        self.p, self.stream, self._ctx, self._owner = p, stream, ctx, owner
+        self.nI = p.nI if p.nI else sample_size(4, p.r, p.n1)
+        self.nJ = p.nJ if p.nJ else sample_size(4, p.r, p.n2)
+        self.last = None
+        return self
+
     def close(self):
+        if getattr(self, "_owner", None) is not None:
+            self._ctx = None
+            return
         if self._ctx:
             ircur_destroy(self._ctx)
             self._ctx = None
@@ -273,6 +320,63 @@ class IRCUR:
         ircur_reconstruct(self._ctx, D, D.stride(0) if D is not None else 0, L, L.stride(0),
                           S, S.stride(0) if S is not None else 0)
         return L, S
+
+
+class IRCURBatch:
+    """Independent IRCUR problems solved together (one kernel launch per
+    iteration step for the whole batch).
+
+    batch = IRCURBatch([dict(n1=500, n2=400, r=3), dict(n1=900, n2=900, r=6, resample=False)])
+    results = batch.solve([D0, D1])       # list of Result
+    L1, S1 = batch[1].reconstruct(D1)     # every IRCUR getter, per instance
+    """
+
+    def __init__(self, problems, stream=None):
+        import torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.params = []
+        for q in problems:
+            q = dict(q)
+            self.params.append(ircur_params(
+                n1=q["n1"], n2=q["n2"], r=q["r"], nI=q.get("nI", 0), nJ=q.get("nJ", 0),
+                zeta0=q.get("zeta0", 0.0), gamma=q.get("gamma", 0.7), tol=q.get("tol", 1e-5),
+                max_iter=q.get("max_iter", 100), resample=int(bool(q.get("resample", True))),
+                seed=q.get("seed", 0), precision=0, reserved=0))
+        self._b = ircur_batch_create(self.params, C.c_void_p(self.stream.cuda_stream))
+        self._views = [IRCUR._view(ircur_batch_instance(self._b, i), p, self.stream, self)
+                       for i, p in enumerate(self.params)]
+        self.last = None
+
+    def __len__(self):
+        return len(self.params)
+
+    def __getitem__(self, i):
+        return self._views[i]
+
+    def solve(self, Ds):
+        assert len(Ds) == len(self.params)
+        for D in Ds:
+            assert D.is_cuda and D.dtype.itemsize == 4 and D.stride(1) == 1
+        status, res = ircur_batch_solve(self._b, Ds, [D.stride(0) for D in Ds])
+        self.last = [Result(r.iters, bool(r.converged), r.flags, r.svd_steps, r.final_err, r.zeta0,
+                            r.zeta_next) for r in res]
+        for v, r in zip(self._views, self.last):
+            v.last = r
+        _check(status, "ircur_batch_solve")
+        return self.last
+
+    def close(self):
+        if self._b:
+            for v in self._views:
+                v._ctx = None
+            ircur_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sample_indices(seed, draw, axis, n, m):

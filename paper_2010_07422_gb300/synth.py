@@ -19,6 +19,11 @@ the supplement's setup):
                      [0, 1].
 * ``random_subset`` -- a sorted uniform m-subset of [0, n) from numpy's PCG64,
                      for handing explicit index sets to both sides.
+* ``planted_device`` -- the ``planted`` recipe drawn directly in device memory
+                     with torch's CUDA generator (FP32 throughout), for large
+                     timing workloads whose values no oracle needs; the
+                     batch recipe ``uneven_batch`` draws the shapes, ranks and
+                     outlier fractions of a set of independent problems.
 """
 
 from __future__ import annotations
@@ -149,3 +154,34 @@ def video_like(h, w, frames, seed, n_rects=(5, 20), noise_std=1e-3, fg_fraction=
     D += noise_std * rng.standard_normal(D.shape)
     np.clip(D, 0.0, 1.0, out=D)
     return Video(D=D.astype(np.float32), background=bg, fg_mask=mask)
+
+
+def planted_device(n1, n2, r, alpha, seed, outlier_scale=10.0, device="cuda"):
+    """The ``planted`` recipe on the device: L = W V^T (W, V ~ N(0,1), FP32),
+    round(alpha n1 n2) outliers on a uniform random support, values uniform in
+    [-s mean|L|, s mean|L|].  Returns the n1 x n2 FP32 tensor D = L + S."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    W = torch.randn(n1, r, generator=g, device=device, dtype=torch.float32)
+    V = torch.randn(n2, r, generator=g, device=device, dtype=torch.float32)
+    D = W @ V.T
+    half = outlier_scale * float(D.abs().mean())
+    k = int(round(alpha * n1 * n2))
+    pos = torch.randperm(n1 * n2, generator=g, device=device)[:k]
+    val = (torch.rand(k, generator=g, device=device, dtype=torch.float32) * 2.0 - 1.0) * half
+    D.view(-1).index_add_(0, pos, val)
+    return D
+
+
+def uneven_batch(count, seed, n_range=(500, 4000), r_range=(2, 10), alpha_range=(0.05, 0.3)):
+    """Shapes of a batch of independent problems: n1, n2 uniform integers in
+    n_range, r uniform in r_range (inclusive), alpha uniform in alpha_range."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n1, n2 = (int(x) for x in rng.integers(n_range[0], n_range[1] + 1, size=2))
+        out.append(dict(n1=n1, n2=n2, r=int(rng.integers(r_range[0], r_range[1] + 1)),
+                        alpha=float(rng.uniform(*alpha_range))))
+    return out
+

@@ -69,6 +69,17 @@ def test_status_strings_and_param_validation_without_gpu(lib):
     assert create(precision=1) == ir.IRCUR_ENOTSUP
     assert create(n1=0) == ir.IRCUR_EINVAL
     assert ctx.value is None
+    # batch argument checks (before any CUDA call)
+    good = ir.ircur_params(n1=100, n2=80, r=3, nI=0, nJ=0, zeta0=0.0, gamma=0.7, tol=1e-5, max_iter=10,
+                           resample=1, seed=0, precision=0, reserved=0)
+    bad = ir.ircur_params(n1=100, n2=80, r=3, nI=0, nJ=0, zeta0=0.0, gamma=1.5, tol=1e-5, max_iter=10,
+                          resample=1, seed=0, precision=0, reserved=0)
+    bh = ctypes.c_void_p()
+    assert lib.ircur_batch_create((ir.ircur_params * 1)(good), 0, None, ctypes.byref(bh)) == ir.IRCUR_EINVAL
+    assert lib.ircur_batch_create((ir.ircur_params * 2)(good, bad), 2, None, ctypes.byref(bh)) == ir.IRCUR_EINVAL
+    assert lib.ircur_batch_create(None, 1, None, ctypes.byref(bh)) == ir.IRCUR_EINVAL
+    assert bh.value is None
+    assert lib.ircur_batch_instance(None, 0) is None
     # sampler argument checks
     assert lib.ircur_sample_indices(0, 0, 0, 10, 11, None, None) == ir.IRCUR_EINVAL
     assert lib.ircur_sample_indices(0, 0, 2, 10, 5, ctypes.c_void_p(16), None) == ir.IRCUR_EINVAL
@@ -82,3 +93,6 @@ def test_fault_injection_alloc_returns_enomem(lib, monkeypatch):
                         resample=1, seed=0, precision=0, reserved=0)
     assert ir._lib().ircur_create(ctypes.byref(p), None, ctypes.byref(ctx)) == ir.IRCUR_ENOMEM
     assert ctx.value is None
+    bh = ctypes.c_void_p()
+    assert ir._lib().ircur_batch_create((ir.ircur_params * 2)(p, p), 2, None, ctypes.byref(bh)) == ir.IRCUR_ENOMEM
+    assert bh.value is None
