@@ -194,6 +194,36 @@ ircur_status ircur_get_trace(ircur_ctx* ctx, double* span_us, int32_t* iters);
 ircur_status ircur_solve_noalloc(const ircur_params* params, const float* D, int64_t ldD, float* A, float* B,
                                  ircur_result* out, void* stream);
 
+/* Differentiation of unrolled IRCUR-F.
+ * ircur_set_record(ctx, 1) makes the following ircur_solve calls record, for
+ * every iteration k, the factors of L_k and the core's factorisation (about
+ * 4 (max_iter + 1) (n1 + n2) R + 8 max_iter |I| R bytes, R = padded rank, plus
+ * the adjoint's scratch of about 4 (|I| n2 + |J| n1) bytes); a recording
+ * solve runs its loop from the host.  Only IRCUR-F (params.resample == 0):
+ * ENOTSUP otherwise.  enable == 0 releases the buffers.  Synchronises the
+ * stream. */
+ircur_status ircur_set_record(ircur_ctx* ctx, int32_t enable);
+
+/* Reverse mode of the map the last recording solve computed: Alg. 1 with the
+ * fixed index sets I, J for exactly its K = iters iterations from L_0 = 0,
+ * with the thresholds zeta_k = gamma^k zeta_0 held fixed, D -> (L, S) where
+ * L = L_K (ircur_reconstruct's L) and S = T_{zeta_K}(D - L) (its S).
+ * Given device cotangents dL, dS (n1 x n2 row-major with leading dimensions
+ * lddL, lddS; either may be null = zero), writes
+ *     dD = d<dL, L>/dD + d<dS, S>/dD
+ * into the device array dD (n1 x n2, lddD; every entry is written).  D must
+ * be the matrix of that solve (device, ldD).  The hard threshold contributes
+ * its almost-everywhere derivative (its keep mask) and the rank-r truncation
+ * the derivative of the truncated SVD, which exists when sigma_r > sigma_{r+1}
+ * for every core (the tail coupling is solved by conjugate gradients on the
+ * complements; IRCUR_ESVD_NOCONV when such a solve does not converge, i.e. the
+ * gap is too small).  zeta_0 = max|D| contributes nothing (its effect is
+ * through the masks only).  Returns ESTATE without a recorded solve, ENOTSUP
+ * if some core had numerical rank < r (IRCUR_FLAG_WRANK).  This adjoint is
+ * not in the paper.  Synchronises the stream. */
+ircur_status ircur_backward(ircur_ctx* ctx, const float* D, int64_t ldD, const float* dL, int64_t lddL,
+                            const float* dS, int64_t lddS, float* dD, int64_t lddD);
+
 /* Batched solves of independent problems.  The paper solves one problem at
  * a time (Alg. 1); a batch runs Alg. 1 on `count` unrelated problems at once
  * -- each with its own shape, rank, sample sizes, thresholds, tolerance,

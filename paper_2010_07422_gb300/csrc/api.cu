@@ -96,6 +96,17 @@ struct ircur_ctx {
   float* hL;
   float* hS;
   IterDesc desc;
+  // recording forward + adjoint workspace (ircur_set_record)
+  void* rec_ws;
+  float* recA;   // (max_iter + 1) x n1 x R   A_k
+  float* recB;   // (max_iter + 1) x R x n2   B_k
+  float* recY;   // max_iter x nI x R
+  float* recVs;  // max_iter x nJ x R
+  float* recT;   // max_iter x R x R
+  AdjStep adj;   // buffers of the reverse steps (per-step fields filled by ircur_backward)
+  float* adjE[2];
+  float* adjF[2];
+  int recorded;  // the last solve recorded its iterations
 };
 
 static void reset_graph(ircur_ctx* c) {
@@ -284,6 +295,7 @@ extern "C" void ircur_destroy(ircur_ctx* c) {
   if (c->hD) cudaFree(c->hD);
   if (c->hL) cudaFree(c->hL);
   if (c->hS) cudaFree(c->hS);
+  if (c->rec_ws) cudaFree(c->rec_ws);
   if (c->ws) cudaFree(c->ws);
   delete c;
 }
@@ -420,6 +432,35 @@ extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, c
   if (ps != IRCUR_OK) return ps;
   const IterDesc& d = c->desc;
   cudaStream_t s = c->stream;
+  c->recorded = 0;
+  if (c->rec_ws) {
+    // Recording forward (for ircur_backward): every iteration's factors and
+    // core factorisation are copied out after it, so the loop is host-driven.
+    const int R = c->Rpad;
+    const size_t nA = (size_t)p.n1 * R, nB = (size_t)R * p.n2;
+    IRCUR_CK(cudaMemsetAsync(c->recA, 0, nA * 4, s));
+    IRCUR_CK(cudaMemsetAsync(c->recB, 0, nB * 4, s));
+    for (int it = 0; it < p.max_iter; ++it) {
+      IRCUR_CK(launch_iteration(d, R, s));
+      const int nx = (it + 1) & 1;
+      IRCUR_CK(cudaMemcpyAsync(c->recA + (size_t)(it + 1) * nA, c->A[nx], nA * 4, cudaMemcpyDeviceToDevice, s));
+      IRCUR_CK(cudaMemcpyAsync(c->recB + (size_t)(it + 1) * nB, c->B[nx], nB * 4, cudaMemcpyDeviceToDevice, s));
+      IRCUR_CK(cudaMemcpyAsync(c->recY + (size_t)it * p.nI * R, c->W, (size_t)p.nI * R * 4,
+                               cudaMemcpyDeviceToDevice, s));
+      IRCUR_CK(cudaMemcpyAsync(c->recVs + (size_t)it * p.nJ * R, c->Vs, (size_t)p.nJ * R * 4,
+                               cudaMemcpyDeviceToDevice, s));
+      IRCUR_CK(cudaMemcpyAsync(c->recT + (size_t)it * R * R, c->Tm, (size_t)R * R * 4, cudaMemcpyDeviceToDevice, s));
+      if ((it & 3) == 3) {
+        ircur_status rs = read_state(c);
+        if (rs != IRCUR_OK) return rs;
+        if (c->host_state.done) break;
+      }
+    }
+    ircur_status rs = read_state(c);
+    if (rs != IRCUR_OK) return rs;
+    c->recorded = 1;
+    return solve_epilogue(c, out);
+  }
   if (use_graph()) {
     if (!c->exec || c->graph_D != D || c->graph_ldD != ldD || c->graph_sample_ahead != d.sampleAhead ||
         c->graph_trace != d.trace) {
@@ -442,6 +483,161 @@ extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, c
   ircur_status rs = read_state(c);
   if (rs != IRCUR_OK) return rs;
   return solve_epilogue(c, out);
+}
+
+extern "C" ircur_status ircur_set_record(ircur_ctx* c, int32_t enable) {
+  if (!c) return IRCUR_EINVAL;
+  IRCUR_CK(cudaStreamSynchronize(c->stream));
+  if (c->rec_ws) {
+    cudaFree(c->rec_ws);
+    c->rec_ws = nullptr;
+  }
+  c->recorded = 0;
+  if (!enable) return IRCUR_OK;
+  const ircur_params& p = c->p;
+  if (p.resample) return IRCUR_ENOTSUP;
+  const int R = c->Rpad;
+  const int64_t n1 = p.n1, n2 = p.n2;
+  const int nI = p.nI, nJ = p.nJ, K = p.max_iter;
+  if (adj_cg_smem_bytes(nI, nJ, R) > 227 * 1024) return IRCUR_ENOTSUP;
+  const int nRowTiles = (int)((n2 + 31) / 32), nColTiles = (int)((n1 + 31) / 32);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  };
+  const size_t oA = take((size_t)(K + 1) * n1 * R * 4), oB = take((size_t)(K + 1) * R * n2 * 4);
+  const size_t oY = take((size_t)K * nI * R * 4), oVs = take((size_t)K * nJ * R * 4), oT = take((size_t)K * R * R * 4);
+  const size_t oE0 = take((size_t)n1 * R * 4), oE1 = take((size_t)n1 * R * 4);
+  const size_t oF0 = take((size_t)R * n2 * 4), oF1 = take((size_t)R * n2 * 4);
+  const size_t oDR = take((size_t)nI * n2 * 4), oDC = take((size_t)nJ * n1 * 4);
+  const size_t oPR = take((size_t)nRowTiles * nI * 2 * R * 4), oPC = take((size_t)nColTiles * nJ * 2 * R * 4);
+  const size_t oPhi = take((size_t)nI * R * 4), oPsi = take((size_t)nJ * R * 4);
+  const size_t oE1v = take((size_t)nI * R * 4), oF2v = take((size_t)nJ * R * 4);
+  const size_t oU = take((size_t)nI * nJ * 4);
+  const size_t oXc = take((size_t)nI * R * 4), oYc = take((size_t)nJ * R * 4);
+  const size_t oWr = take((size_t)nI * R * 4), oVr = take((size_t)nJ * R * 4);
+  const size_t oSig = take((size_t)R * 4), oP = take((size_t)R * R * 4), oG = take((size_t)R * R * 4);
+  const size_t oSt = take(16);
+  cudaError_t e = cudaMalloc(&c->rec_ws, off);
+  if (e != cudaSuccess) {
+    set_error("cudaMalloc(record workspace)", e);
+    cudaGetLastError();
+    c->rec_ws = nullptr;
+    return IRCUR_ENOMEM;
+  }
+  e = cudaMemsetAsync(c->rec_ws, 0, off, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    set_error("cudaMemset(record workspace)", e);
+    cudaFree(c->rec_ws);
+    c->rec_ws = nullptr;
+    return IRCUR_ECUDA;
+  }
+  char* b = static_cast<char*>(c->rec_ws);
+  auto fp = [&](size_t o) { return reinterpret_cast<float*>(b + o); };
+  c->recA = fp(oA);
+  c->recB = fp(oB);
+  c->recY = fp(oY);
+  c->recVs = fp(oVs);
+  c->recT = fp(oT);
+  c->adjE[0] = fp(oE0);
+  c->adjE[1] = fp(oE1);
+  c->adjF[0] = fp(oF0);
+  c->adjF[1] = fp(oF1);
+  AdjStep& a = c->adj;
+  memset(&a, 0, sizeof(a));
+  a.n1 = n1;
+  a.n2 = n2;
+  a.r = p.r;
+  a.nI = nI;
+  a.nJ = nJ;
+  a.I = c->I_all;
+  a.J = c->J_all;
+  a.Prow = c->Prow;
+  a.ldPr = c->ldPr;
+  a.PcolT = c->PcolT;
+  a.ldPc = c->ldPc;
+  a.dDR = fp(oDR);
+  a.dDCt = fp(oDC);
+  a.partR = fp(oPR);
+  a.partC = fp(oPC);
+  a.nRowTiles = nRowTiles;
+  a.nColTiles = nColTiles;
+  a.PhiY = fp(oPhi);
+  a.PsiY = fp(oPsi);
+  a.e1 = fp(oE1v);
+  a.f2 = fp(oF2v);
+  a.Ucore = fp(oU);
+  a.Xc = fp(oXc);
+  a.Yc = fp(oYc);
+  a.Wr = fp(oWr);
+  a.Vr = fp(oVr);
+  a.sig = fp(oSig);
+  a.Pm = fp(oP);
+  a.G11 = fp(oG);
+  a.status = reinterpret_cast<int*>(b + oSt);
+  a.cgMaxIter = 200;
+  return IRCUR_OK;
+}
+
+extern "C" ircur_status ircur_backward(ircur_ctx* c, const float* D, int64_t ldD, const float* dL, int64_t lddL,
+                                       const float* dS, int64_t lddS, float* dD, int64_t lddD) {
+  if (!c || !D || !dD) return IRCUR_EINVAL;
+  if (!c->rec_ws || !c->recorded || !c->solved) return IRCUR_ESTATE;
+  const ircur_params& p = c->p;
+  if (ldD < p.n2 || lddD < p.n2 || (dL && lddL < p.n2) || (dS && lddS < p.n2)) return IRCUR_EINVAL;
+  const State& h = c->host_state;
+  const int K = h.k;
+  if (K < 1) return IRCUR_ESTATE;
+  if (h.flags & IRCUR_FLAG_WRANK) return IRCUR_ENOTSUP;  // a core below rank r: no derivative of H_r^+
+  const int R = c->Rpad;
+  cudaStream_t s = c->stream;
+  AdjStep a = c->adj;
+  IRCUR_CK(cudaMemsetAsync(a.dDR, 0, (size_t)p.nI * p.n2 * 4, s));
+  IRCUR_CK(cudaMemsetAsync(a.dDCt, 0, (size_t)p.nJ * p.n1 * 4, s));
+  IRCUR_CK(cudaMemsetAsync(a.Xc, 0, (size_t)p.nI * R * 4, s));
+  IRCUR_CK(cudaMemsetAsync(a.Yc, 0, (size_t)p.nJ * R * 4, s));
+  IRCUR_CK(cudaMemsetAsync(a.status, 0, 4, s));
+  const size_t nA = (size_t)p.n1 * R, nB = (size_t)R * p.n2;
+  // zeta_k exactly as the device formed it: zeta_0 times gamma, k times, in FP64
+  double* zk = new (std::nothrow) double[K];
+  if (!zk) return IRCUR_ENOMEM;
+  {
+    double z = h.zeta0;
+    for (int k = 0; k < K; ++k) {
+      zk[k] = z;
+      z = z * p.gamma;
+    }
+  }
+  int cur = 0;
+  cudaError_t e = launch_adj_dense(p.n1, p.n2, c->recA + (size_t)K * nA, c->recB + (size_t)K * nB, D, ldD, dL, lddL,
+                                   dS, lddS, dD, lddD, (float)h.zeta, c->adjE[cur], c->adjF[cur], R, s);
+  for (int k = K - 1; k >= 0 && e == cudaSuccess; --k) {
+    a.Ak = c->recA + (size_t)k * nA;
+    a.Bk = c->recB + (size_t)k * nB;
+    a.Y = c->recY + (size_t)k * p.nI * R;
+    a.Vs = c->recVs + (size_t)k * p.nJ * R;
+    a.Tm = c->recT + (size_t)k * R * R;
+    a.zeta = (float)zk[k];
+    a.E = c->adjE[cur];
+    a.F = c->adjF[cur];
+    a.Enew = c->adjE[cur ^ 1];
+    a.Fnew = c->adjF[cur ^ 1];
+    e = launch_adj_step(a, R, k > 0, s);
+    cur ^= 1;
+  }
+  delete[] zk;
+  if (e == cudaSuccess) e = launch_adj_scatter(a, dD, lddD, s);
+  if (e != cudaSuccess) {
+    set_error("ircur_backward", e);
+    return IRCUR_ECUDA;
+  }
+  int status = 0;
+  IRCUR_CK(cudaMemcpyAsync(&status, a.status, 4, cudaMemcpyDeviceToHost, s));
+  IRCUR_CK(cudaStreamSynchronize(s));
+  return status ? (ircur_status)status : IRCUR_OK;
 }
 
 extern "C" ircur_status ircur_get_factors(ircur_ctx* c, float* A, float* B) {

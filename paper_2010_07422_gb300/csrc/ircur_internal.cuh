@@ -109,6 +109,51 @@ struct BatchLaunch {
   int* any_active;         // device flag written by the loop-control kernel
 };
 
+// One reverse step k of the adjoint of unrolled IRCUR-F (k_adjoint.cu).
+// The forward recorded, for every iteration k, the factors of L_k
+// (A_k: n1 x R, B_k: R x n2) and the core factorisation (Y, X T^{-1}, T).
+// Cotangents of L_{k+1} are carried as their projections in the forward's
+// gauge, E = Gbar B_{k+1}^T (n1 x R) and F = A_{k+1}^T Gbar (R x n2).
+struct AdjStep {
+  int64_t n1, n2;
+  int r, nI, nJ;
+  const int* I;         // nI, sorted distinct
+  const int* J;         // nJ
+  const float* Prow;    // D(I,:), nI x ldPr
+  int64_t ldPr;
+  const float* PcolT;   // D(:,J)^T, nJ x ldPc
+  int64_t ldPc;
+  const float* Ak;      // A_k, n1 x R
+  const float* Bk;      // B_k, R x n2
+  const float* Y;       // nI x R
+  const float* Vs;      // nJ x R, X T^{-1}
+  const float* Tm;      // R x R, T(i,p) at i * R + p
+  float zeta;           // zeta_k as the forward compared it (FP32)
+  float* Wr;            // nI x R  exact left singular vectors W_r = Y P
+  float* Vr;            // nJ x R  exact right singular vectors V_r = X Q = Vs P Sigma
+  float* sig;           // R
+  float* Pm;            // R x R, P(i,p) at i * R + p
+  const float* E;       // n1 x R   (of L_{k+1})
+  const float* F;       // R x n2
+  float* Enew;          // n1 x R   (of L_k)
+  float* Fnew;          // R x n2
+  float* dDR;           // nI x n2, accumulated dD(I,:)
+  float* dDCt;          // nJ x n1, accumulated dD(:,J)^T
+  float* partR;         // nRowTiles x nI x 2R
+  float* partC;         // nColTiles x nJ x 2R
+  int nRowTiles, nColTiles;
+  float* PhiY;          // nI x R   R_{k+1} F^T
+  float* PsiY;          // nJ x R   C_{k+1}^T E
+  float* e1;            // nI x R   (row-panel part of Enew(I,:))
+  float* f2;            // nJ x R   (column-panel part of Fnew(:,J)^T)
+  float* Ucore;         // nI x nJ scratch: the core, then its masked cotangent
+  float* Xc;            // nI x R   shifted-system solutions (left complement)
+  float* Yc;            // nJ x R   (right complement)
+  float* G11;           // R x R
+  int* status;          // set on a failed solve (IRCUR_ESVD_NOCONV)
+  int cgMaxIter;
+};
+
 // Launch wrappers (return cudaGetLastError()).
 cudaError_t launch_sample(uint64_t seed, int draw0, int draws, int64_t n1, int64_t n2, int nI, int nJ,
                           int* I_all, int* J_all, int only_axis, cudaStream_t s);
@@ -131,6 +176,13 @@ size_t svd_smem_bytes(int nI, int nJ, int Rpad, bool* core_in_smem);
 cudaError_t launch_batch_iteration(const BatchLaunch& b, int Rpad, cudaStream_t s);
 cudaError_t launch_svd_batch(const BatchLaunch& b, int Rpad, cudaStream_t s);
 cudaError_t launch_sigma(const float* Tm, int r, int Rpad, float* sigma, cudaStream_t s);
+// Adjoint (k_adjoint.cu)
+cudaError_t launch_adj_dense(int64_t n1, int64_t n2, const float* A, const float* B, const float* D, int64_t ldD,
+                             const float* dL, int64_t lddL, const float* dS, int64_t lddS, float* dD,
+                             int64_t lddD, float zetaT, float* E, float* F, int Rpad, cudaStream_t s);
+cudaError_t launch_adj_step(const AdjStep& a, int Rpad, bool need_next, cudaStream_t s);
+size_t adj_cg_smem_bytes(int nI, int nJ, int Rpad);
+cudaError_t launch_adj_scatter(const AdjStep& a, float* dD, int64_t lddD, cudaStream_t s);
 size_t pass_smem_bytes(int nI, int nJ, int Rpad);
 int pad_rank(int r);
 

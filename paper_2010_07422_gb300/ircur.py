@@ -25,7 +25,7 @@ EXPORTED = (
     "ircur_get_errors", "ircur_reconstruct", "ircur_solve_host", "ircur_sample_indices",
     "ircur_status_string", "ircur_last_error_string", "ircur_solve_noalloc", "ircur_set_trace",
     "ircur_get_trace", "ircur_get_cur", "ircur_batch_create", "ircur_batch_destroy", "ircur_batch_solve",
-    "ircur_batch_instance",
+    "ircur_batch_instance", "ircur_set_record", "ircur_backward",
 )
 
 
@@ -82,6 +82,8 @@ def _lib():
         lib.ircur_batch_solve.argtypes = [P, C.POINTER(P), C.POINTER(I64), C.POINTER(ircur_result)]
         lib.ircur_batch_instance.argtypes = [P, I32]
         lib.ircur_batch_instance.restype = P
+        lib.ircur_set_record.argtypes = [P, I32]
+        lib.ircur_backward.argtypes = [P, P, I64, P, I64, P, I64, P, I64]
         lib.ircur_status_string.argtypes = [C.c_int]
         lib.ircur_status_string.restype = C.c_char_p
         lib.ircur_last_error_string.argtypes = []
@@ -190,6 +192,15 @@ def ircur_solve_noalloc(params: ircur_params, D, ldD, A, B, stream=None):
     _check(_lib().ircur_solve_noalloc(C.byref(params), _ptr(D), ldD, _ptr(A), _ptr(B), C.byref(res), stream),
            "ircur_solve_noalloc")
     return res
+
+
+def ircur_set_record(ctx, enable):
+    _check(_lib().ircur_set_record(ctx, int(bool(enable))), "ircur_set_record")
+
+
+def ircur_backward(ctx, D, ldD, dL, lddL, dS, lddS, dD, lddD):
+    _check(_lib().ircur_backward(ctx, _ptr(D), ldD, _ptr(dL), lddL, _ptr(dS), lddS, _ptr(dD), lddD),
+           "ircur_backward")
 
 
 def ircur_batch_create(params_list, stream=None):
@@ -308,6 +319,21 @@ class IRCUR:
     def errors(self):
         return ircur_get_errors(self._ctx, self.p.max_iter)
 
+    def record(self, enable=True):
+        """Make the following solves record their iterations for backward (IRCUR-F)."""
+        ircur_set_record(self._ctx, enable)
+
+    def backward(self, D, dL=None, dS=None, dD=None):
+        """dD = d<dL, L>/dD + d<dS, S>/dD for the last recorded solve (see include/ircur.h)."""
+        import torch
+        if dD is None:
+            dD = torch.empty((self.p.n1, self.p.n2), dtype=torch.float32, device=D.device)
+        for t in (dL, dS):
+            assert t is None or (t.is_cuda and t.dtype == torch.float32 and t.stride(1) == 1)
+        ircur_backward(self._ctx, D, D.stride(0), dL, dL.stride(0) if dL is not None else 0,
+                       dS, dS.stride(0) if dS is not None else 0, dD, dD.stride(0))
+        return dD
+
     def reconstruct(self, D=None, with_sparse=True, L=None, S=None):
         import torch
         n1, n2 = self.p.n1, self.p.n2
@@ -320,6 +346,46 @@ class IRCUR:
         ircur_reconstruct(self._ctx, D, D.stride(0) if D is not None else 0, L, L.stride(0),
                           S, S.stride(0) if S is not None else 0)
         return L, S
+
+
+def _make_function():
+    import torch
+
+    class _Unrolled(torch.autograd.Function):
+        """D -> (L, S) of a recording IRCUR-F solve; backward through ircur_backward."""
+
+        @staticmethod
+        def forward(ctx, D, solver):
+            solver.solve(D)
+            L, S = solver.reconstruct(D)
+            ctx.solver = solver
+            ctx.save_for_backward(D)
+            return L, S
+
+        @staticmethod
+        def backward(ctx, dL, dS):
+            (D,) = ctx.saved_tensors
+            dL = dL.contiguous() if dL is not None else None
+            dS = dS.contiguous() if dS is not None else None
+            return ctx.solver.backward(D, dL, dS), None
+
+    return _Unrolled
+
+
+_FUNCTION = None
+
+
+def ircur_unrolled(D, solver):
+    """Differentiable (L, S) = IRCUR-F(D) for a solver made with resample=False;
+    the solver records its iterations and the backward pass runs the
+    hand-written adjoint.  Gradients flow to D only."""
+    global _FUNCTION
+    if _FUNCTION is None:
+        _FUNCTION = _make_function()
+    if not getattr(solver, "_recording", False):
+        solver.record(True)
+        solver._recording = True
+    return _FUNCTION.apply(D, solver)
 
 
 class IRCURBatch:

@@ -80,6 +80,9 @@ def test_status_strings_and_param_validation_without_gpu(lib):
     assert lib.ircur_batch_create(None, 1, None, ctypes.byref(bh)) == ir.IRCUR_EINVAL
     assert bh.value is None
     assert lib.ircur_batch_instance(None, 0) is None
+    # adjoint argument checks
+    assert lib.ircur_set_record(None, 1) == ir.IRCUR_EINVAL
+    assert lib.ircur_backward(None, None, 0, None, 0, None, 0, None, 0) == ir.IRCUR_EINVAL
     # sampler argument checks
     assert lib.ircur_sample_indices(0, 0, 0, 10, 11, None, None) == ir.IRCUR_EINVAL
     assert lib.ircur_sample_indices(0, 0, 2, 10, 5, ctypes.c_void_p(16), None) == ir.IRCUR_EINVAL

@@ -1,0 +1,133 @@
+"""Adjoint of unrolled IRCUR-F (ircur_set_record / ircur_backward) against the
+FP64 oracle gradient (oracle/ircur_adjoint.py, itself pinned by central finite
+differences in test_adjoint_oracle.py).
+
+Bar: relative Frobenius error of dD <= 1e-5.  The GPU path is FP32 with the
+same index sets and the same threshold decisions as the oracle (no entry sits
+within FP32 rounding of a threshold on these seeded inputs: the forward parity
+tests check the masks); the error budget is FP32 rounding carried through K
+iterations of rank-r products and the shifted conjugate-gradient solves
+(stopped at 1e-6 relative residual), measured at 2e-7 .. 8e-7.
+"""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from oracle import ircur_adjoint as adj  # noqa: E402
+from paper_2010_07422_gb300 import ircur as ir  # noqa: E402
+from paper_2010_07422_gb300 import synth  # noqa: E402
+
+TOL_GRAD = 1e-5
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def setup(n1, n2, r, T, alpha, seed, **kw):
+    p = synth.planted(n1, n2, r, alpha, seed=seed)
+    D = torch.from_numpy(p.D).cuda()
+    s = ir.IRCUR(n1, n2, r, tol=1e-12, max_iter=T, resample=False, seed=seed, **kw)
+    s.record(True)
+    res = s.solve(D)
+    I = oracle.sample_indices(seed, 0, 0, n1, s.nI)
+    J = oracle.sample_indices(seed, 0, 1, n2, s.nJ)
+    return p, D, s, res, I, J
+
+
+@pytest.mark.parametrize("n1,n2,r,T,alpha,seed,which", [
+    (300, 260, 3, 6, 0.1, 1, "both"),
+    (300, 260, 3, 6, 0.1, 1, "L"),
+    (300, 260, 3, 6, 0.1, 1, "S"),
+    (517, 333, 7, 10, 0.1, 2, "both"),
+    (450, 470, 11, 8, 0.05, 3, "both"),   # padded rank 12
+    (1024, 1024, 10, 15, 0.1, 4, "both"),  # the unrolled-training shape at n = 1024
+    (200, 640, 1, 4, 0.2, 5, "both"),
+])
+def test_backward_matches_oracle_gradient(n1, n2, r, T, alpha, seed, which):
+    p, D, s, res, I, J = setup(n1, n2, r, T, alpha, seed)
+    assert res.iters == T and res.flags == 0
+    rng = np.random.default_rng(seed)
+    dL = rng.standard_normal((n1, n2)).astype(np.float32) if which in ("both", "L") else None
+    dS = rng.standard_normal((n1, n2)).astype(np.float32) if which in ("both", "S") else None
+    g = s.backward(D, None if dL is None else torch.from_numpy(dL).cuda(),
+                   None if dS is None else torch.from_numpy(dS).cuda())
+    G = adj.unrolled_vjp(p.D.astype(np.float64), I, J, r, res.zeta0, 0.7, T, dL, dS)
+    gn = g.double().cpu().numpy()
+    assert rel(gn, G) <= TOL_GRAD, rel(gn, G)
+    on = np.zeros((n1, n2), bool)
+    on[I, :] = True
+    on[:, J] = True
+    # outside rows I and columns J only the S output contributes, exactly mask(S) dS
+    assert np.array_equal(gn[~on], G[~on])
+    s.close()
+
+
+def test_backward_at_training_size_properties():
+    """n = 4096, r = 10, T = 15, |I| = |J| = ceil(40 ln 4096) = 333: the gradient of
+    <dL, L> is supported on rows I and columns J, is finite, and is linear in dL."""
+    n, r, T = 4096, 10, 15
+    D = synth.planted_device(n, n, r, 0.1, seed=11)
+    s = ir.IRCUR(n, n, r, tol=1e-12, max_iter=T, resample=False, seed=11)
+    s.record(True)
+    res = s.solve(D)
+    assert res.iters == T and res.flags == 0
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    dL = torch.randn(n, n, device="cuda", generator=g)
+    g1 = s.backward(D, dL, None)
+    g2 = s.backward(D, 2.0 * dL, None)
+    I, J, _ = s.indices()
+    on = torch.zeros(n, n, dtype=torch.bool, device="cuda")
+    on[I.long(), :] = True
+    on[:, J.long()] = True
+    assert torch.isfinite(g1).all()
+    assert float(g1[~on].abs().max()) == 0.0
+    assert float(g1[on].abs().max()) > 0.0
+    assert float((g2 - 2.0 * g1).abs().max()) <= 1e-5 * float(g1.abs().max())
+    s.close()
+
+
+def test_autograd_function_matches_direct_backward():
+    n1, n2, r = 400, 380, 4
+    p = synth.planted(n1, n2, r, 0.1, seed=21)
+    Lt = torch.from_numpy(p.L_true()).float().cuda()
+    D = torch.from_numpy(p.D).cuda().requires_grad_(True)
+    s = ir.IRCUR(n1, n2, r, tol=1e-12, max_iter=8, resample=False, seed=21)
+    L, S = ir.ircur_unrolled(D, s)
+    lam = 0.1
+    loss = ((L - Lt) ** 2).sum() + lam * S.abs().sum()
+    loss.backward()
+    dL = (2.0 * (L - Lt)).detach().contiguous()
+    dS = (lam * torch.sign(S)).detach().contiguous()
+    direct = s.backward(D.detach(), dL, dS)
+    assert torch.allclose(D.grad, direct, rtol=1e-5, atol=1e-6 * float(direct.abs().max()))
+    s.close()
+
+
+def test_backward_errors():
+    n1, n2, r = 200, 180, 2
+    p = synth.planted(n1, n2, r, 0.1, seed=31)
+    D = torch.from_numpy(p.D).cuda()
+    s = ir.IRCUR(n1, n2, r, tol=1e-12, max_iter=3, resample=False, seed=31)
+    s.solve(D)
+    with pytest.raises(ir.IrcurError) as e:  # no recorded solve
+        s.backward(D, torch.ones_like(D))
+    assert e.value.status == ir.IRCUR_ESTATE
+    s.record(True)
+    with pytest.raises(ir.IrcurError) as e:  # recording on, no solve since
+        s.backward(D, torch.ones_like(D))
+    assert e.value.status == ir.IRCUR_ESTATE
+    s.solve(D)
+    s.backward(D, torch.ones_like(D))
+    s.close()
+    sr = ir.IRCUR(n1, n2, r, resample=True)
+    with pytest.raises(ir.IrcurError) as e:  # IRCUR-R is not differentiated
+        sr.record(True)
+    assert e.value.status == ir.IRCUR_ENOTSUP
+    sr.close()
