@@ -49,6 +49,21 @@ typedef enum {
 /* Largest rank r this build supports. */
 #define IRCUR_MAX_RANK 16
 
+/* ircur_params.precision.
+ * FP32: every panel entry, product and threshold decision in FP32 (norms and
+ *   the stopping value in FP64).
+ * BF16_PANELS (IRCUR-F only): the compact panels D(I,:) and D(:,J) are stored
+ *   in BF16 (half their bytes); each iteration's threshold decision
+ *   |D - L_k| > zeta is the FP32 one (an entry within BF16 rounding of zeta,
+ *   |(|d_bf16 - l| - zeta)| <= 2^-8 |d_bf16|, is read again from the FP32 D),
+ *   and every product is FP32.  The kept entries of D enter C and R rounded
+ *   to BF16 (relative error <= 2^-9), so L carries an error of that order and
+ *   e_k has a floor near 2^-9: pass tol >= 1e-3 or a fixed iteration count.
+ *   ircur_get_cur reports C and R from the FP32 D.  Not available to
+ *   batches, recording solves or ircur_solve_noalloc (ENOTSUP / EINVAL). */
+#define IRCUR_PRECISION_FP32 0
+#define IRCUR_PRECISION_BF16_PANELS 1
+
 /* Largest number of instances of one ircur_batch. */
 #define IRCUR_MAX_BATCH 4096
 
@@ -63,7 +78,7 @@ typedef struct {
   int32_t max_iter;  /* iteration cap, >= 1 (the paper loops until e_k <= tol) */
   int32_t resample;  /* 0 = IRCUR-F (fixed I,J), 1 = IRCUR-R (fresh I,J each iteration), Sec. 3.4 */
   uint64_t seed;     /* index-stream seed (used when the caller passes no index sets) */
-  int32_t precision; /* 0 = FP32 (the only value built) */
+  int32_t precision; /* IRCUR_PRECISION_*: 0 = FP32; 1 = BF16 panels (IRCUR-F only) */
   int32_t reserved;  /* must be 0 */
 } ircur_params;
 
@@ -83,7 +98,8 @@ typedef struct ircur_ctx ircur_ctx;
  * allocate its device workspace (about 4*(n1 + n2)*(2r + |J| + |I|) bytes
  * plus max_iter*(|I|+|J|)*4 bytes of index sets).  stream: a cudaStream_t
  * (NULL = legacy default stream).  Returns EINVAL for out-of-range
- * parameters, ENOTSUP for r > IRCUR_MAX_RANK or precision != 0, ENOMEM if
+ * parameters, ENOTSUP for r > IRCUR_MAX_RANK, an unknown precision or BF16 panels
+ * with resample != 0, ENOMEM if
  * the workspace cannot be allocated.  *out is NULL on failure. */
 ircur_status ircur_create(const ircur_params* params, void* stream, ircur_ctx** out);
 

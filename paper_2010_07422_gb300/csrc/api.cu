@@ -127,7 +127,9 @@ static ircur_status validate_params(const ircur_params* p, ircur_params* out) {
   if (q.nJ == 0) q.nJ = default_sample_size(q.r, q.n2);
   if (q.nI < q.r || q.nJ < q.r || q.nI > q.n1 || q.nJ > q.n2) return IRCUR_EINVAL;
   if (q.nI > 512 || q.nJ > 512) return IRCUR_ENOTSUP;
-  if (pass_smem_bytes(q.nI, q.nJ, pad_rank(q.r)) > 227 * 1024) return IRCUR_ENOTSUP;
+  if (q.precision != IRCUR_PRECISION_FP32 && q.precision != IRCUR_PRECISION_BF16_PANELS) return IRCUR_ENOTSUP;
+  if (q.precision == IRCUR_PRECISION_BF16_PANELS && q.resample != 0) return IRCUR_ENOTSUP;
+  if (pass_smem_bytes(q.nI, q.nJ, pad_rank(q.r), nullptr, q.precision != 0) > 227 * 1024) return IRCUR_ENOTSUP;
   {
     bool in_smem = false;
     if (svd_smem_bytes(q.nI, q.nJ, pad_rank(q.r), &in_smem) > 227 * 1024) return IRCUR_ENOTSUP;
@@ -136,7 +138,6 @@ static ircur_status validate_params(const ircur_params* p, ircur_params* out) {
   if (!(q.tol > 0.0)) return IRCUR_EINVAL;
   if (q.max_iter < 1) return IRCUR_EINVAL;
   if (q.resample != 0 && q.resample != 1) return IRCUR_EINVAL;
-  if (q.precision != 0) return IRCUR_ENOTSUP;
   if (q.reserved != 0) return IRCUR_EINVAL;
   if (!(q.zeta0 == q.zeta0)) return IRCUR_EINVAL;
   *out = q;
@@ -159,8 +160,11 @@ static ircur_status create_impl(const ircur_params* params, void* stream, int mi
   c->draws = p.resample ? p.max_iter : 1;
   const int R = c->Rpad;
   const int64_t n1 = p.n1, n2 = p.n2;
-  c->ldPr = (n2 + 3) & ~3ll;
-  c->ldPc = (n1 + 3) & ~3ll;
+  const bool bf16 = p.precision == IRCUR_PRECISION_BF16_PANELS;
+  // compact panels: FP32 rows padded to 16 bytes, or BF16 rows padded to 16 bytes
+  c->ldPr = bf16 ? (n2 + 7) & ~7ll : (n2 + 3) & ~3ll;
+  c->ldPc = bf16 ? (n1 + 7) & ~7ll : (n1 + 3) & ~3ll;
+  const size_t pel = bf16 ? 2 : 4;
   c->ldDT = (n1 + 3) & ~3ll;
 
   // tile configuration of the pass kernel
@@ -178,8 +182,8 @@ static ircur_status create_impl(const ircur_params* params, void* stream, int mi
   };
   const size_t oI = take((size_t)c->draws * p.nI * 4);
   const size_t oJ = take((size_t)c->draws * p.nJ * 4);
-  const size_t oPr = p.resample ? 0 : take((size_t)p.nI * c->ldPr * 4);
-  const size_t oPc = p.resample ? 0 : take((size_t)p.nJ * c->ldPc * 4);
+  const size_t oPr = p.resample ? 0 : take((size_t)p.nI * c->ldPr * pel);
+  const size_t oPc = p.resample ? 0 : take((size_t)p.nJ * c->ldPc * pel);
   const size_t oDT = p.resample ? take((size_t)n2 * c->ldDT * 4) : 0;
   const size_t oA0 = take((size_t)n1 * R * 4), oA1 = take((size_t)n1 * R * 4);
   const size_t oB0 = take((size_t)R * n2 * 4), oB1 = take((size_t)R * n2 * 4);
@@ -212,8 +216,13 @@ static ircur_status create_impl(const ircur_params* params, void* stream, int mi
   char* base = static_cast<char*>(c->ws);
   c->I_all = reinterpret_cast<int*>(base + oI);
   c->J_all = reinterpret_cast<int*>(base + oJ);
-  c->Prow = p.resample ? nullptr : reinterpret_cast<float*>(base + oPr);
-  c->PcolT = p.resample ? nullptr : reinterpret_cast<float*>(base + oPc);
+  c->Prow = (p.resample || bf16) ? nullptr : reinterpret_cast<float*>(base + oPr);
+  c->PcolT = (p.resample || bf16) ? nullptr : reinterpret_cast<float*>(base + oPc);
+  if (bf16) {
+    d.bf16 = 1;
+    d.rowSrcH = reinterpret_cast<const uint16_t*>(base + oPr);
+    d.colSrcH = reinterpret_cast<const uint16_t*>(base + oPc);
+  }
   c->DT = p.resample ? reinterpret_cast<float*>(base + oDT) : nullptr;
   c->A[0] = reinterpret_cast<float*>(base + oA0);
   c->A[1] = reinterpret_cast<float*>(base + oA1);
@@ -495,7 +504,7 @@ extern "C" ircur_status ircur_set_record(ircur_ctx* c, int32_t enable) {
   c->recorded = 0;
   if (!enable) return IRCUR_OK;
   const ircur_params& p = c->p;
-  if (p.resample) return IRCUR_ENOTSUP;
+  if (p.resample || p.precision != IRCUR_PRECISION_FP32) return IRCUR_ENOTSUP;
   const int R = c->Rpad;
   const int64_t n1 = p.n1, n2 = p.n2;
   const int nI = p.nI, nJ = p.nJ, K = p.max_iter;
@@ -865,6 +874,7 @@ extern "C" ircur_status ircur_batch_create(const ircur_params* params, int32_t c
     ircur_params q;
     ircur_status vs = validate_params(&params[i], &q);
     if (vs != IRCUR_OK) return vs;
+    if (q.precision != IRCUR_PRECISION_FP32) return IRCUR_ENOTSUP;
     const int rp = pad_rank(q.r);
     if (rp > Rpad) Rpad = rp;
   }
@@ -907,6 +917,8 @@ extern "C" ircur_status ircur_batch_create(const ircur_params* params, int32_t c
       return IRCUR_ENOTSUP;
     }
     if (ps > bl.pass_smem) bl.pass_smem = ps;
+    if (p.nI > bl.pass_mmax) bl.pass_mmax = p.nI;
+    if (p.nJ > bl.pass_mmax) bl.pass_mmax = p.nJ;
     const int g = in_smem ? 0 : 1;
     grp[i] = (unsigned char)g;
     if (ss > bl.svd_smem[g]) bl.svd_smem[g] = ss;
@@ -925,6 +937,7 @@ extern "C" ircur_status ircur_batch_create(const ircur_params* params, int32_t c
     int a = 0, z = n0;
     for (int i = 0; i < count; ++i) lists[grp[i] ? z++ : a++] = i;
   }
+  bl.pass_smem = pass_smem_bytes(bl.pass_mmax, bl.pass_mmax, Rpad, &bl.pass_nbuf);
   // device workspace: descriptors | tile prefix sums | SVD lists | loop flag
   const size_t oDesc = 0;
   const size_t oTiles = (oDesc + (size_t)count * sizeof(IterDesc) + 255) & ~(size_t)255;

@@ -1,6 +1,7 @@
 // Device helpers shared by the kernels of libircur.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -25,6 +26,24 @@ __device__ __forceinline__ float lowrank_entry(const float* a, const float* b) {
 #pragma unroll
   for (int t = 0; t < R; ++t) acc = fmaf(a[t], b[t], acc);
   return acc;
+}
+
+// BF16 storage of a panel entry (round to nearest even) and its value.
+__device__ __forceinline__ uint16_t f32_to_bf16_bits(float x) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+__device__ __forceinline__ float bf16_bits_to_f32(uint16_t h) { return __uint_as_float((unsigned)h << 16); }
+
+// The precision variant's panel entry: the BF16 value, unless the threshold
+// decision |d - l| > zeta could differ from the FP32 one.  Rounding to BF16
+// moves d by at most 2^-9 |d| (8 significant bits, round to nearest), so the
+// decisions agree whenever ||d_bf16 - l| - zeta| > 2^-8 |d_bf16| (a factor 2
+// of margin); inside that band the FP32 entry is read (`exact`) and used.
+template <typename F>
+__device__ __forceinline__ float bf16_entry(uint16_t h, float l, float zeta, F exact) {
+  const float d = bf16_bits_to_f32(h);
+  if (fabsf(fabsf(d - l) - zeta) <= 0x1p-8f * fabsf(d) + 1e-30f) return exact();
+  return d;
 }
 
 // One entry of D - S_{k+1} on a panel (Alg. 1, Phase I then Phase II):
@@ -105,7 +124,20 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 
+// 4-byte asynchronous copy (any 4-byte aligned address).
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Wait until at most N of this thread's committed copy groups are pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // Nanosecond device clock (comparable across SMs).
 __device__ __forceinline__ unsigned long long global_ns() {

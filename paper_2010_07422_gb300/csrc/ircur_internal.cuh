@@ -16,12 +16,13 @@ constexpr int kNumSMsHint = 152;
 // but ends a lost wait within a few seconds.
 constexpr long long kSpinLimit = 1ll << 26;
 
-// Panel-pass tiling: a block covers kPanelCols consecutive panel columns; a
-// thread owns two adjacent columns and one of kPanelSplit contiguous shares
-// of the panel's rows.
+// Panel-pass tiling: a tile is kPanelCols consecutive panel columns; a block
+// of kPassWarps warps computes one tile at a time, warp h owning row share h
+// and lane c column c.  Each tile leaves its (num, den) partial sums in
+// `partials`.
 constexpr int kPanelCols = 32;
-constexpr int kPanelSplit = 16;
-constexpr int kPanelThreads = (kPanelCols / 2) * kPanelSplit;
+constexpr int kPassWarps = 8;
+constexpr int kPassThreads = 32 * kPassWarps;
 constexpr int kMaxPanelRows = 512;  // largest |I|, |J| the kernels are built for
 
 // Device-resident solver state, written only by the kernels of one solve.
@@ -60,6 +61,12 @@ struct IterDesc {
   int64_t rowLd;
   const float* colSrc;  // D^T (R) or PcolT (F)
   int64_t colLd;
+  // Precision variant (IRCUR-F): the compact panels stored in BF16 (rowLd,
+  // colLd are then their leading dimensions in elements); a threshold
+  // decision within BF16 rounding of zeta is taken again from the FP32 D.
+  int bf16;
+  const uint16_t* rowSrcH;  // D(I,:) in BF16, nI x rowLd
+  const uint16_t* colSrcH;  // D(:,J)^T in BF16, nJ x colLd
   float* Prow;          // F: nI x ldPr
   int64_t ldPr;
   float* PcolT;         // F: nJ x ldPc
@@ -79,7 +86,7 @@ struct IterDesc {
   float* Vs;            // nJ x R   X T^{-1} (column-pass projection; zero for dropped directions)
   float* sigma;         // R        |diag T| (diagnostic)
   float* Tm;            // R x R    Rayleigh-Ritz matrix T = Y^T core X of the last iteration
-  double* partials;     // 2 per pass block
+  double* partials;     // 2 per panel tile (row tiles, then column tiles)
   double* errs;         // max_iter
   State* st;
   int nRowTiles, nColTiles;
@@ -105,6 +112,8 @@ struct BatchLaunch {
   size_t svd_smem[2];
   int svd_roles;           // 1, or 3 when some instance draws its next index sets
   size_t pass_smem;
+  int pass_mmax;           // largest |I|, |J| of the batch (shared-memory layout)
+  int pass_nbuf;           // tile buffers per block (2: prefetch)
   unsigned long long cond; // graph conditional handle (0 = no graph)
   int* any_active;         // device flag written by the loop-control kernel
 };
@@ -183,7 +192,7 @@ cudaError_t launch_adj_dense(int64_t n1, int64_t n2, const float* A, const float
 cudaError_t launch_adj_step(const AdjStep& a, int Rpad, bool need_next, cudaStream_t s);
 size_t adj_cg_smem_bytes(int nI, int nJ, int Rpad);
 cudaError_t launch_adj_scatter(const AdjStep& a, float* dD, int64_t lddD, cudaStream_t s);
-size_t pass_smem_bytes(int nI, int nJ, int Rpad);
+size_t pass_smem_bytes(int nI, int nJ, int Rpad, int* nbuf = nullptr, bool bf16 = false);
 int pad_rank(int r);
 
 }  // namespace ircur

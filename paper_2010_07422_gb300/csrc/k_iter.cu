@@ -44,7 +44,8 @@ __device__ __forceinline__ void core_body(const IterDesc& d, int blk, int nblk) 
 #pragma unroll
     for (int t = 0; t < R; ++t) arow[t] = A[(int64_t)ia * R + t];
     if (threadIdx.x < R) d.AI[(size_t)a * R + threadIdx.x] = A[(int64_t)ia * R + threadIdx.x];
-    const float* rowp = d.rowSrc + (int64_t)(d.resample ? ia : a) * d.rowLd;
+    const float* rowp = d.bf16 ? nullptr : d.rowSrc + (int64_t)(d.resample ? ia : a) * d.rowLd;
+    const uint16_t* rowh = d.bf16 ? d.rowSrcH + (int64_t)a * d.rowLd : nullptr;
     for (int b = threadIdx.x; b < d.nJ; b += blockDim.x) {
       const int j = J[b];
       float bcol[R];
@@ -55,7 +56,9 @@ __device__ __forceinline__ void core_body(const IterDesc& d, int blk, int nblk) 
         for (int t = 0; t < R; ++t) d.BJt[(size_t)b * R + t] = bcol[t];
       }
       const float l = lowrank_entry<R>(arow, bcol);
-      d.core[(int64_t)a * d.ldCore + b] = panel_value(rowp[j], l, zeta);
+      const float dv = d.bf16 ? bf16_entry(rowh[j], l, zeta, [&]() { return d.D[(int64_t)ia * d.ldD + j]; })
+                              : rowp[j];
+      d.core[(int64_t)a * d.ldCore + b] = panel_value(dv, l, zeta);
     }
   }
   if (d.trace) {
@@ -76,7 +79,9 @@ __global__ void __launch_bounds__(256) core_batch_kernel(const IterDesc* __restr
 }
 
 // ---------------------------------------------------------------------------
-// One panel pass over a tile of kPanelCols consecutive panel columns.
+// Panel passes: Alg. 1 Phase I on the panels, the Phase II products and the
+// stopping sums of Sec. 3.3, as one persistent grid over tiles of kPanelCols
+// consecutive panel columns.
 //
 // Row pass (COL = false): the panel is D(I,:) (m = |I| rows); for column j
 //   R_{k+1}(:,j) = D(I,j) - T_zeta(D(I,j) - A_k(I,:) B_k(:,j)),
@@ -89,103 +94,172 @@ __global__ void __launch_bounds__(256) core_batch_kernel(const IterDesc* __restr
 // Both are the same computation on a row-major m x n panel with
 //   side = A_k(I,:) | B_k(:,J)^T (m x R), vec = B_k(:,j) | A_k(i,:)^T,
 //   proj = Y | X T^{-1},  recon = Y | X T^T  (U^+ = X T^{-1} Y^T, see k_svd.cu).
-// The m x kPanelCols tile is staged in shared memory by 16-byte asynchronous
-// copies (the rows are gathered: one small segment per panel row, which the
-// per-instruction cost of bulk TMA copies makes slower), overwritten with
-// D - S, and read back by the second sweep for the explicit residual.  A
-// thread owns two adjacent columns and a contiguous share of the rows
-// (kPanelSplit shares); the partial projections are added in a fixed order.
-template <int R, bool COL>
-__device__ void panel_pass(const IterDesc& d, int tile, int k, float zeta, unsigned char* smem, double* acc2) {
+//
+// A block owns a contiguous run of tiles (the grid is the number of resident
+// blocks); consecutive tiles of one instance and side form a segment whose
+// m x R side, projection and reconstruction matrices are staged in shared
+// memory once.  Tiles are double-buffered: the 16-byte asynchronous copies of
+// tile t+1 (one small segment per gathered panel row) fly while tile t is
+// computed.  Within a tile, warp h owns row share h and lane c column c
+// (conflict-free tile accesses, broadcast reads of the small matrices); the
+// share partial projections and the shares' num/den sums are added in a fixed
+// order into one slot per tile, so e_{k+1} does not depend on how the tiles
+// are spread over blocks.  The block that completes an
+// instance's last tile reduces its slots in a fixed order, evaluates e_{k+1},
+// advances k and zeta, and (single instance) drives the graph's while-node
+// (Alg. 1: "while e_k > epsilon").
+
+struct PassLayout {
+  int m, rx, nbuf;
+  unsigned char* tiles;  // nbuf staging buffers of m x kPanelCols panel entries (FP32 or BF16)
+  size_t tile_bytes;     // bytes of one staging buffer
+  float* vbuf;           // BF16 panels: the FP32 values D - S of the current tile (else null)
+  float* side;
+  float* proj;
+  float* recon;
+  float* part;  // kPassWarps x RX x kPanelCols
+  float* outS;  // RX x kPanelCols
+  double* wsum; // kPassWarps x 2
+};
+
+__host__ __device__ inline size_t pass_layout_floats(int m, int rx, int nbuf, bool bf16 = false) {
+  const size_t tile = bf16 ? (size_t)m * kPanelCols / 2 : (size_t)m * kPanelCols;  // in floats
+  return (size_t)nbuf * tile + (bf16 ? (size_t)m * kPanelCols : 0) + 3 * (size_t)m * rx +
+         (size_t)kPassWarps * rx * kPanelCols + (size_t)rx * kPanelCols + 4 * kPassWarps;
+}
+
+__device__ inline PassLayout pass_layout(unsigned char* smem, int m, int rx, int nbuf, bool bf16) {
+  PassLayout L;
+  L.m = m;
+  L.rx = rx;
+  L.nbuf = nbuf;
+  L.tiles = smem;
+  // m is a multiple of... any m: round the BF16 buffers to 16 bytes
+  L.tile_bytes = bf16 ? (((size_t)m * kPanelCols * 2 + 15) & ~(size_t)15) : (size_t)m * kPanelCols * 4;
+  float* p = reinterpret_cast<float*>(smem + nbuf * L.tile_bytes);
+  L.vbuf = bf16 ? p : nullptr;
+  if (bf16) p += (size_t)m * kPanelCols;
+  L.side = p;
+  L.proj = p + (size_t)m * rx;
+  L.recon = p + 2 * (size_t)m * rx;
+  L.part = p + 3 * (size_t)m * rx;
+  L.outS = L.part + (size_t)kPassWarps * rx * kPanelCols;
+  L.wsum = reinterpret_cast<double*>(L.outS + (size_t)rx * kPanelCols);  // 8-byte aligned: every piece is a multiple of 8 floats
+  return L;
+}
+
+// Where tile t of the grid lives.
+struct TileRef {
+  int inst;    // instance
+  int col;     // 0: row panel, 1: column panel
+  int lt;      // tile within that panel
+  int active;  // the instance is still iterating
+  int k;       // its iteration
+};
+
+// Issue the copies of one panel tile into `buf`: 16-byte asynchronous copies
+// when the rows are 16-byte aligned and the tile is full, 4-byte ones
+// otherwise (BF16 panels, always aligned: plain loads for the ragged tile).
+template <bool COL, bool BF>
+__device__ __forceinline__ void pass_stage_tile(const IterDesc& d, int k, int lt, unsigned char* bufp) {
   const int m = COL ? d.nJ : d.nI;
   const int64_t ncolsTotal = COL ? d.n1 : d.n2;
-  const int cur = k & 1, nxt = cur ^ 1;
-  const int* I = d.I_all + (d.resample ? (int64_t)k * d.nI : 0);
-  const int* J = d.J_all + (d.resample ? (int64_t)k * d.nJ : 0);
-  const int* map = COL ? J : I;
+  const int64_t ld = COL ? d.colLd : d.rowLd;
+  const int64_t j0 = (int64_t)lt * kPanelCols;
+  const int ncols = (int)((ncolsTotal - j0) < kPanelCols ? (ncolsTotal - j0) : kPanelCols);
+  if (BF) {
+    const uint16_t* src = COL ? d.colSrcH : d.rowSrcH;
+    uint16_t* buf = reinterpret_cast<uint16_t*>(bufp);
+    if (ncols == kPanelCols) {
+      constexpr int kV = kPanelCols / 8;
+      for (int q = threadIdx.x; q < m * kV; q += blockDim.x) {
+        const int a = q / kV, c8 = q - a * kV;
+        cp_async16(buf + (size_t)a * kPanelCols + 8 * c8, src + (int64_t)a * ld + j0 + 8 * c8);
+      }
+    } else {
+      for (int q = threadIdx.x; q < m * kPanelCols; q += blockDim.x) {
+        const int a = q / kPanelCols, c = q - a * kPanelCols;
+        buf[q] = c < ncols ? src[(int64_t)a * ld + j0 + c] : (uint16_t)0;
+      }
+    }
+    return;
+  }
+  float* buf = reinterpret_cast<float*>(bufp);
+  const int* map = (COL ? d.J_all : d.I_all) + (d.resample ? (int64_t)k * m : 0);
   const bool mapped = d.resample != 0;
   const float* src = COL ? d.colSrc : d.rowSrc;
-  const int64_t ld = COL ? d.colLd : d.rowLd;
-
-  constexpr int RX = (R + 3) & ~3;                         // 16-byte rows of the small matrices
-  float* tileS = reinterpret_cast<float*>(smem);           // m x kPanelCols
-  float* side = tileS + (size_t)m * kPanelCols;             // m x RX
-  float* proj = side + (size_t)m * RX;                      // m x RX
-  float* recon = COL ? proj + (size_t)m * RX : proj;        // m x RX (row pass: recon == proj)
-  float* part = proj + (size_t)(COL ? 2 : 1) * m * RX;      // kPanelSplit x kPanelCols x RX
-  float* outS = part + (size_t)kPanelSplit * kPanelCols * RX;  // kPanelCols x RX
-
-  const int64_t j0 = (int64_t)tile * kPanelCols;
-  const int ncols = (int)((ncolsTotal - j0) < kPanelCols ? (ncolsTotal - j0) : kPanelCols);
-  const bool vec16 = (COL ? d.colBulk : d.rowBulk) && ncols == kPanelCols;
-
-  // 1. the panel tile: 16-byte asynchronous copies issued first, so that they
-  //    fly during the staging of the small matrices
-  if (vec16) {
+  if ((COL ? d.colBulk : d.rowBulk) && ncols == kPanelCols) {
     constexpr int kV = kPanelCols / 4;
     for (int q = threadIdx.x; q < m * kV; q += blockDim.x) {
       const int a = q / kV, c4 = q - a * kV;
       const int64_t row = mapped ? __ldg(map + a) : a;
-      cp_async16(tileS + (size_t)a * kPanelCols + 4 * c4, src + row * ld + j0 + 4 * c4);
+      cp_async16(buf + (size_t)a * kPanelCols + 4 * c4, src + row * ld + j0 + 4 * c4);
     }
   } else {
+    // rows not 16-byte aligned, or the ragged last tile: 4-byte asynchronous
+    // copies (zeros past the panel's last column)
     for (int q = threadIdx.x; q < m * kPanelCols; q += blockDim.x) {
       const int a = q / kPanelCols, c = q - a * kPanelCols;
-      const int64_t row = mapped ? map[a] : a;
-      tileS[q] = c < ncols ? src[row * ld + j0 + c] : 0.f;
-    }
-  }
-  // 2. the m x R side, projection and reconstruction matrices (rows padded to RX)
-  {
-    const float* sideG = COL ? d.BJt : d.AI;
-    for (int q = threadIdx.x; q < m * RX; q += blockDim.x) {
-      const int a = q / RX, t = q - a * RX;
-      const bool in = t < R;
-      side[q] = in ? sideG[a * R + t] : 0.f;
-      if (COL) {
-        proj[q] = in ? d.Vs[a * R + t] : 0.f;
-        recon[q] = in ? d.V[a * R + t] : 0.f;
+      if (c < ncols) {
+        const int64_t row = mapped ? __ldg(map + a) : a;
+        cp_async4(buf + q, src + row * ld + j0 + c);
       } else {
-        proj[q] = in ? d.W[a * R + t] : 0.f;
+        buf[q] = 0.f;
       }
     }
   }
-  if (vec16) cp_async_wait_all();
-  __syncthreads();
+}
 
-  // thread = (column pair cp, row split h); columns c0 = 2 cp, c0 + 1
-  constexpr int kPairs = kPanelCols / 2;
-  const int cp = threadIdx.x % kPairs, h = threadIdx.x / kPairs;
-  const int c0 = 2 * cp;
-  const int a0 = (int)((long long)h * m / kPanelSplit), a1 = (int)((long long)(h + 1) * m / kPanelSplit);
-  const bool live0 = c0 < ncols, live1 = c0 + 1 < ncols;
-  const int64_t j = j0 + c0;
-  float vec0[R], vec1[R], acc0[R], acc1[R];
+// The m x R side, projection and reconstruction matrices of one segment
+// (rows padded to RX columns with zeros).
+template <int R, bool COL>
+__device__ __forceinline__ void pass_stage_small(const IterDesc& d, const PassLayout& L) {
+  constexpr int RX = (R + 3) & ~3;
+  const int m = COL ? d.nJ : d.nI;
+  const float* sideG = COL ? d.BJt : d.AI;
+  const float* projG = COL ? d.Vs : d.W;
+  for (int q = threadIdx.x; q < m * RX; q += blockDim.x) {
+    const int a = q / RX, t = q - a * RX;
+    const bool in = t < R;
+    L.side[q] = in ? sideG[a * R + t] : 0.f;
+    L.proj[q] = in ? projG[a * R + t] : 0.f;
+    if (COL) L.recon[q] = in ? d.V[a * R + t] : 0.f;
+  }
+}
+
+// One tile: thresholded panel values, projections, explicit residuals.
+template <int R, bool COL, bool BF>
+__device__ __forceinline__ void pass_tile(const IterDesc& d, int k, float zeta, int lt, const PassLayout& L,
+                                          unsigned char* tileP) {
+  // FP32 panels: the tile is overwritten with D - S; BF16 panels: D - S goes
+  // to the FP32 work buffer
+  float* tileS = BF ? L.vbuf : reinterpret_cast<float*>(tileP);
+  const uint16_t* tileH = reinterpret_cast<const uint16_t*>(tileP);
+  constexpr int RX = (R + 3) & ~3;
+  const int m = COL ? d.nJ : d.nI;
+  const int64_t ncolsTotal = COL ? d.n1 : d.n2;
+  const int cur = k & 1, nxt = cur ^ 1;
+  const int lane = threadIdx.x & 31, h = threadIdx.x >> 5;
+  const int64_t j0 = (int64_t)lt * kPanelCols;
+  const int64_t j = j0 + lane;
+  const bool live = j < ncolsTotal;
+  const float* side = L.side;
+  const float* proj = L.proj;
+  const float* recon = COL ? L.recon : L.proj;
+  float vec[R], acc[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) {
-    vec0[t] = vec1[t] = 0.f;
-    acc0[t] = acc1[t] = 0.f;
+    acc[t] = 0.f;
+    if (COL)
+      vec[t] = live ? d.A[cur][j * R + t] : 0.f;
+    else
+      vec[t] = live ? d.B[cur][(int64_t)t * d.n2 + j] : 0.f;
   }
-  if (COL) {
-    const float* A = d.A[cur];
-#pragma unroll
-    for (int t = 0; t < R; ++t) {
-      if (live0) vec0[t] = A[j * R + t];
-      if (live1) vec1[t] = A[(j + 1) * R + t];
-    }
-  } else {
-    const float* B = d.B[cur];
-#pragma unroll
-    for (int t = 0; t < R; ++t) {
-      if (live0) vec0[t] = B[(int64_t)t * d.n2 + j];
-      if (live1) vec1[t] = B[(int64_t)t * d.n2 + j + 1];
-    }
-  }
-  const float m0 = live0 ? 1.f : 0.f, m1 = live1 ? 1.f : 0.f;
+  const float msk = live ? 1.f : 0.f;
+  const int a0 = h * m / kPassWarps, a1 = (h + 1) * m / kPassWarps;
   float den = 0.f;
   for (int a = a0; a < a1; ++a) {
-    float2* cell = reinterpret_cast<float2*>(tileS + (size_t)a * kPanelCols + c0);
-    const float2 dv = *cell;
+    float* cell = tileS + (size_t)a * kPanelCols + lane;
     float sr[R], pr[R];
 #pragma unroll
     for (int t4 = 0; t4 < RX / 4; ++t4) {
@@ -199,41 +273,40 @@ __device__ void panel_pass(const IterDesc& d, int tile, int k, float zeta, unsig
           pr[4 * t4 + e] = p4[e];
         }
     }
-    const float v0 = panel_value(dv.x, lowrank_entry<R>(sr, vec0), zeta) * m0;
-    const float v1 = panel_value(dv.y, lowrank_entry<R>(sr, vec1), zeta) * m1;
-    *cell = make_float2(v0, v1);
-    den = fmaf(dv.x, dv.x, den);
-    den = fmaf(dv.y, dv.y, den);
-#pragma unroll
-    for (int t = 0; t < R; ++t) {
-      acc0[t] = fmaf(pr[t], v0, acc0[t]);
-      acc1[t] = fmaf(pr[t], v1, acc1[t]);
+    const float l = lowrank_entry<R>(sr, vec);
+    float dv;
+    if (BF) {
+      dv = bf16_entry(tileH[(size_t)a * kPanelCols + lane], l, zeta, [&]() {
+        if (!live) return 0.f;
+        return COL ? d.D[j * d.ldD + d.J_all[a]] : d.D[(int64_t)d.I_all[a] * d.ldD + j];
+      });
+    } else {
+      dv = *cell;
     }
+    const float v = panel_value(dv, l, zeta) * msk;
+    *cell = v;
+    den = fmaf(dv, dv, den);
+#pragma unroll
+    for (int t = 0; t < R; ++t) acc[t] = fmaf(pr[t], v, acc[t]);
   }
 #pragma unroll
-  for (int t = 0; t < R; ++t) {
-    part[((size_t)h * kPanelCols + c0) * RX + t] = acc0[t];
-    part[((size_t)h * kPanelCols + c0 + 1) * RX + t] = acc1[t];
-  }
+  for (int t = 0; t < R; ++t) L.part[((size_t)h * RX + t) * kPanelCols + lane] = acc[t];
   __syncthreads();
-  // projections of every column: the kPanelSplit partial sums in a fixed order
-  for (int q = threadIdx.x; q < kPanelCols * R; q += blockDim.x) {
-    const int cc = q / R, t = q - cc * R;
+  // projections of every column: the kPassWarps share sums in a fixed order
+  for (int q = threadIdx.x; q < R * kPanelCols; q += blockDim.x) {
+    const int t = q / kPanelCols, cc = q - t * kPanelCols;
     float sum = 0.f;
 #pragma unroll
-    for (int hh = 0; hh < kPanelSplit; ++hh) sum += part[((size_t)hh * kPanelCols + cc) * RX + t];
-    outS[cc * RX + t] = sum;
+    for (int hh = 0; hh < kPassWarps; ++hh) sum += L.part[((size_t)hh * RX + t) * kPanelCols + cc];
+    L.outS[(size_t)t * kPanelCols + cc] = sum;
   }
   __syncthreads();
-  float out0[R], out1[R];
+  float out[R];
 #pragma unroll
-  for (int t = 0; t < R; ++t) {
-    out0[t] = outS[c0 * RX + t];
-    out1[t] = outS[(c0 + 1) * RX + t];
-  }
+  for (int t = 0; t < R; ++t) out[t] = L.outS[(size_t)t * kPanelCols + lane];
   float num = 0.f;
   for (int a = a0; a < a1; ++a) {
-    const float2 v = *reinterpret_cast<const float2*>(tileS + (size_t)a * kPanelCols + c0);
+    const float v = tileS[(size_t)a * kPanelCols + lane];
     float rr[R];
 #pragma unroll
     for (int t4 = 0; t4 < RX / 4; ++t4) {
@@ -243,97 +316,75 @@ __device__ void panel_pass(const IterDesc& d, int tile, int k, float zeta, unsig
       for (int e = 0; e < 4; ++e)
         if (4 * t4 + e < R) rr[4 * t4 + e] = r4[e];
     }
-    float w0 = 0.f, w1 = 0.f;
+    float w = 0.f;
 #pragma unroll
-    for (int t = 0; t < R; ++t) {
-      w0 = fmaf(rr[t], out0[t], w0);
-      w1 = fmaf(rr[t], out1[t], w1);
-    }
-    const float e0 = (v.x - w0) * m0, e1 = (v.y - w1) * m1;
-    num = fmaf(e0, e0, num);
-    num = fmaf(e1, e1, num);
+    for (int t = 0; t < R; ++t) w = fmaf(rr[t], out[t], w);
+    const float e = (v - w) * msk;
+    num = fmaf(e, e, num);
   }
-  if (h == 0) {
+  if (h == 0 && live) {
     if (COL) {
       float* An = d.A[nxt];
 #pragma unroll
-      for (int t = 0; t < R; ++t) {
-        if (live0) An[j * R + t] = out0[t];
-        if (live1) An[(j + 1) * R + t] = out1[t];
-      }
+      for (int t = 0; t < R; ++t) An[j * R + t] = out[t];
     } else {
       float* Bn = d.B[nxt];
 #pragma unroll
-      for (int t = 0; t < R; ++t) {
-        if (live0) Bn[(int64_t)t * d.n2 + j] = out0[t];
-        if (live1) Bn[(int64_t)t * d.n2 + j + 1] = out1[t];
-      }
+      for (int t = 0; t < R; ++t) Bn[(int64_t)t * d.n2 + j] = out[t];
     }
   }
-  acc2[0] += (double)num;
-  acc2[1] += (double)den;
+  // this share's sums; the tile's slot gets them in share order after the
+  // block's end-of-tile barrier (pass_tile_sums)
+  const double sn = warp_sum((double)num), sd = warp_sum((double)den);
+  if (lane == 0) {
+    L.wsum[2 * h + 0] = sn;
+    L.wsum[2 * h + 1] = sd;
+  }
 }
 
-// Both passes in one grid (row tiles first); the last block to finish reduces
-// the per-block partial sums in a fixed order, evaluates e_{k+1}, advances k
-// and zeta, and drives the graph's while-node (Alg. 1: "while e_k > epsilon").
-template <int R>
-__device__ __forceinline__ void pass_body(const IterDesc& d, int blk, int nblk, unsigned char* smem) {
-  State* st = d.st;
-  if (st->done || st->status) {
-    if (blk == 0 && threadIdx.x == 0) {
-      st->done = 1;
-      if (d.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)d.cond, 0u);
-    }
-    return;
-  }
-  const int k = st->k;
-  const float zeta = (float)st->zeta;
-  trace_start(d.trace, 3 * k + 2);
-  double acc[2] = {0.0, 0.0};
-  const int nPanel = d.nRowTiles + d.nColTiles;
-  if (blk < d.nRowTiles) {
-    panel_pass<R, false>(d, blk, k, zeta, smem, acc);
-  } else if (blk < nPanel) {
-    panel_pass<R, true>(d, blk - d.nRowTiles, k, zeta, smem, acc);
-  }
-
-  __shared__ double red[4][kPanelThreads / 32];
-  __shared__ int is_last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// After the end-of-tile barrier: the tile's num/den in its slot (share order).
+__device__ __forceinline__ void pass_tile_sums(const IterDesc& d, int gtile, const PassLayout& L) {
+  if (threadIdx.x == 0) {
+    double sn = 0.0, sd = 0.0;
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const double v = warp_sum(acc[q]);
-    if (lane == 0) red[q][warp] = v;
+    for (int h = 0; h < kPassWarps; ++h) {
+      sn += L.wsum[2 * h + 0];
+      sd += L.wsum[2 * h + 1];
+    }
+    d.partials[(size_t)gtile * 2 + 0] = sn;
+    d.partials[(size_t)gtile * 2 + 1] = sd;
   }
-  __syncthreads();
-  if (threadIdx.x < 2) {
-    double s = 0.0;
-    for (int w = 0; w < kPanelThreads / 32; ++w) s += red[threadIdx.x][w];
-    d.partials[(size_t)blk * 2 + threadIdx.x] = s;
-  }
+}
+
+// The block that completed an instance's last tile: e_{k+1} from the slots in
+// a fixed order, then k, zeta and the loop condition.
+__device__ void pass_finalize(const IterDesc& d, int k) {
+  State* st = d.st;
+  __shared__ double fin[2][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __threadfence();
-  __syncthreads();
-  trace_stop(d.trace, 3 * d.max_iter, 3 * k + 2);
-  if (threadIdx.x == 0) is_last = (atomicAdd(&st->counter, 1u) == (unsigned)nblk - 1u);
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  // warp q: q = 0,1 row-pass num/den; q = 2,3 column-pass num/den
+  // warp q: q = 0,1 row-pass num/den; q = 2,3 column-pass num/den; lanes
+  // stride over the tiles with four independent accumulators
   if (warp < 4) {
     const int colside = warp >> 1, which = warp & 1;
-    const unsigned b0 = colside ? (unsigned)d.nRowTiles : 0u;
-    const unsigned b1 = colside ? (unsigned)nblk : (unsigned)d.nRowTiles;
-    double s = 0.0;
-    const volatile double* pv = d.partials;
-    for (unsigned b = b0 + lane; b < b1; b += 32) s += pv[(size_t)b * 2 + which];
-    s = warp_sum(s);
-    if (lane == 0) red[2 + (warp >> 1)][warp & 1] = s;
+    const int b0 = colside ? d.nRowTiles : 0;
+    const int b1 = colside ? d.nRowTiles + d.nColTiles : d.nRowTiles;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int b = b0 + lane;
+    for (; b + 96 < b1; b += 128) {
+      s0 += __ldcg(d.partials + (size_t)b * 2 + which);
+      s1 += __ldcg(d.partials + (size_t)(b + 32) * 2 + which);
+      s2 += __ldcg(d.partials + (size_t)(b + 64) * 2 + which);
+      s3 += __ldcg(d.partials + (size_t)(b + 96) * 2 + which);
+    }
+    for (; b < b1; b += 32) s0 += __ldcg(d.partials + (size_t)b * 2 + which);
+    const double s = warp_sum((s0 + s1) + (s2 + s3));
+    if (lane == 0) fin[colside][which] = s;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const double num = sqrt(red[2][0]) + sqrt(red[3][0]);
-    const double den = sqrt(red[2][1]) + sqrt(red[3][1]);
+    const double num = sqrt(fin[0][0]) + sqrt(fin[1][0]);
+    const double den = sqrt(fin[0][1]) + sqrt(fin[1][1]);
     const double e = den > 0.0 ? num / den : 0.0;
     d.errs[k] = e;
     st->e = e;
@@ -344,33 +395,159 @@ __device__ __forceinline__ void pass_body(const IterDesc& d, int blk, int nblk, 
     const int done = (e <= d.tol) || (k + 1 >= d.max_iter) || (st->status != 0);
     st->done = done;
     __threadfence();
-    trace_stop(d.trace, 3 * d.max_iter, 3 * k + 2);
     if (d.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)d.cond, done ? 0u : 1u);
   }
+  __syncthreads();
 }
 
-template <int R>
-__global__ void __launch_bounds__(kPanelThreads, 3) pass_kernel(IterDesc d) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  pass_body<R>(d, blockIdx.x, gridDim.x, smem);
-}
-
-// Batched form: the grid holds every instance's tiles back to back;
-// tile_base[i] is the first block of instance i (tile_base[count] = grid).
-template <int R>
-__global__ void __launch_bounds__(kPanelThreads, 3) pass_batch_kernel(const IterDesc* __restrict__ ds,
-                                                                      const int* __restrict__ tile_base, int count) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  int lo = 0, hi = count - 1;  // instance i with tile_base[i] <= blockIdx.x < tile_base[i + 1]
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (tile_base[mid] <= (int)blockIdx.x)
-      lo = mid;
-    else
-      hi = mid - 1;
+template <int R, bool BATCH, bool BF>
+__device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDesc* __restrict__ ds,
+                                                const int* __restrict__ tile_base, int count, int total,
+                                                int mmax, int nbuf, unsigned char* smem) {
+  constexpr int RX = (R + 3) & ~3;
+  const PassLayout L = pass_layout(smem, mmax, RX, nbuf, BF);
+  if (!BATCH && (d1.st->done || d1.st->status)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      d1.st->done = 1;
+      if (d1.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)d1.cond, 0u);
+    }
+    return;
   }
-  pass_body<R>(ds[lo], (int)blockIdx.x - tile_base[lo], tile_base[lo + 1] - tile_base[lo], smem);
+  const int t0 = (int)((long long)blockIdx.x * total / gridDim.x);
+  const int t1 = (int)((long long)(blockIdx.x + 1) * total / gridDim.x);
+  if (t0 >= t1) return;
+  // tile -> (instance, side, local tile); instances are visited in order
+  int inst = 0;
+  if (BATCH) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_base[mid] <= t0)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    inst = lo;
+  }
+  auto locate = [&](int t, int& in) -> TileRef {
+    if (BATCH)
+      while (tile_base[in + 1] <= t) ++in;
+    const IterDesc& d = BATCH ? ds[in] : d1;
+    TileRef ref;
+    ref.inst = in;
+    const int lt = t - (BATCH ? tile_base[in] : 0);
+    ref.col = lt >= d.nRowTiles;
+    ref.lt = ref.col ? lt - d.nRowTiles : lt;
+    ref.active = !(d.st->done || d.st->status);
+    ref.k = d.st->k;
+    return ref;
+  };
+  auto stage = [&](const TileRef& ref, unsigned char* buf) {
+    const IterDesc& d = BATCH ? ds[ref.inst] : d1;
+    if (ref.col)
+      pass_stage_tile<true, BF>(d, ref.k, ref.lt, buf);
+    else
+      pass_stage_tile<false, BF>(d, ref.k, ref.lt, buf);
+  };
+  __shared__ int is_last;
+  int pin = inst;  // instance cursor of the prefetch
+  TileRef cur = locate(t0, inst);
+  if (cur.active) stage(cur, L.tiles);
+  cp_async_commit();
+  int seg_inst = -1, seg_col = -1, seg_k = 0, run = 0;
+  float zeta = 0.f;
+  for (int t = t0; t < t1; ++t) {
+    if (t > t0) cur = locate(t, inst);
+    const IterDesc& d = BATCH ? ds[cur.inst] : d1;
+    const bool new_seg = cur.inst != seg_inst || cur.col != seg_col;
+    if (new_seg && run > 0) {
+      // close the previous run: count its tiles; the last one finalizes
+      const IterDesc& dp = BATCH ? ds[seg_inst] : d1;
+      __threadfence();
+      __syncthreads();
+      trace_stop(dp.trace, 3 * dp.max_iter, 3 * seg_k + 2);
+      if (threadIdx.x == 0)
+        is_last = (atomicAdd(&dp.st->counter, (unsigned)run) + (unsigned)run ==
+                   (unsigned)(dp.nRowTiles + dp.nColTiles));
+      __syncthreads();
+      if (is_last) pass_finalize(dp, seg_k);
+      run = 0;
+    }
+    const int b = (t - t0) % nbuf;
+    if (nbuf == 1 && t > t0 && cur.active) {
+      stage(cur, L.tiles);
+      cp_async_commit();
+    }
+    bool pre = false;
+    if (nbuf == 2 && t + 1 < t1) {
+      int in2 = pin < inst ? inst : pin;
+      const TileRef nx = locate(t + 1, in2);
+      pin = in2;
+      if (nx.active) {
+        stage(nx, L.tiles + (size_t)(b ^ 1) * L.tile_bytes);
+        pre = true;
+      }
+      cp_async_commit();
+    }
+    if (!cur.active) {
+      seg_inst = cur.inst;
+      seg_col = cur.col;
+      continue;  // an instance that stopped: nothing to do
+    }
+    if (new_seg) {
+      seg_inst = cur.inst;
+      seg_col = cur.col;
+      seg_k = cur.k;
+      zeta = (float)d.st->zeta;
+      trace_start(d.trace, 3 * seg_k + 2);
+      if (cur.col)
+        pass_stage_small<R, true>(d, L);
+      else
+        pass_stage_small<R, false>(d, L);
+    }
+    if (pre)
+      cp_async_wait_group<1>();
+    else
+      cp_async_wait_group<0>();
+    __syncthreads();
+    if (cur.col)
+      pass_tile<R, true, BF>(d, seg_k, zeta, cur.lt, L, L.tiles + (size_t)b * L.tile_bytes);
+    else
+      pass_tile<R, false, BF>(d, seg_k, zeta, cur.lt, L, L.tiles + (size_t)b * L.tile_bytes);
+    __syncthreads();
+    pass_tile_sums(d, t - (BATCH ? tile_base[cur.inst] : 0), L);
+    ++run;
+  }
+  if (run > 0) {
+    const IterDesc& dp = BATCH ? ds[seg_inst] : d1;
+    __threadfence();
+    __syncthreads();
+    trace_stop(dp.trace, 3 * dp.max_iter, 3 * seg_k + 2);
+    if (threadIdx.x == 0)
+      is_last = (atomicAdd(&dp.st->counter, (unsigned)run) + (unsigned)run == (unsigned)(dp.nRowTiles + dp.nColTiles));
+    __syncthreads();
+    if (is_last) pass_finalize(dp, seg_k);
+  }
+  cp_async_wait_group<0>();
 }
+
+template <int R, bool BF>
+__global__ void __launch_bounds__(kPassThreads) pass_kernel(IterDesc d, int nbuf) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int mmax = d.nI > d.nJ ? d.nI : d.nJ;
+  pass_persistent<R, false, BF>(d, nullptr, nullptr, 1, d.nRowTiles + d.nColTiles, mmax, nbuf, smem);
+}
+
+// Batched form: the tiles of every instance back to back (tile_base[i] is the
+// first tile of instance i, tile_base[count] the total).
+template <int R>
+__global__ void __launch_bounds__(kPassThreads) pass_batch_kernel(const IterDesc* __restrict__ ds,
+                                                                  const int* __restrict__ tile_base, int count,
+                                                                  int mmax, int nbuf) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  pass_persistent<R, true, false>(ds[0], ds, tile_base, count, tile_base[count], mmax, nbuf, smem);
+}
+
 
 // Batched loop control: the while-node continues while any instance runs.
 __global__ void batch_check_kernel(const IterDesc* __restrict__ ds, int count, unsigned long long cond,
@@ -389,13 +566,46 @@ __global__ void batch_check_kernel(const IterDesc* __restrict__ ds, int count, u
   }
 }
 
-size_t pass_smem_bytes(int nI, int nJ, int Rpad) {
+// Shared memory of the pass kernel: two tile buffers when they fit next to
+// the small matrices, else one (no prefetch).
+size_t pass_smem_bytes(int nI, int nJ, int Rpad, int* nbuf_out, bool bf16) {
   const int m = nI > nJ ? nI : nJ;
-  const size_t rx = (size_t)((Rpad + 3) & ~3);
-  return (size_t)m * kPanelCols * 4 + 3 * (size_t)m * rx * 4 + (size_t)kPanelSplit * kPanelCols * rx * 4 +
-         (size_t)kPanelCols * rx * 4 + 16;
+  const int rx = (Rpad + 3) & ~3;
+  int nbuf = 2;
+  size_t bytes = pass_layout_floats(m, rx, 2, bf16) * 4 + 64;
+  if (bytes > 227 * 1024) {
+    nbuf = 1;
+    bytes = pass_layout_floats(m, rx, 1, bf16) * 4 + 64;
+  }
+  if (nbuf_out) *nbuf_out = nbuf;
+  return bytes;
 }
 
+// Resident blocks of a pass kernel (cached per kernel and shared-memory size).
+static int pass_grid(const void* fn, size_t smem) {
+  static int num_sms = 0;
+  struct Entry {
+    const void* fn;
+    size_t smem;
+    int blocks;
+  };
+  static Entry cache[64];
+  static int ncache = 0;
+  for (int q = 0; q < ncache; ++q)
+    if (cache[q].fn == fn && cache[q].smem == smem) return cache[q].blocks;
+  if (num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || num_sms <= 0)
+      num_sms = kNumSMsHint;
+  }
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPassThreads, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const int blocks = per_sm * num_sms;
+  if (ncache < 64) cache[ncache++] = Entry{fn, smem, blocks};
+  return blocks;
+}
 cudaError_t launch_svd(const IterDesc& d, int Rpad, cudaStream_t s);
 
 template <int R>
@@ -410,10 +620,22 @@ static cudaError_t launch_iter_r(const IterDesc& d, cudaStream_t s) {
     cudaError_t e = launch_svd(d, R, s);
     if (e != cudaSuccess) return e;
   }
-  const size_t bytes = pass_smem_bytes(d.nI, d.nJ, R);
-  cudaError_t e = cudaFuncSetAttribute(pass_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  int nbuf = 1;
+  const size_t bytes = pass_smem_bytes(d.nI, d.nJ, R, &nbuf, d.bf16 != 0);
+  const int total = d.nRowTiles + d.nColTiles;
+  if (d.bf16) {
+    cudaError_t e = cudaFuncSetAttribute(pass_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    int grid = pass_grid((const void*)pass_kernel<R, true>, bytes);
+    if (grid > total) grid = total;
+    pass_kernel<R, true><<<grid, kPassThreads, bytes, s>>>(d, nbuf);
+    return cudaGetLastError();
+  }
+  cudaError_t e = cudaFuncSetAttribute(pass_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  pass_kernel<R><<<d.nRowTiles + d.nColTiles, kPanelThreads, bytes, s>>>(d);
+  int grid = pass_grid((const void*)pass_kernel<R, false>, bytes);
+  if (grid > total) grid = total;
+  pass_kernel<R, false><<<grid, kPassThreads, bytes, s>>>(d, nbuf);
   return cudaGetLastError();
 }
 
@@ -426,7 +648,11 @@ static cudaError_t launch_batch_iter_r(const BatchLaunch& b, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(pass_batch_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.pass_smem);
   if (e != cudaSuccess) return e;
-  pass_batch_kernel<R><<<b.total_tiles, kPanelThreads, b.pass_smem, s>>>(b.ds, b.tile_base, b.count);
+  {
+    int grid = pass_grid((const void*)pass_batch_kernel<R>, b.pass_smem);
+    if (grid > b.total_tiles) grid = b.total_tiles;
+    pass_batch_kernel<R><<<grid, kPassThreads, b.pass_smem, s>>>(b.ds, b.tile_base, b.count, b.pass_mmax, b.pass_nbuf);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   batch_check_kernel<<<1, 256, 0, s>>>(b.ds, b.count, b.cond, b.any_active);

@@ -271,6 +271,12 @@ cudaError_t launch_setup(const IterDesc& d, double zeta0, cudaStream_t s) {
 __global__ void __launch_bounds__(256) gather_rows_kernel(IterDesc d) {
   const int a = blockIdx.y;
   const float* src = d.D + (int64_t)d.I_all[a] * d.ldD;
+  if (d.bf16) {
+    uint16_t* dst = const_cast<uint16_t*>(d.rowSrcH) + (int64_t)a * d.rowLd;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n2; j += (int64_t)gridDim.x * blockDim.x)
+      dst[j] = f32_to_bf16_bits(__ldg(src + j));
+    return;
+  }
   float* dst = d.Prow + (int64_t)a * d.ldPr;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < d.n2;
        j += (int64_t)gridDim.x * blockDim.x)
@@ -280,6 +286,12 @@ __global__ void __launch_bounds__(256) gather_rows_kernel(IterDesc d) {
 __global__ void __launch_bounds__(256) gather_cols_kernel(IterDesc d) {
   const int b = blockIdx.y;
   const int64_t j = d.J_all[b];
+  if (d.bf16) {
+    uint16_t* dst = const_cast<uint16_t*>(d.colSrcH) + (int64_t)b * d.colLd;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.n1; i += (int64_t)gridDim.x * blockDim.x)
+      dst[i] = f32_to_bf16_bits(__ldg(d.D + i * d.ldD + j));
+    return;
+  }
   float* dst = d.PcolT + (int64_t)b * d.ldPc;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.n1;
        i += (int64_t)gridDim.x * blockDim.x)

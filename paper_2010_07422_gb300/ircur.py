@@ -19,6 +19,7 @@ IRCUR_OK, IRCUR_EINVAL, IRCUR_ENOMEM, IRCUR_ECUDA = 0, 1, 2, 3
 IRCUR_ESVD_NOCONV, IRCUR_ETIMEOUT, IRCUR_ESTATE, IRCUR_ENOTSUP = 4, 5, 6, 7
 IRCUR_FLAG_WRANK, IRCUR_FLAG_SVD_NOCONV = 1, 2
 IRCUR_MAX_RANK = 16
+IRCUR_PRECISION_FP32, IRCUR_PRECISION_BF16_PANELS = 0, 1
 
 EXPORTED = (
     "ircur_create", "ircur_destroy", "ircur_solve", "ircur_get_factors", "ircur_get_indices",
@@ -250,11 +251,11 @@ class IRCUR:
     """
 
     def __init__(self, n1, n2, r, *, nI=0, nJ=0, zeta0=0.0, gamma=0.7, tol=1e-5, max_iter=100,
-                 resample=True, seed=0, stream=None):
+                 resample=True, seed=0, precision=IRCUR_PRECISION_FP32, stream=None):
         import torch
         self.p = ircur_params(n1=n1, n2=n2, r=r, nI=nI, nJ=nJ, zeta0=zeta0, gamma=gamma, tol=tol,
                               max_iter=max_iter, resample=int(bool(resample)), seed=seed,
-                              precision=0, reserved=0)
+                              precision=precision, reserved=0)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._ctx = ircur_create(self.p, C.c_void_p(self.stream.cuda_stream))
         self.nI = nI if nI else sample_size(4, r, n1)
