@@ -122,16 +122,16 @@ struct SvdSmall {
 };
 
 // Adds the partial sums of a product (chunk-major, column-major blocks) in a
-// fixed order.
+// fixed order; every (column, row) output is one thread's sum.
 template <int R>
 __device__ __forceinline__ void reduce_parts(const float* part, int nch, int nout, int ldm, float* out) {
   __syncthreads();
-  for (int t = 0; t < R; ++t) {
-    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-      float s = 0.f;
-      for (int c = 0; c < nch; ++c) s += part[(size_t)c * R * ldm + (size_t)t * ldm + o];
-      out[(size_t)t * ldm + o] = s;
-    }
+  for (int q = threadIdx.x; q < R * nout; q += blockDim.x) {
+    const int t = q / nout, o = q - t * nout;
+    const float* pp = part + (size_t)t * ldm + o;
+    float s = 0.f;
+    for (int c = 0; c < nch; ++c) s += pp[(size_t)c * R * ldm];
+    out[(size_t)t * ldm + o] = s;
   }
   __syncthreads();
 }
@@ -140,7 +140,7 @@ __device__ __forceinline__ void reduce_parts(const float* part, int nch, int nou
 // spaced G apart (lanes on consecutive rows) and an inner chunk; core rows are
 // read as 16-byte vectors and each 4-row slab of every column of X is a
 // 16-byte broadcast shared by the RB rows.  Rows of X beyond nin are zero.
-template <int R, int RB = (R > 8 ? 2 : 4)>
+template <int R, int RB = 2>
 __device__ void core_times(const float* __restrict__ U, int ldu, int nout, int nin, const float* __restrict__ in,
                            float* __restrict__ out, float* part, int ldm, int pch) {
   const int G = (nout + RB - 1) / RB;
@@ -190,42 +190,51 @@ __device__ void core_times(const float* __restrict__ U, int ldu, int nout, int n
   reduce_parts<R>(part, nch, nout, ldm, out);
 }
 
-// out = core^T Y (nout = |J| rows, inner nin = |I|).  A thread owns one
-// output row j (lanes on consecutive j) and an inner chunk stepped by 4: four
-// core entries down column j and one 16-byte broadcast per column of Y.
-// Rows of Y beyond nin are zero.
+// out = core^T Y (nout = |J| rows, inner nin = |I|).  A thread owns four
+// consecutive output rows j..j+3 (a 16-byte vector of every core row; lanes on
+// consecutive vectors) and an inner chunk stepped by 4: four core vectors and
+// one 16-byte broadcast of four rows of Y per column, 16 R FMAs.  Rows of Y
+// beyond nin are zero, columns of the core beyond nout are zero.
 template <int R>
 __device__ void core_t_times(const float* __restrict__ U, int ldu, int nout, int nin, const float* __restrict__ in,
                              float* __restrict__ out, float* part, int ldm, int pch) {
-  const int lanes = (nout + 31) & ~31;
+  const int G = (nout + 3) / 4;  // column groups
+  const int lanes = (G + 31) & ~31;
   int nch = (int)blockDim.x / lanes;
   nch = nch < 1 ? 1 : (nch > pch ? pch : nch);
-  const int c = threadIdx.x / lanes, j = threadIdx.x % lanes;
+  const int c = threadIdx.x / lanes, g = threadIdx.x % lanes;
   const int nin4 = round_up4(nin);
   const int ic = round_up4((nin4 + nch - 1) / nch);
-  if (c < nch && j < nout) {
-    float acc[R];
+  if (c < nch && g < G) {
+    const int j = 4 * g;
+    float acc[4][R];
 #pragma unroll
-    for (int t = 0; t < R; ++t) acc[t] = 0.f;
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+      for (int t = 0; t < R; ++t) acc[e][t] = 0.f;
     const int i0 = c * ic, i1 = i0 + ic < nin4 ? i0 + ic : nin4;
     for (int i = i0; i < i1; i += 4) {
-      const float u0 = U[(size_t)i * ldu + j];
-      const float u1 = i + 1 < nin ? U[(size_t)(i + 1) * ldu + j] : 0.f;
-      const float u2 = i + 2 < nin ? U[(size_t)(i + 2) * ldu + j] : 0.f;
-      const float u3 = i + 3 < nin ? U[(size_t)(i + 3) * ldu + j] : 0.f;
+      float4 u[4];
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        u[kk] = (i + kk < nin) ? *reinterpret_cast<const float4*>(U + (size_t)(i + kk) * ldu + j)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int t = 0; t < R; ++t) {
         const float4 y = *reinterpret_cast<const float4*>(in + (size_t)t * ldm + i);
-        float a = acc[t];
-        a = fmaf(u0, y.x, a);
-        a = fmaf(u1, y.y, a);
-        a = fmaf(u2, y.z, a);
-        a = fmaf(u3, y.w, a);
-        acc[t] = a;
+        acc[0][t] = fmaf(u[3].x, y.w, fmaf(u[2].x, y.z, fmaf(u[1].x, y.y, fmaf(u[0].x, y.x, acc[0][t]))));
+        acc[1][t] = fmaf(u[3].y, y.w, fmaf(u[2].y, y.z, fmaf(u[1].y, y.y, fmaf(u[0].y, y.x, acc[1][t]))));
+        acc[2][t] = fmaf(u[3].z, y.w, fmaf(u[2].z, y.z, fmaf(u[1].z, y.y, fmaf(u[0].z, y.x, acc[2][t]))));
+        acc[3][t] = fmaf(u[3].w, y.w, fmaf(u[2].w, y.z, fmaf(u[1].w, y.y, fmaf(u[0].w, y.x, acc[3][t]))));
       }
     }
 #pragma unroll
-    for (int t = 0; t < R; ++t) part[(size_t)c * R * ldm + (size_t)t * ldm + j] = acc[t];
+    for (int e = 0; e < 4; ++e) {
+      if (j + e < nout) {
+#pragma unroll
+        for (int t = 0; t < R; ++t) part[(size_t)c * R * ldm + (size_t)t * ldm + j + e] = acc[e][t];
+      }
+    }
   }
   reduce_parts<R>(part, nch, nout, ldm, out);
 }
@@ -521,17 +530,23 @@ __device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned c
     const float tol = (float)(nI > nJ ? nI : nJ) * FLT_EPSILON * dmax;
     const bool keep = lane < r && dabs > tol && dabs > 0.f;
     const unsigned kmask = __ballot_sync(0xffffffffu, keep);
-    if (lane < r) {  // column `lane` of T^{-1} by back substitution
+    if (lane < r) {  // column `lane` of T^{-1} by back substitution, in registers
       const int c = lane;
+      float x[R];
+#pragma unroll
       for (int s2 = R - 1; s2 >= 0; --s2) {
         float v = 0.f;
         if (s2 <= c && ((kmask >> s2) & 1u)) {
           v = (s2 == c) ? 1.f : 0.f;
-          for (int u = s2 + 1; u <= c; ++u) v = fmaf(-sm.T[s2 * R + u], sm.tmp[u * R + c], v);
+#pragma unroll
+          for (int u = s2 + 1; u < R; ++u)
+            if (u <= c) v = fmaf(-sm.T[s2 * R + u], x[u], v);
           v = v / sm.T[s2 * R + s2];
         }
-        sm.tmp[s2 * R + c] = v;
+        x[s2] = v;
       }
+#pragma unroll
+      for (int s2 = 0; s2 < R; ++s2) sm.tmp[s2 * R + c] = x[s2];
       sm.sig[lane] = keep ? dabs : 0.f;
     }
     if (lane == 0) {
