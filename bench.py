@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the secondary measurements (batched, adjoint, precision variant)")
     return ap.parse_args()
 
 
@@ -200,6 +202,110 @@ def run_reference(a, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _timed(fn, reps, stream):
+    """Median of `reps` CUDA-event timings (ms) of fn() on `stream`."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def bench_batched(ir, synth, stream, count=64, seed=7):
+    """Uneven independent problems (n1, n2 uniform in [500, 4000], r in 2..10,
+    alpha in [0.05, 0.3], the planted generator): one batch vs a loop of single
+    solves on the same GPU.  Solves/s."""
+    import torch
+    shapes = synth.uneven_batch(count, seed=seed)
+    Ds = [synth.planted_device(q["n1"], q["n2"], q["r"], q["alpha"], seed=100 + i) for i, q in enumerate(shapes)]
+    probs = [dict(n1=q["n1"], n2=q["n2"], r=q["r"], resample=True, seed=i, tol=1e-5, max_iter=100)
+             for i, q in enumerate(shapes)]
+    batch = ir.IRCURBatch(probs)
+    for _ in range(2):
+        res = batch.solve(Ds)
+    tune = batch.autotune(Ds, reps=3)
+    for _ in range(2):
+        res = batch.solve(Ds)
+    t_batch = _timed(lambda: batch.solve(Ds), 5, stream)
+    singles = [ir.IRCUR(q["n1"], q["n2"], q["r"], resample=True, seed=q["seed"], tol=1e-5, max_iter=100)
+               for q in probs]
+    for s_, D_ in zip(singles, Ds):
+        s_.solve(D_)
+    t_loop = _timed(lambda: [s_.solve(D_) for s_, D_ in zip(singles, Ds)], 3, stream)
+    iters = [r_.iters for r_ in res]
+    out = {"workload": f"{count} independent IRCUR-R problems, n1, n2 uniform in [500, 4000], r uniform in 2..10, "
+                       "alpha uniform in [0.05, 0.3], planted generator on the device, tol 1e-5",
+           "solves_per_s": count / (t_batch / 1e3), "ms_per_batch": t_batch,
+           "loop_solves_per_s": count / (t_loop / 1e3), "loop_ms": t_loop, "speedup_vs_loop": t_loop / t_batch,
+           "iters_min_max": [min(iters), max(iters)], "converged": int(sum(r_.converged for r_ in res)),
+           "autotune": tune}
+    for s_ in singles:
+        s_.close()
+    batch.close()
+    return out
+
+
+def bench_adjoint(ir, synth, stream, count=8, n=4096, r=10, T=15):
+    """Unrolled IRCUR-F forward + hand-written backward through autograd:
+    loss = ||L - L_true||_F^2 + 0.1 ||S||_1 per instance."""
+    import torch
+    gens = [synth.planted_device(n, n, r, 0.1, seed=300 + b) for b in range(count)]
+    solvers = [ir.IRCUR(n, n, r, tol=1e-12, max_iter=T, resample=False, seed=b) for b in range(count)]
+    Lt = torch.zeros(n, n, device="cuda")
+
+    def step():
+        for D0, s_ in zip(gens, solvers):
+            D = D0.detach().requires_grad_(True)
+            L, S = ir.ircur_unrolled(D, s_)
+            loss = ((L - Lt) ** 2).sum() + 0.1 * S.abs().sum()
+            loss.backward()
+
+    for _ in range(2):
+        step()
+    t = _timed(step, 5, stream)
+    dL = torch.randn(n, n, device="cuda")
+    tf = _timed(lambda: (solvers[0].solve(gens[0]), solvers[0].reconstruct(gens[0])), 5, stream)
+    tb = _timed(lambda: solvers[0].backward(gens[0], dL, dL), 5, stream)
+    for s_ in solvers:
+        s_.close()
+    return {"workload": f"{count} instances n1 = n2 = {n}, r = {r}, alpha = 0.1, fixed I, J "
+                        f"(|I| = |J| = {ir.sample_size(4, r, n)}), T = {T} unrolled iterations; "
+                        "loss ||L - L_true||^2 + 0.1 ||S||_1 through torch.autograd",
+            "fwd_bwd_ms": t, "per_instance_forward_ms": tf, "per_instance_backward_ms": tb,
+            "note": "gradient parity with the FP64 oracle gradient: tests/test_gpu_adjoint.py"}
+
+
+def bench_precision(ir, synth, stream, K=30):
+    """Video-shaped D (120 x 160 pixels x 3055 frames, r = 2): FP32 panels vs
+    BF16 panels with the FP32 band re-check, same K iterations."""
+    import torch
+    v = synth.video_like(120, 160, 3055, seed=5)
+    D = torch.from_numpy(v.D).cuda()
+    out = {"workload": "video-shaped D 19200 x 3055 (120 x 160 pixels x frames), r = 2, IRCUR-F, "
+                       f"{K} iterations, values in [0, 1]"}
+    Ls = {}
+    for name, prec in (("fp32", ir.IRCUR_PRECISION_FP32), ("bf16_panels", ir.IRCUR_PRECISION_BF16_PANELS)):
+        s_ = ir.IRCUR(19200, 3055, 2, resample=False, precision=prec, tol=1e-12, max_iter=K, seed=1)
+        for _ in range(3):
+            s_.solve(D)
+        out[name + "_solve_ms"] = _timed(lambda: s_.solve(D), 10, stream)
+        L, _ = s_.reconstruct(D, with_sparse=False)
+        Ls[name] = L.double().cpu().numpy()
+        out[name + "_rel_err_vs_background"] = float(np.linalg.norm(Ls[name] - v.background) /
+                                                     np.linalg.norm(v.background))
+        s_.close()
+    out["bf16_rel_diff_vs_fp32_L"] = float(np.linalg.norm(Ls["bf16_panels"] - Ls["fp32"]) / np.linalg.norm(Ls["fp32"]))
+    out["speedup_bf16_vs_fp32"] = out["fp32_solve_ms"] / out["bf16_panels_solve_ms"]
+    out["note"] = "error against the FP64 oracle: tests/test_gpu_precision.py"
+    return out
+
+
 def main():
     a = parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -238,6 +344,10 @@ def main():
         return res
 
     for _ in range(max(3, a.warmup)):
+        step()
+    # pass-kernel launch shape chosen by timing whole solves (ircur_autotune)
+    tune = solver.autotune(D, reps=3)
+    for _ in range(2):
         step()
     torch.cuda.synchronize()
     barrier()
@@ -325,7 +435,8 @@ def main():
                 "unit": "TFLOP/s", "frac": svd_ach / fp32_peak, "traffic": dram_traffic("svd_kernel", f"n{n}_r{r}"),
                 "peak_source": "FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (one CTA by design: "
                                "per-SM share is 1/152 of this)",
-                "algorithmic_flops_per_launch": svd_flops, "avg_launch_us": svd_avg_us}
+                "algorithmic_flops_per_launch": svd_flops, "avg_launch_us": svd_avg_us,
+                "frac_of_one_sm": svd_ach / (fp32_peak / 152)}
     roofs = {"recon_vec_kernel": roof_recon, "pass_kernel": roof_pass, "svd_kernel": roof_svd}
     dominant = max(("svd_kernel", "pass_kernel", "recon_vec_kernel"), key=lambda kk: per_step_us[kk])
 
@@ -382,6 +493,16 @@ def main():
                          f"{c_iters} iterations, {c_el:.1f} s), numpy/BLAS default threads",
                "time_to_tol_ms": 1e3 * c_el / c_solves}
 
+    extras = {}
+    if rank == 0 and world == 1 and not a.no_extras:
+        from paper_2010_07422_gb300 import synth
+        for key, fn in (("batched", bench_batched), ("adjoint", bench_adjoint), ("precision_variant", bench_precision)):
+            try:
+                extras[key] = fn(ir, synth, stream)
+            except Exception as exc:  # a secondary measurement must not cost the headline line
+                extras[key] = {"error": f"{type(exc).__name__}: {exc}"}
+            torch.cuda.synchronize()
+
     if rank == 0:
         launches_per_step = [4 + (2 if not resample else 0) + 3 * it + 1 for it in iters]
         line = {
@@ -403,6 +524,7 @@ def main():
             "roofline": roofs[dominant],
             "roofline_other": {kk: vv for kk, vv in roofs.items() if kk != dominant},
             "kernel_us_per_step": per_step_us,
+            "autotune": tune,
             "timing_note": "kernel spans from the device clock (first block start to last block end) inside "
                            "the CUDA graph; the reconstruction by CUDA events on the solver's stream",
             "cpu_baseline": cpu,
@@ -410,6 +532,7 @@ def main():
             "gpu_launches": int(sum(launches_per_step)),
             "clocks": clocks,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     solver.close()
     if world > 1:

@@ -277,6 +277,30 @@ ircur_status ircur_batch_solve(ircur_batch* b, const float* const* D, const int6
  * ircur_reconstruct after ircur_batch_solve.  Null for i out of range. */
 ircur_ctx* ircur_batch_instance(ircur_batch* b, int32_t i);
 
+/* Autotuning of the panel-pass launch shape (not in the paper).  The pass
+ * kernel is persistent: each block walks a contiguous run of panel tiles.
+ * How many blocks to launch (1, 2, ... resident blocks per SM, or one block
+ * per tile) and whether each block double-buffers its tiles decide how much
+ * of a tile's latency is hidden; the best choice depends on |I|, |J|, n1, n2,
+ * the rank and the GPU.  ircur_autotune runs `reps` (1..16, default 3) timed
+ * solves of D (device, n1 x n2, ldD) per candidate after one untimed solve,
+ * and keeps the candidate with the smallest median solve time for the
+ * context's later solves; *out lists what was timed.  The context's state
+ * afterwards is that of the last solve run.  Synchronises the stream.
+ * ircur_batch_autotune does the same for a batch (D, ldD as for
+ * ircur_batch_solve). */
+#define IRCUR_TUNE_MAX 8
+typedef struct {
+  int32_t count;                        /* candidates timed */
+  int32_t chosen;                       /* index of the candidate kept */
+  int32_t grid[IRCUR_TUNE_MAX];         /* pass-kernel blocks of candidate i */
+  int32_t single_buffer[IRCUR_TUNE_MAX];/* 1: one tile buffer per block */
+  float ms[IRCUR_TUNE_MAX];             /* median solve time of candidate i (ms) */
+} ircur_tune_result;
+ircur_status ircur_autotune(ircur_ctx* ctx, const float* D, int64_t ldD, int32_t reps, ircur_tune_result* out);
+ircur_status ircur_batch_autotune(ircur_batch* b, const float* const* D, const int64_t* ldD, int32_t reps,
+                                  ircur_tune_result* out);
+
 /* Human-readable name of a status code (static string). */
 const char* ircur_status_string(ircur_status s);
 

@@ -87,6 +87,8 @@ struct ircur_ctx {
   int64_t graph_ldD;
   int graph_sample_ahead;
   unsigned long long* graph_trace;
+  int graph_pass_grid;
+  int graph_single;
   unsigned long long* trace;  // kernel-span trace buffer (2 * 3 * max_iter), or null
   // last solve
   int solved;
@@ -357,6 +359,8 @@ static ircur_status build_graph(ircur_ctx* c, const IterDesc& d0) {
   c->graph_ldD = d0.ldD;
   c->graph_sample_ahead = d0.sampleAhead;
   c->graph_trace = d0.trace;
+  c->graph_pass_grid = d0.passGrid;
+  c->graph_single = d0.passSingleBuf;
   return IRCUR_OK;
 }
 
@@ -472,7 +476,7 @@ extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, c
   }
   if (use_graph()) {
     if (!c->exec || c->graph_D != D || c->graph_ldD != ldD || c->graph_sample_ahead != d.sampleAhead ||
-        c->graph_trace != d.trace) {
+        c->graph_trace != d.trace || c->graph_pass_grid != d.passGrid || c->graph_single != d.passSingleBuf) {
       ircur_status bs = build_graph(c, d);
       if (bs != IRCUR_OK) return bs;
     }
@@ -1131,3 +1135,158 @@ extern "C" ircur_status ircur_batch_solve(ircur_batch* b, const float* const* D,
   }
   return first;
 }
+
+// ---------------------------------------------------------------------------
+// Autotuning of the panel-pass launch shape: whole solves timed with CUDA
+// events for each candidate (resident blocks per SM, one or two tile buffers);
+// the fastest stays in the context (or batch).
+
+static int device_sms() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = kNumSMsHint;
+  return n;
+}
+
+struct TuneCand {
+  int grid, single;
+};
+
+static int tune_candidates(int total, int resident2, int resident1, int sms, TuneCand* out) {
+  int n = 0;
+  auto add = [&](int grid, int single) {
+    if (grid > total) grid = total;
+    if (grid < 1) return;
+    for (int q = 0; q < n; ++q)
+      if (out[q].grid == grid && out[q].single == single) return;
+    if (n < IRCUR_TUNE_MAX) out[n++] = TuneCand{grid, single};
+  };
+  const int per2 = resident2 / sms, per1 = resident1 / sms;
+  for (int k = per2; k >= 1; --k) add(k * sms, 0);
+  if (per1 > per2) add(per1 * sms, 1);
+  add(total, 0);  // one block per tile (blocks beyond the resident ones queue)
+  return n;
+}
+
+static float median3(float* v, int n) {
+  for (int i = 1; i < n; ++i)
+    for (int j = i; j > 0 && v[j] < v[j - 1]; --j) {
+      const float t = v[j];
+      v[j] = v[j - 1];
+      v[j - 1] = t;
+    }
+  return v[n / 2];
+}
+
+extern "C" ircur_status ircur_autotune(ircur_ctx* c, const float* D, int64_t ldD, int32_t reps,
+                                       ircur_tune_result* out) {
+  if (!c || !D || !out) return IRCUR_EINVAL;
+  if (reps < 1) reps = 3;
+  if (reps > 16) reps = 16;
+  memset(out, 0, sizeof(*out));
+  const int total = c->desc.nRowTiles + c->desc.nColTiles;
+  const int sms = device_sms();
+  IterDesc probe = c->desc;
+  probe.passSingleBuf = 0;
+  const int res2 = pass_resident_blocks(probe, c->Rpad);
+  probe.passSingleBuf = 1;
+  const int res1 = pass_resident_blocks(probe, c->Rpad);
+  TuneCand cand[IRCUR_TUNE_MAX];
+  const int nc = tune_candidates(total, res2, res1, sms, cand);
+  cudaEvent_t e0, e1;
+  IRCUR_CK(cudaEventCreate(&e0));
+  IRCUR_CK(cudaEventCreate(&e1));
+  ircur_status st = IRCUR_OK;
+  int best = 0;
+  for (int q = 0; q < nc && st == IRCUR_OK; ++q) {
+    c->desc.passGrid = cand[q].grid;
+    c->desc.passSingleBuf = cand[q].single;
+    reset_graph(c);
+    ircur_result r;
+    st = ircur_solve(c, D, ldD, nullptr, nullptr, &r);  // warm-up (records the graph)
+    float t[16];
+    for (int k = 0; k < reps && st == IRCUR_OK; ++k) {
+      cudaEventRecord(e0, c->stream);
+      st = ircur_solve(c, D, ldD, nullptr, nullptr, &r);
+      cudaEventRecord(e1, c->stream);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&t[k], e0, e1);
+    }
+    if (st != IRCUR_OK) break;
+    out->grid[q] = cand[q].grid;
+    out->single_buffer[q] = cand[q].single;
+    out->ms[q] = median3(t, reps);
+    if (out->ms[q] < out->ms[best]) best = q;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  out->count = nc;
+  out->chosen = best;
+  c->desc.passGrid = nc > 0 ? cand[best].grid : 0;
+  c->desc.passSingleBuf = nc > 0 ? cand[best].single : 0;
+  reset_graph(c);
+  return st;
+}
+
+extern "C" ircur_status ircur_batch_autotune(ircur_batch* b, const float* const* D, const int64_t* ldD, int32_t reps,
+                                             ircur_tune_result* out) {
+  if (!b || !D || !ldD || !out) return IRCUR_EINVAL;
+  if (reps < 1) reps = 3;
+  if (reps > 16) reps = 16;
+  memset(out, 0, sizeof(*out));
+  const int sms = device_sms();
+  BatchLaunch& bl = b->bl;
+  const int mm = bl.pass_mmax;
+  bl.pass_grid = 0;
+  bl.pass_smem = pass_smem_bytes(mm, mm, b->Rpad, &bl.pass_nbuf, false, false);
+  const int res2 = pass_batch_resident_blocks(bl, b->Rpad);
+  const size_t smem2 = bl.pass_smem;
+  const int nbuf2 = bl.pass_nbuf;
+  int nbuf1 = 1;
+  const size_t smem1 = pass_smem_bytes(mm, mm, b->Rpad, &nbuf1, false, true);
+  bl.pass_smem = smem1;
+  bl.pass_nbuf = nbuf1;
+  const int res1 = pass_batch_resident_blocks(bl, b->Rpad);
+  TuneCand cand[IRCUR_TUNE_MAX];
+  const int nc = tune_candidates(bl.total_tiles, res2, res1, sms, cand);
+  ircur_result* res = new (std::nothrow) ircur_result[b->count];
+  if (!res) return IRCUR_ENOMEM;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    delete[] res;
+    return IRCUR_ECUDA;
+  }
+  auto apply = [&](const TuneCand& tc) {
+    bl.pass_grid = tc.grid;
+    bl.pass_smem = tc.single ? smem1 : smem2;
+    bl.pass_nbuf = tc.single ? nbuf1 : nbuf2;
+    batch_reset_graph(b);
+  };
+  ircur_status st = IRCUR_OK;
+  int best = 0;
+  for (int q = 0; q < nc && st == IRCUR_OK; ++q) {
+    apply(cand[q]);
+    st = ircur_batch_solve(b, D, ldD, res);
+    float t[16];
+    for (int k = 0; k < reps && st == IRCUR_OK; ++k) {
+      cudaEventRecord(e0, b->stream);
+      st = ircur_batch_solve(b, D, ldD, res);
+      cudaEventRecord(e1, b->stream);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&t[k], e0, e1);
+    }
+    if (st != IRCUR_OK) break;
+    out->grid[q] = cand[q].grid;
+    out->single_buffer[q] = cand[q].single;
+    out->ms[q] = median3(t, reps);
+    if (out->ms[q] < out->ms[best]) best = q;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  delete[] res;
+  out->count = nc;
+  out->chosen = best;
+  if (nc > 0) apply(cand[best]);
+  return st;
+}
+

@@ -93,6 +93,8 @@ struct IterDesc {
   int rowBulk, colBulk; // 1: panel rows are 16-byte aligned (tiles via 16-byte async copies)
   int svdMaxSteps;
   int sampleAhead;      // 1: the core-SVD launch draws the next iteration's I, J (IRCUR-R, own sampler)
+  int passGrid;         // pass-kernel blocks (0: every block that fits the GPU at once), from the autotuner
+  int passSingleBuf;    // 1: one tile buffer per block (no prefetch, less shared memory)
   long long spinLimit;      // first bounded wait on a bulk copy (kSpinLimit unless a fault is injected)
   unsigned long long cond;  // graph conditional handle (0 = no graph)
   unsigned long long* trace;  // optional kernel spans: slot 3k + {0 core, 1 svd, 2 pass}, 3 max_iter slots
@@ -114,6 +116,7 @@ struct BatchLaunch {
   size_t pass_smem;
   int pass_mmax;           // largest |I|, |J| of the batch (shared-memory layout)
   int pass_nbuf;           // tile buffers per block (2: prefetch)
+  int pass_grid;           // pass-kernel blocks (0: every block that fits the GPU at once)
   unsigned long long cond; // graph conditional handle (0 = no graph)
   int* any_active;         // device flag written by the loop-control kernel
 };
@@ -192,7 +195,10 @@ cudaError_t launch_adj_dense(int64_t n1, int64_t n2, const float* A, const float
 cudaError_t launch_adj_step(const AdjStep& a, int Rpad, bool need_next, cudaStream_t s);
 size_t adj_cg_smem_bytes(int nI, int nJ, int Rpad);
 cudaError_t launch_adj_scatter(const AdjStep& a, float* dD, int64_t lddD, cudaStream_t s);
-size_t pass_smem_bytes(int nI, int nJ, int Rpad, int* nbuf = nullptr, bool bf16 = false);
+size_t pass_smem_bytes(int nI, int nJ, int Rpad, int* nbuf = nullptr, bool bf16 = false, bool single = false);
+// Blocks of the pass kernel that are resident on the whole GPU at once.
+int pass_resident_blocks(const IterDesc& d, int Rpad);
+int pass_batch_resident_blocks(const BatchLaunch& b, int Rpad);
 int pad_rank(int r);
 
 }  // namespace ircur

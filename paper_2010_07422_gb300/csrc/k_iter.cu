@@ -568,12 +568,12 @@ __global__ void batch_check_kernel(const IterDesc* __restrict__ ds, int count, u
 
 // Shared memory of the pass kernel: two tile buffers when they fit next to
 // the small matrices, else one (no prefetch).
-size_t pass_smem_bytes(int nI, int nJ, int Rpad, int* nbuf_out, bool bf16) {
+size_t pass_smem_bytes(int nI, int nJ, int Rpad, int* nbuf_out, bool bf16, bool single) {
   const int m = nI > nJ ? nI : nJ;
   const int rx = (Rpad + 3) & ~3;
   int nbuf = 2;
   size_t bytes = pass_layout_floats(m, rx, 2, bf16) * 4 + 64;
-  if (bytes > 227 * 1024) {
+  if (bytes > 227 * 1024 || single) {
     nbuf = 1;
     bytes = pass_layout_floats(m, rx, 1, bf16) * 4 + 64;
   }
@@ -621,19 +621,19 @@ static cudaError_t launch_iter_r(const IterDesc& d, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   int nbuf = 1;
-  const size_t bytes = pass_smem_bytes(d.nI, d.nJ, R, &nbuf, d.bf16 != 0);
+  const size_t bytes = pass_smem_bytes(d.nI, d.nJ, R, &nbuf, d.bf16 != 0, d.passSingleBuf != 0);
   const int total = d.nRowTiles + d.nColTiles;
   if (d.bf16) {
     cudaError_t e = cudaFuncSetAttribute(pass_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    int grid = pass_grid((const void*)pass_kernel<R, true>, bytes);
+    int grid = d.passGrid > 0 ? d.passGrid : pass_grid((const void*)pass_kernel<R, true>, bytes);
     if (grid > total) grid = total;
     pass_kernel<R, true><<<grid, kPassThreads, bytes, s>>>(d, nbuf);
     return cudaGetLastError();
   }
   cudaError_t e = cudaFuncSetAttribute(pass_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  int grid = pass_grid((const void*)pass_kernel<R, false>, bytes);
+  int grid = d.passGrid > 0 ? d.passGrid : pass_grid((const void*)pass_kernel<R, false>, bytes);
   if (grid > total) grid = total;
   pass_kernel<R, false><<<grid, kPassThreads, bytes, s>>>(d, nbuf);
   return cudaGetLastError();
@@ -649,7 +649,7 @@ static cudaError_t launch_batch_iter_r(const BatchLaunch& b, cudaStream_t s) {
   e = cudaFuncSetAttribute(pass_batch_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.pass_smem);
   if (e != cudaSuccess) return e;
   {
-    int grid = pass_grid((const void*)pass_batch_kernel<R>, b.pass_smem);
+    int grid = b.pass_grid > 0 ? b.pass_grid : pass_grid((const void*)pass_batch_kernel<R>, b.pass_smem);
     if (grid > b.total_tiles) grid = b.total_tiles;
     pass_batch_kernel<R><<<grid, kPassThreads, b.pass_smem, s>>>(b.ds, b.tile_base, b.count, b.pass_mmax, b.pass_nbuf);
   }
@@ -658,6 +658,42 @@ static cudaError_t launch_batch_iter_r(const BatchLaunch& b, cudaStream_t s) {
   batch_check_kernel<<<1, 256, 0, s>>>(b.ds, b.count, b.cond, b.any_active);
   return cudaGetLastError();
 }
+
+template <int R>
+static int pass_resident_r(const IterDesc& d) {
+  int nbuf = 1;
+  const size_t bytes = pass_smem_bytes(d.nI, d.nJ, R, &nbuf, d.bf16 != 0, d.passSingleBuf != 0);
+  const void* fn = d.bf16 ? (const void*)pass_kernel<R, true> : (const void*)pass_kernel<R, false>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) return 0;
+  return pass_grid(fn, bytes);
+}
+
+template <int R>
+static int pass_batch_resident_r(const BatchLaunch& b) {
+  const void* fn = (const void*)pass_batch_kernel<R>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.pass_smem) != cudaSuccess) return 0;
+  return pass_grid(fn, b.pass_smem);
+}
+
+#define IRCUR_R_DISPATCH(FN, ARG)    \
+  switch (Rpad) {                    \
+    case 1: return FN<1>(ARG);       \
+    case 2: return FN<2>(ARG);       \
+    case 3: return FN<3>(ARG);       \
+    case 4: return FN<4>(ARG);       \
+    case 5: return FN<5>(ARG);       \
+    case 6: return FN<6>(ARG);       \
+    case 7: return FN<7>(ARG);       \
+    case 8: return FN<8>(ARG);       \
+    case 9: return FN<9>(ARG);       \
+    case 10: return FN<10>(ARG);     \
+    case 12: return FN<12>(ARG);     \
+    case 16: return FN<16>(ARG);     \
+    default: return 0;               \
+  }
+
+int pass_resident_blocks(const IterDesc& d, int Rpad) { IRCUR_R_DISPATCH(pass_resident_r, d) }
+int pass_batch_resident_blocks(const BatchLaunch& b, int Rpad) { IRCUR_R_DISPATCH(pass_batch_resident_r, b) }
 
 cudaError_t launch_batch_iteration(const BatchLaunch& b, int Rpad, cudaStream_t s) {
   switch (Rpad) {

@@ -26,7 +26,7 @@ EXPORTED = (
     "ircur_get_errors", "ircur_reconstruct", "ircur_solve_host", "ircur_sample_indices",
     "ircur_status_string", "ircur_last_error_string", "ircur_solve_noalloc", "ircur_set_trace",
     "ircur_get_trace", "ircur_get_cur", "ircur_batch_create", "ircur_batch_destroy", "ircur_batch_solve",
-    "ircur_batch_instance", "ircur_set_record", "ircur_backward",
+    "ircur_batch_instance", "ircur_set_record", "ircur_backward", "ircur_autotune", "ircur_batch_autotune",
 )
 
 
@@ -41,6 +41,16 @@ class ircur_result(C.Structure):
     _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("flags", C.c_uint32),
                 ("svd_steps", C.c_int32), ("final_err", C.c_double), ("zeta0", C.c_double),
                 ("zeta_next", C.c_double)]
+
+
+class ircur_tune_result(C.Structure):
+    _fields_ = [("count", C.c_int32), ("chosen", C.c_int32), ("grid", C.c_int32 * 8),
+                ("single_buffer", C.c_int32 * 8), ("ms", C.c_float * 8)]
+
+    def as_dict(self):
+        return {"chosen": self.chosen,
+                "candidates": [{"grid": self.grid[i], "single_buffer": self.single_buffer[i],
+                                "ms": self.ms[i]} for i in range(self.count)]}
 
 
 class IrcurError(RuntimeError):
@@ -85,6 +95,8 @@ def _lib():
         lib.ircur_batch_instance.restype = P
         lib.ircur_set_record.argtypes = [P, I32]
         lib.ircur_backward.argtypes = [P, P, I64, P, I64, P, I64, P, I64]
+        lib.ircur_autotune.argtypes = [P, P, I64, I32, C.POINTER(ircur_tune_result)]
+        lib.ircur_batch_autotune.argtypes = [P, C.POINTER(P), C.POINTER(I64), I32, C.POINTER(ircur_tune_result)]
         lib.ircur_status_string.argtypes = [C.c_int]
         lib.ircur_status_string.restype = C.c_char_p
         lib.ircur_last_error_string.argtypes = []
@@ -320,6 +332,12 @@ class IRCUR:
     def errors(self):
         return ircur_get_errors(self._ctx, self.p.max_iter)
 
+    def autotune(self, D, reps=3):
+        """Time the pass-kernel launch shapes on D and keep the fastest (see include/ircur.h)."""
+        out = ircur_tune_result()
+        _check(_lib().ircur_autotune(self._ctx, _ptr(D), D.stride(0), reps, C.byref(out)), "ircur_autotune")
+        return out.as_dict()
+
     def record(self, enable=True):
         """Make the following solves record their iterations for backward (IRCUR-F)."""
         ircur_set_record(self._ctx, enable)
@@ -431,6 +449,15 @@ class IRCURBatch:
             v.last = r
         _check(status, "ircur_batch_solve")
         return self.last
+
+    def autotune(self, Ds, reps=3):
+        """Time the batched pass-kernel launch shapes on Ds and keep the fastest."""
+        n = len(Ds)
+        ptrs = (C.c_void_p * n)(*[d.data_ptr() for d in Ds])
+        ldv = (C.c_int64 * n)(*[d.stride(0) for d in Ds])
+        out = ircur_tune_result()
+        _check(_lib().ircur_batch_autotune(self._b, ptrs, ldv, reps, C.byref(out)), "ircur_batch_autotune")
+        return out.as_dict()
 
     def close(self):
         if self._b:
