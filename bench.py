@@ -50,6 +50,9 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="instead of the headline line: one JSON line per configuration of the size sweep "
+                         "(n in 1000, 2500, 5000, 10000, 20000; r in 5, 10; alpha in 0.1, 0.2, 0.3; F and R)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary measurements (batched, adjoint, precision variant)")
     return ap.parse_args()
@@ -306,8 +309,54 @@ def bench_precision(ir, synth, stream, K=30):
     return out
 
 
+def run_sweep(a):
+    """Time-to-tolerance over the size sweep (planted inputs drawn on the device;
+    the FP64 oracle timed on the host for the sizes it finishes in seconds)."""
+    import torch
+    from paper_2010_07422_gb300 import ircur as ir
+    from paper_2010_07422_gb300 import synth
+    import oracle
+    stream = torch.cuda.current_stream()
+    for n in (1000, 2500, 5000, 10000, 20000):
+        for r in (5, 10):
+            for alpha in (0.1, 0.2, 0.3):
+                if n == 1000 and (r, alpha) != (5, 0.1):
+                    continue
+                D = synth.planted_device(n, n, r, alpha, seed=n + r)
+                for variant in ("F", "R"):
+                    s_ = ir.IRCUR(n, n, r, tol=1e-5, max_iter=100, resample=(variant == "R"), seed=1)
+                    s_.solve(D)
+                    s_.autotune(D, reps=2)
+                    res = s_.solve(D)
+                    ms = _timed(lambda: s_.solve(D), 5, stream)
+                    ir.ircur_set_trace(s_._ctx, True)
+                    s_.solve(D)
+                    spans = ir.ircur_get_trace(s_._ctx, 100)
+                    pass_us = float(np.mean([q for _, _, q in spans]))
+                    svd_us = float(np.mean([v for _, v, _ in spans]))
+                    nI, nJ, Rp = s_.nI, s_.nJ, (r if r <= 10 else 16)
+                    pass_gbs = (4.0 * (nI + nJ) * n + 2 * 4.0 * Rp * 2 * n) / (pass_us * 1e-6) / 1e9
+                    L, _ = s_.reconstruct(D, with_sparse=False)
+                    line = {"sweep": True, "n": n, "r": r, "alpha": alpha, "variant": variant, "m": nI,
+                            "iters": res.iters, "converged": bool(res.converged), "time_to_tol_ms": ms,
+                            "iters_per_s": res.iters / (ms / 1e3), "svd_us": svd_us, "pass_us": pass_us,
+                            "pass_gbs": pass_gbs, "pass_frac_of_measured_hbm": pass_gbs / peaks()[0]}
+                    if n <= 2500:
+                        Dn = D.cpu().numpy()
+                        t0 = time.perf_counter()
+                        ref = oracle.ircur(Dn, r, 0.0, 0.7, 1e-5, 100, resample=(variant == "R"), seed=1)
+                        line["oracle_s"] = time.perf_counter() - t0
+                        line["oracle_iters"] = ref.iters
+                    s_.close()
+                    print(json.dumps(line), flush=True)
+                del D
+
+
 def main():
     a = parse_args()
+    if a.sweep:
+        run_sweep(a)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
