@@ -132,10 +132,7 @@ static ircur_status validate_params(const ircur_params* p, ircur_params* out) {
   if (q.precision != IRCUR_PRECISION_FP32 && q.precision != IRCUR_PRECISION_BF16_PANELS) return IRCUR_ENOTSUP;
   if (q.precision == IRCUR_PRECISION_BF16_PANELS && q.resample != 0) return IRCUR_ENOTSUP;
   if (pass_smem_bytes(q.nI, q.nJ, pad_rank(q.r), nullptr, q.precision != 0) > 227 * 1024) return IRCUR_ENOTSUP;
-  {
-    bool in_smem = false;
-    if (svd_smem_bytes(q.nI, q.nJ, pad_rank(q.r), &in_smem) > 227 * 1024) return IRCUR_ENOTSUP;
-  }
+  if (csvd_smem_bytes(q.nI, q.nJ, pad_rank(q.r)) > 227 * 1024) return IRCUR_ENOTSUP;
   if (!(q.gamma > 0.0 && q.gamma < 1.0)) return IRCUR_EINVAL;
   if (!(q.tol > 0.0)) return IRCUR_EINVAL;
   if (q.max_iter < 1) return IRCUR_EINVAL;
@@ -914,8 +911,8 @@ extern "C" ircur_status ircur_batch_create(const ircur_params* params, int32_t c
     const ircur_ctx* c = b->inst[i];
     const ircur_params& p = c->p;
     const size_t ps = pass_smem_bytes(p.nI, p.nJ, Rpad);
-    bool in_smem = false;
-    const size_t ss = svd_smem_bytes(p.nI, p.nJ, Rpad, &in_smem);
+    const bool in_smem = true;  // one instance list: the cluster SVD always holds the core in shared memory
+    const size_t ss = csvd_smem_bytes(p.nI, p.nJ, Rpad);
     if (ps > 227 * 1024 || ss > 227 * 1024) {
       ircur_batch_destroy(b);
       return IRCUR_ENOTSUP;

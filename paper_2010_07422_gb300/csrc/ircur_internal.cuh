@@ -184,7 +184,6 @@ cudaError_t launch_reconstruct(const float* A, const float* B, int Rpad, int64_t
                                int64_t ldS, const State* st, cudaStream_t s);
 cudaError_t launch_get_cur(const IterDesc& d, int Rpad, int K, const float* D, int64_t ldD, float* C, float* U,
                            float* Rm, cudaStream_t s);
-size_t svd_smem_bytes(int nI, int nJ, int Rpad, bool* core_in_smem);
 cudaError_t launch_batch_iteration(const BatchLaunch& b, int Rpad, cudaStream_t s);
 cudaError_t launch_svd_batch(const BatchLaunch& b, int Rpad, cudaStream_t s);
 cudaError_t launch_sigma(const float* Tm, int r, int Rpad, float* sigma, cudaStream_t s);
@@ -196,6 +195,8 @@ cudaError_t launch_adj_step(const AdjStep& a, int Rpad, bool need_next, cudaStre
 size_t adj_cg_smem_bytes(int nI, int nJ, int Rpad);
 cudaError_t launch_adj_scatter(const AdjStep& a, float* dD, int64_t lddD, cudaStream_t s);
 size_t pass_smem_bytes(int nI, int nJ, int Rpad, int* nbuf = nullptr, bool bf16 = false, bool single = false);
+// Shared memory per CTA of the cluster core SVD.
+size_t csvd_smem_bytes(int nI, int nJ, int Rpad);
 // Blocks of the pass kernel that are resident on the whole GPU at once.
 int pass_resident_blocks(const IterDesc& d, int Rpad);
 int pass_batch_resident_blocks(const BatchLaunch& b, int Rpad);

@@ -2,11 +2,11 @@
 // (Alg. 1 Phase II; Sec. 3.1: U_{k+1} = H_r([D - S_{k+1}]_{I,J}),
 // U^+ = V_r Sigma_r^{-1} W_r^T).
 //
-// One CTA of 512 threads.  The dominant rank-r singular subspaces are found
-// by two-sided subspace (orthogonal) iteration with Cholesky QR, warm-started
-// from the previous iterate's right factor B_k(:,J)^T, whose row space is the
-// right singular subspace of L_k(I,J); the core of iteration k+1 differs from
-// L_k(I,J) only where the threshold decisions differ.  One step is
+// The dominant rank-r singular subspaces are found by two-sided subspace
+// (orthogonal) iteration with Cholesky QR, warm-started from the previous
+// iterate's right factor B_k(:,J)^T, whose row space is the right singular
+// subspace of L_k(I,J); the core of iteration k+1 differs from L_k(I,J) only
+// where the threshold decisions differ.  One step is
 //     P = core X,  Y Rp = P (CholQR),  Q = core^T Y,
 // and the iteration stops once E = Q - X Rp^T, the part of core^T Y outside
 // span X, is below 1e-6 ||Rp||_F (or has stopped shrinking below 1e-5).
@@ -19,17 +19,20 @@
 // values of T on request).  Pivots of T <= max(|I|,|J|) * FLT_EPSILON times
 // the largest are dropped (numerical rank, IRCUR_FLAG_WRANK).
 //
-// Layout: the core sits in shared memory (one bulk copy) with a leading
-// dimension ldu = 4 (mod 8) floats, so 16-byte row vectors read by lanes on
-// consecutive rows hit distinct banks.  The m x r blocks X, Y, Q and the
-// partial sums are column-major (entry (i, t) at t * ldm + i): lanes always
-// run over i, so every access is conflict-free or a broadcast.
+// It runs on a cluster of CTAs that share the core by rows (csvd_body).
+// Layout: the core rows sit in shared memory (one bulk copy per CTA) with a
+// leading dimension ldu = 4 (mod 8) floats, so 16-byte row vectors read by
+// lanes on consecutive rows hit distinct banks.  The m x r blocks X, Y, Q and
+// the partial sums are column-major (entry (i, t) at t * ld + i): lanes run
+// over i, so every access is conflict-free or a broadcast.
 //
 // Precision: FP32 throughout.  GB300's FP64 pipe runs at a small fraction of
 // its FP32 rate, and serial FP64 Cholesky/sqrt/divide chains cost more than
 // the whole rest of the iteration; CholQR2 (the second pass) restores
 // orthogonality to FP32 rounding.
+#include <cooperative_groups.h>
 #include <float.h>
+#include <string.h>
 
 #include "device_common.cuh"
 #include "ircur_internal.cuh"
@@ -37,72 +40,17 @@
 
 namespace ircur {
 
-template <int R>
-struct SvdThreads {
-  static constexpr int value = 512;
-};
-constexpr int kProdChunks = 8;  // max inner-dimension chunks of a core product
+namespace cg = cooperative_groups;
+
 constexpr int kSmallMats = 9;   // G, Rp, U, U2y, U2x, T, Ut, Vt, scratch (R x R each)
 constexpr size_t kSvdSmemBudget = 220 * 1024;
 
 __host__ __device__ constexpr int round_up4(int x) { return (x + 3) & ~3; }
 
-struct SvdLayout {
-  int ldu;  // leading dimension of the core (== ldCore: multiple of 4, ldu/4 odd)
-  int ldm;  // column stride of the m x R blocks: max(nI, nJ) rounded up to 4
-  int pch;  // inner-dimension chunks the partial-sum buffer holds (1..kProdChunks)
-  size_t off_us, off_x, off_y, off_q, off_part, off_small, off_bar, total;
-};
-
-__host__ __device__ inline SvdLayout svd_layout(int nI, int nJ, int ldCore, int R, bool core_in_smem) {
-  SvdLayout L;
-  L.ldu = ldCore;
-  L.ldm = round_up4(nI > nJ ? nI : nJ);
-  const size_t blk = (size_t)L.ldm * R * 4;
-  const size_t small = (size_t)kSmallMats * R * R * 4 + 4 * 32 * 4 + 64;
-  const size_t fixed = (core_in_smem ? (size_t)nI * L.ldu * 4 : 0) + 3 * blk + small + 16;
-  int pch = fixed < kSvdSmemBudget ? (int)((kSvdSmemBudget - fixed) / blk) : 0;
-  L.pch = pch < 1 ? 1 : (pch > kProdChunks ? kProdChunks : pch);
-  size_t off = 0;
-  L.off_us = off;
-  if (core_in_smem) off += (size_t)nI * L.ldu * 4;
-  L.off_x = off;
-  off += blk;
-  L.off_y = off;
-  off += blk;
-  L.off_q = off;
-  off += blk;
-  L.off_part = off;
-  off += (size_t)L.pch * blk;
-  L.off_small = off;
-  off += small;
-  off = (off + 7) & ~(size_t)7;
-  L.off_bar = off;
-  off += 8;
-  L.total = (off + 15) & ~(size_t)15;
-  return L;
-}
-
 static int ld_core(int nJ) {
   int ld = (nJ + 3) & ~3;
   if (((ld / 4) & 1) == 0) ld += 4;
   return ld;
-}
-
-// The core stays in shared memory when that leaves room for at least two
-// partial-sum chunks; otherwise the products read it from global memory (L2).
-size_t svd_smem_bytes(int nI, int nJ, int Rpad, bool* core_in_smem) {
-  const int ldc = ld_core(nJ);
-  SvdLayout L = svd_layout(nI, nJ, ldc, Rpad, true);
-  size_t bytes;
-  if (L.pch >= 2 && L.total <= kSvdSmemBudget) {
-    *core_in_smem = true;
-    bytes = L.total;
-  } else {
-    *core_in_smem = false;
-    bytes = svd_layout(nI, nJ, ldc, Rpad, false).total;
-  }
-  return bytes > sizeof(SamplerSmem) ? bytes : sizeof(SamplerSmem);  // the sampler blocks share the launch
 }
 
 struct SvdSmall {
@@ -121,124 +69,6 @@ struct SvdSmall {
   int* ibuf;    // 16 ints
 };
 
-// Adds the partial sums of a product (chunk-major, column-major blocks) in a
-// fixed order; every (column, row) output is one thread's sum.
-template <int R>
-__device__ __forceinline__ void reduce_parts(const float* part, int nch, int nout, int ldm, float* out) {
-  __syncthreads();
-  for (int q = threadIdx.x; q < R * nout; q += blockDim.x) {
-    const int t = q / nout, o = q - t * nout;
-    const float* pp = part + (size_t)t * ldm + o;
-    float s = 0.f;
-    for (int c = 0; c < nch; ++c) s += pp[(size_t)c * R * ldm];
-    out[(size_t)t * ldm + o] = s;
-  }
-  __syncthreads();
-}
-
-// out = core X (nout = |I| rows, inner nin = |J|).  A thread owns RB rows
-// spaced G apart (lanes on consecutive rows) and an inner chunk; core rows are
-// read as 16-byte vectors and each 4-row slab of every column of X is a
-// 16-byte broadcast shared by the RB rows.  Rows of X beyond nin are zero.
-template <int R, int RB = 2>
-__device__ void core_times(const float* __restrict__ U, int ldu, int nout, int nin, const float* __restrict__ in,
-                           float* __restrict__ out, float* part, int ldm, int pch) {
-  const int G = (nout + RB - 1) / RB;
-  const int lanes = (G + 31) & ~31;
-  int nch = (int)blockDim.x / lanes;
-  nch = nch < 1 ? 1 : (nch > pch ? pch : nch);
-  const int c = threadIdx.x / lanes, og = threadIdx.x % lanes;
-  const int nin4 = round_up4(nin);
-  const int qc = round_up4((nin4 + nch - 1) / nch);
-  if (c < nch && og < G) {
-    float acc[RB][R];
-#pragma unroll
-    for (int kk = 0; kk < RB; ++kk)
-#pragma unroll
-      for (int t = 0; t < R; ++t) acc[kk][t] = 0.f;
-    const int q0 = c * qc, q1 = q0 + qc < nin4 ? q0 + qc : nin4;
-    for (int q = q0; q < q1; q += 4) {
-      float4 u[RB];
-#pragma unroll
-      for (int kk = 0; kk < RB; ++kk) {
-        const int o = og + kk * G;
-        u[kk] = o < nout ? *reinterpret_cast<const float4*>(U + (size_t)o * ldu + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        const float4 x = *reinterpret_cast<const float4*>(in + (size_t)t * ldm + q);
-#pragma unroll
-        for (int kk = 0; kk < RB; ++kk) {
-          float a = acc[kk][t];
-          a = fmaf(u[kk].x, x.x, a);
-          a = fmaf(u[kk].y, x.y, a);
-          a = fmaf(u[kk].z, x.z, a);
-          a = fmaf(u[kk].w, x.w, a);
-          acc[kk][t] = a;
-        }
-      }
-    }
-#pragma unroll
-    for (int kk = 0; kk < RB; ++kk) {
-      const int o = og + kk * G;
-      if (o < nout) {
-#pragma unroll
-        for (int t = 0; t < R; ++t) part[(size_t)c * R * ldm + (size_t)t * ldm + o] = acc[kk][t];
-      }
-    }
-  }
-  reduce_parts<R>(part, nch, nout, ldm, out);
-}
-
-// out = core^T Y (nout = |J| rows, inner nin = |I|).  A thread owns four
-// consecutive output rows j..j+3 (a 16-byte vector of every core row; lanes on
-// consecutive vectors) and an inner chunk stepped by 4: four core vectors and
-// one 16-byte broadcast of four rows of Y per column, 16 R FMAs.  Rows of Y
-// beyond nin are zero, columns of the core beyond nout are zero.
-template <int R>
-__device__ void core_t_times(const float* __restrict__ U, int ldu, int nout, int nin, const float* __restrict__ in,
-                             float* __restrict__ out, float* part, int ldm, int pch) {
-  const int G = (nout + 3) / 4;  // column groups
-  const int lanes = (G + 31) & ~31;
-  int nch = (int)blockDim.x / lanes;
-  nch = nch < 1 ? 1 : (nch > pch ? pch : nch);
-  const int c = threadIdx.x / lanes, g = threadIdx.x % lanes;
-  const int nin4 = round_up4(nin);
-  const int ic = round_up4((nin4 + nch - 1) / nch);
-  if (c < nch && g < G) {
-    const int j = 4 * g;
-    float acc[4][R];
-#pragma unroll
-    for (int e = 0; e < 4; ++e)
-#pragma unroll
-      for (int t = 0; t < R; ++t) acc[e][t] = 0.f;
-    const int i0 = c * ic, i1 = i0 + ic < nin4 ? i0 + ic : nin4;
-    for (int i = i0; i < i1; i += 4) {
-      float4 u[4];
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-        u[kk] = (i + kk < nin) ? *reinterpret_cast<const float4*>(U + (size_t)(i + kk) * ldu + j)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        const float4 y = *reinterpret_cast<const float4*>(in + (size_t)t * ldm + i);
-        acc[0][t] = fmaf(u[3].x, y.w, fmaf(u[2].x, y.z, fmaf(u[1].x, y.y, fmaf(u[0].x, y.x, acc[0][t]))));
-        acc[1][t] = fmaf(u[3].y, y.w, fmaf(u[2].y, y.z, fmaf(u[1].y, y.y, fmaf(u[0].y, y.x, acc[1][t]))));
-        acc[2][t] = fmaf(u[3].z, y.w, fmaf(u[2].z, y.z, fmaf(u[1].z, y.y, fmaf(u[0].z, y.x, acc[2][t]))));
-        acc[3][t] = fmaf(u[3].w, y.w, fmaf(u[2].w, y.z, fmaf(u[1].w, y.y, fmaf(u[0].w, y.x, acc[3][t]))));
-      }
-    }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      if (j + e < nout) {
-#pragma unroll
-        for (int t = 0; t < R; ++t) part[(size_t)c * R * ldm + (size_t)t * ldm + j + e] = acc[e][t];
-      }
-    }
-  }
-  reduce_parts<R>(part, nch, nout, ldm, out);
-}
-
 template <int R>
 __device__ __forceinline__ float sel(const float (&g)[R], int t) {
   float v = 0.f;
@@ -248,14 +78,13 @@ __device__ __forceinline__ float sel(const float (&g)[R], int t) {
   return v;
 }
 
-// Cholesky QR of the nrows x r block Min (column-major, stride ldm) into Mout
-// (may alias): Min = Mout U with U upper triangular (written to Uout).  The
-// Gram matrix is formed by warps (one entry per warp), factorised by warp 0
-// (lane l holds row l of the Schur complement), and applied by forward
-// substitution row by row.  Pivots <= 1e-12 of the largest diagonal entry
-// mark dependent columns: they become zero columns and are counted.
+// Cholesky QR of a column-major block, in three pieces (the cluster SVD
+// reduces the Gram matrix across its CTAs between the first two).
+//
+// gram_block: G(s,t) = M(:,s) . M(:,t) over nrows rows for s <= t < r (one
+// entry per warp, lanes over rows), both triangles written.
 template <int R>
-__device__ int cholqr(const float* Min, float* Mout, int nrows, int r, int ldm, float* Uout, const SvdSmall& sm) {
+__device__ void gram_block(const float* M, int nrows, int ld, int r, float* G) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int npairs = r * (r + 1) / 2;
   for (int p = warp; p < npairs; p += nwarps) {
@@ -265,21 +94,29 @@ __device__ int cholqr(const float* Min, float* Mout, int nrows, int r, int ldm, 
       ++s;
     }
     const int t = s + rem;
-    const float* ms = Min + (size_t)s * ldm;
-    const float* mt = Min + (size_t)t * ldm;
+    const float* ms = M + (size_t)s * ld;
+    const float* mt = M + (size_t)t * ld;
     float acc = 0.f;
     for (int i = lane; i < nrows; i += 32) acc = fmaf(ms[i], mt[i], acc);
     acc = warp_sum(acc);
     if (lane == 0) {
-      sm.G[s * R + t] = acc;
-      sm.G[t * R + s] = acc;
+      G[s * R + t] = acc;
+      G[t * R + s] = acc;
     }
   }
   __syncthreads();
+}
+
+// chol_factor: G = U^T U (warp 0; lane l holds row l of the Schur complement).
+// Pivots <= 1e-12 of the largest diagonal entry mark dependent columns: their
+// rows of U are zero and sm.dinv = 0.  Returns the number of such columns.
+template <int R>
+__device__ int chol_factor(const float* G, int r, float* Uout, const SvdSmall& sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (warp == 0) {
     float g[R];
 #pragma unroll
-    for (int u = 0; u < R; ++u) g[u] = (lane < r && u < r) ? sm.G[lane * R + u] : 0.f;
+    for (int u = 0; u < R; ++u) g[u] = (lane < r && u < r) ? G[lane * R + u] : 0.f;
     float maxd = sel<R>(g, lane);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) maxd = fmaxf(maxd, __shfl_xor_sync(0xffffffffu, maxd, o));
@@ -313,23 +150,38 @@ __device__ int cholqr(const float* Min, float* Mout, int nrows, int r, int ldm, 
     }
   }
   __syncthreads();
-  // Mout = Min U^{-1}: forward substitution y U = m for every row
+  const int brk = sm.ibuf[0];
+  return brk;
+}
+
+// chol_apply: Mout = Min U^{-1} row by row (forward substitution y U = m).
+template <int R>
+__device__ void chol_apply(const float* Min, int ldin, float* Mout, int ldout, int nrows, const float* U,
+                           const SvdSmall& sm) {
   for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
     float m[R], y[R];
 #pragma unroll
-    for (int s = 0; s < R; ++s) m[s] = Min[(size_t)s * ldm + i];
+    for (int s = 0; s < R; ++s) m[s] = Min[(size_t)s * ldin + i];
 #pragma unroll
     for (int t = 0; t < R; ++t) {
       float v = m[t];
 #pragma unroll
-      for (int s = 0; s < t; ++s) v = fmaf(-y[s], Uout[s * R + t], v);
+      for (int s = 0; s < t; ++s) v = fmaf(-y[s], U[s * R + t], v);
       y[t] = v * sm.dinv[t];
     }
 #pragma unroll
-    for (int t = 0; t < R; ++t) Mout[(size_t)t * ldm + i] = y[t];
+    for (int t = 0; t < R; ++t) Mout[(size_t)t * ldout + i] = y[t];
   }
-  const int brk = sm.ibuf[0];
   __syncthreads();
+}
+
+// Cholesky QR of the nrows x r block Min (column-major, stride ldm) into Mout
+// (may alias): Min = Mout U with U upper triangular (written to Uout).
+template <int R>
+__device__ int cholqr(const float* Min, float* Mout, int nrows, int r, int ldm, float* Uout, const SvdSmall& sm) {
+  gram_block<R>(Min, nrows, ldm, r, sm.G);
+  const int brk = chol_factor<R>(sm.G, r, Uout, sm);
+  chol_apply<R>(Min, ldm, Mout, ldm, nrows, Uout, sm);
   return brk;
 }
 
@@ -344,278 +196,6 @@ __device__ __forceinline__ int rr_partner(int p, int k, int n) {
   if (p == k) return n - 1;
   int q = (2 * k - p) % (n - 1);
   return q < 0 ? q + n - 1 : q;
-}
-
-// CS: the core is held in shared memory (a compile-time property, so that
-// every core access compiles to a shared-memory load).
-template <int R, bool CS>
-__device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned char* smem) {
-  constexpr bool core_in_smem = CS;
-  State* st = d.st;
-  if (st->done || st->status) return;
-  const int k = st->k;
-  if (role > 0) {
-    // IRCUR-R drawing its own index sets: blocks 1 and 2 draw I_{k+1}, J_{k+1}
-    // on otherwise idle SMs while block 0 factorises the core (nothing in this
-    // iteration reads them; the next iteration's core kernel does)
-    const int axis = role - 1;
-    if (d.sampleAhead && k + 1 < d.max_iter) {
-      int* out = axis ? const_cast<int*>(d.J_all) + (int64_t)(k + 1) * d.nJ
-                      : const_cast<int*>(d.I_all) + (int64_t)(k + 1) * d.nI;
-      sample_subset(d.seed, k + 1, axis, axis ? d.n2 : d.n1, axis ? d.nJ : d.nI, out,
-                    *reinterpret_cast<SamplerSmem*>(smem));
-    }
-    return;
-  }
-  trace_start(d.trace, 3 * k + 1);
-  const int nI = d.nI, nJ = d.nJ, r = d.r;
-  const SvdLayout L = svd_layout(nI, nJ, d.ldCore, R, core_in_smem);
-  const int ldm = L.ldm, ldu = L.ldu;
-  float* Us = core_in_smem ? reinterpret_cast<float*>(smem + L.off_us) : d.core;
-  float* X = reinterpret_cast<float*>(smem + L.off_x);
-  float* Y = reinterpret_cast<float*>(smem + L.off_y);
-  float* Q = reinterpret_cast<float*>(smem + L.off_q);
-  float* part = reinterpret_cast<float*>(smem + L.off_part);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.off_bar);
-  SvdSmall sm;
-  {
-    float* p = reinterpret_cast<float*>(smem + L.off_small);
-    sm.G = p;
-    p += R * R;
-    sm.Rp = p;
-    p += R * R;
-    sm.U = p;
-    p += R * R;
-    sm.U2y = p;
-    p += R * R;
-    sm.U2x = p;
-    p += R * R;
-    sm.T = p;
-    p += R * R;
-    sm.Ut = p;
-    p += R * R;
-    sm.Vt = p;
-    p += R * R;
-    sm.tmp = p;
-    p += R * R;
-    sm.dinv = p;
-    p += 32;
-    sm.sig = p;
-    p += 32;
-    sm.red = p;
-    p += 64;
-    sm.ibuf = reinterpret_cast<int*>(p);
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-
-  // ---- core into shared memory: one bulk copy (TMA engine) of nI x ldu floats
-  const unsigned core_bytes = (unsigned)((size_t)nI * ldu * 4);
-  if (core_in_smem && threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-    mbar_arrive_expect_tx(bar, core_bytes);
-    bulk_g2s(Us, d.core, core_bytes, bar);
-  }
-  // ---- X, Y, Q zeroed (padding rows must read as zero); warm start X = B_k(:,J)^T
-  for (int q = threadIdx.x; q < 3 * R * ldm; q += blockDim.x) X[q] = 0.f;  // X, Y, Q are contiguous
-  __syncthreads();
-  for (int b = threadIdx.x; b < nJ; b += blockDim.x) {
-#pragma unroll
-    for (int t = 0; t < R; ++t) X[(size_t)t * ldm + b] = (t < r) ? d.BJt[(size_t)b * R + t] : 0.f;
-  }
-  __syncthreads();
-  int brk = cholqr<R>(X, X, nJ, r, ldm, sm.U, sm);
-  if (brk > 0) {  // first iteration (B_0 = 0) or a deficient factor: random start
-    for (int b = threadIdx.x; b < nJ; b += blockDim.x) {
-#pragma unroll
-      for (int t = 0; t < R; ++t)
-        X[(size_t)t * ldm + b] =
-            (t < r) ? hash_uniform(d.seed ^ 0x5bd1e995ull, ((uint64_t)k << 32) ^ (uint64_t)(b * R + t)) : 0.f;
-    }
-    __syncthreads();
-    cholqr<R>(X, X, nJ, r, ldm, sm.U, sm);
-  }
-  if (core_in_smem) {
-    bool ok = mbar_wait_bounded(bar, 0, d.spinLimit);
-    if (!ok) {
-      if (threadIdx.x == 0) atomicExch(&st->status, (int)IRCUR_ETIMEOUT);
-      mbar_wait_bounded(bar, 0, kSpinLimit);  // let the copy land before the block exits
-    }
-    if (!__syncthreads_and(ok)) return;
-  }
-
-  // ---- subspace iteration
-  int steps = 0;
-  bool converged = false;
-  float prev_res = 0.f;
-  while (true) {
-    ++steps;
-    core_times<R>(Us, ldu, nI, nJ, X, Y, part, ldm, L.pch);    // Y = core X
-    cholqr<R>(Y, Y, nI, r, ldm, sm.Rp, sm);                    // Y Rp = core X
-    core_t_times<R>(Us, ldu, nJ, nI, Y, Q, part, ldm, L.pch);  // Q = core^T Y
-    // ||Q - X Rp^T||_F^2 and ||Rp||_F^2 in one block reduction
-    float e2 = 0.f;
-    for (int b = threadIdx.x; b < nJ; b += blockDim.x) {
-      float xr[R];
-#pragma unroll
-      for (int t = 0; t < R; ++t) xr[t] = X[(size_t)t * ldm + b];
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        float v = Q[(size_t)t * ldm + b];
-#pragma unroll
-        for (int s2 = t; s2 < R; ++s2) v = fmaf(-xr[s2], sm.Rp[t * R + s2], v);
-        e2 = fmaf(v, v, e2);
-      }
-    }
-    float rc2 = 0.f;
-    if (threadIdx.x < R * R) rc2 = sm.Rp[threadIdx.x] * sm.Rp[threadIdx.x];
-    e2 = warp_sum(e2);
-    rc2 = warp_sum(rc2);
-    if (lane == 0) {
-      sm.red[warp] = e2;
-      sm.red[32 + warp] = rc2;
-    }
-    __syncthreads();
-    float E2 = 0.f, RC2 = 0.f;
-    for (int w = 0; w < nwarps; ++w) {
-      E2 += sm.red[w];
-      RC2 += sm.red[32 + w];
-    }
-    const float res = sqrtf(E2), nrm = sqrtf(RC2);
-    if (res <= 1e-6f * nrm || (steps > 1 && res > 0.5f * prev_res && res <= 1e-5f * nrm) || !(nrm > 0.f)) {
-      converged = true;
-      break;
-    }
-    if (steps >= d.svdMaxSteps) break;  // keep X, Y, Rp of the same step
-    prev_res = res;
-    cholqr<R>(Q, X, nJ, r, ldm, sm.U, sm);  // X = orth(core^T Y)
-  }
-
-  // ---- second CholQR passes; T = U2y Rp U2x^{-1} = Y^T core X for the new bases
-  cholqr<R>(Y, Y, nI, r, ldm, sm.U2y, sm);
-  cholqr<R>(X, X, nJ, r, ldm, sm.U2x, sm);
-  if (threadIdx.x < 32) {
-    const int s = threadIdx.x;
-    if (s < r) {
-      float row[R];  // (U2y Rp)(s, :)
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        float v = 0.f;
-        for (int u = 0; u < r; ++u) v = fmaf(sm.U2y[s * R + u], sm.Rp[u * R + t], v);
-        row[t] = v;
-      }
-      // T(s,:) U2x = row  (forward substitution; dropped pivots give zeros)
-      float tr[R];
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        float v = row[t];
-#pragma unroll
-        for (int u = 0; u < t; ++u) v = fmaf(-tr[u], sm.U2x[u * R + t], v);
-        tr[t] = (t < r) ? v * sm.dinv[t] : 0.f;
-      }
-#pragma unroll
-      for (int t = 0; t < R; ++t) sm.T[s * R + t] = tr[t];
-    }
-  }
-  __syncthreads();
-
-  // ---- numerical rank from the diagonal of the upper-triangular T (its
-  // singular values up to the off-diagonal part, which the iteration has
-  // driven below 1e-6 of ||T||), and the inverse of T on the kept pivots.
-  if (warp == 0) {
-    const float dabs = lane < r ? fabsf(sm.T[lane * R + lane]) : 0.f;
-    float dmax = dabs;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    const float tol = (float)(nI > nJ ? nI : nJ) * FLT_EPSILON * dmax;
-    const bool keep = lane < r && dabs > tol && dabs > 0.f;
-    const unsigned kmask = __ballot_sync(0xffffffffu, keep);
-    if (lane < r) {  // column `lane` of T^{-1} by back substitution, in registers
-      const int c = lane;
-      float x[R];
-#pragma unroll
-      for (int s2 = R - 1; s2 >= 0; --s2) {
-        float v = 0.f;
-        if (s2 <= c && ((kmask >> s2) & 1u)) {
-          v = (s2 == c) ? 1.f : 0.f;
-#pragma unroll
-          for (int u = s2 + 1; u < R; ++u)
-            if (u <= c) v = fmaf(-sm.T[s2 * R + u], x[u], v);
-          v = v / sm.T[s2 * R + s2];
-        }
-        x[s2] = v;
-      }
-#pragma unroll
-      for (int s2 = 0; s2 < R; ++s2) sm.tmp[s2 * R + c] = x[s2];
-      sm.sig[lane] = keep ? dabs : 0.f;
-    }
-    if (lane == 0) {
-      sm.ibuf[1] = __popc(kmask);
-      sm.ibuf[2] = (int)kmask;
-      for (int t = r; t < R; ++t) {
-        sm.sig[t] = 0.f;
-        for (int u = 0; u < R; ++u) sm.tmp[u * R + t] = 0.f;
-      }
-    }
-  }
-  __syncthreads();
-  const int rank = sm.ibuf[1];
-  const unsigned kmask = (unsigned)sm.ibuf[2];
-  // Outputs for the panel passes (U^+ = X T^{-1} Y^T, the pseudo-inverse of
-  // H_r(core) = Y T X^T):
-  //   W  = Y          (row pass: B_{k+1} = Y^T R, residual R - Y Y^T R),
-  //   Vs = X T^{-1}   (column pass: A_{k+1} = C X T^{-1}),
-  //   V  = X T^T      (column pass residual C - A_{k+1} T X^T = C - C X X^T).
-  for (int i = threadIdx.x; i < nI; i += blockDim.x) {
-#pragma unroll
-    for (int t = 0; t < R; ++t) d.W[(size_t)i * R + t] = ((kmask >> t) & 1u) ? Y[(size_t)t * ldm + i] : 0.f;
-  }
-  for (int b = threadIdx.x; b < nJ; b += blockDim.x) {
-    float x[R];
-#pragma unroll
-    for (int s2 = 0; s2 < R; ++s2) x[s2] = X[(size_t)s2 * ldm + b];
-#pragma unroll
-    for (int t = 0; t < R; ++t) {
-      float vp = 0.f, vr = 0.f;
-#pragma unroll
-      for (int s2 = 0; s2 < R; ++s2) {
-        vp = fmaf(x[s2], sm.tmp[s2 * R + t], vp);
-        vr = fmaf(x[s2], sm.T[t * R + s2], vr);
-      }
-      const bool kt = (kmask >> t) & 1u;
-      d.Vs[(size_t)b * R + t] = kt ? vp : 0.f;
-      d.V[(size_t)b * R + t] = kt ? vr : 0.f;
-    }
-  }
-  if (threadIdx.x < R) d.sigma[threadIdx.x] = sm.sig[threadIdx.x];
-  if (threadIdx.x < R * R) d.Tm[threadIdx.x] = sm.T[threadIdx.x];
-  if (threadIdx.x == 0) {
-    unsigned f = 0u;
-    if (rank < r) f |= IRCUR_FLAG_WRANK;
-    if (!converged) f |= IRCUR_FLAG_SVD_NOCONV;
-    if (f) atomicOr(&st->flags, f);
-    st->svd_steps += steps;
-    st->svd_last_steps = steps;
-  }
-  if (d.trace) {
-    __syncthreads();
-    trace_stop(d.trace, 3 * d.max_iter, 3 * k + 1);
-  }
-}
-
-template <int R, bool CS>
-__global__ void __launch_bounds__(SvdThreads<R>::value, 1) svd_kernel(IterDesc d) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  svd_body<R, CS>(d, blockIdx.x, smem);
-}
-
-// Batched form: blockIdx.x indexes `list` (the instances of one core-layout
-// group), blockIdx.y is the role (0: core SVD, 1 and 2: next index sets).
-template <int R, bool CS>
-__global__ void __launch_bounds__(SvdThreads<R>::value, 1) svd_batch_kernel(const IterDesc* __restrict__ ds,
-                                                                           const int* __restrict__ list) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  svd_body<R, CS>(ds[list[blockIdx.x]], blockIdx.y, smem);
 }
 
 // Singular values of the last Rayleigh-Ritz matrix T (the r largest singular
@@ -673,6 +253,539 @@ __global__ void sigma_kernel(const float* __restrict__ Tm, int r, float* __restr
   if (p < r) sigma[pos] = sg;
 }
 
+// ---------------------------------------------------------------------------
+// Core SVD on a thread-block cluster of kSvdCluster CTAs (distributed shared
+// memory).  The two-sided subspace iteration above, with the core split by
+// rows: CTA c holds rows [c mr, (c+1) mr) of the core in its shared
+// memory (one bulk copy), its own rows of Y and a full copy of X:
+//   Y_c = core_c X                 local rows, no exchange
+//   Gram(Y) = sum_c Y_c^T Y_c      R x R partials summed over the cluster
+//   Q = sum_c core_c^T Y_c         full-size partials summed over the cluster
+//                                  (every CTA forms the whole sum)
+//   Rp, residual, X = orth(Q)      replicated in every CTA
+// Every cluster-wide sum adds the CTAs' partials in rank order, so each CTA
+// holds bit-identical matrices and takes identical branch decisions; two
+// cluster barriers per step.  Outputs: W by rows of Y (each CTA its rows),
+// X T^{-1} and X T^T by slices of rows.
+constexpr int kSvdCluster = 8;
+constexpr int kCsvdThreads = 256;
+
+struct CsvdLayout {
+  int mr;       // core rows per CTA
+  int ldy;      // column stride of the local Y block (mr rounded up to 4)
+  int ldx;      // column stride of X and of the Q partial (nJ rounded up to 4)
+  int js;       // rows of the outputs X T^{-1}, X T^T each CTA writes
+  int pch;      // inner-dimension chunks of the local product
+  size_t off_uc, off_x, off_y, off_qp, off_qs, off_part, off_ra, off_stage, off_small, off_flag, off_bar, total;
+};
+
+__host__ __device__ inline CsvdLayout csvd_layout(int nI, int nJ, int ldu, int R, int cl) {
+  CsvdLayout L;
+  L.mr = (nI + cl - 1) / cl;
+  L.ldy = round_up4(L.mr > 0 ? L.mr : 1);
+  L.ldx = round_up4(nJ);
+  L.js = (nJ + cl - 1) / cl;
+  const size_t small = (size_t)kSmallMats * R * R * 4 + 4 * 32 * 4 + 64;
+  const size_t fixed = (size_t)L.mr * ldu * 4 + 3 * (size_t)R * L.ldx * 4 + (size_t)R * L.ldy * 4 +
+                       (1 + (size_t)cl) * ((size_t)R * R + 4) * 4 + small + 64;
+  int pch = 8;
+  while (pch > 1 && fixed + (size_t)pch * R * L.ldy * 4 > kSvdSmemBudget) --pch;
+  L.pch = pch;
+  size_t off = 0;
+  L.off_uc = off;
+  off += (size_t)L.mr * ldu * 4;
+  L.off_x = off;  // X | Y | Qp | Qs contiguous (zeroed together)
+  off += (size_t)R * L.ldx * 4;
+  L.off_y = off;
+  off += (size_t)R * L.ldy * 4;
+  L.off_qp = off;
+  off += (size_t)R * L.ldx * 4;
+  L.off_qs = off;  // Q = core^T Y, full (every CTA holds the sum of the partials)
+  off += (size_t)R * L.ldx * 4;
+  L.off_part = off;
+  off += (size_t)L.pch * R * L.ldy * 4;
+  L.off_ra = off;
+  off += ((size_t)R * R + 4) * 4;
+  L.off_stage = off;  // cl x (R R + 4): remote partials gathered before a fixed-order sum
+  off += (size_t)cl * ((size_t)R * R + 4) * 4;
+  L.off_small = off;
+  off += small;
+  L.off_flag = (off + 15) & ~(size_t)15;
+  off = L.off_flag + 16;
+  L.off_bar = off;
+  off += 16;
+  L.total = off;
+  return L;
+}
+
+size_t csvd_smem_bytes(int nI, int nJ, int Rpad) {
+  const CsvdLayout L = csvd_layout(nI, nJ, ld_core(nJ), Rpad, kSvdCluster);
+  return L.total > sizeof(SamplerSmem) ? L.total : sizeof(SamplerSmem);
+}
+
+// out(o, t) = sum_q U(o, q) in(q, t), o < nout (the CTA's core rows): two rows
+// per thread, inner chunks, fixed-order chunk sums.
+template <int R>
+__device__ void cl_rows_times(const float* __restrict__ U, int ldu, int nout, int nin, const float* __restrict__ in,
+                              int ldin, float* __restrict__ out, int ldo, float* part, int pch) {
+  constexpr int RB = 2;
+  const int G = (nout + RB - 1) / RB;
+  const int lanes = G > 0 ? (G + 31) & ~31 : 32;
+  int nch = (int)blockDim.x / lanes;
+  nch = nch < 1 ? 1 : (nch > pch ? pch : nch);
+  const int c = threadIdx.x / lanes, og = threadIdx.x % lanes;
+  const int nin4 = round_up4(nin);
+  const int qc = round_up4((nin4 + nch - 1) / nch);
+  if (c < nch && og < G) {
+    float acc[RB][R];
+#pragma unroll
+    for (int kk = 0; kk < RB; ++kk)
+#pragma unroll
+      for (int t = 0; t < R; ++t) acc[kk][t] = 0.f;
+    const int q0 = c * qc, q1 = q0 + qc < nin4 ? q0 + qc : nin4;
+    for (int q = q0; q < q1; q += 4) {
+      float4 u[RB];
+#pragma unroll
+      for (int kk = 0; kk < RB; ++kk) {
+        const int o = og + kk * G;
+        u[kk] = o < nout ? *reinterpret_cast<const float4*>(U + (size_t)o * ldu + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        const float4 x = *reinterpret_cast<const float4*>(in + (size_t)t * ldin + q);
+#pragma unroll
+        for (int kk = 0; kk < RB; ++kk)
+          acc[kk][t] = fmaf(u[kk].w, x.w, fmaf(u[kk].z, x.z, fmaf(u[kk].y, x.y, fmaf(u[kk].x, x.x, acc[kk][t]))));
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < RB; ++kk) {
+      const int o = og + kk * G;
+      if (o < nout) {
+#pragma unroll
+        for (int t = 0; t < R; ++t) part[((size_t)c * R + t) * ldo + o] = acc[kk][t];
+      }
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < R * nout; q += blockDim.x) {
+    const int t = q / nout, o = q - t * nout;
+    float s = 0.f;
+    for (int cc = 0; cc < nch; ++cc) s += part[((size_t)cc * R + t) * ldo + o];
+    out[(size_t)t * ldo + o] = s;
+  }
+  __syncthreads();
+}
+
+// out(j, t) = sum_i U(i, j) y(i, t) over the CTA's nin core rows, j < nout:
+// four columns per thread (16-byte core vectors, 16-byte broadcasts of Y).
+// Rows of y beyond nin read as zero.
+template <int R>
+__device__ void cl_cols_times(const float* __restrict__ U, int ldu, int nout, int nin, const float* __restrict__ y,
+                              int ldy, float* __restrict__ out, int ldo) {
+  const int G = (nout + 3) / 4;
+  const int nin4 = round_up4(nin);
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+    const int j = 4 * g;
+    float acc[4][R];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+      for (int t = 0; t < R; ++t) acc[e][t] = 0.f;
+    for (int i = 0; i < nin4; i += 4) {
+      float4 u[4];
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        u[kk] = (i + kk < nin) ? *reinterpret_cast<const float4*>(U + (size_t)(i + kk) * ldu + j)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        const float4 yv = *reinterpret_cast<const float4*>(y + (size_t)t * ldy + i);
+        acc[0][t] = fmaf(u[3].x, yv.w, fmaf(u[2].x, yv.z, fmaf(u[1].x, yv.y, fmaf(u[0].x, yv.x, acc[0][t]))));
+        acc[1][t] = fmaf(u[3].y, yv.w, fmaf(u[2].y, yv.z, fmaf(u[1].y, yv.y, fmaf(u[0].y, yv.x, acc[1][t]))));
+        acc[2][t] = fmaf(u[3].z, yv.w, fmaf(u[2].z, yv.z, fmaf(u[1].z, yv.y, fmaf(u[0].z, yv.x, acc[2][t]))));
+        acc[3][t] = fmaf(u[3].w, yv.w, fmaf(u[2].w, yv.z, fmaf(u[1].w, yv.y, fmaf(u[0].w, yv.x, acc[3][t]))));
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (j + e < nout) {
+#pragma unroll
+        for (int t = 0; t < R; ++t) out[(size_t)t * ldo + j + e] = acc[e][t];
+      }
+  }
+  __syncthreads();
+}
+
+// dst[q] = sum over the cluster's CTAs (rank order) of src[q], q < count: the
+// kSvdCluster x count remote values are read in parallel into `stage`, then
+// every sum is formed in rank order.  Call after a cluster barrier that
+// follows every CTA's write of src.
+__device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, float* src, float* dst, int count, float* stage) {
+  for (int q = threadIdx.x; q < kSvdCluster * count; q += blockDim.x) {
+    const int c = q / count, i = q - c * count;
+    stage[q] = cl.map_shared_rank(src, c)[i];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < kSvdCluster; ++c) s += stage[c * count + i];
+    dst[i] = s;
+  }
+  __syncthreads();
+}
+
+template <int R>
+__device__ __forceinline__ void csvd_body(const IterDesc& d, int role, unsigned char* smem) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int crank = (int)cl.block_rank();
+  constexpr int ncl = kSvdCluster;
+  State* st = d.st;
+  if (st->done || st->status) return;  // the same for every CTA: the state is fixed during the launch
+  const int k = st->k;
+  if (role > 0) {
+    // IRCUR-R drawing its own index sets: rank 0 of the clusters of roles 1
+    // and 2 draws I_{k+1}, J_{k+1} while the role-0 cluster factorises the core
+    const int axis = role - 1;
+    if (crank == 0 && d.sampleAhead && k + 1 < d.max_iter) {
+      int* out = axis ? const_cast<int*>(d.J_all) + (int64_t)(k + 1) * d.nJ
+                      : const_cast<int*>(d.I_all) + (int64_t)(k + 1) * d.nI;
+      sample_subset(d.seed, k + 1, axis, axis ? d.n2 : d.n1, axis ? d.nJ : d.nI, out,
+                    *reinterpret_cast<SamplerSmem*>(smem));
+    }
+    return;
+  }
+  if (crank == 0) trace_start(d.trace, 3 * k + 1);
+  const int nI = d.nI, nJ = d.nJ, r = d.r, ldu = d.ldCore;
+  const CsvdLayout L = csvd_layout(nI, nJ, ldu, R, ncl);
+  const int row0 = crank * L.mr;
+  const int nrow = nI - row0 < L.mr ? (nI - row0 > 0 ? nI - row0 : 0) : L.mr;
+  const int col0 = crank * L.js;
+  const int ncol = nJ - col0 < L.js ? (nJ - col0 > 0 ? nJ - col0 : 0) : L.js;
+  float* Uc = reinterpret_cast<float*>(smem + L.off_uc);
+  float* X = reinterpret_cast<float*>(smem + L.off_x);
+  float* Y = reinterpret_cast<float*>(smem + L.off_y);
+  float* Qp = reinterpret_cast<float*>(smem + L.off_qp);
+  float* Qs = reinterpret_cast<float*>(smem + L.off_qs);
+  float* part = reinterpret_cast<float*>(smem + L.off_part);
+  float* ra = reinterpret_cast<float*>(smem + L.off_ra);  // Gram(Y) partial
+  float* stage = reinterpret_cast<float*>(smem + L.off_stage);
+  int* flag = reinterpret_cast<int*>(smem + L.off_flag);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.off_bar);
+  SvdSmall sm;
+  {
+    float* p = reinterpret_cast<float*>(smem + L.off_small);
+    sm.G = p;
+    p += R * R;
+    sm.Rp = p;
+    p += R * R;
+    sm.U = p;
+    p += R * R;
+    sm.U2y = p;
+    p += R * R;
+    sm.U2x = p;
+    p += R * R;
+    sm.T = p;
+    p += R * R;
+    sm.Ut = p;
+    p += R * R;
+    sm.Vt = p;
+    p += R * R;
+    sm.tmp = p;
+    p += R * R;
+    sm.dinv = p;
+    p += 32;
+    sm.sig = p;
+    p += 32;
+    sm.red = p;
+    p += 64;
+    sm.ibuf = reinterpret_cast<int*>(p);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  // ---- this CTA's core rows into shared memory: one bulk copy
+  const unsigned bytes = (unsigned)((size_t)nrow * ldu * 4);
+  if (nrow > 0 && threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_g2s(Uc, d.core + (size_t)row0 * ldu, bytes, bar);
+  }
+  // ---- X, Y, Qp, Qs zeroed (padding rows read as zero); X = B_k(:,J)^T
+  {
+    const size_t nz = (L.off_part - L.off_x) / 4;
+    for (size_t q = threadIdx.x; q < nz; q += blockDim.x) X[q] = 0.f;
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nJ; b += blockDim.x) {
+#pragma unroll
+    for (int t = 0; t < R; ++t) X[(size_t)t * L.ldx + b] = (t < r) ? d.BJt[(size_t)b * R + t] : 0.f;
+  }
+  __syncthreads();
+  int brk = cholqr<R>(X, X, nJ, r, L.ldx, sm.U, sm);
+  if (brk > 0) {  // first iteration (B_0 = 0) or a deficient factor: random start
+    for (int b = threadIdx.x; b < nJ; b += blockDim.x) {
+#pragma unroll
+      for (int t = 0; t < R; ++t)
+        X[(size_t)t * L.ldx + b] =
+            (t < r) ? hash_uniform(d.seed ^ 0x5bd1e995ull, ((uint64_t)k << 32) ^ (uint64_t)(b * R + t)) : 0.f;
+    }
+    __syncthreads();
+    cholqr<R>(X, X, nJ, r, L.ldx, sm.U, sm);
+  }
+  bool ok = true;
+  if (nrow > 0) {
+    ok = mbar_wait_bounded(bar, 0, d.spinLimit);
+    if (!ok) {
+      if (threadIdx.x == 0) atomicExch(&st->status, (int)IRCUR_ETIMEOUT);
+      mbar_wait_bounded(bar, 0, kSpinLimit);  // let the copy land before the block exits
+    }
+  }
+  ok = __syncthreads_and(ok);
+  if (threadIdx.x == 0) *flag = ok ? 0 : 1;
+  cl.sync();
+  {
+    const int mine = threadIdx.x < ncl ? *cl.map_shared_rank(flag, (int)threadIdx.x) : 0;
+    if (__syncthreads_or(mine)) {
+      cl.sync();  // nobody leaves while others read its flag
+      return;
+    }
+  }
+
+  // ---- subspace iteration.  With Y = (core X) Rp^{-1}, core^T Y =
+  // (core^T core X) Rp^{-1}: the transposed product runs on the raw local
+  // rows in the same phase as their Gram partial, and Rp^{-1} is applied to
+  // the reduced Q.  Two cluster barriers per step: partials written, partials
+  // read.
+  int steps = 0;
+  bool converged = false;
+  float prev_res = 0.f;
+  while (true) {
+    ++steps;
+    cl_rows_times<R>(Uc, ldu, nrow, nJ, X, L.ldx, Y, L.ldy, part, L.pch);  // Y_c = core_c X (raw)
+    gram_block<R>(Y, nrow, L.ldy, r, ra);                                  // Y_c^T Y_c
+    cl_cols_times<R>(Uc, ldu, nJ, nrow, Y, L.ldy, Qp, L.ldx);              // core_c^T Y_c
+    cl.sync();  // (1) partials written
+    cluster_sum(cl, ra, sm.G, R * R, stage);
+    for (int q = threadIdx.x; q < R * nJ; q += blockDim.x) {  // Q = sum of the partials, rank order
+      const int t = q / nJ, b = q - t * nJ;
+      const size_t at = (size_t)t * L.ldx + b;
+      float v[ncl];
+#pragma unroll
+      for (int c = 0; c < ncl; ++c) v[c] = cl.map_shared_rank(Qp, c)[at];  // all in flight
+      float sacc = 0.f;
+#pragma unroll
+      for (int c = 0; c < ncl; ++c) sacc += v[c];
+      Qs[at] = sacc;
+    }
+    cl.sync();  // (2) partials read: they may be overwritten
+    chol_factor<R>(sm.G, r, sm.Rp, sm);                        // Y Rp = core X
+    chol_apply<R>(Qs, L.ldx, Qs, L.ldx, nJ, sm.Rp, sm);        // Q = core^T Y
+    // ||Q - X Rp^T||_F^2 and ||Rp||_F^2
+    float e2 = 0.f;
+    for (int b = threadIdx.x; b < nJ; b += blockDim.x) {
+      float xr[R];
+#pragma unroll
+      for (int t = 0; t < R; ++t) xr[t] = X[(size_t)t * L.ldx + b];
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        float v = Qs[(size_t)t * L.ldx + b];
+#pragma unroll
+        for (int s2 = t; s2 < R; ++s2) v = fmaf(-xr[s2], sm.Rp[t * R + s2], v);
+        e2 = fmaf(v, v, e2);
+      }
+    }
+    float rc2 = 0.f;
+    if (threadIdx.x < R * R) rc2 = sm.Rp[threadIdx.x] * sm.Rp[threadIdx.x];
+    e2 = warp_sum(e2);
+    rc2 = warp_sum(rc2);
+    if (lane == 0) {
+      sm.red[warp] = e2;
+      sm.red[32 + warp] = rc2;
+    }
+    __syncthreads();
+    float E2 = 0.f, RC2 = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      E2 += sm.red[w];
+      RC2 += sm.red[32 + w];
+    }
+    const float res = sqrtf(E2), nrm = sqrtf(RC2);
+    if (res <= 1e-6f * nrm || (steps > 1 && res > 0.5f * prev_res && res <= 1e-5f * nrm) || !(nrm > 0.f)) {
+      converged = true;
+      break;
+    }
+    if (steps >= d.svdMaxSteps) break;  // keep X, Y, Rp of the same step
+    prev_res = res;
+    cholqr<R>(Qs, X, nJ, r, L.ldx, sm.U, sm);  // X = orth(core^T Y), in every CTA
+  }
+  // Y of the last step: Y = (core X) Rp^{-1} (sm.dinv still belongs to Rp)
+  chol_apply<R>(Y, L.ldy, Y, L.ldy, nrow, sm.Rp, sm);
+
+  // ---- second CholQR passes (Y over the cluster, X replicated); T = U2y Rp U2x^{-1}
+  gram_block<R>(Y, nrow, L.ldy, r, ra);
+  cl.sync();
+  cluster_sum(cl, ra, sm.G, R * R, stage);
+  chol_factor<R>(sm.G, r, sm.U2y, sm);
+  chol_apply<R>(Y, L.ldy, Y, L.ldy, nrow, sm.U2y, sm);
+  cholqr<R>(X, X, nJ, r, L.ldx, sm.U2x, sm);
+  if (threadIdx.x < 32) {
+    const int s2 = threadIdx.x;
+    if (s2 < r) {
+      float row[R];  // (U2y Rp)(s2, :)
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        float v = 0.f;
+        for (int u = 0; u < r; ++u) v = fmaf(sm.U2y[s2 * R + u], sm.Rp[u * R + t], v);
+        row[t] = v;
+      }
+      float tr[R];  // T(s2,:) U2x = row (forward substitution; dropped pivots give zeros)
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        float v = row[t];
+#pragma unroll
+        for (int u = 0; u < t; ++u) v = fmaf(-tr[u], sm.U2x[u * R + t], v);
+        tr[t] = (t < r) ? v * sm.dinv[t] : 0.f;
+      }
+#pragma unroll
+      for (int t = 0; t < R; ++t) sm.T[s2 * R + t] = tr[t];
+    }
+  }
+  __syncthreads();
+  // ---- numerical rank from the diagonal of T, and T^{-1} on the kept pivots
+  if (warp == 0) {
+    const float dabs = lane < r ? fabsf(sm.T[lane * R + lane]) : 0.f;
+    float dmax = dabs;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    const float tol = (float)(nI > nJ ? nI : nJ) * FLT_EPSILON * dmax;
+    const bool keep = lane < r && dabs > tol && dabs > 0.f;
+    const unsigned kmask = __ballot_sync(0xffffffffu, keep);
+    if (lane < r) {
+      const int c = lane;
+      float x[R];
+#pragma unroll
+      for (int s2 = R - 1; s2 >= 0; --s2) {
+        float v = 0.f;
+        if (s2 <= c && ((kmask >> s2) & 1u)) {
+          v = (s2 == c) ? 1.f : 0.f;
+#pragma unroll
+          for (int u = s2 + 1; u < R; ++u)
+            if (u <= c) v = fmaf(-sm.T[s2 * R + u], x[u], v);
+          v = v / sm.T[s2 * R + s2];
+        }
+        x[s2] = v;
+      }
+#pragma unroll
+      for (int s2 = 0; s2 < R; ++s2) sm.Ut[s2 * R + c] = x[s2];
+      sm.sig[lane] = keep ? dabs : 0.f;
+    }
+    if (lane == 0) {
+      sm.ibuf[1] = __popc(kmask);
+      sm.ibuf[2] = (int)kmask;
+      for (int t = r; t < R; ++t) {
+        sm.sig[t] = 0.f;
+        for (int u = 0; u < R; ++u) sm.Ut[u * R + t] = 0.f;
+      }
+    }
+  }
+  __syncthreads();
+  const int rank = sm.ibuf[1];
+  const unsigned kmask = (unsigned)sm.ibuf[2];
+  // Outputs (U^+ = X T^{-1} Y^T): W = Y by this CTA's rows; Vs = X T^{-1} and
+  // V = X T^T by this CTA's slice.
+  for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
+#pragma unroll
+    for (int t = 0; t < R; ++t)
+      d.W[(size_t)(row0 + i) * R + t] = ((kmask >> t) & 1u) ? Y[(size_t)t * L.ldy + i] : 0.f;
+  }
+  for (int bb = threadIdx.x; bb < ncol; bb += blockDim.x) {
+    const int b = col0 + bb;
+    float x[R];
+#pragma unroll
+    for (int s2 = 0; s2 < R; ++s2) x[s2] = X[(size_t)s2 * L.ldx + b];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      float vp = 0.f, vr = 0.f;
+#pragma unroll
+      for (int s2 = 0; s2 < R; ++s2) {
+        vp = fmaf(x[s2], sm.Ut[s2 * R + t], vp);
+        vr = fmaf(x[s2], sm.T[t * R + s2], vr);
+      }
+      const bool kt = (kmask >> t) & 1u;
+      d.Vs[(size_t)b * R + t] = kt ? vp : 0.f;
+      d.V[(size_t)b * R + t] = kt ? vr : 0.f;
+    }
+  }
+  if (crank == 0) {
+    if (threadIdx.x < R) d.sigma[threadIdx.x] = sm.sig[threadIdx.x];
+    if (threadIdx.x < R * R) d.Tm[threadIdx.x] = sm.T[threadIdx.x];
+    if (threadIdx.x == 0) {
+      unsigned f = 0u;
+      if (rank < r) f |= IRCUR_FLAG_WRANK;
+      if (!converged) f |= IRCUR_FLAG_SVD_NOCONV;
+      if (f) atomicOr(&st->flags, f);
+      st->svd_steps += steps;
+      st->svd_last_steps = steps;
+    }
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+  if (crank == 0 && d.trace) {
+    __syncthreads();
+    trace_stop(d.trace, 3 * d.max_iter, 3 * k + 1);
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(kCsvdThreads, 1) csvd_kernel(IterDesc d) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  csvd_body<R>(d, blockIdx.y, smem);
+}
+
+// Batched form: cluster blockIdx.x / kSvdCluster factorises instance
+// list[blockIdx.x / kSvdCluster]; blockIdx.y is the role.
+template <int R>
+__global__ void __launch_bounds__(kCsvdThreads, 1) csvd_batch_kernel(const IterDesc* __restrict__ ds,
+                                                                    const int* __restrict__ list) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  csvd_body<R>(ds[list[blockIdx.x / kSvdCluster]], blockIdx.y, smem);
+}
+
+template <typename... Args>
+static cudaError_t launch_cluster(void (*kernel)(Args...), dim3 grid, size_t smem, cudaStream_t s,
+                                  Args... args) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(kCsvdThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kSvdCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <int R>
+static cudaError_t launch_csvd_r(const IterDesc& d, cudaStream_t s) {
+  const size_t bytes = csvd_smem_bytes(d.nI, d.nJ, R);
+  return launch_cluster(csvd_kernel<R>, dim3(kSvdCluster, 1 + (d.sampleAhead ? 2 : 0), 1), bytes, s, d);
+}
+
+template <int R>
+static cudaError_t launch_csvd_batch_r(const BatchLaunch& b, cudaStream_t s) {
+  const int n = b.svd_n[0] + b.svd_n[1];
+  if (n == 0) return cudaSuccess;
+  return launch_cluster(csvd_batch_kernel<R>, dim3(kSvdCluster * n, b.svd_roles, 1), b.svd_smem[0], s, b.ds,
+                        b.svd_list[0]);
+}
+
 template <int R>
 static cudaError_t launch_sigma_r(const float* Tm, int r, float* sigma, cudaStream_t s) {
   sigma_kernel<R><<<1, 32, 0, s>>>(Tm, r, sigma);
@@ -699,41 +812,12 @@ cudaError_t launch_sigma(const float* Tm, int r, int Rpad, float* sigma, cudaStr
 
 template <int R>
 static cudaError_t launch_svd_r(const IterDesc& d, cudaStream_t s) {
-  bool in_smem = false;
-  const size_t bytes = svd_smem_bytes(d.nI, d.nJ, R, &in_smem);
-  if (in_smem) {
-    cudaError_t e = cudaFuncSetAttribute(svd_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    svd_kernel<R, true><<<1 + (d.sampleAhead ? 2 : 0), SvdThreads<R>::value, bytes, s>>>(d);
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(svd_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    svd_kernel<R, false><<<1 + (d.sampleAhead ? 2 : 0), SvdThreads<R>::value, bytes, s>>>(d);
-  }
-  return cudaGetLastError();
+  return launch_csvd_r<R>(d, s);
 }
 
 template <int R>
 static cudaError_t launch_svd_batch_r(const BatchLaunch& b, cudaStream_t s) {
-  if (b.svd_n[0] > 0) {
-    cudaError_t e = cudaFuncSetAttribute(svd_batch_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)b.svd_smem[0]);
-    if (e != cudaSuccess) return e;
-    svd_batch_kernel<R, true><<<dim3(b.svd_n[0], b.svd_roles), SvdThreads<R>::value, b.svd_smem[0], s>>>(
-        b.ds, b.svd_list[0]);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  if (b.svd_n[1] > 0) {
-    cudaError_t e = cudaFuncSetAttribute(svd_batch_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)b.svd_smem[1]);
-    if (e != cudaSuccess) return e;
-    svd_batch_kernel<R, false><<<dim3(b.svd_n[1], b.svd_roles), SvdThreads<R>::value, b.svd_smem[1], s>>>(
-        b.ds, b.svd_list[1]);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  return launch_csvd_batch_r<R>(b, s);
 }
 
 cudaError_t launch_svd_batch(const BatchLaunch& b, int Rpad, cudaStream_t s) {
