@@ -145,9 +145,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def rank_seed(seed, rank):
+    """Each rank solves its own independent instance (weak scaling, no exchange)."""
+    return seed + 1000 * rank
+
+
 def make_input(a, rank):
     from paper_2010_07422_gb300 import synth
-    return synth.planted(a.n, a.n, a.r, a.alpha, seed=a.seed + 1000 * rank)
+    return synth.planted(a.n, a.n, a.r, a.alpha, seed=rank_seed(a.seed, rank))
+
+
+def aggregate(dist, world, elapsed, units, device):
+    """Whole-job figures over the ranks: the slowest rank's elapsed time and the
+    units every rank processed (one all-reduce each; no data-path collective)."""
+    if world <= 1:
+        return float(elapsed), float(units)
+    import torch
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
 
 
 def cpu_oracle_sample(p, a, seconds, max_steps=None):
@@ -430,14 +448,7 @@ def main():
     recon_ms = [s.elapsed_time(e) for s, e in rec]
     solve_ms = [s.elapsed_time(e) for s, e in sol]
     my_iters = float(sum(iters))
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        it = torch.tensor([my_iters], dtype=torch.float64, device="cuda")
-        dist.all_reduce(it, op=dist.ReduceOp.SUM)
-        total_ms_max, all_iters = float(t.item()), float(it.item())
-    else:
-        total_ms_max, all_iters = total_ms, my_iters
+    total_ms_max, all_iters = aggregate(dist, world, total_ms, my_iters, "cuda")
 
     # accuracy of the last step against the planted truth, on sampled entries
     rng = np.random.default_rng(0)
@@ -505,12 +516,7 @@ def main():
             r2 = ir.ircur_solve_host(e2e_solver._ctx, Dh, Lh, Sh)
             e_iters += r2.iters
         el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            it = torch.tensor([float(e_iters)], dtype=torch.float64, device="cuda")
-            dist.all_reduce(it, op=dist.ReduceOp.SUM)
-            el, e_iters = float(t.item()), float(it.item())
+        el, e_iters = aggregate(dist, world, el, e_iters, "cuda")
         e2e = {"value": e_iters / el, "unit": "iters/s", "h2d_bytes_per_step": 4 * n * n,
                "d2h_bytes_per_step": 8 * n * n, "ms_per_step": 1e3 * el / a.e2e_steps,
                "api": "ircur_solve_host (pinned host D in, dense L and S out)"}
