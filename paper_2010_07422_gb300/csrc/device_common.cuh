@@ -139,6 +139,13 @@ __device__ __forceinline__ void cp_async_wait_group() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Programmatic dependent launch: a primary grid lets the next kernel of the
+// stream start once every CTA has executed launch_dependents (or exited); the
+// dependent grid's griddepcontrol.wait blocks until the primary grid has
+// completed and its memory operations are visible.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Nanosecond device clock (comparable across SMs).
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;

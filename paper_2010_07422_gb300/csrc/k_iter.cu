@@ -14,6 +14,8 @@
 // and L_{k+1}(:,J) = C V_r V_r^T, so the stopping criterion of Sec. 3.3 is
 // e = (||R - W_r W_r^T R||_F + ||C - C V_r V_r^T||_F) / (||D_{I,:}||_F + ||D_{:,J}||_F),
 // each residual formed explicitly (no difference of squared norms).
+#include <string.h>
+
 #include "device_common.cuh"
 #include "ircur_internal.cuh"
 
@@ -98,7 +100,9 @@ __global__ void __launch_bounds__(256) core_batch_kernel(const IterDesc* __restr
 // A block owns a contiguous run of tiles (the grid is the number of resident
 // blocks); consecutive tiles of one instance and side form a segment whose
 // m x R side, projection and reconstruction matrices are staged in shared
-// memory once.  Tiles are double-buffered: the 16-byte asynchronous copies of
+// memory once.  The kernel is launched as a programmatic dependent of the core
+// SVD: its blocks start while the SVD (one cluster) runs, stage and threshold
+// their first tile, and wait for the SVD only before the projections.  Tiles are double-buffered: the 16-byte asynchronous copies of
 // tile t+1 (one small segment per gathered panel row) fly while tile t is
 // computed.  Within a tile, warp h owns row share h and lane c column c
 // (conflict-free tile accesses, broadcast reads of the small matrices); the
@@ -210,27 +214,41 @@ __device__ __forceinline__ void pass_stage_tile(const IterDesc& d, int k, int lt
   }
 }
 
-// The m x R side, projection and reconstruction matrices of one segment
-// (rows padded to RX columns with zeros).
+// The m x R side matrix of one segment (A_k(I,:) | B_k(:,J)^T: outputs of the
+// core kernel), rows padded to RX columns with zeros.
 template <int R, bool COL>
-__device__ __forceinline__ void pass_stage_small(const IterDesc& d, const PassLayout& L) {
+__device__ __forceinline__ void pass_stage_side(const IterDesc& d, const PassLayout& L) {
   constexpr int RX = (R + 3) & ~3;
   const int m = COL ? d.nJ : d.nI;
   const float* sideG = COL ? d.BJt : d.AI;
+  for (int q = threadIdx.x; q < m * RX; q += blockDim.x) {
+    const int a = q / RX, t = q - a * RX;
+    L.side[q] = t < R ? sideG[a * R + t] : 0.f;
+  }
+}
+
+// The m x R projection and reconstruction matrices of one segment (Y | X T^{-1}
+// and X T^T: outputs of the core SVD, which may still be running: wait for it).
+template <int R, bool COL>
+__device__ __forceinline__ void pass_stage_proj(const IterDesc& d, const PassLayout& L, int k) {
+  constexpr int RX = (R + 3) & ~3;
+  pdl_wait();
+  trace_start(d.trace, 3 * k + 2);  // the pass's span starts where it no longer waits for the SVD
+  const int m = COL ? d.nJ : d.nI;
   const float* projG = COL ? d.Vs : d.W;
   for (int q = threadIdx.x; q < m * RX; q += blockDim.x) {
     const int a = q / RX, t = q - a * RX;
     const bool in = t < R;
-    L.side[q] = in ? sideG[a * R + t] : 0.f;
     L.proj[q] = in ? projG[a * R + t] : 0.f;
     if (COL) L.recon[q] = in ? d.V[a * R + t] : 0.f;
   }
+  __syncthreads();
 }
 
 // One tile: thresholded panel values, projections, explicit residuals.
 template <int R, bool COL, bool BF>
 __device__ __forceinline__ void pass_tile(const IterDesc& d, int k, float zeta, int lt, const PassLayout& L,
-                                          unsigned char* tileP) {
+                                          unsigned char* tileP, bool stage_proj) {
   // FP32 panels: the tile is overwritten with D - S; BF16 panels: D - S goes
   // to the FP32 work buffer
   float* tileS = BF ? L.vbuf : reinterpret_cast<float*>(tileP);
@@ -258,20 +276,17 @@ __device__ __forceinline__ void pass_tile(const IterDesc& d, int k, float zeta, 
   const float msk = live ? 1.f : 0.f;
   const int a0 = h * m / kPassWarps, a1 = (h + 1) * m / kPassWarps;
   float den = 0.f;
+  // 1. thresholded values D - S and ||D||^2 (needs only the core kernel's outputs)
   for (int a = a0; a < a1; ++a) {
     float* cell = tileS + (size_t)a * kPanelCols + lane;
-    float sr[R], pr[R];
+    float sr[R];
 #pragma unroll
     for (int t4 = 0; t4 < RX / 4; ++t4) {
       const float4 sv = *reinterpret_cast<const float4*>(side + (size_t)a * RX + 4 * t4);
-      const float4 pv = *reinterpret_cast<const float4*>(proj + (size_t)a * RX + 4 * t4);
-      const float s4[4] = {sv.x, sv.y, sv.z, sv.w}, p4[4] = {pv.x, pv.y, pv.z, pv.w};
+      const float s4[4] = {sv.x, sv.y, sv.z, sv.w};
 #pragma unroll
       for (int e = 0; e < 4; ++e)
-        if (4 * t4 + e < R) {
-          sr[4 * t4 + e] = s4[e];
-          pr[4 * t4 + e] = p4[e];
-        }
+        if (4 * t4 + e < R) sr[4 * t4 + e] = s4[e];
     }
     const float l = lowrank_entry<R>(sr, vec);
     float dv;
@@ -286,6 +301,24 @@ __device__ __forceinline__ void pass_tile(const IterDesc& d, int k, float zeta, 
     const float v = panel_value(dv, l, zeta) * msk;
     *cell = v;
     den = fmaf(dv, dv, den);
+  }
+  // 2. the projections (need the core SVD's outputs)
+  if (COL) {
+    if (stage_proj) pass_stage_proj<R, true>(d, L, k);
+  } else {
+    if (stage_proj) pass_stage_proj<R, false>(d, L, k);
+  }
+  for (int a = a0; a < a1; ++a) {
+    const float v = tileS[(size_t)a * kPanelCols + lane];
+    float pr[R];
+#pragma unroll
+    for (int t4 = 0; t4 < RX / 4; ++t4) {
+      const float4 pv = *reinterpret_cast<const float4*>(proj + (size_t)a * RX + 4 * t4);
+      const float p4[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (4 * t4 + e < R) pr[4 * t4 + e] = p4[e];
+    }
 #pragma unroll
     for (int t = 0; t < R; ++t) acc[t] = fmaf(pr[t], v, acc[t]);
   }
@@ -455,6 +488,7 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
   if (cur.active) stage(cur, L.tiles);
   cp_async_commit();
   int seg_inst = -1, seg_col = -1, seg_k = 0, run = 0;
+  bool proj_staged = false;
   float zeta = 0.f;
   for (int t = t0; t < t1; ++t) {
     if (t > t0) cur = locate(t, inst);
@@ -499,11 +533,11 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
       seg_col = cur.col;
       seg_k = cur.k;
       zeta = (float)d.st->zeta;
-      trace_start(d.trace, 3 * seg_k + 2);
       if (cur.col)
-        pass_stage_small<R, true>(d, L);
+        pass_stage_side<R, true>(d, L);
       else
-        pass_stage_small<R, false>(d, L);
+        pass_stage_side<R, false>(d, L);
+      proj_staged = false;
     }
     if (pre)
       cp_async_wait_group<1>();
@@ -511,9 +545,10 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
       cp_async_wait_group<0>();
     __syncthreads();
     if (cur.col)
-      pass_tile<R, true, BF>(d, seg_k, zeta, cur.lt, L, L.tiles + (size_t)b * L.tile_bytes);
+      pass_tile<R, true, BF>(d, seg_k, zeta, cur.lt, L, L.tiles + (size_t)b * L.tile_bytes, !proj_staged);
     else
-      pass_tile<R, false, BF>(d, seg_k, zeta, cur.lt, L, L.tiles + (size_t)b * L.tile_bytes);
+      pass_tile<R, false, BF>(d, seg_k, zeta, cur.lt, L, L.tiles + (size_t)b * L.tile_bytes, !proj_staged);
+    proj_staged = true;
     __syncthreads();
     pass_tile_sums(d, t - (BATCH ? tile_base[cur.inst] : 0), L);
     ++run;
@@ -608,6 +643,24 @@ static int pass_grid(const void* fn, size_t smem) {
 }
 cudaError_t launch_svd(const IterDesc& d, int Rpad, cudaStream_t s);
 
+// A launch that may overlap the tail of the previous kernel in the stream
+// (programmatic stream serialization; the kernel waits with pdl_wait()).
+template <typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(Args...), int grid, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)grid, 1, 1);
+  cfg.blockDim = dim3(kPassThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <int R>
 static cudaError_t launch_iter_r(const IterDesc& d, cudaStream_t s) {
   {
@@ -628,15 +681,13 @@ static cudaError_t launch_iter_r(const IterDesc& d, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     int grid = d.passGrid > 0 ? d.passGrid : pass_grid((const void*)pass_kernel<R, true>, bytes);
     if (grid > total) grid = total;
-    pass_kernel<R, true><<<grid, kPassThreads, bytes, s>>>(d, nbuf);
-    return cudaGetLastError();
+    return launch_pdl(pass_kernel<R, true>, grid, bytes, s, d, nbuf);
   }
   cudaError_t e = cudaFuncSetAttribute(pass_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   int grid = d.passGrid > 0 ? d.passGrid : pass_grid((const void*)pass_kernel<R, false>, bytes);
   if (grid > total) grid = total;
-  pass_kernel<R, false><<<grid, kPassThreads, bytes, s>>>(d, nbuf);
-  return cudaGetLastError();
+  return launch_pdl(pass_kernel<R, false>, grid, bytes, s, d, nbuf);
 }
 
 template <int R>

@@ -739,6 +739,9 @@ __device__ __forceinline__ void csvd_body(const IterDesc& d, int role, unsigned 
 template <int R>
 __global__ void __launch_bounds__(kCsvdThreads, 1) csvd_kernel(IterDesc d) {
   extern __shared__ __align__(16) unsigned char smem[];
+  // every CTA is resident from here on: the pass kernel may start on the
+  // other SMs (it waits for this grid before reading its outputs)
+  pdl_launch_dependents();
   csvd_body<R>(d, blockIdx.y, smem);
 }
 
