@@ -338,7 +338,10 @@ static ircur_status build_graph(ircur_ctx* c, const IterDesc& d0) {
   d.cond = (unsigned long long)h;
   IRCUR_CK(cudaStreamBeginCaptureToGraph(c->capture_stream, body, nullptr, nullptr, 0,
                                          cudaStreamCaptureModeRelaxed));
-  cudaError_t le = launch_iteration(d, c->Rpad, c->capture_stream);
+  // kGraphUnroll iterations per trip of the while node (the kernels of an
+  // iteration that follows convergence return at once)
+  cudaError_t le = cudaSuccess;
+  for (int u = 0; u < kGraphUnroll && le == cudaSuccess; ++u) le = launch_iteration(d, c->Rpad, c->capture_stream);
   cudaGraph_t captured = nullptr;
   cudaError_t ce = cudaStreamEndCapture(c->capture_stream, &captured);
   if (le != cudaSuccess) {
@@ -1056,7 +1059,8 @@ static ircur_status batch_build_graph(ircur_batch* b, const float* const* D, con
     set_error("batch graph: body capture", e);
     return batch_abort_capture(b, cs, IRCUR_ECUDA);
   }
-  cudaError_t le = launch_batch_iteration(bl, b->Rpad, b->body_stream);
+  cudaError_t le = cudaSuccess;
+  for (int u = 0; u < kGraphUnroll && le == cudaSuccess; ++u) le = launch_batch_iteration(bl, b->Rpad, b->body_stream);
   cudaGraph_t body = nullptr;
   cudaError_t be = cudaStreamEndCapture(b->body_stream, &body);
   if (le != cudaSuccess || be != cudaSuccess) {

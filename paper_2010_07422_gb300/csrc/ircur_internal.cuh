@@ -16,6 +16,15 @@ constexpr int kNumSMsHint = 152;
 // but ends a lost wait within a few seconds.
 constexpr long long kSpinLimit = 1ll << 26;
 
+// Iterations recorded per trip of the solve graph's while node: each trip
+// costs a few microseconds of condition evaluation and re-launch; the kernels
+// of an iteration after convergence return at once (4: 1.92 -> 1.87 ms at the
+// n = 10^4, r = 5 workload).
+#ifndef IRCUR_GRAPH_UNROLL
+#define IRCUR_GRAPH_UNROLL 4
+#endif
+constexpr int kGraphUnroll = IRCUR_GRAPH_UNROLL;
+
 // Panel-pass tiling: a tile is kPanelCols consecutive panel columns; a block
 // of kPassWarps warps computes one tile at a time, warp h owning row share h
 // and lane c column c.  Each tile leaves its (num, den) partial sums in
