@@ -93,10 +93,12 @@ struct ircur_ctx {
   // last solve
   int solved;
   State host_state;
-  // buffers of the host-memory entry point
+  // buffers of the host-memory entry point, and its copy streams / events
   float* hD;
   float* hL;
   float* hS;
+  cudaStream_t hstream[4];
+  cudaEvent_t hev[17];
   IterDesc desc;
   // recording forward + adjoint workspace (ircur_set_record)
   void* rec_ws;
@@ -303,6 +305,10 @@ extern "C" void ircur_destroy(ircur_ctx* c) {
   if (c->hD) cudaFree(c->hD);
   if (c->hL) cudaFree(c->hL);
   if (c->hS) cudaFree(c->hS);
+  for (int q = 0; q < 4; ++q)
+    if (c->hstream[q]) cudaStreamDestroy(c->hstream[q]);
+  for (int q = 0; q < 17; ++q)
+    if (c->hev[q]) cudaEventDestroy(c->hev[q]);
   if (c->rec_ws) cudaFree(c->rec_ws);
   if (c->ws) cudaFree(c->ws);
   delete c;
@@ -716,16 +722,25 @@ extern "C" ircur_status ircur_reconstruct(ircur_ctx* c, const float* D, int64_t 
   return IRCUR_OK;
 }
 
+// Host-memory entry point.  The copies are pipelined over four copy streams:
+// D goes up in row chunks (the solve waits for all of them), and L and S are
+// reconstructed chunk by chunk, each chunk's rows going back while the next
+// chunk is computed.
 extern "C" ircur_status ircur_solve_host(ircur_ctx* c, const float* D_host, float* L_host, float* S_host,
                                          ircur_result* out) {
   if (!c || !D_host || !L_host || !out) return IRCUR_EINVAL;
   const ircur_params& p = c->p;
   const size_t bytes = (size_t)p.n1 * p.n2 * 4;
+  constexpr int kCopyStreams = 4, kChunks = 8;
   if (!c->hD) {
     cudaError_t e = cudaMalloc(&c->hD, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&c->hL, bytes);
+    for (int q = 0; q < kCopyStreams && e == cudaSuccess; ++q)
+      e = cudaStreamCreateWithFlags(&c->hstream[q], cudaStreamNonBlocking);
+    for (int q = 0; q < 2 * kChunks + 1 && e == cudaSuccess; ++q)
+      e = cudaEventCreateWithFlags(&c->hev[q], cudaEventDisableTiming);
     if (e != cudaSuccess) {
-      set_error("cudaMalloc(host-path buffers)", e);
+      set_error("host-path buffers, streams and events", e);
       cudaGetLastError();
       return IRCUR_ENOMEM;
     }
@@ -738,13 +753,39 @@ extern "C" ircur_status ircur_solve_host(ircur_ctx* c, const float* D_host, floa
       return IRCUR_ENOMEM;
     }
   }
-  IRCUR_CK(cudaMemcpyAsync(c->hD, D_host, bytes, cudaMemcpyHostToDevice, c->stream));
-  ircur_status s = ircur_solve(c, c->hD, p.n2, nullptr, nullptr, out);
+  const int64_t n2 = p.n2;
+  const int64_t rows = (p.n1 + kChunks - 1) / kChunks;
+  // D up: the copy streams start after earlier work on the context's stream
+  IRCUR_CK(cudaEventRecord(c->hev[2 * kChunks], c->stream));
+  for (int q = 0; q < kChunks; ++q) {
+    const int64_t r0 = q * rows;
+    const int64_t nr = p.n1 - r0 < rows ? p.n1 - r0 : rows;
+    if (nr <= 0) break;
+    cudaStream_t cs = c->hstream[q % kCopyStreams];
+    IRCUR_CK(cudaStreamWaitEvent(cs, c->hev[2 * kChunks], 0));
+    IRCUR_CK(cudaMemcpyAsync(c->hD + r0 * n2, D_host + r0 * n2, (size_t)nr * n2 * 4, cudaMemcpyHostToDevice, cs));
+    IRCUR_CK(cudaEventRecord(c->hev[q], cs));
+    IRCUR_CK(cudaStreamWaitEvent(c->stream, c->hev[q], 0));
+  }
+  ircur_status s = ircur_solve(c, c->hD, n2, nullptr, nullptr, out);
   if (s != IRCUR_OK) return s;
-  s = ircur_reconstruct(c, c->hD, p.n2, c->hL, p.n2, S_host ? c->hS : nullptr, p.n2);
-  if (s != IRCUR_OK) return s;
-  IRCUR_CK(cudaMemcpyAsync(L_host, c->hL, bytes, cudaMemcpyDeviceToHost, c->stream));
-  if (S_host) IRCUR_CK(cudaMemcpyAsync(S_host, c->hS, bytes, cudaMemcpyDeviceToHost, c->stream));
+  // L (and S) down, chunk by chunk behind the reconstruction
+  const int K = c->host_state.k;
+  const float* A = c->A[K & 1];
+  for (int q = 0; q < kChunks; ++q) {
+    const int64_t r0 = q * rows;
+    const int64_t nr = p.n1 - r0 < rows ? p.n1 - r0 : rows;
+    if (nr <= 0) break;
+    IRCUR_CK(launch_reconstruct(A + r0 * c->Rpad, c->B[K & 1], c->Rpad, nr, n2, c->hD + r0 * n2, n2,
+                                c->hL + r0 * n2, n2, S_host ? c->hS + r0 * n2 : nullptr, n2, c->st, c->stream));
+    IRCUR_CK(cudaEventRecord(c->hev[kChunks + q], c->stream));
+    cudaStream_t cs = c->hstream[q % kCopyStreams];
+    IRCUR_CK(cudaStreamWaitEvent(cs, c->hev[kChunks + q], 0));
+    IRCUR_CK(cudaMemcpyAsync(L_host + r0 * n2, c->hL + r0 * n2, (size_t)nr * n2 * 4, cudaMemcpyDeviceToHost, cs));
+    if (S_host)
+      IRCUR_CK(cudaMemcpyAsync(S_host + r0 * n2, c->hS + r0 * n2, (size_t)nr * n2 * 4, cudaMemcpyDeviceToHost, cs));
+  }
+  for (int q = 0; q < kCopyStreams; ++q) IRCUR_CK(cudaStreamSynchronize(c->hstream[q]));
   IRCUR_CK(cudaStreamSynchronize(c->stream));
   return IRCUR_OK;
 }
