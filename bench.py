@@ -525,6 +525,32 @@ def main():
                "d2h_bytes_per_step": 8 * n * n, "ms_per_step": 1e3 * el / a.e2e_steps,
                "api": "ircur_solve_host (pinned host D in, dense L and S out)"}
         e2e_solver.close()
+        # the same with Alg. 1's own output: the rank-r factors (L = A B; S = T_zeta(D - A B))
+        f_solver = ir.IRCUR(n, n, a.r, gamma=0.7, tol=1e-5, max_iter=100, resample=resample, seed=a.seed + 1 + rank)
+        Dd = torch.empty((n, n), dtype=torch.float32, device="cuda")
+        Ah = torch.empty((n, a.r), dtype=torch.float32).pin_memory()
+        Bh = torch.empty((a.r, n), dtype=torch.float32).pin_memory()
+
+        def host_factors():
+            Dd.copy_(Dh, non_blocking=True)
+            res_ = f_solver.solve(Dd)
+            A_, B_ = f_solver.factors()
+            Ah.copy_(A_, non_blocking=True)
+            Bh.copy_(B_, non_blocking=True)
+            torch.cuda.synchronize()
+            return res_.iters
+
+        host_factors()
+        barrier()
+        t0 = time.perf_counter()
+        f_iters = sum(host_factors() for _ in range(a.e2e_steps))
+        fel = time.perf_counter() - t0
+        fel, f_iters = aggregate(dist, world, fel, f_iters, "cuda")
+        e2e["factors_output"] = {"value": f_iters / fel, "unit": "iters/s", "h2d_bytes_per_step": 4 * n * n,
+                                 "d2h_bytes_per_step": 8 * n * a.r, "ms_per_step": 1e3 * fel / a.e2e_steps,
+                                 "api": "pinned host D in (torch copy), ircur_solve, ircur_get_factors, "
+                                        "factors A (n x r) and B (r x n) out"}
+        f_solver.close()
 
     # the other variant of Sec. 3.4 on the same D, for context (not the headline)
     other = "F" if resample else "R"

@@ -244,18 +244,16 @@ ircur_status ircur_backward(ircur_ctx* ctx, const float* D, int64_t ldD, const f
  * a time (Alg. 1); a batch runs Alg. 1 on `count` unrelated problems at once
  * -- each with its own shape, rank, sample sizes, thresholds, tolerance,
  * iteration cap and variant (params[i]) -- so that many problems too small to
- * fill the GPU on their own share every kernel launch.  Each instance
- * computes what ircur_create + ircur_solve with params[i] (and no explicit
- * index sets) computes: the same index sets, and the same iterates bit for bit
- * when the batch's largest padded rank equals the instance's own (otherwise
- * the wider padding changes only the rounding order of the core
- * factorisation).  An instance that meets its stopping test stops while the
- * others go on.  All instances use the stream given here.
+ * fill the GPU on their own share every kernel launch (instances are grouped
+ * by padded rank; each group's kernels are launched once per iteration).
+ * Each instance computes exactly what ircur_create + ircur_solve with
+ * params[i] (and no explicit index sets) computes, bit for bit: the same index
+ * sets, iterates, stopping iteration and outputs.  An instance that meets its
+ * stopping test stops while the others go on.  All instances use the stream
+ * given here.
  * ircur_batch_create validates every params[i] as ircur_create does (the
- * first failure is returned), allocates one workspace per instance, and
- * returns ENOTSUP when the instances' shared padded rank (the largest of the
- * batch) does not fit an instance's shared-memory layout.  count in
- * [1, IRCUR_MAX_BATCH]. */
+ * first failure is returned) and allocates one workspace per instance.
+ * count in [1, IRCUR_MAX_BATCH]. */
 typedef struct ircur_batch ircur_batch;
 ircur_status ircur_batch_create(const ircur_params* params, int32_t count, void* stream, ircur_batch** out);
 

@@ -858,26 +858,36 @@ extern "C" const char* ircur_last_error_string(void) { return g_last_error; }
 
 // ---------------------------------------------------------------------------
 // Batches of independent problems (each with its own shape, rank, sample
-// sizes and variant) solved together.  Every iteration kernel is launched once
-// per iteration for the whole batch: the core and SVD launches index the
-// instance by a grid dimension, the pass launch lays all instances' tiles end
-// to end, and a one-block kernel ends the loop once every instance has met its
-// own stopping test (instances that stopped skip their blocks).  The instances
-// share one padded rank (the largest), so one set of kernel instantiations
-// serves the batch.
+// sizes and variant) solved together.  Instances are grouped by padded rank;
+// every iteration launches each group's kernels once (the core and SVD
+// launches index the instance by a grid dimension, the pass launch lays the
+// group's tiles end to end), and a one-block kernel ends the loop once every
+// instance has met its own stopping test (instances that stopped skip their
+// blocks).  Each instance keeps its own padded rank, so it computes exactly
+// what a lone solve computes.
+
+constexpr int kMaxRankGroups = 16;
 
 struct ircur_batch {
   int count;
-  int Rpad;
   int max_iter;  // the largest max_iter of the batch
   cudaStream_t stream;
   cudaStream_t capture_stream;
   cudaStream_t body_stream;
-  ircur_ctx** inst;
-  IterDesc* hdesc;
-  void* dws;        // device: descriptors, tile prefix sums, SVD lists, loop flag
-  State* hstates;   // pinned host copies of every instance's state after a solve
-  BatchLaunch bl;
+  ircur_ctx** inst;  // user order
+  int* order;        // position in the descriptor array -> user index
+  int* pos;          // user index -> position
+  IterDesc* hdesc;   // descriptor array order
+  void* dws;         // device: descriptors, tile prefix sums, SVD lists, loop flag
+  IterDesc* ds;      // device descriptors (grouped order)
+  int* any_active;
+  State* hstates;    // pinned host copies of the states (descriptor order)
+  int ngroups;
+  int grpR[kMaxRankGroups];      // padded rank of group g
+  int grpFirst[kMaxRankGroups];  // its first position in the descriptor array
+  BatchLaunch grp[kMaxRankGroups];
+  cudaStream_t gstream[kMaxRankGroups];  // one branch per group (they run concurrently)
+  cudaEvent_t gev[kMaxRankGroups + 1];
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   const float** graph_D;  // the D pointers and leading dimensions the graph was built for
@@ -901,9 +911,15 @@ extern "C" void ircur_batch_destroy(ircur_batch* b) {
   }
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   if (b->body_stream) cudaStreamDestroy(b->body_stream);
+  for (int g = 0; g < kMaxRankGroups; ++g)
+    if (b->gstream[g]) cudaStreamDestroy(b->gstream[g]);
+  for (int g = 0; g <= kMaxRankGroups; ++g)
+    if (b->gev[g]) cudaEventDestroy(b->gev[g]);
   if (b->dws) cudaFree(b->dws);
   if (b->hstates) cudaFreeHost(b->hstates);
   delete[] b->hdesc;
+  delete[] b->order;
+  delete[] b->pos;
   delete[] b->graph_D;
   delete[] b->graph_ld;
   delete b;
@@ -914,81 +930,58 @@ extern "C" ircur_status ircur_batch_create(const ircur_params* params, int32_t c
   if (!out) return IRCUR_EINVAL;
   *out = nullptr;
   if (!params || count < 1 || count > IRCUR_MAX_BATCH) return IRCUR_EINVAL;
-  int Rpad = 1;
   for (int i = 0; i < count; ++i) {
     ircur_params q;
     ircur_status vs = validate_params(&params[i], &q);
     if (vs != IRCUR_OK) return vs;
     if (q.precision != IRCUR_PRECISION_FP32) return IRCUR_ENOTSUP;
-    const int rp = pad_rank(q.r);
-    if (rp > Rpad) Rpad = rp;
   }
   ircur_batch* b = new (std::nothrow) ircur_batch();
   if (!b) return IRCUR_ENOMEM;
   b->count = count;
-  b->Rpad = Rpad;
   b->stream = reinterpret_cast<cudaStream_t>(stream);
   b->inst = new (std::nothrow) ircur_ctx*[count]();
+  b->order = new (std::nothrow) int[count];
+  b->pos = new (std::nothrow) int[count];
   b->hdesc = new (std::nothrow) IterDesc[count];
   b->graph_D = new (std::nothrow) const float*[count]();
   b->graph_ld = new (std::nothrow) int64_t[count]();
-  if (!b->inst || !b->hdesc || !b->graph_D || !b->graph_ld) {
+  if (!b->inst || !b->order || !b->pos || !b->hdesc || !b->graph_D || !b->graph_ld) {
     ircur_batch_destroy(b);
     return IRCUR_ENOMEM;
   }
   for (int i = 0; i < count; ++i) {
-    ircur_status cs = create_impl(&params[i], stream, Rpad, &b->inst[i]);
+    ircur_status cs = create_impl(&params[i], stream, 0, &b->inst[i]);
     if (cs != IRCUR_OK) {
       ircur_batch_destroy(b);
       return cs;
     }
   }
-  // the shared padded rank must still fit each instance's shared-memory layouts
-  BatchLaunch& bl = b->bl;
-  memset(&bl, 0, sizeof(bl));
-  std::unique_ptr<int[]> tiles(new int[count + 1]);
-  std::unique_ptr<int[]> lists(new int[count]);
-  std::unique_ptr<unsigned char[]> grp(new unsigned char[count]);
-  int maxNI = 1, n0 = 0, roles = 1;
-  tiles[0] = 0;
-  for (int i = 0; i < count; ++i) {
-    const ircur_ctx* c = b->inst[i];
-    const ircur_params& p = c->p;
-    const size_t ps = pass_smem_bytes(p.nI, p.nJ, Rpad);
-    const bool in_smem = true;  // one instance list: the cluster SVD always holds the core in shared memory
-    const size_t ss = csvd_smem_bytes(p.nI, p.nJ, Rpad);
-    if (ps > 227 * 1024 || ss > 227 * 1024) {
-      ircur_batch_destroy(b);
-      return IRCUR_ENOTSUP;
-    }
-    if (ps > bl.pass_smem) bl.pass_smem = ps;
-    if (p.nI > bl.pass_mmax) bl.pass_mmax = p.nI;
-    if (p.nJ > bl.pass_mmax) bl.pass_mmax = p.nJ;
-    const int g = in_smem ? 0 : 1;
-    grp[i] = (unsigned char)g;
-    if (ss > bl.svd_smem[g]) bl.svd_smem[g] = ss;
-    if (g == 0) ++n0;
-    const int64_t t = (int64_t)tiles[i] + c->desc.nRowTiles + c->desc.nColTiles;
-    if (t > (1ll << 30)) {
-      ircur_batch_destroy(b);
-      return IRCUR_ENOTSUP;
-    }
-    tiles[i + 1] = (int)t;
-    if (p.nI > maxNI) maxNI = p.nI;
-    if (p.resample) roles = 3;
-    if (p.max_iter > b->max_iter) b->max_iter = p.max_iter;
-  }
+  // descriptor order: by padded rank (stable), one group per padded rank
   {
-    int a = 0, z = n0;
-    for (int i = 0; i < count; ++i) lists[grp[i] ? z++ : a++] = i;
+    int n = 0;
+    for (int rp = 1; rp <= IRCUR_MAX_RANK; ++rp) {
+      const int first = n;
+      for (int i = 0; i < count; ++i)
+        if (b->inst[i]->Rpad == rp) b->order[n++] = i;
+      if (n > first) {
+        b->grpR[b->ngroups] = rp;
+        b->grpFirst[b->ngroups] = first;
+        b->grp[b->ngroups].count = n - first;
+        ++b->ngroups;
+      }
+    }
+    for (int q = 0; q < count; ++q) b->pos[b->order[q]] = q;
   }
-  bl.pass_smem = pass_smem_bytes(bl.pass_mmax, bl.pass_mmax, Rpad, &bl.pass_nbuf);
-  // device workspace: descriptors | tile prefix sums | SVD lists | loop flag
+  // device workspace: descriptors | per-group tile prefix sums | instance list | loop flag
   const size_t oDesc = 0;
   const size_t oTiles = (oDesc + (size_t)count * sizeof(IterDesc) + 255) & ~(size_t)255;
-  const size_t oList = (oTiles + (size_t)(count + 1) * 4 + 255) & ~(size_t)255;
+  const size_t oList = (oTiles + (size_t)(count + b->ngroups) * 4 + 255) & ~(size_t)255;
   const size_t oFlag = (oList + (size_t)count * 4 + 255) & ~(size_t)255;
   const size_t bytes = oFlag + 256;
+  std::unique_ptr<int[]> tiles(new int[count + b->ngroups]);
+  std::unique_ptr<int[]> lists(new int[count]);
+  for (int q = 0; q < count; ++q) lists[q] = q;  // group-relative identity lists share one array
   cudaError_t e = cudaMalloc(&b->dws, bytes);
   if (e != cudaSuccess) {
     set_error("cudaMalloc(batch workspace)", e);
@@ -996,13 +989,65 @@ extern "C" ircur_status ircur_batch_create(const ircur_params* params, int32_t c
     ircur_batch_destroy(b);
     return IRCUR_ENOMEM;
   }
+  char* base = static_cast<char*>(b->dws);
+  b->ds = reinterpret_cast<IterDesc*>(base + oDesc);
+  b->any_active = reinterpret_cast<int*>(base + oFlag);
+  for (int g = 0; g < b->ngroups; ++g) {
+    BatchLaunch& bl = b->grp[g];
+    const int first = b->grpFirst[g], n = bl.count, R = b->grpR[g];
+    memset(&bl, 0, sizeof(bl));
+    bl.count = n;
+    bl.ds = b->ds + first;
+    int* tb = tiles.get() + first + g;
+    tb[0] = 0;
+    int maxNI = 1, roles = 1;
+    for (int q = 0; q < n; ++q) {
+      const ircur_ctx* c = b->inst[b->order[first + q]];
+      const ircur_params& p = c->p;
+      const size_t ss = csvd_smem_bytes(p.nI, p.nJ, R);
+      if (pass_smem_bytes(p.nI, p.nJ, R) > 227 * 1024 || ss > 227 * 1024) {
+        ircur_batch_destroy(b);
+        return IRCUR_ENOTSUP;
+      }
+      if (ss > bl.svd_smem[0]) bl.svd_smem[0] = ss;
+      if (p.nI > bl.pass_mmax) bl.pass_mmax = p.nI;
+      if (p.nJ > bl.pass_mmax) bl.pass_mmax = p.nJ;
+      const int64_t t = (int64_t)tb[q] + c->desc.nRowTiles + c->desc.nColTiles;
+      if (t > (1ll << 30)) {
+        ircur_batch_destroy(b);
+        return IRCUR_ENOTSUP;
+      }
+      tb[q + 1] = (int)t;
+      if (p.nI > maxNI) maxNI = p.nI;
+      if (p.resample) roles = 3;
+      if (p.max_iter > b->max_iter) b->max_iter = p.max_iter;
+    }
+    bl.tile_base = reinterpret_cast<const int*>(base + oTiles) + first + g;
+    bl.total_tiles = tb[n];
+    bl.pass_smem = pass_smem_bytes(bl.pass_mmax, bl.pass_mmax, R, &bl.pass_nbuf);
+    {
+      const int want = (4 * kNumSMsHint + n - 1) / n;
+      bl.core_blocks = want < maxNI ? (want > 0 ? want : 1) : maxNI;
+    }
+    bl.svd_list[0] = reinterpret_cast<const int*>(base + oList);
+    bl.svd_list[1] = bl.svd_list[0];
+    bl.svd_n[0] = n;
+    bl.svd_n[1] = 0;
+    bl.svd_roles = roles;
+    bl.cond = 0;
+    bl.any_active = b->any_active;
+  }
   e = cudaMallocHost(reinterpret_cast<void**>(&b->hstates), (size_t)count * sizeof(State));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->body_stream, cudaStreamNonBlocking);
-  char* base = static_cast<char*>(b->dws);
+  for (int g = 0; g < b->ngroups && e == cudaSuccess; ++g)
+    e = cudaStreamCreateWithFlags(&b->gstream[g], cudaStreamNonBlocking);
+  for (int g = 0; g <= b->ngroups && e == cudaSuccess; ++g)
+    e = cudaEventCreateWithFlags(&b->gev[g], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->dws, 0, bytes, b->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(base + oTiles, tiles.get(), (size_t)(count + 1) * 4, cudaMemcpyHostToDevice, b->stream);
+    e = cudaMemcpyAsync(base + oTiles, tiles.get(), (size_t)(count + b->ngroups) * 4, cudaMemcpyHostToDevice,
+                        b->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(base + oList, lists.get(), (size_t)count * 4, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -1011,23 +1056,27 @@ extern "C" ircur_status ircur_batch_create(const ircur_params* params, int32_t c
     ircur_batch_destroy(b);
     return IRCUR_ECUDA;
   }
-  bl.ds = reinterpret_cast<const IterDesc*>(base + oDesc);
-  bl.count = count;
-  bl.tile_base = reinterpret_cast<const int*>(base + oTiles);
-  bl.total_tiles = tiles[count];
-  {
-    const int want = (4 * kNumSMsHint + count - 1) / count;
-    bl.core_blocks = want < maxNI ? (want > 0 ? want : 1) : maxNI;
-  }
-  bl.svd_list[0] = reinterpret_cast<const int*>(base + oList);
-  bl.svd_list[1] = reinterpret_cast<const int*>(base + oList) + n0;
-  bl.svd_n[0] = n0;
-  bl.svd_n[1] = count - n0;
-  bl.svd_roles = roles;
-  bl.cond = 0;
-  bl.any_active = reinterpret_cast<int*>(base + oFlag);
   *out = b;
   return IRCUR_OK;
+}
+
+// One batched iteration: the rank groups' kernels on concurrent branches
+// (forked from and joined back into s), then the loop control.
+static cudaError_t batch_iteration(ircur_batch* b, unsigned long long cond, cudaStream_t s) {
+  if (b->ngroups == 1) {
+    cudaError_t e = launch_batch_group(b->grp[0], b->grpR[0], s);
+    if (e != cudaSuccess) return e;
+  } else {
+    cudaError_t e = cudaEventRecord(b->gev[b->ngroups], s);
+    for (int g = 0; g < b->ngroups && e == cudaSuccess; ++g) {
+      e = cudaStreamWaitEvent(b->gstream[g], b->gev[b->ngroups], 0);
+      if (e == cudaSuccess) e = launch_batch_group(b->grp[g], b->grpR[g], b->gstream[g]);
+      if (e == cudaSuccess) e = cudaEventRecord(b->gev[g], b->gstream[g]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->gev[g], 0);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return launch_batch_check(b->ds, b->count, cond, b->any_active, s);
 }
 
 extern "C" ircur_ctx* ircur_batch_instance(ircur_batch* b, int32_t i) {
@@ -1038,12 +1087,12 @@ extern "C" ircur_ctx* ircur_batch_instance(ircur_batch* b, int32_t i) {
 // Upload the descriptors the prologues left in each instance (no graph
 // condition of their own: the loop-control kernel owns the batch's).
 static ircur_status batch_upload_descs(ircur_batch* b) {
-  for (int i = 0; i < b->count; ++i) {
-    b->hdesc[i] = b->inst[i]->desc;
-    b->hdesc[i].cond = 0;
+  for (int q = 0; q < b->count; ++q) {
+    b->hdesc[q] = b->inst[b->order[q]]->desc;
+    b->hdesc[q].cond = 0;
   }
-  IRCUR_CK(cudaMemcpyAsync(const_cast<IterDesc*>(b->bl.ds), b->hdesc, (size_t)b->count * sizeof(IterDesc),
-                           cudaMemcpyHostToDevice, b->stream));
+  IRCUR_CK(cudaMemcpyAsync(b->ds, b->hdesc, (size_t)b->count * sizeof(IterDesc), cudaMemcpyHostToDevice,
+                           b->stream));
   return IRCUR_OK;
 }
 
@@ -1092,8 +1141,6 @@ static ircur_status batch_build_graph(ircur_batch* b, const float* const* D, con
     set_error("batch graph: while node", e);
     return batch_abort_capture(b, cs, IRCUR_ECUDA);
   }
-  BatchLaunch bl = b->bl;
-  bl.cond = (unsigned long long)h;
   e = cudaStreamBeginCaptureToGraph(b->body_stream, cp->conditional.phGraph_out[0], nullptr, nullptr, 0,
                                     cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) {
@@ -1101,7 +1148,8 @@ static ircur_status batch_build_graph(ircur_batch* b, const float* const* D, con
     return batch_abort_capture(b, cs, IRCUR_ECUDA);
   }
   cudaError_t le = cudaSuccess;
-  for (int u = 0; u < kGraphUnroll && le == cudaSuccess; ++u) le = launch_batch_iteration(bl, b->Rpad, b->body_stream);
+  for (int u = 0; u < kGraphUnroll && le == cudaSuccess; ++u)
+    le = batch_iteration(b, (unsigned long long)h, b->body_stream);
   cudaGraph_t body = nullptr;
   cudaError_t be = cudaStreamEndCapture(b->body_stream, &body);
   if (le != cudaSuccess || be != cudaSuccess) {
@@ -1109,7 +1157,7 @@ static ircur_status batch_build_graph(ircur_batch* b, const float* const* D, con
     return batch_abort_capture(b, cs, IRCUR_ECUDA);
   }
   for (int i = 0; i < b->count; ++i) {
-    e = cudaMemcpyAsync(b->hstates + i, b->inst[i]->st, sizeof(State), cudaMemcpyDeviceToHost, cs);
+    e = cudaMemcpyAsync(b->hstates + b->pos[i], b->inst[i]->st, sizeof(State), cudaMemcpyDeviceToHost, cs);
     if (e != cudaSuccess) {
       set_error("batch graph: state copy", e);
       return batch_abort_capture(b, cs, IRCUR_ECUDA);
@@ -1159,19 +1207,19 @@ extern "C" ircur_status ircur_batch_solve(ircur_batch* b, const float* const* D,
     if (us != IRCUR_OK) return us;
     int active = 1;
     for (int it = 0; it < b->max_iter && active; ++it) {
-      IRCUR_CK(launch_batch_iteration(b->bl, b->Rpad, s));
+      IRCUR_CK(batch_iteration(b, 0ull, s));
       if ((it & 3) == 3) {
-        IRCUR_CK(cudaMemcpyAsync(&active, b->bl.any_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+        IRCUR_CK(cudaMemcpyAsync(&active, b->any_active, sizeof(int), cudaMemcpyDeviceToHost, s));
         IRCUR_CK(cudaStreamSynchronize(s));
       }
     }
     for (int i = 0; i < b->count; ++i)
-      IRCUR_CK(cudaMemcpyAsync(b->hstates + i, b->inst[i]->st, sizeof(State), cudaMemcpyDeviceToHost, s));
+      IRCUR_CK(cudaMemcpyAsync(b->hstates + b->pos[i], b->inst[i]->st, sizeof(State), cudaMemcpyDeviceToHost, s));
   }
   IRCUR_CK(cudaStreamSynchronize(s));
   ircur_status first = IRCUR_OK;
   for (int i = 0; i < b->count; ++i) {
-    b->inst[i]->host_state = b->hstates[i];
+    b->inst[i]->host_state = b->hstates[b->pos[i]];
     const ircur_status si = solve_epilogue(b->inst[i], &out[i]);
     if (si != IRCUR_OK && first == IRCUR_OK) first = si;
   }
@@ -1277,20 +1325,45 @@ extern "C" ircur_status ircur_batch_autotune(ircur_batch* b, const float* const*
   if (reps > 16) reps = 16;
   memset(out, 0, sizeof(*out));
   const int sms = device_sms();
-  BatchLaunch& bl = b->bl;
-  const int mm = bl.pass_mmax;
-  bl.pass_grid = 0;
-  bl.pass_smem = pass_smem_bytes(mm, mm, b->Rpad, &bl.pass_nbuf, false, false);
-  const int res2 = pass_batch_resident_blocks(bl, b->Rpad);
-  const size_t smem2 = bl.pass_smem;
-  const int nbuf2 = bl.pass_nbuf;
-  int nbuf1 = 1;
-  const size_t smem1 = pass_smem_bytes(mm, mm, b->Rpad, &nbuf1, false, true);
-  bl.pass_smem = smem1;
-  bl.pass_nbuf = nbuf1;
-  const int res1 = pass_batch_resident_blocks(bl, b->Rpad);
+  // per group: resident blocks with two tile buffers and with one
+  int per2[kMaxRankGroups], per1[kMaxRankGroups], nbuf2[kMaxRankGroups], nbuf1[kMaxRankGroups];
+  size_t smem2[kMaxRankGroups], smem1[kMaxRankGroups];
+  int maxper = 1, total = 0;
+  for (int g = 0; g < b->ngroups; ++g) {
+    BatchLaunch& bl = b->grp[g];
+    const int mm = bl.pass_mmax, R = b->grpR[g];
+    bl.pass_grid = 0;
+    smem2[g] = pass_smem_bytes(mm, mm, R, &nbuf2[g], false, false);
+    smem1[g] = pass_smem_bytes(mm, mm, R, &nbuf1[g], false, true);
+    bl.pass_smem = smem2[g];
+    bl.pass_nbuf = nbuf2[g];
+    per2[g] = pass_batch_resident_blocks(bl, R) / sms;
+    bl.pass_smem = smem1[g];
+    bl.pass_nbuf = nbuf1[g];
+    per1[g] = pass_batch_resident_blocks(bl, R) / sms;
+    if (per1[g] > maxper) maxper = per1[g];
+    total += bl.total_tiles;
+  }
+  // candidates: k resident blocks per SM (capped per group) with two or one
+  // tile buffers, or one block per tile (k = 0)
   TuneCand cand[IRCUR_TUNE_MAX];
-  const int nc = tune_candidates(bl.total_tiles, res2, res1, sms, cand);
+  int nc = 0;
+  for (int k = 1; k <= maxper && nc < IRCUR_TUNE_MAX - 1; ++k) {
+    cand[nc++] = TuneCand{k, 0};
+    if (nc < IRCUR_TUNE_MAX - 1) cand[nc++] = TuneCand{k, 1};
+  }
+  cand[nc++] = TuneCand{0, 0};
+  auto apply = [&](const TuneCand& tc) {
+    for (int g = 0; g < b->ngroups; ++g) {
+      BatchLaunch& bl = b->grp[g];
+      const int per = tc.single ? per1[g] : per2[g];
+      const int k = tc.grid == 0 ? 0 : (tc.grid < per ? tc.grid : (per > 0 ? per : 1));
+      bl.pass_smem = tc.single ? smem1[g] : smem2[g];
+      bl.pass_nbuf = tc.single ? nbuf1[g] : nbuf2[g];
+      bl.pass_grid = k == 0 ? bl.total_tiles : k * sms;
+    }
+    batch_reset_graph(b);
+  };
   ircur_result* res = new (std::nothrow) ircur_result[b->count];
   if (!res) return IRCUR_ENOMEM;
   cudaEvent_t e0, e1;
@@ -1298,12 +1371,6 @@ extern "C" ircur_status ircur_batch_autotune(ircur_batch* b, const float* const*
     delete[] res;
     return IRCUR_ECUDA;
   }
-  auto apply = [&](const TuneCand& tc) {
-    bl.pass_grid = tc.grid;
-    bl.pass_smem = tc.single ? smem1 : smem2;
-    bl.pass_nbuf = tc.single ? nbuf1 : nbuf2;
-    batch_reset_graph(b);
-  };
   ircur_status st = IRCUR_OK;
   int best = 0;
   for (int q = 0; q < nc && st == IRCUR_OK; ++q) {
@@ -1318,7 +1385,7 @@ extern "C" ircur_status ircur_batch_autotune(ircur_batch* b, const float* const*
       cudaEventElapsedTime(&t[k], e0, e1);
     }
     if (st != IRCUR_OK) break;
-    out->grid[q] = cand[q].grid;
+    out->grid[q] = cand[q].grid == 0 ? total : cand[q].grid * sms;
     out->single_buffer[q] = cand[q].single;
     out->ms[q] = median3(t, reps);
     if (out->ms[q] < out->ms[best]) best = q;

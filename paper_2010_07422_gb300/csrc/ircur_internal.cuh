@@ -110,8 +110,8 @@ struct IterDesc {
   uint64_t seed;
 };
 
-// One iteration for a batch of independent instances (all with the same
-// padded rank): every kernel covers all instances of the batch.
+// One iteration for a group of independent batch instances with the same
+// padded rank: every kernel covers all instances of the group.
 struct BatchLaunch {
   const IterDesc* ds;      // device array, one descriptor per instance
   int count;
@@ -193,7 +193,11 @@ cudaError_t launch_reconstruct(const float* A, const float* B, int Rpad, int64_t
                                int64_t ldS, const State* st, cudaStream_t s);
 cudaError_t launch_get_cur(const IterDesc& d, int Rpad, int K, const float* D, int64_t ldD, float* C, float* U,
                            float* Rm, cudaStream_t s);
-cudaError_t launch_batch_iteration(const BatchLaunch& b, int Rpad, cudaStream_t s);
+// One iteration of a group of batch instances sharing a padded rank (core,
+// SVD, passes), and the loop control over the whole batch.
+cudaError_t launch_batch_group(const BatchLaunch& b, int Rpad, cudaStream_t s);
+cudaError_t launch_batch_check(const IterDesc* ds, int count, unsigned long long cond, int* any_active,
+                               cudaStream_t s);
 cudaError_t launch_svd_batch(const BatchLaunch& b, int Rpad, cudaStream_t s);
 cudaError_t launch_sigma(const float* Tm, int r, int Rpad, float* sigma, cudaStream_t s);
 // Adjoint (k_adjoint.cu)

@@ -704,9 +704,6 @@ static cudaError_t launch_batch_iter_r(const BatchLaunch& b, cudaStream_t s) {
     if (grid > b.total_tiles) grid = b.total_tiles;
     pass_batch_kernel<R><<<grid, kPassThreads, b.pass_smem, s>>>(b.ds, b.tile_base, b.count, b.pass_mmax, b.pass_nbuf);
   }
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  batch_check_kernel<<<1, 256, 0, s>>>(b.ds, b.count, b.cond, b.any_active);
   return cudaGetLastError();
 }
 
@@ -746,7 +743,13 @@ static int pass_batch_resident_r(const BatchLaunch& b) {
 int pass_resident_blocks(const IterDesc& d, int Rpad) { IRCUR_R_DISPATCH(pass_resident_r, d) }
 int pass_batch_resident_blocks(const BatchLaunch& b, int Rpad) { IRCUR_R_DISPATCH(pass_batch_resident_r, b) }
 
-cudaError_t launch_batch_iteration(const BatchLaunch& b, int Rpad, cudaStream_t s) {
+cudaError_t launch_batch_check(const IterDesc* ds, int count, unsigned long long cond, int* any_active,
+                               cudaStream_t s) {
+  batch_check_kernel<<<1, 256, 0, s>>>(ds, count, cond, any_active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_group(const BatchLaunch& b, int Rpad, cudaStream_t s) {
   switch (Rpad) {
     case 1: return launch_batch_iter_r<1>(b, s);
     case 2: return launch_batch_iter_r<2>(b, s);
