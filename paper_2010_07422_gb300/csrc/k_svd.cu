@@ -253,6 +253,87 @@ __global__ void sigma_kernel(const float* __restrict__ Tm, int r, float* __restr
   if (p < r) sigma[pos] = sg;
 }
 
+
+// Every warp factorises the same R x R Gram matrix G = U^T U in registers (lane
+// l holds row l of the Schur complement) and keeps U and the reciprocal
+// pivots in its own shared slot (Uw, dinvw), so the rows it then transforms
+// need no block barrier; identical arithmetic gives identical factors in every
+// warp and CTA.  Pivots <= 1e-12 of the largest diagonal entry mark dependent
+// columns (zero rows of U, dinv = 0).  Returns the number of those.
+template <int R>
+__device__ int warp_chol(const float* G, int r, float* Uw, float* dinvw) {
+  const int lane = threadIdx.x & 31;
+  float g[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) g[u] = (lane < r && u < r) ? G[lane * R + u] : 0.f;
+  float maxd = sel<R>(g, lane);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) maxd = fmaxf(maxd, __shfl_xor_sync(0xffffffffu, maxd, o));
+  int brk = 0;
+  for (int t = 0; t < r; ++t) {
+    const float gt = sel<R>(g, t);
+    const float dgt = __shfl_sync(0xffffffffu, gt, t);
+    const bool keep = dgt > 1e-12f * maxd && dgt <= FLT_MAX;
+    const float rinv = keep ? rsqrtf(dgt) : 0.f;
+    const float ul = gt * rinv;  // U(t, lane)
+    float urow[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) urow[u] = __shfl_sync(0xffffffffu, ul, u);
+    if (lane == 0) {
+#pragma unroll
+      for (int u = 0; u < R; ++u) Uw[t * R + u] = (u >= t) ? urow[u] : 0.f;
+      dinvw[t] = rinv;
+    }
+    if (lane > t) {
+#pragma unroll
+      for (int u = 0; u < R; ++u) g[u] = fmaf(-ul, urow[u], g[u]);
+    }
+    brk += keep ? 0 : 1;
+  }
+  if (lane == 0) {
+    for (int t = r; t < R; ++t) {
+      dinvw[t] = 0.f;
+      for (int u = 0; u < R; ++u) Uw[t * R + u] = 0.f;
+    }
+  }
+  __syncwarp();
+  return brk;
+}
+
+// y U = m for one row (forward substitution with U from warp_chol).
+template <int R>
+__device__ __forceinline__ void row_subst(const float (&m)[R], float (&y)[R], const float* Uw, const float* dinvw) {
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    float v = m[t];
+#pragma unroll
+    for (int s2 = 0; s2 < t; ++s2) v = fmaf(-y[s2], Uw[s2 * R + t], v);
+    y[t] = v * dinvw[t];
+  }
+}
+
+// Cholesky QR of a column-major block (Min -> Mout, may alias) with the factor
+// formed by every warp; warp 0's copy goes to Uout / sm.dinv for later use.
+template <int R>
+__device__ int cholqr_w(const float* Min, int ldin, float* Mout, int ldout, int nrows, int r, float* Uout,
+                        const SvdSmall& sm, float* slots) {
+  gram_block<R>(Min, nrows, ldin, r, sm.G);
+  const int warp = threadIdx.x >> 5;
+  float* Uw = warp == 0 ? Uout : slots + (size_t)warp * (R * R + R);
+  float* dw = warp == 0 ? sm.dinv : Uw + R * R;
+  const int brk = warp_chol<R>(sm.G, r, Uw, dw);
+  for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+    float m[R], y[R];
+#pragma unroll
+    for (int s2 = 0; s2 < R; ++s2) m[s2] = Min[(size_t)s2 * ldin + i];
+    row_subst<R>(m, y, Uw, dw);
+#pragma unroll
+    for (int t = 0; t < R; ++t) Mout[(size_t)t * ldout + i] = y[t];
+  }
+  __syncthreads();
+  return brk;
+}
+
 // ---------------------------------------------------------------------------
 // Core SVD on a thread-block cluster of kSvdCluster CTAs (distributed shared
 // memory).  The two-sided subspace iteration above, with the core split by
@@ -276,7 +357,8 @@ struct CsvdLayout {
   int ldx;      // column stride of X and of the Q partial (nJ rounded up to 4)
   int js;       // rows of the outputs X T^{-1}, X T^T each CTA writes
   int pch;      // inner-dimension chunks of the local product
-  size_t off_uc, off_x, off_y, off_qp, off_qs, off_part, off_ra, off_stage, off_small, off_flag, off_bar, total;
+  size_t off_uc, off_x, off_y, off_qp, off_qs, off_part, off_ra, off_stage, off_slots, off_small, off_flag, off_bar,
+      total;
 };
 
 __host__ __device__ inline CsvdLayout csvd_layout(int nI, int nJ, int ldu, int R, int cl) {
@@ -287,7 +369,8 @@ __host__ __device__ inline CsvdLayout csvd_layout(int nI, int nJ, int ldu, int R
   L.js = (nJ + cl - 1) / cl;
   const size_t small = (size_t)kSmallMats * R * R * 4 + 4 * 32 * 4 + 64;
   const size_t fixed = (size_t)L.mr * ldu * 4 + 3 * (size_t)R * L.ldx * 4 + (size_t)R * L.ldy * 4 +
-                       (1 + (size_t)cl) * ((size_t)R * R + 4) * 4 + small + 64;
+                       (1 + (size_t)cl) * ((size_t)R * R + 4) * 4 + (size_t)(kCsvdThreads / 32) * (R * R + R) * 4 +
+                       small + 64;
   int pch = 8;
   while (pch > 1 && fixed + (size_t)pch * R * L.ldy * 4 > kSvdSmemBudget) --pch;
   L.pch = pch;
@@ -308,6 +391,8 @@ __host__ __device__ inline CsvdLayout csvd_layout(int nI, int nJ, int ldu, int R
   off += ((size_t)R * R + 4) * 4;
   L.off_stage = off;  // cl x (R R + 4): remote partials gathered before a fixed-order sum
   off += (size_t)cl * ((size_t)R * R + 4) * 4;
+  L.off_slots = off;  // per-warp Cholesky factors
+  off += (size_t)(kCsvdThreads / 32) * (R * R + R) * 4;
   L.off_small = off;
   off += small;
   L.off_flag = (off + 15) & ~(size_t)15;
@@ -471,6 +556,7 @@ __device__ __forceinline__ void csvd_body(const IterDesc& d, int role, unsigned 
   float* part = reinterpret_cast<float*>(smem + L.off_part);
   float* ra = reinterpret_cast<float*>(smem + L.off_ra);  // Gram(Y) partial
   float* stage = reinterpret_cast<float*>(smem + L.off_stage);
+  float* slots = reinterpret_cast<float*>(smem + L.off_slots);
   int* flag = reinterpret_cast<int*>(smem + L.off_flag);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.off_bar);
   SvdSmall sm;
@@ -523,7 +609,7 @@ __device__ __forceinline__ void csvd_body(const IterDesc& d, int role, unsigned 
     for (int t = 0; t < R; ++t) X[(size_t)t * L.ldx + b] = (t < r) ? d.BJt[(size_t)b * R + t] : 0.f;
   }
   __syncthreads();
-  int brk = cholqr<R>(X, X, nJ, r, L.ldx, sm.U, sm);
+  int brk = cholqr_w<R>(X, L.ldx, X, L.ldx, nJ, r, sm.U, sm, slots);
   if (brk > 0) {  // first iteration (B_0 = 0) or a deficient factor: random start
     for (int b = threadIdx.x; b < nJ; b += blockDim.x) {
 #pragma unroll
@@ -532,7 +618,7 @@ __device__ __forceinline__ void csvd_body(const IterDesc& d, int role, unsigned 
             (t < r) ? hash_uniform(d.seed ^ 0x5bd1e995ull, ((uint64_t)k << 32) ^ (uint64_t)(b * R + t)) : 0.f;
     }
     __syncthreads();
-    cholqr<R>(X, X, nJ, r, L.ldx, sm.U, sm);
+    cholqr_w<R>(X, L.ldx, X, L.ldx, nJ, r, sm.U, sm, slots);
   }
   bool ok = true;
   if (nrow > 0) {
@@ -554,21 +640,78 @@ __device__ __forceinline__ void csvd_body(const IterDesc& d, int role, unsigned 
   }
 
   // ---- subspace iteration.  With Y = (core X) Rp^{-1}, core^T Y =
-  // (core^T core X) Rp^{-1}: the transposed product runs on the raw local
-  // rows in the same phase as their Gram partial, and Rp^{-1} is applied to
-  // the reduced Q.  Two cluster barriers per step: partials written, partials
-  // read.
+  // (core^T core X) Rp^{-1}: the transposed product runs on the raw local rows
+  // in the same phase as their Gram partial, and Rp^{-1} is applied to the
+  // summed Q.  Per step: four block barriers and two cluster barriers
+  // (partials written; partials read).
+  const int nwarps = (int)(blockDim.x >> 5);
+  float* Uw = slots + (size_t)warp * (R * R + R);
+  float* dw = Uw + R * R;
   int steps = 0;
   bool converged = false;
   float prev_res = 0.f;
   while (true) {
     ++steps;
-    cl_rows_times<R>(Uc, ldu, nrow, nJ, X, L.ldx, Y, L.ldy, part, L.pch);  // Y_c = core_c X (raw)
-    gram_block<R>(Y, nrow, L.ldy, r, ra);                                  // Y_c^T Y_c
-    cl_cols_times<R>(Uc, ldu, nJ, nrow, Y, L.ldy, Qp, L.ldx);              // core_c^T Y_c
+    // Y_c = core_c X (raw): one warp per local row, lanes over the inner index
+    for (int o = warp; o < nrow; o += nwarps) {
+      float acc[R];
+#pragma unroll
+      for (int t = 0; t < R; ++t) acc[t] = 0.f;
+      for (int q = lane; q < nJ; q += 32) {
+        const float u = Uc[(size_t)o * ldu + q];
+#pragma unroll
+        for (int t = 0; t < R; ++t) acc[t] = fmaf(u, X[(size_t)t * L.ldx + q], acc[t]);
+      }
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        const float sv = warp_sum(acc[t]);
+        if (lane == 0) Y[(size_t)t * L.ldy + o] = sv;
+      }
+    }
+    __syncthreads();
+    // Gram(Y_c) partial (one entry per warp) and core_c^T Y_c (one column per thread)
+    {
+      const int npairs = r * (r + 1) / 2;
+      for (int pq = warp; pq < npairs; pq += nwarps) {
+        int s0 = 0, rem = pq;
+        while (rem >= r - s0) {
+          rem -= r - s0;
+          ++s0;
+        }
+        const int t1 = s0 + rem;
+        float acc = 0.f;
+        for (int i = lane; i < nrow; i += 32) acc = fmaf(Y[(size_t)s0 * L.ldy + i], Y[(size_t)t1 * L.ldy + i], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) {
+          ra[s0 * R + t1] = acc;
+          ra[t1 * R + s0] = acc;
+        }
+      }
+      for (int j = threadIdx.x; j < nJ; j += blockDim.x) {
+        float acc[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) acc[t] = 0.f;
+        for (int i = 0; i < nrow; ++i) {
+          const float u = Uc[(size_t)i * ldu + j];
+#pragma unroll
+          for (int t = 0; t < R; ++t) acc[t] = fmaf(u, Y[(size_t)t * L.ldy + i], acc[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < R; ++t) Qp[(size_t)t * L.ldx + j] = acc[t];
+      }
+    }
     cl.sync();  // (1) partials written
-    cluster_sum(cl, ra, sm.G, R * R, stage);
-    for (int q = threadIdx.x; q < R * nJ; q += blockDim.x) {  // Q = sum of the partials, rank order
+    // the cluster sums, rank order: Gram(Y) and Q = core^T Y_raw
+    for (int q = threadIdx.x; q < R * R; q += blockDim.x) {
+      float v[ncl];
+#pragma unroll
+      for (int c = 0; c < ncl; ++c) v[c] = cl.map_shared_rank(ra, c)[q];
+      float sacc = 0.f;
+#pragma unroll
+      for (int c = 0; c < ncl; ++c) sacc += v[c];
+      sm.G[q] = sacc;
+    }
+    for (int q = threadIdx.x; q < R * nJ; q += blockDim.x) {
       const int t = q / nJ, b = q - t * nJ;
       const size_t at = (size_t)t * L.ldx + b;
       float v[ncl];
@@ -579,37 +722,39 @@ __device__ __forceinline__ void csvd_body(const IterDesc& d, int role, unsigned 
       for (int c = 0; c < ncl; ++c) sacc += v[c];
       Qs[at] = sacc;
     }
-    cl.sync();  // (2) partials read: they may be overwritten
-    chol_factor<R>(sm.G, r, sm.Rp, sm);                        // Y Rp = core X
-    chol_apply<R>(Qs, L.ldx, Qs, L.ldx, nJ, sm.Rp, sm);        // Q = core^T Y
-    // ||Q - X Rp^T||_F^2 and ||Rp||_F^2
-    float e2 = 0.f;
-    for (int b = threadIdx.x; b < nJ; b += blockDim.x) {
-      float xr[R];
+    cl.sync();  // (2) partials read; the sums are visible to the whole block
+    // Y Rp = core X: every warp factorises Gram(Y); Q = Q_raw Rp^{-1} row by
+    // row, with the residual ||Q - X Rp^T||_F^2 of each row
+    {
+      float* Up = warp == 0 ? sm.Rp : Uw;
+      float* dp = warp == 0 ? sm.dinv : dw;
+      warp_chol<R>(sm.G, r, Up, dp);
+      float e2 = 0.f;
+      for (int b = threadIdx.x; b < nJ; b += blockDim.x) {
+        float m[R], y[R], xr[R];
 #pragma unroll
-      for (int t = 0; t < R; ++t) xr[t] = X[(size_t)t * L.ldx + b];
+        for (int t = 0; t < R; ++t) {
+          m[t] = Qs[(size_t)t * L.ldx + b];
+          xr[t] = X[(size_t)t * L.ldx + b];
+        }
+        row_subst<R>(m, y, Up, dp);
 #pragma unroll
-      for (int t = 0; t < R; ++t) {
-        float v = Qs[(size_t)t * L.ldx + b];
+        for (int t = 0; t < R; ++t) {
+          Qs[(size_t)t * L.ldx + b] = y[t];
+          float v = y[t];
 #pragma unroll
-        for (int s2 = t; s2 < R; ++s2) v = fmaf(-xr[s2], sm.Rp[t * R + s2], v);
-        e2 = fmaf(v, v, e2);
+          for (int s2 = t; s2 < R; ++s2) v = fmaf(-xr[s2], Up[t * R + s2], v);
+          e2 = fmaf(v, v, e2);
+        }
       }
-    }
-    float rc2 = 0.f;
-    if (threadIdx.x < R * R) rc2 = sm.Rp[threadIdx.x] * sm.Rp[threadIdx.x];
-    e2 = warp_sum(e2);
-    rc2 = warp_sum(rc2);
-    if (lane == 0) {
-      sm.red[warp] = e2;
-      sm.red[32 + warp] = rc2;
+      e2 = warp_sum(e2);
+      if (lane == 0) sm.red[warp] = e2;
     }
     __syncthreads();
-    float E2 = 0.f, RC2 = 0.f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      E2 += sm.red[w];
-      RC2 += sm.red[32 + w];
-    }
+    float E2 = 0.f;
+    for (int w = 0; w < nwarps; ++w) E2 += sm.red[w];
+    float RC2 = 0.f;
+    for (int q = 0; q < R * R; ++q) RC2 = fmaf(sm.Rp[q], sm.Rp[q], RC2);
     const float res = sqrtf(E2), nrm = sqrtf(RC2);
     if (res <= 1e-6f * nrm || (steps > 1 && res > 0.5f * prev_res && res <= 1e-5f * nrm) || !(nrm > 0.f)) {
       converged = true;
@@ -617,18 +762,38 @@ __device__ __forceinline__ void csvd_body(const IterDesc& d, int role, unsigned 
     }
     if (steps >= d.svdMaxSteps) break;  // keep X, Y, Rp of the same step
     prev_res = res;
-    cholqr<R>(Qs, X, nJ, r, L.ldx, sm.U, sm);  // X = orth(core^T Y), in every CTA
+    cholqr_w<R>(Qs, L.ldx, X, L.ldx, nJ, r, sm.U, sm, slots);  // X = orth(core^T Y), in every CTA
   }
-  // Y of the last step: Y = (core X) Rp^{-1} (sm.dinv still belongs to Rp)
-  chol_apply<R>(Y, L.ldy, Y, L.ldy, nrow, sm.Rp, sm);
+  // Y of the last step: Y = (core X) Rp^{-1}
+  for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
+    float m[R], y[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) m[t] = Y[(size_t)t * L.ldy + i];
+    row_subst<R>(m, y, sm.Rp, sm.dinv);
+#pragma unroll
+    for (int t = 0; t < R; ++t) Y[(size_t)t * L.ldy + i] = y[t];
+  }
+  __syncthreads();
 
   // ---- second CholQR passes (Y over the cluster, X replicated); T = U2y Rp U2x^{-1}
   gram_block<R>(Y, nrow, L.ldy, r, ra);
   cl.sync();
   cluster_sum(cl, ra, sm.G, R * R, stage);
-  chol_factor<R>(sm.G, r, sm.U2y, sm);
-  chol_apply<R>(Y, L.ldy, Y, L.ldy, nrow, sm.U2y, sm);
-  cholqr<R>(X, X, nJ, r, L.ldx, sm.U2x, sm);
+  {
+    float* Up = warp == 0 ? sm.U2y : Uw;
+    float* dp = warp == 0 ? sm.dinv : dw;
+    warp_chol<R>(sm.G, r, Up, dp);
+    for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
+      float m[R], y[R];
+#pragma unroll
+      for (int t = 0; t < R; ++t) m[t] = Y[(size_t)t * L.ldy + i];
+      row_subst<R>(m, y, Up, dp);
+#pragma unroll
+      for (int t = 0; t < R; ++t) Y[(size_t)t * L.ldy + i] = y[t];
+    }
+  }
+  __syncthreads();
+  cholqr_w<R>(X, L.ldx, X, L.ldx, nJ, r, sm.U2x, sm, slots);
   if (threadIdx.x < 32) {
     const int s2 = threadIdx.x;
     if (s2 < r) {
