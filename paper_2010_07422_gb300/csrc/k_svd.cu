@@ -43,7 +43,6 @@ namespace ircur {
 namespace cg = cooperative_groups;
 
 constexpr int kSmallMats = 9;   // G, Rp, U, U2y, U2x, T, Ut, Vt, scratch (R x R each)
-constexpr size_t kSvdSmemBudget = 220 * 1024;
 
 __host__ __device__ constexpr int round_up4(int x) { return (x + 3) & ~3; }
 
@@ -105,84 +104,6 @@ __device__ void gram_block(const float* M, int nrows, int ld, int r, float* G) {
     }
   }
   __syncthreads();
-}
-
-// chol_factor: G = U^T U (warp 0; lane l holds row l of the Schur complement).
-// Pivots <= 1e-12 of the largest diagonal entry mark dependent columns: their
-// rows of U are zero and sm.dinv = 0.  Returns the number of such columns.
-template <int R>
-__device__ int chol_factor(const float* G, int r, float* Uout, const SvdSmall& sm) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (warp == 0) {
-    float g[R];
-#pragma unroll
-    for (int u = 0; u < R; ++u) g[u] = (lane < r && u < r) ? G[lane * R + u] : 0.f;
-    float maxd = sel<R>(g, lane);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) maxd = fmaxf(maxd, __shfl_xor_sync(0xffffffffu, maxd, o));
-    int brk = 0;
-    for (int t = 0; t < r; ++t) {
-      const float gt = sel<R>(g, t);  // entry (lane, t) = (t, lane) of the Schur complement
-      const float dgt = __shfl_sync(0xffffffffu, gt, t);
-      const bool keep = dgt > 1e-12f * maxd && dgt <= FLT_MAX;
-      const float rinv = keep ? rsqrtf(dgt) : 0.f;
-      const float ul = gt * rinv;  // U(t, lane)
-      float urow[R];
-#pragma unroll
-      for (int u = 0; u < R; ++u) urow[u] = __shfl_sync(0xffffffffu, ul, u);  // U(t, u)
-      if (lane == 0) {
-#pragma unroll
-        for (int u = 0; u < R; ++u) Uout[t * R + u] = (u >= t) ? urow[u] : 0.f;
-        sm.dinv[t] = rinv;
-      }
-      if (lane > t) {
-#pragma unroll
-        for (int u = 0; u < R; ++u) g[u] = fmaf(-ul, urow[u], g[u]);
-      }
-      brk += keep ? 0 : 1;
-    }
-    if (lane == 0) {
-      for (int t = r; t < R; ++t) {
-        sm.dinv[t] = 0.f;
-        for (int u = 0; u < R; ++u) Uout[t * R + u] = 0.f;
-      }
-      sm.ibuf[0] = brk;
-    }
-  }
-  __syncthreads();
-  const int brk = sm.ibuf[0];
-  return brk;
-}
-
-// chol_apply: Mout = Min U^{-1} row by row (forward substitution y U = m).
-template <int R>
-__device__ void chol_apply(const float* Min, int ldin, float* Mout, int ldout, int nrows, const float* U,
-                           const SvdSmall& sm) {
-  for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
-    float m[R], y[R];
-#pragma unroll
-    for (int s = 0; s < R; ++s) m[s] = Min[(size_t)s * ldin + i];
-#pragma unroll
-    for (int t = 0; t < R; ++t) {
-      float v = m[t];
-#pragma unroll
-      for (int s = 0; s < t; ++s) v = fmaf(-y[s], U[s * R + t], v);
-      y[t] = v * sm.dinv[t];
-    }
-#pragma unroll
-    for (int t = 0; t < R; ++t) Mout[(size_t)t * ldout + i] = y[t];
-  }
-  __syncthreads();
-}
-
-// Cholesky QR of the nrows x r block Min (column-major, stride ldm) into Mout
-// (may alias): Min = Mout U with U upper triangular (written to Uout).
-template <int R>
-__device__ int cholqr(const float* Min, float* Mout, int nrows, int r, int ldm, float* Uout, const SvdSmall& sm) {
-  gram_block<R>(Min, nrows, ldm, r, sm.G);
-  const int brk = chol_factor<R>(sm.G, r, Uout, sm);
-  chol_apply<R>(Min, ldm, Mout, ldm, nrows, Uout, sm);
-  return brk;
 }
 
 __device__ __forceinline__ float hash_uniform(uint64_t seed, uint64_t ctr) {
@@ -356,9 +277,8 @@ struct CsvdLayout {
   int ldy;      // column stride of the local Y block (mr rounded up to 4)
   int ldx;      // column stride of X and of the Q partial (nJ rounded up to 4)
   int js;       // rows of the outputs X T^{-1}, X T^T each CTA writes
-  int pch;      // inner-dimension chunks of the local product
-  size_t off_uc, off_x, off_y, off_qp, off_qs, off_part, off_ra, off_stage, off_slots, off_small, off_flag, off_bar,
-      total;
+  size_t off_uc, off_x, off_y, off_qp, off_qs, off_end_zero, off_ra, off_stage, off_slots, off_small, off_flag,
+      off_bar, total;
 };
 
 __host__ __device__ inline CsvdLayout csvd_layout(int nI, int nJ, int ldu, int R, int cl) {
@@ -368,12 +288,6 @@ __host__ __device__ inline CsvdLayout csvd_layout(int nI, int nJ, int ldu, int R
   L.ldx = round_up4(nJ);
   L.js = (nJ + cl - 1) / cl;
   const size_t small = (size_t)kSmallMats * R * R * 4 + 4 * 32 * 4 + 64;
-  const size_t fixed = (size_t)L.mr * ldu * 4 + 3 * (size_t)R * L.ldx * 4 + (size_t)R * L.ldy * 4 +
-                       (1 + (size_t)cl) * ((size_t)R * R + 4) * 4 + (size_t)(kCsvdThreads / 32) * (R * R + R) * 4 +
-                       small + 64;
-  int pch = 8;
-  while (pch > 1 && fixed + (size_t)pch * R * L.ldy * 4 > kSvdSmemBudget) --pch;
-  L.pch = pch;
   size_t off = 0;
   L.off_uc = off;
   off += (size_t)L.mr * ldu * 4;
@@ -385,8 +299,7 @@ __host__ __device__ inline CsvdLayout csvd_layout(int nI, int nJ, int ldu, int R
   off += (size_t)R * L.ldx * 4;
   L.off_qs = off;  // Q = core^T Y, full (every CTA holds the sum of the partials)
   off += (size_t)R * L.ldx * 4;
-  L.off_part = off;
-  off += (size_t)L.pch * R * L.ldy * 4;
+  L.off_end_zero = off;
   L.off_ra = off;
   off += ((size_t)R * R + 4) * 4;
   L.off_stage = off;  // cl x (R R + 4): remote partials gathered before a fixed-order sum
@@ -406,100 +319,6 @@ __host__ __device__ inline CsvdLayout csvd_layout(int nI, int nJ, int ldu, int R
 size_t csvd_smem_bytes(int nI, int nJ, int Rpad) {
   const CsvdLayout L = csvd_layout(nI, nJ, ld_core(nJ), Rpad, kSvdCluster);
   return L.total > sizeof(SamplerSmem) ? L.total : sizeof(SamplerSmem);
-}
-
-// out(o, t) = sum_q U(o, q) in(q, t), o < nout (the CTA's core rows): two rows
-// per thread, inner chunks, fixed-order chunk sums.
-template <int R>
-__device__ void cl_rows_times(const float* __restrict__ U, int ldu, int nout, int nin, const float* __restrict__ in,
-                              int ldin, float* __restrict__ out, int ldo, float* part, int pch) {
-  constexpr int RB = 2;
-  const int G = (nout + RB - 1) / RB;
-  const int lanes = G > 0 ? (G + 31) & ~31 : 32;
-  int nch = (int)blockDim.x / lanes;
-  nch = nch < 1 ? 1 : (nch > pch ? pch : nch);
-  const int c = threadIdx.x / lanes, og = threadIdx.x % lanes;
-  const int nin4 = round_up4(nin);
-  const int qc = round_up4((nin4 + nch - 1) / nch);
-  if (c < nch && og < G) {
-    float acc[RB][R];
-#pragma unroll
-    for (int kk = 0; kk < RB; ++kk)
-#pragma unroll
-      for (int t = 0; t < R; ++t) acc[kk][t] = 0.f;
-    const int q0 = c * qc, q1 = q0 + qc < nin4 ? q0 + qc : nin4;
-    for (int q = q0; q < q1; q += 4) {
-      float4 u[RB];
-#pragma unroll
-      for (int kk = 0; kk < RB; ++kk) {
-        const int o = og + kk * G;
-        u[kk] = o < nout ? *reinterpret_cast<const float4*>(U + (size_t)o * ldu + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        const float4 x = *reinterpret_cast<const float4*>(in + (size_t)t * ldin + q);
-#pragma unroll
-        for (int kk = 0; kk < RB; ++kk)
-          acc[kk][t] = fmaf(u[kk].w, x.w, fmaf(u[kk].z, x.z, fmaf(u[kk].y, x.y, fmaf(u[kk].x, x.x, acc[kk][t]))));
-      }
-    }
-#pragma unroll
-    for (int kk = 0; kk < RB; ++kk) {
-      const int o = og + kk * G;
-      if (o < nout) {
-#pragma unroll
-        for (int t = 0; t < R; ++t) part[((size_t)c * R + t) * ldo + o] = acc[kk][t];
-      }
-    }
-  }
-  __syncthreads();
-  for (int q = threadIdx.x; q < R * nout; q += blockDim.x) {
-    const int t = q / nout, o = q - t * nout;
-    float s = 0.f;
-    for (int cc = 0; cc < nch; ++cc) s += part[((size_t)cc * R + t) * ldo + o];
-    out[(size_t)t * ldo + o] = s;
-  }
-  __syncthreads();
-}
-
-// out(j, t) = sum_i U(i, j) y(i, t) over the CTA's nin core rows, j < nout:
-// four columns per thread (16-byte core vectors, 16-byte broadcasts of Y).
-// Rows of y beyond nin read as zero.
-template <int R>
-__device__ void cl_cols_times(const float* __restrict__ U, int ldu, int nout, int nin, const float* __restrict__ y,
-                              int ldy, float* __restrict__ out, int ldo) {
-  const int G = (nout + 3) / 4;
-  const int nin4 = round_up4(nin);
-  for (int g = threadIdx.x; g < G; g += blockDim.x) {
-    const int j = 4 * g;
-    float acc[4][R];
-#pragma unroll
-    for (int e = 0; e < 4; ++e)
-#pragma unroll
-      for (int t = 0; t < R; ++t) acc[e][t] = 0.f;
-    for (int i = 0; i < nin4; i += 4) {
-      float4 u[4];
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-        u[kk] = (i + kk < nin) ? *reinterpret_cast<const float4*>(U + (size_t)(i + kk) * ldu + j)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        const float4 yv = *reinterpret_cast<const float4*>(y + (size_t)t * ldy + i);
-        acc[0][t] = fmaf(u[3].x, yv.w, fmaf(u[2].x, yv.z, fmaf(u[1].x, yv.y, fmaf(u[0].x, yv.x, acc[0][t]))));
-        acc[1][t] = fmaf(u[3].y, yv.w, fmaf(u[2].y, yv.z, fmaf(u[1].y, yv.y, fmaf(u[0].y, yv.x, acc[1][t]))));
-        acc[2][t] = fmaf(u[3].z, yv.w, fmaf(u[2].z, yv.z, fmaf(u[1].z, yv.y, fmaf(u[0].z, yv.x, acc[2][t]))));
-        acc[3][t] = fmaf(u[3].w, yv.w, fmaf(u[2].w, yv.z, fmaf(u[1].w, yv.y, fmaf(u[0].w, yv.x, acc[3][t]))));
-      }
-    }
-#pragma unroll
-    for (int e = 0; e < 4; ++e)
-      if (j + e < nout) {
-#pragma unroll
-        for (int t = 0; t < R; ++t) out[(size_t)t * ldo + j + e] = acc[e][t];
-      }
-  }
-  __syncthreads();
 }
 
 // dst[q] = sum over the cluster's CTAs (rank order) of src[q], q < count: the
@@ -553,7 +372,6 @@ __device__ __forceinline__ void csvd_body(const IterDesc& d, int role, unsigned 
   float* Y = reinterpret_cast<float*>(smem + L.off_y);
   float* Qp = reinterpret_cast<float*>(smem + L.off_qp);
   float* Qs = reinterpret_cast<float*>(smem + L.off_qs);
-  float* part = reinterpret_cast<float*>(smem + L.off_part);
   float* ra = reinterpret_cast<float*>(smem + L.off_ra);  // Gram(Y) partial
   float* stage = reinterpret_cast<float*>(smem + L.off_stage);
   float* slots = reinterpret_cast<float*>(smem + L.off_slots);
@@ -600,7 +418,7 @@ __device__ __forceinline__ void csvd_body(const IterDesc& d, int role, unsigned 
   }
   // ---- X, Y, Qp, Qs zeroed (padding rows read as zero); X = B_k(:,J)^T
   {
-    const size_t nz = (L.off_part - L.off_x) / 4;
+    const size_t nz = (L.off_end_zero - L.off_x) / 4;
     for (size_t q = threadIdx.x; q < nz; q += blockDim.x) X[q] = 0.f;
   }
   __syncthreads();
