@@ -462,6 +462,9 @@ def main():
     Lt = p.L_entries(ri, ci)
     rel_err_truth = float(np.linalg.norm(Lg - Lt) / np.linalg.norm(Lt))
 
+    # Alg. 2 (CUR to SVD) of the last iterate, on request after the solve
+    c2s_us = 1e3 * _timed(lambda: solver.svd(), 5, stream)
+
     # Per-kernel spans of the last timed step (device clock, inside the graph)
     spans = ir.ircur_get_trace(solver._ctx, 100)
     K = len(spans)
@@ -610,6 +613,7 @@ def main():
             "roofline_other": {kk: vv for kk, vv in roofs.items() if kk != dominant},
             "kernel_us_per_step": per_step_us,
             "autotune": tune,
+            "cur_to_svd_us": c2s_us,
             "timing_note": "kernel spans from the device clock (first block start to last block end) inside "
                            "the CUDA graph (the pass kernel from the moment it stops waiting for the core SVD: "
                            "it is launched as a programmatic dependent and overlaps the SVD's tail); the "

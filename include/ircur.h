@@ -210,6 +210,18 @@ ircur_status ircur_get_trace(ircur_ctx* ctx, double* span_us, int32_t* iters);
 ircur_status ircur_solve_noalloc(const ircur_params* params, const float* D, int64_t ldD, float* A, float* B,
                                  ircur_result* out, void* stream);
 
+/* Algorithm 2 (CUR to SVD) for the last solve's iterate L = C U^+ R:
+ * L = W diag(sigma) V^T with W (n1 x r) and V (n2 x r) orthonormal and sigma
+ * (r values) in descending order.  Computed from the skinny factors
+ * (L = A B): one pass over A and B forming A^T A and B B^T with FP64
+ * accumulation, their Cholesky factors, the SVD of the r x r product R_A R_B^T
+ * (FP64 Jacobi), then W = A R_A^{-1} P and V = B^T R_B^{-1} Q -- the
+ * orthonormal factors of Alg. 2's QRs are never formed.  W, V: device,
+ * row-major with leading dimension r; sigma: device.  Columns beyond the
+ * numerical rank have sigma = 0.  ESTATE before a solve; the first call
+ * allocates a small scratch buffer (about 8 (n1 + n2) r^2 / 256 bytes). */
+ircur_status ircur_get_svd(ircur_ctx* ctx, float* W, float* sigma, float* V);
+
 /* Differentiation of unrolled IRCUR-F.
  * ircur_set_record(ctx, 1) makes the following ircur_solve calls record, for
  * every iteration k, the factors of L_k and the core's factorisation (about

@@ -111,6 +111,7 @@ struct ircur_ctx {
   float* adjE[2];
   float* adjF[2];
   int recorded;  // the last solve recorded its iterations
+  void* c2s_ws;  // scratch of ircur_get_svd
 };
 
 static void reset_graph(ircur_ctx* c) {
@@ -310,6 +311,7 @@ extern "C" void ircur_destroy(ircur_ctx* c) {
   for (int q = 0; q < 17; ++q)
     if (c->hev[q]) cudaEventDestroy(c->hev[q]);
   if (c->rec_ws) cudaFree(c->rec_ws);
+  if (c->c2s_ws) cudaFree(c->c2s_ws);
   if (c->ws) cudaFree(c->ws);
   delete c;
 }
@@ -669,6 +671,24 @@ extern "C" ircur_status ircur_get_factors(ircur_ctx* c, float* A, float* B) {
                                cudaMemcpyDeviceToDevice, c->stream));
   if (B)
     IRCUR_CK(cudaMemcpyAsync(B, c->B[K & 1], (size_t)r * c->p.n2 * 4, cudaMemcpyDeviceToDevice, c->stream));
+  return IRCUR_OK;
+}
+
+extern "C" ircur_status ircur_get_svd(ircur_ctx* c, float* W, float* sigma, float* V) {
+  if (!c || !W || !sigma || !V) return IRCUR_EINVAL;
+  if (!c->solved) return IRCUR_ESTATE;
+  const ircur_params& p = c->p;
+  if (!c->c2s_ws) {
+    cudaError_t e = cudaMalloc(&c->c2s_ws, cur_to_svd_scratch_bytes(p.n1, p.n2, c->Rpad));
+    if (e != cudaSuccess) {
+      set_error("cudaMalloc(ircur_get_svd scratch)", e);
+      cudaGetLastError();
+      c->c2s_ws = nullptr;
+      return IRCUR_ENOMEM;
+    }
+  }
+  const int K = c->host_state.k;
+  IRCUR_CK(launch_cur_to_svd(c->A[K & 1], c->B[K & 1], p.n1, p.n2, p.r, c->Rpad, c->c2s_ws, W, sigma, V, c->stream));
   return IRCUR_OK;
 }
 

@@ -208,6 +208,10 @@ cudaError_t launch_adj_step(const AdjStep& a, int Rpad, bool need_next, cudaStre
 size_t adj_cg_smem_bytes(int nI, int nJ, int Rpad);
 cudaError_t launch_adj_scatter(const AdjStep& a, float* dD, int64_t lddD, cudaStream_t s);
 size_t pass_smem_bytes(int nI, int nJ, int Rpad, int* nbuf = nullptr, bool bf16 = false, bool single = false);
+// Alg. 2 on the factored iterate (k_cur2svd.cu).
+size_t cur_to_svd_scratch_bytes(int64_t n1, int64_t n2, int Rpad);
+cudaError_t launch_cur_to_svd(const float* A, const float* B, int64_t n1, int64_t n2, int r, int Rpad, void* scratch,
+                              float* W, float* sigma, float* V, cudaStream_t s);
 // Shared memory per CTA of the cluster core SVD.
 size_t csvd_smem_bytes(int nI, int nJ, int Rpad);
 // Blocks of the pass kernel that are resident on the whole GPU at once.

@@ -27,6 +27,7 @@ EXPORTED = (
     "ircur_status_string", "ircur_last_error_string", "ircur_solve_noalloc", "ircur_set_trace",
     "ircur_get_trace", "ircur_get_cur", "ircur_batch_create", "ircur_batch_destroy", "ircur_batch_solve",
     "ircur_batch_instance", "ircur_set_record", "ircur_backward", "ircur_autotune", "ircur_batch_autotune",
+    "ircur_get_svd",
 )
 
 
@@ -95,6 +96,7 @@ def _lib():
         lib.ircur_batch_instance.restype = P
         lib.ircur_set_record.argtypes = [P, I32]
         lib.ircur_backward.argtypes = [P, P, I64, P, I64, P, I64, P, I64]
+        lib.ircur_get_svd.argtypes = [P, P, P, P]
         lib.ircur_autotune.argtypes = [P, P, I64, I32, C.POINTER(ircur_tune_result)]
         lib.ircur_batch_autotune.argtypes = [P, C.POINTER(P), C.POINTER(I64), I32, C.POINTER(ircur_tune_result)]
         lib.ircur_status_string.argtypes = [C.c_int]
@@ -205,6 +207,10 @@ def ircur_solve_noalloc(params: ircur_params, D, ldD, A, B, stream=None):
     _check(_lib().ircur_solve_noalloc(C.byref(params), _ptr(D), ldD, _ptr(A), _ptr(B), C.byref(res), stream),
            "ircur_solve_noalloc")
     return res
+
+
+def ircur_get_svd(ctx, W, sigma, V):
+    _check(_lib().ircur_get_svd(ctx, _ptr(W), _ptr(sigma), _ptr(V)), "ircur_get_svd")
 
 
 def ircur_set_record(ctx, enable):
@@ -331,6 +337,16 @@ class IRCUR:
 
     def errors(self):
         return ircur_get_errors(self._ctx, self.p.max_iter)
+
+    def svd(self):
+        """Alg. 2: L = W diag(sigma) V^T of the last iterate (W: n1 x r, V: n2 x r)."""
+        import torch
+        r = self.p.r
+        W = torch.empty((self.p.n1, r), dtype=torch.float32, device="cuda")
+        V = torch.empty((self.p.n2, r), dtype=torch.float32, device="cuda")
+        sig = torch.empty(r, dtype=torch.float32, device="cuda")
+        ircur_get_svd(self._ctx, W, sig, V)
+        return W, sig, V
 
     def autotune(self, D, reps=3):
         """Time the pass-kernel launch shapes on D and keep the fastest (see include/ircur.h)."""
