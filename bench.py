@@ -53,6 +53,9 @@ def parse_args():
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the headline line: one JSON line per configuration of the size sweep "
                          "(n in 1000, 2500, 5000, 10000, 20000; r in 5, 10; alpha in 0.1, 0.2, 0.3; F and R)")
+    ap.add_argument("--phase-transition", action="store_true",
+                    help="instead of the headline line: recovery rates over (c_I, alpha) at n = 1000 "
+                         "(50 trials per cell, r = 5 and 10, IRCUR-F and -R) on the batched solver")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default pass launch shape (fixed launch sequence, for profiling)")
     ap.add_argument("--no-extras", action="store_true",
@@ -372,10 +375,63 @@ def run_sweep(a):
                 del D
 
 
+def run_phase_transition(a, n=1000, trials=50, c_values=(0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0, 4.5, 5.0),
+                         alphas=(0.05, 0.1, 0.15, 0.2, 0.25, 0.3, 0.35, 0.4, 0.45, 0.5)):
+    """Empirical phase transition in (c_I, alpha) (Sec. 4.1, Fig. 1) on the
+    batched solver: n = 1000, |I| = |J| = ceil(c_I r ln n), planted problems of
+    the supplement's synthetic setup (outliers uniform in [-E|L|, E|L|],
+    zeta_0 = 2 ||L||_inf, gamma = 0.65, stop at e_k <= 1e-5, at most 100
+    iterations); success = ||L - L_true||_F / ||L_true||_F <= 1e-3.  One batch
+    of len(alphas) x trials problems per (r, variant, c_I)."""
+    import torch
+    from paper_2010_07422_gb300 import ircur as ir
+    from paper_2010_07422_gb300 import synth
+    t_all = time.perf_counter()
+    solves, t_solves = 0, 0.0
+    for r in (5, 10):
+        for variant in ("F", "R"):
+            for c_I in c_values:
+                m = int(min(n, math.ceil(c_I * r * math.log(n))))
+                probs, gens = [], []
+                for ai, alpha in enumerate(alphas):
+                    for tr in range(trials):
+                        seed = 1_000_003 * r + 10_007 * ai + tr
+                        D, W, V = synth.planted_device(n, n, r, alpha, seed=seed, outlier_scale=1.0,
+                                                       return_factors=True)
+                        z0 = 2.0 * float((W @ V.T).abs().max())
+                        gens.append((D, W, V))
+                        probs.append(dict(n1=n, n2=n, r=r, nI=m, nJ=m, resample=(variant == "R"), seed=seed,
+                                          zeta0=z0, gamma=0.65, tol=1e-5, max_iter=100))
+                batch = ir.IRCURBatch(probs)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                batch.solve([g[0] for g in gens])
+                torch.cuda.synchronize()
+                t_solve = time.perf_counter() - t0
+                t_solves += t_solve
+                solves += len(probs)
+                ok = []
+                for i, (D, W, V) in enumerate(gens):
+                    A, B = batch[i].factors()
+                    Lt = W @ V.T
+                    ok.append(float(torch.linalg.norm(A @ B - Lt) / torch.linalg.norm(Lt)) <= 1e-3)
+                batch.close()
+                rates = [sum(ok[ai * trials:(ai + 1) * trials]) / trials for ai in range(len(alphas))]
+                print(json.dumps({"phase_transition": True, "n": n, "r": r, "variant": variant, "c_I": c_I,
+                                  "m": m, "alphas": list(alphas), "success_rate": rates, "trials": trials,
+                                  "batch_solve_s": round(t_solve, 4)}), flush=True)
+                del gens
+    print(json.dumps({"phase_transition_total_s": round(time.perf_counter() - t_all, 1), "solves": solves,
+                      "batch_solve_total_s": round(t_solves, 3)}), flush=True)
+
+
 def main():
     a = parse_args()
     if a.sweep:
         run_sweep(a)
+        return
+    if a.phase_transition:
+        run_phase_transition(a)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -156,10 +156,11 @@ def video_like(h, w, frames, seed, n_rects=(5, 20), noise_std=1e-3, fg_fraction=
     return Video(D=D.astype(np.float32), background=bg, fg_mask=mask)
 
 
-def planted_device(n1, n2, r, alpha, seed, outlier_scale=10.0, device="cuda"):
+def planted_device(n1, n2, r, alpha, seed, outlier_scale=10.0, device="cuda", return_factors=False):
     """The ``planted`` recipe on the device: L = W V^T (W, V ~ N(0,1), FP32),
     round(alpha n1 n2) outliers on a uniform random support, values uniform in
-    [-s mean|L|, s mean|L|].  Returns the n1 x n2 FP32 tensor D = L + S."""
+    [-s mean|L|, s mean|L|].  Returns the n1 x n2 FP32 tensor D = L + S (and
+    W, V when return_factors)."""
     import torch
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
@@ -171,6 +172,8 @@ def planted_device(n1, n2, r, alpha, seed, outlier_scale=10.0, device="cuda"):
     pos = torch.randperm(n1 * n2, generator=g, device=device)[:k]
     val = (torch.rand(k, generator=g, device=device, dtype=torch.float32) * 2.0 - 1.0) * half
     D.view(-1).index_add_(0, pos, val)
+    if return_factors:
+        return D, W, V
     return D
 
 
