@@ -50,8 +50,8 @@ typedef enum {
 #define IRCUR_MAX_RANK 16
 
 /* ircur_params.precision.
- * FP32: every panel entry, product and threshold decision in FP32 (norms and
- *   the stopping value in FP64).
+ * FP32: every panel entry, product, threshold decision and stopping-value
+ *   sum in FP32 (fixed-order sums; the threshold schedule zeta_k in FP64).
  * BF16_PANELS (IRCUR-F only): the compact panels D(I,:) and D(:,J) are stored
  *   in BF16 (half their bytes); each iteration's threshold decision
  *   |D - L_k| > zeta is the FP32 one (an entry within BF16 rounding of zeta,

@@ -77,7 +77,7 @@ struct ircur_ctx {
   float* Vs;
   float* sigma;
   float* Tm;
-  double* partials;
+  float* partials;
   double* errs;
   State* st;
   // graph cache
@@ -135,7 +135,8 @@ static ircur_status validate_params(const ircur_params* p, ircur_params* out) {
   if (q.precision != IRCUR_PRECISION_FP32 && q.precision != IRCUR_PRECISION_BF16_PANELS) return IRCUR_ENOTSUP;
   if (q.precision == IRCUR_PRECISION_BF16_PANELS && q.resample != 0) return IRCUR_ENOTSUP;
   if (pass_smem_bytes(q.nI, q.nJ, pad_rank(q.r), nullptr, q.precision != 0) > 227 * 1024) return IRCUR_ENOTSUP;
-  if (csvd_smem_bytes(q.nI, q.nJ, pad_rank(q.r)) > 227 * 1024) return IRCUR_ENOTSUP;
+  if (!ssvd_fits(q.nI, q.nJ, pad_rank(q.r)) && csvd_smem_bytes(q.nI, q.nJ, pad_rank(q.r)) > 227 * 1024)
+    return IRCUR_ENOTSUP;
   if (!(q.gamma > 0.0 && q.gamma < 1.0)) return IRCUR_EINVAL;
   if (!(q.tol > 0.0)) return IRCUR_EINVAL;
   if (q.max_iter < 1) return IRCUR_EINVAL;
@@ -197,7 +198,7 @@ static ircur_status create_impl(const ircur_params* params, void* stream, int mi
   const size_t oW = take((size_t)p.nI * R * 4), oV = take((size_t)p.nJ * R * 4), oVs = take((size_t)p.nJ * R * 4);
   const size_t oSig = take((size_t)R * 4);
   const size_t oTm = take((size_t)R * R * 4);
-  const size_t oPart = take((size_t)(d.nRowTiles + d.nColTiles) * 2 * 8);
+  const size_t oPart = take((size_t)(d.nRowTiles + d.nColTiles) * 2 * 4);
   const size_t oErr = take((size_t)p.max_iter * 8);
   const size_t oSt = take(sizeof(State));
   c->ws_bytes = off;
@@ -238,7 +239,7 @@ static ircur_status create_impl(const ircur_params* params, void* stream, int mi
   c->Vs = reinterpret_cast<float*>(base + oVs);
   c->sigma = reinterpret_cast<float*>(base + oSig);
   c->Tm = reinterpret_cast<float*>(base + oTm);
-  c->partials = reinterpret_cast<double*>(base + oPart);
+  c->partials = reinterpret_cast<float*>(base + oPart);
   c->errs = reinterpret_cast<double*>(base + oErr);
   c->st = reinterpret_cast<State*>(base + oSt);
   e = cudaMemsetAsync(c->ws, 0, c->ws_bytes, c->stream);
@@ -1000,8 +1001,8 @@ extern "C" ircur_status ircur_batch_create(const ircur_params* params, int32_t c
   const size_t oFlag = (oList + (size_t)count * 4 + 255) & ~(size_t)255;
   const size_t bytes = oFlag + 256;
   std::unique_ptr<int[]> tiles(new int[count + b->ngroups]);
+  // per group: the instances whose core SVD runs on one CTA, then those on a cluster
   std::unique_ptr<int[]> lists(new int[count]);
-  for (int q = 0; q < count; ++q) lists[q] = q;  // group-relative identity lists share one array
   cudaError_t e = cudaMalloc(&b->dws, bytes);
   if (e != cudaSuccess) {
     set_error("cudaMalloc(batch workspace)", e);
@@ -1020,16 +1021,25 @@ extern "C" ircur_status ircur_batch_create(const ircur_params* params, int32_t c
     bl.ds = b->ds + first;
     int* tb = tiles.get() + first + g;
     tb[0] = 0;
-    int maxNI = 1, roles = 1;
+    int maxNI = 1, roles = 1, nOne = 0, nCl = 0;
+    for (int q = 0; q < n; ++q) {
+      const ircur_params& p = b->inst[b->order[first + q]]->p;
+      if (ssvd_fits(p.nI, p.nJ, R)) ++nOne;
+    }
     for (int q = 0; q < n; ++q) {
       const ircur_ctx* c = b->inst[b->order[first + q]];
       const ircur_params& p = c->p;
-      const size_t ss = csvd_smem_bytes(p.nI, p.nJ, R);
+      const bool one = ssvd_fits(p.nI, p.nJ, R);
+      const size_t ss = one ? ssvd_smem_bytes(p.nI, p.nJ, R) : csvd_smem_bytes(p.nI, p.nJ, R);
       if (pass_smem_bytes(p.nI, p.nJ, R) > 227 * 1024 || ss > 227 * 1024) {
         ircur_batch_destroy(b);
         return IRCUR_ENOTSUP;
       }
-      if (ss > bl.svd_smem[0]) bl.svd_smem[0] = ss;
+      if (ss > bl.svd_smem[one ? 0 : 1]) bl.svd_smem[one ? 0 : 1] = ss;
+      if (one)
+        lists[first + (q - nCl)] = q;  // group-relative instance indices
+      else
+        lists[first + nOne + nCl++] = q;
       if (p.nI > bl.pass_mmax) bl.pass_mmax = p.nI;
       if (p.nJ > bl.pass_mmax) bl.pass_mmax = p.nJ;
       const int64_t t = (int64_t)tb[q] + c->desc.nRowTiles + c->desc.nColTiles;
@@ -1049,10 +1059,10 @@ extern "C" ircur_status ircur_batch_create(const ircur_params* params, int32_t c
       const int want = (4 * kNumSMsHint + n - 1) / n;
       bl.core_blocks = want < maxNI ? (want > 0 ? want : 1) : maxNI;
     }
-    bl.svd_list[0] = reinterpret_cast<const int*>(base + oList);
-    bl.svd_list[1] = bl.svd_list[0];
-    bl.svd_n[0] = n;
-    bl.svd_n[1] = 0;
+    bl.svd_list[0] = reinterpret_cast<const int*>(base + oList) + first;
+    bl.svd_list[1] = bl.svd_list[0] + nOne;
+    bl.svd_n[0] = nOne;
+    bl.svd_n[1] = n - nOne;
     bl.svd_roles = roles;
     bl.cond = 0;
     bl.any_active = b->any_active;

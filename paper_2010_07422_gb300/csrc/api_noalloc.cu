@@ -127,7 +127,7 @@ extern "C" ircur_status ircur_solve_noalloc(const ircur_params* params, const fl
   float* Vs = reinterpret_cast<float*>(take((size_t)p.nJ * R * 4));
   float* sigma = reinterpret_cast<float*>(take((size_t)R * 4));
   float* Tm = reinterpret_cast<float*>(take((size_t)R * R * 4));
-  double* partials = reinterpret_cast<double*>(take((size_t)(d.nRowTiles + d.nColTiles) * 2 * 8));
+  float* partials = reinterpret_cast<float*>(take((size_t)(d.nRowTiles + d.nColTiles) * 2 * 4));
   double* errs = reinterpret_cast<double*>(take((size_t)p.max_iter * 8));
   State* st = reinterpret_cast<State*>(take(sizeof(State)));
   if (off > kNaBytes) return IRCUR_EINVAL;  // cannot happen within the limits above

@@ -95,7 +95,7 @@ struct IterDesc {
   float* Vs;            // nJ x R   X T^{-1} (column-pass projection; zero for dropped directions)
   float* sigma;         // R        |diag T| (diagnostic)
   float* Tm;            // R x R    Rayleigh-Ritz matrix T = Y^T core X of the last iteration
-  double* partials;     // 2 per panel tile (row tiles, then column tiles)
+  float* partials;      // 2 per panel tile (row tiles, then column tiles)
   double* errs;         // max_iter
   State* st;
   int nRowTiles, nColTiles;
@@ -214,6 +214,10 @@ cudaError_t launch_cur_to_svd(const float* A, const float* B, int64_t n1, int64_
                               float* W, float* sigma, float* V, cudaStream_t s);
 // Shared memory per CTA of the cluster core SVD.
 size_t csvd_smem_bytes(int nI, int nJ, int Rpad);
+// One-CTA core SVD (R <= 8, the core in one SM's shared memory): its dynamic
+// shared memory, and whether it is the form used for this shape.
+size_t ssvd_smem_bytes(int nI, int nJ, int Rpad);
+bool ssvd_fits(int nI, int nJ, int Rpad);
 // Blocks of the pass kernel that are resident on the whole GPU at once.
 int pass_resident_blocks(const IterDesc& d, int Rpad);
 int pass_batch_resident_blocks(const BatchLaunch& b, int Rpad);

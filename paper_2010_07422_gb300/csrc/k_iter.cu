@@ -123,7 +123,7 @@ struct PassLayout {
   float* recon;
   float* part;  // kPassWarps x RX x kPanelCols
   float* outS;  // RX x kPanelCols
-  double* wsum; // kPassWarps x 2
+  float* wsum;  // kPassWarps x 2
 };
 
 __host__ __device__ inline size_t pass_layout_floats(int m, int rx, int nbuf, bool bf16 = false) {
@@ -148,7 +148,7 @@ __device__ inline PassLayout pass_layout(unsigned char* smem, int m, int rx, int
   L.recon = p + 2 * (size_t)m * rx;
   L.part = p + 3 * (size_t)m * rx;
   L.outS = L.part + (size_t)kPassWarps * rx * kPanelCols;
-  L.wsum = reinterpret_cast<double*>(L.outS + (size_t)rx * kPanelCols);  // 8-byte aligned: every piece is a multiple of 8 floats
+  L.wsum = L.outS + (size_t)rx * kPanelCols;
   return L;
 }
 
@@ -245,29 +245,25 @@ __device__ __forceinline__ void pass_stage_proj(const IterDesc& d, const PassLay
   __syncthreads();
 }
 
-// One tile: thresholded panel values, projections, explicit residuals.
+// One tile, first half: the thresholded values D - S in place (FP32 panels;
+// BF16 panels write them to the FP32 work buffer) and this thread's share of
+// ||D||^2.  Needs only the core kernel's outputs, not the SVD's.
 template <int R, bool COL, bool BF>
-__device__ __forceinline__ void pass_tile(const IterDesc& d, int k, float zeta, int lt, const PassLayout& L,
-                                          unsigned char* tileP, bool stage_proj) {
-  // FP32 panels: the tile is overwritten with D - S; BF16 panels: D - S goes
-  // to the FP32 work buffer
+__device__ __forceinline__ float pass_tile_threshold(const IterDesc& d, int k, float zeta, int lt,
+                                                     const PassLayout& L, unsigned char* tileP) {
   float* tileS = BF ? L.vbuf : reinterpret_cast<float*>(tileP);
   const uint16_t* tileH = reinterpret_cast<const uint16_t*>(tileP);
   constexpr int RX = (R + 3) & ~3;
   const int m = COL ? d.nJ : d.nI;
   const int64_t ncolsTotal = COL ? d.n1 : d.n2;
-  const int cur = k & 1, nxt = cur ^ 1;
+  const int cur = k & 1;
   const int lane = threadIdx.x & 31, h = threadIdx.x >> 5;
-  const int64_t j0 = (int64_t)lt * kPanelCols;
-  const int64_t j = j0 + lane;
+  const int64_t j = (int64_t)lt * kPanelCols + lane;
   const bool live = j < ncolsTotal;
   const float* side = L.side;
-  const float* proj = L.proj;
-  const float* recon = COL ? L.recon : L.proj;
-  float vec[R], acc[R];
+  float vec[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) {
-    acc[t] = 0.f;
     if (COL)
       vec[t] = live ? d.A[cur][j * R + t] : 0.f;
     else
@@ -276,7 +272,6 @@ __device__ __forceinline__ void pass_tile(const IterDesc& d, int k, float zeta, 
   const float msk = live ? 1.f : 0.f;
   const int a0 = h * m / kPassWarps, a1 = (h + 1) * m / kPassWarps;
   float den = 0.f;
-  // 1. thresholded values D - S and ||D||^2 (needs only the core kernel's outputs)
   for (int a = a0; a < a1; ++a) {
     float* cell = tileS + (size_t)a * kPanelCols + lane;
     float sr[R];
@@ -302,12 +297,35 @@ __device__ __forceinline__ void pass_tile(const IterDesc& d, int k, float zeta, 
     *cell = v;
     den = fmaf(dv, dv, den);
   }
-  // 2. the projections (need the core SVD's outputs)
+  return den;
+}
+
+// One tile, second half: the projections (they need the core SVD's outputs,
+// staged on the segment's first tile), the next factor rows and the explicit
+// residuals; this share's num/den go to wsum.
+template <int R, bool COL, bool BF>
+__device__ __forceinline__ void pass_tile_project(const IterDesc& d, int k, int lt, const PassLayout& L,
+                                                  unsigned char* tileP, float den, bool stage_proj) {
+  const float* tileS = BF ? L.vbuf : reinterpret_cast<const float*>(tileP);
+  constexpr int RX = (R + 3) & ~3;
+  const int m = COL ? d.nJ : d.nI;
+  const int64_t ncolsTotal = COL ? d.n1 : d.n2;
+  const int nxt = (k & 1) ^ 1;
+  const int lane = threadIdx.x & 31, h = threadIdx.x >> 5;
+  const int64_t j = (int64_t)lt * kPanelCols + lane;
+  const bool live = j < ncolsTotal;
+  const float* proj = L.proj;
+  const float* recon = COL ? L.recon : L.proj;
+  const float msk = live ? 1.f : 0.f;
+  const int a0 = h * m / kPassWarps, a1 = (h + 1) * m / kPassWarps;
   if (COL) {
     if (stage_proj) pass_stage_proj<R, true>(d, L, k);
   } else {
     if (stage_proj) pass_stage_proj<R, false>(d, L, k);
   }
+  float acc[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) acc[t] = 0.f;
   for (int a = a0; a < a1; ++a) {
     const float v = tileS[(size_t)a * kPanelCols + lane];
     float pr[R];
@@ -368,7 +386,7 @@ __device__ __forceinline__ void pass_tile(const IterDesc& d, int k, float zeta, 
   }
   // this share's sums; the tile's slot gets them in share order after the
   // block's end-of-tile barrier (pass_tile_sums)
-  const double sn = warp_sum((double)num), sd = warp_sum((double)den);
+  const float sn = warp_sum(num), sd = warp_sum(den);
   if (lane == 0) {
     L.wsum[2 * h + 0] = sn;
     L.wsum[2 * h + 1] = sd;
@@ -378,7 +396,7 @@ __device__ __forceinline__ void pass_tile(const IterDesc& d, int k, float zeta, 
 // After the end-of-tile barrier: the tile's num/den in its slot (share order).
 __device__ __forceinline__ void pass_tile_sums(const IterDesc& d, int gtile, const PassLayout& L) {
   if (threadIdx.x == 0) {
-    double sn = 0.0, sd = 0.0;
+    float sn = 0.f, sd = 0.f;
 #pragma unroll
     for (int h = 0; h < kPassWarps; ++h) {
       sn += L.wsum[2 * h + 0];
@@ -390,35 +408,59 @@ __device__ __forceinline__ void pass_tile_sums(const IterDesc& d, int gtile, con
 }
 
 // The block that completed an instance's last tile: e_{k+1} from the slots in
-// a fixed order, then k, zeta and the loop condition.
+// a fixed order, then k, zeta and the loop condition.  Every slot was written
+// before its block's fenced counter increment, which this block has seen:
+// the slots are read from L2 with no further fence.  The kernel's completion
+// orders the state writes before the next kernel and the graph's condition.
 __device__ void pass_finalize(const IterDesc& d, int k) {
   State* st = d.st;
-  __shared__ double fin[2][2];
+  __shared__ float fin[kPassWarps][4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __threadfence();
-  // warp q: q = 0,1 row-pass num/den; q = 2,3 column-pass num/den; lanes
-  // stride over the tiles with four independent accumulators
-  if (warp < 4) {
-    const int colside = warp >> 1, which = warp & 1;
-    const int b0 = colside ? d.nRowTiles : 0;
-    const int b1 = colside ? d.nRowTiles + d.nColTiles : d.nRowTiles;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int b = b0 + lane;
-    for (; b + 96 < b1; b += 128) {
-      s0 += __ldcg(d.partials + (size_t)b * 2 + which);
-      s1 += __ldcg(d.partials + (size_t)(b + 32) * 2 + which);
-      s2 += __ldcg(d.partials + (size_t)(b + 64) * 2 + which);
-      s3 += __ldcg(d.partials + (size_t)(b + 96) * 2 + which);
+  const int nr = d.nRowTiles, nt = d.nRowTiles + d.nColTiles;
+  const float2* slots = reinterpret_cast<const float2*>(d.partials);
+  // thread q adds tiles q, q + 256, ... (row panel to a0, a1, column panel to
+  // a2, a3); the loads of a group of four are all in flight together
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  for (int b = threadIdx.x; b < nt; b += 4 * kPassThreads) {
+    float2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int bb = b + u * kPassThreads;
+      v[u] = bb < nt ? __ldcg(slots + bb) : make_float2(0.f, 0.f);
     }
-    for (; b < b1; b += 32) s0 += __ldcg(d.partials + (size_t)b * 2 + which);
-    const double s = warp_sum((s0 + s1) + (s2 + s3));
-    if (lane == 0) fin[colside][which] = s;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int bb = b + u * kPassThreads;
+      if (bb < nr) {
+        a0 += v[u].x;
+        a1 += v[u].y;
+      } else {
+        a2 += v[u].x;
+        a3 += v[u].y;
+      }
+    }
+  }
+  a0 = warp_sum(a0);
+  a1 = warp_sum(a1);
+  a2 = warp_sum(a2);
+  a3 = warp_sum(a3);
+  if (lane == 0) {
+    fin[warp][0] = a0;
+    fin[warp][1] = a1;
+    fin[warp][2] = a2;
+    fin[warp][3] = a3;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const double num = sqrt(fin[0][0]) + sqrt(fin[1][0]);
-    const double den = sqrt(fin[0][1]) + sqrt(fin[1][1]);
-    const double e = den > 0.0 ? num / den : 0.0;
+    float f[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int w = 0; w < kPassWarps; ++w)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) f[q] += fin[w][q];
+    // e = (||row residual|| + ||column residual||) / (||D(I,:)|| + ||D(:,J)||)
+    const float num = sqrtf(f[0]) + sqrtf(f[2]);
+    const float den = sqrtf(f[1]) + sqrtf(f[3]);
+    const double e = den > 0.f ? (double)(num / den) : 0.0;
     d.errs[k] = e;
     st->e = e;
     st->k = k + 1;
@@ -427,7 +469,6 @@ __device__ void pass_finalize(const IterDesc& d, int k) {
     st->counter = 0u;
     const int done = (e <= d.tol) || (k + 1 >= d.max_iter) || (st->status != 0);
     st->done = done;
-    __threadfence();
     if (d.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)d.cond, done ? 0u : 1u);
   }
   __syncthreads();
@@ -446,8 +487,13 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
     }
     return;
   }
-  const int t0 = (int)((long long)blockIdx.x * total / gridDim.x);
-  const int t1 = (int)((long long)(blockIdx.x + 1) * total / gridDim.x);
+  // contiguous runs, the longer ones on the lowest block indices (the blocks
+  // launched last, which may start only once the SVD has left its SMs, get
+  // the shorter runs)
+  const int q = total / (int)gridDim.x, rem = total - q * (int)gridDim.x;
+  const int bx = (int)blockIdx.x;
+  const int t0 = bx * q + (bx < rem ? bx : rem);
+  const int t1 = t0 + q + (bx < rem ? 1 : 0);
   if (t0 >= t1) return;
   // tile -> (instance, side, local tile); instances are visited in order
   int inst = 0;
@@ -490,6 +536,8 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
   int seg_inst = -1, seg_col = -1, seg_k = 0, run = 0;
   bool proj_staged = false;
   float zeta = 0.f;
+  int early = -1;      // tile thresholded ahead of time (its den in den_early)
+  float den_early = 0.f;
   for (int t = t0; t < t1; ++t) {
     if (t > t0) cur = locate(t, inst);
     const IterDesc& d = BATCH ? ds[cur.inst] : d1;
@@ -513,9 +561,11 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
       cp_async_commit();
     }
     bool pre = false;
+    TileRef nx;
+    nx.active = 0;
     if (nbuf == 2 && t + 1 < t1) {
       int in2 = pin < inst ? inst : pin;
-      const TileRef nx = locate(t + 1, in2);
+      nx = locate(t + 1, in2);
       pin = in2;
       if (nx.active) {
         stage(nx, L.tiles + (size_t)(b ^ 1) * L.tile_bytes);
@@ -544,10 +594,28 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
     else
       cp_async_wait_group<0>();
     __syncthreads();
+    unsigned char* tb = L.tiles + (size_t)b * L.tile_bytes;
+    float den;
+    if (early == t) {
+      den = den_early;
+    } else {
+      den = cur.col ? pass_tile_threshold<R, true, BF>(d, seg_k, zeta, cur.lt, L, tb)
+                    : pass_tile_threshold<R, false, BF>(d, seg_k, zeta, cur.lt, L, tb);
+    }
+    // before the segment's first wait for the SVD: threshold the prefetched
+    // next tile of the same segment as well (FP32 panels: in its own buffer)
+    if (!BF && !proj_staged && pre && nx.inst == cur.inst && nx.col == cur.col) {
+      cp_async_wait_group<0>();
+      __syncthreads();
+      unsigned char* tn = L.tiles + (size_t)(b ^ 1) * L.tile_bytes;
+      den_early = cur.col ? pass_tile_threshold<R, true, BF>(d, seg_k, zeta, nx.lt, L, tn)
+                          : pass_tile_threshold<R, false, BF>(d, seg_k, zeta, nx.lt, L, tn);
+      early = t + 1;
+    }
     if (cur.col)
-      pass_tile<R, true, BF>(d, seg_k, zeta, cur.lt, L, L.tiles + (size_t)b * L.tile_bytes, !proj_staged);
+      pass_tile_project<R, true, BF>(d, seg_k, cur.lt, L, tb, den, !proj_staged);
     else
-      pass_tile<R, false, BF>(d, seg_k, zeta, cur.lt, L, L.tiles + (size_t)b * L.tile_bytes, !proj_staged);
+      pass_tile_project<R, false, BF>(d, seg_k, cur.lt, L, tb, den, !proj_staged);
     proj_staged = true;
     __syncthreads();
     pass_tile_sums(d, t - (BATCH ? tile_base[cur.inst] : 0), L);

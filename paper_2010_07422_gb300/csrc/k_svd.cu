@@ -32,6 +32,7 @@
 // orthogonality to FP32 rounding.
 #include <cooperative_groups.h>
 #include <float.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include "device_common.cuh"
@@ -719,8 +720,10 @@ __device__ __forceinline__ void csvd_body(const IterDesc& d, int role, unsigned 
   }
 }
 
+// Up to R = 7 the cluster SVD fits in 128 registers without spilling; the
+// cap leaves room on its SMs for the pass blocks that start while it runs.
 template <int R>
-__global__ void __launch_bounds__(kCsvdThreads, 1) csvd_kernel(IterDesc d) {
+__global__ void __launch_bounds__(kCsvdThreads, (R <= 7 ? 2 : 1)) csvd_kernel(IterDesc d) {
   extern __shared__ __align__(16) unsigned char smem[];
   // every CTA is resident from here on: the pass kernel may start on the
   // other SMs (it waits for this grid before reading its outputs)
@@ -731,16 +734,503 @@ __global__ void __launch_bounds__(kCsvdThreads, 1) csvd_kernel(IterDesc d) {
 // Batched form: cluster blockIdx.x / kSvdCluster factorises instance
 // list[blockIdx.x / kSvdCluster]; blockIdx.y is the role.
 template <int R>
-__global__ void __launch_bounds__(kCsvdThreads, 1) csvd_batch_kernel(const IterDesc* __restrict__ ds,
+__global__ void __launch_bounds__(kCsvdThreads, (R <= 7 ? 2 : 1)) csvd_batch_kernel(const IterDesc* __restrict__ ds,
                                                                     const int* __restrict__ list) {
   extern __shared__ __align__(16) unsigned char smem[];
   csvd_body<R>(ds[list[blockIdx.x / kSvdCluster]], blockIdx.y, smem);
+}
+
+// ---------------------------------------------------------------------------
+// Core SVD in one CTA, for cores that fit in one SM's shared memory (R <= 8,
+// where the padded rank equals r).  The same two-sided subspace iteration,
+// warm start and stopping rule as the cluster form above, with every
+// exchange inside one block of 1024 threads instead of across a cluster:
+//   P  = core X      threads (row i, column segment s) sum 16-byte column
+//                    quads of their row; thread i adds the segments in order
+//                    and forms its row's Gram(P) products
+//   Q~ = core^T P    threads (column quad q, row segment s), the same way
+//   Rp = chol(Gram P), Q = Q~ Rp^{-1}, the residual Q - X Rp^T and the
+//                    Gram(Q) products by thread j (Q stays in its registers)
+//   X  = Q chol(Gram Q)^{-1}
+// Factors of the r x r Gram matrices are formed redundantly by every warp
+// that owns rows, so the rows they transform need no further barrier: five
+// block barriers per step.  Every sum runs in a fixed order (bit-identical
+// results from launch to launch).
+constexpr int kSsvdThreads = 1024;
+constexpr int kSsvdMaxR = 8;
+constexpr int kSsvdSeg = 8;  // most segments of either partial product
+
+__host__ __device__ constexpr int npairs_of(int R) { return R * (R + 1) / 2; }
+
+struct SsvdLayout {
+  int nq;       // 16-byte column quads of the core, ceil(nJ / 4)
+  int ldx;      // column stride of X and of the core^T P partials (4 nq)
+  int ldy;      // column stride of the P partials (nI rounded up to 4)
+  int ps;       // row stride of P (R rounded up to 4)
+  int s1, qs1;  // P partials: column segments, quads per segment
+  int s3, rs3;  // core^T P partials: row segments, rows per segment
+  int nw;       // warps owning rows, ceil(max(nI, nJ) / 32)
+  int slot;     // floats per warp slot
+  size_t off_uc, off_x, off_p, off_part, off_red, off_slots, off_flag, off_bar, total;
+};
+
+__host__ __device__ inline SsvdLayout ssvd_layout(int nI, int nJ, int ldu, int R) {
+  SsvdLayout L;
+  const int nt = kSsvdThreads;
+  L.nq = (nJ + 3) / 4;
+  L.ldx = 4 * L.nq;
+  L.ldy = round_up4(nI);
+  L.ps = round_up4(R);
+  L.s1 = nt / (nI > 0 ? nI : 1);
+  L.s1 = L.s1 < 1 ? 1 : (L.s1 > kSsvdSeg ? kSsvdSeg : L.s1);
+  L.qs1 = (L.nq + L.s1 - 1) / L.s1;
+  L.s3 = nt / (L.nq > 0 ? L.nq : 1);
+  L.s3 = L.s3 < 1 ? 1 : (L.s3 > kSsvdSeg ? kSsvdSeg : L.s3);
+  L.rs3 = (nI + L.s3 - 1) / L.s3;
+  const int mx = nI > nJ ? nI : nJ;
+  L.nw = (mx + 31) / 32;
+  L.slot = 6 * R * R + 3 * R;
+  const size_t part = (size_t)R * ((size_t)L.s1 * L.ldy > (size_t)L.s3 * L.ldx ? (size_t)L.s1 * L.ldy
+                                                                               : (size_t)L.s3 * L.ldx);
+  size_t off = 0;
+  L.off_uc = off;
+  off += (size_t)nI * ldu * 4;
+  L.off_x = off;
+  off += (size_t)R * L.ldx * 4;
+  L.off_p = off;
+  off += (size_t)nI * L.ps * 4;
+  L.off_part = off;
+  off += part * 4;
+  L.off_red = off;  // per warp: Gram pairs (two sets) and one residual sum
+  off += (size_t)L.nw * (2 * npairs_of(R) + 1) * 4;
+  L.off_slots = off;
+  off += (size_t)L.nw * L.slot * 4;
+  L.off_flag = (off + 15) & ~(size_t)15;
+  off = L.off_flag + 16;
+  L.off_bar = off;
+  off += 16;
+  L.total = off;
+  return L;
+}
+
+size_t ssvd_smem_bytes(int nI, int nJ, int Rpad) {
+  if (Rpad > kSsvdMaxR || nI > kSsvdThreads || nJ > kSsvdThreads || nI < 1 || nJ < 1) return ~(size_t)0;
+  const SsvdLayout L = ssvd_layout(nI, nJ, ld_core(nJ), Rpad);
+  return L.total > sizeof(SamplerSmem) ? L.total : sizeof(SamplerSmem);
+}
+
+bool ssvd_fits(int nI, int nJ, int Rpad) {
+  static const int on = getenv("IRCUR_SSVD") != nullptr;
+  return on && ssvd_smem_bytes(nI, nJ, Rpad) <= 227 * 1024;
+}
+
+// The Gram products of one row (a) summed over the warp; lane 0 writes the
+// R(R+1)/2 upper-triangle sums to out.
+template <int R>
+__device__ __forceinline__ void warp_pair_sums(const float (&a)[R], float* out) {
+  int p = 0;
+#pragma unroll
+  for (int s0 = 0; s0 < R; ++s0) {
+#pragma unroll
+    for (int t1 = s0; t1 < R; ++t1) {
+      const float v = warp_sum(a[s0] * a[t1]);
+      if ((threadIdx.x & 31) == 0) out[p] = v;
+      ++p;
+    }
+  }
+}
+
+// Gw = the sum over warps 0..nw-1 (in order) of their pair sums, both triangles.
+template <int R>
+__device__ __forceinline__ void gram_from_pairs(const float* red, int stride, int nw, float* Gw) {
+  const int lane = threadIdx.x & 31;
+  constexpr int np = npairs_of(R);
+  for (int p = lane; p < np; p += 32) {
+    float v = 0.f;
+    for (int w = 0; w < nw; ++w) v += red[w * stride + p];
+    int s0 = 0, rem = p;
+    while (rem >= R - s0) {
+      rem -= R - s0;
+      ++s0;
+    }
+    const int t1 = s0 + rem;
+    Gw[s0 * R + t1] = v;
+    Gw[t1 * R + s0] = v;
+  }
+  __syncwarp();
+}
+
+template <int R>
+__device__ __forceinline__ void ssvd_body(const IterDesc& d, int role, unsigned char* smem) {
+  static_assert(R <= kSsvdMaxR, "one-CTA core SVD is built for R <= 8");
+  State* st = d.st;
+  if (st->done || st->status) return;  // the same for every thread: the state is fixed during the launch
+  const int k = st->k;
+  if (role > 0) {
+    const int axis = role - 1;
+    if (d.sampleAhead && k + 1 < d.max_iter) {
+      int* out = axis ? const_cast<int*>(d.J_all) + (int64_t)(k + 1) * d.nJ
+                      : const_cast<int*>(d.I_all) + (int64_t)(k + 1) * d.nI;
+      sample_subset(d.seed, k + 1, axis, axis ? d.n2 : d.n1, axis ? d.nJ : d.nI, out,
+                    *reinterpret_cast<SamplerSmem*>(smem));
+    }
+    return;
+  }
+  trace_start(d.trace, 3 * k + 1);
+  const int nI = d.nI, nJ = d.nJ, ldu = d.ldCore;
+  constexpr int np = npairs_of(R);
+  const SsvdLayout L = ssvd_layout(nI, nJ, ldu, R);
+  float* Uc = reinterpret_cast<float*>(smem + L.off_uc);
+  float* X = reinterpret_cast<float*>(smem + L.off_x);
+  float* P = reinterpret_cast<float*>(smem + L.off_p);
+  float* part = reinterpret_cast<float*>(smem + L.off_part);
+  float* redA = reinterpret_cast<float*>(smem + L.off_red);  // nw x np
+  float* redB = redA + (size_t)L.nw * np;                     // nw x np
+  float* redE = redB + (size_t)L.nw * np;                     // nw
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.off_bar);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool rowwarp = warp < L.nw;
+  // this warp's slot: Gram scratch, Rp (+ reciprocal pivots), Uq / U2y, U2x, T, T^{-1}
+  float* Gw = reinterpret_cast<float*>(smem + L.off_slots) + (size_t)(rowwarp ? warp : 0) * L.slot;
+  float* Rpw = Gw + R * R;
+  float* dRp = Rpw + R * R;
+  float* Uqw = dRp + R;
+  float* dUq = Uqw + R * R;
+  float* U2x = dUq + R;
+  float* dU2x = U2x + R * R;
+  float* Tw = dU2x + R;
+  float* Utw = Tw + R * R;
+
+  // ---- the core into shared memory: one bulk copy
+  const unsigned bytes = (unsigned)((size_t)nI * ldu * 4);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_g2s(Uc, d.core, bytes, bar);
+  }
+  for (int q = tid; q < R * L.ldx; q += blockDim.x) X[q] = 0.f;
+  // ---- X = orth(B_k(:,J)^T), or a random start when that is deficient
+  float xb[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) xb[t] = (tid < nJ) ? d.BJt[(size_t)tid * R + t] : 0.f;
+  if (rowwarp) warp_pair_sums<R>(xb, redB + warp * np);
+  __syncthreads();
+  int brk = 0;
+  if (rowwarp) {
+    gram_from_pairs<R>(redB, np, L.nw, Gw);
+    brk = warp_chol<R>(Gw, R, Uqw, dUq);
+    if (brk == 0) {
+      if (tid < nJ) {
+        float y[R];
+        row_subst<R>(xb, y, Uqw, dUq);
+#pragma unroll
+        for (int t = 0; t < R; ++t) X[(size_t)t * L.ldx + tid] = y[t];
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < R; ++t)
+        xb[t] = (tid < nJ)
+                    ? hash_uniform(d.seed ^ 0x5bd1e995ull, ((uint64_t)k << 32) ^ (uint64_t)(tid * R + t))
+                    : 0.f;
+      warp_pair_sums<R>(xb, redA + warp * np);
+    }
+  }
+  __syncthreads();
+  if (rowwarp && brk > 0) {  // brk is the same in every row warp
+    gram_from_pairs<R>(redA, np, L.nw, Gw);
+    warp_chol<R>(Gw, R, Uqw, dUq);
+    if (tid < nJ) {
+      float y[R];
+      row_subst<R>(xb, y, Uqw, dUq);
+#pragma unroll
+      for (int t = 0; t < R; ++t) X[(size_t)t * L.ldx + tid] = y[t];
+    }
+  }
+  bool ok = mbar_wait_bounded(bar, 0, d.spinLimit);
+  if (!ok) {
+    if (tid == 0) atomicExch(&st->status, (int)IRCUR_ETIMEOUT);
+    mbar_wait_bounded(bar, 0, kSpinLimit);  // let the copy land before the block exits
+  }
+  if (!__syncthreads_and(ok)) return;
+  // columns nJ .. 4 nq of the last quad read as zero
+  for (int q = tid; q < nI * (L.ldx - nJ); q += blockDim.x) {
+    const int i = q / (L.ldx - nJ), c = nJ + q % (L.ldx - nJ);
+    Uc[(size_t)i * ldu + c] = 0.f;
+  }
+  __syncthreads();
+
+  // ---- subspace iteration
+  const int seg1 = tid / nI, i1 = tid - seg1 * nI;      // P partials
+  const int seg3 = tid / L.nq, q3 = tid - seg3 * L.nq;  // core^T P partials
+  int steps = 0;
+  bool converged = false;
+  float prev_res = 0.f;
+  float qv[R];
+  while (true) {
+    ++steps;
+    if (seg1 < L.s1) {
+      float acc[R];
+#pragma unroll
+      for (int t = 0; t < R; ++t) acc[t] = 0.f;
+      const int qa = seg1 * L.qs1, qb = qa + L.qs1 < L.nq ? qa + L.qs1 : L.nq;
+      const float* urow = Uc + (size_t)i1 * ldu;
+      for (int q = qa; q < qb; ++q) {
+        const float4 u = *reinterpret_cast<const float4*>(urow + 4 * q);
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+          const float4 x = *reinterpret_cast<const float4*>(X + (size_t)t * L.ldx + 4 * q);
+          acc[t] = fmaf(u.x, x.x, acc[t]);
+          acc[t] = fmaf(u.y, x.y, acc[t]);
+          acc[t] = fmaf(u.z, x.z, acc[t]);
+          acc[t] = fmaf(u.w, x.w, acc[t]);
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < R; ++t) part[(size_t)(seg1 * R + t) * L.ldy + i1] = acc[t];
+    }
+    __syncthreads();
+    if (rowwarp) {
+      float pv[R];
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        float v = 0.f;
+        if (tid < nI)
+          for (int s = 0; s < L.s1; ++s) v += part[(size_t)(s * R + t) * L.ldy + tid];
+        pv[t] = v;
+      }
+      if (tid < nI) {
+#pragma unroll
+        for (int t = 0; t < R; ++t) P[(size_t)tid * L.ps + t] = pv[t];
+      }
+      warp_pair_sums<R>(pv, redA + warp * np);
+    }
+    __syncthreads();
+    if (seg3 < L.s3) {
+      float acc[4][R];
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int t = 0; t < R; ++t) acc[c][t] = 0.f;
+      const int ia = seg3 * L.rs3, ib = ia + L.rs3 < nI ? ia + L.rs3 : nI;
+      for (int i = ia; i < ib; ++i) {
+        const float4 u = *reinterpret_cast<const float4*>(Uc + (size_t)i * ldu + 4 * q3);
+        const float4* prow = reinterpret_cast<const float4*>(P + (size_t)i * L.ps);
+        const float4 pa = prow[0];
+        const float4 pb = (R > 4) ? prow[1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float pall[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
+        float pr[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) pr[t] = pall[t];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+          acc[0][t] = fmaf(u.x, pr[t], acc[0][t]);
+          acc[1][t] = fmaf(u.y, pr[t], acc[1][t]);
+          acc[2][t] = fmaf(u.z, pr[t], acc[2][t]);
+          acc[3][t] = fmaf(u.w, pr[t], acc[3][t]);
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < R; ++t)
+        *reinterpret_cast<float4*>(part + (size_t)(seg3 * R + t) * L.ldx + 4 * q3) =
+            make_float4(acc[0][t], acc[1][t], acc[2][t], acc[3][t]);
+    }
+    __syncthreads();
+    if (rowwarp) {
+      // Rp: Y Rp = P (Y = P Rp^{-1} is never formed inside the loop)
+      gram_from_pairs<R>(redA, np, L.nw, Gw);
+      warp_chol<R>(Gw, R, Rpw, dRp);
+      float e2 = 0.f;
+#pragma unroll
+      for (int t = 0; t < R; ++t) qv[t] = 0.f;
+      if (tid < nJ) {
+        float m[R], xr[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+          float v = 0.f;
+          for (int s = 0; s < L.s3; ++s) v += part[(size_t)(s * R + t) * L.ldx + tid];
+          m[t] = v;
+          xr[t] = X[(size_t)t * L.ldx + tid];
+        }
+        row_subst<R>(m, qv, Rpw, dRp);  // Q = core^T Y
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+          float v = qv[t];
+#pragma unroll
+          for (int s2 = t; s2 < R; ++s2) v = fmaf(-xr[s2], Rpw[t * R + s2], v);
+          e2 = fmaf(v, v, e2);
+        }
+      }
+      warp_pair_sums<R>(qv, redB + warp * np);
+      e2 = warp_sum(e2);
+      if (lane == 0) redE[warp] = e2;
+    }
+    __syncthreads();
+    // the same decision in every thread: sums over the row warps in order
+    float E2 = 0.f, RC2 = 0.f;
+    for (int w = 0; w < L.nw; ++w) E2 += redE[w];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const int pd = t * R - t * (t - 1) / 2;  // pair (t, t)
+      float g = 0.f;
+      for (int w = 0; w < L.nw; ++w) g += redA[w * np + pd];
+      RC2 += g;  // ||Rp||_F^2 = trace Gram(P)
+    }
+    const float res = sqrtf(E2), nrm = sqrtf(RC2);
+    if (res <= 1e-6f * nrm || (steps > 1 && res > 0.5f * prev_res && res <= 1e-5f * nrm) || !(nrm > 0.f)) {
+      converged = true;
+      break;
+    }
+    if (steps >= d.svdMaxSteps) break;  // keep X, P, Rp of the same step
+    prev_res = res;
+    if (rowwarp) {
+      gram_from_pairs<R>(redB, np, L.nw, Gw);
+      warp_chol<R>(Gw, R, Uqw, dUq);
+      if (tid < nJ) {
+        float y[R];
+        row_subst<R>(qv, y, Uqw, dUq);
+#pragma unroll
+        for (int t = 0; t < R; ++t) X[(size_t)t * L.ldx + tid] = y[t];
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- Y = P Rp^{-1}; second CholQR passes of Y and X; T = U2y Rp U2x^{-1}
+  float yv[R], xv[R];
+  if (rowwarp) {
+    {
+      float m[R];
+#pragma unroll
+      for (int t = 0; t < R; ++t) m[t] = (tid < nI) ? P[(size_t)tid * L.ps + t] : 0.f;
+      row_subst<R>(m, yv, Rpw, dRp);
+    }
+#pragma unroll
+    for (int t = 0; t < R; ++t) xv[t] = (tid < nJ) ? X[(size_t)t * L.ldx + tid] : 0.f;
+    warp_pair_sums<R>(yv, redA + warp * np);
+    warp_pair_sums<R>(xv, redB + warp * np);
+  }
+  __syncthreads();
+  if (rowwarp) {
+    gram_from_pairs<R>(redA, np, L.nw, Gw);
+    warp_chol<R>(Gw, R, Uqw, dUq);  // U2y
+    gram_from_pairs<R>(redB, np, L.nw, Gw);
+    warp_chol<R>(Gw, R, U2x, dU2x);
+    if (lane < R) {
+      const int s2 = lane;
+      float row[R];  // (U2y Rp)(s2, :)
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        float v = 0.f;
+#pragma unroll
+        for (int u = 0; u < R; ++u) v = fmaf(Uqw[s2 * R + u], Rpw[u * R + t], v);
+        row[t] = v;
+      }
+      float tr[R];  // T(s2,:) U2x = row (forward substitution; dropped pivots give zeros)
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        float v = row[t];
+#pragma unroll
+        for (int u = 0; u < t; ++u) v = fmaf(-tr[u], U2x[u * R + t], v);
+        tr[t] = v * dU2x[t];
+      }
+#pragma unroll
+      for (int t = 0; t < R; ++t) Tw[s2 * R + t] = tr[t];
+    }
+    __syncwarp();
+    // numerical rank from the diagonal of T, and T^{-1} on the kept pivots
+    const float dabs = lane < R ? fabsf(Tw[lane * R + lane]) : 0.f;
+    float dmax = dabs;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    const float tol = (float)(nI > nJ ? nI : nJ) * FLT_EPSILON * dmax;
+    const bool keep = lane < R && dabs > tol && dabs > 0.f;
+    const unsigned kmask = __ballot_sync(0xffffffffu, keep);
+    if (lane < R) {
+      const int c = lane;
+      float x[R];
+#pragma unroll
+      for (int s2 = R - 1; s2 >= 0; --s2) {
+        float v = 0.f;
+        if (s2 <= c && ((kmask >> s2) & 1u)) {
+          v = (s2 == c) ? 1.f : 0.f;
+#pragma unroll
+          for (int u = s2 + 1; u < R; ++u)
+            if (u <= c) v = fmaf(-Tw[s2 * R + u], x[u], v);
+          v = v / Tw[s2 * R + s2];
+        }
+        x[s2] = v;
+      }
+#pragma unroll
+      for (int s2 = 0; s2 < R; ++s2) Utw[s2 * R + c] = x[s2];
+    }
+    __syncwarp();
+    // outputs (U^+ = X T^{-1} Y^T): W = Y; Vs = X T^{-1}; V = X T^T
+    if (tid < nI) {
+      float y2[R];
+      row_subst<R>(yv, y2, Uqw, dUq);
+#pragma unroll
+      for (int t = 0; t < R; ++t) d.W[(size_t)tid * R + t] = ((kmask >> t) & 1u) ? y2[t] : 0.f;
+    }
+    if (tid < nJ) {
+      float x2[R];
+      row_subst<R>(xv, x2, U2x, dU2x);
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        float vp = 0.f, vr = 0.f;
+#pragma unroll
+        for (int s2 = 0; s2 < R; ++s2) {
+          vp = fmaf(x2[s2], Utw[s2 * R + t], vp);
+          vr = fmaf(x2[s2], Tw[t * R + s2], vr);
+        }
+        const bool kt = (kmask >> t) & 1u;
+        d.Vs[(size_t)tid * R + t] = kt ? vp : 0.f;
+        d.V[(size_t)tid * R + t] = kt ? vr : 0.f;
+      }
+    }
+    if (warp == 0) {
+      if (lane < R) d.sigma[lane] = keep ? dabs : 0.f;
+      for (int q = lane; q < R * R; q += 32) d.Tm[q] = Tw[q];
+      if (lane == 0) {
+        unsigned f = 0u;
+        if (__popc(kmask) < R) f |= IRCUR_FLAG_WRANK;
+        if (!converged) f |= IRCUR_FLAG_SVD_NOCONV;
+        if (f) atomicOr(&st->flags, f);
+        st->svd_steps += steps;
+        st->svd_last_steps = steps;
+      }
+    }
+  }
+  if (d.trace) {
+    __syncthreads();
+    trace_stop(d.trace, 3 * d.max_iter, 3 * k + 1);
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(kSsvdThreads, 1) ssvd_kernel(IterDesc d) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  pdl_launch_dependents();
+  ssvd_body<R>(d, blockIdx.y, smem);
+}
+
+// Batched form: block x factorises instance list[x]; blockIdx.y is the role.
+template <int R>
+__global__ void __launch_bounds__(kSsvdThreads, 1) ssvd_batch_kernel(const IterDesc* __restrict__ ds,
+                                                                    const int* __restrict__ list) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  ssvd_body<R>(ds[list[blockIdx.x]], blockIdx.y, smem);
 }
 
 template <typename... Args>
 static cudaError_t launch_cluster(void (*kernel)(Args...), dim3 grid, size_t smem, cudaStream_t s,
                                   Args... args) {
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the largest shared-memory carveout on the SVD's SMs, so that the pass
+  // blocks launched while it runs fit next to it
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
   memset(&cfg, 0, sizeof(cfg));
@@ -766,10 +1256,38 @@ static cudaError_t launch_csvd_r(const IterDesc& d, cudaStream_t s) {
 
 template <int R>
 static cudaError_t launch_csvd_batch_r(const BatchLaunch& b, cudaStream_t s) {
-  const int n = b.svd_n[0] + b.svd_n[1];
+  const int n = b.svd_n[1];
   if (n == 0) return cudaSuccess;
-  return launch_cluster(csvd_batch_kernel<R>, dim3(kSvdCluster * n, b.svd_roles, 1), b.svd_smem[0], s, b.ds,
-                        b.svd_list[0]);
+  return launch_cluster(csvd_batch_kernel<R>, dim3(kSvdCluster * n, b.svd_roles, 1), b.svd_smem[1], s, b.ds,
+                        b.svd_list[1]);
+}
+
+template <int R>
+static cudaError_t launch_ssvd_r(const IterDesc& d, cudaStream_t s) {
+  if constexpr (R > kSsvdMaxR) {
+    return cudaErrorInvalidValue;
+  } else {
+    const size_t bytes = ssvd_smem_bytes(d.nI, d.nJ, R);
+    cudaError_t e = cudaFuncSetAttribute(ssvd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    ssvd_kernel<R><<<dim3(1, 1 + (d.sampleAhead ? 2 : 0), 1), kSsvdThreads, bytes, s>>>(d);
+    return cudaGetLastError();
+  }
+}
+
+template <int R>
+static cudaError_t launch_ssvd_batch_r(const BatchLaunch& b, cudaStream_t s) {
+  if constexpr (R > kSsvdMaxR) {
+    return b.svd_n[0] ? cudaErrorInvalidValue : cudaSuccess;
+  } else {
+    const int n = b.svd_n[0];
+    if (n == 0) return cudaSuccess;
+    cudaError_t e =
+        cudaFuncSetAttribute(ssvd_batch_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.svd_smem[0]);
+    if (e != cudaSuccess) return e;
+    ssvd_batch_kernel<R><<<dim3(n, b.svd_roles, 1), kSsvdThreads, b.svd_smem[0], s>>>(b.ds, b.svd_list[0]);
+    return cudaGetLastError();
+  }
 }
 
 template <int R>
@@ -798,11 +1316,14 @@ cudaError_t launch_sigma(const float* Tm, int r, int Rpad, float* sigma, cudaStr
 
 template <int R>
 static cudaError_t launch_svd_r(const IterDesc& d, cudaStream_t s) {
+  if (ssvd_fits(d.nI, d.nJ, R)) return launch_ssvd_r<R>(d, s);
   return launch_csvd_r<R>(d, s);
 }
 
 template <int R>
 static cudaError_t launch_svd_batch_r(const BatchLaunch& b, cudaStream_t s) {
+  cudaError_t e = launch_ssvd_batch_r<R>(b, s);
+  if (e != cudaSuccess) return e;
   return launch_csvd_batch_r<R>(b, s);
 }
 
