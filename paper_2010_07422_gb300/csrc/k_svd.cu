@@ -267,8 +267,8 @@ __device__ int cholqr_w(const float* Min, int ldin, float* Mout, int ldout, int 
 //                                  (every CTA forms the whole sum)
 //   Rp, residual, X = orth(Q)      replicated in every CTA
 // Every cluster-wide sum adds the CTAs' partials in rank order, so each CTA
-// holds bit-identical matrices and takes identical branch decisions; two
-// cluster barriers per step.  Outputs: W by rows of Y (each CTA its rows),
+// holds bit-identical matrices and takes identical branch decisions; one
+// cluster barrier per step (the partial buffers alternate).  Outputs: W by rows of Y (each CTA its rows),
 // X T^{-1} and X T^T by slices of rows.
 constexpr int kSvdCluster = 8;
 constexpr int kCsvdThreads = 256;
@@ -278,7 +278,8 @@ struct CsvdLayout {
   int ldy;      // column stride of the local Y block (mr rounded up to 4)
   int ldx;      // column stride of X and of the Q partial (nJ rounded up to 4)
   int js;       // rows of the outputs X T^{-1}, X T^T each CTA writes
-  size_t off_uc, off_x, off_y, off_qp, off_qs, off_end_zero, off_ra, off_stage, off_slots, off_small, off_flag,
+  size_t off_uc, off_x, off_y, off_qp, off_qs, off_qp2, off_end_zero, off_ra, off_ra2, off_stage, off_slots, off_small,
+      off_flag,
       off_bar, total;
 };
 
@@ -292,7 +293,7 @@ __host__ __device__ inline CsvdLayout csvd_layout(int nI, int nJ, int ldu, int R
   size_t off = 0;
   L.off_uc = off;
   off += (size_t)L.mr * ldu * 4;
-  L.off_x = off;  // X | Y | Qp | Qs contiguous (zeroed together)
+  L.off_x = off;  // X | Y | Qp | Qs | Qp2 contiguous (zeroed together)
   off += (size_t)R * L.ldx * 4;
   L.off_y = off;
   off += (size_t)R * L.ldy * 4;
@@ -300,8 +301,12 @@ __host__ __device__ inline CsvdLayout csvd_layout(int nI, int nJ, int ldu, int R
   off += (size_t)R * L.ldx * 4;
   L.off_qs = off;  // Q = core^T Y, full (every CTA holds the sum of the partials)
   off += (size_t)R * L.ldx * 4;
+  L.off_qp2 = off;  // the partials alternate between two buffers from step to step
+  off += (size_t)R * L.ldx * 4;
   L.off_end_zero = off;
   L.off_ra = off;
+  off += ((size_t)R * R + 4) * 4;
+  L.off_ra2 = off;
   off += ((size_t)R * R + 4) * 4;
   L.off_stage = off;  // cl x (R R + 4): remote partials gathered before a fixed-order sum
   off += (size_t)cl * ((size_t)R * R + 4) * 4;
@@ -371,9 +376,11 @@ __device__ __forceinline__ void csvd_body(const IterDesc& d, int role, unsigned 
   float* Uc = reinterpret_cast<float*>(smem + L.off_uc);
   float* X = reinterpret_cast<float*>(smem + L.off_x);
   float* Y = reinterpret_cast<float*>(smem + L.off_y);
-  float* Qp = reinterpret_cast<float*>(smem + L.off_qp);
+  float* Qp0 = reinterpret_cast<float*>(smem + L.off_qp);
   float* Qs = reinterpret_cast<float*>(smem + L.off_qs);
-  float* ra = reinterpret_cast<float*>(smem + L.off_ra);  // Gram(Y) partial
+  float* ra0 = reinterpret_cast<float*>(smem + L.off_ra);  // Gram(Y) partials (two buffers)
+  float* ra1 = reinterpret_cast<float*>(smem + L.off_ra2);
+  float* Qp1 = reinterpret_cast<float*>(smem + L.off_qp2);
   float* stage = reinterpret_cast<float*>(smem + L.off_stage);
   float* slots = reinterpret_cast<float*>(smem + L.off_slots);
   int* flag = reinterpret_cast<int*>(smem + L.off_flag);
@@ -461,8 +468,8 @@ __device__ __forceinline__ void csvd_body(const IterDesc& d, int role, unsigned 
   // ---- subspace iteration.  With Y = (core X) Rp^{-1}, core^T Y =
   // (core^T core X) Rp^{-1}: the transposed product runs on the raw local rows
   // in the same phase as their Gram partial, and Rp^{-1} is applied to the
-  // summed Q.  Per step: four block barriers and two cluster barriers
-  // (partials written; partials read).
+  // summed Q.  Per step: four block barriers and one cluster barrier (partials
+  // written); the partial buffers alternate between steps.
   const int nwarps = (int)(blockDim.x >> 5);
   float* Uw = slots + (size_t)warp * (R * R + R);
   float* dw = Uw + R * R;
@@ -471,6 +478,10 @@ __device__ __forceinline__ void csvd_body(const IterDesc& d, int role, unsigned 
   float prev_res = 0.f;
   while (true) {
     ++steps;
+    // this step's partial buffers: a CTA that reaches the next step's cluster
+    // barrier has finished reading these, so the step after next may reuse them
+    float* ra = (steps & 1) ? ra1 : ra0;
+    float* Qp = (steps & 1) ? Qp1 : Qp0;
     // Y_c = core_c X (raw): one warp per local row, lanes over the inner index
     for (int o = warp; o < nrow; o += nwarps) {
       float acc[R];
@@ -541,7 +552,7 @@ __device__ __forceinline__ void csvd_body(const IterDesc& d, int role, unsigned 
       for (int c = 0; c < ncl; ++c) sacc += v[c];
       Qs[at] = sacc;
     }
-    cl.sync();  // (2) partials read; the sums are visible to the whole block
+    __syncthreads();  // the sums are visible to the whole block
     // Y Rp = core X: every warp factorises Gram(Y); Q = Q_raw Rp^{-1} row by
     // row, with the residual ||Q - X Rp^T||_F^2 of each row
     {
@@ -572,8 +583,9 @@ __device__ __forceinline__ void csvd_body(const IterDesc& d, int role, unsigned 
     __syncthreads();
     float E2 = 0.f;
     for (int w = 0; w < nwarps; ++w) E2 += sm.red[w];
-    float RC2 = 0.f;
-    for (int q = 0; q < R * R; ++q) RC2 = fmaf(sm.Rp[q], sm.Rp[q], RC2);
+    float RC2 = 0.f;  // ||Rp||_F^2 = trace Gram(Y)
+#pragma unroll
+    for (int t = 0; t < R; ++t) RC2 += sm.G[t * R + t];
     const float res = sqrtf(E2), nrm = sqrtf(RC2);
     if (res <= 1e-6f * nrm || (steps > 1 && res > 0.5f * prev_res && res <= 1e-5f * nrm) || !(nrm > 0.f)) {
       converged = true;
@@ -595,9 +607,10 @@ __device__ __forceinline__ void csvd_body(const IterDesc& d, int role, unsigned 
   __syncthreads();
 
   // ---- second CholQR passes (Y over the cluster, X replicated); T = U2y Rp U2x^{-1}
-  gram_block<R>(Y, nrow, L.ldy, r, ra);
+  float* raF = (steps & 1) ? ra0 : ra1;  // not the last step's buffer (others may still read that)
+  gram_block<R>(Y, nrow, L.ldy, r, raF);
   cl.sync();
-  cluster_sum(cl, ra, sm.G, R * R, stage);
+  cluster_sum(cl, raF, sm.G, R * R, stage);
   {
     float* Up = warp == 0 ? sm.U2y : Uw;
     float* dp = warp == 0 ? sm.dinv : dw;
