@@ -245,14 +245,22 @@ def _timed(fn, reps, stream):
 
 def bench_batched(ir, synth, stream, count=64, seed=7):
     """Uneven independent problems (n1, n2 uniform in [500, 4000], r in 2..10,
-    alpha in [0.05, 0.3], the planted generator): one batch vs a loop of single
-    solves on the same GPU.  Solves/s."""
+    alpha in [0.05, 0.3], the planted generator): one batch (one-CTA core SVDs
+    where the core fits, the faster form for many instances; the cluster form
+    timed too) vs a loop of single solves (cluster form, the faster one for a
+    lone solve) on the same GPU.  Solves/s."""
     import torch
     shapes = synth.uneven_batch(count, seed=seed)
     Ds = [synth.planted_device(q["n1"], q["n2"], q["r"], q["alpha"], seed=100 + i) for i, q in enumerate(shapes)]
     probs = [dict(n1=q["n1"], n2=q["n2"], r=q["r"], resample=True, seed=i, tol=1e-5, max_iter=100)
              for i, q in enumerate(shapes)]
-    batch = ir.IRCURBatch(probs)
+    batch_cl = ir.IRCURBatch(probs)
+    for _ in range(2):
+        batch_cl.solve(Ds)
+    batch_cl.autotune(Ds, reps=3)
+    t_batch_cl = _timed(lambda: batch_cl.solve(Ds), 5, stream)
+    batch_cl.close()
+    batch = ir.IRCURBatch([dict(q, svd_form=ir.IRCUR_SVD_ONE_CTA) for q in probs])
     for _ in range(2):
         res = batch.solve(Ds)
     tune = batch.autotune(Ds, reps=3)
@@ -268,6 +276,8 @@ def bench_batched(ir, synth, stream, count=64, seed=7):
     out = {"workload": f"{count} independent IRCUR-R problems, n1, n2 uniform in [500, 4000], r uniform in 2..10, "
                        "alpha uniform in [0.05, 0.3], planted generator on the device, tol 1e-5",
            "solves_per_s": count / (t_batch / 1e3), "ms_per_batch": t_batch,
+           "svd_form": "one CTA where the core fits",
+           "cluster_form_solves_per_s": count / (t_batch_cl / 1e3),
            "loop_solves_per_s": count / (t_loop / 1e3), "loop_ms": t_loop, "speedup_vs_loop": t_loop / t_batch,
            "iters_min_max": [min(iters), max(iters)], "converged": int(sum(r_.converged for r_ in res)),
            "autotune": tune}

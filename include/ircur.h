@@ -64,6 +64,18 @@ typedef enum {
 #define IRCUR_PRECISION_FP32 0
 #define IRCUR_PRECISION_BF16_PANELS 1
 
+/* ircur_params.svd_form: how the core's rank-r truncation H_r (Sec. 3.1) runs
+ * on the GPU.  Both forms compute the same subspace iteration with the same
+ * stopping rule; their results agree to FP32 rounding, not bit for bit.
+ * CLUSTER: one 8-CTA thread-block cluster per core, the core's rows split
+ *   over the 8 SMs (the faster form for one solve).
+ * ONE_CTA: one CTA of 1024 threads per core, the whole core in its shared
+ *   memory; used where the padded rank is <= 8 and the core fits in one SM
+ *   (about |I|, |J| <= 200), the cluster form elsewhere.  Batches of many
+ *   instances run faster with it (one SM per instance instead of eight). */
+#define IRCUR_SVD_CLUSTER 0
+#define IRCUR_SVD_ONE_CTA 1
+
 /* Largest number of instances of one ircur_batch. */
 #define IRCUR_MAX_BATCH 4096
 
@@ -79,7 +91,7 @@ typedef struct {
   int32_t resample;  /* 0 = IRCUR-F (fixed I,J), 1 = IRCUR-R (fresh I,J each iteration), Sec. 3.4 */
   uint64_t seed;     /* index-stream seed (used when the caller passes no index sets) */
   int32_t precision; /* IRCUR_PRECISION_*: 0 = FP32; 1 = BF16 panels (IRCUR-F only) */
-  int32_t reserved;  /* must be 0 */
+  int32_t svd_form;  /* IRCUR_SVD_*: 0 = cluster (default), 1 = one CTA where the core fits */
 } ircur_params;
 
 typedef struct {

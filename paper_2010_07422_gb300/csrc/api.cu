@@ -135,13 +135,14 @@ static ircur_status validate_params(const ircur_params* p, ircur_params* out) {
   if (q.precision != IRCUR_PRECISION_FP32 && q.precision != IRCUR_PRECISION_BF16_PANELS) return IRCUR_ENOTSUP;
   if (q.precision == IRCUR_PRECISION_BF16_PANELS && q.resample != 0) return IRCUR_ENOTSUP;
   if (pass_smem_bytes(q.nI, q.nJ, pad_rank(q.r), nullptr, q.precision != 0) > 227 * 1024) return IRCUR_ENOTSUP;
-  if (!ssvd_fits(q.nI, q.nJ, pad_rank(q.r)) && csvd_smem_bytes(q.nI, q.nJ, pad_rank(q.r)) > 227 * 1024)
+  if (q.svd_form != IRCUR_SVD_CLUSTER && q.svd_form != IRCUR_SVD_ONE_CTA) return IRCUR_EINVAL;
+  if (!(q.svd_form == IRCUR_SVD_ONE_CTA && ssvd_fits(q.nI, q.nJ, pad_rank(q.r))) &&
+      csvd_smem_bytes(q.nI, q.nJ, pad_rank(q.r)) > 227 * 1024)
     return IRCUR_ENOTSUP;
   if (!(q.gamma > 0.0 && q.gamma < 1.0)) return IRCUR_EINVAL;
   if (!(q.tol > 0.0)) return IRCUR_EINVAL;
   if (q.max_iter < 1) return IRCUR_EINVAL;
   if (q.resample != 0 && q.resample != 1) return IRCUR_EINVAL;
-  if (q.reserved != 0) return IRCUR_EINVAL;
   if (!(q.zeta0 == q.zeta0)) return IRCUR_EINVAL;
   *out = q;
   return IRCUR_OK;
@@ -173,6 +174,7 @@ static ircur_status create_impl(const ircur_params* params, void* stream, int mi
   // tile configuration of the pass kernel
   IterDesc& d = c->desc;
   memset(&d, 0, sizeof(d));
+  d.svdOneCta = (p.svd_form == IRCUR_SVD_ONE_CTA && ssvd_fits(p.nI, p.nJ, R)) ? 1 : 0;
   d.nRowTiles = (int)((n2 + kPanelCols - 1) / kPanelCols);
   d.nColTiles = (int)((n1 + kPanelCols - 1) / kPanelCols);
 
@@ -1022,14 +1024,12 @@ extern "C" ircur_status ircur_batch_create(const ircur_params* params, int32_t c
     int* tb = tiles.get() + first + g;
     tb[0] = 0;
     int maxNI = 1, roles = 1, nOne = 0, nCl = 0;
-    for (int q = 0; q < n; ++q) {
-      const ircur_params& p = b->inst[b->order[first + q]]->p;
-      if (ssvd_fits(p.nI, p.nJ, R)) ++nOne;
-    }
+    for (int q = 0; q < n; ++q)
+      if (b->inst[b->order[first + q]]->desc.svdOneCta) ++nOne;
     for (int q = 0; q < n; ++q) {
       const ircur_ctx* c = b->inst[b->order[first + q]];
       const ircur_params& p = c->p;
-      const bool one = ssvd_fits(p.nI, p.nJ, R);
+      const bool one = c->desc.svdOneCta != 0;
       const size_t ss = one ? ssvd_smem_bytes(p.nI, p.nJ, R) : csvd_smem_bytes(p.nI, p.nJ, R);
       if (pass_smem_bytes(p.nI, p.nJ, R) > 227 * 1024 || ss > 227 * 1024) {
         ircur_batch_destroy(b);

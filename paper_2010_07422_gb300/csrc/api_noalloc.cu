@@ -69,7 +69,8 @@ extern "C" ircur_status ircur_solve_noalloc(const ircur_params* params, const fl
   if (p.nJ == 0) p.nJ = (int)fmin((double)p.n2, ceil(4.0 * p.r * log((double)p.n2)));
   if (p.nI < p.r || p.nJ < p.r || p.nI > p.n1 || p.nJ > p.n2) return IRCUR_EINVAL;
   if (!(p.gamma > 0.0 && p.gamma < 1.0) || !(p.tol > 0.0) || p.max_iter < 1) return IRCUR_EINVAL;
-  if (p.resample != 0 || p.precision != 0 || p.reserved != 0) return IRCUR_EINVAL;
+  if (p.resample != 0 || p.precision != 0) return IRCUR_EINVAL;
+  if (p.svd_form != IRCUR_SVD_CLUSTER && p.svd_form != IRCUR_SVD_ONE_CTA) return IRCUR_EINVAL;
   if (!(p.zeta0 == p.zeta0)) return IRCUR_EINVAL;
   // sizes beyond the fixed workspace
   if (p.n1 > kNaMaxN || p.n2 > kNaMaxN || p.nI > kNaMaxM || p.nJ > kNaMaxM || pad_rank(p.r) > kNaMaxR ||
@@ -100,6 +101,7 @@ extern "C" ircur_status ircur_solve_noalloc(const ircur_params* params, const fl
   if (((ldCore / 4) & 1) == 0) ldCore += 4;
   IterDesc d;
   memset(&d, 0, sizeof(d));
+  d.svdOneCta = (p.svd_form == IRCUR_SVD_ONE_CTA && ssvd_fits(p.nI, p.nJ, pad_rank(p.r))) ? 1 : 0;
   d.nRowTiles = (int)((n2 + kPanelCols - 1) / kPanelCols);
   d.nColTiles = (int)((n1 + kPanelCols - 1) / kPanelCols);
   const int64_t ldPr = (n2 + 3) & ~3ll, ldPc = (n1 + 3) & ~3ll;

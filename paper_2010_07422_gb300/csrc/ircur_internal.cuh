@@ -102,6 +102,7 @@ struct IterDesc {
   int rowBulk, colBulk; // 1: panel rows are 16-byte aligned (tiles via 16-byte async copies)
   int svdMaxSteps;
   int sampleAhead;      // 1: the core-SVD launch draws the next iteration's I, J (IRCUR-R, own sampler)
+  int svdOneCta;        // 1: the core SVD runs on one CTA (ssvd_kernel), else on a cluster
   int passGrid;         // pass-kernel blocks (0: every block that fits the GPU at once), from the autotuner
   int passSingleBuf;    // 1: one tile buffer per block (no prefetch, less shared memory)
   long long spinLimit;      // first bounded wait on a bulk copy (kSpinLimit unless a fault is injected)
@@ -215,7 +216,7 @@ cudaError_t launch_cur_to_svd(const float* A, const float* B, int64_t n1, int64_
 // Shared memory per CTA of the cluster core SVD.
 size_t csvd_smem_bytes(int nI, int nJ, int Rpad);
 // One-CTA core SVD (R <= 8, the core in one SM's shared memory): its dynamic
-// shared memory, and whether it is the form used for this shape.
+// shared memory, and whether it can run this shape.
 size_t ssvd_smem_bytes(int nI, int nJ, int Rpad);
 bool ssvd_fits(int nI, int nJ, int Rpad);
 // Blocks of the pass kernel that are resident on the whole GPU at once.

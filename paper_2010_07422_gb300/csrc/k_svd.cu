@@ -32,7 +32,6 @@
 // orthogonality to FP32 rounding.
 #include <cooperative_groups.h>
 #include <float.h>
-#include <stdlib.h>
 #include <string.h>
 
 #include "device_common.cuh"
@@ -832,10 +831,7 @@ size_t ssvd_smem_bytes(int nI, int nJ, int Rpad) {
   return L.total > sizeof(SamplerSmem) ? L.total : sizeof(SamplerSmem);
 }
 
-bool ssvd_fits(int nI, int nJ, int Rpad) {
-  static const int on = getenv("IRCUR_SSVD") != nullptr;
-  return on && ssvd_smem_bytes(nI, nJ, Rpad) <= 227 * 1024;
-}
+bool ssvd_fits(int nI, int nJ, int Rpad) { return ssvd_smem_bytes(nI, nJ, Rpad) <= 227 * 1024; }
 
 // The Gram products of one row (a) summed over the warp; lane 0 writes the
 // R(R+1)/2 upper-triangle sums to out.
@@ -1282,6 +1278,9 @@ static cudaError_t launch_ssvd_r(const IterDesc& d, cudaStream_t s) {
   } else {
     const size_t bytes = ssvd_smem_bytes(d.nI, d.nJ, R);
     cudaError_t e = cudaFuncSetAttribute(ssvd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ssvd_kernel<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     ssvd_kernel<R><<<dim3(1, 1 + (d.sampleAhead ? 2 : 0), 1), kSsvdThreads, bytes, s>>>(d);
     return cudaGetLastError();
@@ -1297,6 +1296,9 @@ static cudaError_t launch_ssvd_batch_r(const BatchLaunch& b, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     cudaError_t e =
         cudaFuncSetAttribute(ssvd_batch_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.svd_smem[0]);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ssvd_batch_kernel<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     ssvd_batch_kernel<R><<<dim3(n, b.svd_roles, 1), kSsvdThreads, b.svd_smem[0], s>>>(b.ds, b.svd_list[0]);
     return cudaGetLastError();
@@ -1329,7 +1331,7 @@ cudaError_t launch_sigma(const float* Tm, int r, int Rpad, float* sigma, cudaStr
 
 template <int R>
 static cudaError_t launch_svd_r(const IterDesc& d, cudaStream_t s) {
-  if (ssvd_fits(d.nI, d.nJ, R)) return launch_ssvd_r<R>(d, s);
+  if (d.svdOneCta) return launch_ssvd_r<R>(d, s);
   return launch_csvd_r<R>(d, s);
 }
 

@@ -20,6 +20,7 @@ IRCUR_ESVD_NOCONV, IRCUR_ETIMEOUT, IRCUR_ESTATE, IRCUR_ENOTSUP = 4, 5, 6, 7
 IRCUR_FLAG_WRANK, IRCUR_FLAG_SVD_NOCONV = 1, 2
 IRCUR_MAX_RANK = 16
 IRCUR_PRECISION_FP32, IRCUR_PRECISION_BF16_PANELS = 0, 1
+IRCUR_SVD_CLUSTER, IRCUR_SVD_ONE_CTA = 0, 1
 
 EXPORTED = (
     "ircur_create", "ircur_destroy", "ircur_solve", "ircur_get_factors", "ircur_get_indices",
@@ -35,7 +36,7 @@ class ircur_params(C.Structure):
     _fields_ = [("n1", C.c_int64), ("n2", C.c_int64), ("r", C.c_int32), ("nI", C.c_int32),
                 ("nJ", C.c_int32), ("zeta0", C.c_double), ("gamma", C.c_double), ("tol", C.c_double),
                 ("max_iter", C.c_int32), ("resample", C.c_int32), ("seed", C.c_uint64),
-                ("precision", C.c_int32), ("reserved", C.c_int32)]
+                ("precision", C.c_int32), ("svd_form", C.c_int32)]
 
 
 class ircur_result(C.Structure):
@@ -269,11 +270,11 @@ class IRCUR:
     """
 
     def __init__(self, n1, n2, r, *, nI=0, nJ=0, zeta0=0.0, gamma=0.7, tol=1e-5, max_iter=100,
-                 resample=True, seed=0, precision=IRCUR_PRECISION_FP32, stream=None):
+                 resample=True, seed=0, precision=IRCUR_PRECISION_FP32, svd_form=0, stream=None):
         import torch
         self.p = ircur_params(n1=n1, n2=n2, r=r, nI=nI, nJ=nJ, zeta0=zeta0, gamma=gamma, tol=tol,
                               max_iter=max_iter, resample=int(bool(resample)), seed=seed,
-                              precision=precision, reserved=0)
+                              precision=precision, svd_form=svd_form)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._ctx = ircur_create(self.p, C.c_void_p(self.stream.cuda_stream))
         self.nI = nI if nI else sample_size(4, r, n1)
@@ -442,7 +443,7 @@ class IRCURBatch:
                 n1=q["n1"], n2=q["n2"], r=q["r"], nI=q.get("nI", 0), nJ=q.get("nJ", 0),
                 zeta0=q.get("zeta0", 0.0), gamma=q.get("gamma", 0.7), tol=q.get("tol", 1e-5),
                 max_iter=q.get("max_iter", 100), resample=int(bool(q.get("resample", True))),
-                seed=q.get("seed", 0), precision=0, reserved=0))
+                seed=q.get("seed", 0), precision=0, svd_form=q.get("svd_form", 0)))
         self._b = ircur_batch_create(self.params, C.c_void_p(self.stream.cuda_stream))
         self._views = [IRCUR._view(ircur_batch_instance(self._b, i), p, self.stream, self)
                        for i, p in enumerate(self.params)]

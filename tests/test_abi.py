@@ -53,7 +53,7 @@ def test_status_strings_and_param_validation_without_gpu(lib):
 
     def create(**kw):
         base = dict(n1=100, n2=80, r=3, nI=0, nJ=0, zeta0=0.0, gamma=0.7, tol=1e-5, max_iter=10,
-                    resample=1, seed=0, precision=0, reserved=0)
+                    resample=1, seed=0, precision=0, svd_form=0)
         base.update(kw)
         return lib.ircur_create(ctypes.byref(ir.ircur_params(**base)), None, ctypes.byref(ctx))
 
@@ -67,13 +67,15 @@ def test_status_strings_and_param_validation_without_gpu(lib):
     assert create(nJ=81) == ir.IRCUR_EINVAL       # |J| > n2
     assert create(resample=2) == ir.IRCUR_EINVAL
     assert create(precision=1) == ir.IRCUR_ENOTSUP
+    assert create(svd_form=2) == ir.IRCUR_EINVAL
+    assert create(svd_form=-1) == ir.IRCUR_EINVAL
     assert create(n1=0) == ir.IRCUR_EINVAL
     assert ctx.value is None
     # batch argument checks (before any CUDA call)
     good = ir.ircur_params(n1=100, n2=80, r=3, nI=0, nJ=0, zeta0=0.0, gamma=0.7, tol=1e-5, max_iter=10,
-                           resample=1, seed=0, precision=0, reserved=0)
+                           resample=1, seed=0, precision=0, svd_form=0)
     bad = ir.ircur_params(n1=100, n2=80, r=3, nI=0, nJ=0, zeta0=0.0, gamma=1.5, tol=1e-5, max_iter=10,
-                          resample=1, seed=0, precision=0, reserved=0)
+                          resample=1, seed=0, precision=0, svd_form=0)
     bh = ctypes.c_void_p()
     assert lib.ircur_batch_create((ir.ircur_params * 1)(good), 0, None, ctypes.byref(bh)) == ir.IRCUR_EINVAL
     assert lib.ircur_batch_create((ir.ircur_params * 2)(good, bad), 2, None, ctypes.byref(bh)) == ir.IRCUR_EINVAL
@@ -93,7 +95,7 @@ def test_fault_injection_alloc_returns_enomem(lib, monkeypatch):
     monkeypatch.setenv("IRCUR_FAULT", "alloc")
     ctx = ctypes.c_void_p()
     p = ir.ircur_params(n1=100, n2=80, r=3, nI=0, nJ=0, zeta0=0.0, gamma=0.7, tol=1e-5, max_iter=10,
-                        resample=1, seed=0, precision=0, reserved=0)
+                        resample=1, seed=0, precision=0, svd_form=0)
     assert ir._lib().ircur_create(ctypes.byref(p), None, ctypes.byref(ctx)) == ir.IRCUR_ENOMEM
     assert ctx.value is None
     bh = ctypes.c_void_p()

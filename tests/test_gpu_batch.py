@@ -148,9 +148,9 @@ def test_batch_errors():
     lib = ir._lib()
     P = ir.ircur_params
     good = P(n1=100, n2=100, r=2, nI=0, nJ=0, zeta0=0.0, gamma=0.7, tol=1e-5, max_iter=10, resample=1, seed=0,
-             precision=0, reserved=0)
+             precision=0, svd_form=0)
     bad = P(n1=100, n2=100, r=0, nI=0, nJ=0, zeta0=0.0, gamma=0.7, tol=1e-5, max_iter=10, resample=1, seed=0,
-            precision=0, reserved=0)
+            precision=0, svd_form=0)
     h = ctypes.c_void_p()
     assert lib.ircur_batch_create((P * 1)(good), 0, None, ctypes.byref(h)) == ir.IRCUR_EINVAL
     assert lib.ircur_batch_create((P * 2)(good, bad), 2, None, ctypes.byref(h)) == ir.IRCUR_EINVAL

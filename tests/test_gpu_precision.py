@@ -114,7 +114,7 @@ def test_precision_variant_errors():
     P = ir.ircur_params
     ctx = ctypes.c_void_p()
     q = P(n1=300, n2=300, r=2, nI=0, nJ=0, zeta0=0.0, gamma=0.7, tol=1e-5, max_iter=10, resample=1, seed=0,
-          precision=ir.IRCUR_PRECISION_BF16_PANELS, reserved=0)
+          precision=ir.IRCUR_PRECISION_BF16_PANELS, svd_form=0)
     assert lib.ircur_create(ctypes.byref(q), None, ctypes.byref(ctx)) == ir.IRCUR_ENOTSUP
     q.precision = 2
     q.resample = 0

@@ -36,7 +36,7 @@ def test_noalloc_matches_the_allocating_entry_point_twice():
     ref.close()
 
     params = ir.ircur_params(n1=n1, n2=n2, r=r, nI=0, nJ=0, zeta0=0.0, gamma=0.7, tol=1e-5, max_iter=100,
-                             resample=0, seed=4, precision=0, reserved=0)
+                             resample=0, seed=4, precision=0, svd_form=0)
     for _ in range(2):  # the second call starts from the first call's leftovers in the shared array
         A = torch.full((n1, r), float("nan"), device="cuda")
         B = torch.full((r, n2), float("nan"), device="cuda")
@@ -48,7 +48,7 @@ def test_noalloc_matches_the_allocating_entry_point_twice():
 
     # sizes beyond the fixed array and IRCUR-R are rejected, nothing is launched
     big = ir.ircur_params(n1=4096, n2=1200, r=r, nI=0, nJ=0, zeta0=0.0, gamma=0.7, tol=1e-5, max_iter=100,
-                          resample=0, seed=4, precision=0, reserved=0)
+                          resample=0, seed=4, precision=0, svd_form=0)
     with pytest.raises(ir.IrcurError) as ei:
         ir.ircur_solve_noalloc(big, D, D.stride(0), A, B, stream)
     assert ei.value.status == ir.IRCUR_EINVAL
