@@ -1272,7 +1272,10 @@ struct TuneCand {
   int grid, single;
 };
 
-static int tune_candidates(int total, int resident2, int resident1, int sms, TuneCand* out) {
+// svd_sms: SMs the core SVD holds while the pass kernel's blocks start (its
+// programmatic dependents); one block fewer fits on each of them, so the
+// largest grid is also tried without those blocks (0: not tried).
+static int tune_candidates(int total, int resident2, int resident1, int sms, int svd_sms, TuneCand* out) {
   int n = 0;
   auto add = [&](int grid, int single) {
     if (grid > total) grid = total;
@@ -1282,6 +1285,7 @@ static int tune_candidates(int total, int resident2, int resident1, int sms, Tun
     if (n < IRCUR_TUNE_MAX) out[n++] = TuneCand{grid, single};
   };
   const int per2 = resident2 / sms, per1 = resident1 / sms;
+  if (svd_sms > 0 && per2 >= 2) add(per2 * sms - svd_sms, 0);
   for (int k = per2; k >= 1; --k) add(k * sms, 0);
   if (per1 > per2) add(per1 * sms, 1);
   add(total, 0);  // one block per tile (blocks beyond the resident ones queue)
@@ -1312,7 +1316,7 @@ extern "C" ircur_status ircur_autotune(ircur_ctx* c, const float* D, int64_t ldD
   probe.passSingleBuf = 1;
   const int res1 = pass_resident_blocks(probe, c->Rpad);
   TuneCand cand[IRCUR_TUNE_MAX];
-  const int nc = tune_candidates(total, res2, res1, sms, cand);
+  const int nc = tune_candidates(total, res2, res1, sms, c->desc.svdOneCta ? 1 : kSvdCluster, cand);
   cudaEvent_t e0, e1;
   IRCUR_CK(cudaEventCreate(&e0));
   IRCUR_CK(cudaEventCreate(&e1));

@@ -31,6 +31,7 @@ constexpr int kGraphUnroll = IRCUR_GRAPH_UNROLL;
 // `partials`.
 constexpr int kPanelCols = 32;
 constexpr int kPassWarps = 8;
+constexpr int kSvdCluster = 8;  // CTAs (SMs) of the cluster form of the core SVD
 constexpr int kPassThreads = 32 * kPassWarps;
 constexpr int kMaxPanelRows = 512;  // largest |I|, |J| the kernels are built for
 

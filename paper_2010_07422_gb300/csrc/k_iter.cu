@@ -162,8 +162,9 @@ struct TileRef {
 };
 
 // Issue the copies of one panel tile into `buf`: 16-byte asynchronous copies
-// when the rows are 16-byte aligned and the tile is full, 4-byte ones
-// otherwise (BF16 panels, always aligned: plain loads for the ragged tile).
+// when the rows are 16-byte aligned (4-byte ones for the last 1..3 columns of
+// a ragged last tile), 4-byte ones otherwise (BF16 panels, always aligned:
+// plain loads for the ragged tile).
 template <bool COL, bool BF>
 __device__ __forceinline__ void pass_stage_tile(const IterDesc& d, int k, int lt, unsigned char* bufp) {
   const int m = COL ? d.nJ : d.nI;
@@ -192,15 +193,32 @@ __device__ __forceinline__ void pass_stage_tile(const IterDesc& d, int k, int lt
   const int* map = (COL ? d.J_all : d.I_all) + (d.resample ? (int64_t)k * m : 0);
   const bool mapped = d.resample != 0;
   const float* src = COL ? d.colSrc : d.rowSrc;
-  if ((COL ? d.colBulk : d.rowBulk) && ncols == kPanelCols) {
+  if (COL ? d.colBulk : d.rowBulk) {
+    // 16-byte copies of whole 4-column groups; on the ragged last tile the
+    // remaining 1..3 columns by 4-byte copies and zeros past the last column
     constexpr int kV = kPanelCols / 4;
+    const int nv = ncols >> 2, rem4 = ncols & 3;
     for (int q = threadIdx.x; q < m * kV; q += blockDim.x) {
       const int a = q / kV, c4 = q - a * kV;
-      const int64_t row = mapped ? __ldg(map + a) : a;
-      cp_async16(buf + (size_t)a * kPanelCols + 4 * c4, src + row * ld + j0 + 4 * c4);
+      float* dst = buf + (size_t)a * kPanelCols + 4 * c4;
+      if (c4 < nv) {
+        const int64_t row = mapped ? __ldg(map + a) : a;
+        cp_async16(dst, src + row * ld + j0 + 4 * c4);
+      } else if (c4 == nv && rem4) {
+        const int64_t row = mapped ? __ldg(map + a) : a;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (e < rem4)
+            cp_async4(dst + e, src + row * ld + j0 + 4 * c4 + e);
+          else
+            dst[e] = 0.f;
+        }
+      } else {
+        *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
   } else {
-    // rows not 16-byte aligned, or the ragged last tile: 4-byte asynchronous
+    // rows not 16-byte aligned: 4-byte asynchronous
     // copies (zeros past the panel's last column)
     for (int q = threadIdx.x; q < m * kPanelCols; q += blockDim.x) {
       const int a = q / kPanelCols, c = q - a * kPanelCols;

@@ -269,7 +269,6 @@ __device__ int cholqr_w(const float* Min, int ldin, float* Mout, int ldout, int 
 // holds bit-identical matrices and takes identical branch decisions; one
 // cluster barrier per step (the partial buffers alternate).  Outputs: W by rows of Y (each CTA its rows),
 // X T^{-1} and X T^T by slices of rows.
-constexpr int kSvdCluster = 8;
 constexpr int kCsvdThreads = 256;
 
 struct CsvdLayout {
