@@ -557,7 +557,7 @@ def main():
     # panel passes: the two panels once, A_k, B_k read, A_{k+1}, B_{k+1} written
     pass_bytes = 4.0 * (nI * n + nJ * n) + 2 * 4.0 * Rp * (n + n)
     roof_pass = roof_hbm("pass_kernel", pass_bytes, float(np.mean(pass_us)), f"n{n}_r{r}")
-    # core SVD: one CTA on one SM; FP32 work per launch = 2 products of 2 nI nJ r
+    # core SVD (one 8-CTA cluster): FP32 work per launch = 2 products of 2 nI nJ r
     # flops per subspace step, plus the Cholesky QR passes (4 (nI + nJ) r^2 per step)
     steps = svd_steps / max(1.0, my_iters)
     svd_flops = steps * (4.0 * nI * nJ * r + 4.0 * (nI + nJ) * r * r)
