@@ -13,5 +13,6 @@ from .ircur_oracle import (  # noqa: F401
     sample_indices,
     sample_size,
     splitmix64,
+    stream_columns,
     truncated_svd,
 )

@@ -22,8 +22,12 @@ Every function follows the paper's steps in the paper's order and notation:
                           S = T_zeta(D - L) at the threshold the next Phase I
                           would use.
 * ``cur_to_svd``       -- Algorithm 2 (CUR to SVD conversion).
+* ``stream_columns``   -- new columns through Alg. 1 with the final iterate's
+                          column space C U^+ held fixed (an extension the
+                          paper leaves implicit: IRCUR-F touches only the
+                          rows I of a column, Sec. 3.4).
 
-Readings taken where the paper is silent (each one is listed in the design doc):
+Readings taken where the paper is silent:
 * ``log`` in |I| = c r log n is the natural log; |I| is rounded up.
 * zeta_{k+1} = gamma^k zeta_0 (Alg. 1): the first iteration (k = 0) thresholds
   at zeta_0 itself.  gamma^k is formed by repeated FP64 multiplication.
@@ -270,3 +274,39 @@ def cur_to_svd(C, U_pinv, R):
     Q_R, R_R = np.linalg.qr(np.asarray(R, np.float64).T)
     W_U, sigma, V_Ut = np.linalg.svd(R_C @ U_pinv @ R_R.T)
     return Q_C @ W_U, sigma, Q_R @ V_Ut.T
+
+
+# --------------------------------------------------------------------------
+# Streaming extension: new columns against a fixed CUR model
+# --------------------------------------------------------------------------
+
+
+def stream_columns(Dnew, result, zeta0, gamma, iters):
+    """New columns d (the columns of Dnew, n1 x c) go through Alg. 1 with the
+    final iterate's C and U^+ (and its row set I) held fixed.  The paper does
+    not state this step; it follows from Alg. 1 because a column enters the
+    iteration only through its entries on the rows I (R = D_{I,:} - S_{I,:}),
+    and L = C U^+ R then extends it to all rows.  Per column, from L_0 = 0:
+
+        for t = 0 .. iters-1:   zeta_t = gamma^t zeta_0
+            S_I = T_{zeta_t}(d_I - [L_t]_I)          (Phase I, on the rows I)
+            r   = d_I - S_I                           (the column's entry of R)
+            [L_{t+1}]_I = C_{I,:} U^+ r               (Phase II, C and U^+ fixed)
+        L = C U^+ r,  S = T_{zeta_iters}(d - L)      (as ``dense_outputs``)
+
+    Returns (L, S), both n1 x c, FP64."""
+    Dnew = np.asarray(Dnew, dtype=np.float64)
+    if Dnew.ndim == 1:
+        Dnew = Dnew[:, None]
+    C, U_pinv, I = result.C, result.U_pinv, result.I
+    d_I = Dnew[I, :]
+    L_I = np.zeros_like(d_I)
+    zeta = float(zeta0)
+    r = d_I
+    for _ in range(iters):
+        S_I = hard_threshold(d_I - L_I, zeta)
+        r = d_I - S_I
+        L_I = C[I, :] @ (U_pinv @ r)
+        zeta = zeta * gamma
+    L = C @ (U_pinv @ r)
+    return L, hard_threshold(Dnew - L, zeta)
