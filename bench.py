@@ -317,6 +317,29 @@ def bench_adjoint(ir, synth, stream, count=8, n=4096, r=10, T=15):
             "note": "gradient parity with the FP64 oracle gradient: tests/test_gpu_adjoint.py"}
 
 
+def bench_stream(ir, synth, stream, n=10000, c=1024, r=5):
+    """New columns against a solved model: planted D of n x (n + c) drawn on
+    the device, IRCUR-F solve on the first n columns, the last c streamed
+    (ircur_stream_columns, the solve's iteration count).  Columns/s, and the
+    dense part's HBM rate (read the new columns, write L and S)."""
+    import torch
+    Dall = synth.planted_device(n, n + c, r, 0.1, seed=41)
+    D = Dall[:, :n].contiguous()
+    Dn = Dall[:, n:].contiguous()
+    del Dall
+    s_ = ir.IRCUR(n, n, r, tol=1e-5, max_iter=100, resample=False, seed=3)
+    res = s_.solve(D)
+    for _ in range(3):
+        s_.stream_columns(Dn)
+    t = _timed(lambda: s_.stream_columns(Dn), 20, stream)
+    out = {"workload": f"planted n1 = {n}, model solved on {n} columns (IRCUR-F, r = {r}, alpha = 0.1), "
+                       f"{c} new columns streamed with {res.iters} iterations each",
+           "columns_per_s": c / (t / 1e3), "ms_per_call": t,
+           "dense_gbs": 12.0 * n * c / (t * 1e-3) / 1e9}
+    s_.close()
+    return out
+
+
 def bench_precision(ir, synth, stream, K=30):
     """Video-shaped D (120 x 160 pixels x 3055 frames, r = 2): FP32 panels vs
     BF16 panels with the FP32 band re-check, same K iterations."""
@@ -650,7 +673,8 @@ def main():
     extras = {}
     if rank == 0 and world == 1 and not a.no_extras:
         from paper_2010_07422_gb300 import synth
-        for key, fn in (("batched", bench_batched), ("adjoint", bench_adjoint), ("precision_variant", bench_precision)):
+        for key, fn in (("batched", bench_batched), ("adjoint", bench_adjoint), ("precision_variant", bench_precision),
+                        ("streaming", bench_stream)):
             try:
                 extras[key] = fn(ir, synth, stream)
             except Exception as exc:  # a secondary measurement must not cost the headline line

@@ -168,6 +168,24 @@ ircur_status ircur_get_errors(ircur_ctx* ctx, double* errs, int32_t* count);
 ircur_status ircur_reconstruct(ircur_ctx* ctx, const float* D, int64_t ldD, float* L, int64_t ldL,
                                float* S, int64_t ldS);
 
+/* Streaming extension (the paper leaves it implicit: Alg. 1 reads a column
+ * only through its rows I, Sec. 3.4, and L = C U^+ R extends it to every
+ * row).  New columns, for example new frames of a video (Sec. 4.2), go
+ * through Alg. 1 with the last solve's C and U^+ (and its rows I) held fixed.
+ * From L_0 = 0, for t < iters, with zeta_t = gamma^t zeta_0 (the solve's
+ * zeta_0 and gamma):
+ *   r = d_I - T_{zeta_t}(d_I - [L_t]_I),   [L_{t+1}]_I = C_{I,:} U^+ r;
+ * then L = C U^+ r and S = T_{zeta_iters}(d - L) for every row.
+ * Dnew: device, n1 x ncols, row-major (ldDn >= ncols), read only.  Lnew and
+ * Snew (Snew may be NULL): device, n1 x ncols (ldL, ldS >= ncols), written.
+ * iters <= 0 means the last solve's iteration count K.  Asynchronous on the
+ * context's stream; uses a scratch of ncols * 4 * r bytes owned by the
+ * context (ENOMEM if it cannot be allocated).  ESTATE before a solve; EINVAL
+ * for NULL or misaligned (not 4-byte) pointers, ncols < 1 or short leading
+ * dimensions; ENOTSUP for ncols > 2^21 - 32. */
+ircur_status ircur_stream_columns(ircur_ctx* ctx, const float* Dnew, int64_t ldDn, int64_t ncols, int32_t iters,
+                                  float* Lnew, int64_t ldL, float* Snew, int64_t ldS);
+
 /* Whole pipeline from host memory: copy D_host (n1 x n2, ld = n2) to the
  * device, solve, reconstruct, and copy L (and S if S_host is not NULL) back
  * to host arrays of n1 x n2 (ld = n2).  Device buffers for D, L and S are

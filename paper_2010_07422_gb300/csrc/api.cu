@@ -112,6 +112,8 @@ struct ircur_ctx {
   float* adjF[2];
   int recorded;  // the last solve recorded its iterations
   void* c2s_ws;  // scratch of ircur_get_svd
+  float* stream_ws;       // scratch of ircur_stream_columns: one R-vector per new column
+  int64_t stream_cols;    // columns it holds
 };
 
 static void reset_graph(ircur_ctx* c) {
@@ -315,6 +317,7 @@ extern "C" void ircur_destroy(ircur_ctx* c) {
     if (c->hev[q]) cudaEventDestroy(c->hev[q]);
   if (c->rec_ws) cudaFree(c->rec_ws);
   if (c->c2s_ws) cudaFree(c->c2s_ws);
+  if (c->stream_ws) cudaFree(c->stream_ws);
   if (c->ws) cudaFree(c->ws);
   delete c;
 }
@@ -726,6 +729,41 @@ extern "C" ircur_status ircur_get_errors(ircur_ctx* c, double* errs, int32_t* co
   if (K > 0) IRCUR_CK(cudaMemcpyAsync(errs, c->errs, (size_t)K * 8, cudaMemcpyDeviceToHost, c->stream));
   IRCUR_CK(cudaStreamSynchronize(c->stream));
   *count = K;
+  return IRCUR_OK;
+}
+
+extern "C" ircur_status ircur_stream_columns(ircur_ctx* c, const float* Dnew, int64_t ldDn, int64_t ncols,
+                                             int32_t iters, float* Lnew, int64_t ldL, float* Snew, int64_t ldS) {
+  if (!c || !Dnew || !Lnew || ncols < 1) return IRCUR_EINVAL;
+  if (!c->solved || c->host_state.k < 1) return IRCUR_ESTATE;
+  if (ldDn < ncols || ldL < ncols || (Snew && ldS < ncols)) return IRCUR_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(Dnew) & 3) || (reinterpret_cast<uintptr_t>(Lnew) & 3) ||
+      (reinterpret_cast<uintptr_t>(Snew) & 3))
+    return IRCUR_EINVAL;
+  if (ncols > 65535ll * 32 || c->p.n1 > (1ll << 33)) return IRCUR_ENOTSUP;  // grid of the dense kernel
+  const int K = c->host_state.k;
+  if (iters <= 0) iters = K;
+  if (c->stream_cols < ncols) {
+    if (c->stream_ws) cudaFree(c->stream_ws);
+    c->stream_ws = nullptr;
+    c->stream_cols = 0;
+    cudaError_t e = cudaMalloc(&c->stream_ws, (size_t)ncols * c->Rpad * 4);
+    if (e != cudaSuccess) {
+      set_error("cudaMalloc(stream scratch)", e);
+      cudaGetLastError();
+      c->stream_ws = nullptr;
+      return IRCUR_ENOMEM;
+    }
+    c->stream_cols = ncols;
+  }
+  const ircur_params& p = c->p;
+  const int draw = p.resample ? K - 1 : 0;  // the rows I of the final iterate
+  const int* I = c->desc.I_all + (int64_t)draw * p.nI;
+  const double zeta0 = c->host_state.zeta0;
+  double zT = zeta0;  // zeta_0 gamma^iters, the threshold of S
+  for (int t = 0; t < iters; ++t) zT *= p.gamma;
+  IRCUR_CK(launch_stream(c->A[K & 1], I, c->desc.W, p.nI, c->Rpad, p.n1, Dnew, ldDn, ncols, iters, zeta0, p.gamma,
+                         (float)zT, c->stream_ws, Lnew, ldL, Snew, ldS, c->stream));
   return IRCUR_OK;
 }
 

@@ -202,6 +202,9 @@ cudaError_t launch_batch_check(const IterDesc* ds, int count, unsigned long long
                                cudaStream_t s);
 cudaError_t launch_svd_batch(const BatchLaunch& b, int Rpad, cudaStream_t s);
 cudaError_t launch_sigma(const float* Tm, int r, int Rpad, float* sigma, cudaStream_t s);
+cudaError_t launch_stream(const float* A, const int* I, const float* Y, int m, int Rpad, int64_t n1, const float* Dn,
+                          int64_t ldDn, int64_t ncols, int iters, double zeta0, double gamma, float zetaT, float* bq,
+                          float* L, int64_t ldL, float* S, int64_t ldS, cudaStream_t s);
 // Adjoint (k_adjoint.cu)
 cudaError_t launch_adj_dense(int64_t n1, int64_t n2, const float* A, const float* B, const float* D, int64_t ldD,
                              const float* dL, int64_t lddL, const float* dS, int64_t lddS, float* dD,

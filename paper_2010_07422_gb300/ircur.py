@@ -28,7 +28,7 @@ EXPORTED = (
     "ircur_status_string", "ircur_last_error_string", "ircur_solve_noalloc", "ircur_set_trace",
     "ircur_get_trace", "ircur_get_cur", "ircur_batch_create", "ircur_batch_destroy", "ircur_batch_solve",
     "ircur_batch_instance", "ircur_set_record", "ircur_backward", "ircur_autotune", "ircur_batch_autotune",
-    "ircur_get_svd",
+    "ircur_get_svd", "ircur_stream_columns",
 )
 
 
@@ -98,6 +98,7 @@ def _lib():
         lib.ircur_set_record.argtypes = [P, I32]
         lib.ircur_backward.argtypes = [P, P, I64, P, I64, P, I64, P, I64]
         lib.ircur_get_svd.argtypes = [P, P, P, P]
+        lib.ircur_stream_columns.argtypes = [P, P, I64, I64, I32, P, I64, P, I64]
         lib.ircur_autotune.argtypes = [P, P, I64, I32, C.POINTER(ircur_tune_result)]
         lib.ircur_batch_autotune.argtypes = [P, C.POINTER(P), C.POINTER(I64), I32, C.POINTER(ircur_tune_result)]
         lib.ircur_status_string.argtypes = [C.c_int]
@@ -165,6 +166,11 @@ def ircur_get_errors(ctx, max_iter):
 
 def ircur_reconstruct(ctx, D, ldD, L, ldL, S=None, ldS=0):
     _check(_lib().ircur_reconstruct(ctx, _ptr(D), ldD, _ptr(L), ldL, _ptr(S), ldS), "ircur_reconstruct")
+
+
+def ircur_stream_columns(ctx, Dnew, ldDn, ncols, iters, L, ldL, S=None, ldS=0):
+    _check(_lib().ircur_stream_columns(ctx, _ptr(Dnew), ldDn, ncols, iters, _ptr(L), ldL, _ptr(S), ldS),
+           "ircur_stream_columns")
 
 
 def ircur_solve_host(ctx, D_host, L_host, S_host=None):
@@ -381,6 +387,19 @@ class IRCUR:
             S = None
         ircur_reconstruct(self._ctx, D, D.stride(0) if D is not None else 0, L, L.stride(0),
                           S, S.stride(0) if S is not None else 0)
+        return L, S
+
+    def stream_columns(self, Dnew, iters=0, with_sparse=True):
+        """New columns (n1 x c, row-major, on the device) against the last
+        solve's CUR model: returns (L, S) for them (S None without with_sparse)."""
+        import torch
+        assert Dnew.is_cuda and Dnew.dtype == torch.float32 and Dnew.stride(1) == 1
+        n1, c = Dnew.shape
+        assert n1 == self.p.n1
+        L = torch.empty((n1, c), dtype=torch.float32, device="cuda")
+        S = torch.empty((n1, c), dtype=torch.float32, device="cuda") if with_sparse else None
+        ircur_stream_columns(self._ctx, Dnew, Dnew.stride(0), c, iters, L, L.stride(0),
+                             S, S.stride(0) if S is not None else 0)
         return L, S
 
 
