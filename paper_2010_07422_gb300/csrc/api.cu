@@ -1417,7 +1417,9 @@ extern "C" ircur_status ircur_batch_autotune(ircur_batch* b, const float* const*
     total += bl.total_tiles;
   }
   // candidates: k resident blocks per SM (capped per group) with two or one
-  // tile buffers, or one block per tile (k = 0)
+  // tile buffers, or one block per tile (k = 0).  (Grids in proportion to each
+  // group's share of the tiles, so that the groups' concurrent pass kernels
+  // split the GPU, measured 1.5-2.3x slower on the 64-instance batch.)
   TuneCand cand[IRCUR_TUNE_MAX];
   int nc = 0;
   for (int k = 1; k <= maxper && nc < IRCUR_TUNE_MAX - 1; ++k) {
@@ -1429,9 +1431,9 @@ extern "C" ircur_status ircur_batch_autotune(ircur_batch* b, const float* const*
     for (int g = 0; g < b->ngroups; ++g) {
       BatchLaunch& bl = b->grp[g];
       const int per = tc.single ? per1[g] : per2[g];
-      const int k = tc.grid == 0 ? 0 : (tc.grid < per ? tc.grid : (per > 0 ? per : 1));
       bl.pass_smem = tc.single ? smem1[g] : smem2[g];
       bl.pass_nbuf = tc.single ? nbuf1[g] : nbuf2[g];
+      const int k = tc.grid == 0 ? 0 : (tc.grid < per ? tc.grid : (per > 0 ? per : 1));
       bl.pass_grid = k == 0 ? bl.total_tiles : k * sms;
     }
     batch_reset_graph(b);

@@ -788,9 +788,11 @@ static cudaError_t launch_batch_iter_r(const BatchLaunch& b, cudaStream_t s) {
   {
     int grid = b.pass_grid > 0 ? b.pass_grid : pass_grid((const void*)pass_batch_kernel<R>, b.pass_smem);
     if (grid > b.total_tiles) grid = b.total_tiles;
-    pass_batch_kernel<R><<<grid, kPassThreads, b.pass_smem, s>>>(b.ds, b.tile_base, b.count, b.pass_mmax, b.pass_nbuf);
+    // a programmatic dependent of the batch's (last) core-SVD launch, as in
+    // the single-instance iteration
+    return launch_pdl(pass_batch_kernel<R>, grid, b.pass_smem, s, b.ds, b.tile_base, b.count, b.pass_mmax,
+                      b.pass_nbuf);
   }
-  return cudaGetLastError();
 }
 
 template <int R>

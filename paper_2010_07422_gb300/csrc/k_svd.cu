@@ -748,6 +748,7 @@ template <int R>
 __global__ void __launch_bounds__(kCsvdThreads, (R <= 7 ? 2 : 1)) csvd_batch_kernel(const IterDesc* __restrict__ ds,
                                                                     const int* __restrict__ list) {
   extern __shared__ __align__(16) unsigned char smem[];
+  pdl_launch_dependents();  // the batched pass kernel may start (it waits before the projections)
   csvd_body<R>(ds[list[blockIdx.x / kSvdCluster]], blockIdx.y, smem);
 }
 
@@ -1227,6 +1228,7 @@ template <int R>
 __global__ void __launch_bounds__(kSsvdThreads, 1) ssvd_batch_kernel(const IterDesc* __restrict__ ds,
                                                                     const int* __restrict__ list) {
   extern __shared__ __align__(16) unsigned char smem[];
+  pdl_launch_dependents();
   ssvd_body<R>(ds[list[blockIdx.x]], blockIdx.y, smem);
 }
 
