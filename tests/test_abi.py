@@ -103,3 +103,29 @@ def test_fault_injection_alloc_returns_enomem(lib, monkeypatch):
     bh = ctypes.c_void_p()
     assert ir._lib().ircur_batch_create((ir.ircur_params * 2)(p, p), 2, None, ctypes.byref(bh)) == ir.IRCUR_ENOMEM
     assert bh.value is None
+
+
+def declared_arity():
+    """Parameter count of every function include/ircur.h declares."""
+    out = {}
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"\b(ircur_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", text):
+            args = m.group(2).strip()
+            out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_the_header(lib):
+    """The ctypes argtypes of every entry point have as many arguments as its
+    declaration (an ABI change in one place and not the other fails here)."""
+    from paper_2010_07422_gb300 import ircur
+    lib_bound = ircur._lib()
+    arity = declared_arity()
+    assert set(arity) == set(declared_functions())
+    for name, n in arity.items():
+        argtypes = getattr(lib_bound, name).argtypes
+        if argtypes is None:  # no-argument functions are left without argtypes
+            assert n == 0, name
+            continue
+        assert len(argtypes) == n, (name, len(argtypes), n)
