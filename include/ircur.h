@@ -233,7 +233,9 @@ ircur_status ircur_get_trace(ircur_ctx* ctx, double* span_us, int32_t* iters);
  * device outputs with L = A B.  stream: cudaStream_t.  Synchronises the
  * stream; *out as for ircur_solve.
  * The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  All calls share the one array (its
+ * first call before any stream capture.  The address is kept for the life of
+ * the device's primary context: resetting the device (cudaDeviceReset) after
+ * that first call is not supported.  All calls share the one array (its
  * contents persist between calls; each call clears what must start at
  * zero), so calls that overlap on the GPU -- from several streams or host
  * threads -- race and must not be issued. */

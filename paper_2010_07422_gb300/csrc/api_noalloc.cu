@@ -79,7 +79,10 @@ extern "C" ircur_status ircur_solve_noalloc(const ircur_params* params, const fl
   if (ldD < p.n2 || (reinterpret_cast<uintptr_t>(D) & 3)) return IRCUR_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
-  // device address of the workspace, looked up once per device
+  // device address of the workspace, looked up once per device (the first
+  // call on each device, with that device current).  The address stays valid
+  // for the life of the device's primary context: a cudaDeviceReset after the
+  // first call is not supported (the module may be reloaded elsewhere).
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= 256) return IRCUR_ECUDA;

@@ -16,6 +16,8 @@
 // each residual formed explicitly (no difference of squared norms).
 #include <string.h>
 
+#include <mutex>
+
 #include "device_common.cuh"
 #include "ircur_internal.cuh"
 
@@ -702,29 +704,35 @@ size_t pass_smem_bytes(int nI, int nJ, int Rpad, int* nbuf_out, bool bf16, bool 
   return bytes;
 }
 
-// Resident blocks of a pass kernel (cached per kernel and shared-memory size).
+// Resident blocks of a pass kernel on the current device, cached per (device,
+// kernel, shared-memory size).  Solves on several host threads may ask at
+// once: the cache is guarded by a mutex.
 static int pass_grid(const void* fn, size_t smem) {
-  static int num_sms = 0;
   struct Entry {
+    int dev;
     const void* fn;
     size_t smem;
     int blocks;
   };
+  static std::mutex mu;
   static Entry cache[64];
   static int ncache = 0;
-  for (int q = 0; q < ncache; ++q)
-    if (cache[q].fn == fn && cache[q].smem == smem) return cache[q].blocks;
-  if (num_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || num_sms <= 0)
-      num_sms = kNumSMsHint;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    for (int q = 0; q < ncache; ++q)
+      if (cache[q].dev == dev && cache[q].fn == fn && cache[q].smem == smem) return cache[q].blocks;
   }
+  int num_sms = 0;
+  if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || num_sms <= 0)
+    num_sms = kNumSMsHint;
   int per_sm = 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPassThreads, smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   const int blocks = per_sm * num_sms;
-  if (ncache < 64) cache[ncache++] = Entry{fn, smem, blocks};
+  std::lock_guard<std::mutex> lock(mu);
+  if (ncache < 64) cache[ncache++] = Entry{dev, fn, smem, blocks};
   return blocks;
 }
 cudaError_t launch_svd(const IterDesc& d, int Rpad, cudaStream_t s);

@@ -19,6 +19,12 @@ the supplement's setup):
                      [0, 1].
 * ``random_subset`` -- a sorted uniform m-subset of [0, n) from numpy's PCG64,
                      for handing explicit index sets to both sides.
+* ``planted_spectrum`` -- the ``planted`` recipe with L = Q1 diag(sigma) Q2^T
+                     for orthonormal Q1, Q2 and a prescribed spectrum sigma
+                     (ill-conditioned low-rank parts).
+* ``lowrank_core_spectrum`` -- a low-rank D whose |I| x |J| core D(I,J), for
+                     given index sets, has exactly the prescribed singular
+                     values (narrow gaps and deficient ranks of the core).
 * ``planted_device`` -- the ``planted`` recipe drawn directly in device memory
                      with torch's CUDA generator (FP32 throughout), for large
                      timing workloads whose values no oracle needs; the
@@ -97,6 +103,57 @@ def planted(n1, n2, r, alpha, seed, outlier_scale=10.0, chunk_rows=2048):
     D.reshape(-1)[pos] = (lv + val).astype(np.float32)
     # the non-outlier entries: FP64 L rounded once to FP32
     return Planted(D=D, W=W, V=V, s_pos=pos, s_val=val, mean_abs_L=mean_abs)
+
+
+def _outliers_into(rng, D, W, V, alpha, outlier_scale, mean_abs):
+    n1, n2 = D.shape
+    k = int(round(alpha * n1 * n2))
+    pos = _distinct_positions(rng, n1 * n2, k)
+    half = outlier_scale * mean_abs
+    val = rng.uniform(-half, half, size=k)
+    rows, cols = np.divmod(pos, n2)
+    lv = np.einsum("kt,kt->k", W[rows], V[cols])
+    D.reshape(-1)[pos] = (lv + val).astype(np.float32)
+    return pos, val
+
+
+def planted_spectrum(n1, n2, sigmas, alpha, seed, outlier_scale=10.0):
+    """Planted pair whose low-rank part has the singular values `sigmas`
+    (times sqrt(n1 n2), so that entries are of order sigmas[0]):
+    L = Q1 diag(s) Q2^T with Q1 (n1 x r), Q2 (n2 x r) orthonormal (QR of
+    Gaussian matrices); outliers as in ``planted``."""
+    rng = np.random.default_rng(seed)
+    sig = np.asarray(sigmas, np.float64) * math.sqrt(n1 * n2)
+    r = sig.size
+    Q1, _ = np.linalg.qr(rng.standard_normal((n1, r)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((n2, r)))
+    W = Q1 * sig
+    V = Q2
+    L = W @ V.T
+    mean_abs = float(np.abs(L).mean())
+    D = L.astype(np.float32)
+    pos, val = _outliers_into(rng, D, W, V, alpha, outlier_scale, mean_abs)
+    return Planted(D=D, W=W, V=V, s_pos=pos, s_val=val, mean_abs_L=mean_abs)
+
+
+def lowrank_core_spectrum(n1, n2, I, J, core_sigmas, seed):
+    """D = W V^T (rank len(core_sigmas), FP32, no outliers) whose core D(I,J)
+    is exactly Q1 diag(core_sigmas) Q2^T up to the FP32 rounding of D, for
+    orthonormal Q1 (|I| x k), Q2 (|J| x k): the rows W(I,:) = Q1 diag(sigmas)
+    and V(J,:) = Q2 are set, the other rows are Gaussian with the core's scale."""
+    rng = np.random.default_rng(seed)
+    s = np.asarray(core_sigmas, np.float64)
+    k = s.size
+    I = np.asarray(I, np.int64)
+    J = np.asarray(J, np.int64)
+    Q1, _ = np.linalg.qr(rng.standard_normal((I.size, k)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((J.size, k)))
+    W = rng.standard_normal((n1, k)) * (s / math.sqrt(I.size))
+    V = rng.standard_normal((n2, k)) / math.sqrt(J.size)
+    W[I] = Q1 * s
+    V[J] = Q2
+    D = (W @ V.T).astype(np.float32)
+    return Planted(D=D, W=W, V=V, s_pos=np.zeros(0, np.int64), s_val=np.zeros(0), mean_abs_L=float(np.abs(D).mean()))
 
 
 def random_subset(n, m, seed):

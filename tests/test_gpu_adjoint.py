@@ -3,9 +3,10 @@ FP64 oracle gradient (oracle/ircur_adjoint.py, itself pinned by central finite
 differences in test_adjoint_oracle.py).
 
 Bar: relative Frobenius error of dD <= 1e-5.  The GPU path is FP32 with the
-same index sets and the same threshold decisions as the oracle (no entry sits
-within FP32 rounding of a threshold on these seeded inputs: the forward parity
-tests check the masks); the error budget is FP32 rounding carried through K
+same index sets and the same threshold decisions as the oracle (the masks
+themselves are compared with the oracle's entry by entry, outside a tie band, in
+test_gpu_masks.py; an entry whose decision flipped would change the gradient far
+beyond the bar); the error budget is FP32 rounding carried through K
 iterations of rank-r products and the shifted conjugate-gradient solves
 (stopped at 1e-6 relative residual), measured at 2e-7 .. 8e-7.
 """

@@ -1,0 +1,140 @@
+"""Parity with the FP64 oracle on cores that are hard for the rank-r truncation
+H_r of Sec. 3.1: ill-conditioned low-rank parts, narrow gaps sigma_r/sigma_{r+1}
+and rank-deficient cores.
+
+Validity range of the GPU's H_r (FP32 products; the iteration is described in
+k_svd.cu).  It matches the oracle to FP32 rounding when
+  * the subspace iteration converges within its step cap, which needs a gap
+    sigma_r > sigma_{r+1}: otherwise IRCUR_FLAG_SVD_NOCONV is set; and
+  * sigma_r / sigma_1 exceeds the FP32 rank cutoff max(|I|,|J|) * 2^-23; a
+    direction below it is dropped (numerical rank < r) and IRCUR_FLAG_WRANK is
+    set, where the oracle's FP64 cutoff max(|I|,|J|) * 2^-52 keeps it.
+The tests below put cores on both sides of each limit and check either parity
+at 1e-5 or the flag.
+"""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2010_07422_gb300 import ircur as ir  # noqa: E402
+from paper_2010_07422_gb300 import synth  # noqa: E402
+
+TOL_LS = 1e-5
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _gpu(D_np, r, max_iter, resample, seed, idx=None):
+    n1, n2 = D_np.shape
+    D = torch.from_numpy(np.ascontiguousarray(D_np)).cuda()
+    nI = idx[0].shape[-1] if idx is not None else 0
+    nJ = idx[1].shape[-1] if idx is not None else 0
+    s = ir.IRCUR(n1, n2, r, nI=nI, nJ=nJ, gamma=0.7, tol=1e-30, max_iter=max_iter, resample=resample, seed=seed)
+    if idx is not None:
+        res = s.solve(D, torch.from_numpy(idx[0].astype(np.int32)).cuda(),
+                      torch.from_numpy(idx[1].astype(np.int32)).cuda())
+    else:
+        res = s.solve(D)
+    L, S = s.reconstruct(D)
+    torch.cuda.synchronize()
+    out = (res, L.double().cpu().numpy(), S.double().cpu().numpy())
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e3, 1e4])
+@pytest.mark.parametrize("resample", [True, False])
+def test_ill_conditioned_lowrank_parity(kappa, resample):
+    """L = Q1 diag(sigma) Q2^T with sigma_1/sigma_5 = kappa (geometric), alpha = 0.1,
+    n = 1000: the cores' sigma_5/sigma_1 reach about 1/kappa (IRCUR-R)."""
+    n, r, seed = 1000, 5, 3
+    p = synth.planted_spectrum(n, n, np.geomspace(1.0, 1.0 / kappa, r), 0.1, seed=int(np.log10(kappa)))
+    ref = oracle.ircur(p.D, r, 0, 0.7, 1e-5, 100, resample=resample, seed=seed)
+    Lo, So = oracle.dense_outputs(p.D, ref)
+    res, L, S = _gpu(p.D, r, ref.iters, resample, seed)
+    assert res.iters == ref.iters
+    assert res.flags == 0, res.flags
+    assert rel(L, Lo) <= TOL_LS, rel(L, Lo)
+    assert rel(S, So) <= TOL_LS, rel(S, So)
+
+
+def _core_problem(n, m, sig, seed):
+    I = synth.random_subset(n, m, seed)
+    J = synth.random_subset(n, m, seed + 1)
+    p = synth.lowrank_core_spectrum(n, n, I, J, sig, seed + 2)
+    return p, I, J
+
+
+def _first_iteration(p, I, J, r):
+    """One iteration with zeta_0 = max|D| (nothing thresholded): L_1 is the CUR of D
+    with U = H_r(D(I,J)) -- the truncation alone decides it."""
+    draws = lambda k: (I, J)  # noqa: E731
+    ref = oracle.ircur(p.D, r, 0, 0.7, 1e-30, 1, nI=I.size, nJ=J.size, resample=False, index_draws=draws)
+    Lo, _ = oracle.dense_outputs(p.D, ref, with_sparse=False)
+    res, L, _ = _gpu(p.D, r, 1, False, 0, idx=(I, J))
+    return ref, Lo, res, L
+
+
+@pytest.mark.parametrize("gap", [1.05, 1.2])
+def test_narrow_gap_core_parity(gap):
+    """Core spectrum (1, .8, .6, .5, .45, .45/gap): r = 5 keeps five directions and
+    drops the sixth, which is within a factor `gap` of the fifth."""
+    n, m, r = 1200, 150, 5
+    sig = [1.0, 0.8, 0.6, 0.5, 0.45, 0.45 / gap]
+    p, I, J = _core_problem(n, m, sig, 40)
+    ref, Lo, res, L = _first_iteration(p, I, J, r)
+    assert ref.ranks == [5]
+    assert res.flags & ir.IRCUR_FLAG_SVD_NOCONV == 0
+    assert rel(L, Lo) <= TOL_LS, rel(L, Lo)
+
+
+def test_gap_below_the_iteration_limit_sets_the_flag():
+    """sigma_5/sigma_6 = 1.0002: subspace iteration cannot separate the two directions
+    within its step cap; the flag says so (or the result is still within 1e-5)."""
+    n, m, r = 1200, 150, 5
+    sig = [1.0, 0.8, 0.6, 0.5, 0.45, 0.45 / 1.0002]
+    p, I, J = _core_problem(n, m, sig, 50)
+    ref, Lo, res, L = _first_iteration(p, I, J, r)
+    assert (res.flags & ir.IRCUR_FLAG_SVD_NOCONV) or rel(L, Lo) <= TOL_LS, (res.flags, rel(L, Lo))
+
+
+@pytest.mark.parametrize("s5,wrank", [(1e-3, False), (1e-4, False), (1e-6, True), (0.0, True)])
+def test_rank_of_the_core(s5, wrank):
+    """Core spectrum (1, .8, .6, .5, s5) with r = 5.  Above the FP32 cutoff
+    (185 * 2^-23 = 2.2e-5 relative) both keep rank 5; below it the GPU keeps 4 and
+    sets IRCUR_FLAG_WRANK.  The oracle's FP64 cutoff keeps s5 = 1e-6 and, at
+    s5 = 0, the FP32 rounding noise of D (about 1e-8 relative): their
+    contributions to L are of relative size 7e-7 and 2e-9, inside the bar."""
+    n, m, r = 1500, 185, 5
+    sig = [1.0, 0.8, 0.6, 0.5] + ([s5] if s5 > 0 else [])
+    p, I, J = _core_problem(n, m, sig, 60 + int(-np.log10(s5)) if s5 > 0 else 70)
+    ref, Lo, res, L = _first_iteration(p, I, J, r)
+    assert ref.ranks == [5]
+    assert bool(res.flags & ir.IRCUR_FLAG_WRANK) == wrank, res.flags
+    assert rel(L, Lo) <= TOL_LS, rel(L, Lo)
+
+
+def test_exactly_rank_deficient_core():
+    """An integer D of exact rank 4 (representable in FP32) with r = 5: the core is
+    exactly rank 4, the oracle's pseudo-inverse drops the fifth direction, the GPU
+    sets IRCUR_FLAG_WRANK, and both give L = D (Thm 1 with rank U = rank L)."""
+    rng = np.random.default_rng(5)
+    n, m, r = 900, 120, 5
+    W = rng.integers(-3, 4, size=(n, 4)).astype(np.float64)
+    V = rng.integers(-3, 4, size=(n, 4)).astype(np.float64)
+    D = (W @ V.T).astype(np.float32)
+    I = synth.random_subset(n, m, 1)
+    J = synth.random_subset(n, m, 2)
+    p = synth.Planted(D=D, W=W, V=V, s_pos=np.zeros(0, np.int64), s_val=np.zeros(0), mean_abs_L=1.0)
+    ref, Lo, res, L = _first_iteration(p, I, J, r)
+    assert ref.ranks == [4]
+    assert res.flags & ir.IRCUR_FLAG_WRANK
+    assert rel(Lo, D.astype(np.float64)) <= 1e-12
+    assert rel(L, Lo) <= TOL_LS, rel(L, Lo)

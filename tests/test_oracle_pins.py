@@ -18,7 +18,8 @@ import numpy as np
 import pytest
 
 from oracle import (cur_product, cur_to_svd, dense_outputs, entries, hard_threshold, ircur,
-                    pinv_from_svd, sample_indices, sample_size, splitmix64, truncated_svd)
+                    numerical_rank, pinv_from_svd, sample_indices, sample_size, splitmix64,
+                    truncated_svd)
 from paper_2010_07422_gb300 import synth
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -43,9 +44,44 @@ def _subsets(n, kmin):
         yield from itertools.combinations(range(n), k)
 
 
+def _exact_rank(M):
+    """Rank of an integer matrix by fraction-free (Bareiss) elimination in Python
+    integers: exact, and independent of LAPACK and of any tolerance."""
+    A = [[int(v) for v in row] for row in np.asarray(M)]
+    rows, cols = len(A), len(A[0]) if A else 0
+    rank, prev = 0, 1
+    for c in range(cols):
+        piv = next((i for i in range(rank, rows) if A[i][c] != 0), None)
+        if piv is None:
+            continue
+        A[rank], A[piv] = A[piv], A[rank]
+        for i in range(rank + 1, rows):
+            for j in range(c + 1, cols):
+                A[i][j] = (A[i][j] * A[rank][c] - A[i][c] * A[rank][j]) // prev
+            A[i][c] = 0
+        prev = A[rank][c]
+        rank += 1
+    return rank
+
+
+def test_exact_rank_helper():
+    assert _exact_rank(np.eye(4)) == 4
+    assert _exact_rank([[1, 2, 3], [2, 4, 6], [1, 0, 1]]) == 2
+    assert _exact_rank(np.zeros((3, 2))) == 0
+    assert _exact_rank([[0, 0, 5], [0, 0, 1]]) == 1
+    rng = np.random.default_rng(1)
+    W, V = rng.integers(-3, 4, (7, 3)), rng.integers(-3, 4, (5, 3))
+    assert _exact_rank(W @ V.T) == min(_exact_rank(W), _exact_rank(V), 3)
+
+
 @pytest.mark.parametrize("r", [1, 2, 3])
 def test_cur_identity_bruteforce(r):
-    """L = C U^+ R for every I, J with rank(U) = rank(L) (Thm 1), all subsets."""
+    """L = C U^+ R for every I, J with rank(U) = rank(L) (Thm 1), all subsets.
+
+    The rank of each core comes from exact integer elimination, not from the
+    oracle's tolerance: where the core is rank deficient the oracle's
+    pseudo-inverse must use exactly that smaller rank (Sec. 3.1 truncation of a
+    matrix whose trailing singular values are zero)."""
     rng = np.random.default_rng(100 + r)
     n = 6
     W = rng.integers(-3, 4, size=(n, r)).astype(float)
@@ -53,22 +89,48 @@ def test_cur_identity_bruteforce(r):
     W[1] = W[0]  # repeated rows/cols make some samples rank deficient
     V[2] = 0.0
     L = W @ V.T
-    assert np.linalg.matrix_rank(L) == r
-    holds = fails_deficient = 0
+    assert _exact_rank(L) == r
+    holds = fails_deficient = deficient = 0
     for I in _subsets(n, r):
         for J in _subsets(n, r):
             C, U, R = L[:, J], L[np.ix_(I, J)], L[I, :]
             W_r, s_r, V_r = truncated_svd(U, r)
             Up, rank = pinv_from_svd(W_r, s_r, V_r, U.shape)
             err = np.linalg.norm(cur_product(C, Up, R) - L)
-            if np.linalg.matrix_rank(U) == r:
-                assert rank == r
+            true_rank = _exact_rank(U)
+            assert rank == true_rank, (I, J, rank, true_rank)
+            if true_rank == r:
                 assert err <= 1e-10 * np.linalg.norm(L)
                 holds += 1
-            elif err > 1e-8 * np.linalg.norm(L):
-                fails_deficient += 1
+            else:
+                deficient += 1
+                if err > 1e-8 * np.linalg.norm(L):
+                    fails_deficient += 1
     assert holds > 100
+    assert deficient > 0
     assert fails_deficient > 0  # rank(U) < rank(L): the identity need not hold
+
+
+def test_numerical_rank_cutoff_is_strict_and_fp64():
+    """The pseudo-inverse drops singular values s <= max(|I|,|J|) * eps64 * s_1:
+    at the cutoff itself the value is dropped (strict >), just above it kept, and
+    a value far below FP32 resolution but above the FP64 cutoff is kept."""
+    eps = np.finfo(np.float64).eps
+    for shape in [(2, 2), (7, 3), (185, 185)]:
+        tol = max(shape) * eps
+        assert numerical_rank(np.array([1.0, tol]), shape) == 1
+        assert numerical_rank(np.array([1.0, 2.0 * tol]), shape) == 2
+        assert numerical_rank(np.array([4.0, 4.0 * tol]), shape) == 1
+        assert numerical_rank(np.array([1.0, 1e-10]), shape) == 2
+        assert numerical_rank(np.array([1.0, 0.5, 0.0]), shape) == 2
+    assert numerical_rank(np.array([0.0, 0.0]), (3, 3)) == 0
+    assert numerical_rank(np.array([]), (3, 3)) == 0
+    # through the SVD: a diagonal core with an exactly known spectrum
+    U = np.diag([3.0, 1.0, 3.0 * 2 * eps, 0.0])
+    W_r, s_r, V_r = truncated_svd(U, 4)
+    Up, rank = pinv_from_svd(W_r, s_r, V_r, U.shape)
+    assert rank == 2
+    assert np.array_equal(np.abs(Up), np.diag([1 / 3.0, 1.0, 0.0, 0.0]))
 
 
 # ---------------------------------------------------------------- pinv, H_r

@@ -19,10 +19,11 @@ torch = pytest.importorskip("torch")
 from paper_2010_07422_gb300 import ircur as ir  # noqa: E402
 from paper_2010_07422_gb300 import synth  # noqa: E402
 
-TOL_LS = 1e-5
-
 
 def test_noalloc_matches_the_allocating_entry_point_twice():
+    """Both entry points run the same kernels with the same launch shapes on the
+    same inputs, so the factors must agree bit for bit -- on the first call and on
+    a second call that finds the first call's leftovers in the shared array."""
     n1, n2, r = 1500, 1200, 5
     p = synth.planted(n1, n2, r, 0.1, seed=21)
     D = torch.from_numpy(p.D).cuda()
@@ -32,7 +33,6 @@ def test_noalloc_matches_the_allocating_entry_point_twice():
     res_ref = ref.solve(D)
     A_ref, B_ref = ref.factors()
     torch.cuda.synchronize()
-    L_ref = (A_ref.double() @ B_ref.double()).cpu().numpy()
     ref.close()
 
     params = ir.ircur_params(n1=n1, n2=n2, r=r, nI=0, nJ=0, zeta0=0.0, gamma=0.7, tol=1e-5, max_iter=100,
@@ -43,8 +43,8 @@ def test_noalloc_matches_the_allocating_entry_point_twice():
         res = ir.ircur_solve_noalloc(params, D, D.stride(0), A, B, stream)
         torch.cuda.synchronize()
         assert res.iters == res_ref.iters and res.converged
-        L = (A.double() @ B.double()).cpu().numpy()
-        assert np.linalg.norm(L - L_ref) <= TOL_LS * np.linalg.norm(L_ref)
+        assert res.final_err == res_ref.final_err
+        assert torch.equal(A, A_ref) and torch.equal(B, B_ref)
 
     # sizes beyond the fixed array and IRCUR-R are rejected, nothing is launched
     big = ir.ircur_params(n1=4096, n2=1200, r=r, nI=0, nJ=0, zeta0=0.0, gamma=0.7, tol=1e-5, max_iter=100,
