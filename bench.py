@@ -80,20 +80,23 @@ def peaks():
 
 
 def dram_traffic(kernel, workload_tag):
-    """DRAM bytes per launch recorded from an ncu capture in profiles/, or None
-    when no capture exists or the kernel's source changed since it was taken."""
-    prof = os.path.join(ROOT, "profiles", "dram_traffic.md")
-    if not os.path.exists(prof):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+    an ncu capture recorded in profiles/dram_traffic.json, or None when no
+    capture exists or the kernel's source file changed since it was taken."""
+    prof = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(prof) as f:
+            caps = json.load(f)["captures"]
+    except Exception:
         return None
-    for line in open(prof):
-        m = re.match(r"\|\s*(\S+)\s*\|\s*(\S+)\s*\|\s*([0-9.e+]+)\s*\|\s*(\S+)\s*\|\s*(\S+)\s*\|", line)
-        if not m or m.group(1) != kernel or m.group(2) != workload_tag:
+    for c in caps:
+        if c.get("kernel") != kernel or c.get("workload") != workload_tag:
             continue
-        src = os.path.join(ROOT, "paper_2010_07422_gb300", "csrc", m.group(4))
+        src = os.path.join(ROOT, "paper_2010_07422_gb300", "csrc", c["source"])
         if not os.path.exists(src):
             return None
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:12]
-        return float(m.group(3)) if sha == m.group(5) else None
+        return float(c["bytes"]) if sha == c["sha256_12"] else None
     return None
 
 
@@ -388,15 +391,23 @@ def run_sweep(a):
                     ir.ircur_set_trace(s_._ctx, True)
                     s_.solve(D)
                     spans = ir.ircur_get_trace(s_._ctx, 100)
-                    pass_us = float(np.mean([q for _, _, q in spans]))
-                    svd_us = float(np.mean([v for _, v, _ in spans]))
+                    pass_us = float(np.mean([q[2] for q in spans]))
+                    pass_post_us = float(np.mean([q[3] for q in spans]))
+                    svd_us = float(np.mean([q[1] for q in spans]))
                     nI, nJ, Rp = s_.nI, s_.nJ, (r if r <= 10 else 16)
-                    pass_gbs = (4.0 * (nI + nJ) * n + 2 * 4.0 * Rp * 2 * n) / (pass_us * 1e-6) / 1e9
+                    pbytes = 4.0 * (nI + nJ) * n + 2 * 4.0 * Rp * 2 * n
+                    pass_gbs = pbytes / (pass_us * 1e-6) / 1e9
                     L, _ = s_.reconstruct(D, with_sparse=False)
                     line = {"sweep": True, "n": n, "r": r, "alpha": alpha, "variant": variant, "m": nI,
                             "iters": res.iters, "converged": bool(res.converged), "time_to_tol_ms": ms,
-                            "iters_per_s": res.iters / (ms / 1e3), "svd_us": svd_us, "pass_us": pass_us,
-                            "pass_gbs": pass_gbs, "pass_frac_of_measured_hbm": pass_gbs / peaks()[0]}
+                            "iters_per_s": res.iters / (ms / 1e3), "svd_us": svd_us,
+                            "pass_us": pass_us, "pass_after_svd_us": pass_post_us,
+                            "pass_bytes": pbytes, "pass_gbs": pass_gbs,
+                            "pass_frac_of_measured_hbm": pass_gbs / peaks()[0],
+                            "pass_gbs_after_svd": pbytes / (pass_post_us * 1e-6) / 1e9,
+                            "span_note": "pass_us: first pass block start (it starts during the core SVD) to "
+                                         "last block end; pass_after_svd_us: from its first return of the "
+                                         "wait for the SVD"}
                     if n <= 2500:
                         Dn = D.cpu().numpy()
                         t0 = time.perf_counter()
@@ -554,15 +565,20 @@ def main():
     # Alg. 2 (CUR to SVD) of the last iterate, on request after the solve
     c2s_us = 1e3 * _timed(lambda: solver.svd(), 5, stream)
 
-    # Per-kernel spans of the last timed step (device clock, inside the graph)
+    # Per-kernel spans of the last timed step (device clock, inside the graph):
+    # Phase I on the core (the SVD's prologue), the core SVD, the panel pass
+    # from its first block's start (its blocks start while the SVD runs) and
+    # from its first return of the wait for the SVD
     spans = ir.ircur_get_trace(solver._ctx, 100)
     K = len(spans)
-    core_us = [c for c, _, _ in spans]
-    svd_us = [v for _, v, _ in spans]
-    pass_us = [q for _, _, q in spans]
+    core_us = [q[0] for q in spans]
+    svd_us = [q[1] for q in spans]
+    pass_us = [q[2] for q in spans]
+    pass_post_us = [q[3] for q in spans]
     rec_avg_us = float(np.mean(recon_ms)) * 1e3
-    per_step_us = {"core_kernel": float(np.sum(core_us)), "csvd_kernel": float(np.sum(svd_us)),
-                   "pass_kernel": float(np.sum(pass_us)), "recon_vec_kernel": rec_avg_us}
+    per_step_us = {"core_phase1_in_svd": float(np.sum(core_us)), "csvd_kernel": float(np.sum(svd_us)),
+                   "pass_kernel": float(np.sum(pass_us)), "pass_kernel_after_svd": float(np.sum(pass_post_us)),
+                   "recon_vec_kernel": rec_avg_us}
     hbm_peak, peak_src = peaks()
     peak_note = ("measured STREAM-style copy (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                  else "fallback 6.8 TB/s")
@@ -577,24 +593,36 @@ def main():
 
     # reconstruction: read D, write L and S (12 bytes per entry) + the factors
     roof_recon = roof_hbm("recon_vec_kernel", 12.0 * n * n + 4.0 * r * 2 * n, rec_avg_us, f"n{n}_r{r}")
-    # panel passes: the two panels once, A_k, B_k read, A_{k+1}, B_{k+1} written
+    # panel passes: the two panels once, A_k, B_k read, A_{k+1}, B_{k+1} written;
+    # the full launch span (its tile loads overlap the SVD) sets the fraction,
+    # the span after the SVD is the time it adds to an iteration
     pass_bytes = 4.0 * (nI * n + nJ * n) + 2 * 4.0 * Rp * (n + n)
     roof_pass = roof_hbm("pass_kernel", pass_bytes, float(np.mean(pass_us)), f"n{n}_r{r}")
-    # core SVD (one 8-CTA cluster): FP32 work per launch = 2 products of 2 nI nJ r
-    # flops per subspace step, plus the Cholesky QR passes (4 (nI + nJ) r^2 per step)
-    steps = svd_steps / max(1.0, my_iters)
-    svd_flops = steps * (4.0 * nI * nJ * r + 4.0 * (nI + nJ) * r * r)
+    roof_pass["span"] = "first block start to last block end (its blocks start while the core SVD runs)"
+    roof_pass["avg_after_svd_us"] = float(np.mean(pass_post_us))
+    roof_pass["achieved_after_svd"] = pass_bytes / (roof_pass["avg_after_svd_us"] * 1e-6) / 1e9
+    # core SVD: FP32 work per launch = one product of 2 nI nJ r flops per
+    # half-step, plus its Cholesky QR (2 (nI or nJ) r^2), and Phase I on the core
+    # (2 r flops per entry)
+    hsteps = svd_steps / max(1.0, my_iters)
+    svd_flops = hsteps * (2.0 * nI * nJ * r + (nI + nJ) * r * r) + 2.0 * r * nI * nJ
     fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12  # TFLOP/s: SMs x FP32 lanes x FMA x max SM clock
     svd_avg_us = float(np.mean(svd_us))
     svd_ach = svd_flops / (svd_avg_us * 1e-6) / 1e12
+    nc_svd = 8
     roof_svd = {"kernel": "csvd_kernel", "bound": "alu", "achieved": svd_ach, "peak": fp32_peak,
                 "unit": "TFLOP/s", "frac": svd_ach / fp32_peak, "traffic": dram_traffic("csvd_kernel", f"n{n}_r{r}"),
                 "peak_source": "FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (one 8-CTA cluster by "
                                "design: its share is 8/152 of this)",
                 "algorithmic_flops_per_launch": svd_flops, "avg_launch_us": svd_avg_us,
-                "frac_of_its_8_sms": svd_ach / (fp32_peak * 8 / 152)}
+                "half_steps_per_launch": hsteps,
+                "frac_of_its_8_sms": svd_ach / (fp32_peak * nc_svd / 152)}
     roofs = {"recon_vec_kernel": roof_recon, "pass_kernel": roof_pass, "csvd_kernel": roof_svd}
-    dominant = max(("csvd_kernel", "pass_kernel", "recon_vec_kernel"), key=lambda kk: per_step_us[kk])
+    # the kernel that takes the most of a step: the pass counts with the time it
+    # adds after the SVD (its earlier part overlaps the SVD)
+    share = {"csvd_kernel": per_step_us["csvd_kernel"], "pass_kernel": per_step_us["pass_kernel_after_svd"],
+             "recon_vec_kernel": per_step_us["recon_vec_kernel"]}
+    dominant = max(share, key=lambda kk: share[kk])
 
     e2e = None
     if a.e2e_steps > 0:
@@ -682,7 +710,11 @@ def main():
             torch.cuda.synchronize()
 
     if rank == 0:
-        launches_per_step = [4 + (2 if not resample else 0) + 3 * it + 1 for it in iters]
+        # per solve: setup, sampler, max|D| (+ D^T for IRCUR-R), zeta_0, the core's
+        # D(I,J) (+ the two panel gathers for IRCUR-F); per iteration the core SVD and
+        # the panel pass, launched for every iteration of each four-iteration graph
+        # trip; the reconstruction
+        launches_per_step = [5 + (2 if not resample else 0) + 2 * 4 * ((it + 3) // 4) + 1 for it in iters]
         line = {
             "metric": METRIC, "value": all_iters / (total_ms_max / 1e3), "unit": "iters/s",
             "n_gpus": world, "steps": a.steps, "warmup": max(3, a.warmup),
@@ -705,9 +737,10 @@ def main():
             "autotune": tune,
             "cur_to_svd_us": c2s_us,
             "timing_note": "kernel spans from the device clock (first block start to last block end) inside "
-                           "the CUDA graph (the pass kernel from the moment it stops waiting for the core SVD: "
-                           "it is launched as a programmatic dependent and overlaps the SVD's tail); the "
-                           "reconstruction by CUDA events on the solver's stream",
+                           "the CUDA graph; the pass kernel is launched as a programmatic dependent of the "
+                           "core SVD and overlaps it: pass_kernel is its whole launch span (used for its "
+                           "roofline fraction), pass_kernel_after_svd the span from its first return of the "
+                           "wait for the SVD; the reconstruction by CUDA events on the solver's stream",
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(sum(launches_per_step)),

@@ -45,6 +45,8 @@ typedef enum {
 /* ircur_result.flags bits */
 #define IRCUR_FLAG_WRANK 1u        /* some core had numerical rank < r (pinv used that rank) */
 #define IRCUR_FLAG_SVD_NOCONV 2u   /* the core's subspace iteration hit its step cap */
+#define IRCUR_FLAG_SVD_GAP 4u      /* some core's truncated subspace stopped at the FP32 floor before its
+                                      gap-scaled accuracy target: sigma_r / sigma_{r+1} too close to 1 */
 
 /* Largest rank r this build supports. */
 #define IRCUR_MAX_RANK 16
@@ -64,15 +66,17 @@ typedef enum {
 #define IRCUR_PRECISION_FP32 0
 #define IRCUR_PRECISION_BF16_PANELS 1
 
-/* ircur_params.svd_form: how the core's rank-r truncation H_r (Sec. 3.1) runs
- * on the GPU.  Both forms compute the same subspace iteration with the same
- * stopping rule; their results agree to FP32 rounding, not bit for bit.
- * CLUSTER: one 8-CTA thread-block cluster per core, the core's rows split
- *   over the 8 SMs (the faster form for one solve).
- * ONE_CTA: one CTA of 1024 threads per core, the whole core in its shared
- *   memory; used where the padded rank is <= 8 and the core fits in one SM
- *   (about |I|, |J| <= 200), the cluster form elsewhere.  Batches of many
- *   instances run faster with it (one SM per instance instead of eight). */
+/* ircur_params.svd_form: how Phase I on the core and the rank-r truncation
+ * H_r (Sec. 3.1) run on the GPU.  Both forms run the same subspace iteration
+ * with the same stopping rule; their results agree to FP32 rounding, not bit
+ * for bit.
+ * CLUSTER: one thread-block cluster of 8 CTAs per core (16 where the core's
+ *   slabs of 8 do not fit), each CTA holding a slab of the core's rows and one
+ *   of its columns (the faster form for one solve).
+ * ONE_CTA: one CTA of 512 threads per core, the whole core in its shared
+ *   memory, where that fits (about |I|, |J| <= 220 at r <= 8); the cluster form
+ *   elsewhere.  Batches of many instances run faster with it (one SM per
+ *   instance instead of eight). */
 #define IRCUR_SVD_CLUSTER 0
 #define IRCUR_SVD_ONE_CTA 1
 
@@ -98,7 +102,7 @@ typedef struct {
   int32_t iters;      /* iterations run, K */
   int32_t converged;  /* 1 if e_K <= tol */
   uint32_t flags;     /* IRCUR_FLAG_* */
-  int32_t svd_steps;  /* subspace-iteration steps summed over all iterations */
+  int32_t svd_steps;  /* products with the core (half-steps of the subspace iteration), all iterations */
   double final_err;   /* e_K, the stopping criterion of Sec. 3.3 */
   double zeta0;       /* zeta_0 actually used (max|D| when requested) */
   double zeta_next;   /* gamma^K zeta_0, the threshold ircur_reconstruct uses for S */
@@ -203,17 +207,20 @@ ircur_status ircur_sample_indices(uint64_t seed, int32_t draw, int32_t axis, int
                                   int32_t* out, void* stream);
 
 /* Kernel-span tracing (for profiling; off by default).  enable != 0
- * allocates a small device buffer (48 * max_iter bytes) and makes every
- * following ircur_solve record, per iteration, the span from the first block
- * start to the last block end of its three kernels (core, core SVD, panel
- * passes) with the device's nanosecond clock; enable == 0 frees it.  The
- * spans are measured inside the CUDA graph, where host-side events cannot
- * be placed. */
+ * allocates a small device buffer (64 * max_iter bytes) and makes every
+ * following ircur_solve record, per iteration, four spans with the device's
+ * nanosecond clock, each to the last block's end of its kernel: Phase I on the
+ * core (the core SVD's prologue) and the whole core SVD, from its first block's
+ * start; the panel pass from its first block's start (its blocks start while
+ * the core SVD runs) and from its first block's return from the wait for the
+ * core SVD.  enable == 0 frees it.  The spans are measured inside the CUDA
+ * graph, where host-side events cannot be placed. */
 ircur_status ircur_set_trace(ircur_ctx* ctx, int32_t enable);
 
-/* Spans of the last traced solve: span_us[3 k + {0, 1, 2}] = microseconds of
- * the core, core-SVD and panel-pass kernels of iteration k (room for
- * 3 * max_iter doubles, host); *iters = K.  ESTATE without tracing or solve. */
+/* Spans of the last traced solve: span_us[4 k + {0, 1, 2, 3}] = microseconds
+ * of the core's Phase I, the core SVD, the panel pass and the panel pass after
+ * its wait, for iteration k (room for 4 * max_iter doubles, host); *iters = K.
+ * ESTATE without tracing or solve. */
 ircur_status ircur_get_trace(ircur_ctx* ctx, double* span_us, int32_t* iters);
 
 /* Allocation-free one-shot solve: ircur_create + ircur_solve +

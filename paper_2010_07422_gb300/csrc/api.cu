@@ -69,9 +69,13 @@ struct ircur_ctx {
   int64_t ldPr, ldPc, ldDT;
   float* A[2];
   float* B[2];
-  float* AI;
-  float* BJt;
-  float* core;
+  float* Dc[2];   // D(I,J) compact (nI x ldDc) and transposed (nJ x ldDcT); IRCUR-F uses [0] only
+  float* DcT[2];
+  int64_t ldDc, ldDcT;
+  unsigned* posI[2];  // index maps by draw parity (IRCUR-F: [0] only)
+  unsigned* posJ[2];
+  float* AI[2];       // compact A_k(I_k,:), B_k(:,J_k)^T by iteration parity
+  float* BJt[2];
   float* W;
   float* V;
   float* Vs;
@@ -89,7 +93,7 @@ struct ircur_ctx {
   unsigned long long* graph_trace;
   int graph_pass_grid;
   int graph_single;
-  unsigned long long* trace;  // kernel-span trace buffer (2 * 3 * max_iter), or null
+  unsigned long long* trace;  // kernel-span trace buffer (2 * kTraceSlots * max_iter), or null
   // last solve
   int solved;
   State host_state;
@@ -138,9 +142,7 @@ static ircur_status validate_params(const ircur_params* p, ircur_params* out) {
   if (q.precision == IRCUR_PRECISION_BF16_PANELS && q.resample != 0) return IRCUR_ENOTSUP;
   if (pass_smem_bytes(q.nI, q.nJ, pad_rank(q.r), nullptr, q.precision != 0) > 227 * 1024) return IRCUR_ENOTSUP;
   if (q.svd_form != IRCUR_SVD_CLUSTER && q.svd_form != IRCUR_SVD_ONE_CTA) return IRCUR_EINVAL;
-  if (!(q.svd_form == IRCUR_SVD_ONE_CTA && ssvd_fits(q.nI, q.nJ, pad_rank(q.r))) &&
-      csvd_smem_bytes(q.nI, q.nJ, pad_rank(q.r)) > 227 * 1024)
-    return IRCUR_ENOTSUP;
+  if (svd_cluster_size(q.nI, q.nJ, pad_rank(q.r), q.svd_form) == 0) return IRCUR_ENOTSUP;
   if (!(q.gamma > 0.0 && q.gamma < 1.0)) return IRCUR_EINVAL;
   if (!(q.tol > 0.0)) return IRCUR_EINVAL;
   if (q.max_iter < 1) return IRCUR_EINVAL;
@@ -176,7 +178,7 @@ static ircur_status create_impl(const ircur_params* params, void* stream, int mi
   // tile configuration of the pass kernel
   IterDesc& d = c->desc;
   memset(&d, 0, sizeof(d));
-  d.svdOneCta = (p.svd_form == IRCUR_SVD_ONE_CTA && ssvd_fits(p.nI, p.nJ, R)) ? 1 : 0;
+  d.svdNC = svd_cluster_size(p.nI, p.nJ, R, p.svd_form);
   d.nRowTiles = (int)((n2 + kPanelCols - 1) / kPanelCols);
   d.nColTiles = (int)((n1 + kPanelCols - 1) / kPanelCols);
 
@@ -194,11 +196,20 @@ static ircur_status create_impl(const ircur_params* params, void* stream, int mi
   const size_t oDT = p.resample ? take((size_t)n2 * c->ldDT * 4) : 0;
   const size_t oA0 = take((size_t)n1 * R * 4), oA1 = take((size_t)n1 * R * 4);
   const size_t oB0 = take((size_t)R * n2 * 4), oB1 = take((size_t)R * n2 * 4);
-  int ldCore = (p.nJ + 3) & ~3;
-  if (((ldCore / 4) & 1) == 0) ldCore += 4;
-  d.ldCore = ldCore;
-  const size_t oCore = take((size_t)p.nI * ldCore * 4);
-  const size_t oAI = take((size_t)p.nI * R * 4), oBJ = take((size_t)p.nJ * R * 4);
+  c->ldDc = (p.nJ + 3) & ~3ll;
+  c->ldDcT = (p.nI + 3) & ~3ll;
+  const int ncore = p.resample ? 2 : 1;
+  size_t oDc[2], oDcT[2], oPosI[2], oPosJ[2], oAIc[2], oBJc[2];
+  for (int q = 0; q < ncore; ++q) {
+    oDc[q] = take((size_t)p.nI * c->ldDc * 4);
+    oDcT[q] = take((size_t)p.nJ * c->ldDcT * 4);
+    oPosI[q] = take((size_t)n1 * 4);
+    oPosJ[q] = take((size_t)n2 * 4);
+  }
+  for (int q = 0; q < 2; ++q) {
+    oAIc[q] = take((size_t)p.nI * R * 4);
+    oBJc[q] = take((size_t)p.nJ * R * 4);
+  }
   const size_t oW = take((size_t)p.nI * R * 4), oV = take((size_t)p.nJ * R * 4), oVs = take((size_t)p.nJ * R * 4);
   const size_t oSig = take((size_t)R * 4);
   const size_t oTm = take((size_t)R * R * 4);
@@ -235,9 +246,14 @@ static ircur_status create_impl(const ircur_params* params, void* stream, int mi
   c->A[1] = reinterpret_cast<float*>(base + oA1);
   c->B[0] = reinterpret_cast<float*>(base + oB0);
   c->B[1] = reinterpret_cast<float*>(base + oB1);
-  c->core = reinterpret_cast<float*>(base + oCore);
-  c->AI = reinterpret_cast<float*>(base + oAI);
-  c->BJt = reinterpret_cast<float*>(base + oBJ);
+  for (int q = 0; q < 2; ++q) {
+    c->Dc[q] = reinterpret_cast<float*>(base + oDc[q < ncore ? q : 0]);
+    c->DcT[q] = reinterpret_cast<float*>(base + oDcT[q < ncore ? q : 0]);
+    c->posI[q] = reinterpret_cast<unsigned*>(base + oPosI[q < ncore ? q : 0]);
+    c->posJ[q] = reinterpret_cast<unsigned*>(base + oPosJ[q < ncore ? q : 0]);
+    c->AI[q] = reinterpret_cast<float*>(base + oAIc[q]);
+    c->BJt[q] = reinterpret_cast<float*>(base + oBJc[q]);
+  }
   c->W = reinterpret_cast<float*>(base + oW);
   c->V = reinterpret_cast<float*>(base + oV);
   c->Vs = reinterpret_cast<float*>(base + oVs);
@@ -280,9 +296,16 @@ static ircur_status create_impl(const ircur_params* params, void* stream, int mi
   d.A[1] = c->A[1];
   d.B[0] = c->B[0];
   d.B[1] = c->B[1];
-  d.core = c->core;
-  d.AI = c->AI;
-  d.BJt = c->BJt;
+  for (int q = 0; q < 2; ++q) {
+    d.Dc[q] = c->Dc[q];
+    d.DcT[q] = c->DcT[q];
+    d.posI[q] = c->posI[q];
+    d.posJ[q] = c->posJ[q];
+    d.AI[q] = c->AI[q];
+    d.BJt[q] = c->BJt[q];
+  }
+  d.ldDc = c->ldDc;
+  d.ldDcT = c->ldDcT;
   d.W = c->W;
   d.V = c->V;
   d.Vs = c->Vs;
@@ -403,21 +426,36 @@ static ircur_status solve_prologue(ircur_ctx* c, const float* D, int64_t ldD, co
   c->desc = d;
   c->solved = 0;
   if (c->trace) {
-    const size_t half = (size_t)3 * p.max_iter * 8;
+    const size_t half = (size_t)kTraceSlots * p.max_iter * 8;
     IRCUR_CK(cudaMemsetAsync(c->trace, 0xFF, half, s));
     IRCUR_CK(cudaMemsetAsync(reinterpret_cast<char*>(c->trace) + half, 0, half, s));
   }
 
   const double zeta0 = p.zeta0 > 0 ? p.zeta0 : 0.0;
   IRCUR_CK(launch_setup(d, zeta0, s));
+  // index maps start empty; A_0 = B_0 = 0, so A_0(I,:) and B_0(:,J) too
+  const int nmap = p.resample ? 2 : 1;
+  for (int q = 0; q < nmap; ++q) {
+    IRCUR_CK(cudaMemsetAsync(c->posI[q], 0, (size_t)p.n1 * 4, s));
+    IRCUR_CK(cudaMemsetAsync(c->posJ[q], 0, (size_t)p.n2 * 4, s));
+  }
+  IRCUR_CK(cudaMemsetAsync(c->AI[0], 0, (size_t)p.nI * c->Rpad * 4, s));
+  IRCUR_CK(cudaMemsetAsync(c->BJt[0], 0, (size_t)p.nJ * c->Rpad * 4, s));
+  // the first draws (IRCUR-R: 0 and 1, the core SVD of iteration k draws
+  // k + 2) and their maps
+  const int first_draws = p.resample ? (p.max_iter < 2 ? p.max_iter : 2) : 1;
   if (idx_I) {
     IRCUR_CK(cudaMemcpyAsync(c->I_all, idx_I, (size_t)c->draws * p.nI * 4, cudaMemcpyDeviceToDevice, s));
     IRCUR_CK(cudaMemcpyAsync(c->J_all, idx_J, (size_t)c->draws * p.nJ * 4, cudaMemcpyDeviceToDevice, s));
     IRCUR_CK(launch_check_indices(c->I_all, c->draws, p.nI, p.n1, &c->st->status, s));
     IRCUR_CK(launch_check_indices(c->J_all, c->draws, p.nJ, p.n2, &c->st->status, s));
+    for (int q = 0; q < first_draws; ++q) {
+      IRCUR_CK(launch_index_map(c->I_all + (size_t)q * p.nI, p.nI, c->posI[q & 1], q, c->st, s));
+      IRCUR_CK(launch_index_map(c->J_all + (size_t)q * p.nJ, p.nJ, c->posJ[q & 1], q, c->st, s));
+    }
   } else {
-    // draw 0 now; IRCUR-R draws k+1 alongside iteration k's core SVD
-    IRCUR_CK(launch_sample(p.seed, 0, 1, p.n1, p.n2, p.nI, p.nJ, c->I_all, c->J_all, -1, s));
+    IRCUR_CK(launch_sample(p.seed, 0, first_draws, p.n1, p.n2, p.nI, p.nJ, c->I_all, c->J_all, -1, s, c->posI,
+                           c->posJ));
   }
   if (p.resample) {
     // D^T for the column panels, with max|D| and the NaN/Inf scan in the same pass
@@ -427,6 +465,8 @@ static ircur_status solve_prologue(ircur_ctx* c, const float* D, int64_t ldD, co
   }
   if (!(p.zeta0 > 0)) IRCUR_CK(launch_finalize_zeta(c->st, s));
   if (!p.resample) IRCUR_CK(launch_gather(d, s));
+  // D(I,J) of the first iteration (IRCUR-F: of every iteration) for the core SVD
+  IRCUR_CK(launch_gather_core(d, 0, 0, s));
   IRCUR_CK(cudaMemsetAsync(c->A[0], 0, (size_t)p.n1 * c->Rpad * 4, s));
   IRCUR_CK(cudaMemsetAsync(c->B[0], 0, (size_t)c->Rpad * p.n2 * 4, s));
   return IRCUR_OK;
@@ -865,7 +905,7 @@ extern "C" ircur_status ircur_sample_indices(uint64_t seed, int32_t draw, int32_
 extern "C" ircur_status ircur_set_trace(ircur_ctx* c, int32_t enable) {
   if (!c) return IRCUR_EINVAL;
   if (enable && !c->trace) {
-    cudaError_t e = cudaMalloc(&c->trace, (size_t)2 * 3 * c->p.max_iter * 8);
+    cudaError_t e = cudaMalloc(&c->trace, (size_t)2 * kTraceSlots * c->p.max_iter * 8);
     if (e != cudaSuccess) {
       set_error("cudaMalloc(trace)", e);
       cudaGetLastError();
@@ -883,7 +923,7 @@ extern "C" ircur_status ircur_set_trace(ircur_ctx* c, int32_t enable) {
 extern "C" ircur_status ircur_get_trace(ircur_ctx* c, double* span_us, int32_t* iters) {
   if (!c || !span_us || !iters) return IRCUR_EINVAL;
   if (!c->trace || !c->solved) return IRCUR_ESTATE;
-  const int n = 3 * c->p.max_iter;
+  const int n = kTraceSlots * c->p.max_iter;
   unsigned long long* h = new (std::nothrow) unsigned long long[2 * (size_t)n];
   if (!h) return IRCUR_ENOMEM;
   cudaError_t e = cudaMemcpyAsync(h, c->trace, (size_t)2 * n * 8, cudaMemcpyDeviceToHost, c->stream);
@@ -894,7 +934,7 @@ extern "C" ircur_status ircur_get_trace(ircur_ctx* c, double* span_us, int32_t* 
     return IRCUR_ECUDA;
   }
   const int K = c->host_state.k;
-  for (int q = 0; q < 3 * K; ++q)
+  for (int q = 0; q < kTraceSlots * K; ++q)
     span_us[q] = (h[n + q] >= h[q] && h[q] != ~0ull) ? (double)(h[n + q] - h[q]) * 1e-3 : 0.0;
   *iters = K;
   delete[] h;
@@ -1041,7 +1081,7 @@ extern "C" ircur_status ircur_batch_create(const ircur_params* params, int32_t c
   const size_t oFlag = (oList + (size_t)count * 4 + 255) & ~(size_t)255;
   const size_t bytes = oFlag + 256;
   std::unique_ptr<int[]> tiles(new int[count + b->ngroups]);
-  // per group: the instances whose core SVD runs on one CTA, then those on a cluster
+  // per group: the instances by the cluster size of their core SVD
   std::unique_ptr<int[]> lists(new int[count]);
   cudaError_t e = cudaMalloc(&b->dws, bytes);
   if (e != cudaSuccess) {
@@ -1061,23 +1101,23 @@ extern "C" ircur_status ircur_batch_create(const ircur_params* params, int32_t c
     bl.ds = b->ds + first;
     int* tb = tiles.get() + first + g;
     tb[0] = 0;
-    int maxNI = 1, roles = 1, nOne = 0, nCl = 0;
-    for (int q = 0; q < n; ++q)
-      if (b->inst[b->order[first + q]]->desc.svdOneCta) ++nOne;
+    int roles = 1;
+    // instances by core-SVD cluster size (1, 8, 16), in group order within each
+    int nf[3] = {0, 0, 0};
+    auto form_of = [](int nc) { return nc == 1 ? 0 : (nc == kSvdCluster ? 1 : 2); };
+    for (int q = 0; q < n; ++q) ++nf[form_of(b->inst[b->order[first + q]]->desc.svdNC)];
+    int fill[3] = {0, nf[0], nf[0] + nf[1]};
     for (int q = 0; q < n; ++q) {
       const ircur_ctx* c = b->inst[b->order[first + q]];
       const ircur_params& p = c->p;
-      const bool one = c->desc.svdOneCta != 0;
-      const size_t ss = one ? ssvd_smem_bytes(p.nI, p.nJ, R) : csvd_smem_bytes(p.nI, p.nJ, R);
+      const int f = form_of(c->desc.svdNC);
+      const size_t ss = svd_smem_bytes(p.nI, p.nJ, R, c->desc.svdNC);
       if (pass_smem_bytes(p.nI, p.nJ, R) > 227 * 1024 || ss > 227 * 1024) {
         ircur_batch_destroy(b);
         return IRCUR_ENOTSUP;
       }
-      if (ss > bl.svd_smem[one ? 0 : 1]) bl.svd_smem[one ? 0 : 1] = ss;
-      if (one)
-        lists[first + (q - nCl)] = q;  // group-relative instance indices
-      else
-        lists[first + nOne + nCl++] = q;
+      if (ss > bl.svd_smem[f]) bl.svd_smem[f] = ss;
+      lists[first + fill[f]++] = q;  // group-relative instance indices
       if (p.nI > bl.pass_mmax) bl.pass_mmax = p.nI;
       if (p.nJ > bl.pass_mmax) bl.pass_mmax = p.nJ;
       const int64_t t = (int64_t)tb[q] + c->desc.nRowTiles + c->desc.nColTiles;
@@ -1086,21 +1126,16 @@ extern "C" ircur_status ircur_batch_create(const ircur_params* params, int32_t c
         return IRCUR_ENOTSUP;
       }
       tb[q + 1] = (int)t;
-      if (p.nI > maxNI) maxNI = p.nI;
       if (p.resample) roles = 3;
       if (p.max_iter > b->max_iter) b->max_iter = p.max_iter;
     }
     bl.tile_base = reinterpret_cast<const int*>(base + oTiles) + first + g;
     bl.total_tiles = tb[n];
     bl.pass_smem = pass_smem_bytes(bl.pass_mmax, bl.pass_mmax, R, &bl.pass_nbuf);
-    {
-      const int want = (4 * kNumSMsHint + n - 1) / n;
-      bl.core_blocks = want < maxNI ? (want > 0 ? want : 1) : maxNI;
-    }
     bl.svd_list[0] = reinterpret_cast<const int*>(base + oList) + first;
-    bl.svd_list[1] = bl.svd_list[0] + nOne;
-    bl.svd_n[0] = nOne;
-    bl.svd_n[1] = n - nOne;
+    bl.svd_list[1] = bl.svd_list[0] + nf[0];
+    bl.svd_list[2] = bl.svd_list[1] + nf[1];
+    for (int f = 0; f < 3; ++f) bl.svd_n[f] = nf[f];
     bl.svd_roles = roles;
     bl.cond = 0;
     bl.any_active = b->any_active;
@@ -1354,7 +1389,7 @@ extern "C" ircur_status ircur_autotune(ircur_ctx* c, const float* D, int64_t ldD
   probe.passSingleBuf = 1;
   const int res1 = pass_resident_blocks(probe, c->Rpad);
   TuneCand cand[IRCUR_TUNE_MAX];
-  const int nc = tune_candidates(total, res2, res1, sms, c->desc.svdOneCta ? 1 : kSvdCluster, cand);
+  const int nc = tune_candidates(total, res2, res1, sms, c->desc.svdNC, cand);
   cudaEvent_t e0, e1;
   IRCUR_CK(cudaEventCreate(&e0));
   IRCUR_CK(cudaEventCreate(&e1));

@@ -31,7 +31,6 @@ constexpr int64_t kNaMaxN = 2048;
 constexpr int kNaMaxM = 192;
 constexpr int kNaMaxR = 8;  // padded rank
 constexpr int kNaMaxIter = 256;
-constexpr int kNaMaxLdCore = 196;  // largest ldCore for |J| <= 192 (rounded up to 4, ld/4 odd)
 
 constexpr size_t na_piece(size_t bytes) { return (bytes + 255) & ~(size_t)255; }
 
@@ -40,8 +39,9 @@ constexpr size_t kNaBytes =
     na_piece((size_t)kNaMaxM * kNaMaxN * 4) +                            // D(I,:)
     na_piece((size_t)kNaMaxM * kNaMaxN * 4) +                            // D(:,J)^T
     4 * na_piece((size_t)kNaMaxN * kNaMaxR * 4) +                        // A[2], B[2]
-    2 * na_piece((size_t)kNaMaxM * kNaMaxR * 4) +                        // A(I,:), B(:,J)^T
-    na_piece((size_t)kNaMaxM * kNaMaxLdCore * 4) +                       // core
+    2 * na_piece((size_t)kNaMaxM * kNaMaxM * 4) +                        // D(I,J), D(I,J)^T
+    2 * na_piece((size_t)kNaMaxN * 4) +                                  // index maps
+    4 * na_piece((size_t)kNaMaxM * kNaMaxR * 4) +                        // A_k(I,:), B_k(:,J)^T by parity
     3 * na_piece((size_t)kNaMaxM * kNaMaxR * 4) +                        // W, V, Vs
     na_piece((size_t)kNaMaxR * 4) + na_piece((size_t)kNaMaxR * kNaMaxR * 4) +  // sigma, T
     na_piece((size_t)((kNaMaxN + kPanelCols - 1) / kPanelCols * 2) * 2 * 8) +  // partials
@@ -100,11 +100,11 @@ extern "C" ircur_status ircur_solve_noalloc(const ircur_params* params, const fl
 
   const int R = pad_rank(p.r);
   const int64_t n1 = p.n1, n2 = p.n2;
-  int ldCore = (p.nJ + 3) & ~3;
-  if (((ldCore / 4) & 1) == 0) ldCore += 4;
+  const int64_t ldDc = (p.nJ + 3) & ~3ll, ldDcT = (p.nI + 3) & ~3ll;
   IterDesc d;
   memset(&d, 0, sizeof(d));
-  d.svdOneCta = (p.svd_form == IRCUR_SVD_ONE_CTA && ssvd_fits(p.nI, p.nJ, pad_rank(p.r))) ? 1 : 0;
+  d.svdNC = svd_cluster_size(p.nI, p.nJ, R, p.svd_form);
+  if (d.svdNC == 0) return IRCUR_EINVAL;
   d.nRowTiles = (int)((n2 + kPanelCols - 1) / kPanelCols);
   d.nColTiles = (int)((n1 + kPanelCols - 1) / kPanelCols);
   const int64_t ldPr = (n2 + 3) & ~3ll, ldPc = (n1 + 3) & ~3ll;
@@ -124,9 +124,16 @@ extern "C" ircur_status ircur_solve_noalloc(const ircur_params* params, const fl
   Ab[1] = reinterpret_cast<float*>(take((size_t)n1 * R * 4));
   Bb[0] = reinterpret_cast<float*>(take((size_t)R * n2 * 4));
   Bb[1] = reinterpret_cast<float*>(take((size_t)R * n2 * 4));
-  float* AI = reinterpret_cast<float*>(take((size_t)p.nI * R * 4));
-  float* BJt = reinterpret_cast<float*>(take((size_t)p.nJ * R * 4));
-  float* core = reinterpret_cast<float*>(take((size_t)p.nI * ldCore * 4));
+  float* Dc = reinterpret_cast<float*>(take((size_t)p.nI * ldDc * 4));
+  float* DcT = reinterpret_cast<float*>(take((size_t)p.nJ * ldDcT * 4));
+  unsigned* posI = reinterpret_cast<unsigned*>(take((size_t)n1 * 4));
+  unsigned* posJ = reinterpret_cast<unsigned*>(take((size_t)n2 * 4));
+  float* AIc[2];
+  float* BJc[2];
+  for (int q = 0; q < 2; ++q) {
+    AIc[q] = reinterpret_cast<float*>(take((size_t)p.nI * R * 4));
+    BJc[q] = reinterpret_cast<float*>(take((size_t)p.nJ * R * 4));
+  }
   float* W = reinterpret_cast<float*>(take((size_t)p.nI * R * 4));
   float* V = reinterpret_cast<float*>(take((size_t)p.nJ * R * 4));
   float* Vs = reinterpret_cast<float*>(take((size_t)p.nJ * R * 4));
@@ -162,10 +169,16 @@ extern "C" ircur_status ircur_solve_noalloc(const ircur_params* params, const fl
   d.A[1] = Ab[1];
   d.B[0] = Bb[0];
   d.B[1] = Bb[1];
-  d.AI = AI;
-  d.BJt = BJt;
-  d.core = core;
-  d.ldCore = ldCore;
+  d.Dc[0] = d.Dc[1] = Dc;
+  d.DcT[0] = d.DcT[1] = DcT;
+  d.posI[0] = d.posI[1] = posI;
+  d.posJ[0] = d.posJ[1] = posJ;
+  for (int q = 0; q < 2; ++q) {
+    d.AI[q] = AIc[q];
+    d.BJt[q] = BJc[q];
+  }
+  d.ldDc = ldDc;
+  d.ldDcT = ldDcT;
   d.W = W;
   d.V = V;
   d.Vs = Vs;
@@ -191,12 +204,15 @@ extern "C" ircur_status ircur_solve_noalloc(const ircur_params* params, const fl
   // the core's padding columns, the state's counters)
   NA_CK(cudaMemsetAsync(ws, 0, off, s));
   NA_CK(launch_setup(d, p.zeta0 > 0 ? p.zeta0 : 0.0, s));
-  NA_CK(launch_sample(p.seed, 0, 1, n1, n2, p.nI, p.nJ, I, J, -1, s));
+  unsigned* maps_I[2] = {posI, posI};
+  unsigned* maps_J[2] = {posJ, posJ};
+  NA_CK(launch_sample(p.seed, 0, 1, n1, n2, p.nI, p.nJ, I, J, -1, s, maps_I, maps_J));
   if (!(p.zeta0 > 0)) {
     NA_CK(launch_maxabs(D, n1, n2, ldD, st, s));
     NA_CK(launch_finalize_zeta(st, s));
   }
   NA_CK(launch_gather(d, s));
+  NA_CK(launch_gather_core(d, 0, 0, s));
   State h;
   memset(&h, 0, sizeof(h));
   for (int it = 0; it < p.max_iter; ++it) {

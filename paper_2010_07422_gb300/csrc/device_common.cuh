@@ -16,6 +16,13 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   return z ^ (z >> 31);
 }
 
+// Index maps: entry i of a map holds index_tag(tag, a) when i is the a-th
+// member of the index set of draw tag - 1 (positions below 2^9, draws below
+// 2^23 - 1); entries of other draws carry other tags, 0 is no draw.
+__host__ __device__ __forceinline__ unsigned index_tag(unsigned tag, int a) { return (tag << 9) | (unsigned)a; }
+__host__ __device__ __forceinline__ bool index_tag_is(unsigned e, unsigned tag) { return (e >> 9) == tag; }
+__host__ __device__ __forceinline__ int index_tag_pos(unsigned e) { return (int)(e & 511u); }
+
 // The low-rank estimate at one entry, L_k(i,j) = A_k(i,:) B_k(:,j), as an FMA
 // chain in the fixed order t = 0..R-1.  Every kernel that evaluates L_k at an
 // entry of the (I,J) block uses this function, so the core, the row panel and

@@ -25,6 +25,12 @@ constexpr long long kSpinLimit = 1ll << 26;
 #endif
 constexpr int kGraphUnroll = IRCUR_GRAPH_UNROLL;
 
+// Kernel-span trace slots per iteration (ircur_set_trace): 0 Phase I on the
+// core (the core SVD's prologue), 1 the core SVD, 2 the panel pass from its
+// first block's start, 3 the panel pass from the first return of its wait for
+// the core SVD; each to the last block's end.
+constexpr int kTraceSlots = 4;
+
 // Panel-pass tiling: a tile is kPanelCols consecutive panel columns; a block
 // of kPassWarps warps computes one tile at a time, warp h owning row share h
 // and lane c column c.  Each tile leaves its (num, den) partial sums in
@@ -87,10 +93,23 @@ struct IterDesc {
   const int* J_all;     // (resample ? max_iter : 1) x nJ
   float* A[2];          // n1 x R row-major (R = padded rank of the kernels)
   float* B[2];          // R x n2 row-major
-  float* AI;            // nI x R    A_k(I,:) gathered by the core kernel
-  float* BJt;           // nJ x R    B_k(:,J)^T gathered by the core kernel
-  float* core;          // nI x ldCore, row-major (columns nJ..ldCore-1 stay zero)
-  int ldCore;           // nJ rounded up to 4, with ldCore/4 odd (conflict-free 16-byte rows)
+  // D(I,J) of an iteration, compact (nI x ldDc) and transposed (nJ x ldDcT),
+  // the core SVD's Phase I input.  IRCUR-F: [0] only, gathered once.  IRCUR-R:
+  // iteration k reads [k & 1]; the panel pass of iteration k gathers
+  // D(I_{k+1}, J_{k+1}) into [(k + 1) & 1] (the solve's prologue gathers k = 0).
+  // Padding columns stay zero.
+  float* Dc[2];
+  float* DcT[2];
+  int64_t ldDc, ldDcT;  // nJ and nI rounded up to 4
+  // Index maps of the draws (k & 1 for IRCUR-R, [0] for IRCUR-F; n1 and n2
+  // entries, see index_tag) and the compact side matrices of iteration k,
+  // AI[k & 1] = A_k(I_k,:) (nI x R) and BJt[k & 1] = B_k(:,J_k)^T (nJ x R),
+  // written through the maps by the panel pass of iteration k - 1 (zero at
+  // k = 0) and read by the core SVD and the pass of iteration k.
+  unsigned* posI[2];
+  unsigned* posJ[2];
+  float* AI[2];
+  float* BJt[2];
   float* W;             // nI x R   Y: orthonormal basis of the core's dominant left subspace
   float* V;             // nJ x R   X T^T (column-pass reconstruction)
   float* Vs;            // nJ x R   X T^{-1} (column-pass projection; zero for dropped directions)
@@ -103,7 +122,7 @@ struct IterDesc {
   int rowBulk, colBulk; // 1: panel rows are 16-byte aligned (tiles via 16-byte async copies)
   int svdMaxSteps;
   int sampleAhead;      // 1: the core-SVD launch draws the next iteration's I, J (IRCUR-R, own sampler)
-  int svdOneCta;        // 1: the core SVD runs on one CTA (ssvd_kernel), else on a cluster
+  int svdNC;            // CTAs of the core SVD's cluster: 1 (one CTA), 8 or 16
   int passGrid;         // pass-kernel blocks (0: every block that fits the GPU at once), from the autotuner
   int passSingleBuf;    // 1: one tile buffer per block (no prefetch, less shared memory)
   long long spinLimit;      // first bounded wait on a bulk copy (kSpinLimit unless a fault is injected)
@@ -119,10 +138,9 @@ struct BatchLaunch {
   int count;
   const int* tile_base;    // device, count + 1 prefix sums of panel tiles
   int total_tiles;
-  int core_blocks;         // blocks per instance of the core kernel
-  const int* svd_list[2];  // device instance lists: [0] core in shared memory, [1] core in global memory
-  int svd_n[2];
-  size_t svd_smem[2];
+  const int* svd_list[3];  // device instance lists by core-SVD cluster size: [0] 1 CTA, [1] 8, [2] 16
+  int svd_n[3];
+  size_t svd_smem[3];
   int svd_roles;           // 1, or 3 when some instance draws its next index sets
   size_t pass_smem;
   int pass_mmax;           // largest |I|, |J| of the batch (shared-memory layout)
@@ -178,8 +196,12 @@ struct AdjStep {
 };
 
 // Launch wrappers (return cudaGetLastError()).
+// draws draw0 .. draw0 + draws - 1; with maps (two per axis, by draw parity)
+// each draw also writes its index map
 cudaError_t launch_sample(uint64_t seed, int draw0, int draws, int64_t n1, int64_t n2, int nI, int nJ,
-                          int* I_all, int* J_all, int only_axis, cudaStream_t s);
+                          int* I_all, int* J_all, int only_axis, cudaStream_t s, unsigned* const* mapI = nullptr,
+                          unsigned* const* mapJ = nullptr);
+cudaError_t launch_index_map(const int* idx, int m, unsigned* map, int draw, const State* st, cudaStream_t s);
 cudaError_t launch_check_indices(const int* idx, int sets, int m, int64_t n, int* status,
                                  cudaStream_t s);
 cudaError_t launch_maxabs(const float* D, int64_t n1, int64_t n2, int64_t ldD, State* st,
@@ -201,7 +223,6 @@ cudaError_t launch_batch_group(const BatchLaunch& b, int Rpad, cudaStream_t s);
 cudaError_t launch_batch_check(const IterDesc* ds, int count, unsigned long long cond, int* any_active,
                                cudaStream_t s);
 cudaError_t launch_svd_batch(const BatchLaunch& b, int Rpad, cudaStream_t s);
-cudaError_t launch_sigma(const float* Tm, int r, int Rpad, float* sigma, cudaStream_t s);
 cudaError_t launch_stream(const float* A, const int* I, const float* Y, int m, int Rpad, int64_t n1, const float* Dn,
                           int64_t ldDn, int64_t ncols, int iters, double zeta0, double gamma, float zetaT, float* bq,
                           float* L, int64_t ldL, float* S, int64_t ldS, cudaStream_t s);
@@ -217,12 +238,16 @@ size_t pass_smem_bytes(int nI, int nJ, int Rpad, int* nbuf = nullptr, bool bf16 
 size_t cur_to_svd_scratch_bytes(int64_t n1, int64_t n2, int Rpad);
 cudaError_t launch_cur_to_svd(const float* A, const float* B, int64_t n1, int64_t n2, int r, int Rpad, void* scratch,
                               float* W, float* sigma, float* V, cudaStream_t s);
-// Shared memory per CTA of the cluster core SVD.
-size_t csvd_smem_bytes(int nI, int nJ, int Rpad);
-// One-CTA core SVD (R <= 8, the core in one SM's shared memory): its dynamic
-// shared memory, and whether it can run this shape.
-size_t ssvd_smem_bytes(int nI, int nJ, int Rpad);
-bool ssvd_fits(int nI, int nJ, int Rpad);
+// Core SVD (k_svd.cu): dynamic shared memory per CTA for a cluster of nc CTAs,
+// whether it fits one SM, and the cluster size a problem runs with (1 for the
+// one-CTA form where it fits, else 8 or 16; 0 if no form fits).
+size_t svd_smem_bytes(int nI, int nJ, int Rpad, int nc);
+bool svd_fits(int nI, int nJ, int Rpad, int nc);
+int svd_cluster_size(int nI, int nJ, int Rpad, int svd_form);
+// Singular values of the last core from its T (k_svd.cu), on request.
+cudaError_t launch_sigma(const float* Tm, int r, int Rpad, float* sigma, cudaStream_t s);
+// D(I,J) of draw `draw` into the compact buffers [buf] (k_setup.cu).
+cudaError_t launch_gather_core(const IterDesc& d, int draw, int buf, cudaStream_t s);
 // Blocks of the pass kernel that are resident on the whole GPU at once.
 int pass_resident_blocks(const IterDesc& d, int Rpad);
 int pass_batch_resident_blocks(const BatchLaunch& b, int Rpad);

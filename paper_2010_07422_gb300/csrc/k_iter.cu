@@ -1,6 +1,6 @@
-// One IRCUR iteration (Alg. 1) on the GPU, in three kernels:
-//   core_kernel  -- [D - S_{k+1}]_{I,J}: Phase I on the |I| x |J| block,
-//   svd_kernel   -- H_r of the core and its pseudo-inverse (k_svd.cu),
+// One IRCUR iteration (Alg. 1) on the GPU, in two kernels:
+//   svd_kernel   -- [D - S_{k+1}]_{I,J} (Phase I on the |I| x |J| block), H_r
+//                   of that core and its pseudo-inverse (k_svd.cu),
 //   pass_kernel  -- the fused row- and column-panel passes and the stopping
 //                   criterion.
 //
@@ -27,59 +27,6 @@ int pad_rank(int r) {
   if (r <= 10) return r;
   if (r <= 12) return 12;
   return 16;
-}
-
-// ---------------------------------------------------------------------------
-template <int R>
-__device__ __forceinline__ void core_body(const IterDesc& d, int blk, int nblk) {
-  const State* st = d.st;
-  if (st->done || st->status) return;
-  const int k = st->k;
-  const float zeta = (float)st->zeta;
-  const int cur = k & 1;
-  const int* I = d.I_all + (d.resample ? (int64_t)k * d.nI : 0);
-  const int* J = d.J_all + (d.resample ? (int64_t)k * d.nJ : 0);
-  const float* A = d.A[cur];
-  const float* B = d.B[cur];
-  trace_start(d.trace, 3 * k + 0);
-  for (int a = blk; a < d.nI; a += nblk) {
-    const int ia = I[a];
-    float arow[R];
-#pragma unroll
-    for (int t = 0; t < R; ++t) arow[t] = A[(int64_t)ia * R + t];
-    if (threadIdx.x < R) d.AI[(size_t)a * R + threadIdx.x] = A[(int64_t)ia * R + threadIdx.x];
-    const float* rowp = d.bf16 ? nullptr : d.rowSrc + (int64_t)(d.resample ? ia : a) * d.rowLd;
-    const uint16_t* rowh = d.bf16 ? d.rowSrcH + (int64_t)a * d.rowLd : nullptr;
-    for (int b = threadIdx.x; b < d.nJ; b += blockDim.x) {
-      const int j = J[b];
-      float bcol[R];
-#pragma unroll
-      for (int t = 0; t < R; ++t) bcol[t] = B[(int64_t)t * d.n2 + j];
-      if (a == 0) {
-#pragma unroll
-        for (int t = 0; t < R; ++t) d.BJt[(size_t)b * R + t] = bcol[t];
-      }
-      const float l = lowrank_entry<R>(arow, bcol);
-      const float dv = d.bf16 ? bf16_entry(rowh[j], l, zeta, [&]() { return d.D[(int64_t)ia * d.ldD + j]; })
-                              : rowp[j];
-      d.core[(int64_t)a * d.ldCore + b] = panel_value(dv, l, zeta);
-    }
-  }
-  if (d.trace) {
-    __syncthreads();
-    trace_stop(d.trace, 3 * d.max_iter, 3 * k + 0);
-  }
-}
-
-template <int R>
-__global__ void __launch_bounds__(256) core_kernel(IterDesc d) {
-  core_body<R>(d, blockIdx.x, gridDim.x);
-}
-
-// Batched form: blockIdx.y selects the instance.
-template <int R>
-__global__ void __launch_bounds__(256) core_batch_kernel(const IterDesc* __restrict__ ds) {
-  core_body<R>(ds[blockIdx.y], blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -234,16 +181,37 @@ __device__ __forceinline__ void pass_stage_tile(const IterDesc& d, int k, int lt
   }
 }
 
-// The m x R side matrix of one segment (A_k(I,:) | B_k(:,J)^T: outputs of the
-// core kernel), rows padded to RX columns with zeros.
+// The m x R side matrix of one segment, A_k(I,:) | B_k(:,J)^T: the compact
+// copies the previous pass wrote through the index maps (the same values the
+// core SVD used for L_k(I,J)), rows padded to RX columns with zeros.
 template <int R, bool COL>
-__device__ __forceinline__ void pass_stage_side(const IterDesc& d, const PassLayout& L) {
+__device__ __forceinline__ void pass_stage_side(const IterDesc& d, const PassLayout& L, int k) {
   constexpr int RX = (R + 3) & ~3;
   const int m = COL ? d.nJ : d.nI;
-  const float* sideG = COL ? d.BJt : d.AI;
+  const float* sideG = COL ? d.BJt[k & 1] : d.AI[k & 1];
   for (int q = threadIdx.x; q < m * RX; q += blockDim.x) {
     const int a = q / RX, t = q - a * RX;
-    L.side[q] = t < R ? sideG[a * R + t] : 0.f;
+    L.side[q] = t < R ? sideG[(size_t)a * R + t] : 0.f;
+  }
+}
+
+// IRCUR-R: the core SVD of iteration k + 1 reads D(I_{k+1}, J_{k+1}) from the
+// compact buffers [(k + 1) & 1].  Row tile lt of iteration k gathers the core
+// rows a = lt, lt + nRowTiles, ... of it before its blocks wait for the core
+// SVD (the index sets of k + 1 were drawn an iteration earlier).
+__device__ __forceinline__ void pass_gather_next_core(const IterDesc& d, int k, int lt) {
+  if (!d.resample || k + 1 >= d.max_iter || lt >= d.nI) return;
+  const int rows = (d.nI - 1 - lt) / d.nRowTiles + 1;
+  const int total = rows * d.nJ;
+  const int* In = d.I_all + (int64_t)(k + 1) * d.nI;
+  const int* Jn = d.J_all + (int64_t)(k + 1) * d.nJ;
+  const int nb = (k + 1) & 1;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int ra = e / d.nJ, b = e - ra * d.nJ;
+    const int a = lt + ra * d.nRowTiles;
+    const float v = __ldcs(d.D + (int64_t)__ldg(In + a) * d.ldD + __ldg(Jn + b));
+    d.Dc[nb][(int64_t)a * d.ldDc + b] = v;
+    d.DcT[nb][(int64_t)b * d.ldDcT + a] = v;
   }
 }
 
@@ -253,7 +221,7 @@ template <int R, bool COL>
 __device__ __forceinline__ void pass_stage_proj(const IterDesc& d, const PassLayout& L, int k) {
   constexpr int RX = (R + 3) & ~3;
   pdl_wait();
-  trace_start(d.trace, 3 * k + 2);  // the pass's span starts where it no longer waits for the SVD
+  trace_start(d.trace, kTraceSlots * k + 3);  // the span after the wait for the SVD
   const int m = COL ? d.nJ : d.nI;
   const float* projG = COL ? d.Vs : d.W;
   for (int q = threadIdx.x; q < m * RX; q += blockDim.x) {
@@ -338,6 +306,12 @@ __device__ __forceinline__ void pass_tile_project(const IterDesc& d, int k, int 
   const float* recon = COL ? L.recon : L.proj;
   const float msk = live ? 1.f : 0.f;
   const int a0 = h * m / kPassWarps, a1 = (h + 1) * m / kPassWarps;
+  // the next iteration's index map entry of this lane's row (column), loaded
+  // before the projections so that its latency overlaps them
+  const int dnext = d.resample ? k + 1 : 0;
+  const unsigned tag_next = (unsigned)(dnext + 1);
+  unsigned pos_next = 0u;
+  if (h == 0 && live) pos_next = __ldcg((COL ? d.posI : d.posJ)[dnext & 1] + j);
   if (COL) {
     if (stage_proj) pass_stage_proj<R, true>(d, L, k);
   } else {
@@ -402,6 +376,14 @@ __device__ __forceinline__ void pass_tile_project(const IterDesc& d, int k, int 
       float* Bn = d.B[nxt];
 #pragma unroll
       for (int t = 0; t < R; ++t) Bn[(int64_t)t * d.n2 + j] = out[t];
+    }
+    // rows (columns) in the next iteration's index set also go to its compact
+    // side matrix, at their position in the set
+    if (index_tag_is(pos_next, tag_next)) {
+      float* side = COL ? d.AI[nxt] : d.BJt[nxt];
+      const int a = index_tag_pos(pos_next);
+#pragma unroll
+      for (int t = 0; t < R; ++t) side[(size_t)a * R + t] = out[t];
     }
   }
   // this share's sums; the tile's slot gets them in share order after the
@@ -507,6 +489,9 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
     }
     return;
   }
+  // the iteration, read before any block can finalize it (kernel-span trace)
+  const int k_trace = BATCH ? 0 : d1.st->k;
+  if (!BATCH) trace_start(d1.trace, kTraceSlots * k_trace + 2);
   // contiguous runs, the longer ones on the lowest block indices (the blocks
   // launched last, which may start only once the SVD has left its SMs, get
   // the shorter runs)
@@ -549,6 +534,15 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
       pass_stage_tile<false, BF>(d, ref.k, ref.lt, buf);
   };
   __shared__ int is_last;
+  // IRCUR-R: this block's share of the next iteration's D(I,J), while the core
+  // SVD runs (row tiles only)
+  {
+    int gin = inst;
+    for (int t = t0; t < t1; ++t) {
+      const TileRef ref = locate(t, gin);
+      if (ref.active && !ref.col) pass_gather_next_core(BATCH ? ds[ref.inst] : d1, ref.k, ref.lt);
+    }
+  }
   int pin = inst;  // instance cursor of the prefetch
   TileRef cur = locate(t0, inst);
   if (cur.active) stage(cur, L.tiles);
@@ -567,7 +561,6 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
       const IterDesc& dp = BATCH ? ds[seg_inst] : d1;
       __threadfence();
       __syncthreads();
-      trace_stop(dp.trace, 3 * dp.max_iter, 3 * seg_k + 2);
       if (threadIdx.x == 0)
         is_last = (atomicAdd(&dp.st->counter, (unsigned)run) + (unsigned)run ==
                    (unsigned)(dp.nRowTiles + dp.nColTiles));
@@ -604,9 +597,9 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
       seg_k = cur.k;
       zeta = (float)d.st->zeta;
       if (cur.col)
-        pass_stage_side<R, true>(d, L);
+        pass_stage_side<R, true>(d, L, seg_k);
       else
-        pass_stage_side<R, false>(d, L);
+        pass_stage_side<R, false>(d, L, seg_k);
       proj_staged = false;
     }
     if (pre)
@@ -645,13 +638,17 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
     const IterDesc& dp = BATCH ? ds[seg_inst] : d1;
     __threadfence();
     __syncthreads();
-    trace_stop(dp.trace, 3 * dp.max_iter, 3 * seg_k + 2);
     if (threadIdx.x == 0)
       is_last = (atomicAdd(&dp.st->counter, (unsigned)run) + (unsigned)run == (unsigned)(dp.nRowTiles + dp.nColTiles));
     __syncthreads();
     if (is_last) pass_finalize(dp, seg_k);
   }
   cp_async_wait_group<0>();
+  if (!BATCH && d1.trace) {
+    __syncthreads();
+    trace_stop(d1.trace, kTraceSlots * d1.max_iter, kTraceSlots * k_trace + 2);
+    trace_stop(d1.trace, kTraceSlots * d1.max_iter, kTraceSlots * k_trace + 3);
+  }
 }
 
 template <int R, bool BF>
@@ -758,12 +755,6 @@ static cudaError_t launch_pdl(void (*kernel)(Args...), int grid, size_t smem, cu
 template <int R>
 static cudaError_t launch_iter_r(const IterDesc& d, cudaStream_t s) {
   {
-    int blocks = d.nI < 4 * kNumSMsHint ? d.nI : 4 * kNumSMsHint;
-    core_kernel<R><<<blocks, 256, 0, s>>>(d);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  {
     cudaError_t e = launch_svd(d, R, s);
     if (e != cudaSuccess) return e;
   }
@@ -786,10 +777,7 @@ static cudaError_t launch_iter_r(const IterDesc& d, cudaStream_t s) {
 
 template <int R>
 static cudaError_t launch_batch_iter_r(const BatchLaunch& b, cudaStream_t s) {
-  core_batch_kernel<R><<<dim3(b.core_blocks, b.count), 256, 0, s>>>(b.ds);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  e = launch_svd_batch(b, R, s);
+  cudaError_t e = launch_svd_batch(b, R, s);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(pass_batch_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.pass_smem);
   if (e != cudaSuccess) return e;

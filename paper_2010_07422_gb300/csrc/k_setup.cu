@@ -13,17 +13,38 @@ namespace ircur {
 // Index sets for `draws` consecutive draws (blockIdx.x) and one or both axes
 // (blockIdx.y), one block per set; see sampler.cuh.
 __global__ void __launch_bounds__(1024) sample_kernel(uint64_t seed, int draw0, int64_t n1, int64_t n2,
-                                                      int nI, int nJ, int* I_all, int* J_all, int only_axis) {
+                                                      int nI, int nJ, int* I_all, int* J_all, int only_axis,
+                                                      unsigned* mapI0, unsigned* mapI1, unsigned* mapJ0,
+                                                      unsigned* mapJ1) {
   __shared__ SamplerSmem S;
   const int axis = only_axis >= 0 ? only_axis : (int)blockIdx.y;
+  const int draw = draw0 + (int)blockIdx.x;
   int* out = axis ? (J_all + (int64_t)blockIdx.x * nJ) : (I_all + (int64_t)blockIdx.x * nI);
-  sample_subset(seed, draw0 + (int)blockIdx.x, axis, axis ? n2 : n1, axis ? nJ : nI, out, S);
+  unsigned* map = axis ? ((draw & 1) ? mapJ1 : mapJ0) : ((draw & 1) ? mapI1 : mapI0);
+  sample_subset(seed, draw, axis, axis ? n2 : n1, axis ? nJ : nI, out, S, map, (unsigned)(draw + 1));
 }
 
 cudaError_t launch_sample(uint64_t seed, int draw0, int draws, int64_t n1, int64_t n2, int nI, int nJ,
-                          int* I_all, int* J_all, int only_axis, cudaStream_t s) {
+                          int* I_all, int* J_all, int only_axis, cudaStream_t s, unsigned* const* mapI,
+                          unsigned* const* mapJ) {
   dim3 grid(draws, only_axis >= 0 ? 1 : 2);
-  sample_kernel<<<grid, 1024, 0, s>>>(seed, draw0, n1, n2, nI, nJ, I_all, J_all, only_axis);
+  sample_kernel<<<grid, 1024, 0, s>>>(seed, draw0, n1, n2, nI, nJ, I_all, J_all, only_axis,
+                                      mapI ? mapI[0] : nullptr, mapI ? mapI[1] : nullptr,
+                                      mapJ ? mapJ[0] : nullptr, mapJ ? mapJ[1] : nullptr);
+  return cudaGetLastError();
+}
+
+// The index maps of caller-supplied sets: map[idx[a]] = index_tag(draw + 1, a).
+// Runs after their check; sets that failed it are never dereferenced.
+__global__ void index_map_kernel(const int* __restrict__ idx, int m, unsigned* __restrict__ map, unsigned tag,
+                                 const State* st) {
+  if (st->status) return;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < m; a += gridDim.x * blockDim.x)
+    map[idx[a]] = index_tag(tag, a);
+}
+
+cudaError_t launch_index_map(const int* idx, int m, unsigned* map, int draw, const State* st, cudaStream_t s) {
+  index_map_kernel<<<(m + 255) / 256, 256, 0, s>>>(idx, m, map, (unsigned)(draw + 1), st);
   return cudaGetLastError();
 }
 
@@ -269,6 +290,7 @@ cudaError_t launch_setup(const IterDesc& d, double zeta0, cudaStream_t s) {
 // IRCUR-F: gather the fixed panels once, D(I,:) -> Prow (nI x ldPr) and
 // D(:,J)^T -> PcolT (nJ x ldPc, row b holds column J_b of D).
 __global__ void __launch_bounds__(256) gather_rows_kernel(IterDesc d) {
+  if (d.st->status) return;  // caller index sets that failed their check are never dereferenced
   const int a = blockIdx.y;
   const float* src = d.D + (int64_t)d.I_all[a] * d.ldD;
   if (d.bf16) {
@@ -284,6 +306,7 @@ __global__ void __launch_bounds__(256) gather_rows_kernel(IterDesc d) {
 }
 
 __global__ void __launch_bounds__(256) gather_cols_kernel(IterDesc d) {
+  if (d.st->status) return;
   const int b = blockIdx.y;
   const int64_t j = d.J_all[b];
   if (d.bf16) {
@@ -305,6 +328,36 @@ cudaError_t launch_gather(const IterDesc& d, cudaStream_t s) {
   int gy = (int)((d.n1 + 255) / 256);
   if (gy > 64) gy = 64;
   gather_cols_kernel<<<dim3(gy, d.nJ), 256, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+}  // namespace ircur
+
+namespace ircur {
+
+// ---------------------------------------------------------------------------
+// D(I,J) of one draw into the compact buffers the core SVD reads:
+// Dc[buf] (nI x ldDc) and its transpose DcT[buf] (nJ x ldDcT).  IRCUR-F
+// gathers it once per solve; IRCUR-R gathers draw 0 here and every later draw
+// in the previous iteration's panel pass.
+__global__ void __launch_bounds__(256) gather_core_kernel(IterDesc d, int draw, int buf) {
+  if (d.st->status) return;  // caller index sets that failed their check are never dereferenced
+  const int* I = d.I_all + (int64_t)draw * d.nI;
+  const int* J = d.J_all + (int64_t)draw * d.nJ;
+  const int64_t total = (int64_t)d.nI * d.nJ;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(e / d.nJ), b = (int)(e - (int64_t)a * d.nJ);
+    const float v = __ldg(d.D + (int64_t)I[a] * d.ldD + J[b]);
+    d.Dc[buf][(int64_t)a * d.ldDc + b] = v;
+    d.DcT[buf][(int64_t)b * d.ldDcT + a] = v;
+  }
+}
+
+cudaError_t launch_gather_core(const IterDesc& d, int draw, int buf, cudaStream_t s) {
+  const int64_t total = (int64_t)d.nI * d.nJ;
+  int blocks = (int)((total + 255) / 256);
+  blocks = blocks < 1 ? 1 : (blocks > 4 * kNumSMsHint ? 4 * kNumSMsHint : blocks);
+  gather_core_kernel<<<blocks, 256, 0, s>>>(d, draw, buf);
   return cudaGetLastError();
 }
 

@@ -1,35 +1,51 @@
-// Rank-r truncation H_r of the |I| x |J| core and its pseudo-inverse
-// (Alg. 1 Phase II; Sec. 3.1: U_{k+1} = H_r([D - S_{k+1}]_{I,J}),
-// U^+ = V_r Sigma_r^{-1} W_r^T).
+// The core of one IRCUR iteration (Alg. 1): Phase I on the |I| x |J| block,
+//   core = [D - S_{k+1}]_{I,J},  S_{k+1} = T_zeta(D - L_k)   (Sec. 3.2),
+// and Phase II, the rank-r truncation U_{k+1} = H_r(core) with its
+// pseudo-inverse U^+ = V_r Sigma_r^{-1} W_r^T (Sec. 3.1), on one thread-block
+// cluster of NC CTAs (NC = 1 .. 16).
 //
-// The dominant rank-r singular subspaces are found by two-sided subspace
-// (orthogonal) iteration with Cholesky QR, warm-started from the previous
-// iterate's right factor B_k(:,J)^T, whose row space is the right singular
-// subspace of L_k(I,J); the core of iteration k+1 differs from L_k(I,J) only
-// where the threshold decisions differ.  One step is
-//     P = core X,  Y Rp = P (CholQR),  Q = core^T Y,
-// and the iteration stops once E = Q - X Rp^T, the part of core^T Y outside
-// span X, is below 1e-6 ||Rp||_F (or has stopped shrinking below 1e-5).
-// Then Y and X get a second CholQR pass and the r x r Rayleigh-Ritz matrix
-// T = Y^T core X follows from the triangular factors without another product
-// (T is upper triangular).  With span Y = span W_r and span X = span V_r,
-// H_r(core) = Y T X^T and its pseudo-inverse is X T^{-1} Y^T = V_r
-// Sigma_r^{-1} W_r^T, so the panel passes need only Y, X T^{-1} and X T^T: no
-// r x r SVD on the iteration's path (sigma_kernel computes the singular
-// values of T on request).  Pivots of T <= max(|I|,|J|) * FLT_EPSILON times
-// the largest are dropped (numerical rank, IRCUR_FLAG_WRANK).
+// Core.  L_k(I,J) = A_k(I,:) B_k(:,J) is evaluated entry by entry with the
+// same FMA chain as the panel passes (lowrank_entry), so the core equals the
+// (I,J) entries of both panels bit for bit.  D(I,J) comes from a compact copy
+// (row-major and transposed), loaded by bulk copies.  CTA c holds the core rows
+// [c mI/NC, ...) (row slab, for core X) and the core columns [c mJ/NC, ...)
+// (column slab, stored transposed, for core^T Y) in shared memory; with NC = 1
+// one copy with an odd leading dimension serves both products conflict-free.
 //
-// It runs on a cluster of CTAs that share the core by rows (csvd_body).
-// Layout: the core rows sit in shared memory (one bulk copy per CTA) with a
-// leading dimension ldu = 4 (mod 8) floats, so 16-byte row vectors read by
-// lanes on consecutive rows hit distinct banks.  The m x r blocks X, Y, Q and
-// the partial sums are column-major (entry (i, t) at t * ld + i): lanes run
-// over i, so every access is conflict-free or a broadcast.
+// Truncation.  Two-sided subspace iteration, warm-started from B_k(:,J)^T, the
+// right factor of the previous iterate on the new columns (the Ritz vectors
+// of the previous core, Sec. 2 of the design notes: the warm start is graded,
+// its columns nearly orthogonal with norms near sigma_i).  Half-steps alternate:
+//   P  = core X            (row slabs)   Y Rp = P    (Cholesky QR, Y replaces P)
+//   Q  = core^T Y          (column slabs) X Uq = Q   (Cholesky QR, X replaces Q)
+// Each half-step ends with one all-gather over distributed shared memory: every
+// CTA pushes its rows of P (or Q) and its partial Gram matrix to every CTA,
+// then one cluster barrier; the r x r Cholesky factors are formed redundantly
+// by every warp from the partials summed in rank order, so every warp of every
+// CTA holds bit-identical factors and takes identical branch decisions.
+// Convergence is tested after every half-step on the residual of the pair it
+// completes: after P, ||core X - Y_prev Uq^T|| (left); after Q,
+// ||core^T Y - X Rp^T|| (right).  The test is scaled by 1 - rho, rho the
+// residual's contraction per half-step (an estimate of sigma_{r+1}/sigma_r),
+// so a narrow gap iterates until the truncated subspace itself is accurate, not
+// only the residual; a residual that stops shrinking has reached the FP32
+// floor (IRCUR_FLAG_SVD_GAP if the target was not met), a step cap ends the
+// rest (IRCUR_FLAG_SVD_NOCONV).
 //
-// Precision: FP32 throughout.  GB300's FP64 pipe runs at a small fraction of
-// its FP32 rate, and serial FP64 Cholesky/sqrt/divide chains cost more than
-// the whole rest of the iteration; CholQR2 (the second pass) restores
-// orthogonality to FP32 rounding.
+// Accuracy.  Cholesky QR in FP32 is accurate when the scaled Gram matrix
+// D^{-1/2} G D^{-1/2} is well conditioned, which the graded warm start gives.
+// When a scaled pivot shows that FP32 cancellation could ruin the factor
+// (pivot / G_tt < 1e-4: an unaligned basis of an ill-conditioned core), the
+// Gram matrix of the gathered block is formed again in FP64 and factorised in
+// FP64, and the basis is rotated to Ritz vectors (one-warp Jacobi SVD of the
+// r x r factor) so that the following half-steps are graded again.
+//
+// Output.  At convergence the pair (Y, X) and T = Y^T core X (Rp, or Uq^T) give
+// H_r(core) = Y T X^T; a one-warp Jacobi SVD T = Ut Sigma Vt^T yields the
+// singular values (numerical rank: sigma_i > max(|I|,|J|) * FLT_EPSILON * sigma_1,
+// else IRCUR_FLAG_WRANK) and the outputs in the Ritz basis:
+//   W = Y Ut (left singular vectors), Vs = X Vt Sigma^{-1}, V = X Vt Sigma,
+// so U^+ = Vs W^T, and the next iteration's warm start is graded.
 #include <cooperative_groups.h>
 #include <float.h>
 #include <string.h>
@@ -42,34 +58,106 @@ namespace ircur {
 
 namespace cg = cooperative_groups;
 
-constexpr int kSmallMats = 9;   // G, Rp, U, U2y, U2x, T, Ut, Vt, scratch (R x R each)
+__host__ __device__ constexpr int svd_np(int R) { return R * (R + 1) / 2; }
+__host__ __device__ constexpr int svd_pow2(int x) { return x <= 1 ? 1 : 2 * svd_pow2((x + 1) / 2); }
+// rows of one product group: G R <= 16 partial sums per lane, reduced together
+__host__ __device__ constexpr int svd_gmax(int R) { return (16 / R) < 1 ? 1 : (16 / R); }
+// largest cluster: loops over the cluster's CTAs are unrolled to this bound
+constexpr int kSvdMaxNC = 16;
+// replicated factors (every warp its own copy) up to R = 10; one shared copy above
+__host__ __device__ constexpr bool svd_rep(int R) { return R <= 10; }
+__host__ __device__ constexpr int svd_slot(int R) { return (svd_np(R) + 2 + 3) & ~3; }
+__host__ __device__ constexpr int svd_wslot(int R) { return (3 * R * R + 2 * R + 4 + 3) & ~3; }
 
-__host__ __device__ constexpr int round_up4(int x) { return (x + 3) & ~3; }
+constexpr int kSvdThreadsCl = 256;   // threads per CTA of a cluster form (NC > 1)
+constexpr int kSvdThreadsOne = 512;  // threads of the one-CTA form (NC = 1)
+constexpr float kPivotFp64 = 1e-4f;  // scaled Cholesky pivot below which the factor is redone in FP64
+constexpr float kRegrade = 0.5f;     // scaled pivot below which the output basis is orthogonalised again
 
-static int ld_core(int nJ) {
-  int ld = (nJ + 3) & ~3;
-  if (((ld / 4) & 1) == 0) ld += 4;
-  return ld;
-}
-
-struct SvdSmall {
-  float* G;     // R x R Gram matrix
-  float* Rp;    // R x R factor of the last P = core X
-  float* U;     // R x R upper Cholesky factor of the last cholqr
-  float* U2y;   // second-pass factor of Y
-  float* U2x;   // second-pass factor of X
-  float* T;     // R x R Rayleigh-Ritz matrix
-  float* Ut;    // R x R
-  float* Vt;    // R x R
-  float* tmp;   // R x R
-  float* dinv;  // R reciprocal pivots
-  float* sig;   // R
-  float* red;   // 64 reduction slots
-  int* ibuf;    // 16 ints
+struct SvdGeom {
+  int nc, nt, nw;
+  int mrI, mcJ;  // rows of a row slab, columns of a column slab
+  int ldr, ldc;  // leading dimensions of the slabs (floats)
+  int ldy, ldx;  // column strides of the gathered blocks P|Y (nI rows) and Q|X (nJ rows), odd
+  int sl, ws;    // floats per exchange slot, per warp slot
+  size_t off_urow, off_ucol, off_p, off_q, off_ps, off_qs, off_red, off_w, off_small, off_r64, off_bar, total;
 };
 
+__host__ __device__ inline int svd_odd(int x) { return (x & 1) ? x : x + 1; }
+
+__host__ __device__ inline SvdGeom svd_geom(int nI, int nJ, int R, int nc) {
+  SvdGeom g;
+  g.nc = nc;
+  g.nt = nc == 1 ? kSvdThreadsOne : kSvdThreadsCl;
+  g.nw = g.nt / 32;
+  g.mrI = (nI + nc - 1) / nc;
+  g.mcJ = (nJ + nc - 1) / nc;
+  // NC = 1: one copy of the core, odd row stride (rows and columns conflict-free);
+  // NC > 1: 16-byte rows (bulk copies), any stride is conflict-free for the lanes-over-k reads
+  g.ldr = nc == 1 ? svd_odd(nJ) : ((nJ + 3) & ~3);
+  g.ldc = (nI + 3) & ~3;
+  g.ldy = svd_odd(nI);
+  g.ldx = svd_odd(nJ);
+  g.sl = svd_slot(R);
+  g.ws = svd_wslot(R);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = (off + bytes + 15) & ~(size_t)15;
+    return o;
+  };
+  g.off_urow = take((size_t)(nc == 1 ? nI : g.mrI) * g.ldr * 4);
+  g.off_ucol = take(nc == 1 ? 0 : (size_t)g.mcJ * g.ldc * 4);
+  g.off_p = take((size_t)R * g.ldy * 4);
+  g.off_q = take((size_t)R * g.ldx * 4);
+  g.off_ps = take((size_t)nc * g.sl * 4);
+  g.off_qs = take((size_t)nc * g.sl * 4);
+  g.off_red = take((size_t)g.nw * g.sl * 4);
+  g.off_w = take((size_t)(svd_rep(R) ? g.nw : 1) * g.ws * 4);
+  g.off_small = take((size_t)(3 * R * R + R + 16) * 4);
+  g.off_r64 = take((size_t)(g.nt + svd_np(R)) * 8);
+  g.off_bar = take(16);
+  g.total = off;
+  return g;
+}
+
+// ---------------------------------------------------------------------------
+// warp building blocks
+
+// Reduce-scatter of NV (a power of two <= 32) values across the warp: lane L
+// returns the sum over all 32 lanes of element L % NV (a fixed summation order).
+template <int NV>
+__device__ __forceinline__ float warp_rs(float (&v)[NV]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int h = NV / 2; h >= 1; h >>= 1) {
+    const bool hi = (lane & h) != 0;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const float send = hi ? v[j] : v[j + h];
+      const float keep = hi ? v[j + h] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+    }
+  }
+  float x = v[0];
+#pragma unroll
+  for (int o = NV; o < 32; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
 template <int R>
-__device__ __forceinline__ float sel(const float (&g)[R], int t) {
+__device__ __forceinline__ void pair_of(int p, int& s, int& t) {
+  s = 0;
+  int rem = p;
+  while (rem >= R - s) {
+    rem -= R - s;
+    ++s;
+  }
+  t = s + rem;
+}
+
+template <int R>
+__device__ __forceinline__ float selr(const float (&g)[R], int t) {
   float v = 0.f;
 #pragma unroll
   for (int u = 0; u < R; ++u)
@@ -77,38 +165,241 @@ __device__ __forceinline__ float sel(const float (&g)[R], int t) {
   return v;
 }
 
-// Cholesky QR of a column-major block, in three pieces (the cluster SVD
-// reduces the Gram matrix across its CTAs between the first two).
-//
-// gram_block: G(s,t) = M(:,s) . M(:,t) over nrows rows for s <= t < r (one
-// entry per warp, lanes over rows), both triangles written.
+// One slab product for a group of G <= svd_gmax(R) output rows starting at
+// `row0`: out(row, t) = sum over the inner index k < ninner of
+// base[row * rs + k * ks] * M[t * ldm + k].  Lanes run over k; the G R partial
+// sums are reduce-scattered, so lane L < G R returns out(row0 + L / R, L % R).
+// Rows >= nvalid contribute zero.
 template <int R>
-__device__ void gram_block(const float* M, int nrows, int ld, int r, float* G) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int npairs = r * (r + 1) / 2;
-  for (int p = warp; p < npairs; p += nwarps) {
-    int s = 0, rem = p;
-    while (rem >= r - s) {
-      rem -= r - s;
-      ++s;
+__device__ __forceinline__ float slab_product(const float* __restrict__ base, int rs, int ks, int row0, int G,
+                                              int nvalid, int ninner, const float* __restrict__ M, int ldm) {
+  constexpr int GM = svd_gmax(R);
+  constexpr int NV = svd_pow2(GM * R);
+  const int lane = threadIdx.x & 31;
+  float v[NV];  // v[g R + t]: partial sum of out(row0 + g, t)
+#pragma unroll
+  for (int e = 0; e < NV; ++e) v[e] = 0.f;
+  for (int k = lane; k < ninner; k += 32) {
+    float mv[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) mv[t] = M[t * ldm + k];
+    const float* up = base + (size_t)k * ks + (size_t)row0 * rs;
+#pragma unroll
+    for (int g = 0; g < GM; ++g) {
+      if (g < G && row0 + g < nvalid) {
+        const float u = up[(size_t)g * rs];
+#pragma unroll
+        for (int t = 0; t < R; ++t) v[g * R + t] = fmaf(u, mv[t], v[g * R + t]);
+      }
     }
-    const int t = s + rem;
-    const float* ms = M + (size_t)s * ld;
-    const float* mt = M + (size_t)t * ld;
-    float acc = 0.f;
-    for (int i = lane; i < nrows; i += 32) acc = fmaf(ms[i], mt[i], acc);
-    acc = warp_sum(acc);
+  }
+  return warp_rs<NV>(v);
+}
+
+// Accumulate the Gram pairs of a group's rows from their reduce-scattered
+// values (lane g R + t holds row g, column t): gp[q] += sum_g v(g,s) v(g,t) for
+// the pairs p = lane + 32 q (upper triangle, row-major pair order).
+template <int R>
+__device__ __forceinline__ void group_gram(float val, int G, const int (&ps)[(svd_np(R) + 31) / 32],
+                                           const int (&pt)[(svd_np(R) + 31) / 32],
+                                           float (&gp)[(svd_np(R) + 31) / 32]) {
+  constexpr int GM = svd_gmax(R);
+  constexpr int PQ = (svd_np(R) + 31) / 32;
+#pragma unroll
+  for (int g = 0; g < GM; ++g) {
+    if (g < G) {
+#pragma unroll
+      for (int q = 0; q < PQ; ++q) {
+        const float a = __shfl_sync(0xffffffffu, val, g * R + ps[q]);
+        const float b = __shfl_sync(0xffffffffu, val, g * R + pt[q]);
+        gp[q] = fmaf(a, b, gp[q]);
+      }
+    }
+  }
+}
+
+// Cholesky factor of the R x R Gram matrix G (full, row-major, in shared
+// memory) formed by one warp in registers (lane l holds row l of the Schur
+// complement): G = U^T U, U upper triangular written to Uw (U(t,u) at t R + u),
+// reciprocal pivots to dw.  Pivots <= 1e-12 of the largest diagonal entry mark
+// dependent columns (zero rows of U, dw = 0).  Returns the number of those and,
+// in minsp, the smallest pivot above noise level relative to its column's
+// diagonal entry of G (1 for an orthogonal block; small values mean FP32
+// cancellation).
+template <int R>
+__device__ int warp_chol(const float* G, int r, float* Uw, float* dw, float& minsp) {
+  const int lane = threadIdx.x & 31;
+  float g[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) g[u] = (lane < r && u < r) ? G[lane * R + u] : 0.f;
+  const float gdiag = selr<R>(g, lane);
+  float maxd = gdiag;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) maxd = fmaxf(maxd, __shfl_xor_sync(0xffffffffu, maxd, o));
+  int brk = 0;
+  float msp = 1.f;
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    if (t < r) {  // the same in every lane
+      const float dgt = __shfl_sync(0xffffffffu, g[t], t);
+      const float g0t = __shfl_sync(0xffffffffu, gdiag, t);
+      const bool keep = dgt > 1e-12f * maxd && dgt <= FLT_MAX;
+      const float rinv = keep ? rsqrtf(dgt) : 0.f;
+      // pivots below 1e-10 of the largest diagonal entry are FP32 noise of the
+      // products themselves (sigma_t / sigma_1 < 1e-5, below the FP32 rank
+      // cutoff): FP64 could not recover them, so they do not count
+      if (keep && dgt > 1e-10f * maxd) msp = fminf(msp, __fdividef(dgt, g0t));
+      const float ul = g[t] * rinv;  // U(t, lane)
+      float urow[R];
+#pragma unroll
+      for (int u = 0; u < R; ++u) urow[u] = __shfl_sync(0xffffffffu, ul, u);
+      if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < R; ++u) Uw[t * R + u] = (u >= t) ? urow[u] : 0.f;
+        dw[t] = rinv;
+      }
+      if (lane > t) {
+#pragma unroll
+        for (int u = t + 1; u < R; ++u) g[u] = fmaf(-ul, urow[u], g[u]);
+      }
+      brk += keep ? 0 : 1;
+    } else if (lane == 0) {
+      dw[t] = 0.f;
+#pragma unroll
+      for (int u = 0; u < R; ++u) Uw[t * R + u] = 0.f;
+    }
+  }
+  __syncwarp();
+  minsp = msp;
+  return brk;
+}
+
+// The same factorisation in FP64 from an FP64 Gram matrix (pairs, upper
+// triangle); the factor and reciprocal pivots are stored in FP32.
+template <int R>
+__device__ void warp_chol64(const double* Gp, int r, float* Uw, float* dw) {
+  const int lane = threadIdx.x & 31;
+  double g[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int s = lane < u ? lane : u, t = lane < u ? u : lane;
+    g[u] = (lane < r && u < r) ? Gp[s * R - s * (s - 1) / 2 + (t - s)] : 0.0;
+  }
+  double maxd = 0.0;
+#pragma unroll
+  for (int u = 0; u < R; ++u)
+    if (u == lane) maxd = g[u];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) maxd = fmax(maxd, __shfl_xor_sync(0xffffffffu, maxd, o));
+  for (int t = 0; t < r; ++t) {
+    double gt = 0.0;
+#pragma unroll
+    for (int u = 0; u < R; ++u)
+      if (u == t) gt = g[u];
+    const double dgt = __shfl_sync(0xffffffffu, gt, t);
+    const bool keep = dgt > 1e-24 * maxd;
+    const double rs = keep ? 1.0 / sqrt(dgt) : 0.0;
+    const double ul = gt * rs;
+    double urow[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) urow[u] = __shfl_sync(0xffffffffu, ul, u);
     if (lane == 0) {
-      G[s * R + t] = acc;
-      G[t * R + s] = acc;
+#pragma unroll
+      for (int u = 0; u < R; ++u) Uw[t * R + u] = (u >= t) ? (float)urow[u] : 0.f;
+      dw[t] = (float)rs;
     }
+    if (lane > t) {
+#pragma unroll
+      for (int u = 0; u < R; ++u) g[u] = fma(-ul, urow[u], g[u]);
+    }
+  }
+  if (lane == 0) {
+    for (int t = r; t < R; ++t) {
+      dw[t] = 0.f;
+      for (int u = 0; u < R; ++u) Uw[t * R + u] = 0.f;
+    }
+  }
+  __syncwarp();
+}
+
+// y U = m for one row (forward substitution with U from warp_chol).
+template <int R>
+__device__ __forceinline__ void row_subst(const float (&m)[R], float (&y)[R], const float* Uw, const float* dw) {
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    float v = m[t];
+#pragma unroll
+    for (int s2 = 0; s2 < t; ++s2) v = fmaf(-y[s2], Uw[s2 * R + t], v);
+    y[t] = v * dw[t];
+  }
+}
+
+// Rows i < n of a column-major block (entry (i,t) at t ld + i) replaced by
+// their solutions y U = row (whole block, one row per thread).
+template <int R>
+__device__ __forceinline__ void block_subst(float* M, int ld, int n, const float* Uw, const float* dw) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float m[R], y[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) m[t] = M[t * ld + i];
+    row_subst<R>(m, y, Uw, dw);
+#pragma unroll
+    for (int t = 0; t < R; ++t) M[t * ld + i] = y[t];
+  }
+}
+
+// Rows i < n of a column-major block replaced by row * Z (Z R x R row-major).
+template <int R>
+__device__ __forceinline__ void block_rotate(float* M, int ld, int n, const float* Z) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float m[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) m[t] = M[t * ld + i];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      float v = 0.f;
+#pragma unroll
+      for (int s2 = 0; s2 < R; ++s2) v = fmaf(m[s2], Z[s2 * R + t], v);
+      M[t * ld + i] = v;
+    }
+  }
+}
+
+// Gram pairs of a whole column-major block (rows < n), FP32 or FP64, by all
+// threads: thread q takes pair q % NP over the rows of chunk q / NP; the chunk
+// sums are added in chunk order.  Result in gout[p] (shared, NP values).
+template <int R, typename A>
+__device__ void block_gram(const float* M, int ld, int n, A* scratch, A* gout) {
+  constexpr int NP = svd_np(R);
+  const int nch = (int)blockDim.x / NP;
+  const int q = threadIdx.x;
+  if (q < nch * NP) {
+    const int p = q % NP, c = q / NP;
+    int s, t;
+    pair_of<R>(p, s, t);
+    A acc = 0;
+    for (int i = c; i < n; i += nch) acc += (A)M[s * ld + i] * (A)M[t * ld + i];
+    scratch[c * NP + p] = acc;
+  }
+  __syncthreads();
+  if (q < NP) {
+    A acc = 0;
+    for (int c = 0; c < nch; ++c) acc += scratch[c * NP + q];
+    gout[q] = acc;
   }
   __syncthreads();
 }
 
-__device__ __forceinline__ float hash_uniform(uint64_t seed, uint64_t ctr) {
-  const uint64_t h = splitmix64(seed ^ splitmix64(ctr));
-  return (float)(h >> 40) * (1.0f / 16777216.0f) * 2.0f - 1.0f;
+// Expand Gram pairs (upper triangle) to a full symmetric R x R matrix (one warp).
+template <int R>
+__device__ __forceinline__ void warp_expand(const float* gp, float* G) {
+  const int lane = threadIdx.x & 31;
+  for (int e = lane; e < R * R; e += 32) {
+    const int i = e / R, j = e - i * R;
+    const int s = i < j ? i : j, t = i < j ? j : i;
+    G[e] = gp[s * R - s * (s - 1) / 2 + (t - s)];
+  }
+  __syncwarp();
 }
 
 // Round-robin (circle method) partner of player p in round k of n (even) players.
@@ -119,23 +410,32 @@ __device__ __forceinline__ int rr_partner(int p, int k, int n) {
   return q < 0 ? q + n - 1 : q;
 }
 
-// Singular values of the last Rayleigh-Ritz matrix T (the r largest singular
-// values of the last core, descending): one-sided Jacobi in one warp, lane p
-// owning column p, round-robin pair ordering.  Used on request only.
+// One-sided Jacobi SVD of the r x r matrix T (T(i,p) at i R + p) in one warp,
+// lane p owning column p: T Vt = Ut diag(sg), written sorted by descending
+// singular value (ties: smaller column first) to Ut, Vt (row-major R x R) and
+// sg; entries beyond r are zero.  A sweep rotates every column pair whose
+// inner product exceeds 1e-6 of its norms (FP32 rounding of the products sits
+// just below); at most 10 sweeps.
 template <int R>
-__global__ void sigma_kernel(const float* __restrict__ Tm, int r, float* __restrict__ sigma) {
-  const int p = threadIdx.x;
-  float tc[R];
+__device__ void warp_jacobi(const float* T, int r, float* Ut, float* Vt, float* sg) {
+  const int p = threadIdx.x & 31;
+  float tc[R], vc[R];
 #pragma unroll
-  for (int i = 0; i < R; ++i) tc[i] = (p < r && i < r) ? Tm[i * R + p] : 0.f;
+  for (int i = 0; i < R; ++i) {
+    tc[i] = (p < r && i < r) ? T[i * R + p] : 0.f;
+    vc[i] = (i == p && p < r) ? 1.f : 0.f;
+  }
   const int nplay = (r + 1) & ~1;
-  for (int sweep = 0; sweep < 30; ++sweep) {
+  for (int sweep = 0; sweep < 10; ++sweep) {
     int rotated = 0;
     for (int rnd = 0; rnd < nplay - 1; ++rnd) {
       const int q = (p < nplay) ? rr_partner(p, rnd, nplay) : p;
-      float tq[R];
+      float tq[R], vq[R];
 #pragma unroll
-      for (int i = 0; i < R; ++i) tq[i] = __shfl_sync(0xffffffffu, tc[i], q);
+      for (int i = 0; i < R; ++i) {
+        tq[i] = __shfl_sync(0xffffffffu, tc[i], q);
+        vq[i] = __shfl_sync(0xffffffffu, vc[i], q);
+      }
       if (p < r && q < r && q != p) {
         const bool lo = p < q;
         float app = 0.f, aqq = 0.f, apq = 0.f;
@@ -156,6 +456,8 @@ __global__ void sigma_kernel(const float* __restrict__ Tm, int r, float* __restr
           for (int i = 0; i < R; ++i) {
             const float a = lo ? tc[i] : tq[i], b = lo ? tq[i] : tc[i];
             tc[i] = lo ? (c * a - s * b) : (s * a + c * b);
+            const float va = lo ? vc[i] : vq[i], vb = lo ? vq[i] : vc[i];
+            vc[i] = lo ? (c * va - s * vb) : (s * va + c * vb);
           }
         }
       }
@@ -165,1182 +467,876 @@ __global__ void sigma_kernel(const float* __restrict__ Tm, int r, float* __restr
   float s2 = 0.f;
 #pragma unroll
   for (int i = 0; i < R; ++i) s2 = fmaf(tc[i], tc[i], s2);
-  const float sg = (p < r) ? sqrtf(s2) : -1.f;
+  const float sv = (p < r) ? sqrtf(s2) : -1.f;
   int pos = 0;
   for (int q = 0; q < r; ++q) {
-    const float sq = __shfl_sync(0xffffffffu, sg, q);
-    pos += (sq > sg) || (sq == sg && q < p);
+    const float sq = __shfl_sync(0xffffffffu, sv, q);
+    pos += (sq > sv) || (sq == sv && q < p);
   }
-  if (p < r) sigma[pos] = sg;
-}
-
-
-// Every warp factorises the same R x R Gram matrix G = U^T U in registers (lane
-// l holds row l of the Schur complement) and keeps U and the reciprocal
-// pivots in its own shared slot (Uw, dinvw), so the rows it then transforms
-// need no block barrier; identical arithmetic gives identical factors in every
-// warp and CTA.  Pivots <= 1e-12 of the largest diagonal entry mark dependent
-// columns (zero rows of U, dinv = 0).  Returns the number of those.
-template <int R>
-__device__ int warp_chol(const float* G, int r, float* Uw, float* dinvw) {
-  const int lane = threadIdx.x & 31;
-  float g[R];
+  if (p < r) {
+    const float inv = sv > 0.f ? 1.f / sv : 0.f;
 #pragma unroll
-  for (int u = 0; u < R; ++u) g[u] = (lane < r && u < r) ? G[lane * R + u] : 0.f;
-  float maxd = sel<R>(g, lane);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) maxd = fmaxf(maxd, __shfl_xor_sync(0xffffffffu, maxd, o));
-  int brk = 0;
-  for (int t = 0; t < r; ++t) {
-    const float gt = sel<R>(g, t);
-    const float dgt = __shfl_sync(0xffffffffu, gt, t);
-    const bool keep = dgt > 1e-12f * maxd && dgt <= FLT_MAX;
-    const float rinv = keep ? rsqrtf(dgt) : 0.f;
-    const float ul = gt * rinv;  // U(t, lane)
-    float urow[R];
-#pragma unroll
-    for (int u = 0; u < R; ++u) urow[u] = __shfl_sync(0xffffffffu, ul, u);
-    if (lane == 0) {
-#pragma unroll
-      for (int u = 0; u < R; ++u) Uw[t * R + u] = (u >= t) ? urow[u] : 0.f;
-      dinvw[t] = rinv;
+    for (int i = 0; i < R; ++i) {
+      Ut[i * R + pos] = tc[i] * inv;
+      Vt[i * R + pos] = vc[i];
     }
-    if (lane > t) {
-#pragma unroll
-      for (int u = 0; u < R; ++u) g[u] = fmaf(-ul, urow[u], g[u]);
-    }
-    brk += keep ? 0 : 1;
+    sg[pos] = sv;
   }
-  if (lane == 0) {
-    for (int t = r; t < R; ++t) {
-      dinvw[t] = 0.f;
-      for (int u = 0; u < R; ++u) Uw[t * R + u] = 0.f;
+  if (p == 0) {
+    for (int c = r; c < R; ++c) {
+      sg[c] = 0.f;
+      for (int i = 0; i < R; ++i) {
+        Ut[i * R + c] = 0.f;
+        Vt[i * R + c] = 0.f;
+      }
     }
+    for (int i = r; i < R; ++i)
+      for (int c = 0; c < r; ++c) {
+        Ut[i * R + c] = 0.f;
+        Vt[i * R + c] = 0.f;
+      }
   }
   __syncwarp();
-  return brk;
 }
 
-// y U = m for one row (forward substitution with U from warp_chol).
-template <int R>
-__device__ __forceinline__ void row_subst(const float (&m)[R], float (&y)[R], const float* Uw, const float* dinvw) {
-#pragma unroll
-  for (int t = 0; t < R; ++t) {
-    float v = m[t];
-#pragma unroll
-    for (int s2 = 0; s2 < t; ++s2) v = fmaf(-y[s2], Uw[s2 * R + t], v);
-    y[t] = v * dinvw[t];
-  }
-}
-
-// Cholesky QR of a column-major block (Min -> Mout, may alias) with the factor
-// formed by every warp; warp 0's copy goes to Uout / sm.dinv for later use.
-template <int R>
-__device__ int cholqr_w(const float* Min, int ldin, float* Mout, int ldout, int nrows, int r, float* Uout,
-                        const SvdSmall& sm, float* slots) {
-  gram_block<R>(Min, nrows, ldin, r, sm.G);
-  const int warp = threadIdx.x >> 5;
-  float* Uw = warp == 0 ? Uout : slots + (size_t)warp * (R * R + R);
-  float* dw = warp == 0 ? sm.dinv : Uw + R * R;
-  const int brk = warp_chol<R>(sm.G, r, Uw, dw);
-  for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
-    float m[R], y[R];
-#pragma unroll
-    for (int s2 = 0; s2 < R; ++s2) m[s2] = Min[(size_t)s2 * ldin + i];
-    row_subst<R>(m, y, Uw, dw);
-#pragma unroll
-    for (int t = 0; t < R; ++t) Mout[(size_t)t * ldout + i] = y[t];
-  }
-  __syncthreads();
-  return brk;
+__device__ __forceinline__ float hash_uniform(uint64_t seed, uint64_t ctr) {
+  const uint64_t h = splitmix64(seed ^ splitmix64(ctr));
+  return (float)(h >> 40) * (1.0f / 16777216.0f) * 2.0f - 1.0f;
 }
 
 // ---------------------------------------------------------------------------
-// Core SVD on a thread-block cluster of kSvdCluster CTAs (distributed shared
-// memory).  The two-sided subspace iteration above, with the core split by
-// rows: CTA c holds rows [c mr, (c+1) mr) of the core in its shared
-// memory (one bulk copy), its own rows of Y and a full copy of X:
-//   Y_c = core_c X                 local rows, no exchange
-//   Gram(Y) = sum_c Y_c^T Y_c      R x R partials summed over the cluster
-//   Q = sum_c core_c^T Y_c         full-size partials summed over the cluster
-//                                  (every CTA forms the whole sum)
-//   Rp, residual, X = orth(Q)      replicated in every CTA
-// Every cluster-wide sum adds the CTAs' partials in rank order, so each CTA
-// holds bit-identical matrices and takes identical branch decisions; one
-// cluster barrier per step (the partial buffers alternate).  Outputs: W by rows of Y (each CTA its rows),
-// X T^{-1} and X T^T by slices of rows.
-constexpr int kCsvdThreads = 256;
+// The kernel body.  role 0: the core and its truncation on a cluster of NC
+// CTAs.  Roles 1, 2 (IRCUR-R with its own sampler): rank 0 of that cluster
+// draws the next iteration's I (role 1) or J (role 2) while role 0 runs.
 
-struct CsvdLayout {
-  int mr;       // core rows per CTA
-  int ldy;      // column stride of the local Y block (mr rounded up to 4)
-  int ldx;      // column stride of X and of the Q partial (nJ rounded up to 4)
-  int js;       // rows of the outputs X T^{-1}, X T^T each CTA writes
-  size_t off_uc, off_x, off_y, off_qp, off_qs, off_qp2, off_end_zero, off_ra, off_ra2, off_stage, off_slots, off_small,
-      off_flag,
-      off_bar, total;
+struct SvdPtrs {
+  float* urow;
+  float* ucol;
+  float* P;  // gathered P, then Y (column-major, nI rows)
+  float* Q;  // gathered Q, then X (column-major, nJ rows)
+  float* ps;
+  float* qs;
+  float* red;
+  float* wbase;
+  float* T;
+  float* Ut;
+  float* Vt;
+  float* sg;
+  int* ib;
+  double* r64;
+  uint64_t* bar;
 };
 
-__host__ __device__ inline CsvdLayout csvd_layout(int nI, int nJ, int ldu, int R, int cl) {
-  CsvdLayout L;
-  L.mr = (nI + cl - 1) / cl;
-  L.ldy = round_up4(L.mr > 0 ? L.mr : 1);
-  L.ldx = round_up4(nJ);
-  L.js = (nJ + cl - 1) / cl;
-  const size_t small = (size_t)kSmallMats * R * R * 4 + 4 * 32 * 4 + 64;
-  size_t off = 0;
-  L.off_uc = off;
-  off += (size_t)L.mr * ldu * 4;
-  L.off_x = off;  // X | Y | Qp | Qs | Qp2 contiguous (zeroed together)
-  off += (size_t)R * L.ldx * 4;
-  L.off_y = off;
-  off += (size_t)R * L.ldy * 4;
-  L.off_qp = off;
-  off += (size_t)R * L.ldx * 4;
-  L.off_qs = off;  // Q = core^T Y, full (every CTA holds the sum of the partials)
-  off += (size_t)R * L.ldx * 4;
-  L.off_qp2 = off;  // the partials alternate between two buffers from step to step
-  off += (size_t)R * L.ldx * 4;
-  L.off_end_zero = off;
-  L.off_ra = off;
-  off += ((size_t)R * R + 4) * 4;
-  L.off_ra2 = off;
-  off += ((size_t)R * R + 4) * 4;
-  L.off_stage = off;  // cl x (R R + 4): remote partials gathered before a fixed-order sum
-  off += (size_t)cl * ((size_t)R * R + 4) * 4;
-  L.off_slots = off;  // per-warp Cholesky factors
-  off += (size_t)(kCsvdThreads / 32) * (R * R + R) * 4;
-  L.off_small = off;
-  off += small;
-  L.off_flag = (off + 15) & ~(size_t)15;
-  off = L.off_flag + 16;
-  L.off_bar = off;
-  off += 16;
-  L.total = off;
-  return L;
+__device__ __forceinline__ SvdPtrs svd_ptrs(unsigned char* smem, const SvdGeom& g, int R) {
+  SvdPtrs p;
+  p.urow = reinterpret_cast<float*>(smem + g.off_urow);
+  p.ucol = reinterpret_cast<float*>(smem + g.off_ucol);
+  p.P = reinterpret_cast<float*>(smem + g.off_p);
+  p.Q = reinterpret_cast<float*>(smem + g.off_q);
+  p.ps = reinterpret_cast<float*>(smem + g.off_ps);
+  p.qs = reinterpret_cast<float*>(smem + g.off_qs);
+  p.red = reinterpret_cast<float*>(smem + g.off_red);
+  p.wbase = reinterpret_cast<float*>(smem + g.off_w);
+  p.T = reinterpret_cast<float*>(smem + g.off_small);
+  p.Ut = p.T + R * R;
+  p.Vt = p.Ut + R * R;
+  p.sg = p.Vt + R * R;
+  p.ib = reinterpret_cast<int*>(p.sg + R);
+  p.r64 = reinterpret_cast<double*>(smem + g.off_r64);
+  p.bar = reinterpret_cast<uint64_t*>(smem + g.off_bar);
+  return p;
 }
 
-size_t csvd_smem_bytes(int nI, int nJ, int Rpad) {
-  const CsvdLayout L = csvd_layout(nI, nJ, ld_core(nJ), Rpad, kSvdCluster);
-  return L.total > sizeof(SamplerSmem) ? L.total : sizeof(SamplerSmem);
+__device__ __forceinline__ void svd_barrier(cg::cluster_group& cl, int nc) {
+  if (nc > 1)
+    cl.sync();
+  else
+    __syncthreads();
 }
 
-// dst[q] = sum over the cluster's CTAs (rank order) of src[q], q < count: the
-// kSvdCluster x count remote values are read in parallel into `stage`, then
-// every sum is formed in rank order.  Call after a cluster barrier that
-// follows every CTA's write of src.
-__device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, float* src, float* dst, int count, float* stage) {
-  for (int q = threadIdx.x; q < kSvdCluster * count; q += blockDim.x) {
-    const int c = q / count, i = q - c * count;
-    stage[q] = cl.map_shared_rank(src, c)[i];
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < count; i += blockDim.x) {
-    float s = 0.f;
+// Gram matrix of the exchange slots (summed in cluster-rank order) into the
+// warp's G, the residual sum and the agreement flag; then the warp's Cholesky
+// factor.  Every warp (or warp 0 only, without replicated factors) runs it.
+template <int R>
+__device__ __forceinline__ int svd_factor(const float* slots, int nc, int sl, int r, float* Gw, float* F, float* dF,
+                                          float& e2, int& bad, float& minsp, float& trace) {
+  constexpr int NP = svd_np(R);
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int c = 0; c < kSvdCluster; ++c) s += stage[c * count + i];
-    dst[i] = s;
+  for (int e0 = 0; e0 < R * R; e0 += 32) {
+    const int e = e0 + lane;
+    if (e < R * R) {
+      const int i = e / R, j = e - i * R;
+      const int s = i < j ? i : j, t = i < j ? j : i;
+      const int p = s * R - s * (s - 1) / 2 + (t - s);
+      float acc = 0.f;
+#pragma unroll
+      for (int c = 0; c < kSvdMaxNC; ++c)
+        if (c < nc) acc += slots[c * sl + p];  // rank order
+      Gw[e] = acc;
+    }
   }
-  __syncthreads();
+  float ee = 0.f, bb = 0.f;
+#pragma unroll
+  for (int c = 0; c < kSvdMaxNC; ++c) {
+    if (c < nc) {
+      ee += slots[c * sl + NP];
+      bb = fmaxf(bb, slots[c * sl + NP + 1]);
+    }
+  }
+  e2 = ee;
+  bad = bb != 0.f;
+  __syncwarp();
+  float tr = 0.f;
+#pragma unroll
+  for (int t = 0; t < R; ++t) tr += t < r ? Gw[t * R + t] : 0.f;
+  trace = tr;
+  return warp_chol<R>(Gw, r, F, dF, minsp);
 }
 
 template <int R>
-__device__ __forceinline__ void csvd_body(const IterDesc& d, int role, unsigned char* smem) {
+__device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned char* smem) {
+  constexpr int NP = svd_np(R);
+  constexpr int PQ = (NP + 31) / 32;
+  constexpr int GM = svd_gmax(R);
+  constexpr bool REP = svd_rep(R);
   cg::cluster_group cl = cg::this_cluster();
+  const int nc = (int)cl.num_blocks();
   const int crank = (int)cl.block_rank();
-  constexpr int ncl = kSvdCluster;
   State* st = d.st;
   if (st->done || st->status) return;  // the same for every CTA: the state is fixed during the launch
   const int k = st->k;
   if (role > 0) {
-    // IRCUR-R drawing its own index sets: rank 0 of the clusters of roles 1
-    // and 2 draws I_{k+1}, J_{k+1} while the role-0 cluster factorises the core
+    // IRCUR-R: the index sets of iteration k + 2 and their map (the panel pass
+    // of iteration k + 1 reads them before it waits for its core SVD); drawn
+    // by the library's sampler, or only mapped when the caller gave them
     const int axis = role - 1;
-    if (crank == 0 && d.sampleAhead && k + 1 < d.max_iter) {
-      int* out = axis ? const_cast<int*>(d.J_all) + (int64_t)(k + 1) * d.nJ
-                      : const_cast<int*>(d.I_all) + (int64_t)(k + 1) * d.nI;
-      sample_subset(d.seed, k + 1, axis, axis ? d.n2 : d.n1, axis ? d.nJ : d.nI, out,
-                    *reinterpret_cast<SamplerSmem*>(smem));
+    const int dn = k + 2;
+    if (crank == 0 && d.resample && dn < d.max_iter) {
+      const int m = axis ? d.nJ : d.nI;
+      int* out = const_cast<int*>(axis ? d.J_all : d.I_all) + (int64_t)dn * m;
+      unsigned* map = axis ? d.posJ[dn & 1] : d.posI[dn & 1];
+      if (d.sampleAhead) {
+        sample_subset(d.seed, dn, axis, axis ? d.n2 : d.n1, m, out, *reinterpret_cast<SamplerSmem*>(smem), map,
+                      (unsigned)(dn + 1));
+      } else {
+        for (int a = threadIdx.x; a < m; a += blockDim.x) map[out[a]] = index_tag((unsigned)(dn + 1), a);
+      }
     }
     return;
   }
-  if (crank == 0) trace_start(d.trace, 3 * k + 1);
-  const int nI = d.nI, nJ = d.nJ, r = d.r, ldu = d.ldCore;
-  const CsvdLayout L = csvd_layout(nI, nJ, ldu, R, ncl);
-  const int row0 = crank * L.mr;
-  const int nrow = nI - row0 < L.mr ? (nI - row0 > 0 ? nI - row0 : 0) : L.mr;
-  const int col0 = crank * L.js;
-  const int ncol = nJ - col0 < L.js ? (nJ - col0 > 0 ? nJ - col0 : 0) : L.js;
-  float* Uc = reinterpret_cast<float*>(smem + L.off_uc);
-  float* X = reinterpret_cast<float*>(smem + L.off_x);
-  float* Y = reinterpret_cast<float*>(smem + L.off_y);
-  float* Qp0 = reinterpret_cast<float*>(smem + L.off_qp);
-  float* Qs = reinterpret_cast<float*>(smem + L.off_qs);
-  float* ra0 = reinterpret_cast<float*>(smem + L.off_ra);  // Gram(Y) partials (two buffers)
-  float* ra1 = reinterpret_cast<float*>(smem + L.off_ra2);
-  float* Qp1 = reinterpret_cast<float*>(smem + L.off_qp2);
-  float* stage = reinterpret_cast<float*>(smem + L.off_stage);
-  float* slots = reinterpret_cast<float*>(smem + L.off_slots);
-  int* flag = reinterpret_cast<int*>(smem + L.off_flag);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.off_bar);
-  SvdSmall sm;
-  {
-    float* p = reinterpret_cast<float*>(smem + L.off_small);
-    sm.G = p;
-    p += R * R;
-    sm.Rp = p;
-    p += R * R;
-    sm.U = p;
-    p += R * R;
-    sm.U2y = p;
-    p += R * R;
-    sm.U2x = p;
-    p += R * R;
-    sm.T = p;
-    p += R * R;
-    sm.Ut = p;
-    p += R * R;
-    sm.Vt = p;
-    p += R * R;
-    sm.tmp = p;
-    p += R * R;
-    sm.dinv = p;
-    p += 32;
-    sm.sig = p;
-    p += 32;
-    sm.red = p;
-    p += 64;
-    sm.ibuf = reinterpret_cast<int*>(p);
+  if (crank == 0) {
+    trace_start(d.trace, kTraceSlots * k + 0);
+    trace_start(d.trace, kTraceSlots * k + 1);
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nI = d.nI, nJ = d.nJ, r = d.r;
+  const SvdGeom g = svd_geom(nI, nJ, R, nc);
+  const SvdPtrs sp = svd_ptrs(smem, g, R);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int NW = (int)(blockDim.x >> 5);
+  const int row0 = nc == 1 ? 0 : crank * g.mrI;
+  const int nrw = nc == 1 ? nI : (nI - row0 < g.mrI ? (nI - row0 > 0 ? nI - row0 : 0) : g.mrI);
+  const int col0 = nc == 1 ? 0 : crank * g.mcJ;
+  const int ncl = nc == 1 ? nJ : (nJ - col0 < g.mcJ ? (nJ - col0 > 0 ? nJ - col0 : 0) : g.mcJ);
+  float* Wsl = sp.wbase + (REP ? (size_t)warp * g.ws : 0);
+  float* Gw = Wsl;
+  float* F1 = Gw + R * R;
+  float* d1 = F1 + R * R;
+  float* F2 = d1 + R;
+  float* d2 = F2 + R * R;
+  const float zeta = (float)st->zeta;
+  const float* AIk = d.AI[k & 1];   // A_k(I_k,:), nI x R
+  const float* BJk = d.BJt[k & 1];  // B_k(:,J_k)^T, nJ x R
+  const int buf = d.resample ? (k & 1) : 0;
+  const float* Dc = d.Dc[buf];
+  const float* DcT = d.DcT[buf];
 
-  // ---- this CTA's core rows into shared memory: one bulk copy
-  const unsigned bytes = (unsigned)((size_t)nrow * ldu * 4);
-  if (nrow > 0 && threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-    mbar_arrive_expect_tx(bar, bytes);
-    bulk_g2s(Uc, d.core + (size_t)row0 * ldu, bytes, bar);
-  }
-  // ---- X, Y, Qp, Qs zeroed (padding rows read as zero); X = B_k(:,J)^T
-  {
-    const size_t nz = (L.off_end_zero - L.off_x) / 4;
-    for (size_t q = threadIdx.x; q < nz; q += blockDim.x) X[q] = 0.f;
-  }
-  __syncthreads();
-  for (int b = threadIdx.x; b < nJ; b += blockDim.x) {
-#pragma unroll
-    for (int t = 0; t < R; ++t) X[(size_t)t * L.ldx + b] = (t < r) ? d.BJt[(size_t)b * R + t] : 0.f;
-  }
-  __syncthreads();
-  int brk = cholqr_w<R>(X, L.ldx, X, L.ldx, nJ, r, sm.U, sm, slots);
-  if (brk > 0) {  // first iteration (B_0 = 0) or a deficient factor: random start
-    for (int b = threadIdx.x; b < nJ; b += blockDim.x) {
-#pragma unroll
-      for (int t = 0; t < R; ++t)
-        X[(size_t)t * L.ldx + b] =
-            (t < r) ? hash_uniform(d.seed ^ 0x5bd1e995ull, ((uint64_t)k << 32) ^ (uint64_t)(b * R + t)) : 0.f;
-    }
-    __syncthreads();
-    cholqr_w<R>(X, L.ldx, X, L.ldx, nJ, r, sm.U, sm, slots);
-  }
-  bool ok = true;
-  if (nrow > 0) {
-    ok = mbar_wait_bounded(bar, 0, d.spinLimit);
-    if (!ok) {
-      if (threadIdx.x == 0) atomicExch(&st->status, (int)IRCUR_ETIMEOUT);
-      mbar_wait_bounded(bar, 0, kSpinLimit);  // let the copy land before the block exits
-    }
-  }
-  ok = __syncthreads_and(ok);
-  if (threadIdx.x == 0) *flag = ok ? 0 : 1;
-  cl.sync();
-  {
-    const int mine = threadIdx.x < ncl ? *cl.map_shared_rank(flag, (int)threadIdx.x) : 0;
-    if (__syncthreads_or(mine)) {
-      cl.sync();  // nobody leaves while others read its flag
-      return;
-    }
-  }
-
-  // ---- subspace iteration.  With Y = (core X) Rp^{-1}, core^T Y =
-  // (core^T core X) Rp^{-1}: the transposed product runs on the raw local rows
-  // in the same phase as their Gram partial, and Rp^{-1} is applied to the
-  // summed Q.  Per step: four block barriers and one cluster barrier (partials
-  // written); the partial buffers alternate between steps.
-  const int nwarps = (int)(blockDim.x >> 5);
-  float* Uw = slots + (size_t)warp * (R * R + R);
-  float* dw = Uw + R * R;
-  int steps = 0;
-  bool converged = false;
-  float prev_res = 0.f;
-  while (true) {
-    ++steps;
-    // this step's partial buffers: a CTA that reaches the next step's cluster
-    // barrier has finished reading these, so the step after next may reuse them
-    float* ra = (steps & 1) ? ra1 : ra0;
-    float* Qp = (steps & 1) ? Qp1 : Qp0;
-    // Y_c = core_c X (raw): one warp per local row, lanes over the inner index
-    for (int o = warp; o < nrow; o += nwarps) {
-      float acc[R];
-#pragma unroll
-      for (int t = 0; t < R; ++t) acc[t] = 0.f;
-      for (int q = lane; q < nJ; q += 32) {
-        const float u = Uc[(size_t)o * ldu + q];
-#pragma unroll
-        for (int t = 0; t < R; ++t) acc[t] = fmaf(u, X[(size_t)t * L.ldx + q], acc[t]);
-      }
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        const float sv = warp_sum(acc[t]);
-        if (lane == 0) Y[(size_t)t * L.ldy + o] = sv;
-      }
-    }
-    __syncthreads();
-    // Gram(Y_c) partial (one entry per warp) and core_c^T Y_c (one column per thread)
-    {
-      const int npairs = r * (r + 1) / 2;
-      for (int pq = warp; pq < npairs; pq += nwarps) {
-        int s0 = 0, rem = pq;
-        while (rem >= r - s0) {
-          rem -= r - s0;
-          ++s0;
-        }
-        const int t1 = s0 + rem;
-        float acc = 0.f;
-        for (int i = lane; i < nrow; i += 32) acc = fmaf(Y[(size_t)s0 * L.ldy + i], Y[(size_t)t1 * L.ldy + i], acc);
-        acc = warp_sum(acc);
-        if (lane == 0) {
-          ra[s0 * R + t1] = acc;
-          ra[t1 * R + s0] = acc;
-        }
-      }
-      for (int j = threadIdx.x; j < nJ; j += blockDim.x) {
-        float acc[R];
-#pragma unroll
-        for (int t = 0; t < R; ++t) acc[t] = 0.f;
-        for (int i = 0; i < nrow; ++i) {
-          const float u = Uc[(size_t)i * ldu + j];
-#pragma unroll
-          for (int t = 0; t < R; ++t) acc[t] = fmaf(u, Y[(size_t)t * L.ldy + i], acc[t]);
-        }
-#pragma unroll
-        for (int t = 0; t < R; ++t) Qp[(size_t)t * L.ldx + j] = acc[t];
-      }
-    }
-    cl.sync();  // (1) partials written
-    // the cluster sums, rank order: Gram(Y) and Q = core^T Y_raw
-    for (int q = threadIdx.x; q < R * R; q += blockDim.x) {
-      float v[ncl];
-#pragma unroll
-      for (int c = 0; c < ncl; ++c) v[c] = cl.map_shared_rank(ra, c)[q];
-      float sacc = 0.f;
-#pragma unroll
-      for (int c = 0; c < ncl; ++c) sacc += v[c];
-      sm.G[q] = sacc;
-    }
-    for (int q = threadIdx.x; q < R * nJ; q += blockDim.x) {
-      const int t = q / nJ, b = q - t * nJ;
-      const size_t at = (size_t)t * L.ldx + b;
-      float v[ncl];
-#pragma unroll
-      for (int c = 0; c < ncl; ++c) v[c] = cl.map_shared_rank(Qp, c)[at];  // all in flight
-      float sacc = 0.f;
-#pragma unroll
-      for (int c = 0; c < ncl; ++c) sacc += v[c];
-      Qs[at] = sacc;
-    }
-    __syncthreads();  // the sums are visible to the whole block
-    // Y Rp = core X: every warp factorises Gram(Y); Q = Q_raw Rp^{-1} row by
-    // row, with the residual ||Q - X Rp^T||_F^2 of each row
-    {
-      float* Up = warp == 0 ? sm.Rp : Uw;
-      float* dp = warp == 0 ? sm.dinv : dw;
-      warp_chol<R>(sm.G, r, Up, dp);
-      float e2 = 0.f;
-      for (int b = threadIdx.x; b < nJ; b += blockDim.x) {
-        float m[R], y[R], xr[R];
-#pragma unroll
-        for (int t = 0; t < R; ++t) {
-          m[t] = Qs[(size_t)t * L.ldx + b];
-          xr[t] = X[(size_t)t * L.ldx + b];
-        }
-        row_subst<R>(m, y, Up, dp);
-#pragma unroll
-        for (int t = 0; t < R; ++t) {
-          Qs[(size_t)t * L.ldx + b] = y[t];
-          float v = y[t];
-#pragma unroll
-          for (int s2 = t; s2 < R; ++s2) v = fmaf(-xr[s2], Up[t * R + s2], v);
-          e2 = fmaf(v, v, e2);
-        }
-      }
-      e2 = warp_sum(e2);
-      if (lane == 0) sm.red[warp] = e2;
-    }
-    __syncthreads();
-    float E2 = 0.f;
-    for (int w = 0; w < nwarps; ++w) E2 += sm.red[w];
-    float RC2 = 0.f;  // ||Rp||_F^2 = trace Gram(Y)
-#pragma unroll
-    for (int t = 0; t < R; ++t) RC2 += sm.G[t * R + t];
-    const float res = sqrtf(E2), nrm = sqrtf(RC2);
-    if (res <= 1e-6f * nrm || (steps > 1 && res > 0.5f * prev_res && res <= 1e-5f * nrm) || !(nrm > 0.f)) {
-      converged = true;
-      break;
-    }
-    if (steps >= d.svdMaxSteps) break;  // keep X, Y, Rp of the same step
-    prev_res = res;
-    cholqr_w<R>(Qs, L.ldx, X, L.ldx, nJ, r, sm.U, sm, slots);  // X = orth(core^T Y), in every CTA
-  }
-  // Y of the last step: Y = (core X) Rp^{-1}
-  for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
-    float m[R], y[R];
-#pragma unroll
-    for (int t = 0; t < R; ++t) m[t] = Y[(size_t)t * L.ldy + i];
-    row_subst<R>(m, y, sm.Rp, sm.dinv);
-#pragma unroll
-    for (int t = 0; t < R; ++t) Y[(size_t)t * L.ldy + i] = y[t];
-  }
-  __syncthreads();
-
-  // ---- second CholQR passes (Y over the cluster, X replicated); T = U2y Rp U2x^{-1}
-  float* raF = (steps & 1) ? ra0 : ra1;  // not the last step's buffer (others may still read that)
-  gram_block<R>(Y, nrow, L.ldy, r, raF);
-  cl.sync();
-  cluster_sum(cl, raF, sm.G, R * R, stage);
-  {
-    float* Up = warp == 0 ? sm.U2y : Uw;
-    float* dp = warp == 0 ? sm.dinv : dw;
-    warp_chol<R>(sm.G, r, Up, dp);
-    for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
-      float m[R], y[R];
-#pragma unroll
-      for (int t = 0; t < R; ++t) m[t] = Y[(size_t)t * L.ldy + i];
-      row_subst<R>(m, y, Up, dp);
-#pragma unroll
-      for (int t = 0; t < R; ++t) Y[(size_t)t * L.ldy + i] = y[t];
-    }
-  }
-  __syncthreads();
-  cholqr_w<R>(X, L.ldx, X, L.ldx, nJ, r, sm.U2x, sm, slots);
-  if (threadIdx.x < 32) {
-    const int s2 = threadIdx.x;
-    if (s2 < r) {
-      float row[R];  // (U2y Rp)(s2, :)
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        float v = 0.f;
-        for (int u = 0; u < r; ++u) v = fmaf(sm.U2y[s2 * R + u], sm.Rp[u * R + t], v);
-        row[t] = v;
-      }
-      float tr[R];  // T(s2,:) U2x = row (forward substitution; dropped pivots give zeros)
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        float v = row[t];
-#pragma unroll
-        for (int u = 0; u < t; ++u) v = fmaf(-tr[u], sm.U2x[u * R + t], v);
-        tr[t] = (t < r) ? v * sm.dinv[t] : 0.f;
-      }
-#pragma unroll
-      for (int t = 0; t < R; ++t) sm.T[s2 * R + t] = tr[t];
-    }
-  }
-  __syncthreads();
-  // ---- numerical rank from the diagonal of T, and T^{-1} on the kept pivots
-  if (warp == 0) {
-    const float dabs = lane < r ? fabsf(sm.T[lane * R + lane]) : 0.f;
-    float dmax = dabs;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    const float tol = (float)(nI > nJ ? nI : nJ) * FLT_EPSILON * dmax;
-    const bool keep = lane < r && dabs > tol && dabs > 0.f;
-    const unsigned kmask = __ballot_sync(0xffffffffu, keep);
-    if (lane < r) {
-      const int c = lane;
-      float x[R];
-#pragma unroll
-      for (int s2 = R - 1; s2 >= 0; --s2) {
-        float v = 0.f;
-        if (s2 <= c && ((kmask >> s2) & 1u)) {
-          v = (s2 == c) ? 1.f : 0.f;
-#pragma unroll
-          for (int u = s2 + 1; u < R; ++u)
-            if (u <= c) v = fmaf(-sm.T[s2 * R + u], x[u], v);
-          v = v / sm.T[s2 * R + s2];
-        }
-        x[s2] = v;
-      }
-#pragma unroll
-      for (int s2 = 0; s2 < R; ++s2) sm.Ut[s2 * R + c] = x[s2];
-      sm.sig[lane] = keep ? dabs : 0.f;
-    }
+  // ---- 1. bulk copies of this CTA's rows and columns of D(I,J) (cluster form)
+  const bool bulk = nc > 1;
+  if (bulk && warp == 0) {
+    const unsigned rowb = (unsigned)(((nJ + 3) & ~3) * 4), colb = (unsigned)(((nI + 3) & ~3) * 4);
     if (lane == 0) {
-      sm.ibuf[1] = __popc(kmask);
-      sm.ibuf[2] = (int)kmask;
-      for (int t = r; t < R; ++t) {
-        sm.sig[t] = 0.f;
-        for (int u = 0; u < R; ++u) sm.Ut[u * R + t] = 0.f;
-      }
+      mbar_init(sp.bar, 1);
+      fence_mbar_init();
+      mbar_arrive_expect_tx(sp.bar, (unsigned)nrw * rowb + (unsigned)ncl * colb);
     }
+    __syncwarp();
+    for (int i = lane; i < nrw; i += 32) bulk_g2s(sp.urow + (size_t)i * g.ldr, Dc + (size_t)(row0 + i) * d.ldDc, rowb, sp.bar);
+    for (int j = lane; j < ncl; j += 32)
+      bulk_g2s(sp.ucol + (size_t)j * g.ldc, DcT + (size_t)(col0 + j) * d.ldDcT, colb, sp.bar);
   }
-  __syncthreads();
-  const int rank = sm.ibuf[1];
-  const unsigned kmask = (unsigned)sm.ibuf[2];
-  // Outputs (U^+ = X T^{-1} Y^T): W = Y by this CTA's rows; Vs = X T^{-1} and
-  // V = X T^T by this CTA's slice.
-  for (int i = threadIdx.x; i < nrow; i += blockDim.x) {
-#pragma unroll
-    for (int t = 0; t < R; ++t)
-      d.W[(size_t)(row0 + i) * R + t] = ((kmask >> t) & 1u) ? Y[(size_t)t * L.ldy + i] : 0.f;
-  }
-  for (int bb = threadIdx.x; bb < ncol; bb += blockDim.x) {
-    const int b = col0 + bb;
-    float x[R];
-#pragma unroll
-    for (int s2 = 0; s2 < R; ++s2) x[s2] = X[(size_t)s2 * L.ldx + b];
+  // ---- 2. A_k(I,:) and B_k(:,J)^T (compact, written by the previous panel
+  // pass): thread q holds rows q and q + blockDim of each in registers (all
+  // loads in flight together), and writes them to P and Q (column-major).  The
+  // column slab below takes A_k(I_i,:) from these registers only: rows of P
+  // owned by other CTAs may already hold their first pushed product (nothing
+  // orders another CTA's first half-step after this prologue), while this
+  // CTA's own rows of P are written by this CTA alone.
+  const int q0 = tid, q1 = tid + (int)blockDim.x;
+  float ai0[R], ai1[R], bj0[R], bj1[R];
+  {
 #pragma unroll
     for (int t = 0; t < R; ++t) {
-      float vp = 0.f, vr = 0.f;
+      ai0[t] = q0 < nI ? AIk[(size_t)q0 * R + t] : 0.f;
+      ai1[t] = q1 < nI ? AIk[(size_t)q1 * R + t] : 0.f;
+      bj0[t] = q0 < nJ ? BJk[(size_t)q0 * R + t] : 0.f;
+      bj1[t] = q1 < nJ ? BJk[(size_t)q1 * R + t] : 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      if (q0 < nI) sp.P[t * g.ldy + q0] = ai0[t];
+      if (q1 < nI) sp.P[t * g.ldy + q1] = ai1[t];
+      if (q0 < nJ) sp.Q[t * g.ldx + q0] = bj0[t];
+      if (q1 < nJ) sp.Q[t * g.ldx + q1] = bj1[t];
+    }
+  }
+  __syncthreads();
+  // ---- 3. the warm start's Gram matrix (its factor is applied after Phase I)
+  float* gout = reinterpret_cast<float*>(sp.r64 + g.nt);  // NP pairs
+  block_gram<R, float>(sp.Q, g.ldx, nJ, reinterpret_cast<float*>(sp.r64), gout);
+  int brk = 0;
+  float msp;
+  if (REP || warp == 0) {
+    warp_expand<R>(gout, Gw);
+    brk = warp_chol<R>(Gw, r, F2, d2, msp);
+  }
+  if (!REP) __syncthreads();
+  if (!REP) {  // every warp needs brk
+    if (tid == 0) sp.ib[0] = brk;
+    __syncthreads();
+    brk = sp.ib[0];
+  }
+  // ---- 4. Phase I on the core: slabs of D(I,J) - T_zeta(D(I,J) - L_k(I,J))
+  bool ok = true;
+  if (bulk) {
+    ok = mbar_wait_bounded(sp.bar, 0, d.spinLimit);
+    if (!ok) {
+      if (tid == 0) atomicExch(&st->status, (int)IRCUR_ETIMEOUT);
+      mbar_wait_bounded(sp.bar, 0, kSpinLimit);  // let the copy land before the block exits
+    }
+    ok = __syncthreads_and(ok);
+  }
+  {
+    // one entry: D - S with S = T_zeta(D - L_k) (the BF16 variant takes the
+    // panels' BF16 decision, re-taken in FP32 within the rounding band)
+    auto entry = [&](float dv32, const float (&a)[R], const float (&b)[R]) {
+      const float l = lowrank_entry<R>(a, b);
+      const float dv = d.bf16 ? bf16_entry(f32_to_bf16_bits(dv32), l, zeta, [&]() { return dv32; }) : dv32;
+      return panel_value(dv, l, zeta);
+    };
+    // row slab (one copy of the whole core for nc == 1): thread per column
+    // (B_k(:,J_j) in registers), the rows' A_k(I_i,:) broadcast reads of own rows
+    for (int half = 0; half < 2; ++half) {
+      const int j = half ? q1 : q0;
+      if (j >= nJ) continue;
+      const float(&bj)[R] = half ? bj1 : bj0;
+      int il = 0;
+      for (; il + 4 <= nrw; il += 4) {
+        float a4[4][R], d4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = row0 + il + u;
+#pragma unroll
+          for (int t = 0; t < R; ++t) a4[u][t] = sp.P[t * g.ldy + i];
+          d4[u] = bulk ? sp.urow[(size_t)(il + u) * g.ldr + j] : __ldg(Dc + (size_t)i * d.ldDc + j);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sp.urow[(size_t)(il + u) * g.ldr + j] = entry(d4[u], a4[u], bj);
+      }
+      for (; il < nrw; ++il) {
+        const int i = row0 + il;
+        float a1[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) a1[t] = sp.P[t * g.ldy + i];
+        const float dv = bulk ? sp.urow[(size_t)il * g.ldr + j] : __ldg(Dc + (size_t)i * d.ldDc + j);
+        sp.urow[(size_t)il * g.ldr + j] = entry(dv, a1, bj);
+      }
+    }
+    // column slab (stored transposed): thread per row (A_k(I_i,:) in
+    // registers), the columns' B_k(:,J_j) broadcast reads of Q
+    if (nc > 1) {
+      for (int half = 0; half < 2; ++half) {
+        const int i = half ? q1 : q0;
+        if (i >= nI) continue;
+        const float(&ai)[R] = half ? ai1 : ai0;
+        int jl = 0;
+        for (; jl + 4 <= ncl; jl += 4) {
+          float b4[4][R], d4[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) b4[u][t] = sp.Q[t * g.ldx + col0 + jl + u];
+            d4[u] = sp.ucol[(size_t)(jl + u) * g.ldc + i];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) sp.ucol[(size_t)(jl + u) * g.ldc + i] = entry(d4[u], ai, b4[u]);
+        }
+        for (; jl < ncl; ++jl) {
+          float b1[R];
+#pragma unroll
+          for (int t = 0; t < R; ++t) b1[t] = sp.Q[t * g.ldx + col0 + jl];
+          sp.ucol[(size_t)jl * g.ldc + i] = entry(sp.ucol[(size_t)jl * g.ldc + i], ai, b1);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (crank == 0) trace_stop(d.trace, kTraceSlots * d.max_iter, kTraceSlots * k + 0);
+  // ---- 5. X_0 = orth(B_k(:,J)^T), or a random start when that is deficient
+  if (brk > 0) {  // first iteration (B_0 = 0) or a deficient warm start
+    for (int q = tid; q < nJ * R; q += blockDim.x) {
+      const int t = q / nJ, b = q - t * nJ;
+      sp.Q[t * g.ldx + b] =
+          (t < r) ? hash_uniform(d.seed ^ 0x5bd1e995ull, ((uint64_t)k << 32) ^ (uint64_t)(b * R + t)) : 0.f;
+    }
+    __syncthreads();
+    block_gram<R, float>(sp.Q, g.ldx, nJ, reinterpret_cast<float*>(sp.r64), gout);
+    if (REP || warp == 0) {
+      warp_expand<R>(gout, Gw);
+      warp_chol<R>(Gw, r, F2, d2, msp);
+    }
+    if (!REP) __syncthreads();
+  }
+  block_subst<R>(sp.Q, g.ldx, nJ, F2, d2);
+  __syncthreads();
+
+  // ---- 6. half-steps
+  int ps_[PQ], pt_[PQ];
+#pragma unroll
+  for (int q = 0; q < PQ; ++q) {
+    const int p = lane + 32 * q;
+    int s = 0, t = 0;
+    if (p < NP) pair_of<R>(p, s, t);
+    ps_[q] = s;
+    pt_[q] = t;
+  }
+  const int rowsP = nrw, rowsQ = ncl;
+  int Gp = (rowsP + NW - 1) / NW;
+  Gp = Gp < 1 ? 1 : (Gp > GM ? GM : Gp);
+  int Gq = (rowsQ + NW - 1) / NW;
+  Gq = Gq < 1 ? 1 : (Gq > GM ? GM : Gq);
+  const float* qbase = nc > 1 ? sp.ucol : sp.urow;
+  const int qrs = nc > 1 ? g.ldc : 1, qks = nc > 1 ? 1 : g.ldr;
+  int h = 0;
+  int exit_kind = 0;  // 1: after a P half-step (T = Rp), 2: after a Q half-step (T = Uq^T)
+  unsigned flags = 0u;
+  float prev_res = -1.f, prev2_res = -1.f, nrmP = 0.f;
+  float rho1 = 1.f, rho2 = 1.f;  // contraction ratios of the two previous tests
+  const float floor_rel = 0.5f * (0.5f * FLT_EPSILON) * sqrtf((float)(nI > nJ ? nI : nJ));
+  float mspP = 1.f, mspQ = 1.f;
+  bool susY = false, susX = false;
+  bool abort_all = false;
+  const int maxh = 2 * d.svdMaxSteps;
+  while (true) {
+    const bool isP = (h & 1) == 0;
+    float* Bf = isP ? sp.P : sp.Q;          // block gathered this half-step
+    const int ldb = isP ? g.ldy : g.ldx;
+    const float* Mb = isP ? sp.Q : sp.P;    // the other side's basis (X or Y)
+    const int ldm = isP ? g.ldx : g.ldy;
+    const int nrows = isP ? rowsP : rowsQ;  // rows this CTA produces
+    const int gbase = isP ? row0 : col0;
+    const int ninner = isP ? nJ : nI;
+    const int G = isP ? Gp : Gq;
+    const float* Fo = isP ? F2 : F1;  // factor of the previous half-step (T of the pair it tests)
+    float gp[PQ];
+#pragma unroll
+    for (int q = 0; q < PQ; ++q) gp[q] = 0.f;
+    float eres = 0.f;
+    const bool test_prev = h > 0;
+    for (int grp = warp; grp * G < nrows; grp += NW) {
+      const int lr0 = grp * G;
+      const float val = isP ? slab_product<R>(sp.urow, g.ldr, 1, lr0, G, nrows, ninner, Mb, ldm)
+                            : slab_product<R>(qbase, qrs, qks, lr0, G, nrows, ninner, Mb, ldm);
+      const int gl = lane / R, tl = lane - (lane / R) * R;
+      const bool mine = lane < G * R && lr0 + gl < nrows;
+      const int gi = gbase + lr0 + gl;
+      if (test_prev && mine) {
+        // residual of the pair this product completes: own rows of the basis
+        // it replaces (Y for P, X for Q) times the previous factor
+        float yu = 0.f;
+#pragma unroll
+        for (int s2 = 0; s2 < R; ++s2) yu = fmaf(Bf[s2 * ldb + gi], Fo[tl * R + s2], yu);
+        const float e = val - yu;
+        eres = fmaf(e, e, eres);
+      }
+      __syncwarp();
+      if (mine) {
+#pragma unroll
+        for (int c = 0; c < kSvdMaxNC; ++c) {
+          if (c < nc) {
+            float* dst = (c == crank) ? Bf : cl.map_shared_rank(Bf, c);
+            dst[tl * ldb + gi] = val;
+          }
+        }
+      }
+      group_gram<R>(mine ? val : 0.f, G, ps_, pt_, gp);
+    }
+    eres = warp_sum(eres);
+#pragma unroll
+    for (int q = 0; q < PQ; ++q) {
+      const int p = lane + 32 * q;
+      if (p < NP) sp.red[warp * g.sl + p] = gp[q];
+    }
+    if (lane == 0) sp.red[warp * g.sl + NP] = eres;
+    __syncthreads();
+    float* slots = isP ? sp.ps : sp.qs;
+    for (int e = tid; e < NP + 2; e += blockDim.x) {
+      float s = 0.f;
+      if (e <= NP) {
+#pragma unroll
+        for (int w = 0; w < kSvdThreadsOne / 32; ++w)
+          if (w < NW) s += sp.red[w * g.sl + e];  // warp order
+      } else {
+        s = ok ? 0.f : 1.f;
+      }
+#pragma unroll
+      for (int c = 0; c < kSvdMaxNC; ++c) {
+        if (c < nc) {
+          float* dst = (c == crank) ? slots : cl.map_shared_rank(slots, c);
+          dst[crank * g.sl + e] = s;
+        }
+      }
+    }
+    svd_barrier(cl, nc);
+    // ---- the factor of this half-step, in every warp
+    float e2 = 0.f, minsp = 1.f, trace = 0.f;
+    int bad = 0;
+    float* Fn = isP ? F1 : F2;
+    float* dn = isP ? d1 : d2;
+    if (REP || warp == 0) svd_factor<R>(slots, nc, g.sl, r, Gw, Fn, dn, e2, bad, minsp, trace);
+    if (!REP) {
+      if (tid == 0) {
+        sp.ib[1] = bad;
+        reinterpret_cast<float*>(sp.ib)[2] = e2;
+        reinterpret_cast<float*>(sp.ib)[3] = minsp;
+        reinterpret_cast<float*>(sp.ib)[4] = trace;
+      }
+      __syncthreads();
+      bad = sp.ib[1];
+      e2 = reinterpret_cast<float*>(sp.ib)[2];
+      minsp = reinterpret_cast<float*>(sp.ib)[3];
+      trace = reinterpret_cast<float*>(sp.ib)[4];
+    }
+    if (bad) {
+      abort_all = true;
+      break;
+    }
+    bool fell_back = false;
+    if (minsp < kPivotFp64) {
+      // FP32 cancellation: the Gram matrix of the whole gathered block in FP64
+      double* gout64 = sp.r64 + g.nt;
+      block_gram<R, double>(Bf, ldb, isP ? nI : nJ, sp.r64, gout64);
+      if (REP || warp == 0) warp_chol64<R>(gout64, r, Fn, dn);
+      if (!REP) __syncthreads();
+      fell_back = true;
+      minsp = 0.f;
+    }
+    if (isP) {
+      nrmP = sqrtf(trace);
+      mspP = minsp;
+      susY = fell_back || minsp < kRegrade;
+    } else {
+      mspQ = minsp;
+      susX = fell_back || minsp < kRegrade;
+    }
+    ++h;
+    // ---- convergence of the pair this half-step completed
+    bool stop = false;
+    if (test_prev) {
+      // rho: contraction of the residual over this half-step (sigma_{r+1} /
+      // sigma_r once the iteration is geometric); near the FP32 floor the
+      // ratio reads ~1 whatever the gap, so the gap is judged by the best of
+      // the last three ratios
+      const float res = sqrtf(e2);
+      const float nrm = nrmP;
+      const float rho = prev_res > 0.f ? res / prev_res : 0.5f;
+      const float rho_min = fminf(rho, fminf(rho1, rho2));
+      const bool narrow = rho_min > 0.8f;
+      const float room = fmaxf(0.05f, 1.f - fminf(rho_min, 1.f));
+      // target: the truncated subspace accurate to ~1e-6 (residual / gap)
+      const bool conv = res <= 1e-6f * nrm * room || !(nrm > 0.f);
+      // the FP32 floor of the residual, about u sqrt(m) / 2 of ||T||
+      const bool at_floor = res <= floor_rel * nrm;
+      const bool stag = h >= 4 && prev2_res > 0.f && res >= 0.97f * prev2_res && res <= 1e-4f * nrm;
+      if (conv || (!narrow && at_floor) || stag) stop = true;
+      if (stop && !conv && narrow) flags |= IRCUR_FLAG_SVD_GAP;
+      rho2 = rho1;
+      rho1 = rho;
+      prev2_res = prev_res;
+      prev_res = res;
+    }
+    if (!stop && h >= maxh) {
+      stop = true;
+      flags |= IRCUR_FLAG_SVD_NOCONV;
+    }
+    // the new basis: Y = P Rp^{-1} or X = Q Uq^{-1}, in place
+    block_subst<R>(Bf, ldb, isP ? nI : nJ, Fn, dn);
+    if (stop) {
+      exit_kind = isP ? 1 : 2;
+      __syncthreads();
+      break;
+    }
+    if (fell_back) {
+      // rotate both bases to the Ritz vectors of T (= Rp, or Uq^T) so that the
+      // next products are graded again; T becomes diag(sigma)
+      __syncthreads();
+      if (warp == 0) {
+        for (int e = lane; e < R * R; e += 32) {
+          const int i = e / R, j = e - i * R;
+          sp.T[e] = isP ? Fn[e] : Fn[j * R + i];
+        }
+        __syncwarp();
+        warp_jacobi<R>(sp.T, r, sp.Ut, sp.Vt, sp.sg);
+      }
+      __syncthreads();
+      block_rotate<R>(sp.P, g.ldy, nI, sp.Ut);
+      block_rotate<R>(sp.Q, g.ldx, nJ, sp.Vt);
+      if (REP || warp == 0) {
+        for (int e = lane; e < R * R; e += 32) {
+          const int i = e / R, j = e - i * R;
+          Fn[e] = (i == j) ? sp.sg[i] : 0.f;
+        }
+        __syncwarp();
+      }
+      // a faster CTA's next pushes must not land while this CTA still rotates
+      svd_barrier(cl, nc);
+      continue;
+    }
+    __syncthreads();
+  }
+  if (abort_all) return;  // a CTA's bulk copy timed out (ETIMEOUT is set); no remote access follows
+
+  // ---- 7. H_r(core) = Y T X^T: orthogonality restored where the last
+  // factorisations were poorly conditioned, then T = Ut Sigma Vt^T
+  if (warp == 0) {
+    for (int e = lane; e < R * R; e += 32) {
+      const int i = e / R, j = e - i * R;
+      sp.T[e] = exit_kind == 1 ? F1[e] : F2[j * R + i];
+    }
+  }
+  __syncthreads();
+  // Re-orthogonalisation Y_old = Y U2y, X_old = X U2x (Cholesky QR).  After a P
+  // half-step the exact relation is core X = Y T (P = Y Rp), so
+  // T <- U2y T U2x^{-1}; after a Q half-step it is Y^T core = T X^T
+  // (Q = X Uq), so T <- U2y^{-T} T U2x^T.
+  float* gout2 = reinterpret_cast<float*>(sp.r64 + g.nt);
+  if (susY) {
+    block_gram<R, float>(sp.P, g.ldy, nI, reinterpret_cast<float*>(sp.r64), gout2);
+    if (warp == 0) {
+      warp_expand<R>(gout2, Gw);
+      warp_chol<R>(Gw, r, sp.Ut, sp.sg, msp);
+      if (lane < R) {
+        float col[R], z[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) col[i] = sp.T[i * R + lane];
+        if (exit_kind == 1) {  // column of U2y T
+#pragma unroll
+          for (int i = 0; i < R; ++i) {
+            float v = 0.f;
+#pragma unroll
+            for (int u = 0; u < R; ++u) v = fmaf(sp.Ut[i * R + u], col[u], v);
+            z[i] = v;
+          }
+        } else {  // column of U2y^{-T} T: z^T U2y = col^T
+          row_subst<R>(col, z, sp.Ut, sp.sg);
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) sp.T[i * R + lane] = z[i];
+      }
+    }
+    __syncthreads();
+    block_subst<R>(sp.P, g.ldy, nI, sp.Ut, sp.sg);
+    __syncthreads();
+  }
+  if (susX) {
+    block_gram<R, float>(sp.Q, g.ldx, nJ, reinterpret_cast<float*>(sp.r64), gout2);
+    if (warp == 0) {
+      warp_expand<R>(gout2, Gw);
+      warp_chol<R>(Gw, r, sp.Vt, sp.sg, msp);
+      if (lane < R) {
+        float row[R], y[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) row[t] = sp.T[lane * R + t];
+        if (exit_kind == 1) {  // row of T U2x^{-1}
+          row_subst<R>(row, y, sp.Vt, sp.sg);
+        } else {  // row of T U2x^T
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            float v = 0.f;
+#pragma unroll
+            for (int u = 0; u < R; ++u) v = fmaf(row[u], sp.Vt[j * R + u], v);
+            y[j] = v;
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < R; ++t) sp.T[lane * R + t] = y[t];
+      }
+    }
+    __syncthreads();
+    block_subst<R>(sp.Q, g.ldx, nJ, sp.Vt, sp.sg);
+    __syncthreads();
+  }
+  // ---- 8. rank and outputs.  With T triangular (no re-orthogonalisation) its
+  // inverse is a back substitution, and sigma_min / sigma_max >=
+  // 1 / (||T||_F ||T^{-1}||_F): above the rank cutoff that certifies rank r,
+  // and H_r(core) = Y T X^T with U^+ = (X T^{-1}) Y^T is output as it stands.
+  // Otherwise (a possibly deficient core, a re-orthogonalised or FP64-rescued
+  // basis) the Jacobi SVD T = Ut Sigma Vt^T decides the numerical rank and the
+  // outputs are written in the Ritz basis.
+  const float rank_tol = (float)(nI > nJ ? nI : nJ) * FLT_EPSILON;
+  bool fast = !(susY || susX);
+  if (warp == 0) {
+    int certified = 0;
+    if (fast) {
+      // T upper (exit after P: Rp) or lower (after Q: Uq^T); Ut <- T^{-1}
+      const float* U = exit_kind == 1 ? F1 : F2;  // upper triangular factor, rows t
+      const float* du = exit_kind == 1 ? d1 : d2;
+      float x[R];
+      const int c = lane;
+#pragma unroll
+      for (int s2 = R - 1; s2 >= 0; --s2) {
+        float v = (s2 == c) ? 1.f : 0.f;
+#pragma unroll
+        for (int u = s2 + 1; u < R; ++u) v = fmaf(-U[s2 * R + u], x[u], v);
+        x[s2] = (c < r && s2 <= c) ? v * du[s2] : 0.f;
+      }
+      float tf = 0.f, itf = 0.f;
 #pragma unroll
       for (int s2 = 0; s2 < R; ++s2) {
-        vp = fmaf(x[s2], sm.Ut[s2 * R + t], vp);
-        vr = fmaf(x[s2], sm.T[t * R + s2], vr);
+        if (c < R) {
+          // U^{-1}(s2, c) = x[s2]; T^{-1} = U^{-1} (after P) or U^{-T} (after Q)
+          if (exit_kind == 1)
+            sp.Ut[s2 * R + c] = x[s2];
+          else
+            sp.Ut[c * R + s2] = x[s2];
+        }
+        itf = fmaf(x[s2], x[s2], itf);
+        const float tv = c < R ? U[s2 * R + c] : 0.f;
+        tf = fmaf(tv, tv, tf);
       }
-      const bool kt = (kmask >> t) & 1u;
-      d.Vs[(size_t)b * R + t] = kt ? vp : 0.f;
-      d.V[(size_t)b * R + t] = kt ? vr : 0.f;
+      tf = warp_sum(tf);
+      itf = warp_sum(itf);
+      // a dropped (dependent) pivot leaves T singular: never certified
+      bool allpiv = true;
+#pragma unroll
+      for (int s2 = 0; s2 < R; ++s2) allpiv = allpiv && (s2 >= r || du[s2] != 0.f);
+      // rank r certified: 1 / (||T||_F ||T^{-1}||_F) > cutoff
+      certified = (allpiv && tf > 0.f && itf > 0.f && rank_tol * rank_tol * tf * itf < 1.f && itf <= FLT_MAX) ? 1 : 0;
+    }
+    if (lane == 0) sp.ib[5] = certified;
+  }
+  __syncthreads();
+  fast = fast && sp.ib[5] != 0;
+  int kr = r;
+  if (!fast) {
+    if (warp == 0) warp_jacobi<R>(sp.T, r, sp.Ut, sp.Vt, sp.sg);
+    __syncthreads();
+    const float tol = rank_tol * sp.sg[0];
+    kr = 0;
+    for (int t = 0; t < r; ++t) kr += (sp.sg[t] > tol && sp.sg[t] > 0.f) ? 1 : 0;
+  }
+  {
+    const int wr = (nI + nc - 1) / nc, w0 = crank * wr, w1 = w0 + wr < nI ? w0 + wr : nI;
+    for (int i = w0 + tid; i < w1; i += blockDim.x) {
+      float y[R];
+#pragma unroll
+      for (int s2 = 0; s2 < R; ++s2) y[s2] = sp.P[s2 * g.ldy + i];
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        float v = y[t];
+        if (!fast) {
+          v = 0.f;
+#pragma unroll
+          for (int s2 = 0; s2 < R; ++s2) v = fmaf(y[s2], sp.Ut[s2 * R + t], v);
+        }
+        d.W[(size_t)i * R + t] = t < kr ? v : 0.f;
+      }
+    }
+    const int vr = (nJ + nc - 1) / nc, v0 = crank * vr, v1 = v0 + vr < nJ ? v0 + vr : nJ;
+    for (int j = v0 + tid; j < v1; j += blockDim.x) {
+      float x[R];
+#pragma unroll
+      for (int s2 = 0; s2 < R; ++s2) x[s2] = sp.Q[s2 * g.ldx + j];
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        float vs = 0.f, vv = 0.f;
+        if (fast) {  // Vs = X T^{-1}, V = X T^T
+#pragma unroll
+          for (int s2 = 0; s2 < R; ++s2) {
+            vs = fmaf(x[s2], sp.Ut[s2 * R + t], vs);
+            vv = fmaf(x[s2], sp.T[t * R + s2], vv);
+          }
+        } else {  // Vs = X Vt Sigma^{-1}, V = X Vt Sigma
+          float v = 0.f;
+#pragma unroll
+          for (int s2 = 0; s2 < R; ++s2) v = fmaf(x[s2], sp.Vt[s2 * R + t], v);
+          vs = t < kr ? v / sp.sg[t] : 0.f;
+          vv = t < kr ? v * sp.sg[t] : 0.f;
+        }
+        const bool kt = t < kr;
+        d.Vs[(size_t)j * R + t] = kt ? vs : 0.f;
+        d.V[(size_t)j * R + t] = kt ? vv : 0.f;
+      }
     }
   }
   if (crank == 0) {
-    if (threadIdx.x < R) d.sigma[threadIdx.x] = sm.sig[threadIdx.x];
-    if (threadIdx.x < R * R) d.Tm[threadIdx.x] = sm.T[threadIdx.x];
-    if (threadIdx.x == 0) {
-      unsigned f = 0u;
-      if (rank < r) f |= IRCUR_FLAG_WRANK;
-      if (!converged) f |= IRCUR_FLAG_SVD_NOCONV;
-      if (f) atomicOr(&st->flags, f);
-      st->svd_steps += steps;
-      st->svd_last_steps = steps;
+    for (int e = tid; e < R * R; e += blockDim.x) {
+      const int i = e / R, j = e - i * R;
+      d.Tm[e] = fast ? sp.T[e] : ((i == j && i < kr) ? sp.sg[i] : 0.f);
     }
-  }
-  cl.sync();  // no CTA leaves while another may still read its shared memory
-  if (crank == 0 && d.trace) {
-    __syncthreads();
-    trace_stop(d.trace, 3 * d.max_iter, 3 * k + 1);
+    if (tid == 0) {
+      unsigned f = flags;
+      if (kr < r) f |= IRCUR_FLAG_WRANK;
+      if (f) atomicOr(&st->flags, f);
+      st->svd_steps += h;
+      st->svd_last_steps = h;
+    }
+    if (d.trace) {
+      __syncthreads();
+      trace_stop(d.trace, kTraceSlots * d.max_iter, kTraceSlots * k + 1);
+    }
   }
 }
 
-// Up to R = 7 the cluster SVD fits in 128 registers without spilling; the
-// cap leaves room on its SMs for the pass blocks that start while it runs.
+// The cluster form caps its registers at 128 per thread up to R = 10, so that
+// the pass blocks launched while it runs fit on its SMs.
 template <int R>
-__global__ void __launch_bounds__(kCsvdThreads, (R <= 7 ? 2 : 1)) csvd_kernel(IterDesc d) {
+__global__ void __launch_bounds__(kSvdThreadsCl, (R <= 10 ? 2 : 1)) csvd_kernel(IterDesc d) {
   extern __shared__ __align__(16) unsigned char smem[];
   // every CTA is resident from here on: the pass kernel may start on the
   // other SMs (it waits for this grid before reading its outputs)
   pdl_launch_dependents();
-  csvd_body<R>(d, blockIdx.y, smem);
+  svd_body<R>(d, blockIdx.y, smem);
 }
 
-// Batched form: cluster blockIdx.x / kSvdCluster factorises instance
-// list[blockIdx.x / kSvdCluster]; blockIdx.y is the role.
 template <int R>
-__global__ void __launch_bounds__(kCsvdThreads, (R <= 7 ? 2 : 1)) csvd_batch_kernel(const IterDesc* __restrict__ ds,
-                                                                    const int* __restrict__ list) {
+__global__ void __launch_bounds__(kSvdThreadsOne, 1) ssvd_kernel(IterDesc d) {
   extern __shared__ __align__(16) unsigned char smem[];
-  pdl_launch_dependents();  // the batched pass kernel may start (it waits before the projections)
-  csvd_body<R>(ds[list[blockIdx.x / kSvdCluster]], blockIdx.y, smem);
+  pdl_launch_dependents();
+  svd_body<R>(d, blockIdx.y, smem);
+}
+
+// Batched forms: cluster (or CTA) x / NC factorises instance list[x / NC].
+template <int R>
+__global__ void __launch_bounds__(kSvdThreadsCl, (R <= 10 ? 2 : 1)) csvd_batch_kernel(const IterDesc* __restrict__ ds,
+                                                                                    const int* __restrict__ list) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  pdl_launch_dependents();
+  svd_body<R>(ds[list[blockIdx.x / cg::this_cluster().num_blocks()]], blockIdx.y, smem);
+}
+
+template <int R>
+__global__ void __launch_bounds__(kSvdThreadsOne, 1) ssvd_batch_kernel(const IterDesc* __restrict__ ds,
+                                                                      const int* __restrict__ list) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  pdl_launch_dependents();
+  svd_body<R>(ds[list[blockIdx.x]], blockIdx.y, smem);
+}
+
+// Singular values of the last core's T (H_r(core) = Y T X^T, so they are the
+// r largest singular values of H_r), on request: one warp's Jacobi SVD.
+template <int R>
+__global__ void sigma_kernel(const float* __restrict__ Tm, int r, float* __restrict__ sigma) {
+  __shared__ float T[R * R], Ut[R * R], Vt[R * R], sg[R];
+  for (int e = threadIdx.x; e < R * R; e += 32) T[e] = Tm[e];
+  __syncwarp();
+  warp_jacobi<R>(T, r, Ut, Vt, sg);
+  if ((int)threadIdx.x < r) sigma[threadIdx.x] = sg[threadIdx.x];
+}
+
+cudaError_t launch_sigma(const float* Tm, int r, int Rpad, float* sigma, cudaStream_t s) {
+  switch (Rpad) {
+#define IRCUR_SIGMA_CASE(RR) \
+  case RR:                   \
+    sigma_kernel<RR><<<1, 32, 0, s>>>(Tm, r, sigma); \
+    break;
+    IRCUR_SIGMA_CASE(1)
+    IRCUR_SIGMA_CASE(2)
+    IRCUR_SIGMA_CASE(3)
+    IRCUR_SIGMA_CASE(4)
+    IRCUR_SIGMA_CASE(5)
+    IRCUR_SIGMA_CASE(6)
+    IRCUR_SIGMA_CASE(7)
+    IRCUR_SIGMA_CASE(8)
+    IRCUR_SIGMA_CASE(9)
+    IRCUR_SIGMA_CASE(10)
+    IRCUR_SIGMA_CASE(12)
+    IRCUR_SIGMA_CASE(16)
+#undef IRCUR_SIGMA_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// Core SVD in one CTA, for cores that fit in one SM's shared memory (R <= 8,
-// where the padded rank equals r).  The same two-sided subspace iteration,
-// warm start and stopping rule as the cluster form above, with every
-// exchange inside one block of 1024 threads instead of across a cluster:
-//   P  = core X      threads (row i, column segment s) sum 16-byte column
-//                    quads of their row; thread i adds the segments in order
-//                    and forms its row's Gram(P) products
-//   Q~ = core^T P    threads (column quad q, row segment s), the same way
-//   Rp = chol(Gram P), Q = Q~ Rp^{-1}, the residual Q - X Rp^T and the
-//                    Gram(Q) products by thread j (Q stays in its registers)
-//   X  = Q chol(Gram Q)^{-1}
-// Factors of the r x r Gram matrices are formed redundantly by every warp
-// that owns rows, so the rows they transform need no further barrier: five
-// block barriers per step.  Every sum runs in a fixed order (bit-identical
-// results from launch to launch).
-constexpr int kSsvdThreads = 1024;
-constexpr int kSsvdMaxR = 8;
-constexpr int kSsvdSeg = 8;  // most segments of either partial product
+// host side
 
-__host__ __device__ constexpr int npairs_of(int R) { return R * (R + 1) / 2; }
-
-struct SsvdLayout {
-  int nq;       // 16-byte column quads of the core, ceil(nJ / 4)
-  int ldx;      // column stride of X and of the core^T P partials (4 nq)
-  int ldy;      // column stride of the P partials (nI rounded up to 4)
-  int ps;       // row stride of P (R rounded up to 4)
-  int s1, qs1;  // P partials: column segments, quads per segment
-  int s3, rs3;  // core^T P partials: row segments, rows per segment
-  int nw;       // warps owning rows, ceil(max(nI, nJ) / 32)
-  int slot;     // floats per warp slot
-  size_t off_uc, off_x, off_p, off_part, off_red, off_slots, off_flag, off_bar, total;
-};
-
-__host__ __device__ inline SsvdLayout ssvd_layout(int nI, int nJ, int ldu, int R) {
-  SsvdLayout L;
-  const int nt = kSsvdThreads;
-  L.nq = (nJ + 3) / 4;
-  L.ldx = 4 * L.nq;
-  L.ldy = round_up4(nI);
-  L.ps = round_up4(R);
-  L.s1 = nt / (nI > 0 ? nI : 1);
-  L.s1 = L.s1 < 1 ? 1 : (L.s1 > kSsvdSeg ? kSsvdSeg : L.s1);
-  L.qs1 = (L.nq + L.s1 - 1) / L.s1;
-  L.s3 = nt / (L.nq > 0 ? L.nq : 1);
-  L.s3 = L.s3 < 1 ? 1 : (L.s3 > kSsvdSeg ? kSsvdSeg : L.s3);
-  L.rs3 = (nI + L.s3 - 1) / L.s3;
-  const int mx = nI > nJ ? nI : nJ;
-  L.nw = (mx + 31) / 32;
-  L.slot = 6 * R * R + 3 * R;
-  const size_t part = (size_t)R * ((size_t)L.s1 * L.ldy > (size_t)L.s3 * L.ldx ? (size_t)L.s1 * L.ldy
-                                                                               : (size_t)L.s3 * L.ldx);
-  size_t off = 0;
-  L.off_uc = off;
-  off += (size_t)nI * ldu * 4;
-  L.off_x = off;
-  off += (size_t)R * L.ldx * 4;
-  L.off_p = off;
-  off += (size_t)nI * L.ps * 4;
-  L.off_part = off;
-  off += part * 4;
-  L.off_red = off;  // per warp: Gram pairs (two sets) and one residual sum
-  off += (size_t)L.nw * (2 * npairs_of(R) + 1) * 4;
-  L.off_slots = off;
-  off += (size_t)L.nw * L.slot * 4;
-  L.off_flag = (off + 15) & ~(size_t)15;
-  off = L.off_flag + 16;
-  L.off_bar = off;
-  off += 16;
-  L.total = off;
-  return L;
+size_t svd_smem_bytes(int nI, int nJ, int Rpad, int nc) {
+  const SvdGeom g = svd_geom(nI, nJ, Rpad, nc);
+  return g.total > sizeof(SamplerSmem) ? g.total : sizeof(SamplerSmem);
 }
 
-size_t ssvd_smem_bytes(int nI, int nJ, int Rpad) {
-  if (Rpad > kSsvdMaxR || nI > kSsvdThreads || nJ > kSsvdThreads || nI < 1 || nJ < 1) return ~(size_t)0;
-  const SsvdLayout L = ssvd_layout(nI, nJ, ld_core(nJ), Rpad);
-  return L.total > sizeof(SamplerSmem) ? L.total : sizeof(SamplerSmem);
-}
+bool svd_fits(int nI, int nJ, int Rpad, int nc) { return svd_smem_bytes(nI, nJ, Rpad, nc) <= 227 * 1024; }
 
-bool ssvd_fits(int nI, int nJ, int Rpad) { return ssvd_smem_bytes(nI, nJ, Rpad) <= 227 * 1024; }
-
-// The Gram products of one row (a) summed over the warp; lane 0 writes the
-// R(R+1)/2 upper-triangle sums to out.
-template <int R>
-__device__ __forceinline__ void warp_pair_sums(const float (&a)[R], float* out) {
-  int p = 0;
-#pragma unroll
-  for (int s0 = 0; s0 < R; ++s0) {
-#pragma unroll
-    for (int t1 = s0; t1 < R; ++t1) {
-      const float v = warp_sum(a[s0] * a[t1]);
-      if ((threadIdx.x & 31) == 0) out[p] = v;
-      ++p;
-    }
-  }
-}
-
-// Gw = the sum over warps 0..nw-1 (in order) of their pair sums, both triangles.
-template <int R>
-__device__ __forceinline__ void gram_from_pairs(const float* red, int stride, int nw, float* Gw) {
-  const int lane = threadIdx.x & 31;
-  constexpr int np = npairs_of(R);
-  for (int p = lane; p < np; p += 32) {
-    float v = 0.f;
-    for (int w = 0; w < nw; ++w) v += red[w * stride + p];
-    int s0 = 0, rem = p;
-    while (rem >= R - s0) {
-      rem -= R - s0;
-      ++s0;
-    }
-    const int t1 = s0 + rem;
-    Gw[s0 * R + t1] = v;
-    Gw[t1 * R + s0] = v;
-  }
-  __syncwarp();
-}
-
-template <int R>
-__device__ __forceinline__ void ssvd_body(const IterDesc& d, int role, unsigned char* smem) {
-  static_assert(R <= kSsvdMaxR, "one-CTA core SVD is built for R <= 8");
-  State* st = d.st;
-  if (st->done || st->status) return;  // the same for every thread: the state is fixed during the launch
-  const int k = st->k;
-  if (role > 0) {
-    const int axis = role - 1;
-    if (d.sampleAhead && k + 1 < d.max_iter) {
-      int* out = axis ? const_cast<int*>(d.J_all) + (int64_t)(k + 1) * d.nJ
-                      : const_cast<int*>(d.I_all) + (int64_t)(k + 1) * d.nI;
-      sample_subset(d.seed, k + 1, axis, axis ? d.n2 : d.n1, axis ? d.nJ : d.nI, out,
-                    *reinterpret_cast<SamplerSmem*>(smem));
-    }
-    return;
-  }
-  trace_start(d.trace, 3 * k + 1);
-  const int nI = d.nI, nJ = d.nJ, ldu = d.ldCore;
-  constexpr int np = npairs_of(R);
-  const SsvdLayout L = ssvd_layout(nI, nJ, ldu, R);
-  float* Uc = reinterpret_cast<float*>(smem + L.off_uc);
-  float* X = reinterpret_cast<float*>(smem + L.off_x);
-  float* P = reinterpret_cast<float*>(smem + L.off_p);
-  float* part = reinterpret_cast<float*>(smem + L.off_part);
-  float* redA = reinterpret_cast<float*>(smem + L.off_red);  // nw x np
-  float* redB = redA + (size_t)L.nw * np;                     // nw x np
-  float* redE = redB + (size_t)L.nw * np;                     // nw
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.off_bar);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool rowwarp = warp < L.nw;
-  // this warp's slot: Gram scratch, Rp (+ reciprocal pivots), Uq / U2y, U2x, T, T^{-1}
-  float* Gw = reinterpret_cast<float*>(smem + L.off_slots) + (size_t)(rowwarp ? warp : 0) * L.slot;
-  float* Rpw = Gw + R * R;
-  float* dRp = Rpw + R * R;
-  float* Uqw = dRp + R;
-  float* dUq = Uqw + R * R;
-  float* U2x = dUq + R;
-  float* dU2x = U2x + R * R;
-  float* Tw = dU2x + R;
-  float* Utw = Tw + R * R;
-
-  // ---- the core into shared memory: one bulk copy
-  const unsigned bytes = (unsigned)((size_t)nI * ldu * 4);
-  if (tid == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-    mbar_arrive_expect_tx(bar, bytes);
-    bulk_g2s(Uc, d.core, bytes, bar);
-  }
-  for (int q = tid; q < R * L.ldx; q += blockDim.x) X[q] = 0.f;
-  // ---- X = orth(B_k(:,J)^T), or a random start when that is deficient
-  float xb[R];
-#pragma unroll
-  for (int t = 0; t < R; ++t) xb[t] = (tid < nJ) ? d.BJt[(size_t)tid * R + t] : 0.f;
-  if (rowwarp) warp_pair_sums<R>(xb, redB + warp * np);
-  __syncthreads();
-  int brk = 0;
-  if (rowwarp) {
-    gram_from_pairs<R>(redB, np, L.nw, Gw);
-    brk = warp_chol<R>(Gw, R, Uqw, dUq);
-    if (brk == 0) {
-      if (tid < nJ) {
-        float y[R];
-        row_subst<R>(xb, y, Uqw, dUq);
-#pragma unroll
-        for (int t = 0; t < R; ++t) X[(size_t)t * L.ldx + tid] = y[t];
-      }
-    } else {
-#pragma unroll
-      for (int t = 0; t < R; ++t)
-        xb[t] = (tid < nJ)
-                    ? hash_uniform(d.seed ^ 0x5bd1e995ull, ((uint64_t)k << 32) ^ (uint64_t)(tid * R + t))
-                    : 0.f;
-      warp_pair_sums<R>(xb, redA + warp * np);
-    }
-  }
-  __syncthreads();
-  if (rowwarp && brk > 0) {  // brk is the same in every row warp
-    gram_from_pairs<R>(redA, np, L.nw, Gw);
-    warp_chol<R>(Gw, R, Uqw, dUq);
-    if (tid < nJ) {
-      float y[R];
-      row_subst<R>(xb, y, Uqw, dUq);
-#pragma unroll
-      for (int t = 0; t < R; ++t) X[(size_t)t * L.ldx + tid] = y[t];
-    }
-  }
-  bool ok = mbar_wait_bounded(bar, 0, d.spinLimit);
-  if (!ok) {
-    if (tid == 0) atomicExch(&st->status, (int)IRCUR_ETIMEOUT);
-    mbar_wait_bounded(bar, 0, kSpinLimit);  // let the copy land before the block exits
-  }
-  if (!__syncthreads_and(ok)) return;
-  // columns nJ .. 4 nq of the last quad read as zero
-  for (int q = tid; q < nI * (L.ldx - nJ); q += blockDim.x) {
-    const int i = q / (L.ldx - nJ), c = nJ + q % (L.ldx - nJ);
-    Uc[(size_t)i * ldu + c] = 0.f;
-  }
-  __syncthreads();
-
-  // ---- subspace iteration
-  const int seg1 = tid / nI, i1 = tid - seg1 * nI;      // P partials
-  const int seg3 = tid / L.nq, q3 = tid - seg3 * L.nq;  // core^T P partials
-  int steps = 0;
-  bool converged = false;
-  float prev_res = 0.f;
-  float qv[R];
-  while (true) {
-    ++steps;
-    if (seg1 < L.s1) {
-      float acc[R];
-#pragma unroll
-      for (int t = 0; t < R; ++t) acc[t] = 0.f;
-      const int qa = seg1 * L.qs1, qb = qa + L.qs1 < L.nq ? qa + L.qs1 : L.nq;
-      const float* urow = Uc + (size_t)i1 * ldu;
-      for (int q = qa; q < qb; ++q) {
-        const float4 u = *reinterpret_cast<const float4*>(urow + 4 * q);
-#pragma unroll
-        for (int t = 0; t < R; ++t) {
-          const float4 x = *reinterpret_cast<const float4*>(X + (size_t)t * L.ldx + 4 * q);
-          acc[t] = fmaf(u.x, x.x, acc[t]);
-          acc[t] = fmaf(u.y, x.y, acc[t]);
-          acc[t] = fmaf(u.z, x.z, acc[t]);
-          acc[t] = fmaf(u.w, x.w, acc[t]);
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < R; ++t) part[(size_t)(seg1 * R + t) * L.ldy + i1] = acc[t];
-    }
-    __syncthreads();
-    if (rowwarp) {
-      float pv[R];
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        float v = 0.f;
-        if (tid < nI)
-          for (int s = 0; s < L.s1; ++s) v += part[(size_t)(s * R + t) * L.ldy + tid];
-        pv[t] = v;
-      }
-      if (tid < nI) {
-#pragma unroll
-        for (int t = 0; t < R; ++t) P[(size_t)tid * L.ps + t] = pv[t];
-      }
-      warp_pair_sums<R>(pv, redA + warp * np);
-    }
-    __syncthreads();
-    if (seg3 < L.s3) {
-      float acc[4][R];
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int t = 0; t < R; ++t) acc[c][t] = 0.f;
-      const int ia = seg3 * L.rs3, ib = ia + L.rs3 < nI ? ia + L.rs3 : nI;
-      for (int i = ia; i < ib; ++i) {
-        const float4 u = *reinterpret_cast<const float4*>(Uc + (size_t)i * ldu + 4 * q3);
-        const float4* prow = reinterpret_cast<const float4*>(P + (size_t)i * L.ps);
-        const float4 pa = prow[0];
-        const float4 pb = (R > 4) ? prow[1] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float pall[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
-        float pr[R];
-#pragma unroll
-        for (int t = 0; t < R; ++t) pr[t] = pall[t];
-#pragma unroll
-        for (int t = 0; t < R; ++t) {
-          acc[0][t] = fmaf(u.x, pr[t], acc[0][t]);
-          acc[1][t] = fmaf(u.y, pr[t], acc[1][t]);
-          acc[2][t] = fmaf(u.z, pr[t], acc[2][t]);
-          acc[3][t] = fmaf(u.w, pr[t], acc[3][t]);
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < R; ++t)
-        *reinterpret_cast<float4*>(part + (size_t)(seg3 * R + t) * L.ldx + 4 * q3) =
-            make_float4(acc[0][t], acc[1][t], acc[2][t], acc[3][t]);
-    }
-    __syncthreads();
-    if (rowwarp) {
-      // Rp: Y Rp = P (Y = P Rp^{-1} is never formed inside the loop)
-      gram_from_pairs<R>(redA, np, L.nw, Gw);
-      warp_chol<R>(Gw, R, Rpw, dRp);
-      float e2 = 0.f;
-#pragma unroll
-      for (int t = 0; t < R; ++t) qv[t] = 0.f;
-      if (tid < nJ) {
-        float m[R], xr[R];
-#pragma unroll
-        for (int t = 0; t < R; ++t) {
-          float v = 0.f;
-          for (int s = 0; s < L.s3; ++s) v += part[(size_t)(s * R + t) * L.ldx + tid];
-          m[t] = v;
-          xr[t] = X[(size_t)t * L.ldx + tid];
-        }
-        row_subst<R>(m, qv, Rpw, dRp);  // Q = core^T Y
-#pragma unroll
-        for (int t = 0; t < R; ++t) {
-          float v = qv[t];
-#pragma unroll
-          for (int s2 = t; s2 < R; ++s2) v = fmaf(-xr[s2], Rpw[t * R + s2], v);
-          e2 = fmaf(v, v, e2);
-        }
-      }
-      warp_pair_sums<R>(qv, redB + warp * np);
-      e2 = warp_sum(e2);
-      if (lane == 0) redE[warp] = e2;
-    }
-    __syncthreads();
-    // the same decision in every thread: sums over the row warps in order
-    float E2 = 0.f, RC2 = 0.f;
-    for (int w = 0; w < L.nw; ++w) E2 += redE[w];
-#pragma unroll
-    for (int t = 0; t < R; ++t) {
-      const int pd = t * R - t * (t - 1) / 2;  // pair (t, t)
-      float g = 0.f;
-      for (int w = 0; w < L.nw; ++w) g += redA[w * np + pd];
-      RC2 += g;  // ||Rp||_F^2 = trace Gram(P)
-    }
-    const float res = sqrtf(E2), nrm = sqrtf(RC2);
-    if (res <= 1e-6f * nrm || (steps > 1 && res > 0.5f * prev_res && res <= 1e-5f * nrm) || !(nrm > 0.f)) {
-      converged = true;
-      break;
-    }
-    if (steps >= d.svdMaxSteps) break;  // keep X, P, Rp of the same step
-    prev_res = res;
-    if (rowwarp) {
-      gram_from_pairs<R>(redB, np, L.nw, Gw);
-      warp_chol<R>(Gw, R, Uqw, dUq);
-      if (tid < nJ) {
-        float y[R];
-        row_subst<R>(qv, y, Uqw, dUq);
-#pragma unroll
-        for (int t = 0; t < R; ++t) X[(size_t)t * L.ldx + tid] = y[t];
-      }
-    }
-    __syncthreads();
-  }
-
-  // ---- Y = P Rp^{-1}; second CholQR passes of Y and X; T = U2y Rp U2x^{-1}
-  float yv[R], xv[R];
-  if (rowwarp) {
-    {
-      float m[R];
-#pragma unroll
-      for (int t = 0; t < R; ++t) m[t] = (tid < nI) ? P[(size_t)tid * L.ps + t] : 0.f;
-      row_subst<R>(m, yv, Rpw, dRp);
-    }
-#pragma unroll
-    for (int t = 0; t < R; ++t) xv[t] = (tid < nJ) ? X[(size_t)t * L.ldx + tid] : 0.f;
-    warp_pair_sums<R>(yv, redA + warp * np);
-    warp_pair_sums<R>(xv, redB + warp * np);
-  }
-  __syncthreads();
-  if (rowwarp) {
-    gram_from_pairs<R>(redA, np, L.nw, Gw);
-    warp_chol<R>(Gw, R, Uqw, dUq);  // U2y
-    gram_from_pairs<R>(redB, np, L.nw, Gw);
-    warp_chol<R>(Gw, R, U2x, dU2x);
-    if (lane < R) {
-      const int s2 = lane;
-      float row[R];  // (U2y Rp)(s2, :)
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        float v = 0.f;
-#pragma unroll
-        for (int u = 0; u < R; ++u) v = fmaf(Uqw[s2 * R + u], Rpw[u * R + t], v);
-        row[t] = v;
-      }
-      float tr[R];  // T(s2,:) U2x = row (forward substitution; dropped pivots give zeros)
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        float v = row[t];
-#pragma unroll
-        for (int u = 0; u < t; ++u) v = fmaf(-tr[u], U2x[u * R + t], v);
-        tr[t] = v * dU2x[t];
-      }
-#pragma unroll
-      for (int t = 0; t < R; ++t) Tw[s2 * R + t] = tr[t];
-    }
-    __syncwarp();
-    // numerical rank from the diagonal of T, and T^{-1} on the kept pivots
-    const float dabs = lane < R ? fabsf(Tw[lane * R + lane]) : 0.f;
-    float dmax = dabs;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    const float tol = (float)(nI > nJ ? nI : nJ) * FLT_EPSILON * dmax;
-    const bool keep = lane < R && dabs > tol && dabs > 0.f;
-    const unsigned kmask = __ballot_sync(0xffffffffu, keep);
-    if (lane < R) {
-      const int c = lane;
-      float x[R];
-#pragma unroll
-      for (int s2 = R - 1; s2 >= 0; --s2) {
-        float v = 0.f;
-        if (s2 <= c && ((kmask >> s2) & 1u)) {
-          v = (s2 == c) ? 1.f : 0.f;
-#pragma unroll
-          for (int u = s2 + 1; u < R; ++u)
-            if (u <= c) v = fmaf(-Tw[s2 * R + u], x[u], v);
-          v = v / Tw[s2 * R + s2];
-        }
-        x[s2] = v;
-      }
-#pragma unroll
-      for (int s2 = 0; s2 < R; ++s2) Utw[s2 * R + c] = x[s2];
-    }
-    __syncwarp();
-    // outputs (U^+ = X T^{-1} Y^T): W = Y; Vs = X T^{-1}; V = X T^T
-    if (tid < nI) {
-      float y2[R];
-      row_subst<R>(yv, y2, Uqw, dUq);
-#pragma unroll
-      for (int t = 0; t < R; ++t) d.W[(size_t)tid * R + t] = ((kmask >> t) & 1u) ? y2[t] : 0.f;
-    }
-    if (tid < nJ) {
-      float x2[R];
-      row_subst<R>(xv, x2, U2x, dU2x);
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        float vp = 0.f, vr = 0.f;
-#pragma unroll
-        for (int s2 = 0; s2 < R; ++s2) {
-          vp = fmaf(x2[s2], Utw[s2 * R + t], vp);
-          vr = fmaf(x2[s2], Tw[t * R + s2], vr);
-        }
-        const bool kt = (kmask >> t) & 1u;
-        d.Vs[(size_t)tid * R + t] = kt ? vp : 0.f;
-        d.V[(size_t)tid * R + t] = kt ? vr : 0.f;
-      }
-    }
-    if (warp == 0) {
-      if (lane < R) d.sigma[lane] = keep ? dabs : 0.f;
-      for (int q = lane; q < R * R; q += 32) d.Tm[q] = Tw[q];
-      if (lane == 0) {
-        unsigned f = 0u;
-        if (__popc(kmask) < R) f |= IRCUR_FLAG_WRANK;
-        if (!converged) f |= IRCUR_FLAG_SVD_NOCONV;
-        if (f) atomicOr(&st->flags, f);
-        st->svd_steps += steps;
-        st->svd_last_steps = steps;
-      }
-    }
-  }
-  if (d.trace) {
-    __syncthreads();
-    trace_stop(d.trace, 3 * d.max_iter, 3 * k + 1);
-  }
-}
-
-template <int R>
-__global__ void __launch_bounds__(kSsvdThreads, 1) ssvd_kernel(IterDesc d) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  pdl_launch_dependents();
-  ssvd_body<R>(d, blockIdx.y, smem);
-}
-
-// Batched form: block x factorises instance list[x]; blockIdx.y is the role.
-template <int R>
-__global__ void __launch_bounds__(kSsvdThreads, 1) ssvd_batch_kernel(const IterDesc* __restrict__ ds,
-                                                                    const int* __restrict__ list) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  pdl_launch_dependents();
-  ssvd_body<R>(ds[list[blockIdx.x]], blockIdx.y, smem);
+// Cluster size of the core SVD: one CTA where the caller asked for it and the
+// whole core fits one SM; else 8 CTAs (16 where the slabs of 8 do not fit).
+// 0: no form fits.
+int svd_cluster_size(int nI, int nJ, int Rpad, int svd_form) {
+  if (svd_form == IRCUR_SVD_ONE_CTA && svd_fits(nI, nJ, Rpad, 1)) return 1;
+  if (svd_fits(nI, nJ, Rpad, kSvdCluster)) return kSvdCluster;
+  if (svd_fits(nI, nJ, Rpad, 16)) return 16;
+  return 0;
 }
 
 template <typename... Args>
-static cudaError_t launch_cluster(void (*kernel)(Args...), dim3 grid, size_t smem, cudaStream_t s,
-                                  Args... args) {
+static cudaError_t launch_svd_grid(void (*kernel)(Args...), int nc, dim3 grid, size_t smem, cudaStream_t s,
+                                   Args... args) {
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   // the largest shared-memory carveout on the SVD's SMs, so that the pass
   // blocks launched while it runs fit next to it
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess && nc > 8) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
   memset(&cfg, 0, sizeof(cfg));
   cfg.gridDim = grid;
-  cfg.blockDim = dim3(kCsvdThreads, 1, 1);
+  cfg.blockDim = dim3(nc == 1 ? kSvdThreadsOne : kSvdThreadsCl, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kSvdCluster;
+  attr[0].val.clusterDim.x = (unsigned)nc;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = nc > 1 ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 template <int R>
-static cudaError_t launch_csvd_r(const IterDesc& d, cudaStream_t s) {
-  const size_t bytes = csvd_smem_bytes(d.nI, d.nJ, R);
-  return launch_cluster(csvd_kernel<R>, dim3(kSvdCluster, 1 + (d.sampleAhead ? 2 : 0), 1), bytes, s, d);
-}
-
-template <int R>
-static cudaError_t launch_csvd_batch_r(const BatchLaunch& b, cudaStream_t s) {
-  const int n = b.svd_n[1];
-  if (n == 0) return cudaSuccess;
-  return launch_cluster(csvd_batch_kernel<R>, dim3(kSvdCluster * n, b.svd_roles, 1), b.svd_smem[1], s, b.ds,
-                        b.svd_list[1]);
-}
-
-template <int R>
-static cudaError_t launch_ssvd_r(const IterDesc& d, cudaStream_t s) {
-  if constexpr (R > kSsvdMaxR) {
-    return cudaErrorInvalidValue;
-  } else {
-    const size_t bytes = ssvd_smem_bytes(d.nI, d.nJ, R);
-    cudaError_t e = cudaFuncSetAttribute(ssvd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ssvd_kernel<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               (int)cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-    ssvd_kernel<R><<<dim3(1, 1 + (d.sampleAhead ? 2 : 0), 1), kSsvdThreads, bytes, s>>>(d);
-    return cudaGetLastError();
-  }
-}
-
-template <int R>
-static cudaError_t launch_ssvd_batch_r(const BatchLaunch& b, cudaStream_t s) {
-  if constexpr (R > kSsvdMaxR) {
-    return b.svd_n[0] ? cudaErrorInvalidValue : cudaSuccess;
-  } else {
-    const int n = b.svd_n[0];
-    if (n == 0) return cudaSuccess;
-    cudaError_t e =
-        cudaFuncSetAttribute(ssvd_batch_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.svd_smem[0]);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ssvd_batch_kernel<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               (int)cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-    ssvd_batch_kernel<R><<<dim3(n, b.svd_roles, 1), kSsvdThreads, b.svd_smem[0], s>>>(b.ds, b.svd_list[0]);
-    return cudaGetLastError();
-  }
-}
-
-template <int R>
-static cudaError_t launch_sigma_r(const float* Tm, int r, float* sigma, cudaStream_t s) {
-  sigma_kernel<R><<<1, 32, 0, s>>>(Tm, r, sigma);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_sigma(const float* Tm, int r, int Rpad, float* sigma, cudaStream_t s) {
-  switch (Rpad) {
-    case 1: return launch_sigma_r<1>(Tm, r, sigma, s);
-    case 2: return launch_sigma_r<2>(Tm, r, sigma, s);
-    case 3: return launch_sigma_r<3>(Tm, r, sigma, s);
-    case 4: return launch_sigma_r<4>(Tm, r, sigma, s);
-    case 5: return launch_sigma_r<5>(Tm, r, sigma, s);
-    case 6: return launch_sigma_r<6>(Tm, r, sigma, s);
-    case 7: return launch_sigma_r<7>(Tm, r, sigma, s);
-    case 8: return launch_sigma_r<8>(Tm, r, sigma, s);
-    case 9: return launch_sigma_r<9>(Tm, r, sigma, s);
-    case 10: return launch_sigma_r<10>(Tm, r, sigma, s);
-    case 12: return launch_sigma_r<12>(Tm, r, sigma, s);
-    case 16: return launch_sigma_r<16>(Tm, r, sigma, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-template <int R>
 static cudaError_t launch_svd_r(const IterDesc& d, cudaStream_t s) {
-  if (d.svdOneCta) return launch_ssvd_r<R>(d, s);
-  return launch_csvd_r<R>(d, s);
+  const int nc = d.svdNC;
+  const size_t bytes = svd_smem_bytes(d.nI, d.nJ, R, nc);
+  const dim3 grid((unsigned)nc, d.resample ? 3 : 1, 1);
+  if (nc == 1) return launch_svd_grid(ssvd_kernel<R>, 1, grid, bytes, s, d);
+  return launch_svd_grid(csvd_kernel<R>, nc, grid, bytes, s, d);
 }
 
 template <int R>
 static cudaError_t launch_svd_batch_r(const BatchLaunch& b, cudaStream_t s) {
-  cudaError_t e = launch_ssvd_batch_r<R>(b, s);
-  if (e != cudaSuccess) return e;
-  return launch_csvd_batch_r<R>(b, s);
+  for (int f = 0; f < 3; ++f) {
+    const int n = b.svd_n[f];
+    if (n == 0) continue;
+    const int nc = f == 0 ? 1 : (f == 1 ? kSvdCluster : 16);
+    const dim3 grid((unsigned)(nc * n), (unsigned)b.svd_roles, 1);
+    cudaError_t e = nc == 1 ? launch_svd_grid(ssvd_batch_kernel<R>, 1, grid, b.svd_smem[f], s, b.ds, b.svd_list[f])
+                            : launch_svd_grid(csvd_batch_kernel<R>, nc, grid, b.svd_smem[f], s, b.ds, b.svd_list[f]);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_svd_batch(const BatchLaunch& b, int Rpad, cudaStream_t s) {

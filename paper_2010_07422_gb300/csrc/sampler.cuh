@@ -68,8 +68,10 @@ __device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned* w
 __device__ __forceinline__ uint64_t sample_key(uint64_t base, int64_t i) { return splitmix64(base ^ (uint64_t)i); }
 
 // Whole block: out[0..m) = the selected indices of draw (seed, draw, axis),
-// 1 <= m <= n < 2^31.
-__device__ inline void sample_subset(uint64_t seed, int draw, int axis, int64_t n, int m, int* out, SamplerSmem& S) {
+// 1 <= m <= n < 2^31.  With a map (n entries), map[out[a]] = index_tag(tag, a)
+// for every a: the position of each selected index, tagged with its draw.
+__device__ inline void sample_subset(uint64_t seed, int draw, int axis, int64_t n, int m, int* out, SamplerSmem& S,
+                                     unsigned* map = nullptr, unsigned tag = 0) {
   const uint64_t base = splitmix64(splitmix64(seed) ^ (uint64_t)(2 * draw + axis));
   const int NT = blockDim.x, tid = threadIdx.x;
   if (tid == 0) {
@@ -153,7 +155,11 @@ __device__ inline void sample_subset(uint64_t seed, int draw, int axis, int64_t 
   unsigned pos = block_exclusive_scan(cnt, S.warp_tot, &S.total);
   for (int64_t i = lo; i < hi; ++i) {
     const uint64_t key = sample_key(base, i);
-    if (((key < tkey) || (key == tkey && i <= tidx)) && pos < (unsigned)m) out[pos++] = (int)i;
+    if (((key < tkey) || (key == tkey && i <= tidx)) && pos < (unsigned)m) {
+      out[pos] = (int)i;
+      if (map) map[i] = index_tag(tag, (int)pos);
+      ++pos;
+    }
   }
   __syncthreads();
 }

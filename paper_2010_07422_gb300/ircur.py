@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libircur.so")
 
 IRCUR_OK, IRCUR_EINVAL, IRCUR_ENOMEM, IRCUR_ECUDA = 0, 1, 2, 3
 IRCUR_ESVD_NOCONV, IRCUR_ETIMEOUT, IRCUR_ESTATE, IRCUR_ENOTSUP = 4, 5, 6, 7
-IRCUR_FLAG_WRANK, IRCUR_FLAG_SVD_NOCONV = 1, 2
+IRCUR_FLAG_WRANK, IRCUR_FLAG_SVD_NOCONV, IRCUR_FLAG_SVD_GAP = 1, 2, 4
 IRCUR_MAX_RANK = 16
 IRCUR_PRECISION_FP32, IRCUR_PRECISION_BF16_PANELS = 0, 1
 IRCUR_SVD_CLUSTER, IRCUR_SVD_ONE_CTA = 0, 1
@@ -200,11 +200,12 @@ def ircur_set_trace(ctx, enable):
 
 
 def ircur_get_trace(ctx, max_iter):
-    """Per-iteration kernel spans (us) of the last traced solve: list of (core, svd, pass)."""
-    buf = (C.c_double * (3 * max_iter))()
+    """Per-iteration kernel spans (us) of the last traced solve: list of
+    (core Phase I, core SVD, panel pass, panel pass after its wait for the SVD)."""
+    buf = (C.c_double * (4 * max_iter))()
     cnt = C.c_int32()
     _check(_lib().ircur_get_trace(ctx, buf, C.byref(cnt)), "ircur_get_trace")
-    return [(buf[3 * k], buf[3 * k + 1], buf[3 * k + 2]) for k in range(cnt.value)]
+    return [tuple(buf[4 * k + q] for q in range(4)) for k in range(cnt.value)]
 
 
 def ircur_solve_noalloc(params: ircur_params, D, ldD, A, B, stream=None):
@@ -286,6 +287,7 @@ class IRCUR:
         self.nI = nI if nI else sample_size(4, r, n1)
         self.nJ = nJ if nJ else sample_size(4, r, n2)
         self.last = None
+        self.solves = 0  # solves issued through this handle (ircur_unrolled checks it)
 
     @classmethod
     def _view(cls, ctx, p, stream, owner):
@@ -295,6 +297,7 @@ class IRCUR:
         self.nI = p.nI if p.nI else sample_size(4, p.r, p.n1)
         self.nJ = p.nJ if p.nJ else sample_size(4, p.r, p.n2)
         self.last = None
+        self.solves = 0
         return self
 
     def close(self):
@@ -313,6 +316,7 @@ class IRCUR:
 
     def solve(self, D, idx_I=None, idx_J=None):
         assert D.is_cuda and D.dtype.itemsize == 4 and D.stride(1) == 1
+        self.solves += 1
         r = ircur_solve(self._ctx, D, D.stride(0), idx_I, idx_J)
         self.last = Result(r.iters, bool(r.converged), r.flags, r.svd_steps, r.final_err, r.zeta0,
                            r.zeta_next)
@@ -414,11 +418,16 @@ def _make_function():
             solver.solve(D)
             L, S = solver.reconstruct(D)
             ctx.solver = solver
+            ctx.generation = solver.solves
             ctx.save_for_backward(D)
             return L, S
 
         @staticmethod
         def backward(ctx, dL, dS):
+            if ctx.solver.solves != ctx.generation:
+                # the solver's recording now belongs to a later solve
+                raise IrcurError(IRCUR_ESTATE, "ircur_unrolled backward: the solver ran another solve "
+                                                "after this forward")
             (D,) = ctx.saved_tensors
             dL = dL.contiguous() if dL is not None else None
             dS = dS.contiguous() if dS is not None else None

@@ -94,6 +94,43 @@ def test_backward_at_training_size_properties():
     s.close()
 
 
+def test_backward_at_training_size_matches_oracle():
+    """The unrolled-training shape itself: n = 4096, r = 10, T = 15 (|I| = |J| = 333),
+    alpha = 0.1, cotangents for L and S: the GPU gradient against the FP64 oracle
+    gradient, entry for entry, in relative Frobenius norm."""
+    n, r, T, seed = 4096, 10, 15, 11
+    p, D, s, res, I, J = setup(n, n, r, T, 0.1, seed)
+    assert res.iters == T and res.flags == 0
+    rng = np.random.default_rng(seed)
+    dL = rng.standard_normal((n, n)).astype(np.float32)
+    dS = rng.standard_normal((n, n)).astype(np.float32)
+    g = s.backward(D, torch.from_numpy(dL).cuda(), torch.from_numpy(dS).cuda())
+    torch.cuda.synchronize()
+    gn = g.double().cpu().numpy()
+    s.close()
+    G = adj.unrolled_vjp(p.D.astype(np.float64), I, J, r, res.zeta0, 0.7, T, dL, dS)
+    assert rel(gn, G) <= TOL_GRAD, rel(gn, G)
+
+
+def test_backward_after_another_solve_is_refused():
+    """The autograd Function holds the solver, whose recording belongs to its last
+    solve: a solve between forward and backward makes backward raise ESTATE
+    instead of differentiating the other solve."""
+    n1, n2, r = 300, 280, 3
+    p = synth.planted(n1, n2, r, 0.1, seed=41)
+    D = torch.from_numpy(p.D).cuda().requires_grad_(True)
+    s = ir.IRCUR(n1, n2, r, tol=1e-12, max_iter=5, resample=False, seed=41)
+    L, S = ir.ircur_unrolled(D, s)
+    s.solve(D.detach() * 2.0)
+    with pytest.raises(ir.IrcurError) as e:
+        (L.sum() + S.sum()).backward()
+    assert e.value.status == ir.IRCUR_ESTATE
+    L2, S2 = ir.ircur_unrolled(D, s)  # a fresh forward differentiates again
+    (L2.sum() + S2.sum()).backward()
+    assert torch.isfinite(D.grad).all()
+    s.close()
+
+
 def test_autograd_function_matches_direct_backward():
     n1, n2, r = 400, 380, 4
     p = synth.planted(n1, n2, r, 0.1, seed=21)
