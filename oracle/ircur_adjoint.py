@@ -35,8 +35,14 @@ def _ht(X, zeta):
     return X * (X.abs() > zeta).to(X.dtype)
 
 
-def unrolled_forward(D, I, J, r, zeta0, gamma, T):
-    """(L_T, S_T) of the T-step fixed-index map above (torch FP64 tensors)."""
+def unrolled_forward(D, I, J, r, zeta0, gamma, T, final_keep=None):
+    """(L_T, S_T) of the T-step fixed-index map above (torch FP64 tensors).
+
+    final_keep (optional boolean n1 x n2 array) replaces the decisions
+    |D - L_T| > zeta_T of the last threshold: the tie reading of T_zeta
+    (Sec. 3.2), where an entry within rounding of zeta may go either way and a
+    caller supplies the side another evaluation took.  The caller checks that
+    it differs from the FP64 decisions only at such ties."""
     I = torch.as_tensor(np.asarray(I, np.int64))
     J = torch.as_tensor(np.asarray(J, np.int64))
     n1, n2 = D.shape
@@ -51,14 +57,18 @@ def unrolled_forward(D, I, J, r, zeta0, gamma, T):
         U_pinv = Vh[:r, :].T @ torch.diag(1.0 / s[:r]) @ W[:, :r].T
         L = C @ U_pinv @ R
         zeta = zeta * gamma
-    S = _ht(D - L, zeta)
+    if final_keep is None:
+        S = _ht(D - L, zeta)
+    else:
+        S = (D - L) * torch.as_tensor(np.asarray(final_keep, bool)).to(D.dtype)
     return L, S
 
 
-def unrolled_vjp(D, I, J, r, zeta0, gamma, T, dL=None, dS=None):
-    """dD = d<dL, L_T> / dD + d<dS, S_T> / dD at D (numpy FP64 in and out)."""
+def unrolled_vjp(D, I, J, r, zeta0, gamma, T, dL=None, dS=None, final_keep=None):
+    """dD = d<dL, L_T> / dD + d<dS, S_T> / dD at D (numpy FP64 in and out);
+    final_keep as in unrolled_forward."""
     Dt = torch.tensor(np.asarray(D, np.float64), requires_grad=True)
-    L, S = unrolled_forward(Dt, I, J, r, zeta0, gamma, T)
+    L, S = unrolled_forward(Dt, I, J, r, zeta0, gamma, T, final_keep)
     loss = torch.zeros((), dtype=torch.float64)
     if dL is not None:
         loss = loss + (torch.as_tensor(np.asarray(dL, np.float64)) * L).sum()

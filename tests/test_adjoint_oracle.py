@@ -107,3 +107,32 @@ def test_one_step_without_outliers_is_the_cur_formula():
     assert np.allclose(G[I, j], want, rtol=1e-10, atol=1e-12)
     rows_not_I = np.setdiff1d(np.arange(D.shape[0]), I)
     assert np.all(G[rows_not_I, j] == 0.0)
+
+
+def test_final_keep_override():
+    """final_keep replaces the last threshold's decisions only: with the FP64
+    decisions themselves nothing changes; with one entry (i, j) outside rows I and
+    columns J flipped, the gradient there becomes the flipped mask times dS_ij
+    (D_ij enters the map nowhere else) and the L output is unchanged."""
+    D, I, J = _case()
+    r, T, g = 3, 5, 0.7
+    z0 = float(np.abs(D).max())
+    rng = np.random.default_rng(8)
+    dL = rng.standard_normal(D.shape)
+    dS = rng.standard_normal(D.shape)
+    keep = adj.masks(D, I, J, r, z0, g, T)[-1]
+    G = adj.unrolled_vjp(D, I, J, r, z0, g, T, dL, dS)
+    assert np.allclose(adj.unrolled_vjp(D, I, J, r, z0, g, T, dL, dS, final_keep=keep), G, rtol=0, atol=1e-12)
+    rows = np.setdiff1d(np.arange(D.shape[0]), I)
+    cols = np.setdiff1d(np.arange(D.shape[1]), J)
+    i, j = int(rows[1]), int(cols[2])
+    flipped = keep.copy()
+    flipped[i, j] = not keep[i, j]
+    G2 = adj.unrolled_vjp(D, I, J, r, z0, g, T, dL, dS, final_keep=flipped)
+    assert G[i, j] == (dS[i, j] if keep[i, j] else 0.0)
+    assert G2[i, j] == (dS[i, j] if flipped[i, j] else 0.0)
+    with torch.no_grad():
+        L1, _ = adj.unrolled_forward(torch.tensor(D), I, J, r, z0, g, T)
+        L2, S2 = adj.unrolled_forward(torch.tensor(D), I, J, r, z0, g, T, flipped)
+    assert torch.equal(L1, L2)
+    assert bool(S2[i, j] != 0) == bool(flipped[i, j])
