@@ -609,14 +609,17 @@ def main():
     fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12  # TFLOP/s: SMs x FP32 lanes x FMA x max SM clock
     svd_avg_us = float(np.mean(svd_us))
     svd_ach = svd_flops / (svd_avg_us * 1e-6) / 1e12
-    nc_svd = 8
+    nc_svd, pass_blocks, pass_bufs = ir.ircur_get_launch_shape(solver._ctx)
     roof_svd = {"kernel": "csvd_kernel", "bound": "alu", "achieved": svd_ach, "peak": fp32_peak,
                 "unit": "TFLOP/s", "frac": svd_ach / fp32_peak, "traffic": dram_traffic("csvd_kernel", f"n{n}_r{r}"),
-                "peak_source": "FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (one 8-CTA cluster by "
-                               "design: its share is 8/152 of this)",
+                "peak_source": f"FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (one {nc_svd}-CTA "
+                               f"cluster by design: its share is {nc_svd}/152 of this)",
+                "cluster_ctas": nc_svd,
                 "algorithmic_flops_per_launch": svd_flops, "avg_launch_us": svd_avg_us,
                 "half_steps_per_launch": hsteps,
-                "frac_of_its_8_sms": svd_ach / (fp32_peak * nc_svd / 152)}
+                "frac_of_its_sms": svd_ach / (fp32_peak * nc_svd / 152)}
+    roof_pass["grid_blocks"] = pass_blocks
+    roof_pass["tile_buffers"] = pass_bufs
     roofs = {"recon_vec_kernel": roof_recon, "pass_kernel": roof_pass, "csvd_kernel": roof_svd}
     # the kernel that takes the most of a step: the pass counts with the time it
     # adds after the SVD (its earlier part overlaps the SVD)

@@ -70,13 +70,15 @@ typedef enum {
  * H_r (Sec. 3.1) run on the GPU.  Both forms run the same subspace iteration
  * with the same stopping rule; their results agree to FP32 rounding, not bit
  * for bit.
- * CLUSTER: one thread-block cluster of 8 CTAs per core (16 where the core's
- *   slabs of 8 do not fit), each CTA holding a slab of the core's rows and one
- *   of its columns (the faster form for one solve).
+ * CLUSTER: one thread-block cluster of 16 CTAs per core where the device runs
+ *   clusters of 16 (a non-portable size, asked once per device), else of 8;
+ *   each CTA holds a slab of the core's rows and one of its columns (the
+ *   faster form for one solve).  The choice depends only on the shape and the
+ *   device, so a batch instance runs the same form as a lone solve.
  * ONE_CTA: one CTA of 512 threads per core, the whole core in its shared
  *   memory, where that fits (about |I|, |J| <= 220 at r <= 8); the cluster form
  *   elsewhere.  Batches of many instances run faster with it (one SM per
- *   instance instead of eight). */
+ *   instance instead of sixteen). */
 #define IRCUR_SVD_CLUSTER 0
 #define IRCUR_SVD_ONE_CTA 1
 
@@ -163,6 +165,15 @@ ircur_status ircur_get_cur(ircur_ctx* ctx, const float* D, int64_t ldD, float* C
  * host array errs (room for max_iter doubles); synchronises.  Returns the
  * count in *count.  ESTATE before the first solve. */
 ircur_status ircur_get_errors(ircur_ctx* ctx, double* errs, int32_t* count);
+
+/* The launch shape the context's iterations run with (no counterpart in the
+ * paper; for benchmarks and reports): *svd_ctas = CTAs of one core SVD (1 for
+ * the one-CTA form, else the cluster size, 8 or 16), *pass_blocks = blocks of
+ * one panel-pass launch (the autotuned grid, else every block that fits the
+ * GPU at once, at most one per tile), *pass_bufs = the pass's tile staging
+ * buffers per block (1 or 2).  Any output pointer may be NULL.  EINVAL for a
+ * NULL ctx; ECUDA if the device query fails. */
+ircur_status ircur_get_launch_shape(ircur_ctx* ctx, int32_t* svd_ctas, int32_t* pass_blocks, int32_t* pass_bufs);
 
 /* Write the dense low-rank part L = C U^+ R of the last solve into L (device,
  * n1 x n2, ldL >= n2) and, if S is not NULL, the sparse part

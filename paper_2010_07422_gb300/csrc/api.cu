@@ -142,7 +142,7 @@ static ircur_status validate_params(const ircur_params* p, ircur_params* out) {
   if (q.precision == IRCUR_PRECISION_BF16_PANELS && q.resample != 0) return IRCUR_ENOTSUP;
   if (pass_smem_bytes(q.nI, q.nJ, pad_rank(q.r), nullptr, q.precision != 0) > 227 * 1024) return IRCUR_ENOTSUP;
   if (q.svd_form != IRCUR_SVD_CLUSTER && q.svd_form != IRCUR_SVD_ONE_CTA) return IRCUR_EINVAL;
-  if (svd_cluster_size(q.nI, q.nJ, pad_rank(q.r), q.svd_form) == 0) return IRCUR_ENOTSUP;
+  if (!svd_shape_ok(q.nI, q.nJ, pad_rank(q.r), q.svd_form)) return IRCUR_ENOTSUP;
   if (!(q.gamma > 0.0 && q.gamma < 1.0)) return IRCUR_EINVAL;
   if (!(q.tol > 0.0)) return IRCUR_EINVAL;
   if (q.max_iter < 1) return IRCUR_EINVAL;
@@ -179,6 +179,10 @@ static ircur_status create_impl(const ircur_params* params, void* stream, int mi
   IterDesc& d = c->desc;
   memset(&d, 0, sizeof(d));
   d.svdNC = svd_cluster_size(p.nI, p.nJ, R, p.svd_form);
+  if (d.svdNC == 0) {  // only a cluster of 16 fits and this device runs none
+    delete c;
+    return IRCUR_ENOTSUP;
+  }
   d.nRowTiles = (int)((n2 + kPanelCols - 1) / kPanelCols);
   d.nColTiles = (int)((n1 + kPanelCols - 1) / kPanelCols);
 
@@ -769,6 +773,23 @@ extern "C" ircur_status ircur_get_errors(ircur_ctx* c, double* errs, int32_t* co
   if (K > 0) IRCUR_CK(cudaMemcpyAsync(errs, c->errs, (size_t)K * 8, cudaMemcpyDeviceToHost, c->stream));
   IRCUR_CK(cudaStreamSynchronize(c->stream));
   *count = K;
+  return IRCUR_OK;
+}
+
+extern "C" ircur_status ircur_get_launch_shape(ircur_ctx* c, int32_t* svd_ctas, int32_t* pass_blocks,
+                                               int32_t* pass_bufs) {
+  if (!c) return IRCUR_EINVAL;
+  const IterDesc& d = c->desc;
+  if (svd_ctas) *svd_ctas = d.svdNC;
+  int nbuf = 1;
+  pass_smem_bytes(d.nI, d.nJ, c->Rpad, &nbuf, d.bf16 != 0, d.passSingleBuf != 0);
+  if (pass_bufs) *pass_bufs = nbuf;
+  if (pass_blocks) {
+    int g = d.passGrid > 0 ? d.passGrid : pass_resident_blocks(d, c->Rpad);
+    if (g <= 0) return IRCUR_ECUDA;
+    const int total = d.nRowTiles + d.nColTiles;
+    *pass_blocks = g < total ? g : total;
+  }
   return IRCUR_OK;
 }
 

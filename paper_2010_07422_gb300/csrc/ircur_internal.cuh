@@ -239,11 +239,16 @@ size_t cur_to_svd_scratch_bytes(int64_t n1, int64_t n2, int Rpad);
 cudaError_t launch_cur_to_svd(const float* A, const float* B, int64_t n1, int64_t n2, int r, int Rpad, void* scratch,
                               float* W, float* sigma, float* V, cudaStream_t s);
 // Core SVD (k_svd.cu): dynamic shared memory per CTA for a cluster of nc CTAs,
-// whether it fits one SM, and the cluster size a problem runs with (1 for the
-// one-CTA form where it fits, else 8 or 16; 0 if no form fits).
+// whether it fits one SM, the cluster size a problem runs with on the current
+// device (1 for the one-CTA form where it fits, else 16 or 8; 0 if no form
+// fits), and whether some form fits at all (shape only, no CUDA call).
 size_t svd_smem_bytes(int nI, int nJ, int Rpad, int nc);
 bool svd_fits(int nI, int nJ, int Rpad, int nc);
 int svd_cluster_size(int nI, int nJ, int Rpad, int svd_form);
+bool svd_shape_ok(int nI, int nJ, int Rpad, int svd_form);
+// Clusters of 16 CTAs of the largest core-SVD configuration the current device
+// holds at once (k_svd_ranks_16.cu).
+int svd_cluster16_capacity();
 // Singular values of the last core from its T (k_svd.cu), on request.
 cudaError_t launch_sigma(const float* Tm, int r, int Rpad, float* sigma, cudaStream_t s);
 // D(I,J) of draw `draw` into the compact buffers [buf] (k_setup.cu).

@@ -3,6 +3,8 @@
 // rank.  The kernels are in svd_kernels.cuh; each rank's launch is
 // instantiated in one of the k_svd_ranks_*.cu files, so that they compile in
 // parallel.
+#include <mutex>
+
 #include "svd_kernels.cuh"
 
 namespace ircur {
@@ -67,14 +69,36 @@ size_t svd_smem_bytes(int nI, int nJ, int Rpad, int nc) {
 
 bool svd_fits(int nI, int nJ, int Rpad, int nc) { return svd_smem_bytes(nI, nJ, Rpad, nc) <= 227 * 1024; }
 
+// Whether the device runs clusters of 16 CTAs (a non-portable size) of the
+// core SVD in its largest configuration (227 KB of shared memory per CTA):
+// asked once per device.
+static bool cluster16_ok() {
+  static std::mutex mu;
+  static signed char known[64];  // 0: not asked yet, 1: yes, -1: no
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return false;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (known[dev] == 0) known[dev] = svd_cluster16_capacity() > 0 ? 1 : -1;
+  return known[dev] > 0;
+}
+
 // Cluster size of the core SVD: one CTA where the caller asked for it and the
-// whole core fits one SM; else 8 CTAs (16 where the slabs of 8 do not fit).
+// whole core fits one SM; else 16 CTAs where the device runs clusters of 16
+// (half the slab work per CTA for one more level of the exchange), else 8.
 // 0: no form fits.
 int svd_cluster_size(int nI, int nJ, int Rpad, int svd_form) {
   if (svd_form == IRCUR_SVD_ONE_CTA && svd_fits(nI, nJ, Rpad, 1)) return 1;
+  if (svd_fits(nI, nJ, Rpad, 16) && cluster16_ok()) return 16;
   if (svd_fits(nI, nJ, Rpad, kSvdCluster)) return kSvdCluster;
-  if (svd_fits(nI, nJ, Rpad, 16)) return 16;
   return 0;
+}
+
+bool svd_shape_ok(int nI, int nJ, int Rpad, int svd_form) {
+  if (svd_form == IRCUR_SVD_ONE_CTA && svd_fits(nI, nJ, Rpad, 1)) return true;
+  return svd_fits(nI, nJ, Rpad, kSvdCluster) || svd_fits(nI, nJ, Rpad, 16);
 }
 
 cudaError_t launch_svd_batch(const BatchLaunch& b, int Rpad, cudaStream_t s) {

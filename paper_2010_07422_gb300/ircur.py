@@ -28,7 +28,7 @@ EXPORTED = (
     "ircur_status_string", "ircur_last_error_string", "ircur_solve_noalloc", "ircur_set_trace",
     "ircur_get_trace", "ircur_get_cur", "ircur_batch_create", "ircur_batch_destroy", "ircur_batch_solve",
     "ircur_batch_instance", "ircur_set_record", "ircur_backward", "ircur_autotune", "ircur_batch_autotune",
-    "ircur_get_svd", "ircur_stream_columns",
+    "ircur_get_svd", "ircur_stream_columns", "ircur_get_launch_shape",
 )
 
 
@@ -82,6 +82,7 @@ def _lib():
         lib.ircur_get_factors.argtypes = [P, P, P]
         lib.ircur_get_indices.argtypes = [P, P, P, P]
         lib.ircur_get_errors.argtypes = [P, C.POINTER(C.c_double), C.POINTER(I32)]
+        lib.ircur_get_launch_shape.argtypes = [P, C.POINTER(I32), C.POINTER(I32), C.POINTER(I32)]
         lib.ircur_reconstruct.argtypes = [P, P, I64, P, I64, P, I64]
         lib.ircur_solve_host.argtypes = [P, P, P, P, C.POINTER(ircur_result)]
         lib.ircur_sample_indices.argtypes = [U64, I32, I32, I64, I32, P, P]
@@ -162,6 +163,13 @@ def ircur_get_errors(ctx, max_iter):
     cnt = C.c_int32()
     _check(_lib().ircur_get_errors(ctx, buf, C.byref(cnt)), "ircur_get_errors")
     return list(buf[: cnt.value])
+
+
+def ircur_get_launch_shape(ctx):
+    """(svd_ctas, pass_blocks, pass_bufs) of the context's iterations."""
+    a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(_lib().ircur_get_launch_shape(ctx, C.byref(a), C.byref(b), C.byref(c)), "ircur_get_launch_shape")
+    return a.value, b.value, c.value
 
 
 def ircur_reconstruct(ctx, D, ldD, L, ldL, S=None, ldS=0):

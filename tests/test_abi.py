@@ -84,6 +84,8 @@ def test_status_strings_and_param_validation_without_gpu(lib):
     assert lib.ircur_batch_instance(None, 0) is None
     # streaming argument checks
     assert lib.ircur_stream_columns(None, None, 0, 1, 0, None, 0, None, 0) == ir.IRCUR_EINVAL
+    # launch-shape query
+    assert lib.ircur_get_launch_shape(None, None, None, None) == ir.IRCUR_EINVAL
     # adjoint argument checks
     assert lib.ircur_set_record(None, 1) == ir.IRCUR_EINVAL
     assert lib.ircur_backward(None, None, 0, None, 0, None, 0, None, 0) == ir.IRCUR_EINVAL
