@@ -69,9 +69,8 @@ struct ircur_ctx {
   int64_t ldPr, ldPc, ldDT;
   float* A[2];
   float* B[2];
-  float* Dc[2];   // D(I,J) compact (nI x ldDc) and transposed (nJ x ldDcT); IRCUR-F uses [0] only
-  float* DcT[2];
-  int64_t ldDc, ldDcT;
+  float* Dc[2];   // D(I,J) compact (nI x ldDc); IRCUR-F uses [0] only
+  int64_t ldDc;
   unsigned* posI[2];  // index maps by draw parity (IRCUR-F: [0] only)
   unsigned* posJ[2];
   float* AI[2];       // compact A_k(I_k,:), B_k(:,J_k)^T by iteration parity
@@ -201,12 +200,10 @@ static ircur_status create_impl(const ircur_params* params, void* stream, int mi
   const size_t oA0 = take((size_t)n1 * R * 4), oA1 = take((size_t)n1 * R * 4);
   const size_t oB0 = take((size_t)R * n2 * 4), oB1 = take((size_t)R * n2 * 4);
   c->ldDc = (p.nJ + 3) & ~3ll;
-  c->ldDcT = (p.nI + 3) & ~3ll;
   const int ncore = p.resample ? 2 : 1;
-  size_t oDc[2], oDcT[2], oPosI[2], oPosJ[2], oAIc[2], oBJc[2];
+  size_t oDc[2], oPosI[2], oPosJ[2], oAIc[2], oBJc[2];
   for (int q = 0; q < ncore; ++q) {
     oDc[q] = take((size_t)p.nI * c->ldDc * 4);
-    oDcT[q] = take((size_t)p.nJ * c->ldDcT * 4);
     oPosI[q] = take((size_t)n1 * 4);
     oPosJ[q] = take((size_t)n2 * 4);
   }
@@ -252,7 +249,6 @@ static ircur_status create_impl(const ircur_params* params, void* stream, int mi
   c->B[1] = reinterpret_cast<float*>(base + oB1);
   for (int q = 0; q < 2; ++q) {
     c->Dc[q] = reinterpret_cast<float*>(base + oDc[q < ncore ? q : 0]);
-    c->DcT[q] = reinterpret_cast<float*>(base + oDcT[q < ncore ? q : 0]);
     c->posI[q] = reinterpret_cast<unsigned*>(base + oPosI[q < ncore ? q : 0]);
     c->posJ[q] = reinterpret_cast<unsigned*>(base + oPosJ[q < ncore ? q : 0]);
     c->AI[q] = reinterpret_cast<float*>(base + oAIc[q]);
@@ -302,14 +298,12 @@ static ircur_status create_impl(const ircur_params* params, void* stream, int mi
   d.B[1] = c->B[1];
   for (int q = 0; q < 2; ++q) {
     d.Dc[q] = c->Dc[q];
-    d.DcT[q] = c->DcT[q];
     d.posI[q] = c->posI[q];
     d.posJ[q] = c->posJ[q];
     d.AI[q] = c->AI[q];
     d.BJt[q] = c->BJt[q];
   }
   d.ldDc = c->ldDc;
-  d.ldDcT = c->ldDcT;
   d.W = c->W;
   d.V = c->V;
   d.Vs = c->Vs;
@@ -354,8 +348,9 @@ static bool use_graph() {
   return !(g && g[0] == '1');
 }
 
-// Build (or reuse) the graph: one conditional while-node whose body is one
-// iteration (core, SVD, passes).  The body is recorded by stream capture on
+// Build (or reuse) the graph: one conditional while-node whose body holds
+// kGraphUnroll iterations (core SVD, then the panel passes, each).  The body is
+// recorded by stream capture on
 // the context's private stream, so any user stream (even the legacy default
 // stream) can launch it.
 static ircur_status build_graph(ircur_ctx* c, const IterDesc& d0) {

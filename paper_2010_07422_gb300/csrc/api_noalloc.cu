@@ -39,7 +39,7 @@ constexpr size_t kNaBytes =
     na_piece((size_t)kNaMaxM * kNaMaxN * 4) +                            // D(I,:)
     na_piece((size_t)kNaMaxM * kNaMaxN * 4) +                            // D(:,J)^T
     4 * na_piece((size_t)kNaMaxN * kNaMaxR * 4) +                        // A[2], B[2]
-    2 * na_piece((size_t)kNaMaxM * kNaMaxM * 4) +                        // D(I,J), D(I,J)^T
+    na_piece((size_t)kNaMaxM * kNaMaxM * 4) +                            // D(I,J)
     2 * na_piece((size_t)kNaMaxN * 4) +                                  // index maps
     4 * na_piece((size_t)kNaMaxM * kNaMaxR * 4) +                        // A_k(I,:), B_k(:,J)^T by parity
     3 * na_piece((size_t)kNaMaxM * kNaMaxR * 4) +                        // W, V, Vs
@@ -100,7 +100,7 @@ extern "C" ircur_status ircur_solve_noalloc(const ircur_params* params, const fl
 
   const int R = pad_rank(p.r);
   const int64_t n1 = p.n1, n2 = p.n2;
-  const int64_t ldDc = (p.nJ + 3) & ~3ll, ldDcT = (p.nI + 3) & ~3ll;
+  const int64_t ldDc = (p.nJ + 3) & ~3ll;
   IterDesc d;
   memset(&d, 0, sizeof(d));
   d.svdNC = svd_cluster_size(p.nI, p.nJ, R, p.svd_form);
@@ -125,7 +125,6 @@ extern "C" ircur_status ircur_solve_noalloc(const ircur_params* params, const fl
   Bb[0] = reinterpret_cast<float*>(take((size_t)R * n2 * 4));
   Bb[1] = reinterpret_cast<float*>(take((size_t)R * n2 * 4));
   float* Dc = reinterpret_cast<float*>(take((size_t)p.nI * ldDc * 4));
-  float* DcT = reinterpret_cast<float*>(take((size_t)p.nJ * ldDcT * 4));
   unsigned* posI = reinterpret_cast<unsigned*>(take((size_t)n1 * 4));
   unsigned* posJ = reinterpret_cast<unsigned*>(take((size_t)n2 * 4));
   float* AIc[2];
@@ -170,7 +169,6 @@ extern "C" ircur_status ircur_solve_noalloc(const ircur_params* params, const fl
   d.B[0] = Bb[0];
   d.B[1] = Bb[1];
   d.Dc[0] = d.Dc[1] = Dc;
-  d.DcT[0] = d.DcT[1] = DcT;
   d.posI[0] = d.posI[1] = posI;
   d.posJ[0] = d.posJ[1] = posJ;
   for (int q = 0; q < 2; ++q) {
@@ -178,7 +176,6 @@ extern "C" ircur_status ircur_solve_noalloc(const ircur_params* params, const fl
     d.BJt[q] = BJc[q];
   }
   d.ldDc = ldDc;
-  d.ldDcT = ldDcT;
   d.W = W;
   d.V = V;
   d.Vs = Vs;

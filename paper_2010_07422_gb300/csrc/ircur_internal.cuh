@@ -36,7 +36,7 @@ constexpr int kTraceSlots = 4;
 // and lane c column c.  Each tile leaves its (num, den) partial sums in
 // `partials`.
 constexpr int kPanelCols = 32;
-constexpr int kPassWarps = 8;
+constexpr int kPassWarps = 16;
 constexpr int kSvdCluster = 8;  // CTAs (SMs) of the cluster form of the core SVD
 constexpr int kPassThreads = 32 * kPassWarps;
 constexpr int kMaxPanelRows = 512;  // largest |I|, |J| the kernels are built for
@@ -93,14 +93,13 @@ struct IterDesc {
   const int* J_all;     // (resample ? max_iter : 1) x nJ
   float* A[2];          // n1 x R row-major (R = padded rank of the kernels)
   float* B[2];          // R x n2 row-major
-  // D(I,J) of an iteration, compact (nI x ldDc) and transposed (nJ x ldDcT),
-  // the core SVD's Phase I input.  IRCUR-F: [0] only, gathered once.  IRCUR-R:
+  // D(I,J) of an iteration, compact (nI x ldDc), the core SVD's Phase I
+  // input.  IRCUR-F: [0] only, gathered once.  IRCUR-R:
   // iteration k reads [k & 1]; the panel pass of iteration k gathers
   // D(I_{k+1}, J_{k+1}) into [(k + 1) & 1] (the solve's prologue gathers k = 0).
   // Padding columns stay zero.
   float* Dc[2];
-  float* DcT[2];
-  int64_t ldDc, ldDcT;  // nJ and nI rounded up to 4
+  int64_t ldDc;  // nJ rounded up to 4 (16-byte rows for the bulk copies)
   // Index maps of the draws (k & 1 for IRCUR-R, [0] for IRCUR-F; n1 and n2
   // entries, see index_tag) and the compact side matrices of iteration k,
   // AI[k & 1] = A_k(I_k,:) (nI x R) and BJt[k & 1] = B_k(:,J_k)^T (nJ x R),

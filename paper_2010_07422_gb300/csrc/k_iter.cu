@@ -211,7 +211,6 @@ __device__ __forceinline__ void pass_gather_next_core(const IterDesc& d, int k, 
     const int a = lt + ra * d.nRowTiles;
     const float v = __ldcs(d.D + (int64_t)__ldg(In + a) * d.ldD + __ldg(Jn + b));
     d.Dc[nb][(int64_t)a * d.ldDc + b] = v;
-    d.DcT[nb][(int64_t)b * d.ldDcT + a] = v;
   }
 }
 
@@ -233,23 +232,11 @@ __device__ __forceinline__ void pass_stage_proj(const IterDesc& d, const PassLay
   __syncthreads();
 }
 
-// One tile, first half: the thresholded values D - S in place (FP32 panels;
-// BF16 panels write them to the FP32 work buffer) and this thread's share of
-// ||D||^2.  Needs only the core kernel's outputs, not the SVD's.
-template <int R, bool COL, bool BF>
-__device__ __forceinline__ float pass_tile_threshold(const IterDesc& d, int k, float zeta, int lt,
-                                                     const PassLayout& L, unsigned char* tileP) {
-  float* tileS = BF ? L.vbuf : reinterpret_cast<float*>(tileP);
-  const uint16_t* tileH = reinterpret_cast<const uint16_t*>(tileP);
-  constexpr int RX = (R + 3) & ~3;
-  const int m = COL ? d.nJ : d.nI;
-  const int64_t ncolsTotal = COL ? d.n1 : d.n2;
+// The lane's column of the current iterate's other factor: B_k(:,j) (row
+// panel) or A_k(i,:)^T (column panel); zero past the panel's last column.
+template <int R, bool COL>
+__device__ __forceinline__ void pass_lane_vec(const IterDesc& d, int k, int64_t j, bool live, float (&vec)[R]) {
   const int cur = k & 1;
-  const int lane = threadIdx.x & 31, h = threadIdx.x >> 5;
-  const int64_t j = (int64_t)lt * kPanelCols + lane;
-  const bool live = j < ncolsTotal;
-  const float* side = L.side;
-  float vec[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) {
     if (COL)
@@ -257,44 +244,75 @@ __device__ __forceinline__ float pass_tile_threshold(const IterDesc& d, int k, f
     else
       vec[t] = live ? d.B[cur][(int64_t)t * d.n2 + j] : 0.f;
   }
+}
+
+// Row a of a tile, the lane's column: the panel entry d, L_k there (the same
+// FMA chain as the core, lowrank_entry), and D - S = D - T_zeta(D - L_k)
+// written in place (BF16 panels: to the FP32 work buffer).  Adds d^2 to den.
+template <int R, bool COL, bool BF>
+__device__ __forceinline__ float pass_entry(const IterDesc& d, const PassLayout& L, float* tileS,
+                                            const uint16_t* tileH, int a, int lane, int64_t j, bool live,
+                                            const float (&vec)[R], float zeta, float msk, float& den) {
+  constexpr int RX = (R + 3) & ~3;
+  float* cell = tileS + (size_t)a * kPanelCols + lane;
+  float sr[R];
+#pragma unroll
+  for (int t4 = 0; t4 < RX / 4; ++t4) {
+    const float4 sv = *reinterpret_cast<const float4*>(L.side + (size_t)a * RX + 4 * t4);
+    const float s4[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (4 * t4 + e < R) sr[4 * t4 + e] = s4[e];
+  }
+  const float l = lowrank_entry<R>(sr, vec);
+  float dv;
+  if (BF) {
+    dv = bf16_entry(tileH[(size_t)a * kPanelCols + lane], l, zeta, [&]() {
+      if (!live) return 0.f;
+      return COL ? d.D[j * d.ldD + d.J_all[a]] : d.D[(int64_t)d.I_all[a] * d.ldD + j];
+    });
+  } else {
+    dv = *cell;
+  }
+  const float v = panel_value(dv, l, zeta) * msk;
+  *cell = v;
+  den = fmaf(dv, dv, den);
+  return v;
+}
+
+// One tile, first half: the thresholded values D - S in place and this
+// thread's share of ||D||^2.  Needs only L_k, not the core SVD's outputs, so
+// it runs while the SVD does.
+template <int R, bool COL, bool BF>
+__device__ __forceinline__ float pass_tile_threshold(const IterDesc& d, int k, float zeta, int lt,
+                                                     const PassLayout& L, unsigned char* tileP) {
+  float* tileS = BF ? L.vbuf : reinterpret_cast<float*>(tileP);
+  const uint16_t* tileH = reinterpret_cast<const uint16_t*>(tileP);
+  const int m = COL ? d.nJ : d.nI;
+  const int64_t ncolsTotal = COL ? d.n1 : d.n2;
+  const int lane = threadIdx.x & 31, h = threadIdx.x >> 5;
+  const int64_t j = (int64_t)lt * kPanelCols + lane;
+  const bool live = j < ncolsTotal;
+  float vec[R];
+  pass_lane_vec<R, COL>(d, k, j, live, vec);
   const float msk = live ? 1.f : 0.f;
   const int a0 = h * m / kPassWarps, a1 = (h + 1) * m / kPassWarps;
   float den = 0.f;
-  for (int a = a0; a < a1; ++a) {
-    float* cell = tileS + (size_t)a * kPanelCols + lane;
-    float sr[R];
-#pragma unroll
-    for (int t4 = 0; t4 < RX / 4; ++t4) {
-      const float4 sv = *reinterpret_cast<const float4*>(side + (size_t)a * RX + 4 * t4);
-      const float s4[4] = {sv.x, sv.y, sv.z, sv.w};
-#pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if (4 * t4 + e < R) sr[4 * t4 + e] = s4[e];
-    }
-    const float l = lowrank_entry<R>(sr, vec);
-    float dv;
-    if (BF) {
-      dv = bf16_entry(tileH[(size_t)a * kPanelCols + lane], l, zeta, [&]() {
-        if (!live) return 0.f;
-        return COL ? d.D[j * d.ldD + d.J_all[a]] : d.D[(int64_t)d.I_all[a] * d.ldD + j];
-      });
-    } else {
-      dv = *cell;
-    }
-    const float v = panel_value(dv, l, zeta) * msk;
-    *cell = v;
-    den = fmaf(dv, dv, den);
-  }
+#pragma unroll 2
+  for (int a = a0; a < a1; ++a) pass_entry<R, COL, BF>(d, L, tileS, tileH, a, lane, j, live, vec, zeta, msk, den);
   return den;
 }
 
 // One tile, second half: the projections (they need the core SVD's outputs,
 // staged on the segment's first tile), the next factor rows and the explicit
-// residuals; this share's num/den go to wsum.
-template <int R, bool COL, bool BF>
+// residuals; this share's num/den go to wsum.  FUSE: the tile was not
+// thresholded ahead of time; the threshold runs in the projection sweep and
+// its ||D||^2 share is added to den.
+template <int R, bool COL, bool BF, bool FUSE>
 __device__ __forceinline__ void pass_tile_project(const IterDesc& d, int k, int lt, const PassLayout& L,
-                                                  unsigned char* tileP, float den, bool stage_proj) {
-  const float* tileS = BF ? L.vbuf : reinterpret_cast<const float*>(tileP);
+                                                  unsigned char* tileP, float den, bool stage_proj, float zeta) {
+  float* tileS = BF ? L.vbuf : reinterpret_cast<float*>(tileP);
+  const uint16_t* tileH = reinterpret_cast<const uint16_t*>(tileP);
   constexpr int RX = (R + 3) & ~3;
   const int m = COL ? d.nJ : d.nI;
   const int64_t ncolsTotal = COL ? d.n1 : d.n2;
@@ -312,6 +330,8 @@ __device__ __forceinline__ void pass_tile_project(const IterDesc& d, int k, int 
   const unsigned tag_next = (unsigned)(dnext + 1);
   unsigned pos_next = 0u;
   if (h == 0 && live) pos_next = __ldcg((COL ? d.posI : d.posJ)[dnext & 1] + j);
+  float vec[R];
+  if (FUSE) pass_lane_vec<R, COL>(d, k, j, live, vec);
   if (COL) {
     if (stage_proj) pass_stage_proj<R, true>(d, L, k);
   } else {
@@ -320,8 +340,10 @@ __device__ __forceinline__ void pass_tile_project(const IterDesc& d, int k, int 
   float acc[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) acc[t] = 0.f;
+#pragma unroll 2
   for (int a = a0; a < a1; ++a) {
-    const float v = tileS[(size_t)a * kPanelCols + lane];
+    const float v = FUSE ? pass_entry<R, COL, BF>(d, L, tileS, tileH, a, lane, j, live, vec, zeta, msk, den)
+                         : tileS[(size_t)a * kPanelCols + lane];
     float pr[R];
 #pragma unroll
     for (int t4 = 0; t4 < RX / 4; ++t4) {
@@ -340,16 +362,20 @@ __device__ __forceinline__ void pass_tile_project(const IterDesc& d, int k, int 
   // projections of every column: the kPassWarps share sums in a fixed order
   for (int q = threadIdx.x; q < R * kPanelCols; q += blockDim.x) {
     const int t = q / kPanelCols, cc = q - t * kPanelCols;
-    float sum = 0.f;
+    float s0 = 0.f, s1 = 0.f;  // even and odd shares, then their sum (a fixed order)
 #pragma unroll
-    for (int hh = 0; hh < kPassWarps; ++hh) sum += L.part[((size_t)hh * RX + t) * kPanelCols + cc];
-    L.outS[(size_t)t * kPanelCols + cc] = sum;
+    for (int hh = 0; hh < kPassWarps; hh += 2) {
+      s0 += L.part[((size_t)hh * RX + t) * kPanelCols + cc];
+      s1 += L.part[((size_t)(hh + 1) * RX + t) * kPanelCols + cc];
+    }
+    L.outS[(size_t)t * kPanelCols + cc] = s0 + s1;
   }
   __syncthreads();
   float out[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) out[t] = L.outS[(size_t)t * kPanelCols + lane];
   float num = 0.f;
+#pragma unroll 2
   for (int a = a0; a < a1; ++a) {
     const float v = tileS[(size_t)a * kPanelCols + lane];
     float rr[R];
@@ -608,10 +634,13 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
       cp_async_wait_group<0>();
     __syncthreads();
     unsigned char* tb = L.tiles + (size_t)b * L.tile_bytes;
-    float den;
+    // a tile met after the segment's wait for the SVD (and not thresholded
+    // ahead of time) is thresholded inside its projection sweep
+    const bool fuse = proj_staged && early != t;
+    float den = 0.f;
     if (early == t) {
       den = den_early;
-    } else {
+    } else if (!fuse) {
       den = cur.col ? pass_tile_threshold<R, true, BF>(d, seg_k, zeta, cur.lt, L, tb)
                     : pass_tile_threshold<R, false, BF>(d, seg_k, zeta, cur.lt, L, tb);
     }
@@ -625,10 +654,17 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
                           : pass_tile_threshold<R, false, BF>(d, seg_k, zeta, nx.lt, L, tn);
       early = t + 1;
     }
-    if (cur.col)
-      pass_tile_project<R, true, BF>(d, seg_k, cur.lt, L, tb, den, !proj_staged);
-    else
-      pass_tile_project<R, false, BF>(d, seg_k, cur.lt, L, tb, den, !proj_staged);
+    if (fuse) {
+      if (cur.col)
+        pass_tile_project<R, true, BF, true>(d, seg_k, cur.lt, L, tb, den, false, zeta);
+      else
+        pass_tile_project<R, false, BF, true>(d, seg_k, cur.lt, L, tb, den, false, zeta);
+    } else {
+      if (cur.col)
+        pass_tile_project<R, true, BF, false>(d, seg_k, cur.lt, L, tb, den, !proj_staged, zeta);
+      else
+        pass_tile_project<R, false, BF, false>(d, seg_k, cur.lt, L, tb, den, !proj_staged, zeta);
+    }
     proj_staged = true;
     __syncthreads();
     pass_tile_sums(d, t - (BATCH ? tile_base[cur.inst] : 0), L);
@@ -652,7 +688,7 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
 }
 
 template <int R, bool BF>
-__global__ void __launch_bounds__(kPassThreads) pass_kernel(IterDesc d, int nbuf) {
+__global__ void __launch_bounds__(kPassThreads, (R <= 10 ? 2 : 1)) pass_kernel(IterDesc d, int nbuf) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int mmax = d.nI > d.nJ ? d.nI : d.nJ;
   pass_persistent<R, false, BF>(d, nullptr, nullptr, 1, d.nRowTiles + d.nColTiles, mmax, nbuf, smem);
@@ -661,7 +697,7 @@ __global__ void __launch_bounds__(kPassThreads) pass_kernel(IterDesc d, int nbuf
 // Batched form: the tiles of every instance back to back (tile_base[i] is the
 // first tile of instance i, tile_base[count] the total).
 template <int R>
-__global__ void __launch_bounds__(kPassThreads) pass_batch_kernel(const IterDesc* __restrict__ ds,
+__global__ void __launch_bounds__(kPassThreads, (R <= 10 ? 2 : 1)) pass_batch_kernel(const IterDesc* __restrict__ ds,
                                                                   const int* __restrict__ tile_base, int count,
                                                                   int mmax, int nbuf) {
   extern __shared__ __align__(16) unsigned char smem[];

@@ -336,8 +336,8 @@ cudaError_t launch_gather(const IterDesc& d, cudaStream_t s) {
 namespace ircur {
 
 // ---------------------------------------------------------------------------
-// D(I,J) of one draw into the compact buffers the core SVD reads:
-// Dc[buf] (nI x ldDc) and its transpose DcT[buf] (nJ x ldDcT).  IRCUR-F
+// D(I,J) of one draw into the compact buffer the core SVD reads, Dc[buf]
+// (nI x ldDc).  IRCUR-F
 // gathers it once per solve; IRCUR-R gathers draw 0 here and every later draw
 // in the previous iteration's panel pass.
 __global__ void __launch_bounds__(256) gather_core_kernel(IterDesc d, int draw, int buf) {
@@ -349,7 +349,6 @@ __global__ void __launch_bounds__(256) gather_core_kernel(IterDesc d, int draw, 
     const int a = (int)(e / d.nJ), b = (int)(e - (int64_t)a * d.nJ);
     const float v = __ldg(d.D + (int64_t)I[a] * d.ldD + J[b]);
     d.Dc[buf][(int64_t)a * d.ldDc + b] = v;
-    d.DcT[buf][(int64_t)b * d.ldDcT + a] = v;
   }
 }
 

@@ -7,15 +7,17 @@
 // Core.  L_k(I,J) = A_k(I,:) B_k(:,J) is evaluated entry by entry with the
 // same FMA chain as the panel passes (lowrank_entry), so the core equals the
 // (I,J) entries of both panels bit for bit.  D(I,J) comes from a compact copy
-// (row-major and transposed), loaded by bulk copies.  CTA c holds the core rows
-// [c mI/NC, ...) (row slab, for core X) and the core columns [c mJ/NC, ...)
-// (column slab, stored transposed, for core^T Y) in shared memory; with NC = 1
-// one copy with an odd leading dimension serves both products conflict-free.
+// (row-major), loaded by bulk copies.  CTA c holds the core rows [c mI/NC, ...)
+// (row slab, for core X) and the core columns [c mJ/NC, ...) (column slab,
+// stored transposed, for core^T Y) in shared memory.  Each entry is formed
+// once, by the owner of its row, and pushed to the owner of its column; with
+// NC = 1 one copy with an odd leading dimension serves both products
+// conflict-free.
 //
 // Truncation.  Two-sided subspace iteration, warm-started from B_k(:,J)^T, the
-// right factor of the previous iterate on the new columns (the Ritz vectors
-// of the previous core: V = X Vt Sigma is graded,
-// its columns nearly orthogonal with norms near sigma_i).  Half-steps alternate:
+// right factor of the previous iterate on the new columns (close to the
+// previous core's X T^T, nearly orthogonal columns graded by T's diagonal),
+// with its columns divided by |T_tt|.  Half-steps alternate:
 //   P  = core X            (row slabs)   Y Rp = P    (Cholesky QR, Y replaces P)
 //   Q  = core^T Y          (column slabs) X Uq = Q   (Cholesky QR, X replaces Q)
 // Each half-step ends with one all-gather over distributed shared memory: every
@@ -97,7 +99,7 @@ __host__ __device__ inline SvdGeom svd_geom(int nI, int nJ, int R, int nc) {
   // NC = 1: one copy of the core, odd row stride (rows and columns conflict-free);
   // NC > 1: 16-byte rows (bulk copies), any stride is conflict-free for the lanes-over-k reads
   g.ldr = nc == 1 ? svd_odd(nJ) : ((nJ + 3) & ~3);
-  g.ldc = (nI + 3) & ~3;
+  g.ldc = svd_odd(nI);  // filled by pushes: an odd stride keeps the lanes' pushes conflict-free
   g.ldy = svd_odd(nI);
   g.ldx = svd_odd(nJ);
   g.sl = svd_slot(R);
@@ -247,10 +249,13 @@ __device__ int warp_chol(const float* G, int r, float* Uw, float* dw, float& min
       const float g0t = __shfl_sync(0xffffffffu, gdiag, t);
       const bool keep = dgt > 1e-12f * maxd && dgt <= FLT_MAX;
       const float rinv = keep ? rsqrtf(dgt) : 0.f;
-      // pivots below 1e-10 of the largest diagonal entry are FP32 noise of the
-      // products themselves (sigma_t / sigma_1 < 1e-5, below the FP32 rank
-      // cutoff): FP64 could not recover them, so they do not count
-      if (keep && dgt > 1e-10f * maxd) msp = fminf(msp, __fdividef(dgt, g0t));
+      // a column whose own diagonal entry is below 1e-10 of the largest is FP32
+      // noise of the products themselves (sigma_t / sigma_1 < 1e-5, below the
+      // FP32 rank cutoff): FP64 could not recover it, so it does not count.  A
+      // live column whose pivot collapsed (small, zero or negative: FP32
+      // cancellation in an ill-conditioned block) reads as 0 and calls for the
+      // FP64 factor.
+      if (g0t > 1e-10f * maxd) msp = fminf(msp, keep ? __fdividef(dgt, g0t) : 0.f);
       const float ul = g[t] * rinv;  // U(t, lane)
       float urow[R];
 #pragma unroll
@@ -506,6 +511,17 @@ __device__ __forceinline__ float hash_uniform(uint64_t seed, uint64_t ctr) {
   return (float)(h >> 40) * (1.0f / 16777216.0f) * 2.0f - 1.0f;
 }
 
+// A random start for the subspace iteration (first iteration, B_0 = 0, or a
+// warm start that lost rank): r columns of uniform [-1, 1) entries from a
+// counter-based hash of (seed, k, entry), zero columns beyond r.
+template <int R>
+__device__ __forceinline__ void svd_random_start(float* Q, int ldx, int nJ, int r, uint64_t seed, int k) {
+  for (int q = threadIdx.x; q < nJ * R; q += blockDim.x) {
+    const int t = q / nJ, b = q - t * nJ;
+    Q[t * ldx + b] = (t < r) ? hash_uniform(seed ^ 0x5bd1e995ull, ((uint64_t)k << 32) ^ (uint64_t)(b * R + t)) : 0.f;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // The kernel body.  role 0: the core and its truncation on a cluster of NC
 // CTAs.  Roles 1, 2 (IRCUR-R with its own sampler): rank 0 of that cluster
@@ -651,64 +667,60 @@ __device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned c
   const float* BJk = d.BJt[k & 1];  // B_k(:,J_k)^T, nJ x R
   const int buf = d.resample ? (k & 1) : 0;
   const float* Dc = d.Dc[buf];
-  const float* DcT = d.DcT[buf];
 
-  // ---- 1. bulk copies of this CTA's rows and columns of D(I,J) (cluster form)
+  // ---- 1. bulk copies of this CTA's rows of D(I,J) (cluster form)
   const bool bulk = nc > 1;
   if (bulk && warp == 0) {
-    const unsigned rowb = (unsigned)(((nJ + 3) & ~3) * 4), colb = (unsigned)(((nI + 3) & ~3) * 4);
+    const unsigned rowb = (unsigned)(((nJ + 3) & ~3) * 4);
     if (lane == 0) {
       mbar_init(sp.bar, 1);
       fence_mbar_init();
-      mbar_arrive_expect_tx(sp.bar, (unsigned)nrw * rowb + (unsigned)ncl * colb);
+      mbar_arrive_expect_tx(sp.bar, (unsigned)nrw * rowb);
     }
     __syncwarp();
     for (int i = lane; i < nrw; i += 32) bulk_g2s(sp.urow + (size_t)i * g.ldr, Dc + (size_t)(row0 + i) * d.ldDc, rowb, sp.bar);
-    for (int j = lane; j < ncl; j += 32)
-      bulk_g2s(sp.ucol + (size_t)j * g.ldc, DcT + (size_t)(col0 + j) * d.ldDcT, colb, sp.bar);
   }
-  // ---- 2. A_k(I,:) and B_k(:,J)^T (compact, written by the previous panel
-  // pass): thread q holds rows q and q + blockDim of each in registers (all
-  // loads in flight together), and writes them to P and Q (column-major).  The
-  // column slab below takes A_k(I_i,:) from these registers only: rows of P
-  // owned by other CTAs may already hold their first pushed product (nothing
-  // orders another CTA's first half-step after this prologue), while this
-  // CTA's own rows of P are written by this CTA alone.
+  // ---- 2. this CTA's rows of A_k(I,:) to its own rows of P (rows of P owned
+  // by other CTAs may already hold their first pushed product: nothing orders
+  // another CTA's first half-step after this prologue, but this CTA's own rows
+  // are written by this CTA alone), and B_k(:,J)^T in registers (thread q:
+  // rows q and q + blockDim), both compact copies the previous panel pass wrote.
+  // The warm start X_0 = B_k(:,J)^T diag(1 / |T_tt|), T the previous core's
+  // (H_r = Y T X^T, T near-diagonal in the graded basis): B_k(:,J)^T is close
+  // to X' T^T, so the scaling leaves columns of comparable norm, as the
+  // dependence cutoff of the Cholesky factor (relative to its largest diagonal
+  // entry) assumes.  k = 0 (B_0 = 0): a random start.
   const int q0 = tid, q1 = tid + (int)blockDim.x;
-  float ai0[R], ai1[R], bj0[R], bj1[R];
+  float bj0[R], bj1[R];
   {
+    float inv[R];
 #pragma unroll
     for (int t = 0; t < R; ++t) {
-      ai0[t] = q0 < nI ? AIk[(size_t)q0 * R + t] : 0.f;
-      ai1[t] = q1 < nI ? AIk[(size_t)q1 * R + t] : 0.f;
+      const float tt = (k > 0 && t < r) ? fabsf(d.Tm[t * R + t]) : 0.f;
+      inv[t] = tt > 0.f ? 1.f / tt : 0.f;
       bj0[t] = q0 < nJ ? BJk[(size_t)q0 * R + t] : 0.f;
       bj1[t] = q1 < nJ ? BJk[(size_t)q1 * R + t] : 0.f;
     }
+    for (int q = tid; q < nrw * R; q += blockDim.x) {
+      const int il = q / R, t = q - il * R;
+      sp.P[t * g.ldy + row0 + il] = AIk[(size_t)(row0 + il) * R + t];
+    }
+    if (k > 0) {
 #pragma unroll
-    for (int t = 0; t < R; ++t) {
-      if (q0 < nI) sp.P[t * g.ldy + q0] = ai0[t];
-      if (q1 < nI) sp.P[t * g.ldy + q1] = ai1[t];
-      if (q0 < nJ) sp.Q[t * g.ldx + q0] = bj0[t];
-      if (q1 < nJ) sp.Q[t * g.ldx + q1] = bj1[t];
+      for (int t = 0; t < R; ++t) {
+        if (q0 < nJ) sp.Q[t * g.ldx + q0] = bj0[t] * inv[t];
+        if (q1 < nJ) sp.Q[t * g.ldx + q1] = bj1[t] * inv[t];
+      }
+    } else {
+      svd_random_start<R>(sp.Q, g.ldx, nJ, r, d.seed, k);
     }
   }
   __syncthreads();
-  // ---- 3. the warm start's Gram matrix (its factor is applied after Phase I)
-  float* gout = reinterpret_cast<float*>(sp.r64 + g.nt);  // NP pairs
-  block_gram<R, float>(sp.Q, g.ldx, nJ, reinterpret_cast<float*>(sp.r64), gout);
-  int brk = 0;
-  float msp;
-  if (REP || warp == 0) {
-    warp_expand<R>(gout, Gw);
-    brk = warp_chol<R>(Gw, r, F2, d2, msp);
-  }
-  if (!REP) __syncthreads();
-  if (!REP) {  // every warp needs brk
-    if (tid == 0) sp.ib[0] = brk;
-    __syncthreads();
-    brk = sp.ib[0];
-  }
-  // ---- 4. Phase I on the core: slabs of D(I,J) - T_zeta(D(I,J) - L_k(I,J))
+  // ---- 3. Phase I on the core, this CTA's rows:
+  // D(I,J) - T_zeta(D(I,J) - L_k(I,J)).  Each entry is formed once, written to
+  // the row slab and pushed to the CTA that owns its column (column slab,
+  // stored transposed); the first half-step's cluster barrier publishes those
+  // pushes before any CTA's first product with the column slab.
   bool ok = true;
   if (bulk) {
     ok = mbar_wait_bounded(sp.bar, 0, d.spinLimit);
@@ -726,12 +738,18 @@ __device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned c
       const float dv = d.bf16 ? bf16_entry(f32_to_bf16_bits(dv32), l, zeta, [&]() { return dv32; }) : dv32;
       return panel_value(dv, l, zeta);
     };
-    // row slab (one copy of the whole core for nc == 1): thread per column
-    // (B_k(:,J_j) in registers), the rows' A_k(I_i,:) broadcast reads of own rows
+    // thread per column (B_k(:,J_j) in registers), the rows' A_k(I_i,:)
+    // broadcast reads of own rows of P
     for (int half = 0; half < 2; ++half) {
       const int j = half ? q1 : q0;
       if (j >= nJ) continue;
       const float(&bj)[R] = half ? bj1 : bj0;
+      float* cdst = nullptr;  // column j of the column slab, at this CTA's first row
+      if (nc > 1) {
+        const int owner = j / g.mcJ;
+        float* loc = sp.ucol + (size_t)(j - owner * g.mcJ) * g.ldc + row0;
+        cdst = owner == crank ? loc : cl.map_shared_rank(loc, owner);
+      }
       int il = 0;
       for (; il + 4 <= nrw; il += 4) {
         float a4[4][R], d4[4];
@@ -743,7 +761,11 @@ __device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned c
           d4[u] = bulk ? sp.urow[(size_t)(il + u) * g.ldr + j] : __ldg(Dc + (size_t)i * d.ldDc + j);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) sp.urow[(size_t)(il + u) * g.ldr + j] = entry(d4[u], a4[u], bj);
+        for (int u = 0; u < 4; ++u) {
+          const float v = entry(d4[u], a4[u], bj);
+          sp.urow[(size_t)(il + u) * g.ldr + j] = v;
+          if (cdst) cdst[il + u] = v;
+        }
       }
       for (; il < nrw; ++il) {
         const int i = row0 + il;
@@ -751,58 +773,17 @@ __device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned c
 #pragma unroll
         for (int t = 0; t < R; ++t) a1[t] = sp.P[t * g.ldy + i];
         const float dv = bulk ? sp.urow[(size_t)il * g.ldr + j] : __ldg(Dc + (size_t)i * d.ldDc + j);
-        sp.urow[(size_t)il * g.ldr + j] = entry(dv, a1, bj);
-      }
-    }
-    // column slab (stored transposed): thread per row (A_k(I_i,:) in
-    // registers), the columns' B_k(:,J_j) broadcast reads of Q
-    if (nc > 1) {
-      for (int half = 0; half < 2; ++half) {
-        const int i = half ? q1 : q0;
-        if (i >= nI) continue;
-        const float(&ai)[R] = half ? ai1 : ai0;
-        int jl = 0;
-        for (; jl + 4 <= ncl; jl += 4) {
-          float b4[4][R], d4[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-#pragma unroll
-            for (int t = 0; t < R; ++t) b4[u][t] = sp.Q[t * g.ldx + col0 + jl + u];
-            d4[u] = sp.ucol[(size_t)(jl + u) * g.ldc + i];
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) sp.ucol[(size_t)(jl + u) * g.ldc + i] = entry(d4[u], ai, b4[u]);
-        }
-        for (; jl < ncl; ++jl) {
-          float b1[R];
-#pragma unroll
-          for (int t = 0; t < R; ++t) b1[t] = sp.Q[t * g.ldx + col0 + jl];
-          sp.ucol[(size_t)jl * g.ldc + i] = entry(sp.ucol[(size_t)jl * g.ldc + i], ai, b1);
-        }
+        const float v = entry(dv, a1, bj);
+        sp.urow[(size_t)il * g.ldr + j] = v;
+        if (cdst) cdst[il] = v;
       }
     }
   }
   __syncthreads();
   if (crank == 0) trace_stop(d.trace, kTraceSlots * d.max_iter, kTraceSlots * k + 0);
-  // ---- 5. X_0 = orth(B_k(:,J)^T), or a random start when that is deficient
-  if (brk > 0) {  // first iteration (B_0 = 0) or a deficient warm start
-    for (int q = tid; q < nJ * R; q += blockDim.x) {
-      const int t = q / nJ, b = q - t * nJ;
-      sp.Q[t * g.ldx + b] =
-          (t < r) ? hash_uniform(d.seed ^ 0x5bd1e995ull, ((uint64_t)k << 32) ^ (uint64_t)(b * R + t)) : 0.f;
-    }
-    __syncthreads();
-    block_gram<R, float>(sp.Q, g.ldx, nJ, reinterpret_cast<float*>(sp.r64), gout);
-    if (REP || warp == 0) {
-      warp_expand<R>(gout, Gw);
-      warp_chol<R>(Gw, r, F2, d2, msp);
-    }
-    if (!REP) __syncthreads();
-  }
-  block_subst<R>(sp.Q, g.ldx, nJ, F2, d2);
-  __syncthreads();
+  float msp;
 
-  // ---- 6. half-steps
+  // ---- 4. half-steps
   int ps_[PQ], pt_[PQ];
 #pragma unroll
   for (int q = 0; q < PQ; ++q) {
@@ -828,6 +809,7 @@ __device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned c
   float mspP = 1.f, mspQ = 1.f;
   bool susY = false, susX = false;
   bool abort_all = false;
+  bool restarted = k == 0;  // k = 0 starts at random already
   const int maxh = 2 * d.svdMaxSteps;
   while (true) {
     const bool isP = (h & 1) == 0;
@@ -933,6 +915,26 @@ __device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned c
       fell_back = true;
       minsp = 0.f;
     }
+    if (h == 0 && !restarted) {
+      // a warm start that lost rank (a previous core of numerical rank < r)
+      // leaves dependent columns in the first block (zero reciprocal pivots of
+      // the final, possibly FP64, factor): the first half-step again from a
+      // random start, once; a core that is itself deficient keeps its
+      // dependent columns and ends with IRCUR_FLAG_WRANK
+      int dep = 0;
+#pragma unroll
+      for (int t = 0; t < R; ++t) dep += (t < r && dn[t] == 0.f) ? 1 : 0;
+      if (dep > 0) {
+        restarted = true;
+        __syncthreads();
+        svd_random_start<R>(sp.Q, g.ldx, nJ, r, d.seed, k);
+        // every CTA has summed this half-step's slots before any CTA pushes
+        // the repeated half-step's
+        svd_barrier(cl, nc);
+        __syncthreads();
+        continue;
+      }
+    }
     if (isP) {
       nrmP = sqrtf(trace);
       mspP = minsp;
@@ -1008,7 +1010,7 @@ __device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned c
   }
   if (abort_all) return;  // a CTA's bulk copy timed out (ETIMEOUT is set); no remote access follows
 
-  // ---- 7. H_r(core) = Y T X^T: orthogonality restored where the last
+  // ---- 5. H_r(core) = Y T X^T: orthogonality restored where the last
   // factorisations were poorly conditioned, then T = Ut Sigma Vt^T
   if (warp == 0) {
     for (int e = lane; e < R * R; e += 32) {
@@ -1078,7 +1080,7 @@ __device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned c
     block_subst<R>(sp.Q, g.ldx, nJ, sp.Vt, sp.sg);
     __syncthreads();
   }
-  // ---- 8. rank and outputs.  With T triangular (no re-orthogonalisation) its
+  // ---- 6. rank and outputs.  With T triangular (no re-orthogonalisation) its
   // inverse is a back substitution, and sigma_min / sigma_max >=
   // 1 / (||T||_F ||T^{-1}||_F): above the rank cutoff that certifies rank r,
   // and H_r(core) = Y T X^T with U^+ = (X T^{-1}) Y^T is output as it stands.
