@@ -94,12 +94,14 @@ __host__ __device__ inline SvdGeom svd_geom(int nI, int nJ, int R, int nc) {
   g.nc = nc;
   g.nt = nc == 1 ? kSvdThreadsOne : kSvdThreadsCl;
   g.nw = g.nt / 32;
-  g.mrI = (nI + nc - 1) / nc;
+  // cluster form: row slabs of a multiple of 4 rows, so that the transposed
+  // quads each CTA pushes into the column slabs start on 16-byte boundaries
+  g.mrI = nc == 1 ? nI : (((nI + nc - 1) / nc + 3) & ~3);
   g.mcJ = (nJ + nc - 1) / nc;
   // NC = 1: one copy of the core, odd row stride (rows and columns conflict-free);
   // NC > 1: 16-byte rows (bulk copies), any stride is conflict-free for the lanes-over-k reads
   g.ldr = nc == 1 ? svd_odd(nJ) : ((nJ + 3) & ~3);
-  g.ldc = svd_odd(nI);  // filled by pushes: an odd stride keeps the lanes' pushes conflict-free
+  g.ldc = (nI + 3) & ~3;  // 16-byte rows: the pushed quads are 16-byte stores
   g.ldy = svd_odd(nI);
   g.ldx = svd_odd(nJ);
   g.sl = svd_slot(R);
@@ -717,8 +719,8 @@ __device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned c
   }
   __syncthreads();
   // ---- 3. Phase I on the core, this CTA's rows:
-  // D(I,J) - T_zeta(D(I,J) - L_k(I,J)).  Each entry is formed once, written to
-  // the row slab and pushed to the CTA that owns its column (column slab,
+  // D(I,J) - T_zeta(D(I,J) - L_k(I,J)).  Each entry is formed once, in the row
+  // slab, which is then pushed to the CTAs that own its columns (column slabs,
   // stored transposed); the first half-step's cluster barrier publishes those
   // pushes before any CTA's first product with the column slab.
   bool ok = true;
@@ -744,12 +746,6 @@ __device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned c
       const int j = half ? q1 : q0;
       if (j >= nJ) continue;
       const float(&bj)[R] = half ? bj1 : bj0;
-      float* cdst = nullptr;  // column j of the column slab, at this CTA's first row
-      if (nc > 1) {
-        const int owner = j / g.mcJ;
-        float* loc = sp.ucol + (size_t)(j - owner * g.mcJ) * g.ldc + row0;
-        cdst = owner == crank ? loc : cl.map_shared_rank(loc, owner);
-      }
       int il = 0;
       for (; il + 4 <= nrw; il += 4) {
         float a4[4][R], d4[4];
@@ -762,9 +758,7 @@ __device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned c
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const float v = entry(d4[u], a4[u], bj);
-          sp.urow[(size_t)(il + u) * g.ldr + j] = v;
-          if (cdst) cdst[il + u] = v;
+          sp.urow[(size_t)(il + u) * g.ldr + j] = entry(d4[u], a4[u], bj);
         }
       }
       for (; il < nrw; ++il) {
@@ -773,13 +767,28 @@ __device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned c
 #pragma unroll
         for (int t = 0; t < R; ++t) a1[t] = sp.P[t * g.ldy + i];
         const float dv = bulk ? sp.urow[(size_t)il * g.ldr + j] : __ldg(Dc + (size_t)i * d.ldDc + j);
-        const float v = entry(dv, a1, bj);
-        sp.urow[(size_t)il * g.ldr + j] = v;
-        if (cdst) cdst[il] = v;
+        sp.urow[(size_t)il * g.ldr + j] = entry(dv, a1, bj);
       }
     }
   }
   __syncthreads();
+  if (nc > 1) {
+    // the row slab to the column slabs, transposed: quads of four consecutive
+    // rows of one column (16-byte stores; rows past the core read as zero)
+    const int nq = (nrw + 3) >> 2;
+    for (int q = tid; q < nq * nJ; q += blockDim.x) {
+      const int j = q / nq, quad = q - j * nq, il = 4 * quad;
+      float4 v;
+      v.x = il + 0 < nrw ? sp.urow[(size_t)(il + 0) * g.ldr + j] : 0.f;
+      v.y = il + 1 < nrw ? sp.urow[(size_t)(il + 1) * g.ldr + j] : 0.f;
+      v.z = il + 2 < nrw ? sp.urow[(size_t)(il + 2) * g.ldr + j] : 0.f;
+      v.w = il + 3 < nrw ? sp.urow[(size_t)(il + 3) * g.ldr + j] : 0.f;
+      const int owner = j / g.mcJ;
+      float* loc = sp.ucol + (size_t)(j - owner * g.mcJ) * g.ldc + row0 + il;
+      float* dst = owner == crank ? loc : cl.map_shared_rank(loc, owner);
+      *reinterpret_cast<float4*>(dst) = v;
+    }
+  }
   if (crank == 0) trace_stop(d.trace, kTraceSlots * d.max_iter, kTraceSlots * k + 0);
   float msp;
 
