@@ -70,18 +70,21 @@ struct PassLayout {
   float* side;
   float* proj;
   float* recon;
-  float* part;  // kPassWarps x RX x kPanelCols
+  float* part;  // nw x RX x kPanelCols (nw: warps of the block)
   float* outS;  // RX x kPanelCols
-  float* wsum;  // kPassWarps x 2
+  float* wsum;  // nw x 2
+  float* lvec;      // nbuf x (kPanelCols x RX): the tile's columns of the other factor (pass_stage_lane)
+  unsigned* lpos;   // nbuf x kPanelCols: the next draw's position-map entries of the tile's columns
 };
 
-__host__ __device__ inline size_t pass_layout_floats(int m, int rx, int nbuf, bool bf16 = false) {
+__host__ __device__ inline size_t pass_layout_floats(int m, int rx, int nbuf, bool bf16, int nw) {
   const size_t tile = bf16 ? (size_t)m * kPanelCols / 2 : (size_t)m * kPanelCols;  // in floats
   return (size_t)nbuf * tile + (bf16 ? (size_t)m * kPanelCols : 0) + 3 * (size_t)m * rx +
-         (size_t)kPassWarps * rx * kPanelCols + (size_t)rx * kPanelCols + 4 * kPassWarps;
+         (size_t)nw * rx * kPanelCols + (size_t)rx * kPanelCols + 4 * nw +
+         (size_t)nbuf * ((size_t)kPanelCols * rx + kPanelCols);
 }
 
-__device__ inline PassLayout pass_layout(unsigned char* smem, int m, int rx, int nbuf, bool bf16) {
+__device__ inline PassLayout pass_layout(unsigned char* smem, int m, int rx, int nbuf, bool bf16, int nw) {
   PassLayout L;
   L.m = m;
   L.rx = rx;
@@ -96,8 +99,10 @@ __device__ inline PassLayout pass_layout(unsigned char* smem, int m, int rx, int
   L.proj = p + (size_t)m * rx;
   L.recon = p + 2 * (size_t)m * rx;
   L.part = p + 3 * (size_t)m * rx;
-  L.outS = L.part + (size_t)kPassWarps * rx * kPanelCols;
+  L.outS = L.part + (size_t)nw * rx * kPanelCols;
   L.wsum = L.outS + (size_t)rx * kPanelCols;
+  L.lvec = L.wsum + 4 * nw;  // 16-byte aligned: every piece above is a multiple of 4 floats
+  L.lpos = reinterpret_cast<unsigned*>(L.lvec + (size_t)nbuf * kPanelCols * rx);
   return L;
 }
 
@@ -181,6 +186,44 @@ __device__ __forceinline__ void pass_stage_tile(const IterDesc& d, int k, int lt
   }
 }
 
+// The tile's columns (rows) of the current iterate's other factor, B_k(:,j)
+// for the row panel (lv[t kPanelCols + c]) or A_k(i,:) for the column panel
+// (lv[c R + t]), and the next draw's position-map entries of the same columns
+// (lp[c]), copied asynchronously with the tile; zero past the panel's last
+// column.
+template <int R, bool COL>
+__device__ __forceinline__ void pass_stage_lane(const IterDesc& d, int k, int lt, float* lv, unsigned* lp) {
+  const int cur = k & 1;
+  const int64_t ncolsTotal = COL ? d.n1 : d.n2;
+  const int64_t j0 = (int64_t)lt * kPanelCols;
+  const int ncols = (int)((ncolsTotal - j0) < kPanelCols ? (ncolsTotal - j0) : kPanelCols);
+  if (COL) {
+    // ncols R consecutive floats; the source starts on a 16-byte boundary
+    // (j0 R 4 bytes = 128 lt R)
+    const float* src = d.A[cur] + j0 * R;
+    const int nf = ncols * R, n4 = nf >> 2;
+    for (int q = threadIdx.x; q < n4; q += blockDim.x) cp_async16(lv + 4 * q, src + 4 * q);
+    for (int q = 4 * n4 + (int)threadIdx.x; q < nf; q += blockDim.x) cp_async4(lv + q, src + q);
+    for (int q = nf + (int)threadIdx.x; q < kPanelCols * R; q += blockDim.x) lv[q] = 0.f;
+  } else {
+    for (int q = threadIdx.x; q < R * kPanelCols; q += blockDim.x) {
+      const int t = q / kPanelCols, c = q - t * kPanelCols;
+      if (c < ncols)
+        cp_async4(lv + q, d.B[cur] + (int64_t)t * d.n2 + j0 + c);
+      else
+        lv[q] = 0.f;
+    }
+  }
+  const int dnext = d.resample ? k + 1 : 0;
+  const unsigned* map = (COL ? d.posI : d.posJ)[dnext & 1] + j0;
+  for (int q = threadIdx.x; q < kPanelCols; q += blockDim.x) {
+    if (q < ncols)
+      cp_async4(lp + q, map + q);
+    else
+      lp[q] = 0u;
+  }
+}
+
 // The m x R side matrix of one segment, A_k(I,:) | B_k(:,J)^T: the compact
 // copies the previous pass wrote through the index maps (the same values the
 // core SVD used for L_k(I,J)), rows padded to RX columns with zeros.
@@ -232,18 +275,13 @@ __device__ __forceinline__ void pass_stage_proj(const IterDesc& d, const PassLay
   __syncthreads();
 }
 
-// The lane's column of the current iterate's other factor: B_k(:,j) (row
-// panel) or A_k(i,:)^T (column panel); zero past the panel's last column.
+// The lane's column of the current iterate's other factor, B_k(:,j) (row
+// panel) or A_k(i,:)^T (column panel), from the tile's staged copy (zero past
+// the panel's last column).
 template <int R, bool COL>
-__device__ __forceinline__ void pass_lane_vec(const IterDesc& d, int k, int64_t j, bool live, float (&vec)[R]) {
-  const int cur = k & 1;
+__device__ __forceinline__ void pass_lane_vec(const float* lv, int lane, float (&vec)[R]) {
 #pragma unroll
-  for (int t = 0; t < R; ++t) {
-    if (COL)
-      vec[t] = live ? d.A[cur][j * R + t] : 0.f;
-    else
-      vec[t] = live ? d.B[cur][(int64_t)t * d.n2 + j] : 0.f;
-  }
+  for (int t = 0; t < R; ++t) vec[t] = COL ? lv[lane * R + t] : lv[t * kPanelCols + lane];
 }
 
 // Row a of a tile, the lane's column: the panel entry d, L_k there (the same
@@ -283,9 +321,9 @@ __device__ __forceinline__ float pass_entry(const IterDesc& d, const PassLayout&
 // One tile, first half: the thresholded values D - S in place and this
 // thread's share of ||D||^2.  Needs only L_k, not the core SVD's outputs, so
 // it runs while the SVD does.
-template <int R, bool COL, bool BF>
+template <int R, bool COL, bool BF, int NW>
 __device__ __forceinline__ float pass_tile_threshold(const IterDesc& d, int k, float zeta, int lt,
-                                                     const PassLayout& L, unsigned char* tileP) {
+                                                     const PassLayout& L, unsigned char* tileP, const float* lv) {
   float* tileS = BF ? L.vbuf : reinterpret_cast<float*>(tileP);
   const uint16_t* tileH = reinterpret_cast<const uint16_t*>(tileP);
   const int m = COL ? d.nJ : d.nI;
@@ -294,9 +332,9 @@ __device__ __forceinline__ float pass_tile_threshold(const IterDesc& d, int k, f
   const int64_t j = (int64_t)lt * kPanelCols + lane;
   const bool live = j < ncolsTotal;
   float vec[R];
-  pass_lane_vec<R, COL>(d, k, j, live, vec);
+  pass_lane_vec<R, COL>(lv, lane, vec);
   const float msk = live ? 1.f : 0.f;
-  const int a0 = h * m / kPassWarps, a1 = (h + 1) * m / kPassWarps;
+  const int a0 = h * m / NW, a1 = (h + 1) * m / NW;
   float den = 0.f;
 #pragma unroll 2
   for (int a = a0; a < a1; ++a) pass_entry<R, COL, BF>(d, L, tileS, tileH, a, lane, j, live, vec, zeta, msk, den);
@@ -308,9 +346,10 @@ __device__ __forceinline__ float pass_tile_threshold(const IterDesc& d, int k, f
 // residuals; this share's num/den go to wsum.  FUSE: the tile was not
 // thresholded ahead of time; the threshold runs in the projection sweep and
 // its ||D||^2 share is added to den.
-template <int R, bool COL, bool BF, bool FUSE>
+template <int R, bool COL, bool BF, bool FUSE, int NW>
 __device__ __forceinline__ void pass_tile_project(const IterDesc& d, int k, int lt, const PassLayout& L,
-                                                  unsigned char* tileP, float den, bool stage_proj, float zeta) {
+                                                  unsigned char* tileP, float den, bool stage_proj, float zeta,
+                                                  const float* lv, const unsigned* lp) {
   float* tileS = BF ? L.vbuf : reinterpret_cast<float*>(tileP);
   const uint16_t* tileH = reinterpret_cast<const uint16_t*>(tileP);
   constexpr int RX = (R + 3) & ~3;
@@ -323,15 +362,13 @@ __device__ __forceinline__ void pass_tile_project(const IterDesc& d, int k, int 
   const float* proj = L.proj;
   const float* recon = COL ? L.recon : L.proj;
   const float msk = live ? 1.f : 0.f;
-  const int a0 = h * m / kPassWarps, a1 = (h + 1) * m / kPassWarps;
-  // the next iteration's index map entry of this lane's row (column), loaded
-  // before the projections so that its latency overlaps them
+  const int a0 = h * m / NW, a1 = (h + 1) * m / NW;
+  // the next iteration's index map entry of this lane's row (column)
   const int dnext = d.resample ? k + 1 : 0;
   const unsigned tag_next = (unsigned)(dnext + 1);
-  unsigned pos_next = 0u;
-  if (h == 0 && live) pos_next = __ldcg((COL ? d.posI : d.posJ)[dnext & 1] + j);
+  const unsigned pos_next = lp[lane];
   float vec[R];
-  if (FUSE) pass_lane_vec<R, COL>(d, k, j, live, vec);
+  if (FUSE) pass_lane_vec<R, COL>(lv, lane, vec);
   if (COL) {
     if (stage_proj) pass_stage_proj<R, true>(d, L, k);
   } else {
@@ -359,12 +396,12 @@ __device__ __forceinline__ void pass_tile_project(const IterDesc& d, int k, int 
 #pragma unroll
   for (int t = 0; t < R; ++t) L.part[((size_t)h * RX + t) * kPanelCols + lane] = acc[t];
   __syncthreads();
-  // projections of every column: the kPassWarps share sums in a fixed order
+  // projections of every column: the NW share sums in a fixed order
   for (int q = threadIdx.x; q < R * kPanelCols; q += blockDim.x) {
     const int t = q / kPanelCols, cc = q - t * kPanelCols;
     float s0 = 0.f, s1 = 0.f;  // even and odd shares, then their sum (a fixed order)
 #pragma unroll
-    for (int hh = 0; hh < kPassWarps; hh += 2) {
+    for (int hh = 0; hh < NW; hh += 2) {
       s0 += L.part[((size_t)hh * RX + t) * kPanelCols + cc];
       s1 += L.part[((size_t)(hh + 1) * RX + t) * kPanelCols + cc];
     }
@@ -422,11 +459,12 @@ __device__ __forceinline__ void pass_tile_project(const IterDesc& d, int k, int 
 }
 
 // After the end-of-tile barrier: the tile's num/den in its slot (share order).
+template <int NW>
 __device__ __forceinline__ void pass_tile_sums(const IterDesc& d, int gtile, const PassLayout& L) {
   if (threadIdx.x == 0) {
     float sn = 0.f, sd = 0.f;
 #pragma unroll
-    for (int h = 0; h < kPassWarps; ++h) {
+    for (int h = 0; h < NW; ++h) {
       sn += L.wsum[2 * h + 0];
       sd += L.wsum[2 * h + 1];
     }
@@ -440,25 +478,26 @@ __device__ __forceinline__ void pass_tile_sums(const IterDesc& d, int gtile, con
 // before its block's fenced counter increment, which this block has seen:
 // the slots are read from L2 with no further fence.  The kernel's completion
 // orders the state writes before the next kernel and the graph's condition.
+template <int NW>
 __device__ void pass_finalize(const IterDesc& d, int k) {
   State* st = d.st;
-  __shared__ float fin[kPassWarps][4];
+  __shared__ float fin[NW][4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nr = d.nRowTiles, nt = d.nRowTiles + d.nColTiles;
   const float2* slots = reinterpret_cast<const float2*>(d.partials);
   // thread q adds tiles q, q + 256, ... (row panel to a0, a1, column panel to
   // a2, a3); the loads of a group of four are all in flight together
   float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-  for (int b = threadIdx.x; b < nt; b += 4 * kPassThreads) {
+  for (int b = threadIdx.x; b < nt; b += 4 * 32 * NW) {
     float2 v[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int bb = b + u * kPassThreads;
+      const int bb = b + u * 32 * NW;
       v[u] = bb < nt ? __ldcg(slots + bb) : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int bb = b + u * kPassThreads;
+      const int bb = b + u * 32 * NW;
       if (bb < nr) {
         a0 += v[u].x;
         a1 += v[u].y;
@@ -482,7 +521,7 @@ __device__ void pass_finalize(const IterDesc& d, int k) {
   if (threadIdx.x == 0) {
     float f[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int w = 0; w < kPassWarps; ++w)
+    for (int w = 0; w < NW; ++w)
 #pragma unroll
       for (int q = 0; q < 4; ++q) f[q] += fin[w][q];
     // e = (||row residual|| + ||column residual||) / (||D(I,:)|| + ||D(:,J)||)
@@ -502,12 +541,12 @@ __device__ void pass_finalize(const IterDesc& d, int k) {
   __syncthreads();
 }
 
-template <int R, bool BATCH, bool BF>
+template <int R, bool BATCH, bool BF, int NW>
 __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDesc* __restrict__ ds,
                                                 const int* __restrict__ tile_base, int count, int total,
                                                 int mmax, int nbuf, unsigned char* smem) {
   constexpr int RX = (R + 3) & ~3;
-  const PassLayout L = pass_layout(smem, mmax, RX, nbuf, BF);
+  const PassLayout L = pass_layout(smem, mmax, RX, nbuf, BF, NW);
   if (!BATCH && (d1.st->done || d1.st->status)) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       d1.st->done = 1;
@@ -539,6 +578,11 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
     }
     inst = lo;
   }
+  // An instance's state (k, done, status) is fixed while this kernel runs:
+  // only the block that completes its last tile advances it, after every
+  // block has located all of its tiles.  It is read once per instance met.
+  int st_inst = -1, st_active = 0, st_k = 0;
+  float st_zeta = 0.f;
   auto locate = [&](int t, int& in) -> TileRef {
     if (BATCH)
       while (tile_base[in + 1] <= t) ++in;
@@ -548,16 +592,29 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
     const int lt = t - (BATCH ? tile_base[in] : 0);
     ref.col = lt >= d.nRowTiles;
     ref.lt = ref.col ? lt - d.nRowTiles : lt;
-    ref.active = !(d.st->done || d.st->status);
-    ref.k = d.st->k;
+    if (in != st_inst) {
+      st_inst = in;
+      st_active = !(d.st->done || d.st->status);
+      st_k = d.st->k;
+      st_zeta = (float)d.st->zeta;
+    }
+    ref.active = st_active;
+    ref.k = st_k;
     return ref;
   };
-  auto stage = [&](const TileRef& ref, unsigned char* buf) {
+  // a tile and its lane data into staging buffer bi
+  auto stage = [&](const TileRef& ref, int bi) {
     const IterDesc& d = BATCH ? ds[ref.inst] : d1;
-    if (ref.col)
+    unsigned char* buf = L.tiles + (size_t)bi * L.tile_bytes;
+    float* lv = L.lvec + (size_t)bi * kPanelCols * RX;
+    unsigned* lp = L.lpos + (size_t)bi * kPanelCols;
+    if (ref.col) {
       pass_stage_tile<true, BF>(d, ref.k, ref.lt, buf);
-    else
+      pass_stage_lane<R, true>(d, ref.k, ref.lt, lv, lp);
+    } else {
       pass_stage_tile<false, BF>(d, ref.k, ref.lt, buf);
+      pass_stage_lane<R, false>(d, ref.k, ref.lt, lv, lp);
+    }
   };
   __shared__ int is_last;
   // IRCUR-R: this block's share of the next iteration's D(I,J), while the core
@@ -571,7 +628,7 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
   }
   int pin = inst;  // instance cursor of the prefetch
   TileRef cur = locate(t0, inst);
-  if (cur.active) stage(cur, L.tiles);
+  if (cur.active) stage(cur, 0);
   cp_async_commit();
   int seg_inst = -1, seg_col = -1, seg_k = 0, run = 0;
   bool proj_staged = false;
@@ -591,12 +648,12 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
         is_last = (atomicAdd(&dp.st->counter, (unsigned)run) + (unsigned)run ==
                    (unsigned)(dp.nRowTiles + dp.nColTiles));
       __syncthreads();
-      if (is_last) pass_finalize(dp, seg_k);
+      if (is_last) pass_finalize<NW>(dp, seg_k);
       run = 0;
     }
     const int b = (t - t0) % nbuf;
     if (nbuf == 1 && t > t0 && cur.active) {
-      stage(cur, L.tiles);
+      stage(cur, 0);
       cp_async_commit();
     }
     bool pre = false;
@@ -607,7 +664,7 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
       nx = locate(t + 1, in2);
       pin = in2;
       if (nx.active) {
-        stage(nx, L.tiles + (size_t)(b ^ 1) * L.tile_bytes);
+        stage(nx, b ^ 1);
         pre = true;
       }
       cp_async_commit();
@@ -621,7 +678,7 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
       seg_inst = cur.inst;
       seg_col = cur.col;
       seg_k = cur.k;
-      zeta = (float)d.st->zeta;
+      zeta = st_inst == cur.inst ? st_zeta : (float)d.st->zeta;
       if (cur.col)
         pass_stage_side<R, true>(d, L, seg_k);
       else
@@ -634,6 +691,8 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
       cp_async_wait_group<0>();
     __syncthreads();
     unsigned char* tb = L.tiles + (size_t)b * L.tile_bytes;
+    const float* lvb = L.lvec + (size_t)b * kPanelCols * RX;
+    const unsigned* lpb = L.lpos + (size_t)b * kPanelCols;
     // a tile met after the segment's wait for the SVD (and not thresholded
     // ahead of time) is thresholded inside its projection sweep
     const bool fuse = proj_staged && early != t;
@@ -641,8 +700,8 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
     if (early == t) {
       den = den_early;
     } else if (!fuse) {
-      den = cur.col ? pass_tile_threshold<R, true, BF>(d, seg_k, zeta, cur.lt, L, tb)
-                    : pass_tile_threshold<R, false, BF>(d, seg_k, zeta, cur.lt, L, tb);
+      den = cur.col ? pass_tile_threshold<R, true, BF, NW>(d, seg_k, zeta, cur.lt, L, tb, lvb)
+                    : pass_tile_threshold<R, false, BF, NW>(d, seg_k, zeta, cur.lt, L, tb, lvb);
     }
     // before the segment's first wait for the SVD: threshold the prefetched
     // next tile of the same segment as well (FP32 panels: in its own buffer)
@@ -650,24 +709,25 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
       cp_async_wait_group<0>();
       __syncthreads();
       unsigned char* tn = L.tiles + (size_t)(b ^ 1) * L.tile_bytes;
-      den_early = cur.col ? pass_tile_threshold<R, true, BF>(d, seg_k, zeta, nx.lt, L, tn)
-                          : pass_tile_threshold<R, false, BF>(d, seg_k, zeta, nx.lt, L, tn);
+      const float* lvn = L.lvec + (size_t)(b ^ 1) * kPanelCols * RX;
+      den_early = cur.col ? pass_tile_threshold<R, true, BF, NW>(d, seg_k, zeta, nx.lt, L, tn, lvn)
+                          : pass_tile_threshold<R, false, BF, NW>(d, seg_k, zeta, nx.lt, L, tn, lvn);
       early = t + 1;
     }
     if (fuse) {
       if (cur.col)
-        pass_tile_project<R, true, BF, true>(d, seg_k, cur.lt, L, tb, den, false, zeta);
+        pass_tile_project<R, true, BF, true, NW>(d, seg_k, cur.lt, L, tb, den, false, zeta, lvb, lpb);
       else
-        pass_tile_project<R, false, BF, true>(d, seg_k, cur.lt, L, tb, den, false, zeta);
+        pass_tile_project<R, false, BF, true, NW>(d, seg_k, cur.lt, L, tb, den, false, zeta, lvb, lpb);
     } else {
       if (cur.col)
-        pass_tile_project<R, true, BF, false>(d, seg_k, cur.lt, L, tb, den, !proj_staged, zeta);
+        pass_tile_project<R, true, BF, false, NW>(d, seg_k, cur.lt, L, tb, den, !proj_staged, zeta, lvb, lpb);
       else
-        pass_tile_project<R, false, BF, false>(d, seg_k, cur.lt, L, tb, den, !proj_staged, zeta);
+        pass_tile_project<R, false, BF, false, NW>(d, seg_k, cur.lt, L, tb, den, !proj_staged, zeta, lvb, lpb);
     }
     proj_staged = true;
     __syncthreads();
-    pass_tile_sums(d, t - (BATCH ? tile_base[cur.inst] : 0), L);
+    pass_tile_sums<NW>(d, t - (BATCH ? tile_base[cur.inst] : 0), L);
     ++run;
   }
   if (run > 0) {
@@ -677,7 +737,7 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
     if (threadIdx.x == 0)
       is_last = (atomicAdd(&dp.st->counter, (unsigned)run) + (unsigned)run == (unsigned)(dp.nRowTiles + dp.nColTiles));
     __syncthreads();
-    if (is_last) pass_finalize(dp, seg_k);
+    if (is_last) pass_finalize<NW>(dp, seg_k);
   }
   cp_async_wait_group<0>();
   if (!BATCH && d1.trace) {
@@ -687,11 +747,14 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
   }
 }
 
-template <int R, bool BF>
-__global__ void __launch_bounds__(kPassThreads, (R <= 10 ? 2 : 1)) pass_kernel(IterDesc d, int nbuf) {
+// NW warps per block: 16, two blocks per SM up to R = 10 (64 registers); 32
+// (one block per SM, 64 registers) where the shared memory of one 16-warp
+// block already fills an SM (pass_warps).
+template <int R, bool BF, int NW>
+__global__ void __launch_bounds__(32 * NW, (NW == 32 || R > 10) ? 1 : 2) pass_kernel(IterDesc d, int nbuf) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int mmax = d.nI > d.nJ ? d.nI : d.nJ;
-  pass_persistent<R, false, BF>(d, nullptr, nullptr, 1, d.nRowTiles + d.nColTiles, mmax, nbuf, smem);
+  pass_persistent<R, false, BF, NW>(d, nullptr, nullptr, 1, d.nRowTiles + d.nColTiles, mmax, nbuf, smem);
 }
 
 // Batched form: the tiles of every instance back to back (tile_base[i] is the
@@ -701,7 +764,7 @@ __global__ void __launch_bounds__(kPassThreads, (R <= 10 ? 2 : 1)) pass_batch_ke
                                                                   const int* __restrict__ tile_base, int count,
                                                                   int mmax, int nbuf) {
   extern __shared__ __align__(16) unsigned char smem[];
-  pass_persistent<R, true, false>(ds[0], ds, tile_base, count, tile_base[count], mmax, nbuf, smem);
+  pass_persistent<R, true, false, kPassWarps>(ds[0], ds, tile_base, count, tile_base[count], mmax, nbuf, smem);
 }
 
 
@@ -722,25 +785,37 @@ __global__ void batch_check_kernel(const IterDesc* __restrict__ ds, int count, u
   }
 }
 
-// Shared memory of the pass kernel: two tile buffers when they fit next to
-// the small matrices, else one (no prefetch).
-size_t pass_smem_bytes(int nI, int nJ, int Rpad, int* nbuf_out, bool bf16, bool single) {
+// Shared memory of the pass kernel with nw warps per block: two tile buffers
+// when they fit next to the small matrices, else one (no prefetch).
+size_t pass_smem_bytes(int nI, int nJ, int Rpad, int* nbuf_out, bool bf16, bool single, int nw) {
   const int m = nI > nJ ? nI : nJ;
   const int rx = (Rpad + 3) & ~3;
   int nbuf = 2;
-  size_t bytes = pass_layout_floats(m, rx, 2, bf16) * 4 + 64;
+  size_t bytes = pass_layout_floats(m, rx, 2, bf16, nw) * 4 + 64;
   if (bytes > 227 * 1024 || single) {
     nbuf = 1;
-    bytes = pass_layout_floats(m, rx, 1, bf16) * 4 + 64;
+    bytes = pass_layout_floats(m, rx, 1, bf16, nw) * 4 + 64;
   }
   if (nbuf_out) *nbuf_out = nbuf;
   return bytes;
 }
 
+// Warps per block of the single-instance pass: 32 where one 16-warp block's
+// shared memory leaves no room for a second on an SM (large |I|, |J| or r)
+// and the 32-warp block fits with the same tile buffers, for padded ranks
+// 8..10 (64 registers a thread); 16 otherwise.
+int pass_warps(int nI, int nJ, int Rpad, bool bf16, bool single) {
+  if (Rpad < 8 || Rpad > 10) return kPassWarps;
+  int nb16 = 0, nb32 = 0;
+  const size_t b16 = pass_smem_bytes(nI, nJ, Rpad, &nb16, bf16, single, kPassWarps);
+  const size_t b32 = pass_smem_bytes(nI, nJ, Rpad, &nb32, bf16, single, 2 * kPassWarps);
+  return (2 * b16 > 228 * 1024 && b32 <= 227 * 1024 && nb32 == nb16) ? 2 * kPassWarps : kPassWarps;
+}
+
 // Resident blocks of a pass kernel on the current device, cached per (device,
 // kernel, shared-memory size).  Solves on several host threads may ask at
 // once: the cache is guarded by a mutex.
-static int pass_grid(const void* fn, size_t smem) {
+static int pass_grid(const void* fn, size_t smem, int threads) {
   struct Entry {
     int dev;
     const void* fn;
@@ -761,7 +836,7 @@ static int pass_grid(const void* fn, size_t smem) {
   if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || num_sms <= 0)
     num_sms = kNumSMsHint;
   int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPassThreads, smem) != cudaSuccess || per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   const int blocks = per_sm * num_sms;
   std::lock_guard<std::mutex> lock(mu);
@@ -773,11 +848,12 @@ cudaError_t launch_svd(const IterDesc& d, int Rpad, cudaStream_t s);
 // A launch that may overlap the tail of the previous kernel in the stream
 // (programmatic stream serialization; the kernel waits with pdl_wait()).
 template <typename... Args>
-static cudaError_t launch_pdl(void (*kernel)(Args...), int grid, size_t smem, cudaStream_t s, Args... args) {
+static cudaError_t launch_pdl(void (*kernel)(Args...), int grid, int threads, size_t smem, cudaStream_t s,
+                              Args... args) {
   cudaLaunchConfig_t cfg;
   memset(&cfg, 0, sizeof(cfg));
   cfg.gridDim = dim3((unsigned)grid, 1, 1);
-  cfg.blockDim = dim3(kPassThreads, 1, 1);
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -788,27 +864,36 @@ static cudaError_t launch_pdl(void (*kernel)(Args...), int grid, size_t smem, cu
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// The single-instance pass kernel for R and the block's warp count, the
+// shared memory it takes and its staging buffers.
+template <int R>
+static const void* pass_fn(const IterDesc& d, size_t* bytes, int* nbuf, int* nw) {
+  const bool bf = d.bf16 != 0, single = d.passSingleBuf != 0;
+  *nw = pass_warps(d.nI, d.nJ, R, bf, single);
+  *bytes = pass_smem_bytes(d.nI, d.nJ, R, nbuf, bf, single, *nw);
+  if constexpr (R >= 8 && R <= 10) {
+    if (*nw == 2 * kPassWarps)
+      return bf ? (const void*)pass_kernel<R, true, 2 * kPassWarps> : (const void*)pass_kernel<R, false, 2 * kPassWarps>;
+  }
+  return bf ? (const void*)pass_kernel<R, true, kPassWarps> : (const void*)pass_kernel<R, false, kPassWarps>;
+}
+
 template <int R>
 static cudaError_t launch_iter_r(const IterDesc& d, cudaStream_t s) {
   {
     cudaError_t e = launch_svd(d, R, s);
     if (e != cudaSuccess) return e;
   }
-  int nbuf = 1;
-  const size_t bytes = pass_smem_bytes(d.nI, d.nJ, R, &nbuf, d.bf16 != 0, d.passSingleBuf != 0);
+  size_t bytes = 0;
+  int nbuf = 1, nw = kPassWarps;
+  const void* fn = pass_fn<R>(d, &bytes, &nbuf, &nw);
   const int total = d.nRowTiles + d.nColTiles;
-  if (d.bf16) {
-    cudaError_t e = cudaFuncSetAttribute(pass_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    int grid = d.passGrid > 0 ? d.passGrid : pass_grid((const void*)pass_kernel<R, true>, bytes);
-    if (grid > total) grid = total;
-    return launch_pdl(pass_kernel<R, true>, grid, bytes, s, d, nbuf);
-  }
-  cudaError_t e = cudaFuncSetAttribute(pass_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  int grid = d.passGrid > 0 ? d.passGrid : pass_grid((const void*)pass_kernel<R, false>, bytes);
+  int grid = d.passGrid > 0 ? d.passGrid : pass_grid(fn, bytes, 32 * nw);
   if (grid > total) grid = total;
-  return launch_pdl(pass_kernel<R, false>, grid, bytes, s, d, nbuf);
+  auto kernel = reinterpret_cast<void (*)(IterDesc, int)>(const_cast<void*>(fn));
+  return launch_pdl(kernel, grid, 32 * nw, bytes, s, d, nbuf);
 }
 
 template <int R>
@@ -818,29 +903,29 @@ static cudaError_t launch_batch_iter_r(const BatchLaunch& b, cudaStream_t s) {
   e = cudaFuncSetAttribute(pass_batch_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.pass_smem);
   if (e != cudaSuccess) return e;
   {
-    int grid = b.pass_grid > 0 ? b.pass_grid : pass_grid((const void*)pass_batch_kernel<R>, b.pass_smem);
+    int grid = b.pass_grid > 0 ? b.pass_grid : pass_grid((const void*)pass_batch_kernel<R>, b.pass_smem, kPassThreads);
     if (grid > b.total_tiles) grid = b.total_tiles;
     // a programmatic dependent of the batch's (last) core-SVD launch, as in
     // the single-instance iteration
-    return launch_pdl(pass_batch_kernel<R>, grid, b.pass_smem, s, b.ds, b.tile_base, b.count, b.pass_mmax,
-                      b.pass_nbuf);
+    return launch_pdl(pass_batch_kernel<R>, grid, kPassThreads, b.pass_smem, s, b.ds, b.tile_base, b.count,
+                      b.pass_mmax, b.pass_nbuf);
   }
 }
 
 template <int R>
 static int pass_resident_r(const IterDesc& d) {
-  int nbuf = 1;
-  const size_t bytes = pass_smem_bytes(d.nI, d.nJ, R, &nbuf, d.bf16 != 0, d.passSingleBuf != 0);
-  const void* fn = d.bf16 ? (const void*)pass_kernel<R, true> : (const void*)pass_kernel<R, false>;
+  size_t bytes = 0;
+  int nbuf = 1, nw = kPassWarps;
+  const void* fn = pass_fn<R>(d, &bytes, &nbuf, &nw);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) return 0;
-  return pass_grid(fn, bytes);
+  return pass_grid(fn, bytes, 32 * nw);
 }
 
 template <int R>
 static int pass_batch_resident_r(const BatchLaunch& b) {
   const void* fn = (const void*)pass_batch_kernel<R>;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.pass_smem) != cudaSuccess) return 0;
-  return pass_grid(fn, b.pass_smem);
+  return pass_grid(fn, b.pass_smem, kPassThreads);
 }
 
 #define IRCUR_R_DISPATCH(FN, ARG)    \

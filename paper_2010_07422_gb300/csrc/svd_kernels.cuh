@@ -185,6 +185,7 @@ __device__ __forceinline__ float slab_product(const float* __restrict__ base, in
   float v[NV];  // v[g R + t]: partial sum of out(row0 + g, t)
 #pragma unroll
   for (int e = 0; e < NV; ++e) v[e] = 0.f;
+#pragma unroll 2
   for (int k = lane; k < ninner; k += 32) {
     float mv[R];
 #pragma unroll
@@ -271,6 +272,56 @@ __device__ int warp_chol(const float* G, int r, float* Uw, float* dw, float& min
 #pragma unroll
         for (int u = t + 1; u < R; ++u) g[u] = fmaf(-ul, urow[u], g[u]);
       }
+      brk += keep ? 0 : 1;
+    } else if (lane == 0) {
+      dw[t] = 0.f;
+#pragma unroll
+      for (int u = 0; u < R; ++u) Uw[t * R + u] = 0.f;
+    }
+  }
+  __syncwarp();
+  minsp = msp;
+  return brk;
+}
+
+// Cholesky factor of the R x R Gram matrix G (full, row-major, shared memory)
+// formed in every lane's registers, with the FMA order of warp_chol (so the
+// same factor bit for bit): no shuffles on the dependent path.
+template <int R>
+__device__ int lane_chol(const float* G, int r, float* Uw, float* dw, float& minsp) {
+  const int lane = threadIdx.x & 31;
+  float a[R][R];
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) a[i][j] = (i < r && j < r && j >= i) ? G[i * R + j] : 0.f;
+  float maxd = 0.f;
+#pragma unroll
+  for (int i = 0; i < R; ++i) maxd = fmaxf(maxd, a[i][i]);
+  float g0[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) g0[i] = a[i][i];
+  int brk = 0;
+  float msp = 1.f;
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    if (t < r) {
+      const float dgt = a[t][t];
+      const bool keep = dgt > 1e-12f * maxd && dgt <= FLT_MAX;
+      const float rinv = keep ? rsqrtf(dgt) : 0.f;
+      if (g0[t] > 1e-10f * maxd) msp = fminf(msp, keep ? __fdividef(dgt, g0[t]) : 0.f);
+      float urow[R];
+#pragma unroll
+      for (int u = 0; u < R; ++u) urow[u] = (u >= t) ? a[t][u] * rinv : 0.f;
+      if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < R; ++u) Uw[t * R + u] = urow[u];
+        dw[t] = rinv;
+      }
+#pragma unroll
+      for (int i = t + 1; i < R; ++i)
+#pragma unroll
+        for (int u = i; u < R; ++u) a[i][u] = fmaf(-urow[i], urow[u], a[i][u]);
       brk += keep ? 0 : 1;
     } else if (lane == 0) {
       dw[t] = 0.f;
@@ -611,7 +662,11 @@ __device__ __forceinline__ int svd_factor(const float* slots, int nc, int sl, in
 #pragma unroll
   for (int t = 0; t < R; ++t) tr += t < r ? Gw[t * R + t] : 0.f;
   trace = tr;
-  return warp_chol<R>(Gw, r, F, dF, minsp);
+  // up to R = 8 the whole factor fits a lane's registers (no shuffles)
+  if constexpr (R <= 8)
+    return lane_chol<R>(Gw, r, F, dF, minsp);
+  else
+    return warp_chol<R>(Gw, r, F, dF, minsp);
 }
 
 template <int R>
