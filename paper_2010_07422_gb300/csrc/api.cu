@@ -777,8 +777,7 @@ extern "C" ircur_status ircur_get_launch_shape(ircur_ctx* c, int32_t* svd_ctas, 
   const IterDesc& d = c->desc;
   if (svd_ctas) *svd_ctas = d.svdNC;
   int nbuf = 1;
-  const int nw = pass_warps(d.nI, d.nJ, c->Rpad, d.bf16 != 0, d.passSingleBuf != 0);
-  pass_smem_bytes(d.nI, d.nJ, c->Rpad, &nbuf, d.bf16 != 0, d.passSingleBuf != 0, nw);
+  pass_smem_bytes(d.nI, d.nJ, c->Rpad, &nbuf, d.bf16 != 0, d.passSingleBuf != 0);
   if (pass_bufs) *pass_bufs = nbuf;
   if (pass_blocks) {
     int g = d.passGrid > 0 ? d.passGrid : pass_resident_blocks(d, c->Rpad);

@@ -35,6 +35,30 @@ __device__ __forceinline__ float lowrank_entry(const float* a, const float* b) {
   return acc;
 }
 
+// Two FMAs in one packed FP32 instruction (fma.rn.f32x2): d.x = fma(a.x, b.x,
+// c.x), d.y = fma(a.y, b.y, c.y), each rounded to nearest like fmaf, so a
+// chain of them gives, element by element, the values of the scalar chain.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  unsigned long long ua, ub, uc, ud;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ua) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ub) : "f"(b.x), "f"(b.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(uc) : "f"(c.x), "f"(c.y));
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(ud) : "l"(ua), "l"(ub), "l"(uc));
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(ud));
+  return d;
+}
+
+// lowrank_entry for two columns at once: a broadcast to both, b0 and b1 the
+// two columns; element for element the same FMA chain as lowrank_entry.
+template <int R>
+__device__ __forceinline__ float2 lowrank_entry2(const float* a, const float2* b) {
+  float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int t = 0; t < R; ++t) acc = ffma2(make_float2(a[t], a[t]), b[t], acc);
+  return acc;
+}
+
 // BF16 storage of a panel entry (round to nearest even) and its value.
 __device__ __forceinline__ uint16_t f32_to_bf16_bits(float x) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(x));

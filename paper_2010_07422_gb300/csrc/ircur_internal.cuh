@@ -32,9 +32,8 @@ constexpr int kGraphUnroll = IRCUR_GRAPH_UNROLL;
 constexpr int kTraceSlots = 4;
 
 // Panel-pass tiling: a tile is kPanelCols consecutive panel columns; a block
-// of kPassWarps warps (2 kPassWarps for large single-instance panels at
-// padded ranks 8..10, pass_warps) computes one tile at a time, warp h owning
-// row share h and lane c column c.  Each tile leaves its (num, den) partial sums in
+// of kPassWarps warps computes one tile at a time, warp h owning row share h
+// and lane l the column pair 2 (l & 15), 2 (l & 15) + 1 on every other row.  Each tile leaves its (num, den) partial sums in
 // `partials`.
 constexpr int kPanelCols = 32;
 constexpr int kPassWarps = 16;
@@ -235,7 +234,6 @@ size_t adj_cg_smem_bytes(int nI, int nJ, int Rpad);
 cudaError_t launch_adj_scatter(const AdjStep& a, float* dD, int64_t lddD, cudaStream_t s);
 size_t pass_smem_bytes(int nI, int nJ, int Rpad, int* nbuf = nullptr, bool bf16 = false, bool single = false,
                        int nw = kPassWarps);
-int pass_warps(int nI, int nJ, int Rpad, bool bf16, bool single);
 // Alg. 2 on the factored iterate (k_cur2svd.cu).
 size_t cur_to_svd_scratch_bytes(int64_t n1, int64_t n2, int Rpad);
 cudaError_t launch_cur_to_svd(const float* A, const float* B, int64_t n1, int64_t n2, int r, int Rpad, void* scratch,

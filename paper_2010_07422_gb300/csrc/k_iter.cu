@@ -275,46 +275,66 @@ __device__ __forceinline__ void pass_stage_proj(const IterDesc& d, const PassLay
   __syncthreads();
 }
 
-// The lane's column of the current iterate's other factor, B_k(:,j) (row
+// Tile work layout: lane l of warp h owns the column pair c0 = 2 (l & 15),
+// c0 + 1, and the rows a0(h) + (l >> 4), +2, +4, ... of the warp's row share,
+// so that each broadcast read of a row of the small matrices serves two
+// entries and the r-wide products run as packed FP32 pairs (ffma2).
+
+// The pair's columns of the current iterate's other factor, B_k(:,j) (row
 // panel) or A_k(i,:)^T (column panel), from the tile's staged copy (zero past
 // the panel's last column).
 template <int R, bool COL>
-__device__ __forceinline__ void pass_lane_vec(const float* lv, int lane, float (&vec)[R]) {
+__device__ __forceinline__ void pass_pair_vec(const float* lv, int c0, float2 (&vec)[R]) {
 #pragma unroll
-  for (int t = 0; t < R; ++t) vec[t] = COL ? lv[lane * R + t] : lv[t * kPanelCols + lane];
+  for (int t = 0; t < R; ++t)
+    vec[t] = COL ? make_float2(lv[c0 * R + t], lv[(c0 + 1) * R + t])
+                 : *reinterpret_cast<const float2*>(lv + t * kPanelCols + c0);
 }
 
-// Row a of a tile, the lane's column: the panel entry d, L_k there (the same
-// FMA chain as the core, lowrank_entry), and D - S = D - T_zeta(D - L_k)
-// written in place (BF16 panels: to the FP32 work buffer).  Adds d^2 to den.
-template <int R, bool COL, bool BF>
-__device__ __forceinline__ float pass_entry(const IterDesc& d, const PassLayout& L, float* tileS,
-                                            const uint16_t* tileH, int a, int lane, int64_t j, bool live,
-                                            const float (&vec)[R], float zeta, float msk, float& den) {
+// Row a of the small matrix M (RX floats a row) as R values.
+template <int R>
+__device__ __forceinline__ void pass_row(const float* M, int a, float (&v)[R]) {
   constexpr int RX = (R + 3) & ~3;
-  float* cell = tileS + (size_t)a * kPanelCols + lane;
-  float sr[R];
 #pragma unroll
   for (int t4 = 0; t4 < RX / 4; ++t4) {
-    const float4 sv = *reinterpret_cast<const float4*>(L.side + (size_t)a * RX + 4 * t4);
-    const float s4[4] = {sv.x, sv.y, sv.z, sv.w};
+    const float4 q = *reinterpret_cast<const float4*>(M + (size_t)a * RX + 4 * t4);
+    const float q4[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
     for (int e = 0; e < 4; ++e)
-      if (4 * t4 + e < R) sr[4 * t4 + e] = s4[e];
+      if (4 * t4 + e < R) v[4 * t4 + e] = q4[e];
   }
-  const float l = lowrank_entry<R>(sr, vec);
-  float dv;
+}
+
+// Row a of a tile, the pair's columns: the panel entries d, L_k there (the
+// same FMA chain as the core, element for element), and D - S = D -
+// T_zeta(D - L_k) written in place (BF16 panels: to the FP32 work buffer).
+// Adds d^2 to den.  Columns past the panel's last are zero in the tile and in
+// the staged factor, so they give zero.
+template <int R, bool COL, bool BF>
+__device__ __forceinline__ float2 pass_entry2(const IterDesc& d, const PassLayout& L, float* tileS,
+                                              const uint16_t* tileH, int a, int c0, int64_t j0,
+                                              const float2 (&vec)[R], float zeta, float2& den) {
+  float sr[R];
+  pass_row<R>(L.side, a, sr);
+  const float2 l = lowrank_entry2<R>(sr, vec);
+  float2* cell = reinterpret_cast<float2*>(tileS + (size_t)a * kPanelCols + c0);
+  float2 dv;
   if (BF) {
-    dv = bf16_entry(tileH[(size_t)a * kPanelCols + lane], l, zeta, [&]() {
-      if (!live) return 0.f;
+    const int64_t ncolsTotal = COL ? d.n1 : d.n2;
+    const uint32_t hv = *reinterpret_cast<const uint32_t*>(tileH + (size_t)a * kPanelCols + c0);
+    auto fp32 = [&](int c) {
+      const int64_t j = j0 + c;
+      if (j >= ncolsTotal) return 0.f;
       return COL ? d.D[j * d.ldD + d.J_all[a]] : d.D[(int64_t)d.I_all[a] * d.ldD + j];
-    });
+    };
+    dv.x = bf16_entry((uint16_t)(hv & 0xffffu), l.x, zeta, [&]() { return fp32(c0); });
+    dv.y = bf16_entry((uint16_t)(hv >> 16), l.y, zeta, [&]() { return fp32(c0 + 1); });
   } else {
     dv = *cell;
   }
-  const float v = panel_value(dv, l, zeta) * msk;
+  const float2 v = make_float2(panel_value(dv.x, l.x, zeta), panel_value(dv.y, l.y, zeta));
   *cell = v;
-  den = fmaf(dv, dv, den);
+  den = ffma2(dv, dv, den);
   return v;
 }
 
@@ -327,18 +347,16 @@ __device__ __forceinline__ float pass_tile_threshold(const IterDesc& d, int k, f
   float* tileS = BF ? L.vbuf : reinterpret_cast<float*>(tileP);
   const uint16_t* tileH = reinterpret_cast<const uint16_t*>(tileP);
   const int m = COL ? d.nJ : d.nI;
-  const int64_t ncolsTotal = COL ? d.n1 : d.n2;
   const int lane = threadIdx.x & 31, h = threadIdx.x >> 5;
-  const int64_t j = (int64_t)lt * kPanelCols + lane;
-  const bool live = j < ncolsTotal;
-  float vec[R];
-  pass_lane_vec<R, COL>(lv, lane, vec);
-  const float msk = live ? 1.f : 0.f;
+  const int c0 = 2 * (lane & 15), hr = lane >> 4;
+  const int64_t j0 = (int64_t)lt * kPanelCols;
+  float2 vec[R];
+  pass_pair_vec<R, COL>(lv, c0, vec);
   const int a0 = h * m / NW, a1 = (h + 1) * m / NW;
-  float den = 0.f;
+  float2 den = make_float2(0.f, 0.f);
 #pragma unroll 2
-  for (int a = a0; a < a1; ++a) pass_entry<R, COL, BF>(d, L, tileS, tileH, a, lane, j, live, vec, zeta, msk, den);
-  return den;
+  for (int a = a0 + hr; a < a1; a += 2) pass_entry2<R, COL, BF>(d, L, tileS, tileH, a, c0, j0, vec, zeta, den);
+  return den.x + den.y;
 }
 
 // One tile, second half: the projections (they need the core SVD's outputs,
@@ -348,7 +366,7 @@ __device__ __forceinline__ float pass_tile_threshold(const IterDesc& d, int k, f
 // its ||D||^2 share is added to den.
 template <int R, bool COL, bool BF, bool FUSE, int NW>
 __device__ __forceinline__ void pass_tile_project(const IterDesc& d, int k, int lt, const PassLayout& L,
-                                                  unsigned char* tileP, float den, bool stage_proj, float zeta,
+                                                  unsigned char* tileP, float den_in, bool stage_proj, float zeta,
                                                   const float* lv, const unsigned* lp) {
   float* tileS = BF ? L.vbuf : reinterpret_cast<float*>(tileP);
   const uint16_t* tileH = reinterpret_cast<const uint16_t*>(tileP);
@@ -357,44 +375,41 @@ __device__ __forceinline__ void pass_tile_project(const IterDesc& d, int k, int 
   const int64_t ncolsTotal = COL ? d.n1 : d.n2;
   const int nxt = (k & 1) ^ 1;
   const int lane = threadIdx.x & 31, h = threadIdx.x >> 5;
-  const int64_t j = (int64_t)lt * kPanelCols + lane;
-  const bool live = j < ncolsTotal;
+  const int c0 = 2 * (lane & 15), hr = lane >> 4;
+  const int64_t j0 = (int64_t)lt * kPanelCols;
   const float* proj = L.proj;
   const float* recon = COL ? L.recon : L.proj;
-  const float msk = live ? 1.f : 0.f;
   const int a0 = h * m / NW, a1 = (h + 1) * m / NW;
-  // the next iteration's index map entry of this lane's row (column)
-  const int dnext = d.resample ? k + 1 : 0;
-  const unsigned tag_next = (unsigned)(dnext + 1);
-  const unsigned pos_next = lp[lane];
-  float vec[R];
-  if (FUSE) pass_lane_vec<R, COL>(lv, lane, vec);
+  float2 vec[R];
+  if (FUSE) pass_pair_vec<R, COL>(lv, c0, vec);
   if (COL) {
     if (stage_proj) pass_stage_proj<R, true>(d, L, k);
   } else {
     if (stage_proj) pass_stage_proj<R, false>(d, L, k);
   }
-  float acc[R];
+  float2 den2 = make_float2(0.f, 0.f);
+  float2 acc[R];
 #pragma unroll
-  for (int t = 0; t < R; ++t) acc[t] = 0.f;
+  for (int t = 0; t < R; ++t) acc[t] = make_float2(0.f, 0.f);
 #pragma unroll 2
-  for (int a = a0; a < a1; ++a) {
-    const float v = FUSE ? pass_entry<R, COL, BF>(d, L, tileS, tileH, a, lane, j, live, vec, zeta, msk, den)
-                         : tileS[(size_t)a * kPanelCols + lane];
+  for (int a = a0 + hr; a < a1; a += 2) {
+    const float2 v = FUSE ? pass_entry2<R, COL, BF>(d, L, tileS, tileH, a, c0, j0, vec, zeta, den2)
+                          : *reinterpret_cast<const float2*>(tileS + (size_t)a * kPanelCols + c0);
     float pr[R];
+    pass_row<R>(proj, a, pr);
 #pragma unroll
-    for (int t4 = 0; t4 < RX / 4; ++t4) {
-      const float4 pv = *reinterpret_cast<const float4*>(proj + (size_t)a * RX + 4 * t4);
-      const float p4[4] = {pv.x, pv.y, pv.z, pv.w};
-#pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if (4 * t4 + e < R) pr[4 * t4 + e] = p4[e];
-    }
-#pragma unroll
-    for (int t = 0; t < R; ++t) acc[t] = fmaf(pr[t], v, acc[t]);
+    for (int t = 0; t < R; ++t) acc[t] = ffma2(make_float2(pr[t], pr[t]), v, acc[t]);
   }
+  // the two half-warps' rows, then this warp's share of every column
 #pragma unroll
-  for (int t = 0; t < R; ++t) L.part[((size_t)h * RX + t) * kPanelCols + lane] = acc[t];
+  for (int t = 0; t < R; ++t) {
+    acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, 16);
+    acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, 16);
+  }
+  if (hr == 0) {
+#pragma unroll
+    for (int t = 0; t < R; ++t) *reinterpret_cast<float2*>(L.part + ((size_t)h * RX + t) * kPanelCols + c0) = acc[t];
+  }
   __syncthreads();
   // projections of every column: the NW share sums in a fixed order
   for (int q = threadIdx.x; q < R * kPanelCols; q += blockDim.x) {
@@ -408,50 +423,55 @@ __device__ __forceinline__ void pass_tile_project(const IterDesc& d, int k, int 
     L.outS[(size_t)t * kPanelCols + cc] = s0 + s1;
   }
   __syncthreads();
-  float out[R];
+  float2 out[R];
 #pragma unroll
-  for (int t = 0; t < R; ++t) out[t] = L.outS[(size_t)t * kPanelCols + lane];
-  float num = 0.f;
+  for (int t = 0; t < R; ++t) out[t] = *reinterpret_cast<const float2*>(L.outS + (size_t)t * kPanelCols + c0);
+  float2 num2 = make_float2(0.f, 0.f);
 #pragma unroll 2
-  for (int a = a0; a < a1; ++a) {
-    const float v = tileS[(size_t)a * kPanelCols + lane];
+  for (int a = a0 + hr; a < a1; a += 2) {
+    const float2 v = *reinterpret_cast<const float2*>(tileS + (size_t)a * kPanelCols + c0);
     float rr[R];
+    pass_row<R>(recon, a, rr);
+    float2 w = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int t4 = 0; t4 < RX / 4; ++t4) {
-      const float4 rv = *reinterpret_cast<const float4*>(recon + (size_t)a * RX + 4 * t4);
-      const float r4[4] = {rv.x, rv.y, rv.z, rv.w};
-#pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if (4 * t4 + e < R) rr[4 * t4 + e] = r4[e];
-    }
-    float w = 0.f;
-#pragma unroll
-    for (int t = 0; t < R; ++t) w = fmaf(rr[t], out[t], w);
-    const float e = (v - w) * msk;
-    num = fmaf(e, e, num);
+    for (int t = 0; t < R; ++t) w = ffma2(make_float2(rr[t], rr[t]), out[t], w);
+    const float2 e = make_float2(v.x - w.x, v.y - w.y);
+    num2 = ffma2(e, e, num2);
   }
-  if (h == 0 && live) {
-    if (COL) {
-      float* An = d.A[nxt];
+  if (h == 0 && hr == 0) {
+    // the next iteration's index map entries of the pair's rows (columns)
+    const int dnext = d.resample ? k + 1 : 0;
+    const unsigned tag_next = (unsigned)(dnext + 1);
 #pragma unroll
-      for (int t = 0; t < R; ++t) An[j * R + t] = out[t];
-    } else {
-      float* Bn = d.B[nxt];
+    for (int u = 0; u < 2; ++u) {
+      const int64_t j = j0 + c0 + u;
+      if (j >= ncolsTotal) continue;
+      float o[R];
 #pragma unroll
-      for (int t = 0; t < R; ++t) Bn[(int64_t)t * d.n2 + j] = out[t];
-    }
-    // rows (columns) in the next iteration's index set also go to its compact
-    // side matrix, at their position in the set
-    if (index_tag_is(pos_next, tag_next)) {
-      float* side = COL ? d.AI[nxt] : d.BJt[nxt];
-      const int a = index_tag_pos(pos_next);
+      for (int t = 0; t < R; ++t) o[t] = u ? out[t].y : out[t].x;
+      if (COL) {
+        float* An = d.A[nxt];
 #pragma unroll
-      for (int t = 0; t < R; ++t) side[(size_t)a * R + t] = out[t];
+        for (int t = 0; t < R; ++t) An[j * R + t] = o[t];
+      } else {
+        float* Bn = d.B[nxt];
+#pragma unroll
+        for (int t = 0; t < R; ++t) Bn[(int64_t)t * d.n2 + j] = o[t];
+      }
+      // rows (columns) in the next iteration's index set also go to its
+      // compact side matrix, at their position in the set
+      const unsigned pos_next = lp[c0 + u];
+      if (index_tag_is(pos_next, tag_next)) {
+        float* side = COL ? d.AI[nxt] : d.BJt[nxt];
+        const int a = index_tag_pos(pos_next);
+#pragma unroll
+        for (int t = 0; t < R; ++t) side[(size_t)a * R + t] = o[t];
+      }
     }
   }
   // this share's sums; the tile's slot gets them in share order after the
   // block's end-of-tile barrier (pass_tile_sums)
-  const float sn = warp_sum(num), sd = warp_sum(den);
+  const float sn = warp_sum(num2.x + num2.y), sd = warp_sum(den_in + (den2.x + den2.y));
   if (lane == 0) {
     L.wsum[2 * h + 0] = sn;
     L.wsum[2 * h + 1] = sd;
@@ -747,11 +767,10 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
   }
 }
 
-// NW warps per block: 16, two blocks per SM up to R = 10 (64 registers); 32
-// (one block per SM, 64 registers) where the shared memory of one 16-warp
-// block already fills an SM (pass_warps).
+// NW warps per block; two blocks per SM up to R = 7 (64 registers a thread),
+// one above (the pair layout keeps 4R FP32 values of the two columns live).
 template <int R, bool BF, int NW>
-__global__ void __launch_bounds__(32 * NW, (NW == 32 || R > 10) ? 1 : 2) pass_kernel(IterDesc d, int nbuf) {
+__global__ void __launch_bounds__(32 * NW, R <= 7 ? 2 : 1) pass_kernel(IterDesc d, int nbuf) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int mmax = d.nI > d.nJ ? d.nI : d.nJ;
   pass_persistent<R, false, BF, NW>(d, nullptr, nullptr, 1, d.nRowTiles + d.nColTiles, mmax, nbuf, smem);
@@ -760,7 +779,7 @@ __global__ void __launch_bounds__(32 * NW, (NW == 32 || R > 10) ? 1 : 2) pass_ke
 // Batched form: the tiles of every instance back to back (tile_base[i] is the
 // first tile of instance i, tile_base[count] the total).
 template <int R>
-__global__ void __launch_bounds__(kPassThreads, (R <= 10 ? 2 : 1)) pass_batch_kernel(const IterDesc* __restrict__ ds,
+__global__ void __launch_bounds__(kPassThreads, R <= 7 ? 2 : 1) pass_batch_kernel(const IterDesc* __restrict__ ds,
                                                                   const int* __restrict__ tile_base, int count,
                                                                   int mmax, int nbuf) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -798,18 +817,6 @@ size_t pass_smem_bytes(int nI, int nJ, int Rpad, int* nbuf_out, bool bf16, bool 
   }
   if (nbuf_out) *nbuf_out = nbuf;
   return bytes;
-}
-
-// Warps per block of the single-instance pass: 32 where one 16-warp block's
-// shared memory leaves no room for a second on an SM (large |I|, |J| or r)
-// and the 32-warp block fits with the same tile buffers, for padded ranks
-// 8..10 (64 registers a thread); 16 otherwise.
-int pass_warps(int nI, int nJ, int Rpad, bool bf16, bool single) {
-  if (Rpad < 8 || Rpad > 10) return kPassWarps;
-  int nb16 = 0, nb32 = 0;
-  const size_t b16 = pass_smem_bytes(nI, nJ, Rpad, &nb16, bf16, single, kPassWarps);
-  const size_t b32 = pass_smem_bytes(nI, nJ, Rpad, &nb32, bf16, single, 2 * kPassWarps);
-  return (2 * b16 > 228 * 1024 && b32 <= 227 * 1024 && nb32 == nb16) ? 2 * kPassWarps : kPassWarps;
 }
 
 // Resident blocks of a pass kernel on the current device, cached per (device,
@@ -869,12 +876,8 @@ static cudaError_t launch_pdl(void (*kernel)(Args...), int grid, int threads, si
 template <int R>
 static const void* pass_fn(const IterDesc& d, size_t* bytes, int* nbuf, int* nw) {
   const bool bf = d.bf16 != 0, single = d.passSingleBuf != 0;
-  *nw = pass_warps(d.nI, d.nJ, R, bf, single);
+  *nw = kPassWarps;
   *bytes = pass_smem_bytes(d.nI, d.nJ, R, nbuf, bf, single, *nw);
-  if constexpr (R >= 8 && R <= 10) {
-    if (*nw == 2 * kPassWarps)
-      return bf ? (const void*)pass_kernel<R, true, 2 * kPassWarps> : (const void*)pass_kernel<R, false, 2 * kPassWarps>;
-  }
   return bf ? (const void*)pass_kernel<R, true, kPassWarps> : (const void*)pass_kernel<R, false, kPassWarps>;
 }
 
