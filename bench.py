@@ -263,6 +263,12 @@ def bench_batched(ir, synth, stream, count=64, seed=7):
     batch_cl.autotune(Ds, reps=3)
     t_batch_cl = _timed(lambda: batch_cl.solve(Ds), 5, stream)
     batch_cl.close()
+    batch_c8 = ir.IRCURBatch([dict(q, svd_form=ir.IRCUR_SVD_CLUSTER8) for q in probs])
+    for _ in range(2):
+        batch_c8.solve(Ds)
+    batch_c8.autotune(Ds, reps=3)
+    t_batch_c8 = _timed(lambda: batch_c8.solve(Ds), 5, stream)
+    batch_c8.close()
     batch = ir.IRCURBatch([dict(q, svd_form=ir.IRCUR_SVD_ONE_CTA) for q in probs])
     for _ in range(2):
         res = batch.solve(Ds)
@@ -281,6 +287,7 @@ def bench_batched(ir, synth, stream, count=64, seed=7):
            "solves_per_s": count / (t_batch / 1e3), "ms_per_batch": t_batch,
            "svd_form": "one CTA where the core fits",
            "cluster_form_solves_per_s": count / (t_batch_cl / 1e3),
+           "cluster8_form_solves_per_s": count / (t_batch_c8 / 1e3),
            "loop_solves_per_s": count / (t_loop / 1e3), "loop_ms": t_loop, "speedup_vs_loop": t_loop / t_batch,
            "iters_min_max": [min(iters), max(iters)], "converged": int(sum(r_.converged for r_ in res)),
            "autotune": tune}

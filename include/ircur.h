@@ -77,10 +77,12 @@ typedef enum {
  *   device, so a batch instance runs the same form as a lone solve.
  * ONE_CTA: one CTA of 512 threads per core, the whole core in its shared
  *   memory, where that fits (about |I|, |J| <= 220 at r <= 8); the cluster form
- *   elsewhere.  Batches of many instances run faster with it (one SM per
- *   instance instead of sixteen). */
+ *   elsewhere.  One SM per instance instead of sixteen.
+ * CLUSTER8: a cluster of 8 CTAs per core where the slabs of 8 fit (16
+ *   elsewhere): for batches, where more instances then run at once. */
 #define IRCUR_SVD_CLUSTER 0
 #define IRCUR_SVD_ONE_CTA 1
+#define IRCUR_SVD_CLUSTER8 2
 
 /* Largest number of instances of one ircur_batch. */
 #define IRCUR_MAX_BATCH 4096
@@ -97,7 +99,7 @@ typedef struct {
   int32_t resample;  /* 0 = IRCUR-F (fixed I,J), 1 = IRCUR-R (fresh I,J each iteration), Sec. 3.4 */
   uint64_t seed;     /* index-stream seed (used when the caller passes no index sets) */
   int32_t precision; /* IRCUR_PRECISION_*: 0 = FP32; 1 = BF16 panels (IRCUR-F only) */
-  int32_t svd_form;  /* IRCUR_SVD_*: 0 = cluster (default), 1 = one CTA where the core fits */
+  int32_t svd_form;  /* IRCUR_SVD_*: 0 = cluster (default), 1 = one CTA where the core fits, 2 = cluster of 8 */
 } ircur_params;
 
 typedef struct {

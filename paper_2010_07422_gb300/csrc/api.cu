@@ -140,7 +140,8 @@ static ircur_status validate_params(const ircur_params* p, ircur_params* out) {
   if (q.precision != IRCUR_PRECISION_FP32 && q.precision != IRCUR_PRECISION_BF16_PANELS) return IRCUR_ENOTSUP;
   if (q.precision == IRCUR_PRECISION_BF16_PANELS && q.resample != 0) return IRCUR_ENOTSUP;
   if (pass_smem_bytes(q.nI, q.nJ, pad_rank(q.r), nullptr, q.precision != 0) > 227 * 1024) return IRCUR_ENOTSUP;
-  if (q.svd_form != IRCUR_SVD_CLUSTER && q.svd_form != IRCUR_SVD_ONE_CTA) return IRCUR_EINVAL;
+  if (q.svd_form != IRCUR_SVD_CLUSTER && q.svd_form != IRCUR_SVD_ONE_CTA && q.svd_form != IRCUR_SVD_CLUSTER8)
+    return IRCUR_EINVAL;
   if (!svd_shape_ok(q.nI, q.nJ, pad_rank(q.r), q.svd_form)) return IRCUR_ENOTSUP;
   if (!(q.gamma > 0.0 && q.gamma < 1.0)) return IRCUR_EINVAL;
   if (!(q.tol > 0.0)) return IRCUR_EINVAL;

@@ -75,13 +75,14 @@ struct PassLayout {
   float* wsum;  // nw x 2
   float* lvec;      // nbuf x (kPanelCols x RX): the tile's columns of the other factor (pass_stage_lane)
   unsigned* lpos;   // nbuf x kPanelCols: the next draw's position-map entries of the tile's columns
+  int* idx;         // 2 m: I_k then J_k (IRCUR-R, single instance), the rows the tiles gather
 };
 
 __host__ __device__ inline size_t pass_layout_floats(int m, int rx, int nbuf, bool bf16, int nw) {
   const size_t tile = bf16 ? (size_t)m * kPanelCols / 2 : (size_t)m * kPanelCols;  // in floats
   return (size_t)nbuf * tile + (bf16 ? (size_t)m * kPanelCols : 0) + 3 * (size_t)m * rx +
          (size_t)nw * rx * kPanelCols + (size_t)rx * kPanelCols + 4 * nw +
-         (size_t)nbuf * ((size_t)kPanelCols * rx + kPanelCols);
+         (size_t)nbuf * ((size_t)kPanelCols * rx + kPanelCols) + 2 * (size_t)m;
 }
 
 __device__ inline PassLayout pass_layout(unsigned char* smem, int m, int rx, int nbuf, bool bf16, int nw) {
@@ -103,6 +104,7 @@ __device__ inline PassLayout pass_layout(unsigned char* smem, int m, int rx, int
   L.wsum = L.outS + (size_t)rx * kPanelCols;
   L.lvec = L.wsum + 4 * nw;  // 16-byte aligned: every piece above is a multiple of 4 floats
   L.lpos = reinterpret_cast<unsigned*>(L.lvec + (size_t)nbuf * kPanelCols * rx);
+  L.idx = reinterpret_cast<int*>(L.lpos + (size_t)nbuf * kPanelCols);
   return L;
 }
 
@@ -120,7 +122,8 @@ struct TileRef {
 // a ragged last tile), 4-byte ones otherwise (BF16 panels, always aligned:
 // plain loads for the ragged tile).
 template <bool COL, bool BF>
-__device__ __forceinline__ void pass_stage_tile(const IterDesc& d, int k, int lt, unsigned char* bufp) {
+__device__ __forceinline__ void pass_stage_tile(const IterDesc& d, int k, int lt, unsigned char* bufp,
+                                                const int* smap) {
   const int m = COL ? d.nJ : d.nI;
   const int64_t ncolsTotal = COL ? d.n1 : d.n2;
   const int64_t ld = COL ? d.colLd : d.rowLd;
@@ -144,7 +147,8 @@ __device__ __forceinline__ void pass_stage_tile(const IterDesc& d, int k, int lt
     return;
   }
   float* buf = reinterpret_cast<float*>(bufp);
-  const int* map = (COL ? d.J_all : d.I_all) + (d.resample ? (int64_t)k * m : 0);
+  // the gathered rows: the block's shared copy of the index set, else global
+  const int* map = smap ? smap : (COL ? d.J_all : d.I_all) + (d.resample ? (int64_t)k * m : 0);
   const bool mapped = d.resample != 0;
   const float* src = COL ? d.colSrc : d.rowSrc;
   if (COL ? d.colBulk : d.rowBulk) {
@@ -156,10 +160,10 @@ __device__ __forceinline__ void pass_stage_tile(const IterDesc& d, int k, int lt
       const int a = q / kV, c4 = q - a * kV;
       float* dst = buf + (size_t)a * kPanelCols + 4 * c4;
       if (c4 < nv) {
-        const int64_t row = mapped ? __ldg(map + a) : a;
+        const int64_t row = mapped ? map[a] : a;
         cp_async16(dst, src + row * ld + j0 + 4 * c4);
       } else if (c4 == nv && rem4) {
-        const int64_t row = mapped ? __ldg(map + a) : a;
+        const int64_t row = mapped ? map[a] : a;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           if (e < rem4)
@@ -177,7 +181,7 @@ __device__ __forceinline__ void pass_stage_tile(const IterDesc& d, int k, int lt
     for (int q = threadIdx.x; q < m * kPanelCols; q += blockDim.x) {
       const int a = q / kPanelCols, c = q - a * kPanelCols;
       if (c < ncols) {
-        const int64_t row = mapped ? __ldg(map + a) : a;
+        const int64_t row = mapped ? map[a] : a;
         cp_async4(buf + q, src + row * ld + j0 + c);
       } else {
         buf[q] = 0.f;
@@ -622,6 +626,18 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
     ref.k = st_k;
     return ref;
   };
+  // IRCUR-R, single instance: the index sets of this iteration in shared
+  // memory, read by every tile's gathers (null: gathers read them from global)
+  const int* smI = nullptr;
+  const int* smJ = nullptr;
+  if (!BATCH && d1.resample) {
+    const int kk = locate(t0, inst).k;
+    for (int q = threadIdx.x; q < d1.nI; q += blockDim.x) L.idx[q] = d1.I_all[(int64_t)kk * d1.nI + q];
+    for (int q = threadIdx.x; q < d1.nJ; q += blockDim.x) L.idx[d1.nI + q] = d1.J_all[(int64_t)kk * d1.nJ + q];
+    __syncthreads();
+    smI = L.idx;
+    smJ = L.idx + d1.nI;
+  }
   // a tile and its lane data into staging buffer bi
   auto stage = [&](const TileRef& ref, int bi) {
     const IterDesc& d = BATCH ? ds[ref.inst] : d1;
@@ -629,10 +645,10 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
     float* lv = L.lvec + (size_t)bi * kPanelCols * RX;
     unsigned* lp = L.lpos + (size_t)bi * kPanelCols;
     if (ref.col) {
-      pass_stage_tile<true, BF>(d, ref.k, ref.lt, buf);
+      pass_stage_tile<true, BF>(d, ref.k, ref.lt, buf, smJ);
       pass_stage_lane<R, true>(d, ref.k, ref.lt, lv, lp);
     } else {
-      pass_stage_tile<false, BF>(d, ref.k, ref.lt, buf);
+      pass_stage_tile<false, BF>(d, ref.k, ref.lt, buf, smI);
       pass_stage_lane<R, false>(d, ref.k, ref.lt, lv, lp);
     }
   };

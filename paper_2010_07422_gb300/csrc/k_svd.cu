@@ -86,11 +86,13 @@ static bool cluster16_ok() {
 }
 
 // Cluster size of the core SVD: one CTA where the caller asked for it and the
-// whole core fits one SM; else 16 CTAs where the device runs clusters of 16
-// (half the slab work per CTA for one more level of the exchange), else 8.
+// whole core fits one SM; 8 CTAs where the caller asked for them and the slabs
+// of 8 fit; else 16 CTAs where the device runs clusters of 16 (half the slab
+// work per CTA for one more level of the exchange), else 8.
 // 0: no form fits.
 int svd_cluster_size(int nI, int nJ, int Rpad, int svd_form) {
   if (svd_form == IRCUR_SVD_ONE_CTA && svd_fits(nI, nJ, Rpad, 1)) return 1;
+  if (svd_form == IRCUR_SVD_CLUSTER8 && svd_fits(nI, nJ, Rpad, kSvdCluster)) return kSvdCluster;
   if (svd_fits(nI, nJ, Rpad, 16) && cluster16_ok()) return 16;
   if (svd_fits(nI, nJ, Rpad, kSvdCluster)) return kSvdCluster;
   return 0;

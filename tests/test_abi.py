@@ -67,7 +67,7 @@ def test_status_strings_and_param_validation_without_gpu(lib):
     assert create(nJ=81) == ir.IRCUR_EINVAL       # |J| > n2
     assert create(resample=2) == ir.IRCUR_EINVAL
     assert create(precision=1) == ir.IRCUR_ENOTSUP
-    assert create(svd_form=2) == ir.IRCUR_EINVAL
+    assert create(svd_form=3) == ir.IRCUR_EINVAL
     assert create(svd_form=-1) == ir.IRCUR_EINVAL
     assert create(n1=0) == ir.IRCUR_EINVAL
     assert ctx.value is None

@@ -77,6 +77,7 @@ def test_batch_of_one_cta_instances_equals_lone_solves():
           dict(n1=700, n2=450, r=2, resample=False, seed=2, svd_form=1),
           dict(n1=620, n2=600, r=8, resample=True, seed=3, svd_form=1),
           dict(n1=640, n2=530, r=5, resample=True, seed=4, svd_form=0),   # cluster form in the same group
+          dict(n1=660, n2=540, r=5, resample=True, seed=6, svd_form=2),   # cluster of 8 in the same group
           dict(n1=1200, n2=1100, r=6, nI=230, nJ=230, resample=True, seed=5, svd_form=1)]  # falls back
     Ds = [torch.from_numpy(synth.planted(q["n1"], q["n2"], q["r"], 0.1, seed=30 + i).D).cuda()
           for i, q in enumerate(qs)]
@@ -92,3 +93,19 @@ def test_batch_of_one_cta_instances_equals_lone_solves():
         assert torch.equal(A, Ab) and torch.equal(B, Bb)
         s.close()
     batch.close()
+
+
+@pytest.mark.parametrize("resample", [True, False])
+def test_cluster_of_8_matches_oracle(resample):
+    """svd_form = IRCUR_SVD_CLUSTER8 (8 CTAs where the slabs of 8 fit): parity with
+    the oracle at 1e-5 and agreement with the default cluster form."""
+    p = synth.planted(1000, 1000, 5, 0.1, seed=7)
+    ref = oracle.ircur(p.D, 5, 0.0, 0.7, 1e-5, 100, resample=resample, seed=3)
+    K = ref.iters
+    got = solve(p.D, 5, ir.IRCUR_SVD_CLUSTER8, tol=1e-12, max_iter=K, resample=resample, seed=3)
+    Lo, So = oracle.dense_outputs(p.D, ref)
+    assert got[0].iters == K and got[0].flags == 0
+    assert rel(got[1], Lo) <= TOL_LS, rel(got[1], Lo)
+    assert rel(got[2], So) <= TOL_LS, rel(got[2], So)
+    cl = solve(p.D, 5, ir.IRCUR_SVD_CLUSTER, tol=1e-12, max_iter=K, resample=resample, seed=3)
+    assert rel(got[1], cl[1]) <= TOL_LS
