@@ -378,7 +378,12 @@ static ircur_status build_graph(ircur_ctx* c, const IterDesc& d0) {
   // kGraphUnroll iterations per trip of the while node (the kernels of an
   // iteration that follows convergence return at once)
   cudaError_t le = cudaSuccess;
-  for (int u = 0; u < kGraphUnroll && le == cudaSuccess; ++u) le = launch_iteration(d, c->Rpad, c->capture_stream);
+  static_assert(kGraphUnroll % 2 == 0, "an even unroll keeps each node's iteration parity fixed");
+  for (int u = 0; u < kGraphUnroll && le == cudaSuccess; ++u) {
+    IterDesc du = d;
+    du.par = u & 1;
+    le = launch_iteration(du, c->Rpad, c->capture_stream);
+  }
   cudaGraph_t captured = nullptr;
   cudaError_t ce = cudaStreamEndCapture(c->capture_stream, &captured);
   if (le != cudaSuccess) {
@@ -508,7 +513,9 @@ extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, c
     IRCUR_CK(cudaMemsetAsync(c->recA, 0, nA * 4, s));
     IRCUR_CK(cudaMemsetAsync(c->recB, 0, nB * 4, s));
     for (int it = 0; it < p.max_iter; ++it) {
-      IRCUR_CK(launch_iteration(d, R, s));
+      IterDesc du = d;
+      du.par = it & 1;
+      IRCUR_CK(launch_iteration(du, R, s));
       const int nx = (it + 1) & 1;
       IRCUR_CK(cudaMemcpyAsync(c->recA + (size_t)(it + 1) * nA, c->A[nx], nA * 4, cudaMemcpyDeviceToDevice, s));
       IRCUR_CK(cudaMemcpyAsync(c->recB + (size_t)(it + 1) * nB, c->B[nx], nB * 4, cudaMemcpyDeviceToDevice, s));
@@ -539,7 +546,9 @@ extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, c
     // Host-driven loop (profiling and debugging: every kernel is a separate
     // launch).  The device flag is polled every few iterations.
     for (int it = 0; it < p.max_iter; ++it) {
-      IRCUR_CK(launch_iteration(d, c->Rpad, s));
+      IterDesc du = d;
+      du.par = it & 1;
+      IRCUR_CK(launch_iteration(du, c->Rpad, s));
       if ((it & 3) == 3) {
         ircur_status rs = read_state(c);
         if (rs != IRCUR_OK) return rs;
@@ -1182,7 +1191,8 @@ extern "C" ircur_status ircur_batch_create(const ircur_params* params, int32_t c
 
 // One batched iteration: the rank groups' kernels on concurrent branches
 // (forked from and joined back into s), then the loop control.
-static cudaError_t batch_iteration(ircur_batch* b, unsigned long long cond, cudaStream_t s) {
+static cudaError_t batch_iteration(ircur_batch* b, unsigned long long cond, cudaStream_t s, int par) {
+  for (int g = 0; g < b->ngroups; ++g) b->grp[g].par = par;
   if (b->ngroups == 1) {
     cudaError_t e = launch_batch_group(b->grp[0], b->grpR[0], s);
     if (e != cudaSuccess) return e;
@@ -1269,7 +1279,7 @@ static ircur_status batch_build_graph(ircur_batch* b, const float* const* D, con
   }
   cudaError_t le = cudaSuccess;
   for (int u = 0; u < kGraphUnroll && le == cudaSuccess; ++u)
-    le = batch_iteration(b, (unsigned long long)h, b->body_stream);
+    le = batch_iteration(b, (unsigned long long)h, b->body_stream, u & 1);
   cudaGraph_t body = nullptr;
   cudaError_t be = cudaStreamEndCapture(b->body_stream, &body);
   if (le != cudaSuccess || be != cudaSuccess) {
@@ -1327,7 +1337,7 @@ extern "C" ircur_status ircur_batch_solve(ircur_batch* b, const float* const* D,
     if (us != IRCUR_OK) return us;
     int active = 1;
     for (int it = 0; it < b->max_iter && active; ++it) {
-      IRCUR_CK(batch_iteration(b, 0ull, s));
+      IRCUR_CK(batch_iteration(b, 0ull, s, it & 1));
       if ((it & 3) == 3) {
         IRCUR_CK(cudaMemcpyAsync(&active, b->any_active, sizeof(int), cudaMemcpyDeviceToHost, s));
         IRCUR_CK(cudaStreamSynchronize(s));

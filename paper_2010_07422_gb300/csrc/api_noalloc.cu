@@ -213,6 +213,7 @@ extern "C" ircur_status ircur_solve_noalloc(const ircur_params* params, const fl
   State h;
   memset(&h, 0, sizeof(h));
   for (int it = 0; it < p.max_iter; ++it) {
+    d.par = it & 1;
     NA_CK(launch_iteration(d, R, s));
     if ((it & 3) == 3 || it + 1 == p.max_iter) {
       NA_CK(cudaMemcpyAsync(&h, st, sizeof(State), cudaMemcpyDeviceToHost, s));

@@ -100,6 +100,12 @@ struct IterDesc {
   // Padding columns stay zero.
   float* Dc[2];
   int64_t ldDc;  // nJ rounded up to 4 (16-byte rows for the bulk copies)
+  // Parity of the iteration this launch runs (k & 1 while the solve is still
+  // iterating): known at launch (graph node u of a trip of kGraphUnroll, an
+  // even count, runs k = trip kGraphUnroll + u; the host loops launch k in
+  // order), so the core SVD can load the compact buffers [k & 1] before it has
+  // read k.  Set by the launching code, not by the context.
+  int par;
   // Index maps of the draws (k & 1 for IRCUR-R, [0] for IRCUR-F; n1 and n2
   // entries, see index_tag) and the compact side matrices of iteration k,
   // AI[k & 1] = A_k(I_k,:) (nI x R) and BJt[k & 1] = B_k(:,J_k)^T (nJ x R),
@@ -147,6 +153,7 @@ struct BatchLaunch {
   int pass_grid;           // pass-kernel blocks (0: every block that fits the GPU at once)
   unsigned long long cond; // graph conditional handle (0 = no graph)
   int* any_active;         // device flag written by the loop-control kernel
+  int par;                 // parity of the iteration launched (IterDesc::par)
 };
 
 // One reverse step k of the adjoint of unrolled IRCUR-F (k_adjoint.cu).

@@ -670,17 +670,45 @@ __device__ __forceinline__ int svd_factor(const float* slots, int nc, int sl, in
 }
 
 template <int R>
-__device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned char* smem) {
+__device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned char* smem, int par) {
   constexpr int NP = svd_np(R);
   constexpr int PQ = (NP + 31) / 32;
   constexpr int GM = svd_gmax(R);
   constexpr bool REP = svd_rep(R);
+  constexpr int kPre = 4;  // values of this CTA's rows of A_k(I,:) a thread prefetches
   cg::cluster_group cl = cg::this_cluster();
   const int nc = (int)cl.num_blocks();
   const int crank = (int)cl.block_rank();
   State* st = d.st;
+  // Role 0: B_k(:,J)^T, this CTA's rows of A_k(I,:) and T's diagonal from the
+  // buffers of this launch's parity, loaded before the state (their latency
+  // overlaps its load); reloaded below in the (unexpected) case that the
+  // parity differs from k's.
+  const SvdGeom g0 = svd_geom(d.nI, d.nJ, R, nc);
+  const int prow0 = nc == 1 ? 0 : crank * g0.mrI;
+  const int pnrw = nc == 1 ? d.nI : (d.nI - prow0 < g0.mrI ? (d.nI - prow0 > 0 ? d.nI - prow0 : 0) : g0.mrI);
+  const int pq0 = threadIdx.x, pq1 = threadIdx.x + (int)blockDim.x;
+  float bj0[R], bj1[R], tdiag[R], apre[kPre];
+  const bool pre_ai = pnrw * R <= kPre * (int)blockDim.x;
+  auto load_side = [&](int pb) {
+    const float* BJp = d.BJt[pb];
+    const float* AIp = d.AI[pb];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      bj0[t] = pq0 < d.nJ ? BJp[(size_t)pq0 * R + t] : 0.f;
+      bj1[t] = pq1 < d.nJ ? BJp[(size_t)pq1 * R + t] : 0.f;
+      tdiag[t] = d.Tm[t * R + t];
+    }
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) {
+      const int q = (int)threadIdx.x + u * (int)blockDim.x;
+      apre[u] = (pre_ai && q < pnrw * R) ? AIp[(size_t)prow0 * R + q] : 0.f;
+    }
+  };
+  if (role == 0) load_side(par & 1);
   if (st->done || st->status) return;  // the same for every CTA: the state is fixed during the launch
   const int k = st->k;
+  if (role == 0 && (k & 1) != (par & 1)) load_side(k & 1);
   if (role > 0) {
     // IRCUR-R: the index sets of iteration k + 2 and their map (the panel pass
     // of iteration k + 1 reads them before it waits for its core SVD); drawn
@@ -721,7 +749,6 @@ __device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned c
   float* d2 = F2 + R * R;
   const float zeta = (float)st->zeta;
   const float* AIk = d.AI[k & 1];   // A_k(I_k,:), nI x R
-  const float* BJk = d.BJt[k & 1];  // B_k(:,J_k)^T, nJ x R
   const int buf = d.resample ? (k & 1) : 0;
   const float* Dc = d.Dc[buf];
 
@@ -748,19 +775,27 @@ __device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned c
   // dependence cutoff of the Cholesky factor (relative to its largest diagonal
   // entry) assumes.  k = 0 (B_0 = 0): a random start.
   const int q0 = tid, q1 = tid + (int)blockDim.x;
-  float bj0[R], bj1[R];
   {
     float inv[R];
 #pragma unroll
     for (int t = 0; t < R; ++t) {
-      const float tt = (k > 0 && t < r) ? fabsf(d.Tm[t * R + t]) : 0.f;
+      const float tt = (k > 0 && t < r) ? fabsf(tdiag[t]) : 0.f;
       inv[t] = tt > 0.f ? 1.f / tt : 0.f;
-      bj0[t] = q0 < nJ ? BJk[(size_t)q0 * R + t] : 0.f;
-      bj1[t] = q1 < nJ ? BJk[(size_t)q1 * R + t] : 0.f;
     }
-    for (int q = tid; q < nrw * R; q += blockDim.x) {
-      const int il = q / R, t = q - il * R;
-      sp.P[t * g.ldy + row0 + il] = AIk[(size_t)(row0 + il) * R + t];
+    if (pre_ai) {
+#pragma unroll
+      for (int u = 0; u < kPre; ++u) {
+        const int q = tid + u * (int)blockDim.x;
+        if (q < nrw * R) {
+          const int il = q / R, t = q - il * R;
+          sp.P[t * g.ldy + row0 + il] = apre[u];
+        }
+      }
+    } else {
+      for (int q = tid; q < nrw * R; q += blockDim.x) {
+        const int il = q / R, t = q - il * R;
+        sp.P[t * g.ldy + row0 + il] = AIk[(size_t)(row0 + il) * R + t];
+      }
     }
     if (k > 0) {
 #pragma unroll
@@ -1204,47 +1239,42 @@ __device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned c
     for (int t = 0; t < r; ++t) kr += (sp.sg[t] > tol && sp.sg[t] > 0.f) ? 1 : 0;
   }
   {
+    // one thread per output entry (row, t), this CTA's share of the rows; the
+    // same FMA chain per entry as a row-per-thread loop
     const int wr = (nI + nc - 1) / nc, w0 = crank * wr, w1 = w0 + wr < nI ? w0 + wr : nI;
-    for (int i = w0 + tid; i < w1; i += blockDim.x) {
-      float y[R];
+    for (int q = tid; q < (w1 - w0) * R; q += blockDim.x) {
+      const int i = w0 + q / R, t = q - (q / R) * R;
+      float v = sp.P[t * g.ldy + i];
+      if (!fast) {
+        v = 0.f;
 #pragma unroll
-      for (int s2 = 0; s2 < R; ++s2) y[s2] = sp.P[s2 * g.ldy + i];
-#pragma unroll
-      for (int t = 0; t < R; ++t) {
-        float v = y[t];
-        if (!fast) {
-          v = 0.f;
-#pragma unroll
-          for (int s2 = 0; s2 < R; ++s2) v = fmaf(y[s2], sp.Ut[s2 * R + t], v);
-        }
-        d.W[(size_t)i * R + t] = t < kr ? v : 0.f;
+        for (int s2 = 0; s2 < R; ++s2) v = fmaf(sp.P[s2 * g.ldy + i], sp.Ut[s2 * R + t], v);
       }
+      d.W[(size_t)i * R + t] = t < kr ? v : 0.f;
     }
     const int vr = (nJ + nc - 1) / nc, v0 = crank * vr, v1 = v0 + vr < nJ ? v0 + vr : nJ;
-    for (int j = v0 + tid; j < v1; j += blockDim.x) {
+    for (int q = tid; q < (v1 - v0) * R; q += blockDim.x) {
+      const int j = v0 + q / R, t = q - (q / R) * R;
       float x[R];
 #pragma unroll
       for (int s2 = 0; s2 < R; ++s2) x[s2] = sp.Q[s2 * g.ldx + j];
+      float vs = 0.f, vv = 0.f;
+      if (fast) {  // Vs = X T^{-1}, V = X T^T
 #pragma unroll
-      for (int t = 0; t < R; ++t) {
-        float vs = 0.f, vv = 0.f;
-        if (fast) {  // Vs = X T^{-1}, V = X T^T
-#pragma unroll
-          for (int s2 = 0; s2 < R; ++s2) {
-            vs = fmaf(x[s2], sp.Ut[s2 * R + t], vs);
-            vv = fmaf(x[s2], sp.T[t * R + s2], vv);
-          }
-        } else {  // Vs = X Vt Sigma^{-1}, V = X Vt Sigma
-          float v = 0.f;
-#pragma unroll
-          for (int s2 = 0; s2 < R; ++s2) v = fmaf(x[s2], sp.Vt[s2 * R + t], v);
-          vs = t < kr ? v / sp.sg[t] : 0.f;
-          vv = t < kr ? v * sp.sg[t] : 0.f;
+        for (int s2 = 0; s2 < R; ++s2) {
+          vs = fmaf(x[s2], sp.Ut[s2 * R + t], vs);
+          vv = fmaf(x[s2], sp.T[t * R + s2], vv);
         }
-        const bool kt = t < kr;
-        d.Vs[(size_t)j * R + t] = kt ? vs : 0.f;
-        d.V[(size_t)j * R + t] = kt ? vv : 0.f;
+      } else {  // Vs = X Vt Sigma^{-1}, V = X Vt Sigma
+        float v = 0.f;
+#pragma unroll
+        for (int s2 = 0; s2 < R; ++s2) v = fmaf(x[s2], sp.Vt[s2 * R + t], v);
+        vs = t < kr ? v / sp.sg[t] : 0.f;
+        vv = t < kr ? v * sp.sg[t] : 0.f;
       }
+      const bool kt = t < kr;
+      d.Vs[(size_t)j * R + t] = kt ? vs : 0.f;
+      d.V[(size_t)j * R + t] = kt ? vv : 0.f;
     }
   }
   if (crank == 0) {
@@ -1274,31 +1304,32 @@ __global__ void __launch_bounds__(kSvdThreadsCl, (R <= 10 ? 2 : 1)) csvd_kernel(
   // every CTA is resident from here on: the pass kernel may start on the
   // other SMs (it waits for this grid before reading its outputs)
   pdl_launch_dependents();
-  svd_body<R>(d, blockIdx.y, smem);
+  svd_body<R>(d, blockIdx.y, smem, d.par);
 }
 
 template <int R>
 __global__ void __launch_bounds__(kSvdThreadsOne, 1) ssvd_kernel(IterDesc d) {
   extern __shared__ __align__(16) unsigned char smem[];
   pdl_launch_dependents();
-  svd_body<R>(d, blockIdx.y, smem);
+  svd_body<R>(d, blockIdx.y, smem, d.par);
 }
 
 // Batched forms: cluster (or CTA) x / NC factorises instance list[x / NC].
 template <int R>
 __global__ void __launch_bounds__(kSvdThreadsCl, (R <= 10 ? 2 : 1)) csvd_batch_kernel(const IterDesc* __restrict__ ds,
-                                                                                    const int* __restrict__ list) {
+                                                                                    const int* __restrict__ list,
+                                                                                    int par) {
   extern __shared__ __align__(16) unsigned char smem[];
   pdl_launch_dependents();
-  svd_body<R>(ds[list[blockIdx.x / cg::this_cluster().num_blocks()]], blockIdx.y, smem);
+  svd_body<R>(ds[list[blockIdx.x / cg::this_cluster().num_blocks()]], blockIdx.y, smem, par);
 }
 
 template <int R>
 __global__ void __launch_bounds__(kSvdThreadsOne, 1) ssvd_batch_kernel(const IterDesc* __restrict__ ds,
-                                                                      const int* __restrict__ list) {
+                                                                      const int* __restrict__ list, int par) {
   extern __shared__ __align__(16) unsigned char smem[];
   pdl_launch_dependents();
-  svd_body<R>(ds[list[blockIdx.x]], blockIdx.y, smem);
+  svd_body<R>(ds[list[blockIdx.x]], blockIdx.y, smem, par);
 }
 
 // Singular values of the last core's T (H_r(core) = Y T X^T, so they are the
@@ -1358,8 +1389,8 @@ cudaError_t svd_launch_batch_r(const BatchLaunch& b, cudaStream_t s) {
     if (n == 0) continue;
     const int nc = f == 0 ? 1 : (f == 1 ? kSvdCluster : 16);
     const dim3 grid((unsigned)(nc * n), (unsigned)b.svd_roles, 1);
-    cudaError_t e = nc == 1 ? launch_svd_grid(ssvd_batch_kernel<R>, 1, grid, b.svd_smem[f], s, b.ds, b.svd_list[f])
-                            : launch_svd_grid(csvd_batch_kernel<R>, nc, grid, b.svd_smem[f], s, b.ds, b.svd_list[f]);
+    cudaError_t e = nc == 1 ? launch_svd_grid(ssvd_batch_kernel<R>, 1, grid, b.svd_smem[f], s, b.ds, b.svd_list[f], b.par)
+                            : launch_svd_grid(csvd_batch_kernel<R>, nc, grid, b.svd_smem[f], s, b.ds, b.svd_list[f], b.par);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
