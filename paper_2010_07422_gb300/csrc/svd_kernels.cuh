@@ -831,13 +831,31 @@ __device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned c
       return panel_value(dv, l, zeta);
     };
     // thread per column (B_k(:,J_j) in registers), the rows' A_k(I_i,:)
-    // broadcast reads of own rows of P
+    // broadcast reads of own rows of P.  The one-CTA form, whose threads
+    // outnumber the columns, gives each column to ngrp threads, each with a
+    // share of the rows (the first group holds B_k(:,J_j) already, the others
+    // read it from the compact copy).
+    const int ngrp = (nc == 1 && nJ > 0 && (int)blockDim.x >= 2 * nJ) ? (int)blockDim.x / nJ : 1;
     for (int half = 0; half < 2; ++half) {
-      const int j = half ? q1 : q0;
-      if (j >= nJ) continue;
-      const float(&bj)[R] = half ? bj1 : bj0;
-      int il = 0;
-      for (; il + 4 <= nrw; il += 4) {
+      int j, ra = 0, rb = nrw;
+      float bj[R];
+      if (ngrp > 1) {
+        const int grp = tid / nJ;
+        if (half == 1 || grp >= ngrp) continue;
+        j = tid - grp * nJ;
+        ra = grp * nrw / ngrp;
+        rb = (grp + 1) * nrw / ngrp;
+        const float* BJc = d.BJt[k & 1];
+#pragma unroll
+        for (int t = 0; t < R; ++t) bj[t] = grp == 0 ? bj0[t] : BJc[(size_t)j * R + t];
+      } else {
+        j = half ? q1 : q0;
+        if (j >= nJ) continue;
+#pragma unroll
+        for (int t = 0; t < R; ++t) bj[t] = half ? bj1[t] : bj0[t];
+      }
+      int il = ra;
+      for (; il + 4 <= rb; il += 4) {
         float a4[4][R], d4[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -851,7 +869,7 @@ __device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned c
           sp.urow[(size_t)(il + u) * g.ldr + j] = entry(d4[u], a4[u], bj);
         }
       }
-      for (; il < nrw; ++il) {
+      for (; il < rb; ++il) {
         const int i = row0 + il;
         float a1[R];
 #pragma unroll
