@@ -1015,6 +1015,10 @@ struct ircur_batch {
   BatchLaunch grp[kMaxRankGroups];
   cudaStream_t gstream[kMaxRankGroups];  // one branch per group (they run concurrently)
   cudaEvent_t gev[kMaxRankGroups + 1];
+  // several groups, IRCUR-R: the look-ahead draws on a branch of their own
+  bool sample_branch;
+  cudaStream_t sstream;
+  cudaEvent_t sev;
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   const float** graph_D;  // the D pointers and leading dimensions the graph was built for
@@ -1042,6 +1046,8 @@ extern "C" void ircur_batch_destroy(ircur_batch* b) {
     if (b->gstream[g]) cudaStreamDestroy(b->gstream[g]);
   for (int g = 0; g <= kMaxRankGroups; ++g)
     if (b->gev[g]) cudaEventDestroy(b->gev[g]);
+  if (b->sstream) cudaStreamDestroy(b->sstream);
+  if (b->sev) cudaEventDestroy(b->sev);
   if (b->dws) cudaFree(b->dws);
   if (b->hstates) cudaFreeHost(b->hstates);
   delete[] b->hdesc;
@@ -1173,6 +1179,10 @@ extern "C" ircur_status ircur_batch_create(const ircur_params* params, int32_t c
     e = cudaStreamCreateWithFlags(&b->gstream[g], cudaStreamNonBlocking);
   for (int g = 0; g <= b->ngroups && e == cudaSuccess; ++g)
     e = cudaEventCreateWithFlags(&b->gev[g], cudaEventDisableTiming);
+  for (int g = 0; g < b->ngroups; ++g)
+    if (b->grp[g].svd_roles > 1) b->sample_branch = b->ngroups > 1;
+  if (b->sample_branch && e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->sstream, cudaStreamNonBlocking);
+  if (b->sample_branch && e == cudaSuccess) e = cudaEventCreateWithFlags(&b->sev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->dws, 0, bytes, b->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(base + oTiles, tiles.get(), (size_t)(count + b->ngroups) * 4, cudaMemcpyHostToDevice,
@@ -1189,18 +1199,39 @@ extern "C" ircur_status ircur_batch_create(const ircur_params* params, int32_t c
   return IRCUR_OK;
 }
 
-// One batched iteration: the rank groups' kernels on concurrent branches
-// (forked from and joined back into s), then the loop control.
+// One batched iteration, then the loop control.  One rank group: its core SVD
+// and its panel pass (a programmatic dependent of the SVD) on s.  Several:
+// every group's core SVD on a branch of its own, and the IRCUR-R look-ahead
+// draws on one more, all forked from s and joined back; then every group's
+// panel pass the same way.  (With the passes in the SVD branches, the pass
+// blocks of the groups whose SVD ended first held the SMs that the other
+// groups' SVDs waited for.)
 static cudaError_t batch_iteration(ircur_batch* b, unsigned long long cond, cudaStream_t s, int par) {
   for (int g = 0; g < b->ngroups; ++g) b->grp[g].par = par;
   if (b->ngroups == 1) {
     cudaError_t e = launch_batch_group(b->grp[0], b->grpR[0], s);
     if (e != cudaSuccess) return e;
   } else {
-    cudaError_t e = cudaEventRecord(b->gev[b->ngroups], s);
-    for (int g = 0; g < b->ngroups && e == cudaSuccess; ++g) {
-      e = cudaStreamWaitEvent(b->gstream[g], b->gev[b->ngroups], 0);
-      if (e == cudaSuccess) e = launch_batch_group(b->grp[g], b->grpR[g], b->gstream[g]);
+    const int ng = b->ngroups;
+    cudaError_t e = cudaEventRecord(b->gev[ng], s);
+    if (e == cudaSuccess && b->sample_branch) {
+      e = cudaStreamWaitEvent(b->sstream, b->gev[ng], 0);
+      if (e == cudaSuccess) e = launch_sample_ahead_batch(b->ds, b->count, b->sstream);
+      if (e == cudaSuccess) e = cudaEventRecord(b->sev, b->sstream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->sev, 0);
+    }
+    for (int g = 0; g < ng && e == cudaSuccess; ++g) {
+      BatchLaunch bl = b->grp[g];
+      if (b->sample_branch) bl.svd_roles = 1;
+      e = cudaStreamWaitEvent(b->gstream[g], b->gev[ng], 0);
+      if (e == cudaSuccess) e = launch_svd_batch(bl, b->grpR[g], b->gstream[g]);
+      if (e == cudaSuccess) e = cudaEventRecord(b->gev[g], b->gstream[g]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->gev[g], 0);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->gev[ng], s);
+    for (int g = 0; g < ng && e == cudaSuccess; ++g) {
+      e = cudaStreamWaitEvent(b->gstream[g], b->gev[ng], 0);
+      if (e == cudaSuccess) e = launch_batch_pass(b->grp[g], b->grpR[g], b->gstream[g]);
       if (e == cudaSuccess) e = cudaEventRecord(b->gev[g], b->gstream[g]);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->gev[g], 0);
     }

@@ -229,6 +229,11 @@ cudaError_t launch_batch_group(const BatchLaunch& b, int Rpad, cudaStream_t s);
 cudaError_t launch_batch_check(const IterDesc* ds, int count, unsigned long long cond, int* any_active,
                                cudaStream_t s);
 cudaError_t launch_svd_batch(const BatchLaunch& b, int Rpad, cudaStream_t s);
+// The same iteration in two phases, for batches of several rank groups: the
+// core SVD alone (its look-ahead draws left to launch_sample_ahead_batch when
+// svd_roles is 1), then the panel pass as a plain launch.
+cudaError_t launch_batch_pass(const BatchLaunch& b, int Rpad, cudaStream_t s);
+cudaError_t launch_sample_ahead_batch(const IterDesc* ds, int count, cudaStream_t s);
 cudaError_t launch_stream(const float* A, const int* I, const float* Y, int m, int Rpad, int64_t n1, const float* Dn,
                           int64_t ldDn, int64_t ncols, int iters, double zeta0, double gamma, float zetaT, float* bq,
                           float* L, int64_t ldL, float* S, int64_t ldS, cudaStream_t s);

@@ -931,6 +931,19 @@ static cudaError_t launch_batch_iter_r(const BatchLaunch& b, cudaStream_t s) {
   }
 }
 
+// The batched pass alone, after its group's core SVD has ended (no
+// programmatic overlap: its wait returns at once).
+template <int R>
+static cudaError_t launch_batch_pass_r(const BatchLaunch& b, cudaStream_t s) {
+  cudaError_t e =
+      cudaFuncSetAttribute(pass_batch_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.pass_smem);
+  if (e != cudaSuccess) return e;
+  int grid = b.pass_grid > 0 ? b.pass_grid : pass_grid((const void*)pass_batch_kernel<R>, b.pass_smem, kPassThreads);
+  if (grid > b.total_tiles) grid = b.total_tiles;
+  pass_batch_kernel<R><<<grid, kPassThreads, b.pass_smem, s>>>(b.ds, b.tile_base, b.count, b.pass_mmax, b.pass_nbuf);
+  return cudaGetLastError();
+}
+
 template <int R>
 static int pass_resident_r(const IterDesc& d) {
   size_t bytes = 0;
@@ -971,6 +984,24 @@ cudaError_t launch_batch_check(const IterDesc* ds, int count, unsigned long long
                                cudaStream_t s) {
   batch_check_kernel<<<1, 256, 0, s>>>(ds, count, cond, any_active);
   return cudaGetLastError();
+}
+
+cudaError_t launch_batch_pass(const BatchLaunch& b, int Rpad, cudaStream_t s) {
+  switch (Rpad) {
+    case 1: return launch_batch_pass_r<1>(b, s);
+    case 2: return launch_batch_pass_r<2>(b, s);
+    case 3: return launch_batch_pass_r<3>(b, s);
+    case 4: return launch_batch_pass_r<4>(b, s);
+    case 5: return launch_batch_pass_r<5>(b, s);
+    case 6: return launch_batch_pass_r<6>(b, s);
+    case 7: return launch_batch_pass_r<7>(b, s);
+    case 8: return launch_batch_pass_r<8>(b, s);
+    case 9: return launch_batch_pass_r<9>(b, s);
+    case 10: return launch_batch_pass_r<10>(b, s);
+    case 12: return launch_batch_pass_r<12>(b, s);
+    case 16: return launch_batch_pass_r<16>(b, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_batch_group(const BatchLaunch& b, int Rpad, cudaStream_t s) {

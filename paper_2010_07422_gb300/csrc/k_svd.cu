@@ -121,6 +121,24 @@ cudaError_t launch_svd_batch(const BatchLaunch& b, int Rpad, cudaStream_t s) {
   }
 }
 
+// Batched IRCUR-R: the look-ahead draws (roles 1 and 2 of a core-SVD launch)
+// as a launch of their own, one CTA per (instance, axis), so that a batch's
+// core-SVD grid carries no cluster that only one CTA of works in.  The
+// iteration k comes from the instance's state: the launch must end before the
+// panel pass of the same iteration advances it.
+__global__ void __launch_bounds__(512) sample_ahead_batch_kernel(const IterDesc* __restrict__ ds) {
+  __shared__ SamplerSmem S;
+  const IterDesc& d = ds[blockIdx.x];
+  const State* st = d.st;
+  if (st->done || st->status) return;
+  svd_sample_ahead(d, st->k, (int)blockIdx.y, S);
+}
+
+cudaError_t launch_sample_ahead_batch(const IterDesc* ds, int count, cudaStream_t s) {
+  sample_ahead_batch_kernel<<<dim3((unsigned)count, 2, 1), 512, 0, s>>>(ds);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_svd(const IterDesc& d, int Rpad, cudaStream_t s) {
   switch (Rpad) {
     case 1: return svd_launch_r<1>(d, s);

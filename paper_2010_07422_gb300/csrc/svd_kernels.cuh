@@ -669,6 +669,23 @@ __device__ __forceinline__ int svd_factor(const float* slots, int nc, int sl, in
     return warp_chol<R>(Gw, r, F, dF, minsp);
 }
 
+// IRCUR-R: the index sets of iteration k + 2 on one axis (0: I, 1: J) and
+// their map (the panel pass of iteration k + 1 reads them before it waits for
+// its core SVD); drawn by the library's sampler, or only mapped when the
+// caller gave them.  The drawn set is sorted, whatever the block size.
+__device__ __forceinline__ void svd_sample_ahead(const IterDesc& d, int k, int axis, SamplerSmem& S) {
+  const int dn = k + 2;
+  if (!d.resample || dn >= d.max_iter) return;
+  const int m = axis ? d.nJ : d.nI;
+  int* out = const_cast<int*>(axis ? d.J_all : d.I_all) + (int64_t)dn * m;
+  unsigned* map = axis ? d.posJ[dn & 1] : d.posI[dn & 1];
+  if (d.sampleAhead) {
+    sample_subset(d.seed, dn, axis, axis ? d.n2 : d.n1, m, out, S, map, (unsigned)(dn + 1));
+  } else {
+    for (int a = threadIdx.x; a < m; a += blockDim.x) map[out[a]] = index_tag((unsigned)(dn + 1), a);
+  }
+}
+
 template <int R>
 __device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned char* smem, int par) {
   constexpr int NP = svd_np(R);
@@ -710,22 +727,7 @@ __device__ __forceinline__ void svd_body(const IterDesc& d, int role, unsigned c
   const int k = st->k;
   if (role == 0 && (k & 1) != (par & 1)) load_side(k & 1);
   if (role > 0) {
-    // IRCUR-R: the index sets of iteration k + 2 and their map (the panel pass
-    // of iteration k + 1 reads them before it waits for its core SVD); drawn
-    // by the library's sampler, or only mapped when the caller gave them
-    const int axis = role - 1;
-    const int dn = k + 2;
-    if (crank == 0 && d.resample && dn < d.max_iter) {
-      const int m = axis ? d.nJ : d.nI;
-      int* out = const_cast<int*>(axis ? d.J_all : d.I_all) + (int64_t)dn * m;
-      unsigned* map = axis ? d.posJ[dn & 1] : d.posI[dn & 1];
-      if (d.sampleAhead) {
-        sample_subset(d.seed, dn, axis, axis ? d.n2 : d.n1, m, out, *reinterpret_cast<SamplerSmem*>(smem), map,
-                      (unsigned)(dn + 1));
-      } else {
-        for (int a = threadIdx.x; a < m; a += blockDim.x) map[out[a]] = index_tag((unsigned)(dn + 1), a);
-      }
-    }
+    if (crank == 0) svd_sample_ahead(d, k, role - 1, *reinterpret_cast<SamplerSmem*>(smem));
     return;
   }
   if (crank == 0) {
