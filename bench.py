@@ -55,7 +55,7 @@ def parse_args():
                          "(n in 1000, 2500, 5000, 10000, 20000; r in 5, 10; alpha in 0.1, 0.2, 0.3; F and R)")
     ap.add_argument("--phase-transition", action="store_true",
                     help="instead of the headline line: recovery rates over (c_I, alpha) at n = 1000 "
-                         "(50 trials per cell, r = 5 and 10, IRCUR-F and -R) on the batched solver")
+                         "(50 trials per cell, r = 5, 10 and 20, IRCUR-F and -R) on the batched solver")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default pass launch shape (fixed launch sequence, for profiling)")
     ap.add_argument("--no-extras", action="store_true",
@@ -445,7 +445,7 @@ def run_phase_transition(a, n=1000, trials=50, c_values=(0.5, 1.0, 1.5, 2.0, 2.5
     from paper_2010_07422_gb300 import synth
     t_all = time.perf_counter()
     solves, t_solves = 0, 0.0
-    for r in (5, 10):
+    for r in (5, 10, 20):
         for variant in ("F", "R"):
             for c_I in c_values:
                 m = int(min(n, math.ceil(c_I * r * math.log(n))))
@@ -459,7 +459,14 @@ def run_phase_transition(a, n=1000, trials=50, c_values=(0.5, 1.0, 1.5, 2.0, 2.5
                         gens.append((D, W, V))
                         probs.append(dict(n1=n, n2=n, r=r, nI=m, nJ=m, resample=(variant == "R"), seed=seed,
                                           zeta0=z0, gamma=0.65, tol=1e-5, max_iter=100))
-                batch = ir.IRCURBatch(probs)
+                try:
+                    batch = ir.IRCURBatch(probs)
+                except ir.IrcurError as e:
+                    # the core (m x m at rank r) does not fit the GPU's shared memory
+                    print(json.dumps({"phase_transition": True, "n": n, "r": r, "variant": variant, "c_I": c_I,
+                                      "m": m, "unsupported": str(e)}), flush=True)
+                    del gens
+                    continue
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 batch.solve([g[0] for g in gens])
@@ -666,6 +673,28 @@ def main():
         Dd = torch.empty((n, n), dtype=torch.float32, device="cuda")
         Ah = torch.empty((n, a.r), dtype=torch.float32).pin_memory()
         Bh = torch.empty((a.r, n), dtype=torch.float32).pin_memory()
+
+        # the step's copies alone, for comparison: D up, then L and S down (the
+        # same pinned buffers and bytes, one copy each)
+        def copies():
+            c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            c0.record(stream)
+            Dd.copy_(Dh, non_blocking=True)
+            c1.record(stream)
+            Lh.copy_(Dd, non_blocking=True)
+            Sh.copy_(Dd, non_blocking=True)
+            c2.record(stream)
+            torch.cuda.synchronize()
+            return c0.elapsed_time(c1), c1.elapsed_time(c2)
+
+        copies()
+        ct = [copies() for _ in range(3)]
+        h2d_ms = float(np.median([u for u, _ in ct]))
+        d2h_ms = float(np.median([v for _, v in ct]))
+        e2e["copies_alone"] = {"h2d_ms": h2d_ms, "h2d_gb_per_s": 4 * n * n / (h2d_ms * 1e6),
+                               "d2h_ms": d2h_ms, "d2h_gb_per_s": 8 * n * n / (d2h_ms * 1e6),
+                               "ms": h2d_ms + d2h_ms,
+                               "what": "pinned host buffers, D up then L and S down, CUDA events, no compute"}
 
         def host_factors():
             Dd.copy_(Dh, non_blocking=True)

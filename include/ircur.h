@@ -49,7 +49,7 @@ typedef enum {
                                       gap-scaled accuracy target: sigma_r / sigma_{r+1} too close to 1 */
 
 /* Largest rank r this build supports. */
-#define IRCUR_MAX_RANK 16
+#define IRCUR_MAX_RANK 20
 
 /* ircur_params.precision.
  * FP32: every panel entry, product, threshold decision and stopping-value

@@ -743,6 +743,7 @@ static cudaError_t launch_adj_step_r(const AdjStep& a, bool need_next, cudaStrea
     case 10: return FN<10>(__VA_ARGS__);        \
     case 12: return FN<12>(__VA_ARGS__);        \
     case 16: return FN<16>(__VA_ARGS__);        \
+    case 20: return FN<20>(__VA_ARGS__);        \
     default: return cudaErrorInvalidValue;      \
   }
 

@@ -288,6 +288,7 @@ cudaError_t launch_cur_to_svd(const float* A, const float* B, int64_t n1, int64_
     case 10: return launch_c2s_r<10>(A, B, n1, n2, r, scratch, W, sigma, V, s);
     case 12: return launch_c2s_r<12>(A, B, n1, n2, r, scratch, W, sigma, V, s);
     case 16: return launch_c2s_r<16>(A, B, n1, n2, r, scratch, W, sigma, V, s);
+    case 20: return launch_c2s_r<20>(A, B, n1, n2, r, scratch, W, sigma, V, s);
     default: return cudaErrorInvalidValue;
   }
 }

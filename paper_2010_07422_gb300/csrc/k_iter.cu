@@ -26,7 +26,8 @@ namespace ircur {
 int pad_rank(int r) {
   if (r <= 10) return r;
   if (r <= 12) return 12;
-  return 16;
+  if (r <= 16) return 16;
+  return 20;
 }
 
 // ---------------------------------------------------------------------------
@@ -974,6 +975,7 @@ static int pass_batch_resident_r(const BatchLaunch& b) {
     case 10: return FN<10>(ARG);     \
     case 12: return FN<12>(ARG);     \
     case 16: return FN<16>(ARG);     \
+    case 20: return FN<20>(ARG);     \
     default: return 0;               \
   }
 
@@ -1000,6 +1002,7 @@ cudaError_t launch_batch_pass(const BatchLaunch& b, int Rpad, cudaStream_t s) {
     case 10: return launch_batch_pass_r<10>(b, s);
     case 12: return launch_batch_pass_r<12>(b, s);
     case 16: return launch_batch_pass_r<16>(b, s);
+    case 20: return launch_batch_pass_r<20>(b, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1018,6 +1021,7 @@ cudaError_t launch_batch_group(const BatchLaunch& b, int Rpad, cudaStream_t s) {
     case 10: return launch_batch_iter_r<10>(b, s);
     case 12: return launch_batch_iter_r<12>(b, s);
     case 16: return launch_batch_iter_r<16>(b, s);
+    case 20: return launch_batch_iter_r<20>(b, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1036,6 +1040,7 @@ cudaError_t launch_iteration(const IterDesc& d, int Rpad, cudaStream_t s) {
     case 10: return launch_iter_r<10>(d, s);
     case 12: return launch_iter_r<12>(d, s);
     case 16: return launch_iter_r<16>(d, s);
+    case 20: return launch_iter_r<20>(d, s);
     default: return cudaErrorInvalidValue;
   }
 }

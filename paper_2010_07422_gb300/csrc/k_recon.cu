@@ -144,6 +144,7 @@ cudaError_t launch_reconstruct(const float* A, const float* B, int Rpad, int64_t
     case 10: return launch_recon_r<10>(A, B, n1, n2, D, ldD, L, ldL, S, ldS, st, s);
     case 12: return launch_recon_r<12>(A, B, n1, n2, D, ldD, L, ldL, S, ldS, st, s);
     case 16: return launch_recon_r<16>(A, B, n1, n2, D, ldD, L, ldL, S, ldS, st, s);
+    case 20: return launch_recon_r<20>(A, B, n1, n2, D, ldD, L, ldL, S, ldS, st, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -226,6 +227,7 @@ cudaError_t launch_get_cur(const IterDesc& d, int Rpad, int K, const float* D, i
     IRCUR_CUR_CASE(10)
     IRCUR_CUR_CASE(12)
     IRCUR_CUR_CASE(16)
+    IRCUR_CUR_CASE(20)
 #undef IRCUR_CUR_CASE
     default:
       return cudaErrorInvalidValue;

@@ -138,6 +138,7 @@ cudaError_t launch_stream(const float* A, const int* I, const float* Y, int m, i
     IRCUR_STREAM_CASE(10)
     IRCUR_STREAM_CASE(12)
     IRCUR_STREAM_CASE(16)
+    IRCUR_STREAM_CASE(20)
 #undef IRCUR_STREAM_CASE
     default:
       return cudaErrorInvalidValue;

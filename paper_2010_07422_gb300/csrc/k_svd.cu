@@ -33,6 +33,8 @@ extern template cudaError_t svd_launch_r<12>(const IterDesc&, cudaStream_t);
 extern template cudaError_t svd_launch_batch_r<12>(const BatchLaunch&, cudaStream_t);
 extern template cudaError_t svd_launch_r<16>(const IterDesc&, cudaStream_t);
 extern template cudaError_t svd_launch_batch_r<16>(const BatchLaunch&, cudaStream_t);
+extern template cudaError_t svd_launch_r<20>(const IterDesc&, cudaStream_t);
+extern template cudaError_t svd_launch_batch_r<20>(const BatchLaunch&, cudaStream_t);
 
 cudaError_t launch_sigma(const float* Tm, int r, int Rpad, float* sigma, cudaStream_t s) {
   switch (Rpad) {
@@ -52,6 +54,7 @@ cudaError_t launch_sigma(const float* Tm, int r, int Rpad, float* sigma, cudaStr
     IRCUR_SIGMA_CASE(10)
     IRCUR_SIGMA_CASE(12)
     IRCUR_SIGMA_CASE(16)
+    IRCUR_SIGMA_CASE(20)
 #undef IRCUR_SIGMA_CASE
     default:
       return cudaErrorInvalidValue;
@@ -117,6 +120,7 @@ cudaError_t launch_svd_batch(const BatchLaunch& b, int Rpad, cudaStream_t s) {
     case 10: return svd_launch_batch_r<10>(b, s);
     case 12: return svd_launch_batch_r<12>(b, s);
     case 16: return svd_launch_batch_r<16>(b, s);
+    case 20: return svd_launch_batch_r<20>(b, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -153,6 +157,7 @@ cudaError_t launch_svd(const IterDesc& d, int Rpad, cudaStream_t s) {
     case 10: return svd_launch_r<10>(d, s);
     case 12: return svd_launch_r<12>(d, s);
     case 16: return svd_launch_r<16>(d, s);
+    case 20: return svd_launch_r<20>(d, s);
     default: return cudaErrorInvalidValue;
   }
 }

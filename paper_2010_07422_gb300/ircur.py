@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libircur.so")
 IRCUR_OK, IRCUR_EINVAL, IRCUR_ENOMEM, IRCUR_ECUDA = 0, 1, 2, 3
 IRCUR_ESVD_NOCONV, IRCUR_ETIMEOUT, IRCUR_ESTATE, IRCUR_ENOTSUP = 4, 5, 6, 7
 IRCUR_FLAG_WRANK, IRCUR_FLAG_SVD_NOCONV, IRCUR_FLAG_SVD_GAP = 1, 2, 4
-IRCUR_MAX_RANK = 16
+IRCUR_MAX_RANK = 20
 IRCUR_PRECISION_FP32, IRCUR_PRECISION_BF16_PANELS = 0, 1
 IRCUR_SVD_CLUSTER, IRCUR_SVD_ONE_CTA, IRCUR_SVD_CLUSTER8 = 0, 1, 2
 

@@ -58,7 +58,7 @@ def test_status_strings_and_param_validation_without_gpu(lib):
         return lib.ircur_create(ctypes.byref(ir.ircur_params(**base)), None, ctypes.byref(ctx))
 
     assert create(r=0) == ir.IRCUR_EINVAL
-    assert create(r=17) == ir.IRCUR_ENOTSUP
+    assert create(r=21) == ir.IRCUR_ENOTSUP
     assert create(gamma=1.0) == ir.IRCUR_EINVAL
     assert create(gamma=0.0) == ir.IRCUR_EINVAL
     assert create(tol=0.0) == ir.IRCUR_EINVAL

@@ -120,6 +120,36 @@ def test_ragged_shapes_parity(n1, n2, r, alpha, resample):
     assert rel(S, So) <= TOL_LS, rel(S, So)
 
 
+@pytest.mark.parametrize("n1,n2,r,m,resample", [
+    (1000, 1000, 20, 277, True),   # r = 20 of Fig. 1: |I| = |J| = ceil(2 r ln n)
+    (1000, 1000, 20, 415, False),  # c_I = 3: the largest rank-20 core that fits
+    (700, 900, 17, 300, True),     # padded rank 20, ragged
+])
+def test_rank_20_parity(n1, n2, r, m, resample):
+    p = synth.planted(n1, n2, r, 0.1, seed=n1 + r + m)
+    ref = oracle_run(p.D, r, max_iter=100, tol=1e-5, resample=resample, seed=3, nI=m, nJ=m)
+    K = ref.iters
+    s, res, L, S = gpu_solve(p.D, r, max_iter=K, resample=resample, seed=3, nI=m, nJ=m)
+    Lo, So = oracle.dense_outputs(p.D, ref)
+    assert res.iters == K
+    assert rel(L, Lo) <= TOL_LS, (rel(L, Lo), res.flags)
+    assert rel(S, So) <= TOL_LS, (rel(S, So), res.flags)
+    # no rank lost and no step cap; IRCUR_FLAG_SVD_GAP may report an early
+    # core whose sigma_20 / sigma_21 was narrow (outliers not yet removed)
+    assert res.flags & ~ir.IRCUR_FLAG_SVD_GAP == 0, res.flags
+
+
+def test_rank_20_limits():
+    """r = 21 is beyond the built ranks.  At r = 20 the core SVD's cluster of 16
+    CTAs holds a 415 x 415 core (c_I = 3 at n = 1000) in shared memory, not a
+    484 x 484 one (c_I = 3.5): ENOTSUP."""
+    with pytest.raises(RuntimeError, match="ENOTSUP"):
+        ir.IRCUR(1000, 1000, 21, nI=200, nJ=200)
+    with pytest.raises(RuntimeError, match="ENOTSUP"):
+        ir.IRCUR(1000, 1000, 20, nI=484, nJ=484)
+    ir.IRCUR(1000, 1000, 20, nI=415, nJ=415).close()
+
+
 def test_explicit_indices_padded_ld_and_unaligned_pointer():
     """Caller-supplied index sets (drawn by numpy), ldD > n2 and a D pointer
     that is 4- but not 16-byte aligned (the non-bulk row path)."""

@@ -1,7 +1,8 @@
 """Recovery outcomes of the phase-transition experiment (Sec. 4.1, Fig. 1) on
 the batched solver against the FP64 oracle, problem by problem.
 
-Setup of the supplement's synthetic tests: n = 1000, r = 5, outliers uniform
+Setup of the supplement's synthetic tests: n = 1000, r = 5 (and a smaller
+sample at r = 20, Fig. 1's third rank), outliers uniform
 in [-E|L|, E|L|], zeta_0 = 2 ||L||_inf, gamma = 0.65, stop at e_k <= 1e-5;
 success = ||L - L_true||_F / ||L_true||_F <= 1e-3.  The sample straddles the
 transition (c_I in {1.5, 3}, alpha in {0.1, 0.3, 0.45}, IRCUR-F and -R).  A
@@ -28,32 +29,33 @@ N, R = 1000, 5
 BOUND = 1e-3
 
 
-def cases():
+def cases(r, c_values, alphas, trials, seed_base=500):
     out = []
-    for c_I in (1.5, 3.0):
-        m = int(math.ceil(c_I * R * math.log(N)))
-        for alpha in (0.1, 0.3, 0.45):
-            for t in range(3):
+    for c_I in c_values:
+        m = int(math.ceil(c_I * r * math.log(N)))
+        for alpha in alphas:
+            for t in range(trials):
                 for resample in (False, True):
-                    out.append(dict(m=m, alpha=alpha, data_seed=500 + 10 * t + int(round(alpha * 100)),
+                    out.append(dict(m=m, alpha=alpha, data_seed=seed_base + 10 * t + int(round(alpha * 100)),
                                     seed=7 + t, resample=resample))
     return out
 
 
-def test_phase_transition_outcomes_match_oracle():
-    cs = cases()
+def outcomes(r, cs):
+    """Relative errors against the planted L of the oracle and of the batched
+    solve, problem by problem."""
     probs, Ds, Lts, errs_o = [], [], [], []
     for q in cs:
-        p = synth.planted(N, N, R, q["alpha"], seed=q["data_seed"], outlier_scale=1.0)
+        p = synth.planted(N, N, r, q["alpha"], seed=q["data_seed"], outlier_scale=1.0)
         Lt = p.L_true()
         z0 = 2.0 * float(np.abs(Lt).max())
-        ref = oracle.ircur(p.D, R, z0, 0.65, 1e-5, 100, nI=q["m"], nJ=q["m"], resample=q["resample"],
+        ref = oracle.ircur(p.D, r, z0, 0.65, 1e-5, 100, nI=q["m"], nJ=q["m"], resample=q["resample"],
                            seed=q["seed"])
         Lo, _ = oracle.dense_outputs(p.D, ref, with_sparse=False)
         errs_o.append(float(np.linalg.norm(Lo - Lt) / np.linalg.norm(Lt)))
         Ds.append(torch.from_numpy(p.D).cuda())
         Lts.append(torch.from_numpy(Lt).cuda())
-        probs.append(dict(n1=N, n2=N, r=R, nI=q["m"], nJ=q["m"], resample=q["resample"], seed=q["seed"],
+        probs.append(dict(n1=N, n2=N, r=r, nI=q["m"], nJ=q["m"], resample=q["resample"], seed=q["seed"],
                           zeta0=z0, gamma=0.65, tol=1e-5, max_iter=100))
     batch = ir.IRCURBatch(probs)
     batch.solve(Ds)
@@ -63,6 +65,10 @@ def test_phase_transition_outcomes_match_oracle():
         L = A.double() @ B.double()
         errs_g.append(float(torch.linalg.norm(L - Lts[i]) / torch.linalg.norm(Lts[i])))
     batch.close()
+    return errs_o, errs_g
+
+
+def check_classification(cs, errs_o, errs_g, unscored):
     scored = 0
     for q, eo, eg in zip(cs, errs_o, errs_g):
         if BOUND / 10 < eo < BOUND * 10:
@@ -71,6 +77,19 @@ def test_phase_transition_outcomes_match_oracle():
         assert (eg <= BOUND) == (eo <= BOUND), (q, eo, eg)
         if eo <= BOUND / 10:
             assert eg <= BOUND / 10, (q, eo, eg)
-    assert scored >= len(cs) - 6
+    assert scored >= len(cs) - unscored
+
+
+def test_phase_transition_outcomes_match_oracle():
+    cs = cases(R, (1.5, 3.0), (0.1, 0.3, 0.45), 3)
+    errs_o, errs_g = outcomes(R, cs)
+    check_classification(cs, errs_o, errs_g, 6)
     ok = [e <= BOUND for e in errs_o]
     assert any(ok) and not all(ok)  # the sample spans the transition
+
+
+def test_phase_transition_rank_20():
+    """The r = 20 panel of Fig. 1 at c_I = 1 and 2 (|I| = |J| = 139, 277)."""
+    cs = cases(20, (1.0, 2.0), (0.1, 0.3), 1, seed_base=20500)
+    errs_o, errs_g = outcomes(20, cs)
+    check_classification(cs, errs_o, errs_g, 2)
