@@ -32,9 +32,9 @@ constexpr int kGraphUnroll = IRCUR_GRAPH_UNROLL;
 constexpr int kTraceSlots = 4;
 
 // Panel-pass tiling: a tile is kPanelCols consecutive panel columns; a block
-// of kPassWarps warps computes one tile at a time, warp h owning share h of
-// the tile's row pairs and lane l column l.  Each tile leaves its (num, den)
-// partial sums in `partials`.
+// of kPassWarps warps computes one tile at a time, warp h owning row share h
+// and lane l the column pair 2 (l & 15), 2 (l & 15) + 1 on every other row.  Each tile leaves its (num, den) partial sums in
+// `partials`.
 constexpr int kPanelCols = 32;
 constexpr int kPassWarps = 16;
 constexpr int kSvdCluster = 8;  // CTAs (SMs) of the cluster form of the core SVD

@@ -81,7 +81,7 @@ struct PassLayout {
 
 __host__ __device__ inline size_t pass_layout_floats(int m, int rx, int nbuf, bool bf16, int nw) {
   const size_t tile = bf16 ? (size_t)m * kPanelCols / 2 : (size_t)m * kPanelCols;  // in floats
-  return (size_t)nbuf * tile + (bf16 ? (size_t)m * kPanelCols : 0) + 3 * (size_t)((m + 1) & ~1) * rx +
+  return (size_t)nbuf * tile + (bf16 ? (size_t)m * kPanelCols : 0) + 3 * (size_t)m * rx +
          (size_t)nw * rx * kPanelCols + (size_t)rx * kPanelCols + 4 * nw +
          (size_t)nbuf * ((size_t)kPanelCols * rx + kPanelCols) + 2 * (size_t)m;
 }
@@ -97,11 +97,10 @@ __device__ inline PassLayout pass_layout(unsigned char* smem, int m, int rx, int
   float* p = reinterpret_cast<float*>(smem + nbuf * L.tile_bytes);
   L.vbuf = bf16 ? p : nullptr;
   if (bf16) p += (size_t)m * kPanelCols;
-  const size_t mp = (size_t)((m + 1) & ~1);  // the small matrices hold an even number of rows
   L.side = p;
-  L.proj = p + mp * rx;
-  L.recon = p + 2 * mp * rx;
-  L.part = p + 3 * mp * rx;
+  L.proj = p + (size_t)m * rx;
+  L.recon = p + 2 * (size_t)m * rx;
+  L.part = p + 3 * (size_t)m * rx;
   L.outS = L.part + (size_t)nw * rx * kPanelCols;
   L.wsum = L.outS + (size_t)rx * kPanelCols;
   L.lvec = L.wsum + 4 * nw;  // 16-byte aligned: every piece above is a multiple of 4 floats
@@ -230,10 +229,6 @@ __device__ __forceinline__ void pass_stage_lane(const IterDesc& d, int k, int lt
   }
 }
 
-// Position of element (a, t) in the pair-interleaved small matrices (rows a,
-// a + 1 of column t side by side; see the tile work layout below).
-__device__ __forceinline__ int pass_pair_index(int a, int t, int RX) { return ((a >> 1) * RX + t) * 2 + (a & 1); }
-
 // The m x R side matrix of one segment, A_k(I,:) | B_k(:,J)^T: the compact
 // copies the previous pass wrote through the index maps (the same values the
 // core SVD used for L_k(I,J)), rows padded to RX columns with zeros.
@@ -242,10 +237,9 @@ __device__ __forceinline__ void pass_stage_side(const IterDesc& d, const PassLay
   constexpr int RX = (R + 3) & ~3;
   const int m = COL ? d.nJ : d.nI;
   const float* sideG = COL ? d.BJt[k & 1] : d.AI[k & 1];
-  const int mp = (m + 1) & ~1;
-  for (int q = threadIdx.x; q < mp * RX; q += blockDim.x) {
+  for (int q = threadIdx.x; q < m * RX; q += blockDim.x) {
     const int a = q / RX, t = q - a * RX;
-    L.side[pass_pair_index(a, t, RX)] = (t < R && a < m) ? sideG[(size_t)a * R + t] : 0.f;
+    L.side[q] = t < R ? sideG[(size_t)a * R + t] : 0.f;
   }
 }
 
@@ -277,95 +271,76 @@ __device__ __forceinline__ void pass_stage_proj(const IterDesc& d, const PassLay
   trace_start(d.trace, kTraceSlots * k + 3);  // the span after the wait for the SVD
   const int m = COL ? d.nJ : d.nI;
   const float* projG = COL ? d.Vs : d.W;
-  const int mp = (m + 1) & ~1;
-  for (int q = threadIdx.x; q < mp * RX; q += blockDim.x) {
+  for (int q = threadIdx.x; q < m * RX; q += blockDim.x) {
     const int a = q / RX, t = q - a * RX;
-    const bool in = t < R && a < m;
-    const int e = pass_pair_index(a, t, RX);
-    L.proj[e] = in ? projG[a * R + t] : 0.f;
-    if (COL) L.recon[e] = in ? d.V[a * R + t] : 0.f;
+    const bool in = t < R;
+    L.proj[q] = in ? projG[a * R + t] : 0.f;
+    if (COL) L.recon[q] = in ? d.V[a * R + t] : 0.f;
   }
   __syncthreads();
 }
 
-// Tile work layout: lane l of warp h owns column l of the tile and the row
-// pairs (a, a + 1), a = a0(h), a0(h) + 2, ... of the warp's share.  The m x R
-// small matrices (side, projection, reconstruction) are stored pair-interleaved
-// by rows: element (a, t) at ((a >> 1) RX + t) 2 + (a & 1), so one broadcast
-// 16-byte read gives two (row a, row a + 1) pairs and the r-wide products run
-// as packed FP32 pairs (ffma2) whose other operand, duplicated once per tile,
-// is the lane's column of the other factor or of the projections.  A missing
-// last row (odd m) reads as zero in the small matrices and is never read from
-// or written to the tile.
+// Tile work layout: lane l of warp h owns the column pair c0 = 2 (l & 15),
+// c0 + 1, and the rows a0(h) + (l >> 4), +2, +4, ... of the warp's row share,
+// so that each broadcast read of a row of the small matrices serves two
+// entries and the r-wide products run as packed FP32 pairs (ffma2).
 
-// The lane's column of the current iterate's other factor, B_k(:,j) (row
+// The pair's columns of the current iterate's other factor, B_k(:,j) (row
 // panel) or A_k(i,:)^T (column panel), from the tile's staged copy (zero past
-// the panel's last column), each value duplicated into a pair.
+// the panel's last column).
 template <int R, bool COL>
-__device__ __forceinline__ void pass_lane_vec(const float* lv, int c, float2 (&vec)[R]) {
+__device__ __forceinline__ void pass_pair_vec(const float* lv, int c0, float2 (&vec)[R]) {
 #pragma unroll
-  for (int t = 0; t < R; ++t) {
-    const float b = COL ? lv[c * R + t] : lv[t * kPanelCols + c];
-    vec[t] = make_float2(b, b);
-  }
+  for (int t = 0; t < R; ++t)
+    vec[t] = COL ? make_float2(lv[c0 * R + t], lv[(c0 + 1) * R + t])
+                 : *reinterpret_cast<const float2*>(lv + t * kPanelCols + c0);
 }
 
-// Rows a, a + 1 (a even) of a pair-interleaved small matrix as R pairs.
+// Row a of the small matrix M (RX floats a row) as R values.
 template <int R>
-__device__ __forceinline__ void pass_pair_rows(const float* M, int a, float2 (&v)[R]) {
+__device__ __forceinline__ void pass_row(const float* M, int a, float (&v)[R]) {
   constexpr int RX = (R + 3) & ~3;
-  const float4* q4 = reinterpret_cast<const float4*>(M + (size_t)(a >> 1) * RX * 2);
 #pragma unroll
-  for (int t2 = 0; t2 < RX / 2; ++t2) {
-    const float4 q = q4[t2];
-    if (2 * t2 < R) v[2 * t2] = make_float2(q.x, q.y);
-    if (2 * t2 + 1 < R) v[2 * t2 + 1] = make_float2(q.z, q.w);
+  for (int t4 = 0; t4 < RX / 4; ++t4) {
+    const float4 q = *reinterpret_cast<const float4*>(M + (size_t)a * RX + 4 * t4);
+    const float q4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (4 * t4 + e < R) v[4 * t4 + e] = q4[e];
   }
 }
 
-// Rows a, a + 1 of a tile, the lane's column: the panel entries d, L_k there
-// (per entry the same FMA chain as the core, element for element), and D - S
-// = D - T_zeta(D - L_k) written in place (BF16 panels: to the FP32 work
-// buffer).  Adds d^2 to den.  Columns past the panel's last are zero in the
-// tile and in the staged factor, so they give zero; row a + 1 = m gives zero.
+// Row a of a tile, the pair's columns: the panel entries d, L_k there (the
+// same FMA chain as the core, element for element), and D - S = D -
+// T_zeta(D - L_k) written in place (BF16 panels: to the FP32 work buffer).
+// Adds d^2 to den.  Columns past the panel's last are zero in the tile and in
+// the staged factor, so they give zero.
 template <int R, bool COL, bool BF>
-__device__ __forceinline__ float2 pass_entry_pair(const IterDesc& d, const PassLayout& L, float* tileS,
-                                                  const uint16_t* tileH, int a, int m, int c, int64_t j0,
-                                                  const float2 (&vec)[R], float zeta, float2& den) {
-  float2 sp[R];
-  pass_pair_rows<R>(L.side, a, sp);
-  float2 l = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int t = 0; t < R; ++t) l = ffma2(sp[t], vec[t], l);
-  const bool hi = a + 1 < m;
-  float* cell = tileS + (size_t)a * kPanelCols + c;
+__device__ __forceinline__ float2 pass_entry2(const IterDesc& d, const PassLayout& L, float* tileS,
+                                              const uint16_t* tileH, int a, int c0, int64_t j0,
+                                              const float2 (&vec)[R], float zeta, float2& den) {
+  float sr[R];
+  pass_row<R>(L.side, a, sr);
+  const float2 l = lowrank_entry2<R>(sr, vec);
+  float2* cell = reinterpret_cast<float2*>(tileS + (size_t)a * kPanelCols + c0);
   float2 dv;
   if (BF) {
     const int64_t ncolsTotal = COL ? d.n1 : d.n2;
-    const int64_t j = j0 + c;
-    auto fp32 = [&](int row) {
+    const uint32_t hv = *reinterpret_cast<const uint32_t*>(tileH + (size_t)a * kPanelCols + c0);
+    auto fp32 = [&](int c) {
+      const int64_t j = j0 + c;
       if (j >= ncolsTotal) return 0.f;
-      return COL ? d.D[j * d.ldD + d.J_all[row]] : d.D[(int64_t)d.I_all[row] * d.ldD + j];
+      return COL ? d.D[j * d.ldD + d.J_all[a]] : d.D[(int64_t)d.I_all[a] * d.ldD + j];
     };
-    dv.x = bf16_entry(tileH[(size_t)a * kPanelCols + c], l.x, zeta, [&]() { return fp32(a); });
-    dv.y = hi ? bf16_entry(tileH[(size_t)(a + 1) * kPanelCols + c], l.y, zeta, [&]() { return fp32(a + 1); })
-              : 0.f;
+    dv.x = bf16_entry((uint16_t)(hv & 0xffffu), l.x, zeta, [&]() { return fp32(c0); });
+    dv.y = bf16_entry((uint16_t)(hv >> 16), l.y, zeta, [&]() { return fp32(c0 + 1); });
   } else {
-    dv = make_float2(cell[0], hi ? cell[kPanelCols] : 0.f);
+    dv = *cell;
   }
-  const float2 v = make_float2(panel_value(dv.x, l.x, zeta), hi ? panel_value(dv.y, l.y, zeta) : 0.f);
-  cell[0] = v.x;
-  if (hi) cell[kPanelCols] = v.y;
+  const float2 v = make_float2(panel_value(dv.x, l.x, zeta), panel_value(dv.y, l.y, zeta));
+  *cell = v;
   den = ffma2(dv, dv, den);
   return v;
-}
-
-// The even row bounds of warp h's share of the tile's row pairs.
-template <int NW>
-__device__ __forceinline__ void pass_share(int m, int h, int& a0, int& a1) {
-  const int np = (m + 1) >> 1;
-  a0 = 2 * (h * np / NW);
-  a1 = 2 * ((h + 1) * np / NW);
 }
 
 // One tile, first half: the thresholded values D - S in place and this
@@ -377,15 +352,15 @@ __device__ __forceinline__ float pass_tile_threshold(const IterDesc& d, int k, f
   float* tileS = BF ? L.vbuf : reinterpret_cast<float*>(tileP);
   const uint16_t* tileH = reinterpret_cast<const uint16_t*>(tileP);
   const int m = COL ? d.nJ : d.nI;
-  const int c = threadIdx.x & 31, h = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, h = threadIdx.x >> 5;
+  const int c0 = 2 * (lane & 15), hr = lane >> 4;
   const int64_t j0 = (int64_t)lt * kPanelCols;
   float2 vec[R];
-  pass_lane_vec<R, COL>(lv, c, vec);
-  int a0, a1;
-  pass_share<NW>(m, h, a0, a1);
+  pass_pair_vec<R, COL>(lv, c0, vec);
+  const int a0 = h * m / NW, a1 = (h + 1) * m / NW;
   float2 den = make_float2(0.f, 0.f);
 #pragma unroll 2
-  for (int a = a0; a < a1; a += 2) pass_entry_pair<R, COL, BF>(d, L, tileS, tileH, a, m, c, j0, vec, zeta, den);
+  for (int a = a0 + hr; a < a1; a += 2) pass_entry2<R, COL, BF>(d, L, tileS, tileH, a, c0, j0, vec, zeta, den);
   return den.x + den.y;
 }
 
@@ -404,14 +379,14 @@ __device__ __forceinline__ void pass_tile_project(const IterDesc& d, int k, int 
   const int m = COL ? d.nJ : d.nI;
   const int64_t ncolsTotal = COL ? d.n1 : d.n2;
   const int nxt = (k & 1) ^ 1;
-  const int c = threadIdx.x & 31, h = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, h = threadIdx.x >> 5;
+  const int c0 = 2 * (lane & 15), hr = lane >> 4;
   const int64_t j0 = (int64_t)lt * kPanelCols;
   const float* proj = L.proj;
   const float* recon = COL ? L.recon : L.proj;
-  int a0, a1;
-  pass_share<NW>(m, h, a0, a1);
+  const int a0 = h * m / NW, a1 = (h + 1) * m / NW;
   float2 vec[R];
-  if (FUSE) pass_lane_vec<R, COL>(lv, c, vec);
+  if (FUSE) pass_pair_vec<R, COL>(lv, c0, vec);
   if (COL) {
     if (stage_proj) pass_stage_proj<R, true>(d, L, k);
   } else {
@@ -422,23 +397,24 @@ __device__ __forceinline__ void pass_tile_project(const IterDesc& d, int k, int 
 #pragma unroll
   for (int t = 0; t < R; ++t) acc[t] = make_float2(0.f, 0.f);
 #pragma unroll 2
-  for (int a = a0; a < a1; a += 2) {
-    float2 v;
-    if (FUSE) {
-      v = pass_entry_pair<R, COL, BF>(d, L, tileS, tileH, a, m, c, j0, vec, zeta, den2);
-    } else {
-      const float* cell = tileS + (size_t)a * kPanelCols + c;
-      v = make_float2(cell[0], a + 1 < m ? cell[kPanelCols] : 0.f);
-    }
-    float2 pp[R];
-    pass_pair_rows<R>(proj, a, pp);
+  for (int a = a0 + hr; a < a1; a += 2) {
+    const float2 v = FUSE ? pass_entry2<R, COL, BF>(d, L, tileS, tileH, a, c0, j0, vec, zeta, den2)
+                          : *reinterpret_cast<const float2*>(tileS + (size_t)a * kPanelCols + c0);
+    float pr[R];
+    pass_row<R>(proj, a, pr);
 #pragma unroll
-    for (int t = 0; t < R; ++t) acc[t] = ffma2(pp[t], v, acc[t]);
+    for (int t = 0; t < R; ++t) acc[t] = ffma2(make_float2(pr[t], pr[t]), v, acc[t]);
   }
-  // this warp's share of the lane's column: its even-row chain, then its
-  // odd-row chain
+  // the two half-warps' rows, then this warp's share of every column
 #pragma unroll
-  for (int t = 0; t < R; ++t) L.part[((size_t)h * RX + t) * kPanelCols + c] = acc[t].x + acc[t].y;
+  for (int t = 0; t < R; ++t) {
+    acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, 16);
+    acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, 16);
+  }
+  if (hr == 0) {
+#pragma unroll
+    for (int t = 0; t < R; ++t) *reinterpret_cast<float2*>(L.part + ((size_t)h * RX + t) * kPanelCols + c0) = acc[t];
+  }
   __syncthreads();
   // projections of every column: the NW share sums in a fixed order
   for (int q = threadIdx.x; q < R * kPanelCols; q += blockDim.x) {
@@ -454,54 +430,54 @@ __device__ __forceinline__ void pass_tile_project(const IterDesc& d, int k, int 
   __syncthreads();
   float2 out[R];
 #pragma unroll
-  for (int t = 0; t < R; ++t) {
-    const float o = L.outS[(size_t)t * kPanelCols + c];
-    out[t] = make_float2(o, o);
-  }
+  for (int t = 0; t < R; ++t) out[t] = *reinterpret_cast<const float2*>(L.outS + (size_t)t * kPanelCols + c0);
   float2 num2 = make_float2(0.f, 0.f);
 #pragma unroll 2
-  for (int a = a0; a < a1; a += 2) {
-    const float* cell = tileS + (size_t)a * kPanelCols + c;
-    const float2 v = make_float2(cell[0], a + 1 < m ? cell[kPanelCols] : 0.f);
-    float2 rr[R];
-    pass_pair_rows<R>(recon, a, rr);
+  for (int a = a0 + hr; a < a1; a += 2) {
+    const float2 v = *reinterpret_cast<const float2*>(tileS + (size_t)a * kPanelCols + c0);
+    float rr[R];
+    pass_row<R>(recon, a, rr);
     float2 w = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int t = 0; t < R; ++t) w = ffma2(rr[t], out[t], w);
+    for (int t = 0; t < R; ++t) w = ffma2(make_float2(rr[t], rr[t]), out[t], w);
     const float2 e = make_float2(v.x - w.x, v.y - w.y);
     num2 = ffma2(e, e, num2);
   }
-  if (h == 0) {
-    // the next iteration's factor entries of the lane's row (column), and the
-    // index map entry of it
+  if (h == 0 && hr == 0) {
+    // the next iteration's index map entries of the pair's rows (columns)
     const int dnext = d.resample ? k + 1 : 0;
     const unsigned tag_next = (unsigned)(dnext + 1);
-    const int64_t j = j0 + c;
-    if (j < ncolsTotal) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t j = j0 + c0 + u;
+      if (j >= ncolsTotal) continue;
+      float o[R];
+#pragma unroll
+      for (int t = 0; t < R; ++t) o[t] = u ? out[t].y : out[t].x;
       if (COL) {
         float* An = d.A[nxt];
 #pragma unroll
-        for (int t = 0; t < R; ++t) An[j * R + t] = out[t].x;
+        for (int t = 0; t < R; ++t) An[j * R + t] = o[t];
       } else {
         float* Bn = d.B[nxt];
 #pragma unroll
-        for (int t = 0; t < R; ++t) Bn[(int64_t)t * d.n2 + j] = out[t].x;
+        for (int t = 0; t < R; ++t) Bn[(int64_t)t * d.n2 + j] = o[t];
       }
       // rows (columns) in the next iteration's index set also go to its
       // compact side matrix, at their position in the set
-      const unsigned pos_next = lp[c];
+      const unsigned pos_next = lp[c0 + u];
       if (index_tag_is(pos_next, tag_next)) {
         float* side = COL ? d.AI[nxt] : d.BJt[nxt];
         const int a = index_tag_pos(pos_next);
 #pragma unroll
-        for (int t = 0; t < R; ++t) side[(size_t)a * R + t] = out[t].x;
+        for (int t = 0; t < R; ++t) side[(size_t)a * R + t] = o[t];
       }
     }
   }
   // this share's sums; the tile's slot gets them in share order after the
   // block's end-of-tile barrier (pass_tile_sums)
   const float sn = warp_sum(num2.x + num2.y), sd = warp_sum(den_in + (den2.x + den2.y));
-  if (c == 0) {
+  if (lane == 0) {
     L.wsum[2 * h + 0] = sn;
     L.wsum[2 * h + 1] = sd;
   }
@@ -809,8 +785,7 @@ __device__ __forceinline__ void pass_persistent(const IterDesc& d1, const IterDe
 }
 
 // NW warps per block; two blocks per SM up to R = 7 (64 registers a thread),
-// one above (the row-pair layout keeps 4R FP32 values of the lane's column
-// live: its duplicated factor or projection column and the pair sums).
+// one above (the pair layout keeps 4R FP32 values of the two columns live).
 template <int R, bool BF, int NW>
 __global__ void __launch_bounds__(32 * NW, R <= 7 ? 2 : 1) pass_kernel(IterDesc d, int nbuf) {
   extern __shared__ __align__(16) unsigned char smem[];
