@@ -415,8 +415,10 @@ static ircur_status read_state(ircur_ctx* c) {
 // Everything of a solve before the iteration loop: descriptor for this D,
 // state reset, index sets, zeta_0 = max|D| (and D^T for IRCUR-R), the fixed
 // panels of IRCUR-F, A_0 = B_0 = 0.  Returns the descriptor in c->desc.
+// scanned: the caller has already reset the state and run the scan of D
+// (max|D|, the NaN/Inf check and, for IRCUR-R, D^T) on this stream.
 static ircur_status solve_prologue(ircur_ctx* c, const float* D, int64_t ldD, const int32_t* idx_I,
-                                   const int32_t* idx_J, cudaStream_t s) {
+                                   const int32_t* idx_J, cudaStream_t s, bool scanned = false) {
   const ircur_params& p = c->p;
   if (ldD < p.n2 || (reinterpret_cast<uintptr_t>(D) & 3)) return IRCUR_EINVAL;
   if ((idx_I == nullptr) != (idx_J == nullptr)) return IRCUR_EINVAL;
@@ -437,7 +439,7 @@ static ircur_status solve_prologue(ircur_ctx* c, const float* D, int64_t ldD, co
   }
 
   const double zeta0 = p.zeta0 > 0 ? p.zeta0 : 0.0;
-  IRCUR_CK(launch_setup(d, zeta0, s));
+  if (!scanned) IRCUR_CK(launch_setup(d, zeta0, s));
   // index maps start empty; A_0 = B_0 = 0, so A_0(I,:) and B_0(:,J) too
   const int nmap = p.resample ? 2 : 1;
   for (int q = 0; q < nmap; ++q) {
@@ -462,10 +464,10 @@ static ircur_status solve_prologue(ircur_ctx* c, const float* D, int64_t ldD, co
     IRCUR_CK(launch_sample(p.seed, 0, first_draws, p.n1, p.n2, p.nI, p.nJ, c->I_all, c->J_all, -1, s, c->posI,
                            c->posJ));
   }
-  if (p.resample) {
+  if (!scanned && p.resample) {
     // D^T for the column panels, with max|D| and the NaN/Inf scan in the same pass
     IRCUR_CK(launch_transpose_maxabs(D, p.n1, p.n2, ldD, c->DT, c->ldDT, c->st, s));
-  } else if (!(p.zeta0 > 0)) {
+  } else if (!scanned && !(p.zeta0 > 0)) {
     IRCUR_CK(launch_maxabs(D, p.n1, p.n2, ldD, c->st, s));
   }
   if (!(p.zeta0 > 0)) IRCUR_CK(launch_finalize_zeta(c->st, s));
@@ -496,11 +498,11 @@ static ircur_status solve_epilogue(ircur_ctx* c, ircur_result* out) {
   return IRCUR_OK;
 }
 
-extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, const int32_t* idx_I,
-                                    const int32_t* idx_J, ircur_result* out) {
+static ircur_status solve_impl(ircur_ctx* c, const float* D, int64_t ldD, const int32_t* idx_I,
+                               const int32_t* idx_J, ircur_result* out, bool scanned) {
   if (!c || !D || !out) return IRCUR_EINVAL;
   const ircur_params& p = c->p;
-  ircur_status ps = solve_prologue(c, D, ldD, idx_I, idx_J, c->stream);
+  ircur_status ps = solve_prologue(c, D, ldD, idx_I, idx_J, c->stream, scanned);
   if (ps != IRCUR_OK) return ps;
   const IterDesc& d = c->desc;
   cudaStream_t s = c->stream;
@@ -559,6 +561,11 @@ extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, c
   ircur_status rs = read_state(c);
   if (rs != IRCUR_OK) return rs;
   return solve_epilogue(c, out);
+}
+
+extern "C" ircur_status ircur_solve(ircur_ctx* c, const float* D, int64_t ldD, const int32_t* idx_I,
+                                    const int32_t* idx_J, ircur_result* out) {
+  return solve_impl(c, D, ldD, idx_I, idx_J, out, false);
 }
 
 extern "C" ircur_status ircur_set_record(ircur_ctx* c, int32_t enable) {
@@ -850,9 +857,12 @@ extern "C" ircur_status ircur_reconstruct(ircur_ctx* c, const float* D, int64_t 
 }
 
 // Host-memory entry point.  The copies are pipelined over four copy streams:
-// D goes up in row chunks (the solve waits for all of them), and L and S are
+// D goes up in row chunks, each scanned as soon as it has landed (max|D|, the
+// NaN/Inf check and, for IRCUR-R, its columns of D^T) while the next chunks
+// are still on their way; the iterations wait for all of them.  L and S are
 // reconstructed chunk by chunk, each chunk's rows going back while the next
-// chunk is computed.
+// chunk is computed.  Chunks start on multiples of 64 rows (the transpose's
+// tile), so that every chunk's part of D^T starts on a 16-byte boundary.
 extern "C" ircur_status ircur_solve_host(ircur_ctx* c, const float* D_host, float* L_host, float* S_host,
                                          ircur_result* out) {
   if (!c || !D_host || !L_host || !out) return IRCUR_EINVAL;
@@ -881,7 +891,9 @@ extern "C" ircur_status ircur_solve_host(ircur_ctx* c, const float* D_host, floa
     }
   }
   const int64_t n2 = p.n2;
-  const int64_t rows = (p.n1 + kChunks - 1) / kChunks;
+  const int64_t rows = ((p.n1 + kChunks - 1) / kChunks + 63) / 64 * 64;
+  // the state reset comes before the first scan (the scans accumulate max|D|)
+  IRCUR_CK(launch_setup(c->desc, p.zeta0 > 0 ? p.zeta0 : 0.0, c->stream));
   // D up: the copy streams start after earlier work on the context's stream
   IRCUR_CK(cudaEventRecord(c->hev[2 * kChunks], c->stream));
   for (int q = 0; q < kChunks; ++q) {
@@ -893,8 +905,12 @@ extern "C" ircur_status ircur_solve_host(ircur_ctx* c, const float* D_host, floa
     IRCUR_CK(cudaMemcpyAsync(c->hD + r0 * n2, D_host + r0 * n2, (size_t)nr * n2 * 4, cudaMemcpyHostToDevice, cs));
     IRCUR_CK(cudaEventRecord(c->hev[q], cs));
     IRCUR_CK(cudaStreamWaitEvent(c->stream, c->hev[q], 0));
+    if (p.resample)
+      IRCUR_CK(launch_transpose_maxabs(c->hD + r0 * n2, nr, n2, n2, c->DT + r0, c->ldDT, c->st, c->stream));
+    else if (!(p.zeta0 > 0))
+      IRCUR_CK(launch_maxabs(c->hD + r0 * n2, nr, n2, n2, c->st, c->stream));
   }
-  ircur_status s = ircur_solve(c, c->hD, n2, nullptr, nullptr, out);
+  ircur_status s = solve_impl(c, c->hD, n2, nullptr, nullptr, out, true);
   if (s != IRCUR_OK) return s;
   // L (and S) down, chunk by chunk behind the reconstruction
   const int K = c->host_state.k;

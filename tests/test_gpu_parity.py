@@ -212,6 +212,29 @@ def test_host_memory_entry_point_matches_device_path():
     assert np.array_equal(Lh.astype(np.float64), L) and np.array_equal(Sh.astype(np.float64), S)
 
 
+@pytest.mark.parametrize("n1,n2,resample", [(700, 640, False), (1000, 333, True), (64, 500, True)])
+def test_host_entry_point_chunked_scan(n1, n2, resample):
+    """The host path scans D chunk by chunk as the chunks land (max|D|, the
+    NaN/Inf check, D^T for IRCUR-R; chunks on 64-row boundaries, a ragged last
+    one, fewer rows than chunks): the same result as the device path, bit for
+    bit, and a NaN in a late chunk is still rejected."""
+    p = synth.planted(n1, n2, 3, 0.1, seed=n1 + n2)
+    s, res, L, S = gpu_solve(p.D, 3, max_iter=100, tol=1e-5, resample=resample, seed=6)
+    s2 = ir.IRCUR(n1, n2, 3, tol=1e-5, resample=resample, seed=6)
+    Lh = np.empty((n1, n2), np.float32)
+    Sh = np.empty((n1, n2), np.float32)
+    r2 = ir.ircur_solve_host(s2._ctx, np.ascontiguousarray(p.D), Lh, Sh)
+    assert r2.iters == res.iters and r2.zeta0 == res.zeta0
+    assert np.array_equal(Lh.astype(np.float64), L) and np.array_equal(Sh.astype(np.float64), S)
+    bad = np.ascontiguousarray(p.D).copy()
+    bad[n1 - 1, n2 // 2] = np.inf
+    with pytest.raises(ir.IrcurError) as ei:
+        ir.ircur_solve_host(s2._ctx, bad, Lh, Sh)
+    assert ei.value.status == ir.IRCUR_EINVAL
+    r3 = ir.ircur_solve_host(s2._ctx, np.ascontiguousarray(p.D), Lh, Sh)
+    assert r3.iters == res.iters and np.array_equal(Lh.astype(np.float64), L)
+
+
 # ---------------------------------------------------------------- errors and faults
 def test_nonfinite_D_and_bad_indices_are_rejected_and_context_reusable():
     p = synth.planted(200, 200, 2, 0.1, seed=10)
