@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_small_kernel(AdjStep a) {
   }
   __syncthreads();
   if (threadIdx.x < R) a.sig[threadIdx.x] = ss[threadIdx.x];
-  if (threadIdx.x < R * R) a.Pm[threadIdx.x] = Ps[threadIdx.x];
+  for (int q = threadIdx.x; q < R * R; q += blockDim.x) a.Pm[q] = Ps[q];  // R * R may exceed the block
   for (int q = threadIdx.x; q < a.nI * R; q += blockDim.x) {
     const int row = q / R, p = q - row * R;
     float s = 0.f;

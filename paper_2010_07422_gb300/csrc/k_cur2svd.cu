@@ -105,8 +105,11 @@ __device__ void c2s_backsolve(const double* U, const double* Y, int r, double* X
 // M = R_A R_B^T, its SVD by one-sided Jacobi (lane p owns column p of M and of
 // the rotation Q), and the r x r maps T_A = R_A^{-1} P, T_B = R_B^{-1} Q with
 // the singular values sorted in descending order.
+// (launched with R * R threads, at least a warp: the bound keeps R = 20's 400
+// threads within the register file)
 template <int R>
-__global__ void c2s_small_kernel(const double* __restrict__ part, int nbA, int nbB, int r, float* __restrict__ sigma,
+__global__ void __launch_bounds__(R * R < 32 ? 32 : R * R)
+    c2s_small_kernel(const double* __restrict__ part, int nbA, int nbB, int r, float* __restrict__ sigma,
                                  float* __restrict__ TA, float* __restrict__ TB) {
   __shared__ double GA[R * R], GB[R * R], RA[R * R], RB[R * R], P[R * R], Q[R * R], XA[R * R], XB[R * R];
   __shared__ double sg[R];
@@ -224,9 +227,9 @@ __global__ void c2s_apply_kernel(const float* __restrict__ A, int64_t n1, const 
                                  int r, const float* __restrict__ TA, const float* __restrict__ TB,
                                  float* __restrict__ W, float* __restrict__ V) {
   __shared__ float ta[R * R], tb[R * R];
-  if (threadIdx.x < R * R) {
-    ta[threadIdx.x] = TA[threadIdx.x];
-    tb[threadIdx.x] = TB[threadIdx.x];
+  for (int q = threadIdx.x; q < R * R; q += blockDim.x) {  // R * R may exceed the block
+    ta[q] = TA[q];
+    tb[q] = TB[q];
   }
   __syncthreads();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

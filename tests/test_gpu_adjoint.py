@@ -105,6 +105,21 @@ def test_backward_matches_oracle_gradient(n1, n2, r, T, alpha, seed, which):
     s.close()
 
 
+def test_backward_rank_20():
+    """r = 18 (padded rank 20) with |I| = |J| = 240: the same gradient parity."""
+    n1, n2, r, T, seed = 600, 560, 18, 5, 6
+    p, D, s, res, I, J = setup(n1, n2, r, T, 0.1, seed, nI=240, nJ=240)
+    assert res.iters == T and res.flags & ~ir.IRCUR_FLAG_SVD_GAP == 0
+    rng = np.random.default_rng(seed)
+    dL = rng.standard_normal((n1, n2)).astype(np.float32)
+    dS = rng.standard_normal((n1, n2)).astype(np.float32)
+    g = s.backward(D, torch.from_numpy(dL).cuda(), torch.from_numpy(dS).cuda())
+    keep, _ = gpu_final_keep(p, D, s, I, J, r, T, res.zeta0)
+    G = adj.unrolled_vjp(p.D.astype(np.float64), I, J, r, res.zeta0, 0.7, T, dL, dS, final_keep=keep)
+    assert rel(g.double().cpu().numpy(), G) <= TOL_GRAD, rel(g.double().cpu().numpy(), G)
+    s.close()
+
+
 def test_backward_at_training_size_properties():
     """n = 4096, r = 10, T = 15, |I| = |J| = ceil(40 ln 4096) = 333: the gradient of
     <dL, L> is supported on rows I and columns J, is finite, and is linear in dL."""

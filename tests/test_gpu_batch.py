@@ -120,6 +120,24 @@ def test_batch_mixed_ranks_match_oracle():
     batch.close()
 
 
+def test_batch_with_rank_20_group():
+    """Ranks 3 and 20 (two rank groups: the two-phase iteration with the
+    separate look-ahead draws), IRCUR-R and -F: each instance equals its lone
+    solve bit for bit."""
+    probs = [dict(n1=900, n2=800, r=20, nI=250, nJ=260, resample=True, seed=1),
+             dict(n1=500, n2=700, r=3, resample=True, seed=2),
+             dict(n1=820, n2=760, r=17, nI=230, nJ=230, resample=False, seed=3)]
+    Ds = [to_dev(synth.planted(q["n1"], q["n2"], q["r"], 0.1, seed=40 + i).D) for i, q in enumerate(probs)]
+    batch = ir.IRCURBatch([dict(q, tol=1e-5, max_iter=100) for q in probs])
+    got = batch.solve(Ds)
+    for i, (q, D) in enumerate(zip(probs, Ds)):
+        res, A, B, L, S = lone(D, dict(q, tol=1e-5, max_iter=100))
+        assert (got[i].iters, got[i].final_err) == (res.iters, res.final_err)
+        Lb, Sb = batch[i].reconstruct(D)
+        assert np.array_equal(Lb.cpu().numpy(), L) and np.array_equal(Sb.cpu().numpy(), S)
+    batch.close()
+
+
 def test_batch_replay_rebuild_and_host_loop(monkeypatch):
     """Replaying the recorded graph, recording a new one for new D pointers, and
     the host-driven loop all give the same results."""

@@ -25,13 +25,13 @@ from paper_2010_07422_gb300 import synth  # noqa: E402
     (450, 470, 11, 0.05, True),   # padded rank 12
     (10000, 10000, 5, 0.1, True),  # the benchmark's size
 ])
-def test_cur_to_svd_matches_oracle(n1, n2, r, alpha, resample):
+def test_cur_to_svd_matches_oracle(n1, n2, r, alpha, resample, m=None):
     p = synth.planted(n1, n2, r, alpha, seed=n1 + r)
-    ref = oracle.ircur(p.D, r, 0.0, 0.7, 1e-5, 100, resample=resample, seed=3)
+    ref = oracle.ircur(p.D, r, 0.0, 0.7, 1e-5, 100, resample=resample, seed=3, nI=m, nJ=m)
     Wo, so, Vo = oracle.cur_to_svd(ref.C, ref.U_pinv, ref.R)
     Wo, so, Vo = Wo[:, :r], so[:r], Vo[:, :r]
     D = torch.from_numpy(p.D).cuda()
-    s = ir.IRCUR(n1, n2, r, tol=1e-12, max_iter=ref.iters, resample=resample, seed=3)
+    s = ir.IRCUR(n1, n2, r, nI=m or 0, nJ=m or 0, tol=1e-12, max_iter=ref.iters, resample=resample, seed=3)
     res = s.solve(D)
     assert res.iters == ref.iters
     W, sig, V = (t.double().cpu().numpy() for t in s.svd())
@@ -46,6 +46,11 @@ def test_cur_to_svd_matches_oracle(n1, n2, r, alpha, resample):
     assert np.all(np.abs(np.sum(W * Wo, axis=0)) >= 1 - 1e-4)
     assert np.all(np.abs(np.sum(V * Vo, axis=0)) >= 1 - 1e-4)
     s.close()
+
+
+def test_cur_to_svd_rank_20():
+    """r = 20 (Fig. 1's third rank) with |I| = |J| = 277 at n = 1000."""
+    test_cur_to_svd_matches_oracle(1000, 1000, 20, 0.1, True, m=277)
 
 
 def test_cur_to_svd_needs_a_solve():

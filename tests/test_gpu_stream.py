@@ -28,7 +28,7 @@ def setup(n1, n2, c, r, alpha, resample, seed, **kw):
     p = synth.planted(n1, n2 + c, r, alpha, seed=seed)
     D = np.ascontiguousarray(p.D[:, :n2])
     Dn = np.ascontiguousarray(p.D[:, n2:])
-    ref = oracle.ircur(D, r, 0.0, 0.7, 1e-5, 100, resample=resample, seed=seed)
+    ref = oracle.ircur(D, r, 0.0, 0.7, 1e-5, 100, resample=resample, seed=seed, nI=kw.get("nI"), nJ=kw.get("nJ"))
     s = ir.IRCUR(n1, n2, r, tol=1e-12, max_iter=ref.iters, resample=resample, seed=seed, **kw)
     res = s.solve(torch.from_numpy(D).cuda())
     assert res.iters == ref.iters
@@ -54,6 +54,17 @@ def test_stream_matches_oracle(n1, n2, c, r, alpha, resample, iters):
     if not iters:  # with the solve's iteration count the new columns' planted part is recovered
         Lt = (p.W @ p.V.T)[:, n2:]
         assert rel(Lg, Lt) <= 1e-3
+    s.close()
+
+
+def test_stream_rank_20():
+    """r = 20 with |I| = |J| = 277: the streamed columns against the oracle."""
+    n1, n2, c, r = 1000, 900, 50, 20
+    p, D, Dn, ref, s = setup(n1, n2, c, r, 0.1, False, seed=31, nI=277, nJ=277)
+    Lo, So = oracle.stream_columns(Dn, ref, ref.zetas[0], 0.7, ref.iters)
+    L, S = s.stream_columns(torch.from_numpy(Dn).cuda())
+    assert rel(L.double().cpu().numpy(), Lo) <= TOL
+    assert rel(S.double().cpu().numpy(), So) <= TOL
     s.close()
 
 
