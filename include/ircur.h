@@ -118,7 +118,9 @@ typedef struct ircur_ctx ircur_ctx;
  * allocate its device workspace (about 4*(n1 + n2)*(2r + |J| + |I|) bytes
  * plus max_iter*(|I|+|J|)*4 bytes of index sets).  stream: a cudaStream_t
  * (NULL = legacy default stream).  Returns EINVAL for out-of-range
- * parameters, ENOTSUP for r > IRCUR_MAX_RANK, an unknown precision or BF16 panels
+ * parameters, ENOTSUP for r > IRCUR_MAX_RANK, for |I|, |J| whose core or panel
+ * tiles do not fit the GPU's shared memory at the padded rank (at r = 20 a
+ * core of about 440 x 440 is the largest), an unknown precision or BF16 panels
  * with resample != 0, ENOMEM if
  * the workspace cannot be allocated.  *out is NULL on failure. */
 ircur_status ircur_create(const ircur_params* params, void* stream, ircur_ctx** out);
