@@ -101,7 +101,8 @@ def dram_traffic(kernel, workload_tag):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms in the background,
+    each sample stamped with the host clock when it is read."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -114,7 +115,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
                  "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -123,9 +124,12 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
+        """Statistics of the samples read between host times t0 and t1 (the timed
+        region, widened by one sampling period each side); of every sample since
+        start() (warm-up and timed region) if none fell inside."""
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -136,7 +140,13 @@ class ClockSampler:
         self.t.join(timeout=2)
         sm, smax, reasons = [], [], set()
         names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines
+        window = "warm-up and timed region"
+        if t0 is not None:
+            inside = [x for x in self.lines if t0 - 0.05 <= x[0] <= t1 + 0.05]
+            if inside:
+                lines, window = inside, "timed region"
+        for _, ln in lines:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -150,7 +160,7 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": float(max(smax)) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "window": window}
 
 
 def rank_seed(seed, rank):
@@ -532,6 +542,9 @@ def main():
         solver.reconstruct(D, L=L, S=S)
         return res
 
+    # clocks sampled from the warm-up on (nvidia-smi takes a while to report)
+    clk = ClockSampler(local)
+    clk.start()
     for _ in range(max(3, a.warmup)):
         step()
     # pass-kernel launch shape chosen by timing whole solves (ircur_autotune)
@@ -544,8 +557,7 @@ def main():
     barrier()
     torch.cuda.synchronize()
 
-    clk = ClockSampler(local)
-    clk.start()
+    t_host0 = time.perf_counter()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     rec = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
@@ -566,7 +578,7 @@ def main():
         svd_steps += res.svd_steps
     ev1.record(stream)
     torch.cuda.synchronize()
-    clocks = clk.stop()
+    clocks = clk.stop(t_host0, time.perf_counter())
     barrier()
     total_ms = ev0.elapsed_time(ev1)
     recon_ms = [s.elapsed_time(e) for s, e in rec]
